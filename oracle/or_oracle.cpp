@@ -1,0 +1,583 @@
+// Oracle (test infrastructure only; never linked into the product path).
+//
+// A plain, slow FP64 CPU implementation of the forward ray-tracing method of
+// "Generalized Ray Tracing for Axions in Astrophysical Plasmas" (McDonald &
+// Witte): sampling of the resonant conversion surface and the per-ray power
+// weight (Sec. 3-4, Eqs. AxionCollInt, ForwardTracingEquation1, PowerCurved,
+// CPAnisoCurved, AngleDefAniso, GaussianDist), integration of Hamilton's
+// equations (Eq. Hamilton with Eq. StrongBHam) to a large radius, binning of
+// the escaped power on the sky and in frequency (Sec. 2.2), and the backward
+// image-plane estimator (Sec. 2.1, Eq. BackPower, and the multiple level
+// crossings of Sec. 5.1.3).  Only the tests, the smoke check and the CPU
+// baseline of the benchmark load this library.
+#include <atomic>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "or_dopri.hpp"
+#include "or_model.hpp"
+
+namespace orc {
+
+enum {
+  RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,
+  RAY_NAN = 5, RAY_STIFF = 6, RAY_LAMBDA_END = 7
+};
+
+// Trace options vector layout (shared with the Python wrapper of the oracle).
+enum { TO_RTOL = 0, TO_ATOL, TO_R_OUT, TO_MAX_STEPS, TO_LAMBDA_MAX, TO_R_CAPTURE, TO_COUNT };
+
+struct TraceOpts {
+  double rtol, atol, r_out, lambda_max, r_capture;
+  long max_steps;
+};
+
+inline TraceOpts make_opts(const double* t) {
+  TraceOpts o;
+  o.rtol = t[TO_RTOL];
+  o.atol = t[TO_ATOL];
+  o.r_out = t[TO_R_OUT];
+  o.max_steps = (long)t[TO_MAX_STEPS];
+  o.lambda_max = t[TO_LAMBDA_MAX];
+  o.r_capture = t[TO_R_CAPTURE];
+  return o;
+}
+
+static inline double norm3(const double v[3]) {
+  return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Axion speed at infinity.  Eq. GaussianDist gives the Maxwellian
+// f ~ exp(-|k|^2 / k0^2); the speed x = |k_inf| / k0 then has density
+// (4/sqrt(pi)) x^2 exp(-x^2) and CDF erf(x) - (2/sqrt(pi)) x exp(-x^2).
+// Inverted by bisection.  Eq. fa_approx's monochromatic option gives x = 1.
+static double maxwell_speed(int fa_model, double u) {
+  if (fa_model == FA_DELTA) return 1.0;
+  const double c = 2.0 / std::sqrt(units::PI);
+  double lo = 0.0, hi = 30.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double F = std::erf(mid) - c * mid * std::exp(-mid * mid);
+    if (F < u) lo = mid; else hi = mid;
+    if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// ---------------------------------------------------------------------------
+// Kinematic resonance (Sec. 2.4 and Sec. 4: k^a_mu = k^gamma_mu).  Along the
+// radial line through direction n, with the orthonormal-frame direction khat
+// of the momentum and the Killing energy omega_inf = -k_t held fixed, the
+// axion has local |k|^2 = omega_inf^2 / A(r) - m_a^2 and energy
+// E_a = omega_inf / sqrt(A); the photon with the same k has the LO energy.
+// h(r) = E_gamma - E_a vanishes on the leaf of the foliation of Eq.
+// Hypersurfaces that this (khat, omega_inf) selects.
+template <class T>
+static T resonance_h(const Star& s, const double m[3], const double n[3], const double khat[3],
+                     double omega_inf, T r, T* E_out = nullptr, T* K2_out = nullptr,
+                     T* wp2_out = nullptr, T* cos2_out = nullptr) {
+  T A = 1.0 - s.rs / r;
+  T K2 = omega_inf * omega_inf / A - 1.0;  // local axion |k|^2 / m_a^2
+  T Ea = sqrt(1.0 + K2);
+  T x[3] = {r * n[0], r * n[1], r * n[2]};
+  T wp2 = plasma_freq2(s, m, x);
+  T B[3];
+  dipole_field(m, x, B);
+  T Bn = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  T kb = (khat[0] * B[0] + khat[1] * B[1] + khat[2] * B[2]) / Bn;
+  T cos2 = kb * kb;
+  T Eg = photon_energy(s.dispersion, K2, wp2, cos2);
+  if (E_out) *E_out = Ea;
+  if (K2_out) *K2_out = K2;
+  if (wp2_out) *wp2_out = wp2;
+  if (cos2_out) *cos2_out = cos2;
+  return Eg - Ea;
+}
+
+// Root of h on (1, inf) (units of R): h(1) > 0 is required (the photon is
+// heavier than the axion at the surface); the bracket is widened by doubling
+// until h < 0 and then bisected to the last representable digit.  h is
+// monotone along the radial line for the Goldreich-Julian profile outside the
+// surface, so the root is unique.
+static bool resonance_root(const Star& s, const double m[3], const double n[3],
+                           const double khat[3], double omega_inf, double* r_out) {
+  double lo = 1.0;
+  if (!(resonance_h<double>(s, m, n, khat, omega_inf, lo) > 0.0)) return false;
+  double hi = 2.0;
+  int it = 0;
+  while (!(resonance_h<double>(s, m, n, khat, omega_inf, hi) < 0.0)) {
+    lo = hi;
+    hi *= 2.0;
+    if (++it > 60) return false;
+  }
+  for (int k = 0; k < 400; ++k) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (resonance_h<double>(s, m, n, khat, omega_inf, mid) > 0.0) lo = mid; else hi = mid;
+  }
+  *r_out = 0.5 * (lo + hi);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// One forward sample and its weight.  The power of Eq. PowerCurved, with the
+// divergence of P_agamma cancelled against cos(theta_n) (Eq. AngleDefAniso,
+// Eq. CPAnisoCurved), is the phase-space integral
+//   P = int d^3k_loc int dV  A^{1/2} delta(E_gamma - E_a) Psi f_a ,
+//   Psi = (pi/2) g^2 |B|^2 (E^4 sin^2 th_B / D) E,
+//   D = cos^2 th_B w_p^2 (w_p^2 - 2E^2) + E^4,
+// where dV is the proper volume, d^3k_loc the orthonormal-frame momentum
+// volume, and A^{1/2} the time dilation dt -> sqrt|g_tt| dt (the A^{1/2}
+// prefactor of sqrt|h_k|).  The isotropic plasma uses Psi = (pi/2) g^2 |B|^2
+// sin^2 th_B E (Eq. ProbIsoCurved with its power of E made dimensionally
+// consistent).  Samples: direction n uniform on the sphere, khat uniform on
+// the sphere, |k_inf| from the Maxwellian, and the resonance root r* along n.
+static void sample_one(const Star& s, const double u[6], long N, double st[8], double* w,
+                       unsigned char* status) {
+  using units::PI;
+  const double ct = 1.0 - 2.0 * u[0];
+  const double stt = std::sqrt(std::fmax(0.0, (1.0 - ct) * (1.0 + ct)));
+  const double ph = 2.0 * PI * u[1];
+  const double n[3] = {stt * std::cos(ph), stt * std::sin(ph), ct};
+  const double ck = 1.0 - 2.0 * u[2];
+  const double sk = std::sqrt(std::fmax(0.0, (1.0 - ck) * (1.0 + ck)));
+  const double pk = 2.0 * PI * u[3];
+  const double khat[3] = {sk * std::cos(pk), sk * std::sin(pk), ck};
+  const double xs = maxwell_speed(s.fa_model, u[4]);
+  const double kinf = xs * s.v0;                       // |k_inf| / m_a
+  const double delta = kinf * kinf / (std::sqrt(1.0 + kinf * kinf) + 1.0);
+  const double omega_inf = 1.0 + delta;                // omega_inf / m_a
+  const double psi = (s.phase_mode == PHASE_UNIFORM) ? 2.0 * PI * u[5] : s.psi;
+  double m[3];
+  magnetic_axis(s, psi, m);
+  for (int i = 0; i < 8; ++i) st[i] = 0.0;
+  st[6] = delta;
+  st[7] = psi;
+  *w = 0.0;
+  double r;
+  if (!resonance_root(s, m, n, khat, omega_inf, &r)) {
+    *status = RAY_NO_ROOT;
+    return;
+  }
+  // derivative dh/dr along the leaf (dual numbers)
+  double E, K2, wp2, cos2;
+  Dual<1> rd = Dual<1>::var(r, 0);
+  Dual<1> hd = resonance_h<Dual<1>>(s, m, n, khat, omega_inf, rd);
+  resonance_h<double>(s, m, n, khat, omega_inf, r, &E, &K2, &wp2, &cos2);
+  const double dhdr = hd.d[0];                          // units m_a / R
+  const double A = 1.0 - s.rs / r;
+  const double kloc = std::sqrt(K2);
+  const double sin2 = 1.0 - cos2;
+  // field magnitude [eV^2]
+  double x[3] = {r * n[0], r * n[1], r * n[2]};
+  double B[3];
+  dipole_field(m, x, B);
+  const double Bmag = s.B0_eV2 * norm3(B);
+  // Psi [eV^3]
+  const double Ephys = E * s.ma_eV;
+  double shape;
+  if (s.dispersion == DISP_ISO) {
+    shape = sin2;
+  } else {
+    const double D = cos2 * wp2 * (wp2 - 2.0 * E * E) + E * E * E * E;
+    shape = E * E * E * E * sin2 / D;
+  }
+  const double Psi = 0.5 * PI * s.g_eV * s.g_eV * Bmag * Bmag * shape * Ephys;
+  // Jacobians of the sample space (n, khat, |k_inf|) -> (x, k_loc):
+  //   dV          = A^{-1/2} r^2 dr dOmega_n
+  //   d^3k_loc    = (k_loc k_inf / A) d|k_inf| dOmega_k       (at fixed r)
+  //   int dr delta(h(r)) = 1 / |dh/dr|
+  //   f_a / pdf(|k_inf|) = n_inf / (4 pi k_inf^2)  (Maxwellian or delta)
+  //   pdf(n) pdf(khat) = 1 / (4 pi)^2
+  const double r_eV = r * s.R_inv_eV;                   // [eV^-1]
+  const double kloc_eV = kloc * s.ma_eV, kinf_eV = kinf * s.ma_eV;
+  const double dhdr_eV = std::fabs(dhdr) * s.ma_eV / s.R_inv_eV;  // [eV^2]
+  const double vol = std::pow(A, -0.5) * r_eV * r_eV;
+  const double mom = kloc_eV * kinf_eV / A;
+  const double tdil = std::sqrt(A);
+  const double fa_over_pdf = s.n_inf / (4.0 * PI * kinf_eV * kinf_eV);
+  const double W = vol * mom * tdil * Psi * fa_over_pdf / dhdr_eV * (4.0 * PI) * (4.0 * PI);
+  const double EV2_W = units::EV_J / units::HBAR_EV_S;  // 1 eV^2 of power in W
+  *w = W / (double)N * EV2_W;
+  // initial photon phase-space point: orthonormal k = |k| khat, covariant
+  // Cartesian components k = k_o + (1/sqrt(A) - 1)(n.k_o) n
+  double ko[3] = {kloc * khat[0], kloc * khat[1], kloc * khat[2]};
+  double nko = n[0] * ko[0] + n[1] * ko[1] + n[2] * ko[2];
+  for (int i = 0; i < 3; ++i) {
+    st[i] = x[i] * s.R_km;
+    st[3 + i] = (ko[i] + (1.0 / std::sqrt(A) - 1.0) * nko * n[i]) * s.ma_eV;
+  }
+  *status = RAY_READY;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive Dormand-Prince integration of one ray (scaled units), from
+// lambda = 0 to the first of: r = r_out (located on the dense output),
+// r <= r_capture, lambda = lambda_max (if > 0), max_steps accepted steps.
+struct RayRHS {
+  const Star* s;
+  const double* m;
+  double omega_inf;
+  long nev = 0;
+  void operator()(const double y[6], double dy[6]) {
+    rhs(*s, m, omega_inf, y, dy);
+    ++nev;
+  }
+};
+
+static int trace_ray(const Star& s, const double m[3], double omega_inf, double y[6],
+                     const TraceOpts& o, long* nacc_out, long* nrej_out, double* lam_out) {
+  RayRHS f{&s, m, omega_inf};
+  double f0[6];
+  f(y, f0);
+  double lam = 0.0;
+  double hmax = (o.lambda_max > 0.0) ? o.lambda_max : 1e30;
+  double h = dp5_initial_step(f, y, f0, o.rtol, o.atol, hmax);
+  long nacc = 0, nrej = 0;
+  bool last_rej = false;
+  int status = RAY_MAXSTEPS;
+  double K[7][6], ynew[6], err[6];
+  while (true) {
+    if (nacc >= o.max_steps || nacc + nrej >= 4 * o.max_steps) { status = RAY_MAXSTEPS; break; }
+    bool clipped = false;
+    if (o.lambda_max > 0.0 && lam + h >= o.lambda_max) { h = o.lambda_max - lam; clipped = true; }
+    dp5_step(f, y, f0, h, ynew, err, K);
+    double en = dp5_error_norm(y, ynew, err, o.rtol, o.atol);
+    if (!std::isfinite(en)) {
+      ++nrej;
+      h *= 0.2;
+      last_rej = true;
+      if (h < 1e-12) { status = RAY_NAN; break; }
+      continue;
+    }
+    if (en <= 1.0) {
+      ++nacc;
+      double rnew = norm3(ynew);
+      if (rnew >= o.r_out) {
+        // locate |x(th)| = r_out on the continuous extension
+        double lo = 0.0, hi = 1.0, yd[6];
+        for (int it = 0; it < 200; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          dp5_dense(y, ynew, K, h, mid, yd);
+          if (norm3(yd) < o.r_out) lo = mid; else hi = mid;
+        }
+        double th = 0.5 * (lo + hi);
+        dp5_dense(y, ynew, K, h, th, yd);
+        for (int i = 0; i < 6; ++i) y[i] = yd[i];
+        lam += th * h;
+        status = RAY_ESCAPED;
+        break;
+      }
+      for (int i = 0; i < 6; ++i) { y[i] = ynew[i]; f0[i] = K[6][i]; }
+      lam += h;
+      if (rnew <= o.r_capture) { status = RAY_CAPTURED; break; }
+      if (clipped) { status = RAY_LAMBDA_END; break; }
+      h *= dp5_step_factor(en, true, last_rej);
+      last_rej = false;
+    } else {
+      ++nrej;
+      h *= dp5_step_factor(en, false, last_rej);
+      last_rej = true;
+      if (h < 1e-12) { status = RAY_STIFF; break; }
+    }
+  }
+  *nacc_out = nacc;
+  *nrej_out = nrej;
+  if (lam_out) *lam_out = lam;
+  return status;
+}
+
+// Physical SoA state (rows: x[3] km, k[3] eV, delta, psi) <-> scaled ray.
+static void load_ray(const Star& s, const double* state, long n, long i, double y[6],
+                     double* omega_inf, double m[3]) {
+  for (int c = 0; c < 3; ++c) {
+    y[c] = state[c * n + i] / s.R_km;
+    y[3 + c] = state[(3 + c) * n + i] / s.ma_eV;
+  }
+  *omega_inf = 1.0 + state[6 * n + i];
+  magnetic_axis(s, state[7 * n + i], m);
+}
+
+static void store_ray(const Star& s, double* state, long n, long i, const double y[6]) {
+  for (int c = 0; c < 3; ++c) {
+    state[c * n + i] = y[c] * s.R_km;
+    state[(3 + c) * n + i] = y[3 + c] * s.ma_eV;
+  }
+}
+
+template <class F>
+static void parallel_for(long n, int nthreads, F body) {
+  if (nthreads <= 1 || n < 2) {
+    for (long i = 0; i < n; ++i) body(i);
+    return;
+  }
+  std::atomic<long> next(0);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        long i = next.fetch_add(1);
+        if (i >= n) break;
+        body(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+// Classical 4th-order Runge-Kutta with a fixed step (brute-force check).
+static void rk4_fixed(const Star& s, const double m[3], double omega_inf, double y[6],
+                      double lam_end, long nsteps) {
+  RayRHS f{&s, m, omega_inf};
+  const double h = lam_end / (double)nsteps;
+  double k1[6], k2[6], k3[6], k4[6], t[6];
+  for (long it = 0; it < nsteps; ++it) {
+    f(y, k1);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    f(t, k2);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    f(t, k3);
+    for (int i = 0; i < 6; ++i) t[i] = y[i] + h * k3[i];
+    f(t, k4);
+    for (int i = 0; i < 6; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  }
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+int or_version(void) { return 1; }
+
+// Samples n conversion points.  u: SoA 6 x n uniforms in (0, 1).  state: SoA
+// 8 x n (x km, k eV, delta, psi).  Returns the number of rays with a root.
+long or_sample(const double* sp, long n, const double* u, double* state, double* weight,
+               unsigned char* status, int nthreads) {
+  Star s = make_star(sp);
+  std::atomic<long> nroot(0);
+  parallel_for(n, nthreads, [&](long i) {
+    double ui[6], st[8];
+    for (int c = 0; c < 6; ++c) ui[c] = u[c * n + i];
+    sample_one(s, ui, n, st, &weight[i], &status[i]);
+    for (int c = 0; c < 8; ++c) state[c * n + i] = st[c];
+    if (status[i] == RAY_READY) nroot.fetch_add(1);
+  });
+  return nroot.load();
+}
+
+// Traces every READY ray in place.  nacc / nrej / lam may be null.
+void or_trace_forward(const double* sp, const double* topt, long n, double* state,
+                      unsigned char* status, int* nacc, int* nrej, double* lam, int nthreads) {
+  Star s = make_star(sp);
+  TraceOpts o = make_opts(topt);
+  parallel_for(n, nthreads, [&](long i) {
+    if (status[i] != RAY_READY) {
+      if (nacc) nacc[i] = 0;
+      if (nrej) nrej[i] = 0;
+      if (lam) lam[i] = 0.0;
+      return;
+    }
+    double y[6], om, m[3];
+    load_ray(s, state, n, i, y, &om, m);
+    long na = 0, nr = 0;
+    double l = 0.0;
+    status[i] = (unsigned char)trace_ray(s, m, om, y, o, &na, &nr, &l);
+    store_ray(s, state, n, i, y);
+    if (nacc) nacc[i] = (int)na;
+    if (nrej) nrej[i] = (int)nr;
+    if (lam) lam[i] = l;
+  });
+}
+
+// Fixed-step RK4 from the given states over lambda in [0, lam_end[i]].
+void or_trace_rk4(const double* sp, long n, double* state, const double* lam_end, long nsteps,
+                  int nthreads) {
+  Star s = make_star(sp);
+  parallel_for(n, nthreads, [&](long i) {
+    double y[6], om, m[3];
+    load_ray(s, state, n, i, y, &om, m);
+    rk4_fixed(s, m, om, y, lam_end[i], nsteps);
+    store_ray(s, state, n, i, y);
+  });
+}
+
+// H / m_a^2 and Hamilton's equations (scaled units: d(x/R)/dl, d(k/m_a)/dl)
+// at each state column.
+void or_hamiltonian(const double* sp, long n, const double* state, double* H, double* dydl) {
+  Star s = make_star(sp);
+  for (long i = 0; i < n; ++i) {
+    double y[6], om, m[3];
+    load_ray(s, state, n, i, y, &om, m);
+    H[i] = hamiltonian<double>(s, m, om, y, y + 3);
+    if (dydl) {
+      double dy[6];
+      rhs(s, m, om, y, dy);
+      for (int c = 0; c < 6; ++c) dydl[c * n + i] = dy[c];
+    }
+  }
+}
+
+// omega_p^2 / m_a^2 at physical positions x (3 x n, km) for magnetic phase psi.
+void or_plasma_freq2(const double* sp, long n, const double* x, double psi, double* out) {
+  Star s = make_star(sp);
+  double m[3];
+  magnetic_axis(s, psi, m);
+  for (long i = 0; i < n; ++i) {
+    double xs[3] = {x[i] / s.R_km, x[n + i] / s.R_km, x[2 * n + i] / s.R_km};
+    out[i] = plasma_freq2<double>(s, m, xs);
+  }
+}
+
+// LO (or isotropic) photon energy for given |k|^2, omega_p^2, cos^2.
+double or_photon_energy(int dispersion, double K2, double wp2, double cos2) {
+  return photon_energy<double>(dispersion, K2, wp2, cos2);
+}
+
+// Inverse CDF of the Maxwellian speed (units of k0).
+double or_maxwell_speed(int fa_model, double u) { return maxwell_speed(fa_model, u); }
+
+// Resonance function and root along a radial line (units of R and m_a).
+double or_resonance_h(const double* sp, const double* n, const double* khat, double omega_inf,
+                      double psi, double r, double* dhdr) {
+  Star s = make_star(sp);
+  double m[3];
+  magnetic_axis(s, psi, m);
+  Dual<1> hd = resonance_h<Dual<1>>(s, m, n, khat, omega_inf, Dual<1>::var(r, 0));
+  if (dhdr) *dhdr = hd.d[0];
+  return hd.v;
+}
+
+int or_resonance_root(const double* sp, const double* n, const double* khat, double omega_inf,
+                      double psi, double* r) {
+  Star s = make_star(sp);
+  double m[3];
+  magnetic_axis(s, psi, m);
+  return resonance_root(s, m, n, khat, omega_inf, r) ? 1 : 0;
+}
+
+// Derived star constants: [rs/R, omega_p^2(R, magnetic pole)/m_a^2 /2 (the
+// coefficient of r^-3 |3 cos(th) m.n - cos(th_m)|), B0 in eV^2, R in eV^-1,
+// n_inf in eV^3, GJ density coefficient Omega B0 / (e) in cm^-3].
+void or_star_constants(const double* sp, double* out) {
+  Star s = make_star(sp);
+  out[0] = s.rs;
+  out[1] = s.e_hl * s.omega_eV * s.B0_eV2 / units::ME_EV / (s.ma_eV * s.ma_eV);
+  out[2] = s.B0_eV2;
+  out[3] = s.R_inv_eV;
+  out[4] = s.n_inf;
+  const double hbarc_cm = units::HBARC_EV_KM * 1e5;
+  out[5] = s.omega_eV * s.B0_eV2 / s.e_hl / (hbarc_cm * hbarc_cm * hbarc_cm);
+}
+
+// Sky / frequency histogram of ESCAPED rays.  Sky direction = orthonormal
+// momentum direction at the end point; theta uniform on [0, pi] (nth bins),
+// phi on [0, 2 pi) (nph bins); frequency variable y = delta / (v0^2 / 2) on
+// [nu_lo, nu_hi) (nnu bins).  hist is nth x nph x nnu (row-major), in W per
+// bin; out_of_range receives the weight with y outside the range.
+void or_bin(const double* sp, long n, const double* state, const double* weight,
+            const unsigned char* status, int nth, int nph, int nnu, double nu_lo, double nu_hi,
+            double* hist, double* out_of_range) {
+  Star s = make_star(sp);
+  std::memset(hist, 0, sizeof(double) * (size_t)nth * nph * nnu);
+  *out_of_range = 0.0;
+  for (long i = 0; i < n; ++i) {
+    if (status[i] != RAY_ESCAPED) continue;
+    double x[3], k[3];
+    for (int c = 0; c < 3; ++c) {
+      x[c] = state[c * n + i] / s.R_km;
+      k[c] = state[(3 + c) * n + i];
+    }
+    double r = norm3(x);
+    double nn[3] = {x[0] / r, x[1] / r, x[2] / r};
+    double A = 1.0 - s.rs_prop / r;
+    double kn = nn[0] * k[0] + nn[1] * k[1] + nn[2] * k[2];
+    double ko[3];
+    for (int c = 0; c < 3; ++c) ko[c] = k[c] + (std::sqrt(A) - 1.0) * kn * nn[c];
+    double kmag = norm3(ko);
+    double cz = std::fmax(-1.0, std::fmin(1.0, ko[2] / kmag));
+    double th = std::acos(cz);
+    double ph = std::atan2(ko[1], ko[0]);
+    if (ph < 0.0) ph += 2.0 * units::PI;
+    int ith = (int)std::floor(th / (units::PI / nth));
+    if (ith >= nth) ith = nth - 1;
+    int iph = (int)std::floor(ph / (2.0 * units::PI / nph));
+    if (iph >= nph) iph -= nph;
+    double y = state[6 * n + i] / (0.5 * s.v0 * s.v0);
+    if (!(y >= nu_lo && y < nu_hi)) { *out_of_range += weight[i]; continue; }
+    int inu = (int)std::floor((y - nu_lo) / ((nu_hi - nu_lo) / nnu));
+    if (inu >= nnu) inu = nnu - 1;
+    hist[((size_t)ith * nph + iph) * nnu + inu] += weight[i];
+  }
+}
+
+// The Dormand-Prince tableau as used above: c[7], a[7*6], b[7], bh[7], e[7], d[7].
+void or_dp5_tableau(double* c, double* a, double* b, double* bh, double* e, double* d) {
+  for (int i = 0; i < 7; ++i) {
+    c[i] = DP5::c[i]; b[i] = DP5::b[i]; bh[i] = DP5::bh[i]; e[i] = DP5::e[i]; d[i] = DP5::d[i];
+    for (int j = 0; j < 6; ++j) a[i * 6 + j] = DP5::a[i][j];
+  }
+}
+
+// The same adaptive integrator (initial step, dp5_step, error norm,
+// controller) on the linear test equation y' = M y, y in R^6, from 0 to T.
+// Returns the number of accepted steps; y is overwritten by y(T).
+long or_dp5_linear(const double* M, double* y, double T, double rtol, double atol) {
+  struct Lin {
+    const double* M;
+    void operator()(const double v[6], double dv[6]) {
+      for (int i = 0; i < 6; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 6; ++j) acc += M[i * 6 + j] * v[j];
+        dv[i] = acc;
+      }
+    }
+  } f{M};
+  double f0[6], K[7][6], ynew[6], err[6];
+  f(y, f0);
+  double t = 0.0, h = dp5_initial_step(f, y, f0, rtol, atol, T);
+  long nacc = 0;
+  bool last_rej = false;
+  while (t < T && nacc < 10000000) {
+    if (t + h > T) h = T - t;
+    dp5_step(f, y, f0, h, ynew, err, K);
+    double en = dp5_error_norm(y, ynew, err, rtol, atol);
+    if (en <= 1.0) {
+      for (int i = 0; i < 6; ++i) { y[i] = ynew[i]; f0[i] = K[6][i]; }
+      t += h;
+      ++nacc;
+      h *= dp5_step_factor(en, true, last_rej);
+      last_rej = false;
+    } else {
+      h *= dp5_step_factor(en, false, last_rej);
+      last_rej = true;
+    }
+  }
+  return nacc;
+}
+
+// One step of size h on y' = M y followed by the continuous extension at th.
+void or_dp5_linear_dense(const double* M, const double* y0, double h, double th, double* out) {
+  struct Lin {
+    const double* M;
+    void operator()(const double v[6], double dv[6]) {
+      for (int i = 0; i < 6; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 6; ++j) acc += M[i * 6 + j] * v[j];
+        dv[i] = acc;
+      }
+    }
+  } f{M};
+  double f0[6], K[7][6], ynew[6], err[6];
+  f(y0, f0);
+  dp5_step(f, y0, f0, h, ynew, err, K);
+  dp5_dense(y0, ynew, K, h, th, out);
+}
+
+}  // extern "C"
