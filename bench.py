@@ -1,0 +1,352 @@
+"""Benchmark of the forward hot path on the production-size workload.
+
+Workload (one "step"): 16 sub-batches x 65536 forward rays on a misaligned
+magnetar-like rotator (B0 = 1.6e14 G, P = 3.76 s, theta_m = 30 deg,
+M = 1.5 Msun, R = 11 km), axion masses log-uniform in [1e-6, 5e-3] eV (one per
+sub-batch, seed 1), rotation phase uniform per ray: conversion-surface
+sampling (FP64) -> Dormand-Prince 5(4) trace to r = 1000 R at rtol 1e-10 ->
+fixed-point binning into 64 x 32 x 128 (theta, phi, frequency) bins per
+sub-batch.  Inputs are synthetic (SplitMix64 uniforms) and resident in HBM
+when the timed region starts; the L2 is flushed (256 MiB write) before every
+timed step.
+
+Reported: accepted ray-steps/s (value), rays/s, the roofline of the trace
+kernel (FP64 ALU), an end-to-end number through the C ABI with host buffers,
+and the oracle timed on the host cores.  ``--impl reference`` times the
+oracle alone (the CPU reference arm) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-steps/s & rays/s at 1e-6 rel. flux err; mixed vs FP64; adjoint/forward ratio"
+UNIT = "ray-steps/s"
+NBINS = (64, 32, 128)
+# Nominal GB300 ALU peaks derived from the unit counts and the maximum clock:
+# 152 SMs x 2070 MHz; FP64 4 flop/clk/SM (1.26 TFLOP/s, the nominal GB300
+# FP64 rate); FP32 128 lanes x 2 flop/clk/SM (80.5 TFLOP/s).
+SMS, CLK = 152, 2.070e9
+PEAK_FP64 = SMS * 4 * CLK
+PEAK_FP32 = SMS * 256 * CLK
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2048,
+                    help="rays per non-empty sub-batch in the CPU baseline")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _flops_per_attempt(rt):
+    L = rt.lib()
+    L.rt_flops_per_step.restype = ctypes.c_int
+    L.rt_flops_per_step.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_double)]
+    o = (ctypes.c_double * 4)()
+    L.rt_flops_per_step(0, 0, o)
+    return list(o)
+
+
+def _workload():
+    from paper_2309_08655_gb300 import inputs as I
+    cfg = I.CONFIG1
+    return cfg, I.stars_config1(cfg["seed"], cfg["nsub"])
+
+
+def _oracle_sample_run(stars, cfg, per_sub, nthreads):
+    """Oracle on the first ``per_sub`` rays of each non-empty sub-batch."""
+    import numpy as np
+    import oracle
+    from paper_2309_08655_gb300 import inputs as I
+    steps = rays = 0
+    t0 = time.perf_counter()
+    for j, kw in enumerate(stars):
+        sv = oracle.star_vector(**kw)
+        u = I.sample_uniforms(cfg["seed"] * 1000 + j, per_sub)
+        st, w, s = oracle.sample(sv, u, nthreads)
+        if not (s == oracle.RAY_READY).any():
+            continue
+        na, nr, _ = oracle.trace_forward(sv, oracle.trace_opts(rtol=cfg["rtol"],
+                                         r_out_over_R=cfg["r_out_over_R"]), st, s, nthreads)
+        oracle.bin_rays(sv, st, w, s, *NBINS, cfg["nu_lo"], cfg["nu_hi"])
+        steps += int(na.sum())
+        rays += int(np.sum(s != oracle.RAY_NO_ROOT))
+    return steps, rays, time.perf_counter() - t0
+
+
+def _cpu_baseline(stars, cfg, per_sub):
+    nthreads = os.cpu_count() or 1
+    steps, rays, dt = _oracle_sample_run(stars, cfg, per_sub, nthreads)
+    nonempty = sum(1 for _ in stars)
+    return {"value": steps / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "rays_per_s": rays / dt, "seconds": dt,
+            "sample": f"first {per_sub} rays of each of the {nonempty} sub-batches "
+                      f"(empty ones sample only), {rays} traced rays, {steps} accepted steps"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg, stars = _workload()
+    per = max(16, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        _oracle_sample_run(stars, cfg, max(8, per // 4), os.cpu_count() or 1)
+    tot_steps = tot_rays = 0
+    tot_t = 0.0
+    for _ in range(args.steps):
+        s, r, dt = _oracle_sample_run(stars, cfg, per, os.cpu_count() or 1)
+        tot_steps += s
+        tot_rays += r
+        tot_t += dt
+    v = tot_steps / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"] + " (bounded sample)", "rays_per_sub_batch": per,
+                   "rtol": cfg["rtol"], "r_out_over_R": cfg["r_out_over_R"]},
+        "rays_per_s": tot_rays / tot_t,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1,
+                         "kind": "oracle",
+                         "sample": f"first {per} rays of each of the 16 sub-batches per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2309_08655_gb300 import build as B
+    from paper_2309_08655_gb300 import inputs as I
+    from paper_2309_08655_gb300 import rt
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    dev = torch.device("cuda", local)
+    cfg, stars_kw = _workload()
+    nsub, nper = cfg["nsub"], cfg["n_per_sub"]
+    nth, nph, nnu = NBINS
+    stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
+    # weak scaling: every rank traces its own seeded copy of the workload
+    seeds = [cfg["seed"] * 1000 + j + 100000 * rank for j in range(nsub)]
+    u_host = [torch.from_numpy(I.sample_uniforms(s, nper)).pin_memory() for s in seeds]
+    u = [x.to(dev) for x in u_host]
+    state = [torch.empty((8, nper), dtype=torch.float64, device=dev) for _ in range(nsub)]
+    w = [torch.empty(nper, dtype=torch.float64, device=dev) for _ in range(nsub)]
+    st = [torch.empty(nper, dtype=torch.uint8, device=dev) for _ in range(nsub)]
+    hist = torch.empty((nsub, nth, nph, nnu), dtype=torch.float64, device=dev)
+    oor = torch.empty(nsub, dtype=torch.float64, device=dev)
+    ctr = torch.zeros((nsub, 4), dtype=torch.int64, device=dev)
+    hist_host = torch.empty_like(hist, device="cpu").pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    opts = rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
+                        precision=rt.PREC_FP64)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nsub)]
+
+    def step(record=False, uin=None):
+        ctr.zero_()
+        for j in range(nsub):
+            src = u[j] if uin is None else uin[j]
+            rt.rt_sample_conversion_surface(stars[j], nper, src, state[j], w[j], st[j],
+                                            stream=stream)
+            if record:
+                ev[j][0].record(stream)
+            rt.rt_trace_forward(stars[j], nper, state[j], st[j], None, None, ctr[j], opts,
+                                stream=stream)
+            if record:
+                ev[j][1].record(stream)
+            rt.rt_bin_spectrum(stars[j], nper, state[j], w[j], st[j], nth, nph, nnu,
+                               cfg["nu_lo"], cfg["nu_hi"], hist[j], None, None, oor[j:j + 1],
+                               stream=stream)
+
+    launches_per_step = nsub * 5   # sample, trace, 3 binning kernels
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    t_steps, t_trace, steps_acc, steps_rej, rays = [], [], 0, 0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)                      # L2 flush, outside the timed events
+        e0.record(stream)
+        step(record=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_steps.append(e0.elapsed_time(e1) / 1e3)
+        t_trace.append(sum(a.elapsed_time(b) for a, b in ev) / 1e3 / nsub)
+        c = ctr.sum(0).cpu().numpy()
+        steps_acc += int(c[0])
+        steps_rej += int(c[1])
+        rays += int(c[2])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    T = sum(t_steps)
+    if ws > 1:
+        tt = torch.tensor([T], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        T = float(tt[0])
+        cs = torch.tensor([steps_acc, rays], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(cs)
+        steps_acc_all, rays_all = float(cs[0]), float(cs[1])
+    else:
+        steps_acc_all, rays_all = steps_acc, rays
+    value = steps_acc_all / T
+    # roofline of the dominant kernel (the trace): algorithmic flops per launch
+    fl = _flops_per_attempt(rt)
+    attempts = (steps_acc + steps_rej) / (args.steps * nsub)
+    rays_per_launch = rays / (args.steps * nsub)
+    flops_launch = attempts * fl[1] + rays_per_launch * fl[2]
+    achieved = flops_launch / statistics.mean(t_trace)
+
+    # end to end through the C ABI with host buffers: H2D uniforms, D2H histograms
+    t_e2e = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(nsub):
+            u[j].copy_(u_host[j], non_blocking=True)
+        step()
+        hist_host.copy_(hist, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_val = steps_acc / args.steps * len(t_e2e) / sum(t_e2e)
+    h2d = sum(x.numel() * 8 for x in u_host)
+    d2h = hist.numel() * 8
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(stars_kw, cfg, args.cpu_sample)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "rays_per_step": nsub * nper,
+                   "sub_batches": nsub, "rtol": cfg["rtol"],
+                   "r_out_over_R": cfg["r_out_over_R"], "bins": list(NBINS),
+                   "precision": "fp64", "l2": "flushed before each step (256 MiB write)"},
+        "rays_per_s": rays_all / T,
+        "accepted_steps_per_step": steps_acc / args.steps,
+        "rejected_steps_per_step": steps_rej / args.steps,
+        "roofline": {"kernel": "trace_fp64_kernel", "bound": "alu", "achieved": achieved / 1e12,
+                     "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / PEAK_FP64, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                     "flops_per_attempt": fl[1], "attempts_per_launch": attempts,
+                     "trace_ms_per_launch": 1e3 * statistics.mean(t_trace)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * rt.h - C ABI of the GB300 (sm_103a) batched Hamiltonian ray tracer for
+ * photons produced by resonant axion-photon conversion in a neutron-star
+ * magnetosphere (J. I. McDonald and S. J. Witte, "Generalized Ray Tracing for
+ * Axions in Astrophysical Plasmas", arXiv:2309.08655).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All arrays are caller-owned DEVICE pointers (any CUDA allocation on the
+ *   current device), accessed on the caller's stream `stream` (a
+ *   cudaStream_t passed as void*; NULL = legacy default stream).  Calls are
+ *   asynchronous unless stated otherwise; they return after enqueueing work.
+ * - Ray state is structure-of-arrays, RT_STATE_ROWS x n float64, row r of ray
+ *   i at state[r * n + i]:
+ *     rows 0-2  x^i, Cartesianised Schwarzschild position [km]
+ *     rows 3-5  k_i, covariant Cartesian momentum [eV]
+ *     row  6    delta = omega_inf / m_a - 1, with k_t = -omega_inf conserved
+ *     row  7    psi, rotation phase of the frozen magnetosphere [rad]
+ * - Per-ray status is one uint8 per ray (RT_RAY_*).
+ * - Errors: functions return rt_status and never abort.  Argument errors
+ *   return RT_EINVAL, an unsupported option RT_EUNSUPPORTED, CUDA errors
+ *   (launch failures, or an earlier asynchronous fault surfacing)
+ *   RT_ECUDA; rt_last_error() then returns a thread-local message.  Per-ray
+ *   problems are reported in the status array, not by the return value.
+ * - Thread safety: rt_star handles are immutable after rt_init_star and may
+ *   be used from several host threads, except that rt_bin_spectrum calls
+ *   sharing one handle must be serialised on one stream (they share the
+ *   handle's scratch accumulator).
+ */
+#ifndef RT_AXION_H
+#define RT_AXION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_STATE_ROWS 8
+#define RT_UNIFORM_ROWS 6
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,
+  RT_ENOMEM = 2,
+  RT_ECUDA = 3,
+  RT_EEMPTY_SURFACE = 4,  /* the resonance cannot exist anywhere outside the star */
+  RT_EPARTIAL = 5,        /* returned by rt_count_status when some rays hit a bound */
+  RT_EUNSUPPORTED = 6
+} rt_status;
+
+/* Per-ray status codes. */
+enum {
+  RT_RAY_READY = 0,      /* sampled, not yet traced */
+  RT_RAY_ESCAPED = 1,    /* reached r = r_out (located exactly on the dense output) */
+  RT_RAY_CAPTURED = 2,   /* reached r <= r_capture (the stellar surface) */
+  RT_RAY_NO_ROOT = 3,    /* no resonance on this sample's radial line (weight 0) */
+  RT_RAY_MAXSTEPS = 4,   /* max_steps accepted steps (or 4 x max_steps attempts) */
+  RT_RAY_NAN = 5,        /* non-finite state or error estimate */
+  RT_RAY_STIFF = 6,      /* step size fell below 1e-12 (units of R) */
+  RT_RAY_LAMBDA_END = 7, /* reached lambda_max (only when lambda_max > 0) */
+  RT_RAY_NSTATUS = 8
+};
+
+/* Model switches. */
+enum { RT_DISP_ANISO = 0, RT_DISP_ISO = 1 };
+enum { RT_RES_KINEMATIC = 0 };
+enum { RT_FA_MAXWELL = 0, RT_FA_DELTA = 1 };
+enum { RT_WEIGHT_PAG = 0 };
+enum { RT_METRIC_FULL = 0, RT_METRIC_FLAT = 1 };
+enum { RT_PHASE_FIXED = 0, RT_PHASE_UNIFORM = 1 };
+enum { RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3 };
+enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
+
+/*
+ * Star, plasma and axion parameters (Sec. 5 fiducials; Eq. GJDensity).
+ *   M_sun          stellar mass [solar masses]; r_s = 2 G M / c^2
+ *   R_km           stellar radius [km]; also the unit of length inside kernels
+ *   B0_G           dipole field at the magnetic pole of the surface [G]
+ *   P_s            rotation period [s] (sets Omega in n_GJ = 2 Omega.B / e)
+ *   theta_m_rad    misalignment of the magnetic axis from the rotation axis z
+ *   psi_rad        rotation phase used when phase_mode == RT_PHASE_FIXED
+ *   m_a_eV         axion mass [eV]; also the unit of momentum inside kernels
+ *   g_agg_GeVinv   axion-photon coupling [GeV^-1]
+ *   rho_dm_GeV_cm3 asymptotic dark-matter density; n_inf = rho / m_a
+ *   v0_kms         Maxwellian dispersion, f ~ exp(-|k|^2 / (m_a v0)^2)
+ *   dispersion     RT_DISP_ANISO (Eq. StrongBHam) or RT_DISP_ISO (Eq. DispIsotropic)
+ *   resonance      RT_RES_KINEMATIC (k^a_mu = k^gamma_mu)
+ *   fa_model       RT_FA_MAXWELL (Eq. GaussianDist) or RT_FA_DELTA (|k_inf| = m_a v0)
+ *   weight_mode    RT_WEIGHT_PAG (conversion probability, Eq. CPAnisoCurved)
+ *   prop_metric    RT_METRIC_FULL, or RT_METRIC_FLAT (M = 0 in propagation only)
+ *   phase_mode     RT_PHASE_FIXED or RT_PHASE_UNIFORM (psi = 2 pi u5 per sample)
+ *   plasma         RT_PLASMA_GJ; the others are analytic test media
+ *   plasma_a       omega_p^2 / m_a^2 (HOMOG) or its gradient d/d(z/R) (LINEAR_Z)
+ */
+typedef struct {
+  double M_sun, R_km, B0_G, P_s, theta_m_rad, psi_rad, m_a_eV, g_agg_GeVinv, rho_dm_GeV_cm3,
+      v0_kms;
+  int32_t dispersion, resonance, fa_model, weight_mode, prop_metric, phase_mode, plasma,
+      reserved;
+  double plasma_a;
+} rt_star_params;
+
+/*
+ * Integration options (adaptive Dormand-Prince 5(4), Sec. 2.4's "high
+ * precision ODE solvers").
+ *   rtol, atol        tolerances on the state scaled to x/R and k/m_a
+ *   r_out_over_R      escape radius (event located on the dense output)
+ *   lambda_max        stop at this worldline parameter (units: R / m_a^2 scaled
+ *                     Hamiltonian); 0 = no limit
+ *   r_capture_over_R  capture radius (1 = stellar surface)
+ *   precision         RT_PREC_FP64 or RT_PREC_MIXED
+ *   max_steps         bound on accepted steps per ray
+ *   block             threads per block of the persistent kernel (0 = auto)
+ *   blocks_per_sm     resident blocks per SM for the persistent grid (0 = auto)
+ */
+typedef struct {
+  double rtol, atol, r_out_over_R, lambda_max, r_capture_over_R;
+  int32_t precision, max_steps, block, blocks_per_sm;
+} rt_trace_opts;
+
+typedef struct rt_star rt_star; /* opaque, library-owned */
+
+/*
+ * rt_init_star - validate parameters and build a star handle (host only;
+ * allocates the handle and a small device block).  Derived constants follow
+ * Sec. 5 (Eq. GJDensity) and Sec. 4.1 (Eq. SchwarzshildMetric1).
+ * Returns RT_EINVAL on non-finite or out-of-range parameters (R <= r_s,
+ * m_a <= 0, ...), RT_EUNSUPPORTED on unknown model switches.  *out is NULL on
+ * error.  The handle is bound to the device current at this call.
+ */
+rt_status rt_init_star(const rt_star_params* params, rt_star** out);
+void rt_destroy_star(rt_star* star);
+
+/*
+ * rt_star_info - derived constants of a handle (host, synchronous), in
+ * out[0..7]: r_s/R, omega_p^2 coefficient / m_a^2 (omega_p^2 / m_a^2 =
+ * c r^-3 |3 cos th (m.n) - cos th_m|, r in units of R), B0 [eV^2], R [eV^-1],
+ * n_inf [eV^3], v0 [c], maximum omega_p^2 / m_a^2 on the surface, and 1 if the
+ * resonance surface is empty for every direction (else 0).
+ */
+rt_status rt_star_info(const rt_star* star, double* out8);
+
+/*
+ * rt_sample_conversion_surface - forward Monte-Carlo samples of the
+ * resonant conversion surface and their power weights (Sec. 3, Eq.
+ * ForwardTracingEquation1; Sec. 4.2, Eq. PowerCurved with Eq. CPAnisoCurved
+ * and Eq. AngleDefAniso; Sec. 4.3, Eq. GaussianDist).
+ *   n           number of samples (>= 0); the weights are normalised by n
+ *   d_uniforms  RT_UNIFORM_ROWS x n float64 in (0, 1), SoA: rows 0-1 the
+ *               direction of the conversion point (cos th = 1 - 2u0,
+ *               phi = 2 pi u1), rows 2-3 the momentum direction in the
+ *               static orthonormal frame, row 4 the Maxwellian speed
+ *               (inverse CDF), row 5 the rotation phase (phase_mode UNIFORM)
+ *   d_state     out: RT_STATE_ROWS x n initial photon states
+ *   d_weight    out: n power weights [W]; the sum over samples estimates
+ *               the total power; 0 for samples without a resonance
+ *   d_status    out: RT_RAY_READY or RT_RAY_NO_ROOT
+ * The resonance r_k is found in FP64 on the radial line through the sampled
+ * direction, with the momentum direction and omega_inf held fixed.
+ */
+rt_status rt_sample_conversion_surface(const rt_star* star, int64_t n, const double* d_uniforms,
+                                       double* d_state, double* d_weight, uint8_t* d_status,
+                                       void* stream);
+
+/*
+ * rt_trace_forward - integrate Hamilton's equations (Eq. Hamilton) of the
+ * strong-field Hamiltonian (Eq. StrongBHam) for every ray whose status is
+ * RT_RAY_READY, in place, until escape, capture or a bound (Sec. 2.2).
+ * One GPU thread per ray in a persistent kernel whose warps refill finished
+ * lanes from a global queue.
+ *   d_state    in/out: RT_STATE_ROWS x n; on escape the state at r = r_out
+ *   d_status   in/out: READY rays get their final status; others untouched
+ *   d_nacc, d_nrej  out (may be NULL): accepted / rejected steps per ray
+ *   d_counters in/out (may be NULL): 4 int64 accumulated with atomics:
+ *              accepted steps, rejected steps, rays traced, rays escaped
+ *   opts       integration options (host pointer, read during the call)
+ * Deterministic: the same inputs give bitwise identical outputs.
+ */
+rt_status rt_trace_forward(const rt_star* star, int64_t n, double* d_state, uint8_t* d_status,
+                           int32_t* d_nacc, int32_t* d_nrej, int64_t* d_counters,
+                           const rt_trace_opts* opts, void* stream);
+
+/*
+ * rt_bin_spectrum - sky map and spectrum of ESCAPED rays (Sec. 2.2: the
+ * power of the rays landing in a bin of the sphere at infinity).  Sky
+ * direction = direction of the orthonormal-frame momentum at the end point:
+ * theta uniform on [0, pi] (nth bins; theta = pi goes to the last bin), phi
+ * on [0, 2 pi) (nph bins).  Frequency variable y = delta / (v0^2 / 2) on
+ * [nu_lo, nu_hi) (nnu bins); rays outside add to *d_out_of_range.
+ *   d_hist  out: nth x nph x nnu float64 [W per bin], row-major
+ *   d_sky   out (may be NULL): nth x nph, the sum over frequency
+ *   d_spec  out (may be NULL): nnu, the sum over the sky
+ *   d_out_of_range out: 1 float64
+ * Sums are accumulated in 64-bit fixed point (scale 2^e chosen from the
+ * largest escaped weight so that no sum can overflow) and are therefore
+ * independent of the order of the atomics.  Uses a scratch accumulator owned
+ * by the handle (allocated on first use, grown when a larger histogram is
+ * requested; RT_ENOMEM if that fails).
+ */
+rt_status rt_bin_spectrum(const rt_star* star, int64_t n, const double* d_state,
+                          const double* d_weight, const uint8_t* d_status, int32_t nth,
+                          int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,
+                          double* d_sky, double* d_spec, double* d_out_of_range, void* stream);
+
+/*
+ * rt_count_status - histogram of per-ray status codes (synchronises the
+ * stream).  counts: host array of RT_RAY_NSTATUS int64.  Returns RT_EPARTIAL
+ * if any ray ended in MAXSTEPS, NAN or STIFF, else RT_OK.
+ */
+rt_status rt_count_status(int64_t n, const uint8_t* d_status, int64_t* counts, void* stream);
+
+/*
+ * rt_flops_per_step - algorithmic operation counts of the integrator (host
+ * only), for roofline reports: out4[0] flops of one evaluation of the
+ * analytic right-hand side of Hamilton's equations, out4[1] flops of one
+ * Dormand-Prince step attempt (6 evaluations + stage combinations + error
+ * norm + controller), out4[2] flops of the initial-step heuristic, out4[3]
+ * divisions, square roots and powers per attempt.  A fused multiply-add
+ * counts 2 flops; each division or square root counts 1.  RT_EINVAL for
+ * unknown model switches.
+ */
+rt_status rt_flops_per_step(int32_t dispersion, int32_t plasma, double* out4);
+
+/* Thread-local message describing the last error of this thread. */
+const char* rt_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_AXION_H */

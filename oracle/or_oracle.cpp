@@ -55,16 +55,26 @@ static inline double norm3(const double v[3]) {
 // Axion speed at infinity.  Eq. GaussianDist gives the Maxwellian
 // f ~ exp(-|k|^2 / k0^2); the speed x = |k_inf| / k0 then has density
 // (4/sqrt(pi)) x^2 exp(-x^2) and CDF erf(x) - (2/sqrt(pi)) x exp(-x^2).
-// Inverted by bisection.  Eq. fa_approx's monochromatic option gives x = 1.
+// Inverted by bisection; for u > 1/2 the complementary form
+// erfc(x) + (2/sqrt(pi)) x exp(-x^2) = 1 - u is solved instead (1 - u is
+// exact there), which keeps the tail well conditioned.  Eq. fa_approx's
+// monochromatic option gives x = 1.
 static double maxwell_speed(int fa_model, double u) {
   if (fa_model == FA_DELTA) return 1.0;
   const double c = 2.0 / std::sqrt(units::PI);
+  const bool upper = u > 0.5;
+  const double v = upper ? 1.0 - u : u;
   double lo = 0.0, hi = 30.0;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
-    double F = std::erf(mid) - c * mid * std::exp(-mid * mid);
-    if (F < u) lo = mid; else hi = mid;
-    if (hi - lo <= 2.0 * DBL_EPSILON * hi) break;
+    if (mid <= lo || mid >= hi) break;
+    if (upper) {
+      double Q = std::erfc(mid) + c * mid * std::exp(-mid * mid);   // decreasing
+      if (Q > v) lo = mid; else hi = mid;
+    } else {
+      double F = std::erf(mid) - c * mid * std::exp(-mid * mid);    // increasing
+      if (F < v) lo = mid; else hi = mid;
+    }
   }
   return 0.5 * (lo + hi);
 }

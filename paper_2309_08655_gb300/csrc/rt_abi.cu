@@ -1,0 +1,366 @@
+// C ABI of the ray tracer (include/rt.h): argument validation, derived star
+// constants, handle-owned scratch, and kernel launches on the caller's stream.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_device.cuh"
+#include "rt_internal.h"
+
+namespace {
+
+// Constants (the values the paper asks to keep identical everywhere, Sec. 2.4).
+constexpr double PI = 3.14159265358979323846;
+constexpr double HBARC_EV_KM = 1.973269804e-10;  // hbar c [eV km], CODATA 2018
+constexpr double HBAR_EV_S = 6.582119569e-16;     // hbar [eV s], CODATA 2018
+constexpr double ALPHA = 7.2973525693e-3;         // fine-structure constant, CODATA 2018
+constexpr double ME_EV = 510998.95;               // electron mass [eV], CODATA 2018
+constexpr double EV_J = 1.602176634e-19;          // exact
+constexpr double C_KM_S = 299792.458;             // exact
+constexpr double GM_SUN_KM = 1.4766250;           // G Msun / c^2 [km], IAU 2015 nominal
+
+thread_local std::string g_err;
+
+rt_status fail(rt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+rt_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(RT_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool is_finite_val(double v) { return std::isfinite(v); }
+
+// Device arrays must be device (or managed) memory of the current device.
+rt_status check_dev_ptr(const void* p, const char* name) {
+  if (p == nullptr) return fail(RT_EINVAL, "%s is NULL", name);
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RT_EINVAL, "%s is not a CUDA pointer", name);
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(RT_EINVAL, "%s must be device memory", name);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return fail(RT_EINVAL, "%s lives on device %d, current device is %d", name, a.device, dev);
+  return RT_OK;
+}
+
+}  // namespace
+
+struct rt_star {
+  rt_star_params p;
+  rtk::StarDev h;               // host copy of the descriptor
+  rtk::StarDev* d = nullptr;    // device copy
+  unsigned long long* d_queue = nullptr;  // trace work-queue counter (scratch)
+  long long* d_bins = nullptr;  // binning accumulator (scratch)
+  size_t bins_cap = 0;
+  int device = 0;
+  double wp2_surface_max = 0.0;
+  bool empty = false;
+};
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+int32_t rt_version(void) { return 100; }
+
+rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
+  if (out == nullptr) return fail(RT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (p == nullptr) return fail(RT_EINVAL, "params is NULL");
+  const double vals[] = {p->M_sun, p->R_km, p->B0_G, p->P_s, p->theta_m_rad, p->psi_rad,
+                         p->m_a_eV, p->g_agg_GeVinv, p->rho_dm_GeV_cm3, p->v0_kms,
+                         p->plasma_a};
+  for (double v : vals)
+    if (!is_finite_val(v)) return fail(RT_EINVAL, "non-finite star parameter");
+  if (p->M_sun < 0) return fail(RT_EINVAL, "M_sun must be >= 0");
+  if (!(p->R_km > 0)) return fail(RT_EINVAL, "R_km must be > 0");
+  const double rs = 2.0 * p->M_sun * GM_SUN_KM / p->R_km;
+  if (!(rs < 1.0)) return fail(RT_EINVAL, "R_km must exceed the Schwarzschild radius");
+  if (!(p->m_a_eV > 0)) return fail(RT_EINVAL, "m_a_eV must be > 0");
+  if (!(p->P_s > 0)) return fail(RT_EINVAL, "P_s must be > 0");
+  if (p->B0_G < 0 || p->g_agg_GeVinv < 0 || p->rho_dm_GeV_cm3 < 0)
+    return fail(RT_EINVAL, "B0_G, g_agg_GeVinv and rho_dm_GeV_cm3 must be >= 0");
+  if (!(p->v0_kms > 0 && p->v0_kms < C_KM_S)) return fail(RT_EINVAL, "v0_kms out of range");
+  if (p->dispersion != RT_DISP_ANISO && p->dispersion != RT_DISP_ISO)
+    return fail(RT_EUNSUPPORTED, "unknown dispersion %d", p->dispersion);
+  if (p->resonance != RT_RES_KINEMATIC)
+    return fail(RT_EUNSUPPORTED, "unsupported resonance mode %d", p->resonance);
+  if (p->fa_model != RT_FA_MAXWELL && p->fa_model != RT_FA_DELTA)
+    return fail(RT_EUNSUPPORTED, "unknown fa_model %d", p->fa_model);
+  if (p->weight_mode != RT_WEIGHT_PAG)
+    return fail(RT_EUNSUPPORTED, "unsupported weight_mode %d", p->weight_mode);
+  if (p->prop_metric != RT_METRIC_FULL && p->prop_metric != RT_METRIC_FLAT)
+    return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
+  if (p->phase_mode != RT_PHASE_FIXED && p->phase_mode != RT_PHASE_UNIFORM)
+    return fail(RT_EUNSUPPORTED, "unknown phase_mode %d", p->phase_mode);
+  if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_LINEAR_Z)
+    return fail(RT_EUNSUPPORTED, "unknown plasma %d", p->plasma);
+
+  rt_star* s = new (std::nothrow) rt_star;
+  if (!s) return fail(RT_ENOMEM, "host allocation failed");
+  s->p = *p;
+  rtk::StarDev& h = s->h;
+  memset(&h, 0, sizeof(h));
+  h.rs = rs;
+  h.rs_prop = (p->prop_metric == RT_METRIC_FLAT) ? 0.0 : rs;
+  // Goldreich-Julian: n_e = 2 |Omega.B| / e, omega_p^2 = e^2 n_e / m_e (Eq.
+  // GJDensity, Heaviside-Lorentz natural units), dipole B = B0/2 (R/r)^3 (...)
+  const double e_hl = std::sqrt(4.0 * PI * ALPHA);
+  const double omega_eV = HBAR_EV_S * 2.0 * PI / p->P_s;
+  const double hbarc_cm = HBARC_EV_KM * 1e5;
+  const double B0_eV2 =
+      p->B0_G * std::sqrt((1e-7 / EV_J) * hbarc_cm * hbarc_cm * hbarc_cm / (4.0 * PI));
+  h.cp = e_hl * omega_eV * B0_eV2 / ME_EV / (p->m_a_eV * p->m_a_eV);
+  h.plasma_a = p->plasma_a;
+  h.cos_tm = std::cos(p->theta_m_rad);
+  h.sin_tm = std::sin(p->theta_m_rad);
+  h.psi_fixed = p->psi_rad;
+  h.v0 = p->v0_kms / C_KM_S;
+  h.R_km = p->R_km;
+  h.ma_eV = p->m_a_eV;
+  h.R_eV = p->R_km / HBARC_EV_KM;
+  h.B0_eV2 = B0_eV2;
+  h.g_eV = p->g_agg_GeVinv * 1e-9;
+  h.n_inf = p->rho_dm_GeV_cm3 * 1e9 * hbarc_cm * hbarc_cm * hbarc_cm / p->m_a_eV;
+  h.w_unit = EV_J / HBAR_EV_S;
+  h.dispersion = p->dispersion;
+  h.plasma = p->plasma;
+  h.fa_model = p->fa_model;
+  h.phase_mode = p->phase_mode;
+  // Largest omega_p^2 / m_a^2 on the surface: max over n of
+  // |3 n_z (m.n) - cos th_m| = (3 + |cos th_m|) / 2 (eigenvalues of the
+  // symmetrised z m^T).  A kinematic resonance needs omega_p > m_a somewhere.
+  switch (p->plasma) {
+    case RT_PLASMA_GJ: s->wp2_surface_max = h.cp * 0.5 * (3.0 + std::fabs(h.cos_tm)); break;
+    case RT_PLASMA_HOMOG: s->wp2_surface_max = p->plasma_a; break;
+    case RT_PLASMA_LINEAR_Z: s->wp2_surface_max = std::fabs(p->plasma_a) * 1e30; break;
+    default: s->wp2_surface_max = 0.0; break;
+  }
+  s->empty = !(s->wp2_surface_max > 1.0);
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  void* blk = nullptr;
+  e = cudaMalloc(&blk, 256 + sizeof(rtk::StarDev));
+  if (e != cudaSuccess) {
+    delete s;
+    return (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "cudaMalloc failed")
+                                            : cuda_fail(e, "cudaMalloc");
+  }
+  s->d_queue = (unsigned long long*)blk;
+  s->d = (rtk::StarDev*)((char*)blk + 256);
+  e = cudaMemcpy(s->d, &h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    delete s;
+    return cuda_fail(e, "cudaMemcpy");
+  }
+  *out = s;
+  return RT_OK;
+}
+
+void rt_destroy_star(rt_star* s) {
+  if (!s) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) cudaSetDevice(s->device);
+  if (s->d_bins) cudaFree(s->d_bins);
+  if (s->d_queue) cudaFree(s->d_queue);
+  if (cur != s->device) cudaSetDevice(cur);
+  delete s;
+}
+
+rt_status rt_star_info(const rt_star* s, double* out) {
+  if (!s || !out) return fail(RT_EINVAL, "NULL argument");
+  out[0] = s->h.rs;
+  out[1] = s->h.cp;
+  out[2] = s->h.B0_eV2;
+  out[3] = s->h.R_eV;
+  out[4] = s->h.n_inf;
+  out[5] = s->h.v0;
+  out[6] = s->wp2_surface_max;
+  out[7] = s->empty ? 1.0 : 0.0;
+  return RT_OK;
+}
+
+rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double* d_u,
+                                       double* d_state, double* d_weight, uint8_t* d_status,
+                                       void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
+  if (n == 0) return s->empty ? RT_EEMPTY_SURFACE : RT_OK;
+  rt_status st;
+  if ((st = check_dev_ptr(d_u, "d_uniforms")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_weight, "d_weight")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  rtk::SampleParams p;
+  p.s = s->h;
+  p.n = n;
+  p.u = d_u;
+  p.state = d_state;
+  p.weight = d_weight;
+  p.status = d_status;
+  cudaError_t e = rtk::launch_sample(p, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sample kernel");
+  return s->empty ? RT_EEMPTY_SURFACE : RT_OK;
+}
+
+static rt_status check_opts(const rt_trace_opts* o) {
+  if (!o) return fail(RT_EINVAL, "opts is NULL");
+  if (!(o->rtol > 0 && o->rtol < 1) || !(o->atol > 0 && o->atol < 1))
+    return fail(RT_EINVAL, "rtol and atol must be in (0, 1)");
+  if (!(o->r_capture_over_R > 0) || !(o->r_out_over_R > o->r_capture_over_R) ||
+      !is_finite_val(o->r_out_over_R))
+    return fail(RT_EINVAL, "need 0 < r_capture_over_R < r_out_over_R < inf");
+  if (!(o->lambda_max >= 0) || !is_finite_val(o->lambda_max))
+    return fail(RT_EINVAL, "lambda_max must be finite and >= 0");
+  if (o->max_steps <= 0) return fail(RT_EINVAL, "max_steps must be > 0");
+  if (o->max_steps > (1 << 28)) return fail(RT_EINVAL, "max_steps too large");
+  if (o->precision != RT_PREC_FP64 && o->precision != RT_PREC_MIXED)
+    return fail(RT_EINVAL, "unknown precision %d", o->precision);
+  if (o->block < 0 || o->blocks_per_sm < 0) return fail(RT_EINVAL, "negative launch parameter");
+  return RT_OK;
+}
+
+rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t* d_status,
+                           int32_t* d_nacc, int32_t* d_nrej, int64_t* d_counters,
+                           const rt_trace_opts* o, void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (n == 0) return RT_OK;
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
+  if (d_nrej && (st = check_dev_ptr(d_nrej, "d_nrej")) != RT_OK) return st;
+  if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
+  if (o->precision != RT_PREC_FP64)
+    return fail(RT_EUNSUPPORTED, "precision %d not available", o->precision);
+  rtk::TraceParams p;
+  p.stars = s->d;
+  p.nstars = 1;
+  p.offsets = nullptr;
+  p.n = n;
+  p.state = d_state;
+  p.status = d_status;
+  p.nacc = d_nacc;
+  p.nrej = d_nrej;
+  p.counters = d_counters;
+  p.queue = s->d_queue;
+  p.rtol = o->rtol;
+  p.atol = o->atol;
+  p.r_out = o->r_out_over_R;
+  p.lambda_max = o->lambda_max;
+  p.r_capture = o->r_capture_over_R;
+  p.max_steps = o->max_steps;
+  cudaError_t e = rtk::launch_trace_fp64(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace kernel");
+  return RT_OK;
+}
+
+rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
+                          const double* d_weight, const uint8_t* d_status, int32_t nth,
+                          int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,
+                          double* d_sky, double* d_spec, double* d_oor, void* stream) {
+  rt_star* s = const_cast<rt_star*>(s_);
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
+  if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
+  if ((int64_t)nth * nph * nnu > (int64_t)1 << 28) return fail(RT_EINVAL, "too many bins");
+  if (!is_finite_val(nu_lo) || !is_finite_val(nu_hi) || !(nu_hi > nu_lo))
+    return fail(RT_EINVAL, "need finite nu_lo < nu_hi");
+  rt_status st;
+  if (n > 0) {
+    if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_weight, "d_weight")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  }
+  if ((st = check_dev_ptr(d_hist, "d_hist")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_oor, "d_out_of_range")) != RT_OK) return st;
+  if (d_sky && (st = check_dev_ptr(d_sky, "d_sky")) != RT_OK) return st;
+  if (d_spec && (st = check_dev_ptr(d_spec, "d_spec")) != RT_OK) return st;
+  const size_t need = rtk::bin_scratch_entries(nth, nph, nnu);
+  if (need > s->bins_cap) {
+    if (s->d_bins) {
+      cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+      cudaFree(s->d_bins);
+      s->d_bins = nullptr;
+      s->bins_cap = 0;
+    }
+    void* b = nullptr;
+    cudaError_t e = cudaMalloc(&b, need * sizeof(long long));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RT_ENOMEM, "cannot allocate %zu bytes of binning scratch",
+                  need * sizeof(long long));
+    }
+    s->d_bins = (long long*)b;
+    s->bins_cap = need;
+  }
+  rtk::BinParams p;
+  p.star = s->d;
+  p.n = n;
+  p.state = d_state;
+  p.weight = d_weight;
+  p.status = d_status;
+  p.nth = nth;
+  p.nph = nph;
+  p.nnu = nnu;
+  p.nu_lo = nu_lo;
+  p.nu_hi = nu_hi;
+  p.acc = s->d_bins;
+  p.hist = d_hist;
+  p.sky = d_sky;
+  p.spec = d_spec;
+  p.oor = d_oor;
+  cudaError_t e = rtk::launch_bin(p, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bin kernels");
+  return RT_OK;
+}
+
+rt_status rt_count_status(int64_t n, const uint8_t* d_status, int64_t* counts, void* stream) {
+  if (!counts) return fail(RT_EINVAL, "counts is NULL");
+  for (int i = 0; i < RT_RAY_NSTATUS; ++i) counts[i] = 0;
+  if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
+  if (n == 0) return RT_OK;
+  rt_status st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  std::vector<uint8_t> h((size_t)n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), d_status, (size_t)n, cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  for (int64_t i = 0; i < n; ++i) {
+    if (h[i] >= RT_RAY_NSTATUS) return fail(RT_EINVAL, "invalid status %d at %lld", h[i], (long long)i);
+    counts[h[i]]++;
+  }
+  if (counts[RT_RAY_MAXSTEPS] || counts[RT_RAY_NAN] || counts[RT_RAY_STIFF]) return RT_EPARTIAL;
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Host-side declarations shared between the C ABI (rt_abi.cu) and the kernel
+// translation units.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_device.cuh"
+
+namespace rtk {
+
+struct TraceParams {
+  const StarDev* stars;     // device array of nstars star descriptors
+  int nstars;
+  const int64_t* offsets;   // device, nstars + 1 ray offsets (unused when nstars == 1)
+  int64_t n;
+  double* state;
+  uint8_t* status;
+  int32_t* nacc;
+  int32_t* nrej;
+  int64_t* counters;
+  unsigned long long* queue;  // scratch: next unclaimed ray
+  double rtol, atol, r_out, lambda_max, r_capture;
+  int max_steps;
+};
+
+struct SampleParams {
+  StarDev s;
+  int64_t n;
+  const double* u;
+  double* state;
+  double* weight;
+  uint8_t* status;
+};
+
+struct BinParams {
+  const StarDev* star;      // device descriptor
+  int64_t n;
+  const double* state;
+  const double* weight;
+  const uint8_t* status;
+  int nth, nph, nnu;
+  double nu_lo, nu_hi;
+  long long* acc;           // scratch: [0] max weight bits, [1] out of range, hist, sky, spec
+  double* hist;
+  double* sky;
+  double* spec;
+  double* oor;
+};
+
+cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
+cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,
+                              cudaStream_t stream);
+cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
+
+// Number of int64 scratch entries rt_bin_spectrum needs.
+inline size_t bin_scratch_entries(int nth, int nph, int nnu) {
+  return 2 + (size_t)nth * nph * nnu + (size_t)nth * nph + (size_t)nnu;
+}
+
+}  // namespace rtk

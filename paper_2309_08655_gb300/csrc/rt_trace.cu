@@ -1,0 +1,316 @@
+// Persistent forward ray-tracing kernel: one thread per ray, Dormand-Prince
+// 5(4) adaptive integration of Hamilton's equations (Eq. Hamilton) with the
+// analytic right-hand side of rt_device.cuh, warp-level refill of finished
+// lanes from a global work queue (ballot + popc prefix, one atomic per warp
+// refill).  Termination (Sec. 2.2): r = r_out located on the dense output,
+// capture at r <= r_capture, lambda_max, or the step bounds.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_device.cuh"
+#include "rt_internal.h"
+
+namespace rtk {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ void rhs64(const RayConst<double>& c, const double* y, double* f) {
+  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+}
+
+__device__ __forceinline__ double step_factor(double err, bool accepted, bool last_rej) {
+  double fac = (err > 0.0) ? 0.9 * pow(err, -0.2) : 5.0;
+  fac = fmin(5.0, fmax(0.2, fac));
+  if (!accepted || last_rej) fac = fmin(fac, 1.0);
+  return fac;
+}
+
+// Hairer's two-evaluation initial step (order 5).
+__device__ double initial_step(const RayConst<double>& c, const double* y0, const double* f0,
+                               double rtol, double atol, double hmax) {
+  double dnf = 0.0, dny = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double sk = atol + rtol * fabs(y0[i]);
+    dnf += (f0[i] / sk) * (f0[i] / sk);
+    dny += (y0[i] / sk) * (y0[i] / sk);
+  }
+  double h = (dnf <= 1e-10 || dny <= 1e-10) ? 1e-6 : sqrt(dny / dnf) * 0.01;
+  h = fmin(h, hmax);
+  double y1[6], f1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y1[i] = y0[i] + h * f0[i];
+  rhs64(c, y1, f1);
+  double der2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double sk = atol + rtol * fabs(y0[i]);
+    der2 += ((f1[i] - f0[i]) / sk) * ((f1[i] - f0[i]) / sk);
+  }
+  der2 = sqrt(der2) / h;
+  const double der12 = fmax(fabs(der2), sqrt(dnf));
+  const double h1 = (der12 <= 1e-15) ? fmax(1e-6, h * 1e-3) : pow(0.01 / der12, 0.2);
+  return fmin(fmin(100.0 * h, h1), hmax);
+}
+
+struct Lane {
+  RayConst<double> c;
+  double y[6], f0[6];
+  double h, lam;
+  int na, nr;
+  bool last_rej;
+  double R_km, ma_eV;
+};
+
+__device__ __forceinline__ int find_star(const TraceParams& p, int64_t i) {
+  if (p.nstars <= 1) return 0;
+  int lo = 0, hi = p.nstars - 1;   // offsets[s] <= i < offsets[s + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.offsets[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ void load_lane(const TraceParams& p, int64_t i, Lane& L) {
+  const StarDev& s = p.stars[find_star(p, i)];
+  const int64_t n = p.n;
+  L.R_km = s.R_km;
+  L.ma_eV = s.ma_eV;
+  const double iR = 1.0 / s.R_km, im = 1.0 / s.ma_eV;
+  L.y[0] = p.state[i] * iR;
+  L.y[1] = p.state[n + i] * iR;
+  L.y[2] = p.state[2 * n + i] * iR;
+  L.y[3] = p.state[3 * n + i] * im;
+  L.y[4] = p.state[4 * n + i] * im;
+  L.y[5] = p.state[5 * n + i] * im;
+  const double om = 1.0 + p.state[6 * n + i];
+  const double psi = p.state[7 * n + i];
+  double sp, cpsi;
+  sincos(psi, &sp, &cpsi);
+  L.c.rs = s.rs_prop;
+  L.c.cp = s.cp;
+  L.c.pa = s.plasma_a;
+  L.c.W2 = om * om;
+  L.c.iW2 = 1.0 / (om * om);
+  L.c.m0 = s.sin_tm * cpsi;
+  L.c.m1 = s.sin_tm * sp;
+  L.c.m2 = s.cos_tm;
+  L.c.disp = s.dispersion;
+  L.c.plasma = s.plasma;
+  rhs64(L.c, L.y, L.f0);
+  const double hmax = (p.lambda_max > 0.0) ? p.lambda_max : 1e30;
+  L.h = initial_step(L.c, L.y, L.f0, p.rtol, p.atol, hmax);
+  L.lam = 0.0;
+  L.na = 0;
+  L.nr = 0;
+  L.last_rej = false;
+}
+
+__device__ void store_lane(const TraceParams& p, int64_t i, const Lane& L, int st) {
+  const int64_t n = p.n;
+  p.state[i] = L.y[0] * L.R_km;
+  p.state[n + i] = L.y[1] * L.R_km;
+  p.state[2 * n + i] = L.y[2] * L.R_km;
+  p.state[3 * n + i] = L.y[3] * L.ma_eV;
+  p.state[4 * n + i] = L.y[4] * L.ma_eV;
+  p.state[5 * n + i] = L.y[5] * L.ma_eV;
+  p.status[i] = (uint8_t)st;
+  if (p.nacc) p.nacc[i] = L.na;
+  if (p.nrej) p.nrej[i] = L.nr;
+}
+
+// One attempted Dormand-Prince step.  Returns -1 to continue, else the final
+// ray status.
+__device__ int advance(const TraceParams& p, Lane& L) {
+  if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
+  bool clipped = false;
+  double h = L.h;
+  if (p.lambda_max > 0.0 && L.lam + h >= p.lambda_max) {
+    h = p.lambda_max - L.lam;
+    clipped = true;
+  }
+  const double* y = L.y;
+  const double* k1 = L.f0;
+  double t[6], k2[6], k3[6], k4[6], k5[6], k6[6], k7[6], yn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (DP::a21 * k1[i]);
+  rhs64(L.c, t, k2);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (DP::a31 * k1[i] + DP::a32 * k2[i]);
+  rhs64(L.c, t, k3);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a41 * k1[i] + DP::a42 * k2[i] + DP::a43 * k3[i]);
+  rhs64(L.c, t, k4);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a51 * k1[i] + DP::a52 * k2[i] + DP::a53 * k3[i] + DP::a54 * k4[i]);
+  rhs64(L.c, t, k5);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a61 * k1[i] + DP::a62 * k2[i] + DP::a63 * k3[i] + DP::a64 * k4[i] +
+                       DP::a65 * k5[i]);
+  rhs64(L.c, t, k6);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    yn[i] = y[i] + h * (DP::b1 * k1[i] + DP::b3 * k3[i] + DP::b4 * k4[i] + DP::b5 * k5[i] +
+                        DP::b6 * k6[i]);
+  rhs64(L.c, yn, k7);
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double e = h * (DP::e1 * k1[i] + DP::e3 * k3[i] + DP::e4 * k4[i] + DP::e5 * k5[i] +
+                          DP::e6 * k6[i] + DP::e7 * k7[i]);
+    const double sc = p.atol + p.rtol * fmax(fabs(y[i]), fabs(yn[i]));
+    s += (e / sc) * (e / sc);
+  }
+  const double en = sqrt(s / 6.0);
+  if (!isfinite(en)) {
+    ++L.nr;
+    L.h = h * 0.2;
+    L.last_rej = true;
+    return (L.h < 1e-12) ? RAY_NAN : -1;
+  }
+  if (en <= 1.0) {
+    ++L.na;
+    const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+    if (rnew >= p.r_out) {
+      // locate |x(th)| = r_out on the continuous extension by bisection
+      double r3[6], r4[6], r5[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double r2 = yn[i] - y[i];
+        r3[i] = h * k1[i] - r2;
+        r4[i] = r2 - h * k7[i] - r3[i];
+        r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
+                     DP::d6 * k6[i] + DP::d7 * k7[i]);
+        t[i] = r2;
+      }
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double xd[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          xd[i] = y[i] + mid * (t[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+        const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+        if (rd < p.r_out) lo = mid; else hi = mid;
+      }
+      const double th = 0.5 * (lo + hi);
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        yn[i] = y[i] + th * (t[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+#pragma unroll
+      for (int i = 0; i < 6; ++i) L.y[i] = yn[i];
+      L.lam += th * h;
+      return RAY_ESCAPED;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      L.y[i] = yn[i];
+      L.f0[i] = k7[i];
+    }
+    L.lam += h;
+    if (rnew <= p.r_capture) return RAY_CAPTURED;
+    if (clipped) return RAY_LAMBDA_END;
+    L.h = h * step_factor(en, true, L.last_rej);
+    L.last_rej = false;
+    return -1;
+  }
+  ++L.nr;
+  L.h = h * step_factor(en, false, L.last_rej);
+  L.last_rej = true;
+  return (L.h < 1e-12) ? RAY_STIFF : -1;
+}
+
+__global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
+  const int lane = threadIdx.x & 31;
+  int64_t ray = -1;   // -1: needs a ray, -2: queue exhausted
+  Lane L;
+  long long acc = 0, rej = 0, traced = 0, esc = 0;
+  for (;;) {
+    const bool need = (ray == -1);
+    const unsigned mneed = __ballot_sync(FULL, need);
+    if (mneed) {
+      const int leader = __ffs(mneed) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
+        if (idx >= p.n) {
+          ray = -2;
+        } else if (p.status[idx] != RAY_READY) {
+          ray = -1;
+        } else {
+          ray = idx;
+          load_lane(p, idx, L);
+        }
+      }
+    }
+    const unsigned live = __ballot_sync(FULL, ray != -2);
+    if (live == 0) break;
+    if (ray >= 0) {
+      const int st = advance(p, L);
+      if (st >= 0) {
+        store_lane(p, ray, L, st);
+        acc += L.na;
+        rej += L.nr;
+        traced += 1;
+        esc += (st == RAY_ESCAPED);
+        ray = -1;
+      }
+    }
+  }
+  if (p.counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_down_sync(FULL, acc, o);
+      rej += __shfl_down_sync(FULL, rej, o);
+      traced += __shfl_down_sync(FULL, traced, o);
+      esc += __shfl_down_sync(FULL, esc, o);
+    }
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&p.counters[0], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&p.counters[1], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&p.counters[2], (unsigned long long)traced);
+      atomicAdd((unsigned long long*)&p.counters[3], (unsigned long long)esc);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,
+                              cudaStream_t stream) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (block <= 0) block = 128;
+  if (block > 128) block = 128;            // __launch_bounds__(128)
+  block = (block / 32) * 32;
+  if (block < 32) block = 32;
+  if (blocks_per_sm <= 0) {
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_fp64_kernel, block, 0);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = occ > 0 ? occ : 1;
+  }
+  const int64_t warps_needed = (p.n + 31) / 32;
+  int64_t grid = (int64_t)nsm * blocks_per_sm;
+  const int64_t max_useful = (warps_needed * 32 + block - 1) / block;
+  if (grid > max_useful) grid = max_useful;
+  if (grid < 1) grid = 1;
+  e = cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  trace_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of the C ABI in ``include/rt.h`` (same function names).
+
+Only argument marshalling happens here: torch tensors provide device memory
+(``data_ptr()``) and the stream (``torch.cuda.current_stream()``); every step
+of the computation runs in the CUDA library.  If the library is missing or a
+CUDA device is absent, calls raise ``RtError`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import library_path
+
+STATE_ROWS = 8
+UNIFORM_ROWS = 6
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_EEMPTY_SURFACE, RT_EPARTIAL, RT_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EEMPTY_SURFACE", "EPARTIAL", "EUNSUPPORTED"]
+(RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT, RAY_MAXSTEPS, RAY_NAN, RAY_STIFF,
+ RAY_LAMBDA_END) = range(8)
+RAY_NSTATUS = 8
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class rt_star_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in [
+        "M_sun", "R_km", "B0_G", "P_s", "theta_m_rad", "psi_rad", "m_a_eV", "g_agg_GeVinv",
+        "rho_dm_GeV_cm3", "v0_kms"]] + [(k, ctypes.c_int32) for k in [
+            "dispersion", "resonance", "fa_model", "weight_mode", "prop_metric", "phase_mode",
+            "plasma", "reserved"]] + [("plasma_a", ctypes.c_double)]
+
+
+class rt_trace_opts(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in [
+        "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
+        (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm"]]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RtError(RT_ECUDA, f"CUDA library not built ({path}); run "
+                                    "paper_2309_08655_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        L.rt_init_star.restype = ctypes.c_int
+        L.rt_init_star.argtypes = [ctypes.POINTER(rt_star_params), ctypes.POINTER(_vp)]
+        L.rt_destroy_star.restype = None
+        L.rt_destroy_star.argtypes = [_vp]
+        L.rt_star_info.restype = ctypes.c_int
+        L.rt_star_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        L.rt_sample_conversion_surface.restype = ctypes.c_int
+        L.rt_sample_conversion_surface.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+        L.rt_trace_forward.restype = ctypes.c_int
+        L.rt_trace_forward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
+                                       ctypes.POINTER(rt_trace_opts), _vp]
+        L.rt_bin_spectrum.restype = ctypes.c_int
+        L.rt_bin_spectrum.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.rt_count_status.restype = ctypes.c_int
+        L.rt_count_status.argtypes = [ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+        L.rt_last_error.restype = ctypes.c_char_p
+        L.rt_last_error.argtypes = []
+        L.rt_version.restype = ctypes.c_int32
+        L.rt_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(status: int, allow=(RT_OK,)) -> int:
+    if status not in allow:
+        raise RtError(status, lib().rt_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a tensor (or None / int)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(**kw) -> rt_star_params:
+    """rt_star_params from keyword arguments; unspecified fields are 0 except
+    the paper's fiducial values for the coupling, density and dispersion."""
+    p = rt_star_params()
+    p.g_agg_GeVinv = 1e-12
+    p.rho_dm_GeV_cm3 = 0.45
+    p.v0_kms = 200.0
+    alias = {"theta_m": "theta_m_rad", "psi": "psi_rad", "g_GeVinv": "g_agg_GeVinv",
+             "rho_GeV_cm3": "rho_dm_GeV_cm3"}
+    for k, v in kw.items():
+        setattr(p, alias.get(k, k), v)
+    return p
+
+
+def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capture_over_R=1.0,
+              precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0) -> rt_trace_opts:
+    o = rt_trace_opts()
+    o.rtol = rtol
+    o.atol = rtol if atol is None else atol
+    o.r_out_over_R = r_out_over_R
+    o.lambda_max = lambda_max
+    o.r_capture_over_R = r_capture_over_R
+    o.precision = precision
+    o.max_steps = max_steps
+    o.block = block
+    o.blocks_per_sm = blocks_per_sm
+    return o
+
+
+class Star:
+    """Owning wrapper of an ``rt_star`` handle."""
+
+    def __init__(self, params: rt_star_params | None = None, **kw):
+        if params is None:
+            params = make_params(**kw)
+        h = _vp()
+        _check(lib().rt_init_star(ctypes.byref(params), ctypes.byref(h)))
+        self.handle = h
+        self.params = params
+
+    def info(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        _check(lib().rt_star_info(self.handle, out))
+        keys = ["rs_over_R", "wp2_coef", "B0_eV2", "R_inv_eV", "n_inf_eV3", "v0",
+                "wp2_surface_max", "empty"]
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_destroy_star(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_init_star(params: rt_star_params) -> Star:
+    return Star(params)
+
+
+def rt_destroy_star(star: Star) -> None:
+    star.close()
+
+
+def rt_sample_conversion_surface(star: Star, n, uniforms, state, weight, status, stream=None,
+                                 allow_empty=True) -> int:
+    allow = (RT_OK, RT_EEMPTY_SURFACE) if allow_empty else (RT_OK,)
+    return _check(lib().rt_sample_conversion_surface(
+        star.handle, int(n), _ptr(uniforms), _ptr(state), _ptr(weight), _ptr(status),
+        _stream(stream)), allow)
+
+
+def rt_trace_forward(star: Star, n, state, status, nacc=None, nrej=None, counters=None,
+                     opts: rt_trace_opts | None = None, stream=None) -> int:
+    if opts is None:
+        opts = make_opts()
+    return _check(lib().rt_trace_forward(
+        star.handle, int(n), _ptr(state), _ptr(status), _ptr(nacc), _ptr(nrej), _ptr(counters),
+        ctypes.byref(opts), _stream(stream)))
+
+
+def rt_bin_spectrum(star: Star, n, state, weight, status, nth, nph, nnu, nu_lo, nu_hi, hist,
+                    sky=None, spec=None, out_of_range=None, stream=None) -> int:
+    return _check(lib().rt_bin_spectrum(
+        star.handle, int(n), _ptr(state), _ptr(weight), _ptr(status), int(nth), int(nph),
+        int(nnu), float(nu_lo), float(nu_hi), _ptr(hist), _ptr(sky), _ptr(spec),
+        _ptr(out_of_range), _stream(stream)))
+
+
+def rt_count_status(n, status, stream=None) -> tuple[int, list[int]]:
+    counts = (ctypes.c_int64 * RAY_NSTATUS)()
+    st = _check(lib().rt_count_status(int(n), _ptr(status), counts, _stream(stream)),
+                (RT_OK, RT_EPARTIAL))
+    return st, list(counts)
+
+
+def rt_last_error() -> str:
+    return lib().rt_last_error().decode()
+
+
+def rt_version() -> int:
+    return int(lib().rt_version())
+
+
+EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conversion_surface",
+            "rt_trace_forward", "rt_bin_spectrum", "rt_count_status", "rt_last_error",
+            "rt_version"]

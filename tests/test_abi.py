@@ -1,0 +1,64 @@
+"""The C ABI library: builds for sm_103a, loads, exports every symbol that
+include/rt.h declares, and validates arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2309_08655_gb300 import build as B
+from paper_2309_08655_gb300 import rt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return rt.lib()
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "rt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared_functions()
+    assert "rt_trace_forward" in names and len(names) >= 8
+    for name in names:
+        assert hasattr(L, name), name
+    for name in rt.EXPORTED:
+        assert name in names
+
+
+def test_struct_layouts_match_header():
+    # 10 doubles, 8 int32, 1 double / 5 doubles, 4 int32 (no padding surprises)
+    assert ctypes.sizeof(rt.rt_star_params) == 10 * 8 + 8 * 4 + 8
+    assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 4 * 4
+    assert rt.rt_star_params.plasma_a.offset == 112
+
+
+def test_version_and_error_paths_without_gpu(L):
+    assert rt.rt_version() >= 100
+    with pytest.raises(rt.RtError) as e:
+        rt.Star(rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=-1.0))
+    assert e.value.status == rt.RT_EINVAL and "m_a_eV" in str(e.value)
+    with pytest.raises(rt.RtError) as e:
+        rt.Star(rt.make_params(M_sun=5.0, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5))
+    assert e.value.status == rt.RT_EINVAL          # R below the Schwarzschild radius
+    with pytest.raises(rt.RtError) as e:
+        rt.Star(rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5,
+                               dispersion=7))
+    assert e.value.status == rt.RT_EUNSUPPORTED
+    st = L.rt_trace_forward(None, 10, None, None, None, None, None, None, None)
+    assert st == rt.RT_EINVAL
+    st = L.rt_init_star(None, ctypes.byref(ctypes.c_void_p()))
+    assert st == rt.RT_EINVAL and b"NULL" in L.rt_last_error()
+
+
+def test_objects_are_sm103a():
+    # every object is compiled for sm_103a only (one -gencode)
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(B.library_path())

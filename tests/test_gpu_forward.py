@@ -1,0 +1,213 @@
+"""Parity of the CUDA forward path (sampling, FP64 tracing, binning) with the
+FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerances: FP64 end points 1e-10 relative on the well-conditioned set (rays
+whose oracle end point moves by < 100 rtol when rtol is divided by 10); binned
+flux 1e-4 relative L1; sampled states and weights 1e-12 (both sides take the
+same FP64 root, differing only in rounding).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2309_08655_gb300 import inputs as I  # noqa: E402
+from paper_2309_08655_gb300 import rt  # noqa: E402
+
+from . import gpu_util as G  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2309_08655_gb300.build import build
+    build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _star_vec(oracle, kw):
+    return oracle.star_vector(**kw)
+
+
+def _config0(n=4096, first=0):
+    kw = I.star_config0()
+    u = I.sample_uniforms(I.CONFIG0["seed"], n, first)
+    return kw, u
+
+
+def test_sample_parity_config0(oracle):
+    kw, u = _config0()
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, u)
+    assert code == rt.RT_OK
+    st_g, w_g, s_g = G.to_np(st_d, w_d, s_d)
+    st_o, w_o, s_o = oracle.sample(_star_vec(oracle, kw), u)
+    assert np.array_equal(s_g, s_o)
+    ok = s_o == oracle.RAY_READY
+    assert ok.sum() > 3000
+    assert G.rel_state_diff(st_g[:, ok], st_o[:, ok]).max() < 1e-12
+    assert np.array_equal(st_g[6:], st_o[6:]) or np.abs(st_g[6:] - st_o[6:]).max() < 1e-22
+    assert np.abs(w_g[ok] / w_o[ok] - 1).max() < 1e-11
+    assert np.all(w_g[~ok] == 0)
+
+
+@pytest.mark.parametrize("sub", [0, 5, 7, 13])
+def test_sample_parity_misaligned_rotator(oracle, sub):
+    kw = I.stars_config1()[sub]
+    u = I.sample_uniforms(100 + sub, 2048)
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, u)
+    st_g, w_g, s_g = G.to_np(st_d, w_d, s_d)
+    st_o, w_o, s_o = oracle.sample(_star_vec(oracle, kw), u)
+    info = star.info()
+    if info["empty"]:
+        assert code == rt.RT_EEMPTY_SURFACE
+        assert np.all(s_g == rt.RAY_NO_ROOT) and np.all(w_g == 0)
+    else:
+        assert code == rt.RT_OK
+    assert np.array_equal(s_g, s_o)
+    ok = s_o == oracle.RAY_READY
+    if ok.any():
+        assert G.rel_state_diff(st_g[:, ok], st_o[:, ok]).max() < 1e-12
+        assert np.abs(w_g[ok] / w_o[ok] - 1).max() < 1e-11
+    assert np.allclose(st_g[7], st_o[7], rtol=0, atol=1e-15)
+
+
+def _trace_parity(oracle, kw, u, rtol=1e-10, **topt):
+    """GPU and oracle trace the same (oracle-sampled) initial states."""
+    sv = _star_vec(oracle, kw)
+    st0, w0, s0 = oracle.sample(sv, u)
+    ref, sref, good = G.well_conditioned(oracle, sv, st0, s0, rtol, **topt)
+    star = rt.Star(rt.make_params(**kw))
+    st_d = torch.from_numpy(st0.copy()).cuda()
+    s_d = torch.from_numpy(s0.copy()).cuda()
+    nacc, nrej, ctr = G.gpu_trace(star, st_d, s_d, rtol=rtol, **_gpu_opts(topt))
+    st_g, s_g, na = G.to_np(st_d, s_d, nacc)
+    return st0, s0, ref, sref, good, st_g, s_g, na, ctr.cpu().numpy()
+
+
+def _gpu_opts(topt):
+    m = {"r_out_over_R": "r_out_over_R", "max_steps": "max_steps", "lambda_max": "lambda_max",
+         "r_capture_over_R": "r_capture_over_R"}
+    return {m[k]: v for k, v in topt.items()}
+
+
+def test_trace_parity_config0_fp64(oracle):
+    kw, u = _config0()
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _trace_parity(oracle, kw, u, rtol=1e-10)
+    traced = s0 == oracle.RAY_READY
+    # statuses agree (up to the rare ill-conditioned grazing ray)
+    assert (s_g[traced] == sref[traced]).mean() > 0.995
+    g = good & traced & (s_g == sref)
+    assert g.sum() > 0.85 * traced.sum()
+    d = G.rel_state_diff(st_g[:, g], ref[:, g])
+    assert d.max() < 1e-10, np.sort(d)[-5:]
+    # the step counters add up
+    assert ctr[2] == traced.sum()
+    assert ctr[0] == na.sum()
+    assert ctr[3] == (s_g == rt.RAY_ESCAPED).sum()
+
+
+def test_bin_parity_config0(oracle):
+    kw, u = _config0()
+    sv = _star_vec(oracle, kw)
+    star, st_d, w_d, s_d, _ = G.gpu_sample(kw, u)
+    G.gpu_trace(star, st_d, s_d, rtol=1e-10)
+    hist, sky, spec, oor = G.gpu_bin(star, st_d, w_d, s_d)
+    st_o, w_o, s_o = oracle.sample(sv, u)
+    oracle.trace_forward(sv, oracle.trace_opts(rtol=1e-10), st_o, s_o)
+    h_o, oor_o = oracle.bin_rays(sv, st_o, w_o, s_o)
+    l1 = np.abs(hist - h_o).sum() / h_o.sum()
+    assert l1 < 1e-4, l1
+    w_g = w_d.cpu().numpy()
+    s_g = s_d.cpu().numpy()
+    esc = w_g[s_g == rt.RAY_ESCAPED].sum()
+    assert abs(hist.sum() + oor - esc) <= 1e-9 * esc
+    assert np.allclose(sky, hist.sum(axis=2), rtol=1e-12, atol=0)
+    assert np.allclose(spec, hist.sum(axis=(0, 1)), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 257])
+def test_ragged_sizes(oracle, n):
+    kw, u = _config0(n, first=777)
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _trace_parity(oracle, kw, u)
+    g = good & (s0 == 0) & (s_g == sref)
+    if g.any():
+        assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+
+
+def test_zero_rays_and_empty_surface():
+    kw = I.star_config0()
+    star = rt.Star(rt.make_params(**kw))
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert rt.rt_sample_conversion_surface(star, 0, e, e, e, e) == rt.RT_OK
+    assert rt.rt_trace_forward(star, 0, e, e) == rt.RT_OK
+    heavy = dict(kw, m_a_eV=1e-3)
+    u = I.sample_uniforms(9, 512)
+    star2, st, w, s, code = G.gpu_sample(heavy, u)
+    assert code == rt.RT_EEMPTY_SURFACE
+    assert bool((s == rt.RAY_NO_ROOT).all()) and float(w.abs().sum()) == 0.0
+    nacc, nrej, ctr = G.gpu_trace(star2, st, s)
+    assert int(ctr[2]) == 0 and bool((s == rt.RAY_NO_ROOT).all())
+
+
+def test_max_steps_bound_matches_oracle(oracle):
+    kw, u = _config0(256, first=4096)
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _trace_parity(oracle, kw, u, max_steps=40)
+    traced = s0 == 0
+    assert np.array_equal(s_g[traced], sref[traced])
+    assert (s_g == rt.RAY_MAXSTEPS).sum() > 10
+    code, counts = rt.rt_count_status(256, torch.from_numpy(s_g).cuda())
+    assert code == rt.RT_EPARTIAL and counts[rt.RAY_MAXSTEPS] == (s_g == rt.RAY_MAXSTEPS).sum()
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    kw = I.star_config0()
+    star = rt.Star(rt.make_params(**kw))
+    st = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    s = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_forward(star, 4, st, s, opts=rt.make_opts(rtol=-1.0))
+    assert e.value.status == rt.RT_EINVAL
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_forward(star, 4, st.cpu(), s)      # host memory is refused
+    assert e.value.status == rt.RT_EINVAL
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_bin_spectrum(star, 4, st, st[0], s, 0, 32, 128, 0.0, 9.0, st)
+    assert e.value.status == rt.RT_EINVAL
+
+
+def test_deterministic_bitwise():
+    kw, u = _config0(2048)
+    outs = []
+    for _ in range(2):
+        star, st, w, s, _ = G.gpu_sample(kw, u)
+        G.gpu_trace(star, st, s)
+        h = G.gpu_bin(star, st, w, s)[0]
+        outs.append((st.cpu().numpy(), s.cpu().numpy(), h))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_closed_form_media_on_gpu():
+    # flat space, planar-stratified isotropic plasma omega_p^2 = a z: parabola
+    a = 0.02
+    kw = dict(M_sun=0.0, R_km=1.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5, dispersion=1, plasma=3,
+              plasma_a=a)
+    star = rt.Star(rt.make_params(**kw))
+    k0 = np.array([0.3, 0.1, 0.6])
+    x0 = np.array([0.0, 0.0, 10.0])
+    om2 = (k0**2).sum() + a * x0[2]
+    st = np.zeros((8, 1))
+    st[:3, 0] = x0
+    st[3:6, 0] = k0 * 1e-5
+    st[6, 0] = np.sqrt(om2) - 1
+    st_d = torch.from_numpy(st).cuda()
+    s_d = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    lam = 40.0
+    G.gpu_trace(star, st_d, s_d, rtol=1e-12, lambda_max=lam, r_out_over_R=1e9,
+                r_capture_over_R=1e-3)
+    out = st_d.cpu().numpy()[:, 0]
+    assert int(s_d.cpu()[0]) == rt.RAY_LAMBDA_END
+    assert np.allclose(out[:2], x0[:2] + 2 * k0[:2] * lam, atol=1e-9)
+    assert abs(out[2] - (x0[2] + 2 * k0[2] * lam - a * lam**2)) < 1e-8
+    assert abs(out[5] / 1e-5 - (k0[2] - a * lam)) < 1e-11
