@@ -223,7 +223,7 @@ def run_ours(args):
     st = [torch.empty(nper, dtype=torch.uint8, device=dev) for _ in range(nsub)]
     hist = torch.empty((nsub, nth, nph, nnu), dtype=torch.float64, device=dev)
     oor = torch.empty(nsub, dtype=torch.float64, device=dev)
-    ctr = torch.zeros((nsub, 4), dtype=torch.int64, device=dev)
+    ctr = torch.zeros((nsub, 8), dtype=torch.int64, device=dev)
     hist_host = torch.empty_like(hist, device="cpu").pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     opts = rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],

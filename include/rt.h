@@ -39,6 +39,7 @@ extern "C" {
 
 #define RT_STATE_ROWS 8
 #define RT_UNIFORM_ROWS 6
+#define RT_COUNTERS 8
 
 typedef enum {
   RT_OK = 0,
@@ -173,10 +174,19 @@ rt_status rt_sample_conversion_surface(const rt_star* star, int64_t n, const dou
  *   d_state    in/out: RT_STATE_ROWS x n; on escape the state at r = r_out
  *   d_status   in/out: READY rays get their final status; others untouched
  *   d_nacc, d_nrej  out (may be NULL): accepted / rejected steps per ray
- *   d_counters in/out (may be NULL): 4 int64 accumulated with atomics:
- *              accepted steps, rejected steps, rays traced, rays escaped
+ *   d_counters in/out (may be NULL): RT_COUNTERS int64 accumulated with
+ *              atomics: accepted steps, rejected steps, rays finished, rays
+ *              escaped, rays promoted from FP32 to FP64, step attempts of the
+ *              promoted rays in FP64, 2 reserved
  *   opts       integration options (host pointer, read during the call)
- * Deterministic: the same inputs give bitwise identical outputs.
+ * RT_PREC_FP64: every stage in FP64; deterministic (bitwise identical outputs
+ * for identical inputs).  RT_PREC_MIXED: the stages and their combinations run
+ * in FP32 and the state accumulates in FP64; where the FP32 rounding floor of
+ * the embedded error estimate reaches a quarter of the tolerance on a rejected
+ * step, the ray continues in FP64 from that point (a second kernel on the same
+ * stream).  Use rtol >= 1e-8 with RT_PREC_MIXED; lambda_max must be 0.
+ * Calls sharing one handle must be serialised on one stream (the handle owns
+ * the work-queue counter).
  */
 rt_status rt_trace_forward(const rt_star* star, int64_t n, double* d_state, uint8_t* d_status,
                            int32_t* d_nacc, int32_t* d_nrej, int64_t* d_counters,

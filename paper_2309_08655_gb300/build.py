@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt_axion.so")
-SOURCES = ["rt_abi.cu", "rt_sample.cu", "rt_trace.cu", "rt_bin.cu", "rt_flops.cu"]
+SOURCES = ["rt_abi.cu", "rt_sample.cu", "rt_trace.cu", "rt_trace_mixed.cu", "rt_bin.cu",
+           "rt_flops.cu"]
 HEADERS = ["rt_device.cuh", "rt_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -258,8 +258,8 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
   if (d_nrej && (st = check_dev_ptr(d_nrej, "d_nrej")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
-  if (o->precision != RT_PREC_FP64)
-    return fail(RT_EUNSUPPORTED, "precision %d not available", o->precision);
+  if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
+    return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
   rtk::TraceParams p;
   p.stars = s->d;
   p.nstars = 1;
@@ -277,7 +277,17 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.lambda_max = o->lambda_max;
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
-  cudaError_t e = rtk::launch_trace_fp64(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+  p.claim_status = rtk::RAY_READY;
+  cudaError_t e;
+  if (o->precision == RT_PREC_MIXED) {
+    e = rtk::launch_trace_mixed(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
+    p.claim_status = rtk::RAY_PROMOTED;   // FP64 pass over the promoted rays
+    e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
+    return RT_OK;
+  }
+  e = rtk::launch_trace_fp64(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "trace kernel");
   return RT_OK;
 }

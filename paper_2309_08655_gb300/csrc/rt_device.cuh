@@ -47,15 +47,35 @@ enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 enum {
   RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,
-  RAY_NAN = 5, RAY_STIFF = 6, RAY_LAMBDA_END = 7
+  RAY_NAN = 5, RAY_STIFF = 6, RAY_LAMBDA_END = 7,
+  RAY_PROMOTED = 8   // internal: handed from the FP32 pass to the FP64 pass
 };
 
-__device__ __forceinline__ double rt_rsqrt(double v) { return rsqrt(v); }
-__device__ __forceinline__ float rt_rsqrt(float v) { return rsqrtf(v); }
-__device__ __forceinline__ double rt_sqrt(double v) { return sqrt(v); }
-__device__ __forceinline__ float rt_sqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double rt_rcp(double v) { return 1.0 / v; }
-__device__ __forceinline__ float rt_rcp(float v) { return __frcp_rn(v); }
+// (The host branches exist for host-side instantiation in tests of the formula.)
+RT_HD __forceinline__ double rt_rsqrt(double v) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(v);
+#else
+  return 1.0 / sqrt(v);
+#endif
+}
+RT_HD __forceinline__ float rt_rsqrt(float v) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(v);
+#else
+  return 1.0f / sqrtf(v);
+#endif
+}
+RT_HD __forceinline__ double rt_sqrt(double v) { return sqrt(v); }
+RT_HD __forceinline__ float rt_sqrt(float v) { return sqrtf(v); }
+RT_HD __forceinline__ double rt_rcp(double v) { return 1.0 / v; }
+RT_HD __forceinline__ float rt_rcp(float v) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(v);
+#else
+  return 1.0f / v;
+#endif
+}
 
 // Constants of one ray in the working precision T.
 template <class T>

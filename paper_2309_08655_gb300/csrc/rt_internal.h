@@ -21,7 +21,12 @@ struct TraceParams {
   unsigned long long* queue;  // scratch: next unclaimed ray
   double rtol, atol, r_out, lambda_max, r_capture;
   int max_steps;
+  int claim_status;           // rays with this status are traced (READY, or PROMOTED)
 };
+
+// Per-call counters (int64): accepted steps, rejected steps, rays finished,
+// rays escaped, rays promoted from FP32 to FP64, FP64 steps of promoted rays.
+enum { CTR_ACC = 0, CTR_REJ, CTR_RAYS, CTR_ESC, CTR_PROMOTED, CTR_PROMOTED_STEPS, CTR_COUNT = 8 };
 
 struct SampleParams {
   StarDev s;
@@ -50,6 +55,8 @@ struct BinParams {
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
 cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,
                               cudaStream_t stream);
+cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
+                               cudaStream_t stream);
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
 
 // Number of int64 scratch entries rt_bin_spectrum needs.

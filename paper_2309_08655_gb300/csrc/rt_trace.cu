@@ -106,6 +106,10 @@ __device__ void load_lane(const TraceParams& p, int64_t i, Lane& L) {
   L.lam = 0.0;
   L.na = 0;
   L.nr = 0;
+  if (p.claim_status == RAY_PROMOTED) {   // resume a ray handed over by the FP32 pass
+    if (p.nacc) L.na = p.nacc[i];
+    if (p.nrej) L.nr = p.nrej[i];
+  }
   L.last_rej = false;
 }
 
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   int64_t ray = -1;   // -1: needs a ray, -2: queue exhausted
   Lane L;
   long long acc = 0, rej = 0, traced = 0, esc = 0;
+  int na0 = 0, nr0 = 0;   // steps a resumed ray had already taken in FP32
   for (;;) {
     const bool need = (ray == -1);
     const unsigned mneed = __ballot_sync(FULL, need);
@@ -244,11 +249,13 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
         const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
         if (idx >= p.n) {
           ray = -2;
-        } else if (p.status[idx] != RAY_READY) {
+        } else if (p.status[idx] != p.claim_status) {
           ray = -1;
         } else {
           ray = idx;
           load_lane(p, idx, L);
+          na0 = L.na;
+          nr0 = L.nr;
         }
       }
     }
@@ -258,8 +265,8 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       const int st = advance(p, L);
       if (st >= 0) {
         store_lane(p, ray, L, st);
-        acc += L.na;
-        rej += L.nr;
+        acc += L.na - na0;
+        rej += L.nr - nr0;
         traced += 1;
         esc += (st == RAY_ESCAPED);
         ray = -1;
@@ -275,10 +282,13 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       esc += __shfl_down_sync(FULL, esc, o);
     }
     if (lane == 0) {
-      atomicAdd((unsigned long long*)&p.counters[0], (unsigned long long)acc);
-      atomicAdd((unsigned long long*)&p.counters[1], (unsigned long long)rej);
-      atomicAdd((unsigned long long*)&p.counters[2], (unsigned long long)traced);
-      atomicAdd((unsigned long long*)&p.counters[3], (unsigned long long)esc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ACC], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_REJ], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&p.counters[CTR_RAYS], (unsigned long long)traced);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ESC], (unsigned long long)esc);
+      if (p.claim_status == RAY_PROMOTED)
+        atomicAdd((unsigned long long*)&p.counters[CTR_PROMOTED_STEPS],
+                  (unsigned long long)(acc + rej));
     }
   }
 }

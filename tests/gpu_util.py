@@ -30,7 +30,7 @@ def gpu_trace(star, state, status, **opts):
     n = state.shape[1]
     nacc = torch.zeros(n, dtype=torch.int32, device=dev())
     nrej = torch.zeros(n, dtype=torch.int32, device=dev())
-    ctr = torch.zeros(4, dtype=torch.int64, device=dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev())
     rt.rt_trace_forward(star, n, state, status, nacc, nrej, ctr, rt.make_opts(**opts))
     torch.cuda.synchronize()
     return nacc, nrej, ctr
@@ -60,15 +60,44 @@ def rel_state_diff(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.maximum(dx, dk)
 
 
-def well_conditioned(oracle, star_vec, state0, status0, rtol, limit=100.0, **kw):
-    """Oracle end states at rtol and rtol/10; rays whose end point moves by less
-    than limit * rtol between the two are the well-conditioned set."""
+def perturbed(state0, eps, seed):
+    rng = np.random.default_rng(seed)
+    p = state0.copy()
+    p[:6] *= 1.0 + eps * rng.standard_normal(p[:6].shape)
+    return p
+
+
+def well_conditioned(oracle, star_vec, state0, status0, rtol, kappa_max=1e3, eps=1e-12, **kw):
+    """Oracle end states at rtol, plus the condition number of every ray: the
+    relative end-point change per relative change of the initial state,
+    kappa = max over two random perturbations of size eps.  Rays produced
+    near a reflection, grazing the star or scattered between the plasma walls
+    of the magnetosphere amplify perturbations by many orders of magnitude
+    (chaotic scattering); GPU-vs-oracle agreement at rounding level is only
+    defined for rays with kappa * (rounding ~1e-14) well below the tolerance.
+    Returns (end states, statuses, well-conditioned mask, kappa)."""
     a = state0.copy()
     sa = status0.copy()
     oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), a, sa)
-    b = state0.copy()
+    kappa = np.zeros(state0.shape[1])
+    same = np.ones(state0.shape[1], dtype=bool)
+    for seed in (1, 2):
+        b = perturbed(state0, eps, seed)
+        sb = status0.copy()
+        oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), b, sb)
+        kappa = np.maximum(kappa, rel_state_diff(b, a) / eps)
+        same &= sb == sa
+    good = same & (kappa < kappa_max)
+    return a, sa, good, kappa
+
+
+def rounding_spread(oracle, star_vec, state0, status0, rtol, eps=1e-15, **kw):
+    """End-point spread of the oracle itself under a rounding-size (eps)
+    perturbation of the initial state: the scale GPU deviations are compared to."""
+    a = state0.copy()
+    sa = status0.copy()
+    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), a, sa)
+    b = perturbed(state0, eps, 3)
     sb = status0.copy()
-    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol / 10, **kw), b, sb)
-    sens = rel_state_diff(a, b) / rtol
-    good = (sa == sb) & (sens < limit)
-    return a, sa, good
+    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), b, sb)
+    return rel_state_diff(b, a), (sb == sa)
