@@ -48,22 +48,53 @@ RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT = 0, 1, 2, 3
 RAY_MAXSTEPS, RAY_NAN, RAY_STIFF, RAY_LAMBDA_END = 4, 5, 6, 7
 
 _lib = None
+_lib_contracted = None
+# The "contracted" build is the same source compiled with fused multiply-add
+# contraction: a second, equally valid FP64 evaluation of every formula.  The
+# spread between the two builds measures how much a ray's end point moves under
+# rounding-level changes of every operation; the GPU tests compare the CUDA
+# path's deviations against that spread.
+_SO_CONTRACTED = os.path.join(_HERE, "liboracle_contracted.so")
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so in place (g++, FP64, no FMA contraction)."""
+def _flags(variant: str) -> list[str]:
+    if variant == "contracted":
+        import platform
+        extra = ["-mfma"] if platform.machine() in ("x86_64", "AMD64") else []
+        return ["-ffp-contract=fast"] + extra
+    return ["-ffp-contract=off"]
+
+
+def build(force: bool = False, variant: str = "strict") -> str:
+    """Compile liboracle.so in place (g++, FP64; the reference build has no
+    FMA contraction)."""
+    so = _SO if variant == "strict" else _SO_CONTRACTED
     srcs = [os.path.join(_HERE, s) for s in _SRC]
     deps = srcs + [os.path.join(_HERE, h) for h in _HDR]
-    if not force and os.path.exists(_SO):
-        so_t = os.path.getmtime(_SO)
+    if not force and os.path.exists(so):
+        so_t = os.path.getmtime(so)
         if all(os.path.getmtime(d) <= so_t for d in deps):
-            return _SO
-    tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+            return so
+    tmp = so + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", *_flags(variant), "-fPIC", "-shared", "-pthread",
            "-o", tmp] + srcs
     subprocess.check_call(cmd, cwd=_HERE)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def lib_contracted():
+    global _lib_contracted
+    if _lib_contracted is None:
+        build(variant="contracted")
+        L = ctypes.CDLL(_SO_CONTRACTED)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.or_trace_forward.restype = None
+        L.or_trace_forward.argtypes = [dp, dp, ctypes.c_long, dp, ctypes.POINTER(ctypes.c_uint8),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       dp, ctypes.c_int]
+        _lib_contracted = L
+    return _lib_contracted
 
 
 def lib():
@@ -155,7 +186,7 @@ def sample(star: np.ndarray, u: np.ndarray, nthreads: int | None = None):
 
 
 def trace_forward(star: np.ndarray, opts: np.ndarray, state: np.ndarray, status: np.ndarray,
-                  nthreads: int | None = None):
+                  nthreads: int | None = None, variant: str = "strict"):
     """Traces READY rays in place.  Returns (nacc, nrej, lambda_end)."""
     assert state.flags.c_contiguous and state.dtype == np.float64 and state.shape[0] == 8
     assert status.dtype == np.uint8
@@ -163,8 +194,9 @@ def trace_forward(star: np.ndarray, opts: np.ndarray, state: np.ndarray, status:
     nacc = np.zeros(n, dtype=np.int32)
     nrej = np.zeros(n, dtype=np.int32)
     lam = np.zeros(n)
-    lib().or_trace_forward(_dp(star), _dp(opts), n, _dp(state), _u8(status), _ip(nacc),
-                           _ip(nrej), _dp(lam), nthreads or default_threads())
+    L = lib() if variant == "strict" else lib_contracted()
+    L.or_trace_forward(_dp(star), _dp(opts), n, _dp(state), _u8(status), _ip(nacc), _ip(nrej),
+                       _dp(lam), nthreads or default_threads())
     return nacc, nrej, lam
 
 

@@ -108,9 +108,19 @@ inline void dipole_field(const double m[3], const T x[3], T B[3]) {
   for (int i = 0; i < 3; ++i) B[i] = f * (3.0 * mu * n[i] - m[i]);
 }
 
-// omega_p^2 / m_a^2 at x (units of R).
+// Sign of Omega . B at x (the Goldreich-Julian charge changes sign on the null
+// cone Omega . B = 0, where |n_e| has a kink).
+inline int gj_branch(const double m[3], const double x[3]) {
+  double B[3];
+  dipole_field(m, x, B);
+  return B[2] < 0.0 ? -1 : 1;
+}
+
+// omega_p^2 / m_a^2 at x (units of R).  sigma = 0 evaluates |n_e|; sigma = +-1
+// evaluates sigma * n_e, the smooth continuation of one side of the null cone
+// (used inside an integration step, see trace_ray).
 template <class T>
-inline T plasma_freq2(const Star& s, const double m[3], const T x[3]) {
+inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma = 0) {
   switch (s.plasma) {
     case PLASMA_VACUUM: return T(0.0);
     case PLASMA_HOMOG: return T(s.plasma_a);
@@ -122,7 +132,8 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3]) {
   T Bhat[3];
   dipole_field(m, x, Bhat);
   T omega_dot_B = s.omega_eV * Bhat[2] * s.B0_eV2;     // Omega along z
-  T n_e = 2.0 * fabs(omega_dot_B) / s.e_hl;           // [eV^3]
+  T absOB = (sigma == 0) ? fabs(omega_dot_B) : double(sigma) * omega_dot_B;
+  T n_e = 2.0 * absOB / s.e_hl;                       // [eV^3]
   T wp2 = s.e_hl * s.e_hl * n_e / units::ME_EV;       // [eV^2]
   return wp2 / (s.ma_eV * s.ma_eV);
 }
@@ -131,7 +142,7 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3]) {
 // snapshot of the plasma, so dk_t/dlambda = 0).
 template <class T>
 inline T hamiltonian(const Star& s, const double m[3], double omega_inf, const T x[3],
-                     const T k[3]) {
+                     const T k[3], int sigma = 0) {
   T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   T n[3] = {x[0] / r, x[1] / r, x[2] / r};
   T A = 1.0 - s.rs_prop / r;
@@ -145,7 +156,7 @@ inline T hamiltonian(const Star& s, const double m[3], double omega_inf, const T
       kk = kk + gij * k[i] * k[j];
     }
   T g_kk = kk - omega2;                          // g^{mu nu} k_mu k_nu
-  T wp2 = plasma_freq2(s, m, x);
+  T wp2 = plasma_freq2(s, m, x, sigma);
   if (s.dispersion == DISP_ISO) return g_kk + wp2;
   // components of k in the static orthonormal frame: radial sqrt(A) k_r,
   // tangential unchanged
@@ -170,16 +181,16 @@ inline T photon_energy(int dispersion, T K2, T wp2, T cos2) {
 }
 
 // Hamilton's equations (Eq. Hamilton): dx/dlambda = dH/dk, dk/dlambda = -dH/dx,
-// derivatives by dual numbers.
+// derivatives by dual numbers (sigma: see plasma_freq2).
 inline void rhs(const Star& s, const double m[3], double omega_inf, const double y[6],
-                double dy[6]) {
+                double dy[6], int sigma = 0) {
   typedef Dual<6> D;
   D x[3], k[3];
   for (int i = 0; i < 3; ++i) {
     x[i] = D::var(y[i], i);
     k[i] = D::var(y[3 + i], 3 + i);
   }
-  D H = hamiltonian(s, m, omega_inf, x, k);
+  D H = hamiltonian(s, m, omega_inf, x, k, sigma);
   for (int i = 0; i < 3; ++i) {
     dy[i] = H.d[3 + i];
     dy[3 + i] = -H.d[i];

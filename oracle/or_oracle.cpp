@@ -233,16 +233,44 @@ struct RayRHS {
   const Star* s;
   const double* m;
   double omega_inf;
+  int sigma = 0;        // branch of the Goldreich-Julian density (0: |n_e|)
   long nev = 0;
   void operator()(const double y[6], double dy[6]) {
-    rhs(*s, m, omega_inf, y, dy);
+    rhs(*s, m, omega_inf, y, dy, sigma);
     ++nev;
   }
 };
 
+// The Goldreich-Julian density |2 Omega . B / e| has a kink on the null cone
+// Omega . B = 0 (Eq. GJDensity): omega_p^2 is continuous there but its
+// gradient, and so dk/dlambda, jumps.  An embedded error estimate cannot
+// resolve a jump inside a step; the step controller would shrink the step to
+// rtol-sized slivers at every crossing.  So each step integrates the smooth
+// continuation of the side it starts on (sigma = sign(Omega . B)); when an
+// accepted step ends on the other side, the crossing is located on the
+// continuous extension, the step is redone to end just past it, and sigma is
+// switched there.  This integrates the same piecewise-smooth equations.
+constexpr double SWITCH_MIN_FRACTION = 1e-6;   // a crossing this close to the start switches at once
+constexpr double SWITCH_OVERSHOOT = 1e-10;     // relative overshoot of the redone step
+
+static double locate_switch(const double m[3], const double y[6], const double ynew[6],
+                            const double K[7][6], double h, int sigma) {
+  // largest th in [0, 1] with sigma * (Omega . B)(x(th)) >= 0, by bisection
+  double lo = 0.0, hi = 1.0, yd[6];
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    dp5_dense(y, ynew, K, h, mid, yd);
+    if (sigma * gj_branch(m, yd) >= 0) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 static int trace_ray(const Star& s, const double m[3], double omega_inf, double y[6],
                      const TraceOpts& o, long* nacc_out, long* nrej_out, double* lam_out) {
   RayRHS f{&s, m, omega_inf};
+  const bool gj = (s.plasma == PLASMA_GJ);
+  if (gj) f.sigma = gj_branch(m, y);
   double f0[6];
   f(y, f0);
   double lam = 0.0;
@@ -250,6 +278,8 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
   double h = dp5_initial_step(f, y, f0, o.rtol, o.atol, hmax);
   long nacc = 0, nrej = 0;
   bool last_rej = false;
+  bool switching = false;      // the current attempt ends just past a crossing
+  double h_resume = 0.0;       // step size to resume with after the crossing
   int status = RAY_MAXSTEPS;
   double K[7][6], ynew[6], err[6];
   while (true) {
@@ -266,6 +296,20 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
       continue;
     }
     if (en <= 1.0) {
+      if (gj && !switching && f.sigma * gj_branch(m, ynew) < 0) {
+        // the accepted step crossed the null cone: end the step just past it
+        double th = locate_switch(m, y, ynew, K, h, f.sigma);
+        ++nrej;
+        if (th < SWITCH_MIN_FRACTION) {
+          f.sigma = -f.sigma;          // already at the cone: switch here
+          f(y, f0);
+        } else {
+          h_resume = h;
+          h = h * th * (1.0 + SWITCH_OVERSHOOT);
+          switching = true;
+        }
+        continue;
+      }
       ++nacc;
       double rnew = norm3(ynew);
       if (rnew >= o.r_out) {
@@ -288,7 +332,16 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
       lam += h;
       if (rnew <= o.r_capture) { status = RAY_CAPTURED; break; }
       if (clipped) { status = RAY_LAMBDA_END; break; }
-      h *= dp5_step_factor(en, true, last_rej);
+      if (gj && f.sigma * gj_branch(m, y) < 0) {
+        f.sigma = -f.sigma;            // past the cone: continue on the other side
+        f(y, f0);
+      }
+      if (switching) {
+        h = h_resume;
+        switching = false;
+      } else {
+        h *= dp5_step_factor(en, true, last_rej);
+      }
       last_rej = false;
     } else {
       ++nrej;
