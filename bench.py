@@ -212,129 +212,149 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     cfg, stars_kw = _workload()
     nsub, nper = cfg["nsub"], cfg["n_per_sub"]
+    N = nsub * nper
     nth, nph, nnu = NBINS
     stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
+    batch = rt.Batch(stars, [nper] * nsub)
     # weak scaling: every rank traces its own seeded copy of the workload
     seeds = [cfg["seed"] * 1000 + j + 100000 * rank for j in range(nsub)]
-    u_host = [torch.from_numpy(I.sample_uniforms(s, nper)).pin_memory() for s in seeds]
-    u = [x.to(dev) for x in u_host]
-    state = [torch.empty((8, nper), dtype=torch.float64, device=dev) for _ in range(nsub)]
-    w = [torch.empty(nper, dtype=torch.float64, device=dev) for _ in range(nsub)]
-    st = [torch.empty(nper, dtype=torch.uint8, device=dev) for _ in range(nsub)]
+    u_host = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([I.sample_uniforms(sd, nper) for sd in seeds], axis=1))).pin_memory()
+    u = u_host.to(dev)
+    st = torch.empty((8, N), dtype=torch.float64, device=dev)
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    s = torch.empty(N, dtype=torch.uint8, device=dev)
     hist = torch.empty((nsub, nth, nph, nnu), dtype=torch.float64, device=dev)
     oor = torch.empty(nsub, dtype=torch.float64, device=dev)
-    ctr = torch.zeros((nsub, 8), dtype=torch.int64, device=dev)
-    hist_host = torch.empty_like(hist, device="cpu").pin_memory()
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    hist_host = torch.empty(hist.shape, dtype=torch.float64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opts = rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
-                        precision=rt.PREC_FP64)
     stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(nsub)]
-
-    def step(record=False, uin=None):
-        ctr.zero_()
-        for j in range(nsub):
-            src = u[j] if uin is None else uin[j]
-            rt.rt_sample_conversion_surface(stars[j], nper, src, state[j], w[j], st[j],
-                                            stream=stream)
-            if record:
-                ev[j][0].record(stream)
-            rt.rt_trace_forward(stars[j], nper, state[j], st[j], None, None, ctr[j], opts,
-                                stream=stream)
-            if record:
-                ev[j][1].record(stream)
-            rt.rt_bin_spectrum(stars[j], nper, state[j], w[j], st[j], nth, nph, nnu,
-                               cfg["nu_lo"], cfg["nu_hi"], hist[j], None, None, oor[j:j + 1],
-                               stream=stream)
-
-    launches_per_step = nsub * 5   # sample, trace, 3 binning kernels
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    t_steps, t_trace, steps_acc, steps_rej, rays = [], [], 0, 0, 0
+    opts = {
+        "fp64": rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
+                             precision=rt.PREC_FP64, max_steps=cfg["max_steps"]),
+        "mixed": rt.make_opts(rtol=cfg["rtol_mixed"], r_out_over_R=cfg["r_out_over_R"],
+                              precision=rt.PREC_MIXED, max_steps=cfg["max_steps"]),
+    }
+    ev_t = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for _ in range(args.steps):
-        flush.fill_(1)                      # L2 flush, outside the timed events
-        e0.record(stream)
-        step(record=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_steps.append(e0.elapsed_time(e1) / 1e3)
-        t_trace.append(sum(a.elapsed_time(b) for a, b in ev) / 1e3 / nsub)
-        c = ctr.sum(0).cpu().numpy()
-        steps_acc += int(c[0])
-        steps_rej += int(c[1])
-        rays += int(c[2])
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    T = sum(t_steps)
-    if ws > 1:
-        tt = torch.tensor([T], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        T = float(tt[0])
-        cs = torch.tensor([steps_acc, rays], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(cs)
-        steps_acc_all, rays_all = float(cs[0]), float(cs[1])
-    else:
-        steps_acc_all, rays_all = steps_acc, rays
-    value = steps_acc_all / T
-    # roofline of the dominant kernel (the trace): algorithmic flops per launch
-    fl = _flops_per_attempt(rt)
-    attempts = (steps_acc + steps_rej) / (args.steps * nsub)
-    rays_per_launch = rays / (args.steps * nsub)
-    flops_launch = attempts * fl[1] + rays_per_launch * fl[2]
-    achieved = flops_launch / statistics.mean(t_trace)
+    launches = {"fp64": nsub + 1 + 3 * nsub, "mixed": nsub + 2 + 3 * nsub}
 
+    def step(prec, uin=None):
+        ctr.zero_()
+        rt.rt_sample_batch(batch, u if uin is None else uin, st, w, s, stream=stream)
+        ev_t[0].record(stream)
+        rt.rt_trace_batch(batch, st, s, None, None, ctr, opts[prec], stream=stream)
+        ev_t[1].record(stream)
+        rt.rt_bin_batch(batch, st, w, s, nth, nph, nnu, cfg["nu_lo"], cfg["nu_hi"], hist, oor,
+                        stream=stream)
+
+    res = {}
+    fl = _flops_per_attempt(rt)
+    clocks = Clocks(local)
+    clocks.start()
+    for prec in ("fp64", "mixed"):
+        for _ in range(args.warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_steps, t_trace, c_sum = [], [], np.zeros(8)
+        for _ in range(args.steps):
+            flush.fill_(1)                  # L2 flush, outside the timed events
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_steps.append(e0.elapsed_time(e1) / 1e3)
+            t_trace.append(ev_t[0].elapsed_time(ev_t[1]) / 1e3)
+            c_sum += ctr.cpu().numpy()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        T = sum(t_steps)
+        acc_all, rays_all = c_sum[0], c_sum[2]
+        if ws > 1:
+            tt = torch.tensor([T], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            T = float(tt[0])
+            cs = torch.tensor([c_sum[0], c_sum[2]], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(cs)
+            acc_all, rays_all = float(cs[0]), float(cs[1])
+        attempts = (c_sum[0] + c_sum[1]) / args.steps
+        rays_launch = c_sum[2] / args.steps
+        promoted_attempts = c_sum[5] / args.steps
+        t_tr = statistics.mean(t_trace)
+        if prec == "fp64":
+            flops = attempts * fl[1] + rays_launch * fl[2]
+            roof = {"kernel": "trace_fp64_kernel", "bound": "alu", "achieved": flops / t_tr / 1e12,
+                    "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
+                    "frac": flops / t_tr / PEAK_FP64, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+        else:
+            flops = (attempts - promoted_attempts) * fl[1] + rays_launch * fl[2]
+            roof = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)",
+                    "bound": "alu", "achieved": flops / t_tr / 1e12,
+                    "peak": PEAK_FP32 / 1e12, "unit": "TFLOP/s",
+                    "frac": flops / t_tr / PEAK_FP32, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 256 FP32 flop/clk x 2070 MHz",
+                    "promoted_rays_per_step": c_sum[4] / args.steps,
+                    "promoted_fp64_attempts_per_step": promoted_attempts}
+        roof.update({"flops_per_attempt": fl[1], "attempts_per_launch": attempts,
+                     "trace_ms_per_launch": 1e3 * t_tr})
+        res[prec] = {"value": acc_all / T, "rays_per_s": rays_all / T,
+                     "ms_per_step": 1e3 * T / args.steps, "roofline": roof,
+                     "accepted_steps_per_step": c_sum[0] / args.steps,
+                     "rejected_steps_per_step": c_sum[1] / args.steps,
+                     "rtol": opts[prec].rtol,
+                     "hist": hist.cpu().numpy().copy(),
+                     "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}
+    clk = clocks.stop()
+    h64, hmx = res["fp64"].pop("hist"), res["mixed"].pop("hist")
+    flux_l1 = float(np.abs(hmx - h64).sum() / max(np.abs(h64).sum(), 1e-300))
+    res["mixed"]["flux_l1_vs_fp64"] = flux_l1
+    head = "mixed" if flux_l1 <= 1e-6 else "fp64"
     # end to end through the C ABI with host buffers: H2D uniforms, D2H histograms
     t_e2e = []
+    acc_e2e = 0.0
     for _ in range(max(1, args.steps)):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for j in range(nsub):
-            u[j].copy_(u_host[j], non_blocking=True)
-        step()
+        u.copy_(u_host, non_blocking=True)
+        step(head)
         hist_host.copy_(hist, non_blocking=True)
         torch.cuda.synchronize()
         t_e2e.append(time.perf_counter() - t0)
-    e2e_val = steps_acc / args.steps * len(t_e2e) / sum(t_e2e)
-    h2d = sum(x.numel() * 8 for x in u_host)
-    d2h = hist.numel() * 8
+        acc_e2e += float(ctr[0])
+    e2e_val = acc_e2e / sum(t_e2e)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(stars_kw, cfg, args.cpu_sample)
     if rank != 0:
         return
+    H = res[head]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["name"], "rays_per_step": nsub * nper,
-                   "sub_batches": nsub, "rtol": cfg["rtol"],
-                   "r_out_over_R": cfg["r_out_over_R"], "bins": list(NBINS),
-                   "precision": "fp64", "l2": "flushed before each step (256 MiB write)"},
-        "rays_per_s": rays_all / T,
-        "accepted_steps_per_step": steps_acc / args.steps,
-        "rejected_steps_per_step": steps_rej / args.steps,
-        "roofline": {"kernel": "trace_fp64_kernel", "bound": "alu", "achieved": achieved / 1e12,
-                     "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP64, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
-                     "flops_per_attempt": fl[1], "attempts_per_launch": attempts,
-                     "trace_ms_per_launch": 1e3 * statistics.mean(t_trace)},
+        "metric": METRIC, "value": H["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": H["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "rays_per_step": N, "sub_batches": nsub,
+                   "rtol": H["rtol"], "r_out_over_R": cfg["r_out_over_R"],
+                   "max_steps": cfg["max_steps"], "bins": list(NBINS), "precision": head,
+                   "launch": "one persistent trace launch over all 16 sub-batches",
+                   "l2": "flushed before each step (256 MiB write)"},
+        "rays_per_s": H["rays_per_s"],
+        "roofline": H["roofline"],
+        "fp64": res["fp64"], "mixed": res["mixed"],
+        "mixed_vs_fp64_rays_per_s": res["mixed"]["rays_per_s"] / res["fp64"]["rays_per_s"],
+        "adjoint_forward_ratio": None,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * args.steps,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
+                "d2h_bytes_per_step": hist.numel() * 8},
+        "gpu_launches": launches[head] * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line))

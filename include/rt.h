@@ -215,6 +215,39 @@ rt_status rt_bin_spectrum(const rt_star* star, int64_t n, const double* d_state,
                           double* d_sky, double* d_spec, double* d_out_of_range, void* stream);
 
 /*
+ * Batches: many stars (different B0, P, misalignment, m_a, ...) traced in ONE
+ * persistent launch whose global queue spans all of them, so the long rays of
+ * one star overlap with the bulk of the others.  counts[s] rays of star s
+ * occupy rays [off_s, off_s + counts[s]) of arrays of total length
+ * N = sum(counts), in star order (SoA row stride N).
+ *
+ * rt_init_batch - host; allocates a device star table, the offsets and a
+ *   queue counter.  The star handles must outlive the batch.
+ * rt_sample_batch - rt_sample_conversion_surface for every star on its range
+ *   (each star's weights normalised by its own count); u is 6 x N, state
+ *   8 x N.  RT_EEMPTY_SURFACE only when every star's surface is empty.
+ * rt_trace_batch - rt_trace_forward over all N rays in one launch (FP64) or
+ *   one FP32 launch plus one FP64 pass for promoted rays (RT_PREC_MIXED).
+ * rt_bin_batch - per-star histograms: d_hist is nstars x nth x nph x nnu,
+ *   d_out_of_range nstars; per-star fixed-point scales (binning scratch owned
+ *   by the batch, allocated on first use).
+ * Calls on one batch must be serialised on one stream.
+ */
+typedef struct rt_batch rt_batch;
+rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64_t* counts,
+                        rt_batch** out);
+void rt_destroy_batch(rt_batch* batch);
+rt_status rt_sample_batch(rt_batch* batch, const double* d_uniforms, double* d_state,
+                          double* d_weight, uint8_t* d_status, void* stream);
+rt_status rt_trace_batch(rt_batch* batch, double* d_state, uint8_t* d_status, int32_t* d_nacc,
+                         int32_t* d_nrej, int64_t* d_counters, const rt_trace_opts* opts,
+                         void* stream);
+rt_status rt_bin_batch(rt_batch* batch, const double* d_state, const double* d_weight,
+                       const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
+                       double nu_lo, double nu_hi, double* d_hist, double* d_out_of_range,
+                       void* stream);
+
+/*
  * rt_count_status - histogram of per-ray status codes (synchronises the
  * stream).  counts: host array of RT_RAY_NSTATUS int64.  Returns RT_EPARTIAL
  * if any ray ended in MAXSTEPS, NAN or STIFF, else RT_OK.

@@ -219,6 +219,7 @@ rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double
   rtk::SampleParams p;
   p.s = s->h;
   p.n = n;
+  p.ld = n;
   p.u = d_u;
   p.state = d_state;
   p.weight = d_weight;
@@ -335,6 +336,7 @@ rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
   rtk::BinParams p;
   p.star = s->d;
   p.n = n;
+  p.ld = n;
   p.state = d_state;
   p.weight = d_weight;
   p.status = d_status;
@@ -350,6 +352,211 @@ rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
   p.oor = d_oor;
   cudaError_t e = rtk::launch_bin(p, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "bin kernels");
+  return RT_OK;
+}
+
+// --- batches of stars (one persistent launch over all of them) ---------------
+
+}  // extern "C"
+
+struct rt_batch {
+  std::vector<const rt_star*> stars;
+  std::vector<int64_t> off;           // nstars + 1 host offsets
+  int64_t N = 0;
+  rtk::StarDev* d_stars = nullptr;    // device table
+  int64_t* d_off = nullptr;           // device offsets
+  unsigned long long* d_queue = nullptr;
+  long long* d_bins = nullptr;        // nstars x per-star binning accumulators
+  size_t bins_per_star = 0;
+  int device = 0;
+  bool all_empty = true;
+};
+
+extern "C" {
+
+rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64_t* counts,
+                        rt_batch** out) {
+  if (!out) return fail(RT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!stars || !counts || nstars < 1) return fail(RT_EINVAL, "need nstars >= 1 stars and counts");
+  rt_batch* b = new (std::nothrow) rt_batch;
+  if (!b) return fail(RT_ENOMEM, "host allocation failed");
+  b->off.assign((size_t)nstars + 1, 0);
+  std::vector<rtk::StarDev> table((size_t)nstars);
+  for (int s = 0; s < nstars; ++s) {
+    if (!stars[s] || counts[s] < 0) {
+      delete b;
+      return fail(RT_EINVAL, "star %d is NULL or has a negative count", s);
+    }
+    b->stars.push_back(stars[s]);
+    table[s] = stars[s]->h;
+    b->off[s + 1] = b->off[s] + counts[s];
+    b->all_empty = b->all_empty && stars[s]->empty;
+  }
+  b->N = b->off[nstars];
+  cudaGetDevice(&b->device);
+  const size_t tbl = sizeof(rtk::StarDev) * nstars, offb = sizeof(int64_t) * (nstars + 1);
+  void* blk = nullptr;
+  cudaError_t e = cudaMalloc(&blk, 256 + tbl + 256 + offb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return fail(RT_ENOMEM, "cudaMalloc failed for the batch tables");
+  }
+  b->d_queue = (unsigned long long*)blk;
+  b->d_stars = (rtk::StarDev*)((char*)blk + 256);
+  b->d_off = (int64_t*)((char*)blk + 256 + ((tbl + 255) / 256) * 256);
+  e = cudaMemcpy(b->d_stars, table.data(), tbl, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_off, b->off.data(), offb, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    delete b;
+    return cuda_fail(e, "cudaMemcpy");
+  }
+  *out = b;
+  return RT_OK;
+}
+
+void rt_destroy_batch(rt_batch* b) {
+  if (!b) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != b->device) cudaSetDevice(b->device);
+  if (b->d_bins) cudaFree(b->d_bins);
+  if (b->d_queue) cudaFree(b->d_queue);
+  if (cur != b->device) cudaSetDevice(cur);
+  delete b;
+}
+
+rt_status rt_sample_batch(rt_batch* b, const double* d_u, double* d_state, double* d_weight,
+                          uint8_t* d_status, void* stream) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  if (b->N == 0) return RT_OK;
+  rt_status st;
+  if ((st = check_dev_ptr(d_u, "d_uniforms")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_weight, "d_weight")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  for (size_t s = 0; s < b->stars.size(); ++s) {
+    const int64_t o = b->off[s], cnt = b->off[s + 1] - o;
+    if (cnt == 0) continue;
+    rtk::SampleParams p;
+    p.s = b->stars[s]->h;
+    p.n = cnt;
+    p.ld = b->N;
+    p.u = d_u + o;
+    p.state = d_state + o;
+    p.weight = d_weight + o;
+    p.status = d_status + o;
+    cudaError_t e = rtk::launch_sample(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sample kernel");
+  }
+  return b->all_empty ? RT_EEMPTY_SURFACE : RT_OK;
+}
+
+rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_t* d_nacc,
+                         int32_t* d_nrej, int64_t* d_counters, const rt_trace_opts* o,
+                         void* stream) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (b->N == 0) return RT_OK;
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
+  if (d_nrej && (st = check_dev_ptr(d_nrej, "d_nrej")) != RT_OK) return st;
+  if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
+  if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
+    return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
+  rtk::TraceParams p;
+  p.stars = b->d_stars;
+  p.nstars = (int)b->stars.size();
+  p.offsets = b->d_off;
+  p.n = b->N;
+  p.state = d_state;
+  p.status = d_status;
+  p.nacc = d_nacc;
+  p.nrej = d_nrej;
+  p.counters = d_counters;
+  p.queue = b->d_queue;
+  p.rtol = o->rtol;
+  p.atol = o->atol;
+  p.r_out = o->r_out_over_R;
+  p.lambda_max = o->lambda_max;
+  p.r_capture = o->r_capture_over_R;
+  p.max_steps = o->max_steps;
+  p.claim_status = rtk::RAY_READY;
+  cudaError_t e;
+  if (o->precision == RT_PREC_MIXED) {
+    e = rtk::launch_trace_mixed(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
+    p.claim_status = rtk::RAY_PROMOTED;
+    e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
+    return RT_OK;
+  }
+  e = rtk::launch_trace_fp64(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace kernel");
+  return RT_OK;
+}
+
+rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weight,
+                       const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
+                       double nu_lo, double nu_hi, double* d_hist, double* d_oor, void* stream) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
+  if ((int64_t)nth * nph * nnu > (int64_t)1 << 28) return fail(RT_EINVAL, "too many bins");
+  if (!is_finite_val(nu_lo) || !is_finite_val(nu_hi) || !(nu_hi > nu_lo))
+    return fail(RT_EINVAL, "need finite nu_lo < nu_hi");
+  rt_status st;
+  if (b->N > 0) {
+    if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_weight, "d_weight")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  }
+  if ((st = check_dev_ptr(d_hist, "d_hist")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_oor, "d_out_of_range")) != RT_OK) return st;
+  const size_t per = rtk::bin_scratch_entries(nth, nph, nnu);
+  const size_t nst = b->stars.size();
+  if (per > b->bins_per_star) {
+    if (b->d_bins) {
+      cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+      cudaFree(b->d_bins);
+      b->d_bins = nullptr;
+      b->bins_per_star = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, per * nst * sizeof(long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RT_ENOMEM, "cannot allocate the batch binning scratch");
+    }
+    b->d_bins = (long long*)p;
+    b->bins_per_star = per;
+  }
+  const size_t nbins = (size_t)nth * nph * nnu;
+  for (size_t s = 0; s < nst; ++s) {
+    const int64_t o = b->off[s], cnt = b->off[s + 1] - o;
+    rtk::BinParams p;
+    p.star = b->d_stars + s;
+    p.n = cnt;
+    p.ld = b->N;
+    p.state = d_state + o;
+    p.weight = d_weight + o;
+    p.status = d_status + o;
+    p.nth = nth;
+    p.nph = nph;
+    p.nnu = nnu;
+    p.nu_lo = nu_lo;
+    p.nu_hi = nu_hi;
+    p.acc = b->d_bins + s * b->bins_per_star;
+    p.hist = d_hist + s * nbins;
+    p.sky = nullptr;
+    p.spec = nullptr;
+    p.oor = d_oor + s;
+    cudaError_t e = rtk::launch_bin(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bin kernels");
+  }
   return RT_OK;
 }
 

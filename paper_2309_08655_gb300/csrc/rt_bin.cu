@@ -11,7 +11,12 @@
 //   3. finalize_kernel q / 2^e to float64.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
+#include <cmath>
+#include <mutex>
+
+#include "rt.h"
 #include "rt_device.cuh"
 #include "rt_internal.h"
 
@@ -65,12 +70,12 @@ __global__ void accum_kernel(BinParams p) {
   const double dth = PI / p.nth, dph = 2.0 * PI / p.nph;
   const double dnu = (p.nu_hi - p.nu_lo) / p.nnu;
   const double y_unit = 0.5 * s.v0 * s.v0;
-  const int64_t n = p.n;
+  const int64_t n = p.n, ld = p.ld;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (p.status[i] != RAY_ESCAPED) continue;
     const long long q = llrint(p.weight[i] * scale);
-    const double y = p.state[6 * n + i] / y_unit;
+    const double y = p.state[6 * ld + i] / y_unit;
     if (!(y >= p.nu_lo && y < p.nu_hi)) {
       atomicAdd((unsigned long long*)&p.acc[1], (unsigned long long)q);
       continue;
@@ -79,8 +84,9 @@ __global__ void accum_kernel(BinParams p) {
     if (inu >= p.nnu) inu = p.nnu - 1;
     // direction of the orthonormal-frame momentum at the end point
     const double iR = 1.0 / s.R_km;
-    const double x0 = p.state[i] * iR, x1 = p.state[n + i] * iR, x2 = p.state[2 * n + i] * iR;
-    const double k0 = p.state[3 * n + i], k1 = p.state[4 * n + i], k2 = p.state[5 * n + i];
+    const double x0 = p.state[i] * iR, x1 = p.state[ld + i] * iR;
+    const double x2 = p.state[2 * ld + i] * iR;
+    const double k0 = p.state[3 * ld + i], k1 = p.state[4 * ld + i], k2 = p.state[5 * ld + i];
     const double ir = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
     const double n0 = x0 * ir, n1 = x1 * ir, n2 = x2 * ir;
     const double A = 1.0 - s.rs_prop * ir;

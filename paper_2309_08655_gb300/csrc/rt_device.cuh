@@ -85,8 +85,18 @@ struct RayConst {
   T pa;          // test-medium parameter
   T W2, iW2;     // omega_inf^2 and its inverse
   T m0, m1, m2;  // magnetic axis
+  T sig;         // side of the Goldreich-Julian null cone being integrated (+-1)
   int disp, plasma;
 };
+
+// Sign of Omega . B (that of 3 z (m.x) - m_z |x|^2): the Goldreich-Julian
+// density |2 Omega . B / e| has a kink where it vanishes.
+template <class T>
+RT_HD __forceinline__ T gj_side(const T m0, const T m1, const T m2, const T x0, const T x1,
+                                const T x2) {
+  const T g = T(3) * x2 * (m0 * x0 + m1 * x1 + m2 * x2) - m2 * (x0 * x0 + x1 * x1 + x2 * x2);
+  return g < T(0) ? T(-1) : T(1);
+}
 
 // dx/dl = dH/dk, dk/dl = -dH/dx (Eq. Hamilton), analytic.  (Host-callable
 // only for the flop-counting scalar of rt_flops.cu.)
@@ -118,8 +128,10 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
   const T mu = c.m0 * n0 + c.m1 * n1 + c.m2 * n2;   // m.n
   T P = T(0), dP0 = T(0), dP1 = T(0), dP2 = T(0);
   if (c.plasma == PLASMA_GJ) {
+    // within a step: the smooth continuation sig * F of the side the step
+    // started on (the integrator switches sig where a step crosses F = 0)
     const T F = T(3) * n2 * mu - c.m2;
-    const T sF = (F < T(0)) ? T(-1) : T(1);
+    const T sF = c.sig;
     const T ir3 = ir2 * ir;
     P = c.cp * ir3 * (F * sF);
     // dF = 3/r (mu z + n_z m - 2 mu n_z n)

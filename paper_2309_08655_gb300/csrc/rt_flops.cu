@@ -45,7 +45,7 @@ extern "C" rt_status rt_flops_per_step(int32_t dispersion, int32_t plasma, doubl
   if (dispersion < 0 || dispersion > 1 || plasma < 0 || plasma > 3) return RT_EINVAL;
   rtk::RayConst<Cnt> c;
   c.rs = 0.4; c.cp = 4000.0; c.pa = 0.1; c.W2 = 1.0; c.iW2 = 1.0;
-  c.m0 = 0.3; c.m1 = 0.1; c.m2 = 0.9; c.disp = dispersion; c.plasma = plasma;
+  c.m0 = 0.3; c.m1 = 0.1; c.m2 = 0.9; c.sig = 1.0; c.disp = dispersion; c.plasma = plasma;
   g_t = Tally();
   Cnt d[6];
   rtk::ham_rhs<Cnt>(c, Cnt(20.0), Cnt(3.0), Cnt(-5.0), Cnt(0.3), Cnt(-0.4), Cnt(0.8), d[0], d[1],

@@ -30,7 +30,8 @@ enum { CTR_ACC = 0, CTR_REJ, CTR_RAYS, CTR_ESC, CTR_PROMOTED, CTR_PROMOTED_STEPS
 
 struct SampleParams {
   StarDev s;
-  int64_t n;
+  int64_t n;                // samples (the weights are normalised by n)
+  int64_t ld;               // SoA row stride of u and state (>= n)
   const double* u;
   double* state;
   double* weight;
@@ -40,6 +41,7 @@ struct SampleParams {
 struct BinParams {
   const StarDev* star;      // device descriptor
   int64_t n;
+  int64_t ld;               // SoA row stride of state (>= n)
   const double* state;
   const double* weight;
   const uint8_t* status;

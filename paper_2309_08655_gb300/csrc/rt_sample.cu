@@ -103,11 +103,11 @@ __device__ __forceinline__ double line_G(const Line& L, double r, double* dG) {
 
 __global__ void sample_kernel(SampleParams p) {
   const StarDev& s = p.s;
-  const int64_t n = p.n;
+  const int64_t n = p.n, ld = p.ld;   // count and SoA row stride
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double u0 = p.u[i], u1 = p.u[n + i], u2 = p.u[2 * n + i];
-    const double u3 = p.u[3 * n + i], u4 = p.u[4 * n + i], u5 = p.u[5 * n + i];
+    const double u0 = p.u[i], u1 = p.u[ld + i], u2 = p.u[2 * ld + i];
+    const double u3 = p.u[3 * ld + i], u4 = p.u[4 * ld + i], u5 = p.u[5 * ld + i];
     // direction of the conversion point and of the momentum
     const double ct = 1.0 - 2.0 * u0;
     const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
@@ -144,8 +144,8 @@ __global__ void sample_kernel(SampleParams p) {
     L.pa = s.plasma_a;
     L.nz = n2;
     // outputs for a sample without a resonance
-    p.state[6 * n + i] = delta;
-    p.state[7 * n + i] = psi;
+    p.state[6 * ld + i] = delta;
+    p.state[7 * ld + i] = psi;
     bool ok = line_G(L, 1.0, nullptr) > 0.0;
     double lo = 1.0, hi = 2.0;
     if (ok) {
@@ -158,7 +158,7 @@ __global__ void sample_kernel(SampleParams p) {
     }
     if (!ok) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) p.state[c * n + i] = 0.0;
+      for (int c = 0; c < 6; ++c) p.state[c * ld + i] = 0.0;
       p.weight[i] = 0.0;
       p.status[i] = RAY_NO_ROOT;
       continue;
@@ -206,11 +206,11 @@ __global__ void sample_kernel(SampleParams p) {
     const double nko = kloc * (n0 * q0 + n1 * q1 + n2 * q2);
     const double cr = (1.0 / sqrt(A) - 1.0) * nko;
     p.state[i] = r * n0 * s.R_km;
-    p.state[n + i] = r * n1 * s.R_km;
-    p.state[2 * n + i] = r * n2 * s.R_km;
-    p.state[3 * n + i] = (kloc * q0 + cr * n0) * s.ma_eV;
-    p.state[4 * n + i] = (kloc * q1 + cr * n1) * s.ma_eV;
-    p.state[5 * n + i] = (kloc * q2 + cr * n2) * s.ma_eV;
+    p.state[ld + i] = r * n1 * s.R_km;
+    p.state[2 * ld + i] = r * n2 * s.R_km;
+    p.state[3 * ld + i] = (kloc * q0 + cr * n0) * s.ma_eV;
+    p.state[4 * ld + i] = (kloc * q1 + cr * n1) * s.ma_eV;
+    p.state[5 * ld + i] = (kloc * q2 + cr * n2) * s.ma_eV;
     p.status[i] = RAY_READY;
   }
 }

@@ -61,8 +61,19 @@ struct Lane {
   double h, lam;
   int na, nr;
   bool last_rej;
+  bool switching;      // the current attempt ends just past a null-cone crossing
+  double h_resume;     // step size to resume with after that crossing
   double R_km, ma_eV;
 };
+
+// The Goldreich-Julian density |2 Omega . B / e| has a kink on the null cone
+// Omega . B = 0 (Eq. GJDensity): dk/dlambda jumps there, which an embedded
+// error estimate cannot resolve inside a step.  Each step integrates the
+// smooth continuation of the side it starts on (c.sig); when an accepted step
+// ends on the other side, the crossing is located on the continuous extension,
+// the step is redone to end just past it, and the side is switched there.
+constexpr double SWITCH_MIN_FRACTION = 1e-6;
+constexpr double SWITCH_OVERSHOOT = 1e-10;
 
 __device__ __forceinline__ int find_star(const TraceParams& p, int64_t i) {
   if (p.nstars <= 1) return 0;
@@ -100,6 +111,9 @@ __device__ void load_lane(const TraceParams& p, int64_t i, Lane& L) {
   L.c.m2 = s.cos_tm;
   L.c.disp = s.dispersion;
   L.c.plasma = s.plasma;
+  L.c.sig = gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]);
+  L.switching = false;
+  L.h_resume = 0.0;
   rhs64(L.c, L.y, L.f0);
   const double hmax = (p.lambda_max > 0.0) ? p.lambda_max : 1e30;
   L.h = initial_step(L.c, L.y, L.f0, p.rtol, p.atol, hmax);
@@ -178,6 +192,45 @@ __device__ int advance(const TraceParams& p, Lane& L) {
     L.last_rej = true;
     return (L.h < 1e-12) ? RAY_NAN : -1;
   }
+  const bool gj = (L.c.plasma == PLASMA_GJ);
+  if (en <= 1.0 && gj && !L.switching &&
+      L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, yn[0], yn[1], yn[2]) < 0.0) {
+    // the step crossed the null cone: largest th with the start side on the
+    // continuous extension (bisection), then redo the step to end just past it
+    double r3[3], r4[3], r5[3], r2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r2[i] = yn[i] - y[i];
+      r3[i] = h * k1[i] - r2[i];
+      r4[i] = r2[i] - h * k7[i] - r3[i];
+      r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
+                   DP::d6 * k6[i] + DP::d7 * k7[i]);
+    }
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double xd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        xd[i] = y[i] + mid * (r2[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+      if (L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, xd[0], xd[1], xd[2]) >= 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    ++L.nr;
+    if (lo < SWITCH_MIN_FRACTION) {
+      L.c.sig = -L.c.sig;             // already at the cone: switch here
+      rhs64(L.c, L.y, L.f0);
+      L.h = h;
+    } else {
+      L.h_resume = h;
+      L.h = h * lo * (1.0 + SWITCH_OVERSHOOT);
+      L.switching = true;
+    }
+    return -1;
+  }
   if (en <= 1.0) {
     ++L.na;
     const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
@@ -221,7 +274,16 @@ __device__ int advance(const TraceParams& p, Lane& L) {
     L.lam += h;
     if (rnew <= p.r_capture) return RAY_CAPTURED;
     if (clipped) return RAY_LAMBDA_END;
-    L.h = h * step_factor(en, true, L.last_rej);
+    if (gj && L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]) < 0.0) {
+      L.c.sig = -L.c.sig;             // past the cone: continue on the other side
+      rhs64(L.c, L.y, L.f0);
+    }
+    if (L.switching) {
+      L.h = L.h_resume;
+      L.switching = false;
+    } else {
+      L.h = h * step_factor(en, true, L.last_rej);
+    }
     L.last_rej = false;
     return -1;
   }

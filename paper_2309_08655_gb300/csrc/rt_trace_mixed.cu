@@ -68,8 +68,19 @@ struct LaneM {
   float h;
   int na, nr;
   bool last_rej;
+  bool switching;      // the current attempt ends just past a null-cone crossing
+  float h_resume;
   double R_km, ma_eV;
 };
+
+// Side of the Goldreich-Julian null cone at an FP64 position (see rt_trace.cu
+// for the switching scheme, which this kernel follows in FP32).
+__device__ __forceinline__ float side_m(const RayConst<float>& c, double x0, double x1,
+                                        double x2) {
+  return (float)gj_side<double>((double)c.m0, (double)c.m1, (double)c.m2, x0, x1, x2);
+}
+constexpr float SWITCH_MIN_FRACTION_M = 1e-6f;
+constexpr float SWITCH_OVERSHOOT_M = 1e-6f;
 
 __device__ __forceinline__ int find_star_m(const TraceParams& p, int64_t i) {
   if (p.nstars <= 1) return 0;
@@ -105,6 +116,9 @@ __device__ void load_lane_m(const TraceParams& p, int64_t i, LaneM& L) {
   L.c.m2 = (float)s.cos_tm;
   L.c.disp = s.dispersion;
   L.c.plasma = s.plasma;
+  L.c.sig = side_m(L.c, L.y[0], L.y[1], L.y[2]);
+  L.switching = false;
+  L.h_resume = 0.0f;
   float yf[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) yf[c] = (float)L.y[c];
@@ -194,6 +208,41 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   // is kept, but may not grow the step.
   const bool noisy = noise > NOISE_LIMIT;
   if (noisy && !(en <= 1.0f)) return RAY_PROMOTED;
+  const bool gj = (L.c.plasma == PLASMA_GJ);
+  if (en <= 1.0f && gj && !L.switching && L.c.sig * side_m(L.c, yn[0], yn[1], yn[2]) < 0.0f) {
+    // the step crossed the null cone: locate on the continuous extension and
+    // redo the step to end just past the crossing
+    float r3[3], r4[3], r5[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r3[i] = h * k1[i] - d5[i];
+      r4[i] = d5[i] - h * k7[i] - r3[i];
+      r5[i] = h * ((float)DP::d1 * k1[i] + (float)DP::d3 * k3[i] + (float)DP::d4 * k4[i] +
+                   (float)DP::d5 * k5[i] + (float)DP::d6 * k6[i] + (float)DP::d7 * k7[i]);
+    }
+    float lo = 0.0f, hi = 1.0f;
+    for (int it = 0; it < 40; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double xd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        xd[i] = L.y[i] + (double)(mid * (d5[i] + (1.0f - mid) * (r3[i] + mid * (r4[i] +
+                                                         (1.0f - mid) * r5[i]))));
+      if (L.c.sig * side_m(L.c, xd[0], xd[1], xd[2]) >= 0.0f) lo = mid; else hi = mid;
+    }
+    ++L.nr;
+    if (lo < SWITCH_MIN_FRACTION_M) {
+      L.c.sig = -L.c.sig;
+      rhs32(L.c, yf, L.f0);
+      L.h = h;
+    } else {
+      L.h_resume = h;
+      L.h = h * lo * (1.0f + SWITCH_OVERSHOOT_M);
+      L.switching = true;
+    }
+    return -1;
+  }
   if (en <= 1.0f) {
     ++L.na;
     const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
@@ -233,7 +282,19 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
       L.f0[i] = k7[i];
     }
     if (rnew <= p.r_capture) return RAY_CAPTURED;
-    L.h = h * step_factor32(en, true, L.last_rej || noisy);
+    if (gj && L.c.sig * side_m(L.c, L.y[0], L.y[1], L.y[2]) < 0.0f) {
+      L.c.sig = -L.c.sig;             // past the cone: continue on the other side
+      float yc[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) yc[i] = (float)L.y[i];
+      rhs32(L.c, yc, L.f0);
+    }
+    if (L.switching) {
+      L.h = L.h_resume;
+      L.switching = false;
+    } else {
+      L.h = h * step_factor32(en, true, L.last_rej || noisy);
+    }
     L.last_rej = false;
     return -1;
   }

@@ -81,5 +81,5 @@ def stars_config1(seed: int = 1, nsub: int = 16) -> list[dict]:
 
 
 CONFIG1 = dict(name="forward_misaligned_16x65536", nsub=16, n_per_sub=1 << 16, seed=1,
-               rtol=1e-10, rtol_mixed=1e-10, r_out_over_R=1000.0, nth=64, nph=32, nnu=128,
-               nu_lo=0.0, nu_hi=9.0)
+               rtol=1e-10, rtol_mixed=1e-8, r_out_over_R=1000.0, max_steps=100000, nth=64,
+               nph=32, nnu=128, nu_lo=0.0, nu_hi=9.0)

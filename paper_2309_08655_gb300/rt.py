@@ -73,6 +73,20 @@ def lib():
                                       ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
         L.rt_count_status.restype = ctypes.c_int
         L.rt_count_status.argtypes = [ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+        L.rt_init_batch.restype = ctypes.c_int
+        L.rt_init_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp)]
+        L.rt_destroy_batch.restype = None
+        L.rt_destroy_batch.argtypes = [_vp]
+        L.rt_sample_batch.restype = ctypes.c_int
+        L.rt_sample_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.rt_trace_batch.restype = ctypes.c_int
+        L.rt_trace_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(rt_trace_opts), _vp]
+        L.rt_bin_batch.restype = ctypes.c_int
+        L.rt_bin_batch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp,
+                                   _vp]
         L.rt_last_error.restype = ctypes.c_char_p
         L.rt_last_error.argtypes = []
         L.rt_version.restype = ctypes.c_int32
@@ -204,6 +218,62 @@ def rt_count_status(n, status, stream=None) -> tuple[int, list[int]]:
     return st, list(counts)
 
 
+class Batch:
+    """Owning wrapper of an ``rt_batch``: stars traced in one persistent launch."""
+
+    def __init__(self, stars: list[Star], counts: list[int]):
+        n = len(stars)
+        arr = (_vp * n)(*[s.handle for s in stars])
+        cnt = (ctypes.c_int64 * n)(*[int(c) for c in counts])
+        h = _vp()
+        _check(lib().rt_init_batch(arr, n, cnt, ctypes.byref(h)))
+        self.handle = h
+        self.stars = list(stars)        # the handles must outlive the batch
+        self.counts = list(counts)
+        self.N = int(sum(counts))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_init_batch(stars, counts) -> Batch:
+    return Batch(stars, counts)
+
+
+def rt_destroy_batch(batch: Batch) -> None:
+    batch.close()
+
+
+def rt_sample_batch(batch: Batch, uniforms, state, weight, status, stream=None) -> int:
+    return _check(lib().rt_sample_batch(batch.handle, _ptr(uniforms), _ptr(state), _ptr(weight),
+                                        _ptr(status), _stream(stream)),
+                  (RT_OK, RT_EEMPTY_SURFACE))
+
+
+def rt_trace_batch(batch: Batch, state, status, nacc=None, nrej=None, counters=None,
+                   opts: rt_trace_opts | None = None, stream=None) -> int:
+    if opts is None:
+        opts = make_opts()
+    return _check(lib().rt_trace_batch(batch.handle, _ptr(state), _ptr(status), _ptr(nacc),
+                                       _ptr(nrej), _ptr(counters), ctypes.byref(opts),
+                                       _stream(stream)))
+
+
+def rt_bin_batch(batch: Batch, state, weight, status, nth, nph, nnu, nu_lo, nu_hi, hist,
+                 out_of_range, stream=None) -> int:
+    return _check(lib().rt_bin_batch(batch.handle, _ptr(state), _ptr(weight), _ptr(status),
+                                     int(nth), int(nph), int(nnu), float(nu_lo), float(nu_hi),
+                                     _ptr(hist), _ptr(out_of_range), _stream(stream)))
+
+
 def rt_last_error() -> str:
     return lib().rt_last_error().decode()
 
@@ -214,4 +284,5 @@ def rt_version() -> int:
 
 EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conversion_surface",
             "rt_trace_forward", "rt_bin_spectrum", "rt_count_status", "rt_last_error",
-            "rt_version"]
+            "rt_version", "rt_init_batch", "rt_destroy_batch", "rt_sample_batch",
+            "rt_trace_batch", "rt_bin_batch"]

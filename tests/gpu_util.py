@@ -67,37 +67,22 @@ def perturbed(state0, eps, seed):
     return p
 
 
-def well_conditioned(oracle, star_vec, state0, status0, rtol, kappa_max=1e3, eps=1e-12, **kw):
-    """Oracle end states at rtol, plus the condition number of every ray: the
-    relative end-point change per relative change of the initial state,
-    kappa = max over two random perturbations of size eps.  Rays produced
-    near a reflection, grazing the star or scattered between the plasma walls
-    of the magnetosphere amplify perturbations by many orders of magnitude
-    (chaotic scattering); GPU-vs-oracle agreement at rounding level is only
-    defined for rays with kappa * (rounding ~1e-14) well below the tolerance.
-    Returns (end states, statuses, well-conditioned mask, kappa)."""
+def well_conditioned(oracle, star_vec, state0, status0, rtol, spread_max=1e-12, **kw):
+    """Oracle end states at rtol (strict FP64 build) and the spread between the
+    strict build and the same source compiled with FMA contraction -- two
+    equally valid FP64 evaluations.  Many production rays are produced near a
+    reflection or scatter between the plasma walls of the magnetosphere and
+    amplify rounding by orders of magnitude; agreement at the 1e-10 level is
+    only defined for rays whose end point is insensitive to rounding (spread
+    <= spread_max).  Returns (end states, statuses, well-conditioned mask,
+    spread)."""
     a = state0.copy()
     sa = status0.copy()
     oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), a, sa)
-    kappa = np.zeros(state0.shape[1])
-    same = np.ones(state0.shape[1], dtype=bool)
-    for seed in (1, 2):
-        b = perturbed(state0, eps, seed)
-        sb = status0.copy()
-        oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), b, sb)
-        kappa = np.maximum(kappa, rel_state_diff(b, a) / eps)
-        same &= sb == sa
-    good = same & (kappa < kappa_max)
-    return a, sa, good, kappa
-
-
-def rounding_spread(oracle, star_vec, state0, status0, rtol, eps=1e-15, **kw):
-    """End-point spread of the oracle itself under a rounding-size (eps)
-    perturbation of the initial state: the scale GPU deviations are compared to."""
-    a = state0.copy()
-    sa = status0.copy()
-    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), a, sa)
-    b = perturbed(state0, eps, 3)
+    b = state0.copy()
     sb = status0.copy()
-    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), b, sb)
-    return rel_state_diff(b, a), (sb == sa)
+    oracle.trace_forward(star_vec, oracle.trace_opts(rtol=rtol, **kw), b, sb,
+                         variant="contracted")
+    spread = rel_state_diff(b, a)
+    good = (sa == sb) & (spread <= spread_max)
+    return a, sa, good, spread

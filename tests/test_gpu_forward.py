@@ -76,12 +76,13 @@ def _trace_parity(oracle, kw, u, rtol=1e-10, **topt):
     """GPU and oracle trace the same (oracle-sampled) initial states."""
     sv = _star_vec(oracle, kw)
     st0, w0, s0 = oracle.sample(sv, u)
-    ref, sref, good, kappa = G.well_conditioned(oracle, sv, st0, s0, rtol, **topt)
+    ref, sref, good, spread = G.well_conditioned(oracle, sv, st0, s0, rtol, **topt)
     star = rt.Star(rt.make_params(**kw))
     st_d = torch.from_numpy(st0.copy()).cuda()
     s_d = torch.from_numpy(s0.copy()).cuda()
     nacc, nrej, ctr = G.gpu_trace(star, st_d, s_d, rtol=rtol, **_gpu_opts(topt))
     st_g, s_g, na = G.to_np(st_d, s_d, nacc)
+    _trace_parity.spread = spread
     return st0, s0, ref, sref, good, st_g, s_g, na, ctr.cpu().numpy()
 
 
@@ -97,18 +98,17 @@ def test_trace_parity_config0_fp64(oracle):
     traced = s0 == oracle.RAY_READY
     # statuses agree (up to the rare ill-conditioned grazing ray)
     assert (s_g[traced] == sref[traced]).mean() > 0.995
-    # well-conditioned set (kappa < 1e3): end points within 1e-10
+    # well-conditioned set (oracle strict vs contracted within 1e-12): 1e-10
     g = good & traced & (s_g == sref)
-    assert g.sum() > 0.1 * traced.sum()
+    assert g.sum() > 0.2 * traced.sum()
     d = G.rel_state_diff(st_g[:, g], ref[:, g])
     assert d.max() < 1e-10, np.sort(d)[-5:]
-    # all rays: GPU deviations are of the size the oracle itself shows under a
-    # 1e-15 perturbation of the initial state (rounding-level differences,
-    # amplified by the ray's own sensitivity)
-    spread, same = G.rounding_spread(oracle, _star_vec(oracle, kw), st0, s0, 1e-10)
-    m = traced & (s_g == sref) & same
+    # all rays: GPU deviations are of the size of the oracle's own spread
+    # between two valid FP64 evaluations (rounding amplified by the ray)
+    spread = _trace_parity.spread
+    m = traced & (s_g == sref)
     dev_all = G.rel_state_diff(st_g[:, m], ref[:, m])
-    for q in (50, 90):
+    for q in (50, 90, 99):
         assert np.percentile(dev_all, q) <= 10 * np.percentile(spread[m], q) + 1e-12, q
     # the step counters add up
     assert ctr[2] == traced.sum()
