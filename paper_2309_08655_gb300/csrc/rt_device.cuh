@@ -98,12 +98,15 @@ RT_HD __forceinline__ T gj_side(const T m0, const T m1, const T m2, const T x0, 
   return g < T(0) ? T(-1) : T(1);
 }
 
-// dx/dl = dH/dk, dk/dl = -dH/dx (Eq. Hamilton), analytic.  (Host-callable
-// only for the flop-counting scalar of rt_flops.cu.)
-template <class T>
+// dx/dl = dH/dk, dk/dl = -dH/dx (Eq. Hamilton), analytic.  With XCORR the
+// position derivative is returned without its flat-space part 2k (the caller
+// then adds 2k itself, in higher precision).  (Host-callable only for the
+// flop-counting scalar of rt_flops.cu.)
+template <class T, bool XCORR = false, bool FIN = false>
 RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
                                         const T x2, const T k0, const T k1, const T k2, T& dx0,
-                                        T& dx1, T& dx2, T& dk0, T& dk1, T& dk2) {
+                                        T& dx1, T& dx2, T& dk0, T& dk1, T& dk2,
+                                        const T F_in = T(0)) {
   const T r2 = x0 * x0 + x1 * x1 + x2 * x2;
   const T ir = rt_rsqrt(r2);
   const T n0 = x0 * ir, n1 = x1 * ir, n2 = x2 * ir;
@@ -116,9 +119,9 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
   // metric part: H_g = -W2/A + k.k + (A-1) kr^2
   //   dH_g/dk = 2k + 2(A-1) kr n
   //   dH_g/dx = (W/A + kr^2) dA + 2(A-1) kr dkr,  dA = rs r^-2 n, dkr = (k - kr n)/r
-  T gk0 = T(2) * (k0 + Am1 * kr * n0);
-  T gk1 = T(2) * (k1 + Am1 * kr * n1);
-  T gk2 = T(2) * (k2 + Am1 * kr * n2);
+  T gk0 = T(2) * ((XCORR ? T(0) : k0) + Am1 * kr * n0);
+  T gk1 = T(2) * ((XCORR ? T(0) : k1) + Am1 * kr * n1);
+  T gk2 = T(2) * ((XCORR ? T(0) : k2) + Am1 * kr * n2);
   const T cA = (W * iA + kr * kr) * c.rs * ir2;
   const T ckr = T(2) * Am1 * kr * ir;
   T gx0 = cA * n0 + ckr * (k0 - kr * n0);
@@ -129,8 +132,10 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
   T P = T(0), dP0 = T(0), dP1 = T(0), dP2 = T(0);
   if (c.plasma == PLASMA_GJ) {
     // within a step: the smooth continuation sig * F of the side the step
-    // started on (the integrator switches sig where a step crosses F = 0)
-    const T F = T(3) * n2 * mu - c.m2;
+    // started on (the integrator switches sig where a step crosses F = 0).
+    // FIN: F supplied by the caller (evaluated in higher precision: near the
+    // null cone F is a small difference of O(1) terms)
+    const T F = FIN ? F_in : T(3) * n2 * mu - c.m2;
     const T sF = c.sig;
     const T ir3 = ir2 * ir;
     P = c.cp * ir3 * (F * sF);

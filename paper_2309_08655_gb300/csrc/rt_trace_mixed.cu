@@ -1,13 +1,23 @@
 // Mixed-precision forward tracing: the Dormand-Prince stages (the analytic
 // right-hand side and the stage combinations) run in FP32 with FP32
 // accumulation of the increments; the ray state is kept in FP64 and receives
-// each accepted increment in FP64.  FP32 rounding puts a noise floor under the
-// embedded error estimate; when that floor reaches a quarter of the tolerance
-// the estimate no longer steers the step size, and the ray is promoted: it is
-// handed, from its current state, to the FP64 kernel (resume pass) for the
-// rest of its path.  This happens where the controller demands steps too
-// short for FP32 -- typically near the stellar surface or close to a turning
-// point at the resonance.
+// each accepted increment in FP64.
+//
+// Increment splitting.  The position derivative is dx/dl = 2k + c(x, k), where
+// the correction c (metric and plasma terms) is small away from the star.  With
+// k_j = k_n + dk_j at stage j, the increment is
+//   h sum_j b_j (2 k_j + c_j) = 2 h k_n + h sum_j b_j R_j,  R_j = 2 dk_j + c_j,
+// (sum_j b_j = 1): the large part 2 h k_n is formed in FP64 from the FP64
+// state, and only the small parts R_j pass through FP32.  The embedded error
+// estimate of the positions is h sum_j e_j R_j exactly (sum_j e_j = 0), and the
+// continuous extension likewise splits (sum_j d_j = 0).  FP32 rounding thus
+// acts on small quantities instead of on k itself.
+//
+// FP32 rounding still puts a noise floor under the error estimate of the
+// momenta; where a rejected step's estimate sits on that floor three times in
+// a row, the ray is promoted: it is handed, from its current state, to the
+// FP64 kernel (resume pass) for the rest of its path.  The Goldreich-Julian
+// null cone is crossed by the same located branch switch as in rt_trace.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,21 +32,47 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float EPS32 = 5.9604645e-8f;     // unit roundoff 2^-24
 constexpr float NOISE_C = 4.0f;             // rounding amplification allowed in a stage
 constexpr float NOISE_LIMIT = 0.25f;
+constexpr int NOISY_REJECTIONS_TO_PROMOTE = 3;
+constexpr float SWITCH_MIN_FRACTION_M = 1e-6f;
+constexpr float SWITCH_OVERSHOOT_M = 1e-6f;
 
-__device__ __forceinline__ void rhs32(const RayConst<float>& c, const float* y, float* f) {
-  ham_rhs<float>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+// c(x, k) and dk/dl at a point with FP64 position xd and FP32 momentum kf.
+// The Goldreich-Julian angular factor F = 3 n_z (m.n) - m_z is a small
+// difference of O(1) terms next to the null cone (where rays are guided for
+// thousands of steps), so it is formed in FP64 from the FP64 position and
+// magnetic axis; everything else runs in FP32.
+__device__ __forceinline__ void rhs32c(const RayConst<float>& c, const double* md,
+                                       const double* xd, const float* kf, float* f) {
+  const double r2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+  const double g = 3.0 * xd[2] * (md[0] * xd[0] + md[1] * xd[1] + md[2] * xd[2]) - md[2] * r2;
+  const float F = (float)g * __frcp_rn((float)r2);
+  ham_rhs<float, true, true>(c, (float)xd[0], (float)xd[1], (float)xd[2], kf[0], kf[1], kf[2],
+                             f[0], f[1], f[2], f[3], f[4], f[5], F);
 }
 
-__device__ __forceinline__ float step_factor32(float err, bool accepted, bool last_rej) {
+__device__ __forceinline__ float side_md(const double* md, double x0, double x1, double x2) {
+  return (float)gj_side<double>(md[0], md[1], md[2], x0, x1, x2);
+}
+
+__device__ __forceinline__ float step_factor32(float err, bool accepted, bool no_growth) {
   float fac = (err > 0.0f) ? 0.9f * exp2f(-0.2f * log2f(err)) : 5.0f;
   fac = fminf(5.0f, fmaxf(0.2f, fac));
-  if (!accepted || last_rej) fac = fminf(fac, 1.0f);
+  if (!accepted || no_growth) fac = fminf(fac, 1.0f);
   return fac;
 }
 
-__device__ float initial_step32(const RayConst<float>& c, const float* y0, const float* f0,
-                                float rtol, float atol, float hmax) {
-  float dnf = 0.0f, dny = 0.0f;
+// Hairer's initial step, on the full derivative f = (2k + c, dk/dl).
+__device__ float initial_step32(const RayConst<float>& c, const double* md, const double* yd,
+                                const float* f0c, float rtol, float atol) {
+  float y0[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y0[i] = (float)yd[i];
+  float f0[6], dnf = 0.0f, dny = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    f0[i] = 2.0f * y0[3 + i] + f0c[i];
+    f0[3 + i] = f0c[3 + i];
+  }
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float sk = atol + rtol * fabsf(y0[i]);
@@ -44,43 +80,39 @@ __device__ float initial_step32(const RayConst<float>& c, const float* y0, const
     dny += (y0[i] / sk) * (y0[i] / sk);
   }
   float h = (dnf <= 1e-10f || dny <= 1e-10f) ? 1e-6f : sqrtf(dny / dnf) * 0.01f;
-  h = fminf(h, hmax);
-  float y1[6], f1[6];
+  float y1[6], f1c[6];
+  double x1d[3];
 #pragma unroll
   for (int i = 0; i < 6; ++i) y1[i] = y0[i] + h * f0[i];
-  rhs32(c, y1, f1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x1d[i] = yd[i] + (double)(h * f0[i]);
+  rhs32c(c, md, x1d, y1 + 3, f1c);
   float der2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
+    const float f1 = (i < 3) ? 2.0f * y1[3 + i] + f1c[i] : f1c[i];
     const float sk = atol + rtol * fabsf(y0[i]);
-    der2 += ((f1[i] - f0[i]) / sk) * ((f1[i] - f0[i]) / sk);
+    der2 += ((f1 - f0[i]) / sk) * ((f1 - f0[i]) / sk);
   }
   der2 = sqrtf(der2) / h;
   const float der12 = fmaxf(fabsf(der2), sqrtf(dnf));
   const float h1 = (der12 <= 1e-15f) ? fmaxf(1e-6f, h * 1e-3f) : exp2f(0.2f * log2f(0.01f / der12));
-  return fminf(fminf(100.0f * h, h1), hmax);
+  return fminf(100.0f * h, h1);
 }
 
 struct LaneM {
   RayConst<float> c;
+  double md[3];        // magnetic axis in FP64 (for the null-cone factor)
   double y[6];
-  float f0[6];
+  float f0[6];         // (c, dk/dl) at y (first-same-as-last)
   float h;
   int na, nr;
+  int noisy_rej;       // consecutive rejections on the FP32 noise floor
   bool last_rej;
   bool switching;      // the current attempt ends just past a null-cone crossing
   float h_resume;
   double R_km, ma_eV;
 };
-
-// Side of the Goldreich-Julian null cone at an FP64 position (see rt_trace.cu
-// for the switching scheme, which this kernel follows in FP32).
-__device__ __forceinline__ float side_m(const RayConst<float>& c, double x0, double x1,
-                                        double x2) {
-  return (float)gj_side<double>((double)c.m0, (double)c.m1, (double)c.m2, x0, x1, x2);
-}
-constexpr float SWITCH_MIN_FRACTION_M = 1e-6f;
-constexpr float SWITCH_OVERSHOOT_M = 1e-6f;
 
 __device__ __forceinline__ int find_star_m(const TraceParams& p, int64_t i) {
   if (p.nstars <= 1) return 0;
@@ -111,21 +143,25 @@ __device__ void load_lane_m(const TraceParams& p, int64_t i, LaneM& L) {
   L.c.pa = (float)s.plasma_a;
   L.c.W2 = (float)(om * om);
   L.c.iW2 = (float)(1.0 / (om * om));
-  L.c.m0 = (float)(s.sin_tm * cpsi);
-  L.c.m1 = (float)(s.sin_tm * sp);
-  L.c.m2 = (float)s.cos_tm;
+  L.md[0] = s.sin_tm * cpsi;
+  L.md[1] = s.sin_tm * sp;
+  L.md[2] = s.cos_tm;
+  L.c.m0 = (float)L.md[0];
+  L.c.m1 = (float)L.md[1];
+  L.c.m2 = (float)L.md[2];
   L.c.disp = s.dispersion;
   L.c.plasma = s.plasma;
-  L.c.sig = side_m(L.c, L.y[0], L.y[1], L.y[2]);
+  L.c.sig = side_md(L.md, L.y[0], L.y[1], L.y[2]);
   L.switching = false;
   L.h_resume = 0.0f;
-  float yf[6];
+  float kf[3];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) yf[c] = (float)L.y[c];
-  rhs32(L.c, yf, L.f0);
-  L.h = initial_step32(L.c, yf, L.f0, (float)p.rtol, (float)p.atol, 1e30f);
-  L.na = p.nacc ? 0 : 0;
+  for (int c = 0; c < 3; ++c) kf[c] = (float)L.y[3 + c];
+  rhs32c(L.c, L.md, L.y, kf, L.f0);
+  L.h = initial_step32(L.c, L.md, L.y, L.f0, (float)p.rtol, (float)p.atol);
+  L.na = 0;
   L.nr = 0;
+  L.noisy_rej = 0;
   L.last_rej = false;
 }
 
@@ -141,8 +177,19 @@ __device__ void store_lane_m(const TraceParams& p, int64_t i, const LaneM& L, in
   if (p.nrej) p.nrej[i] = L.nr;
 }
 
-// One attempted FP32 step.  Returns -1 to continue, RAY_PROMOTED to hand the
-// ray to the FP64 pass, else the final status.
+// Position on the continuous extension at fraction th (FP64 large part + FP32
+// small part).
+__device__ __forceinline__ void dense_x(const LaneM& L, float h, float th, const float* sR,
+                                        const float* r3, const float* r4, const float* r5,
+                                        double* xd) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    xd[i] = L.y[i] + (double)th * 2.0 * (double)h * L.y[3 + i] +
+            (double)(th * (sR[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]))));
+}
+
+// One attempted step.  Returns -1 to continue, RAY_PROMOTED to hand the ray to
+// the FP64 pass, else the final status.
 __device__ int advance_m(const TraceParams& p, LaneM& L) {
   if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
   const float h = L.h;
@@ -150,91 +197,122 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   float yf[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) yf[i] = (float)L.y[i];
-  const float* k1 = L.f0;
-  float t[6], k2[6], k3[6], k4[6], k5[6], k6[6], k7[6], d5[6];
+  // stage derivatives: R (position, small part) and K (momentum), j = 1..7
+  float R1[3], R2[3], R3[3], R4[3], R5[3], R6[3], R7[3];
+  float K1[3], K2[3], K3[3], K4[3], K5[3], K6[3], K7[3];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) t[i] = yf[i] + h * ((float)DP::a21 * k1[i]);
-  rhs32(L.c, t, k2);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) t[i] = yf[i] + h * ((float)DP::a31 * k1[i] + (float)DP::a32 * k2[i]);
-  rhs32(L.c, t, k3);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    t[i] = yf[i] + h * ((float)DP::a41 * k1[i] + (float)DP::a42 * k2[i] + (float)DP::a43 * k3[i]);
-  rhs32(L.c, t, k4);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    t[i] = yf[i] + h * ((float)DP::a51 * k1[i] + (float)DP::a52 * k2[i] +
-                        (float)DP::a53 * k3[i] + (float)DP::a54 * k4[i]);
-  rhs32(L.c, t, k5);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    t[i] = yf[i] + h * ((float)DP::a61 * k1[i] + (float)DP::a62 * k2[i] +
-                        (float)DP::a63 * k3[i] + (float)DP::a64 * k4[i] +
-                        (float)DP::a65 * k5[i]);
-  rhs32(L.c, t, k6);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    d5[i] = h * ((float)DP::b1 * k1[i] + (float)DP::b3 * k3[i] + (float)DP::b4 * k4[i] +
-                 (float)DP::b5 * k5[i] + (float)DP::b6 * k6[i]);
-    t[i] = yf[i] + d5[i];
+  for (int i = 0; i < 3; ++i) {
+    R1[i] = L.f0[i];
+    K1[i] = L.f0[3 + i];
   }
-  rhs32(L.c, t, k7);
-  float s = 0.0f, sn = 0.0f;
+  float t[6], f[6], dks[3];
+  double xs[3];
+#define RT_STAGE(Rout, Kout, cj, SUMR, SUMK)                                          \
+  {                                                                                   \
+    _Pragma("unroll") for (int i = 0; i < 3; ++i) {                                   \
+      dks[i] = h * (SUMK);                                                            \
+      xs[i] = L.y[i] + (double)(2.0f * h * (float)(cj) * yf[3 + i] + h * (SUMR));     \
+      t[3 + i] = yf[3 + i] + dks[i];                                                  \
+    }                                                                                 \
+    rhs32c(L.c, L.md, xs, t + 3, f);                                                  \
+    _Pragma("unroll") for (int i = 0; i < 3; ++i) {                                   \
+      Rout[i] = 2.0f * dks[i] + f[i];                                                 \
+      Kout[i] = f[3 + i];                                                             \
+    }                                                                                 \
+  }
+  RT_STAGE(R2, K2, 1.0 / 5.0, (float)DP::a21 * R1[i], (float)DP::a21 * K1[i]);
+  RT_STAGE(R3, K3, 3.0 / 10.0, (float)DP::a31 * R1[i] + (float)DP::a32 * R2[i],
+           (float)DP::a31 * K1[i] + (float)DP::a32 * K2[i]);
+  RT_STAGE(R4, K4, 4.0 / 5.0,
+           (float)DP::a41 * R1[i] + (float)DP::a42 * R2[i] + (float)DP::a43 * R3[i],
+           (float)DP::a41 * K1[i] + (float)DP::a42 * K2[i] + (float)DP::a43 * K3[i]);
+  RT_STAGE(R5, K5, 8.0 / 9.0,
+           (float)DP::a51 * R1[i] + (float)DP::a52 * R2[i] + (float)DP::a53 * R3[i] +
+               (float)DP::a54 * R4[i],
+           (float)DP::a51 * K1[i] + (float)DP::a52 * K2[i] + (float)DP::a53 * K3[i] +
+               (float)DP::a54 * K4[i]);
+  RT_STAGE(R6, K6, 1.0,
+           (float)DP::a61 * R1[i] + (float)DP::a62 * R2[i] + (float)DP::a63 * R3[i] +
+               (float)DP::a64 * R4[i] + (float)DP::a65 * R5[i],
+           (float)DP::a61 * K1[i] + (float)DP::a62 * K2[i] + (float)DP::a63 * K3[i] +
+               (float)DP::a64 * K4[i] + (float)DP::a65 * K5[i]);
+#undef RT_STAGE
+  // 5th-order increments: small position part and momentum
+  float sR[3], dK[3];
   double yn[6];
 #pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    sR[i] = h * ((float)DP::b1 * R1[i] + (float)DP::b3 * R3[i] + (float)DP::b4 * R4[i] +
+                 (float)DP::b5 * R5[i] + (float)DP::b6 * R6[i]);
+    dK[i] = h * ((float)DP::b1 * K1[i] + (float)DP::b3 * K3[i] + (float)DP::b4 * K4[i] +
+                 (float)DP::b5 * K5[i] + (float)DP::b6 * K6[i]);
+    yn[i] = L.y[i] + 2.0 * (double)h * L.y[3 + i] + (double)sR[i];
+    yn[3 + i] = L.y[3 + i] + (double)dK[i];
+  }
+  // stage 7 at the new point (first-same-as-last)
+  float fn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t[i] = (float)yn[i];
+  rhs32c(L.c, L.md, yn, t + 3, fn);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R7[i] = 2.0f * dK[i] + fn[i];
+    K7[i] = fn[3 + i];
+  }
+  // error estimate (sum_j e_j = 0 removes the 2 h k_n part) and its FP32 floor
+  float s = 0.0f, snk = 0.0f;
+#pragma unroll
   for (int i = 0; i < 6; ++i) {
-    yn[i] = L.y[i] + (double)d5[i];
-    const float a1 = (float)DP::e1 * k1[i], a3 = (float)DP::e3 * k3[i];
-    const float a4 = (float)DP::e4 * k4[i], a5 = (float)DP::e5 * k5[i];
-    const float a6 = (float)DP::e6 * k6[i], a7 = (float)DP::e7 * k7[i];
+    const bool xp = i < 3;
+    const int c = xp ? i : i - 3;
+    const float v1 = xp ? R1[c] : K1[c], v3 = xp ? R3[c] : K3[c], v4 = xp ? R4[c] : K4[c];
+    const float v5 = xp ? R5[c] : K5[c], v6 = xp ? R6[c] : K6[c], v7 = xp ? R7[c] : K7[c];
+    const float a1 = (float)DP::e1 * v1, a3 = (float)DP::e3 * v3, a4 = (float)DP::e4 * v4;
+    const float a5 = (float)DP::e5 * v5, a6 = (float)DP::e6 * v6, a7 = (float)DP::e7 * v7;
     const float e = h * (a1 + a3 + a4 + a5 + a6 + a7);
-    const float nz = NOISE_C * EPS32 * fabsf(h) *
-                     (fabsf(a1) + fabsf(a3) + fabsf(a4) + fabsf(a5) + fabsf(a6) + fabsf(a7));
     const float sc = atol + rtol * fmaxf(fabsf(yf[i]), fabsf((float)yn[i]));
     s += (e / sc) * (e / sc);
-    sn += (nz / sc) * (nz / sc);
+    if (!xp) {
+      const float nz = NOISE_C * EPS32 * fabsf(h) *
+                       (fabsf(a1) + fabsf(a3) + fabsf(a4) + fabsf(a5) + fabsf(a6) + fabsf(a7));
+      snk += (nz / sc) * (nz / sc);
+    }
   }
   const float en = sqrtf(s / 6.0f);
-  const float noise = sqrtf(sn / 6.0f);
+  const bool noisy = sqrtf(snk / 6.0f) > NOISE_LIMIT;
   if (!isfinite(en)) {
     ++L.nr;
     L.h = h * 0.2f;
     L.last_rej = true;
     return (L.h < 1e-12f) ? RAY_NAN : -1;
   }
-  // A rejection whose error estimate sits on the FP32 noise floor cannot be
-  // trusted: the ray continues in FP64.  An accepted step on the noise floor
-  // is kept, but may not grow the step.
-  const bool noisy = noise > NOISE_LIMIT;
-  if (noisy && !(en <= 1.0f)) return RAY_PROMOTED;
+  // continuous-extension pieces (small parts), for the event locations
+  float r3[3], r4[3], r5[3];
   const bool gj = (L.c.plasma == PLASMA_GJ);
-  if (en <= 1.0f && gj && !L.switching && L.c.sig * side_m(L.c, yn[0], yn[1], yn[2]) < 0.0f) {
-    // the step crossed the null cone: locate on the continuous extension and
-    // redo the step to end just past the crossing
-    float r3[3], r4[3], r5[3];
+  const bool need_dense = (en <= 1.0f);
+  if (need_dense) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      r3[i] = h * k1[i] - d5[i];
-      r4[i] = d5[i] - h * k7[i] - r3[i];
-      r5[i] = h * ((float)DP::d1 * k1[i] + (float)DP::d3 * k3[i] + (float)DP::d4 * k4[i] +
-                   (float)DP::d5 * k5[i] + (float)DP::d6 * k6[i] + (float)DP::d7 * k7[i]);
+      r3[i] = h * R1[i] - sR[i];
+      r4[i] = sR[i] - h * R7[i] - r3[i];
+      r5[i] = h * ((float)DP::d1 * R1[i] + (float)DP::d3 * R3[i] + (float)DP::d4 * R4[i] +
+                   (float)DP::d5 * R5[i] + (float)DP::d6 * R6[i] + (float)DP::d7 * R7[i]);
     }
+  }
+  if (en <= 1.0f && gj && !L.switching && L.c.sig * side_md(L.md, yn[0], yn[1], yn[2]) < 0.0f) {
+    // the step crossed the null cone: locate and redo the step to end just past it
     float lo = 0.0f, hi = 1.0f;
     for (int it = 0; it < 40; ++it) {
       const float mid = 0.5f * (lo + hi);
       if (mid <= lo || mid >= hi) break;
       double xd[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-        xd[i] = L.y[i] + (double)(mid * (d5[i] + (1.0f - mid) * (r3[i] + mid * (r4[i] +
-                                                         (1.0f - mid) * r5[i]))));
-      if (L.c.sig * side_m(L.c, xd[0], xd[1], xd[2]) >= 0.0f) lo = mid; else hi = mid;
+      dense_x(L, h, mid, sR, r3, r4, r5, xd);
+      if (L.c.sig * side_md(L.md, xd[0], xd[1], xd[2]) >= 0.0f) lo = mid; else hi = mid;
     }
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION_M) {
       L.c.sig = -L.c.sig;
-      rhs32(L.c, yf, L.f0);
+      rhs32c(L.c, L.md, L.y, yf + 3, L.f0);
       L.h = h;
     } else {
       L.h_resume = h;
@@ -245,49 +323,42 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   }
   if (en <= 1.0f) {
     ++L.na;
+    L.noisy_rej = 0;
     const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
     if (rnew >= p.r_out) {
-      // locate |x(th)| = r_out on the continuous extension (FP32 increments
-      // added to the FP64 state)
-      float r3[6], r4[6], r5[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        r3[i] = h * k1[i] - d5[i];
-        r4[i] = d5[i] - h * k7[i] - r3[i];
-        r5[i] = h * ((float)DP::d1 * k1[i] + (float)DP::d3 * k3[i] + (float)DP::d4 * k4[i] +
-                     (float)DP::d5 * k5[i] + (float)DP::d6 * k6[i] + (float)DP::d7 * k7[i]);
-      }
-      double lo = 0.0, hi = 1.0;
+      // locate |x(th)| = r_out on the continuous extension
+      float lo = 0.0f, hi = 1.0f;
       for (int it = 0; it < 60; ++it) {
-        const double mid = 0.5 * (lo + hi);
+        const float mid = 0.5f * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        const float m = (float)mid;
         double xd[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          xd[i] = L.y[i] +
-                  (double)(m * (d5[i] + (1.0f - m) * (r3[i] + m * (r4[i] + (1.0f - m) * r5[i]))));
+        dense_x(L, h, mid, sR, r3, r4, r5, xd);
         const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
         if (rd < p.r_out) lo = mid; else hi = mid;
       }
-      const float th = (float)(0.5 * (lo + hi));
+      const float th = 0.5f * (lo + hi);
+      double xd[3];
+      dense_x(L, h, th, sR, r3, r4, r5, xd);
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-        L.y[i] += (double)(th * (d5[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]))));
+      for (int i = 0; i < 3; ++i) {
+        const float q3 = h * K1[i] - dK[i];
+        const float q4 = dK[i] - h * K7[i] - q3;
+        const float q5 = h * ((float)DP::d1 * K1[i] + (float)DP::d3 * K3[i] +
+                              (float)DP::d4 * K4[i] + (float)DP::d5 * K5[i] +
+                              (float)DP::d6 * K6[i] + (float)DP::d7 * K7[i]);
+        L.y[3 + i] += (double)(th * (dK[i] + (1.0f - th) * (q3 + th * (q4 + (1.0f - th) * q5))));
+        L.y[i] = xd[i];
+      }
       return RAY_ESCAPED;
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      L.y[i] = yn[i];
-      L.f0[i] = k7[i];
-    }
-    if (rnew <= p.r_capture) return RAY_CAPTURED;
-    if (gj && L.c.sig * side_m(L.c, L.y[0], L.y[1], L.y[2]) < 0.0f) {
-      L.c.sig = -L.c.sig;             // past the cone: continue on the other side
-      float yc[6];
+    for (int i = 0; i < 6; ++i) L.y[i] = yn[i];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) yc[i] = (float)L.y[i];
-      rhs32(L.c, yc, L.f0);
+    for (int i = 0; i < 6; ++i) L.f0[i] = fn[i];
+    if (rnew <= p.r_capture) return RAY_CAPTURED;
+    if (gj && L.c.sig * side_md(L.md, L.y[0], L.y[1], L.y[2]) < 0.0f) {
+      L.c.sig = -L.c.sig;             // past the cone: continue on the other side
+      rhs32c(L.c, L.md, L.y, t + 3, L.f0);
     }
     if (L.switching) {
       L.h = L.h_resume;
@@ -298,6 +369,8 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
     L.last_rej = false;
     return -1;
   }
+  if (noisy && ++L.noisy_rej >= NOISY_REJECTIONS_TO_PROMOTE) return RAY_PROMOTED;
+  if (!noisy) L.noisy_rej = 0;
   ++L.nr;
   L.h = h * step_factor32(en, false, L.last_rej);
   L.last_rej = true;
@@ -356,11 +429,11 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
       promoted += __shfl_down_sync(FULL, promoted, o);
     }
     if (lane == 0) {
-      atomicAdd((unsigned long long*)&p.counters[0], (unsigned long long)acc);
-      atomicAdd((unsigned long long*)&p.counters[1], (unsigned long long)rej);
-      atomicAdd((unsigned long long*)&p.counters[2], (unsigned long long)traced);
-      atomicAdd((unsigned long long*)&p.counters[3], (unsigned long long)esc);
-      atomicAdd((unsigned long long*)&p.counters[4], (unsigned long long)promoted);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ACC], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_REJ], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&p.counters[CTR_RAYS], (unsigned long long)traced);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ESC], (unsigned long long)esc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_PROMOTED], (unsigned long long)promoted);
     }
   }
 }

@@ -1,0 +1,64 @@
+"""Small, self-contained forward case for kernel profiling (ncu) and quick timing.
+
+    python -m paper_2309_08655_gb300.profile_case --precision fp64 --n 1024
+
+Samples n rays of the aligned 200 km-surface star (seed 0), traces them once in
+the requested precision (one persistent trace launch, after one untimed warm-up
+launch on a copy) and bins them; prints the trace time and step counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import inputs as I
+from . import rt
+from .build import build
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--rtol", type=float, default=None)
+    ap.add_argument("--config", choices=["config0", "config1"], default="config0")
+    a = ap.parse_args()
+    build()
+    dev = torch.device("cuda:0")
+    if a.config == "config0":
+        kw = I.star_config0()
+    else:
+        kw = I.stars_config1()[15]
+    u = torch.from_numpy(I.sample_uniforms(0, a.n)).to(dev)
+    star = rt.Star(rt.make_params(**kw))
+    st = torch.empty((8, a.n), dtype=torch.float64, device=dev)
+    w = torch.empty(a.n, dtype=torch.float64, device=dev)
+    s = torch.empty(a.n, dtype=torch.uint8, device=dev)
+    rt.rt_sample_conversion_surface(star, a.n, u, st, w, s)
+    prec = rt.PREC_FP64 if a.precision == "fp64" else rt.PREC_MIXED
+    rtol = a.rtol if a.rtol is not None else (1e-10 if prec == rt.PREC_FP64 else 1e-8)
+    opts = rt.make_opts(rtol=rtol, precision=prec)
+    st0, s0 = st.clone(), s.clone()
+    rt.rt_trace_forward(star, a.n, st0, s0, opts=opts)          # warm-up
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    rt.rt_trace_forward(star, a.n, st, s, counters=ctr, opts=opts)
+    e1.record()
+    hist = torch.empty((64, 32, 128), dtype=torch.float64, device=dev)
+    oor = torch.empty(1, dtype=torch.float64, device=dev)
+    rt.rt_bin_spectrum(star, a.n, st, w, s, 64, 32, 128, 0.0, 9.0, hist, None, None, oor)
+    torch.cuda.synchronize()
+    c = ctr.cpu().numpy()
+    print(json.dumps({"precision": a.precision, "n": a.n, "rtol": rtol,
+                      "trace_ms": e0.elapsed_time(e1), "accepted": int(c[0]),
+                      "rejected": int(c[1]), "rays": int(c[2]), "promoted": int(c[4]),
+                      "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}))
+
+
+if __name__ == "__main__":
+    main()
