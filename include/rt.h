@@ -248,6 +248,37 @@ rt_status rt_bin_batch(rt_batch* batch, const double* d_state, const double* d_w
                        void* stream);
 
 /*
+ * rt_bin_spectrum_noalloc - rt_bin_spectrum for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a service of the
+ * library.  Some callers run under a device-memory budget that someone else
+ * manages (a framework's caching allocator, a fixed pool shared through MPS)
+ * or cannot afford the device-wide synchronisation that cudaMalloc and
+ * cudaFree can imply (a real-time pipeline); rt_bin_spectrum would allocate
+ * its fixed-point accumulator on first use.  This entry point allocates
+ * nothing: its accumulator is a file-scope device array of
+ * RT_BIN_NOALLOC_MAX_ENTRIES int64 (4 MiB) that every GPU which loads the
+ * library holds until the process exits.  It takes the star parameters by
+ * value (no rt_star handle) and otherwise has the arguments, outputs and
+ * fixed-point semantics of rt_bin_spectrum.
+ *   Limit: 2 + nth*nph*nnu + nth*nph + nnu <= RT_BIN_NOALLOC_MAX_ENTRIES,
+ *   else RT_EINVAL (message in rt_last_error()).
+ *   Set-up: the first call on a device looks up the device address of the
+ *   array (cudaGetSymbolAddress, with that device current); make that first
+ *   call before any stream capture.
+ *   Sharing: every call on a device uses the same array; each call clears
+ *   the part it uses (an asynchronous memset on `stream`) and leaves its sums
+ *   there afterwards.  Calls that overlap on the GPU (different streams, or
+ *   different host threads without ordering) race and corrupt each other's
+ *   results: order them on one stream.
+ */
+#define RT_BIN_NOALLOC_MAX_ENTRIES (1 << 19)
+rt_status rt_bin_spectrum_noalloc(const rt_star_params* params, int64_t n, const double* d_state,
+                                  const double* d_weight, const uint8_t* d_status, int32_t nth,
+                                  int32_t nph, int32_t nnu, double nu_lo, double nu_hi,
+                                  double* d_hist, double* d_sky, double* d_spec,
+                                  double* d_out_of_range, void* stream);
+
+/*
  * rt_count_status - histogram of per-ray status codes (synchronises the
  * stream).  counts: host array of RT_RAY_NSTATUS int64.  Returns RT_EPARTIAL
  * if any ray ended in MAXSTEPS, NAN or STIFF, else RT_OK.

@@ -65,6 +65,8 @@ rt_status check_dev_ptr(const void* p, const char* name) {
 
 }  // namespace
 
+void rtk::set_last_error(const char* msg) { g_err = msg; }
+
 struct rt_star {
   rt_star_params p;
   rtk::StarDev h;               // host copy of the descriptor

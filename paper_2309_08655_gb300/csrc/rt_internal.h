@@ -61,6 +61,9 @@ cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_s
                                cudaStream_t stream);
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
 
+// Sets the thread-local message returned by rt_last_error().
+void set_last_error(const char* msg);
+
 // Number of int64 scratch entries rt_bin_spectrum needs.
 inline size_t bin_scratch_entries(int nth, int nph, int nnu) {
   return 2 + (size_t)nth * nph * nnu + (size_t)nth * nph + (size_t)nnu;
