@@ -93,6 +93,11 @@ def lib_contracted():
         L.or_trace_forward.argtypes = [dp, dp, ctypes.c_long, dp, ctypes.POINTER(ctypes.c_uint8),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        dp, ctypes.c_int]
+        L.or_trace_backward.restype = None
+        L.or_trace_backward.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                        ctypes.POINTER(ctypes.c_uint8),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         _lib_contracted = L
     return _lib_contracted
 
@@ -130,6 +135,10 @@ def lib():
         L.or_bin.restype = None
         L.or_bin.argtypes = [dp, ctypes.c_long, dp, dp, u8p, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.or_trace_backward.restype = None
+        L.or_trace_backward.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                                        u8p, ip, ctypes.c_int]
         L.or_dp5_tableau.restype = None
         L.or_dp5_tableau.argtypes = [dp, dp, dp, dp, dp, dp]
         L.or_dp5_linear.restype = ctypes.c_long
@@ -290,3 +299,17 @@ def dp5_linear_dense(M, y0, h, th):
     out = np.zeros(6)
     lib().or_dp5_linear_dense(_dp(M), _dp(y0), float(h), float(th), _dp(out))
     return out
+
+
+def trace_backward(star, opts, nx, ny, incl, dist_over_R=1e4, bmax_over_R=50.0, Lc_cut_km=0.0,
+                   nthreads=None, variant: str = "strict"):
+    """Backward image (ny, nx) of pixel contributions to dP/dOmega [W/sr] at
+    inclination incl (rad) from the rotation axis; returns (image, status, ncross)."""
+    img = np.zeros((ny, nx))
+    st = np.zeros((ny, nx), dtype=np.uint8)
+    nc = np.zeros((ny, nx), dtype=np.int32)
+    L = lib() if variant == "strict" else lib_contracted()
+    L.or_trace_backward(_dp(star), _dp(opts), int(nx), int(ny), float(incl),
+                            float(dist_over_R), float(bmax_over_R), float(Lc_cut_km), _dp(img),
+                            _u8(st), _ip(nc), nthreads or default_threads())
+    return img, st, nc

@@ -140,8 +140,8 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma 
 
 // The photon Hamiltonian H(x, k) / m_a^2 with k_t = -omega_inf fixed (static
 // snapshot of the plasma, so dk_t/dlambda = 0).
-template <class T>
-inline T hamiltonian(const Star& s, const double m[3], double omega_inf, const T x[3],
+template <class T, class W = double>
+inline T hamiltonian(const Star& s, const double m[3], W omega_inf, const T x[3],
                      const T k[3], int sigma = 0) {
   T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   T n[3] = {x[0] / r, x[1] / r, x[2] / r};

@@ -266,8 +266,17 @@ static double locate_switch(const double m[3], const double y[6], const double y
   return lo;
 }
 
+// Called after every accepted step with the step's start and end, its stages
+// (for the continuous extension) and the null-cone branch in use.
+struct StepHook {
+  virtual void on_step(const double y[6], const double ynew[6], const double K[7][6], double h,
+                       int sigma) = 0;
+  virtual ~StepHook() {}
+};
+
 static int trace_ray(const Star& s, const double m[3], double omega_inf, double y[6],
-                     const TraceOpts& o, long* nacc_out, long* nrej_out, double* lam_out) {
+                     const TraceOpts& o, long* nacc_out, long* nrej_out, double* lam_out,
+                     StepHook* hook = nullptr) {
   RayRHS f{&s, m, omega_inf};
   const bool gj = (s.plasma == PLASMA_GJ);
   if (gj) f.sigma = gj_branch(m, y);
@@ -311,6 +320,7 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
         continue;
       }
       ++nacc;
+      if (hook) hook->on_step(y, ynew, K, h, f.sigma);
       double rnew = norm3(ynew);
       if (rnew >= o.r_out) {
         // locate |x(th)| = r_out on the continuous extension
@@ -354,6 +364,192 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
   *nrej_out = nrej;
   if (lam_out) *lam_out = lam;
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// Backward image-plane estimator (Sec. 2.1, Eq. BackPower; every level
+// crossing along the worldline contributes, Sec. 5.1.3).
+//
+// Liouville's theorem carries the forward phase-space integral
+//   P = int d^3x d^3k j,   j = sqrt(A) delta(E_gamma - E_a) Psi f_a
+// (the integrand behind the forward weights) to the asymptotic phase space of
+// the photons crossing a distant plane in direction Omega, where
+// d^3x d^3k = dA dt omega^2 domega dOmega in vacuum.  Hence
+//   dP/dOmega = int dA int domega omega^2 int_ray j dt,
+// and the ray integral of the delta function is a sum over the crossings of
+// g = E_gamma - E_a = 0 (the photon on shell meets the axion shell
+// omega^2 - |k|^2 = m_a^2 with the same k_mu):
+//   int_ray j dt = sum_c sqrt(A) Psi f_a |dt/dl| / |dg/dl|.
+// The line is narrow (width ~ v0^2), so the rays are traced at its centre
+// omega_0 = m_a sqrt(1 + v0^2) and the frequency integral of f_a is analytic:
+//   int domega omega^2 f_a = omega_0 n_inf / (2 pi^{3/2} k0)  (Maxwellian),
+//                           omega_0 n_inf / (4 pi k0)         (monochromatic).
+// Pixels are rectangles 2 b_max / nx by 2 b_max / ny; each ray goes through a pixel
+// centre perpendicular to the plane.  The time-reversed ray (k -> -k, same
+// Hamiltonian, H even in k) is integrated inward from the plane.
+// IR cut (Sec. 4.4, garbled there): L_c = E / |dE_gamma/ds - dE_a/ds| along the
+// ray (a length); crossings with L_c > Lc_cut are dropped when Lc_cut > 0.
+
+// g = E_gamma - E_a at a photon phase-space point (scaled units): omega from
+// the Killing energy, the axion energy with the same k.
+template <class T>
+static T crossing_g(const Star& s, double omega_inf, const T x[3], const T k[3]) {
+  T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  T n[3] = {x[0] / r, x[1] / r, x[2] / r};
+  T A = 1.0 - s.rs_prop / r;
+  T omega = omega_inf / sqrt(A);
+  T kn = n[0] * k[0] + n[1] * k[1] + n[2] * k[2];
+  T kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + (A - 1.0) * kn * kn;   // g^{ij} k_i k_j
+  return omega - sqrt(1.0 + kk);
+}
+
+struct BackwardAcc : StepHook {
+  const Star* s;
+  const double* m;
+  double omega_inf;
+  double Lc_cut;        // units of R (0: no cut)
+  double sum = 0.0;     // sum over crossings of sqrt(A) Psi |dt/dl| / |dg/dl| [eV^2]
+  int ncross = 0, ncut = 0;
+  bool have_g = false;
+  double g_prev = 0.0;
+
+  double g_at(const double y[6]) const { return crossing_g<double>(*s, omega_inf, y, y + 3); }
+
+  void contribution(const double y[6], int sigma) {
+    using units::PI;
+    // dg/dl = grad_y g . f(y)  (dual numbers, oracle RHS)
+    typedef Dual<6> D;
+    D xd[3], kd[3];
+    for (int i = 0; i < 3; ++i) {
+      xd[i] = D::var(y[i], i);
+      kd[i] = D::var(y[3 + i], 3 + i);
+    }
+    D gd = crossing_g<D>(*s, omega_inf, xd, kd);
+    double f[6];
+    rhs(*s, m, omega_inf, y, f, sigma);
+    double dg = 0.0;
+    for (int i = 0; i < 6; ++i) dg += gd.d[i] * f[i];
+    // dt/dl = dH/dk_t = -dH/d(omega_inf)
+    Dual<1> w = Dual<1>::var(omega_inf, 0);
+    Dual<1> xw[3], kw[3];
+    for (int i = 0; i < 3; ++i) { xw[i] = Dual<1>(y[i]); kw[i] = Dual<1>(y[3 + i]); }
+    Dual<1> Hw = hamiltonian(*s, m, w, xw, kw, sigma);
+    const double dtdl = std::fabs(Hw.d[0]);
+    // proper speed along the ray, for the conversion length
+    const double r = norm3(y);
+    const double n[3] = {y[0] / r, y[1] / r, y[2] / r};
+    const double A = 1.0 - s->rs_prop / r;
+    const double vn = n[0] * f[0] + n[1] * f[1] + n[2] * f[2];
+    const double v2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + (1.0 / A - 1.0) * vn * vn;
+    const double E = omega_inf / std::sqrt(A);                  // units of m_a
+    const double Lc = E * std::sqrt(v2) / std::fabs(dg);        // units of R
+    ++ncross;
+    if (Lc_cut > 0.0 && Lc > Lc_cut) { ++ncut; return; }
+    // Psi at the crossing
+    const double wp2 = plasma_freq2<double>(*s, m, y);
+    double B[3];
+    dipole_field(m, y, B);
+    const double Bn = norm3(B);
+    const double kn = n[0] * y[3] + n[1] * y[4] + n[2] * y[5];
+    double ko[3];
+    for (int i = 0; i < 3; ++i) ko[i] = y[3 + i] + (std::sqrt(A) - 1.0) * kn * n[i];
+    const double ko2 = ko[0] * ko[0] + ko[1] * ko[1] + ko[2] * ko[2];
+    const double kb = (ko[0] * B[0] + ko[1] * B[1] + ko[2] * B[2]);
+    const double cos2 = kb * kb / (ko2 * Bn * Bn);
+    const double sin2 = 1.0 - cos2;
+    double shape;
+    if (s->dispersion == DISP_ISO) {
+      shape = sin2;
+    } else {
+      const double Dd = cos2 * wp2 * (wp2 - 2.0 * E * E) + E * E * E * E;
+      shape = E * E * E * E * sin2 / Dd;
+    }
+    const double Bmag = s->B0_eV2 * Bn;
+    const double Psi = 0.5 * PI * s->g_eV * s->g_eV * Bmag * Bmag * shape * (E * s->ma_eV);
+    // |dt/dl| / |dg/dl| in eV^-2: (R / m_a) x the scaled ratio
+    const double ratio = dtdl / std::fabs(dg) * s->R_inv_eV / s->ma_eV;
+    sum += std::sqrt(A) * Psi * ratio;
+  }
+
+  int subdiv = 16;      // sign of g sampled at subdiv points of each step
+
+  void on_step(const double y[6], const double ynew[6], const double K[7][6], double h,
+               int sigma) override {
+    if (!have_g) { g_prev = g_at(y); have_g = true; }
+    // A ray that turns near the resonance crosses it twice within a short
+    // stretch; the sign of g is therefore sampled on the continuous extension
+    // at subdiv points per step, and every sign change is located.
+    double yd[6];
+    double th0 = 0.0, gA = g_prev;
+    for (int q = 1; q <= subdiv; ++q) {
+      const double th1 = (double)q / subdiv;
+      double gB;
+      if (q == subdiv) {
+        gB = g_at(ynew);
+      } else {
+        dp5_dense(y, ynew, K, h, th1, yd);
+        gB = g_at(yd);
+      }
+      if ((gA < 0.0) != (gB < 0.0)) {
+        double lo = th0, hi = th1;
+        const bool negA = gA < 0.0;
+        for (int it = 0; it < 200; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          dp5_dense(y, ynew, K, h, mid, yd);
+          if ((g_at(yd) < 0.0) == negA) lo = mid; else hi = mid;
+        }
+        dp5_dense(y, ynew, K, h, 0.5 * (lo + hi), yd);
+        contribution(yd, sigma);
+      }
+      th0 = th1;
+      gA = gB;
+    }
+    g_prev = gA;
+  }
+};
+
+static void backward_pixel(const Star& s, const TraceOpts& base, double incl, double D,
+                           double bx, double by, double omega_inf, double Lc_cut_km,
+                           double* value, unsigned char* status, int* ncross) {
+  double m[3];
+  magnetic_axis(s, s.psi, m);
+  const double o[3] = {std::sin(incl), 0.0, std::cos(incl)};
+  const double e1[3] = {std::cos(incl), 0.0, -std::sin(incl)};
+  const double e2[3] = {0.0, 1.0, 0.0};
+  double y[6];
+  for (int i = 0; i < 3; ++i) y[i] = D * o[i] + bx * e1[i] + by * e2[i];
+  // on-shell |k| along the orthonormal direction d = -o (time-reversed photon)
+  const double r = norm3(y);
+  const double n[3] = {y[0] / r, y[1] / r, y[2] / r};
+  const double A = 1.0 - s.rs_prop / r;
+  const double dn = -(n[0] * o[0] + n[1] * o[1] + n[2] * o[2]);
+  auto Hs = [&](double sk) {
+    double k[3];
+    for (int i = 0; i < 3; ++i) k[i] = sk * (-o[i] + (1.0 / std::sqrt(A) - 1.0) * dn * n[i]);
+    return hamiltonian<double>(s, m, omega_inf, y, k);
+  };
+  double lo = 0.0, hi = 4.0 * omega_inf;
+  for (int it = 0; it < 300; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (Hs(mid) < 0.0) lo = mid; else hi = mid;
+  }
+  const double sk = 0.5 * (lo + hi);
+  for (int i = 0; i < 3; ++i) y[3 + i] = sk * (-o[i] + (1.0 / std::sqrt(A) - 1.0) * dn * n[i]);
+  TraceOpts opt = base;
+  opt.r_out = r;                 // escaped once back at the plane's distance
+  opt.lambda_max = 0.0;
+  BackwardAcc acc;
+  acc.s = &s;
+  acc.m = m;
+  acc.omega_inf = omega_inf;
+  acc.Lc_cut = Lc_cut_km / s.R_km;
+  long na, nr;
+  double lam;
+  *status = (unsigned char)trace_ray(s, m, omega_inf, y, opt, &na, &nr, &lam, &acc);
+  *value = acc.sum;
+  *ncross = acc.ncross - acc.ncut;
 }
 
 // Physical SoA state (rows: x[3] km, k[3] eV, delta, psi) <-> scaled ray.
@@ -456,6 +652,36 @@ void or_trace_forward(const double* sp, const double* topt, long n, double* stat
     if (nacc) nacc[i] = (int)na;
     if (nrej) nrej[i] = (int)nr;
     if (lam) lam[i] = l;
+  });
+}
+
+// Backward image: ny x nx pixels (row-major, y index slow), value = the pixel's
+// contribution to dP/dOmega [W / sr] (frequency integrated over the line),
+// plus status and the number of crossings counted per pixel.  The star's
+// fixed phase psi is used.
+void or_trace_backward(const double* sp, const double* topt, int nx, int ny, double incl,
+                       double dist_over_R, double bmax_over_R, double Lc_cut_km, double* image,
+                       unsigned char* status, int* ncross, int nthreads) {
+  using units::PI;
+  Star s = make_star(sp);
+  TraceOpts o = make_opts(topt);
+  const double v0 = s.v0;
+  const double omega_inf = std::sqrt(1.0 + v0 * v0);          // line centre / m_a
+  const double k0 = v0 * s.ma_eV, w0 = omega_inf * s.ma_eV;   // [eV]
+  const double Fa = (s.fa_model == FA_DELTA) ? w0 * s.n_inf / (4.0 * PI * k0)
+                                             : w0 * s.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
+  const double dbx = 2.0 * bmax_over_R / nx, dby = 2.0 * bmax_over_R / ny;   // units of R
+  const double area_eV = (dbx * s.R_inv_eV) * (dby * s.R_inv_eV);          // [eV^-2]
+  const double EV2_W = units::EV_J / units::HBAR_EV_S;
+  parallel_for((long)nx * ny, nthreads, [&](long p) {
+    const int i = (int)(p % nx), j = (int)(p / nx);
+    const double bx = -bmax_over_R + (i + 0.5) * dbx;
+    const double by = -bmax_over_R + (j + 0.5) * dby;
+    double v;
+    int nc;
+    backward_pixel(s, o, incl, dist_over_R, bx, by, omega_inf, Lc_cut_km, &v, &status[p], &nc);
+    image[p] = area_eV * Fa * v * EV2_W;
+    if (ncross) ncross[p] = nc;
   });
 }
 
