@@ -215,6 +215,48 @@ rt_status rt_bin_spectrum(const rt_star* star, int64_t n, const double* d_state,
                           double* d_sky, double* d_spec, double* d_out_of_range, void* stream);
 
 /*
+ * rt_trace_backward - image of the axion-induced radio power on a plane far
+ * from the star, by backward ray tracing (Sec. 2.1, Eq. BackPower; every
+ * resonance crossing counted, Sec. 5.1.3).  By Liouville's theorem the
+ * phase-space integral of the forward method equals, per solid angle of the
+ * observer, the integral over the plane of the frequency-integrated emission
+ * along each ray reaching it.  Pixel (i, j) of an ny x nx grid (row-major, j
+ * slow) is the square of side 2 b_max / nx by 2 b_max / ny centred on
+ * b = (-b_max + (i + 1/2) db_x, -b_max + (j + 1/2) db_y) on the plane
+ * through D o, o = (sin incl, 0, cos incl) the direction to the observer
+ * (rotation axis z, magnetic axis at the star's fixed phase psi_rad), plane
+ * axes e1 = (cos incl, 0, -sin incl) and e2 = (0, 1, 0).  Its ray leaves the
+ * plane along -o with the on-shell momentum at the line centre omega_inf =
+ * m_a sqrt(1 + v0^2), is integrated (FP64 DP5(4), opts->rtol/atol,
+ * max_steps) until it returns to its starting radius or is captured, and at
+ * every sign change of g = E_gamma - E_a = omega - sqrt(m_a^2 + |k|^2) along
+ * it (sampled at 16 points of each accepted step on the continuous
+ * extension, located by bisection) adds sqrt(A) Psi |dt/dl| / |dg/dl|.
+ * The pixel value is that sum x pixel area x int domega omega^2 f_a
+ * (omega_0 n_inf / (2 pi^{3/2} k0) for the Maxwellian, omega_0 n_inf /
+ * (4 pi k0) for the monochromatic distribution): dP/dOmega in W / sr.
+ * Crossings whose conversion length E / |dg/ds| (s: proper length) exceeds
+ * Lc_cut_km are dropped when Lc_cut_km > 0 (the IR cut, Sec. 4.4).
+ *   nx, ny        pixels per side (>= 1, nx * ny <= 2^31)
+ *   incl_rad      observer inclination from the rotation axis [rad]
+ *   dist_over_R   plane distance / R (> bmax_over_R * sqrt(2) + 1)
+ *   bmax_over_R   half-width of the plane / R (> 0)
+ *   d_image       out: ny x nx float64 [W / sr]
+ *   d_status      out: ny x nx final ray status (RT_RAY_ESCAPED normally)
+ *   d_ncross      out (may be NULL): ny x nx crossings counted (after the cut)
+ *   d_counters    in/out (may be NULL): RT_COUNTERS int64 accumulated:
+ *                 accepted steps, rejected steps, pixels finished, pixels
+ *                 escaped, -, -, crossings counted
+ *   opts          rtol, atol, r_capture_over_R, max_steps used (precision
+ *                 must be RT_PREC_FP64); r_out_over_R, lambda_max ignored
+ * Deterministic.  Calls sharing one handle must be serialised on one stream.
+ */
+rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double incl_rad,
+                            double dist_over_R, double bmax_over_R, double Lc_cut_km,
+                            double* d_image, uint8_t* d_status, int32_t* d_ncross,
+                            int64_t* d_counters, const rt_trace_opts* opts, void* stream);
+
+/*
  * Batches: many stars (different B0, P, misalignment, m_a, ...) traced in ONE
  * persistent launch whose global queue spans all of them, so the long rays of
  * one star overlap with the bulk of the others.  counts[s] rays of star s

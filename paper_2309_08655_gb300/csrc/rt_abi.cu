@@ -295,6 +295,59 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   return RT_OK;
 }
 
+rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double incl_rad,
+                            double dist_over_R, double bmax_over_R, double Lc_cut_km,
+                            double* d_image, uint8_t* d_status, int32_t* d_ncross,
+                            int64_t* d_counters, const rt_trace_opts* o, void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (o->precision != RT_PREC_FP64)
+    return fail(RT_EUNSUPPORTED, "rt_trace_backward supports RT_PREC_FP64 only");
+  if (nx < 1 || ny < 1) return fail(RT_EINVAL, "nx and ny must be >= 1");
+  if ((int64_t)nx * ny > ((int64_t)1 << 31)) return fail(RT_EINVAL, "nx * ny > 2^31");
+  if (!is_finite_val(incl_rad) || !is_finite_val(dist_over_R) || !is_finite_val(bmax_over_R) ||
+      !is_finite_val(Lc_cut_km))
+    return fail(RT_EINVAL, "non-finite argument");
+  if (!(bmax_over_R > 0)) return fail(RT_EINVAL, "bmax_over_R must be > 0");
+  if (!(dist_over_R > bmax_over_R * std::sqrt(2.0) + 1.0))
+    return fail(RT_EINVAL, "dist_over_R must exceed bmax_over_R * sqrt(2) + 1");
+  if (Lc_cut_km < 0) return fail(RT_EINVAL, "Lc_cut_km must be >= 0");
+  if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
+  if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
+  const rtk::StarDev& h = s->h;
+  // line centre and the analytic frequency integral of f_a (Eq. GaussianDist)
+  const double W = std::sqrt(1.0 + h.v0 * h.v0);
+  const double k0 = h.v0 * h.ma_eV, w0 = W * h.ma_eV;
+  const double Fa = (h.fa_model == rtk::FA_DELTA) ? w0 * h.n_inf / (4.0 * PI * k0)
+                                                  : w0 * h.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
+  const double dbx = 2.0 * bmax_over_R / nx * h.R_eV, dby = 2.0 * bmax_over_R / ny * h.R_eV;
+  rtk::BackLaunch b;
+  b.star = &h;
+  b.nx = nx;
+  b.ny = ny;
+  b.incl = incl_rad;
+  b.D = dist_over_R;
+  b.bmax = bmax_over_R;
+  b.W = W;
+  b.Lc_cut = Lc_cut_km / h.R_km;
+  b.img_scale = dbx * dby * Fa * h.w_unit;
+  b.rtol = o->rtol;
+  b.atol = o->atol;
+  b.r_capture = o->r_capture_over_R;
+  b.max_steps = o->max_steps;
+  b.image = d_image;
+  b.status = d_status;
+  b.ncross = d_ncross;
+  b.counters = d_counters;
+  b.queue = s->d_queue;
+  cudaError_t e = rtk::launch_backward(b, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward kernel");
+  return RT_OK;
+}
+
 rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
                           const double* d_weight, const uint8_t* d_status, int32_t nth,
                           int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,

@@ -25,8 +25,12 @@ struct TraceParams {
 };
 
 // Per-call counters (int64): accepted steps, rejected steps, rays finished,
-// rays escaped, rays promoted from FP32 to FP64, FP64 steps of promoted rays.
-enum { CTR_ACC = 0, CTR_REJ, CTR_RAYS, CTR_ESC, CTR_PROMOTED, CTR_PROMOTED_STEPS, CTR_COUNT = 8 };
+// rays escaped, rays promoted from FP32 to FP64, FP64 steps of promoted rays,
+// resonance crossings counted by the backward tracer.
+enum {
+  CTR_ACC = 0, CTR_REJ, CTR_RAYS, CTR_ESC, CTR_PROMOTED, CTR_PROMOTED_STEPS, CTR_CROSS,
+  CTR_COUNT = 8
+};
 
 struct SampleParams {
   StarDev s;
@@ -60,6 +64,26 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
                                cudaStream_t stream);
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
+
+// Backward image-plane tracing (one ray per pixel, ny x nx row-major).
+struct BackLaunch {
+  const StarDev* star;      // host descriptor (copied into the kernel parameters)
+  int nx, ny;
+  double incl;              // inclination of the line of sight from the rotation axis [rad]
+  double D;                 // plane distance / R
+  double bmax;              // half-width of the plane / R
+  double W;                 // omega_inf / m_a traced
+  double Lc_cut;            // conversion-length cut / R (0: none)
+  double img_scale;         // multiplies each pixel's crossing sum
+  double rtol, atol, r_capture;
+  int max_steps;
+  double* image;
+  uint8_t* status;
+  int32_t* ncross;
+  int64_t* counters;
+  unsigned long long* queue;
+};
+cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream);
 
 // Sets the thread-local message returned by rt_last_error().
 void set_last_error(const char* msg);

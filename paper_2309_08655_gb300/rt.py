@@ -71,6 +71,18 @@ def lib():
         L.rt_bin_spectrum.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                       ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.rt_trace_backward.restype = ctypes.c_int
+        L.rt_trace_backward.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp,
+                                        _vp, _vp, _vp, ctypes.POINTER(rt_trace_opts), _vp]
+        L.rt_bin_spectrum_noalloc.restype = ctypes.c_int
+        L.rt_bin_spectrum_noalloc.argtypes = [ctypes.POINTER(rt_star_params), ctypes.c_int64,
+                                              _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                              _vp, _vp, _vp, _vp, _vp]
+        L.rt_flops_per_step.restype = ctypes.c_int
+        L.rt_flops_per_step.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_double)]
         L.rt_count_status.restype = ctypes.c_int
         L.rt_count_status.argtypes = [ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
         L.rt_init_batch.restype = ctypes.c_int
@@ -211,6 +223,32 @@ def rt_bin_spectrum(star: Star, n, state, weight, status, nth, nph, nnu, nu_lo, 
         _ptr(out_of_range), _stream(stream)))
 
 
+def rt_trace_backward(star: Star, nx, ny, incl_rad, dist_over_R, bmax_over_R, image, status,
+                      ncross=None, counters=None, Lc_cut_km=0.0,
+                      opts: rt_trace_opts | None = None, stream=None) -> int:
+    if opts is None:
+        opts = make_opts()
+    return _check(lib().rt_trace_backward(
+        star.handle, int(nx), int(ny), float(incl_rad), float(dist_over_R), float(bmax_over_R),
+        float(Lc_cut_km), _ptr(image), _ptr(status), _ptr(ncross), _ptr(counters),
+        ctypes.byref(opts), _stream(stream)))
+
+
+def rt_bin_spectrum_noalloc(params: rt_star_params, n, state, weight, status, nth, nph, nnu,
+                            nu_lo, nu_hi, hist, sky=None, spec=None, out_of_range=None,
+                            stream=None) -> int:
+    return _check(lib().rt_bin_spectrum_noalloc(
+        ctypes.byref(params), int(n), _ptr(state), _ptr(weight), _ptr(status), int(nth),
+        int(nph), int(nnu), float(nu_lo), float(nu_hi), _ptr(hist), _ptr(sky), _ptr(spec),
+        _ptr(out_of_range), _stream(stream)))
+
+
+def rt_flops_per_step(dispersion: int, plasma: int) -> list[float]:
+    out = (ctypes.c_double * 4)()
+    _check(lib().rt_flops_per_step(int(dispersion), int(plasma), out))
+    return list(out)
+
+
 def rt_count_status(n, status, stream=None) -> tuple[int, list[int]]:
     counts = (ctypes.c_int64 * RAY_NSTATUS)()
     st = _check(lib().rt_count_status(int(n), _ptr(status), counts, _stream(stream)),
@@ -285,4 +323,5 @@ def rt_version() -> int:
 EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conversion_surface",
             "rt_trace_forward", "rt_bin_spectrum", "rt_count_status", "rt_last_error",
             "rt_version", "rt_init_batch", "rt_destroy_batch", "rt_sample_batch",
-            "rt_trace_batch", "rt_bin_batch"]
+            "rt_trace_batch", "rt_bin_batch", "rt_trace_backward", "rt_bin_spectrum_noalloc",
+            "rt_flops_per_step"]

@@ -1,0 +1,156 @@
+"""Parity of the CUDA backward image-plane tracer (Sec. 2.1, Eq. BackPower;
+every resonance crossing, Sec. 5.1.3) with the FP64 oracle, through the C ABI.
+
+Both sides trace one time-reversed ray per pixel centre from the same plane
+and sum sqrt(A) Psi |dt/dl| / |dg/dl| over the sign changes of g = E_gamma -
+E_a.  A pixel's value is a smooth function of the ray except where a crossing
+pair appears or disappears (a ray grazing the resonance): there two equally
+valid FP64 evaluations disagree.  The well-conditioned set is therefore the
+pixels on which the oracle's strict build and its FMA-contracted build agree
+in status and crossing count and to 1e-10 in value; on it the GPU must agree
+to 1e-8 relative (the factor 100 between the two bounds is the one the
+forward end-point tests use).  The image total is compared with a bound of
+ten times the strict-contracted spread of the total.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2309_08655_gb300 import rt  # noqa: E402
+
+from . import gpu_util as G  # noqa: E402
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2309_08655_gb300.build import build
+    build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _star(dispersion, theta_m=0.5, psi=0.4, m_a_eV=1e-5, fa_model=0):
+    """B0 = 1e14 G, P = 1 s, M = 1.4 Msun, R = 10 km; with m_a = 1e-5 eV the
+    conversion surface lies within 2 R (a plane 4 R wide sees all of it)."""
+    return dict(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=theta_m, psi=psi,
+                m_a_eV=m_a_eV, g_GeVinv=1e-12, rho_GeV_cm3=0.45, v0_kms=200.0,
+                dispersion=dispersion, resonance=0, fa_model=fa_model, weight_mode=0,
+                prop_metric=0, phase_mode=0, plasma=0, plasma_a=0.0)
+
+
+def gpu_backward(kw, nx, ny, incl, D, bmax, Lc_cut_km=0.0, rtol=RTOL):
+    star = rt.Star(rt.make_params(**kw))
+    img = torch.full((ny, nx), float("nan"), dtype=torch.float64, device=G.dev())
+    st = torch.full((ny, nx), 255, dtype=torch.uint8, device=G.dev())
+    nc = torch.full((ny, nx), -1, dtype=torch.int32, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img, st, nc, ctr, Lc_cut_km=Lc_cut_km,
+                         opts=rt.make_opts(rtol=rtol))
+    torch.cuda.synchronize()
+    return img.cpu().numpy(), st.cpu().numpy(), nc.cpu().numpy(), ctr.cpu().numpy()
+
+
+def oracle_backward(oracle, kw, nx, ny, incl, D, bmax, Lc_cut_km=0.0, rtol=RTOL):
+    sv = oracle.star_vector(**kw)
+    o = oracle.trace_opts(rtol=rtol)
+    a = oracle.trace_backward(sv, o, nx, ny, incl, D, bmax, Lc_cut_km)
+    b = oracle.trace_backward(sv, o, nx, ny, incl, D, bmax, Lc_cut_km, variant="contracted")
+    return a, b
+
+
+def _compare(a, b, g, min_good=0.9):
+    (ia, sa, na), (ib, sb, nb) = a, b
+    ig, sg, ng, ctr = g
+    scale = np.maximum(np.abs(ia), 1e-300)
+    spread = np.abs(ia - ib) / scale
+    good = (sa == sb) & (na == nb) & (spread <= 1e-10)
+    lit = na > 0
+    if lit.any():
+        assert good[lit].mean() >= min_good, good[lit].mean()
+    assert np.array_equal(sg[good], sa[good])
+    assert np.array_equal(ng[good], na[good])
+    rel = np.abs(ig - ia) / scale
+    assert np.all(np.isfinite(ig))
+    worst = rel[good].max() if good.any() else 0.0
+    assert worst <= 1e-8, worst
+    tot_spread = abs(ia.sum() - ib.sum())
+    assert abs(ig.sum() - ia.sum()) <= 10.0 * tot_spread + 1e-9 * abs(ia.sum()), (
+        ig.sum(), ia.sum(), tot_spread)
+    assert int(ctr[2]) == ia.size                       # every pixel finished
+    assert int(ctr[6]) == int(ng.sum())                 # crossings counted
+    return good
+
+
+@pytest.mark.parametrize("dispersion", [0, 1])
+def test_backward_parity_misaligned(oracle, dispersion):
+    kw = _star(dispersion)
+    args = (24, 20, 1.0, 1e4, 2.0)       # ragged: nx != ny, neither a warp multiple
+    a, b = oracle_backward(oracle, kw, *args)
+    g = gpu_backward(kw, *args)
+    _compare(a, b, g)
+    # the plane sees the emission; a ray leaves the resonance as often as it
+    # enters it (the plasma reflects it before it reaches the star)
+    assert (a[2] > 0).mean() > 0.2
+    assert a[0].sum() > 0
+    assert np.all(g[2] % 2 == 0)
+
+
+def test_backward_parity_aligned_pole_on(oracle):
+    """Aligned rotator seen from the rotation axis: the image is symmetric
+    under the reflection of the plane's e2 axis (y -> -y) and, with an even
+    grid, under b -> -b."""
+    kw = _star(0, theta_m=0.0, psi=0.0)
+    args = (16, 16, 0.0, 1e4, 2.0)
+    a, b = oracle_backward(oracle, kw, *args)
+    g = gpu_backward(kw, *args)
+    good = _compare(a, b, g)
+    img = g[0]
+    sym = good & good[::-1, ::-1]
+    assert np.allclose(img[sym], img[::-1, ::-1][sym], rtol=1e-8, atol=0)
+
+
+def test_backward_conversion_length_cut(oracle):
+    kw = _star(0)
+    args = (16, 12, 0.7, 1e4, 2.0)
+    full = gpu_backward(kw, *args)
+    a, b = oracle_backward(oracle, kw, *args, Lc_cut_km=1.0)
+    g = gpu_backward(kw, *args, Lc_cut_km=1.0)
+    _compare(a, b, g)
+    # the cut only removes crossings
+    assert np.all(g[2] <= full[2])
+    assert g[0].sum() < full[0].sum()
+
+
+def test_backward_single_pixel_and_empty_ray(oracle):
+    """One pixel; and a pixel whose ray never meets the conversion surface
+    (b far outside it) contributes exactly zero."""
+    kw = _star(1)
+    a, b = oracle_backward(oracle, kw, 1, 1, 0.3, 1e4, 0.5)
+    g = gpu_backward(kw, 1, 1, 0.3, 1e4, 0.5)
+    assert g[1][0, 0] == a[1][0, 0]
+    assert a[2][0, 0] > 0
+    if a[2][0, 0] == b[2][0, 0] and abs(a[0][0, 0] - b[0][0, 0]) <= 1e-10 * abs(a[0][0, 0]):
+        assert abs(g[0][0, 0] - a[0][0, 0]) <= 1e-8 * abs(a[0][0, 0])
+    # a 2 x 1 plane 20 R wide: both pixel centres at |b| = 5 R miss the surface
+    g2 = gpu_backward(kw, 2, 1, 0.3, 1e4, 10.0)
+    assert np.all(g2[0] == 0.0) and np.all(g2[2] == 0)
+    assert np.all(g2[1] == rt.RAY_ESCAPED)
+
+
+def test_backward_rejects_bad_arguments():
+    kw = _star(0)
+    star = rt.Star(rt.make_params(**kw))
+    img = torch.zeros((4, 4), dtype=torch.float64, device=G.dev())
+    st = torch.zeros((4, 4), dtype=torch.uint8, device=G.dev())
+    with pytest.raises(rt.RtError):
+        rt.rt_trace_backward(star, 4, 4, 0.3, 5.0, 6.0, img, st)        # plane inside the box
+    with pytest.raises(rt.RtError):
+        rt.rt_trace_backward(star, 4, 4, 0.3, 1e4, 6.0, img, st,
+                             opts=rt.make_opts(precision=rt.PREC_MIXED, rtol=1e-8))
+    with pytest.raises(rt.RtError):
+        rt.rt_trace_backward(star, 4, 4, math.nan, 1e4, 6.0, img, st)
