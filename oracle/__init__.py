@@ -43,7 +43,7 @@ STAR_DEFAULTS = dict(
     fa_model=0, weight_mode=0, prop_metric=0, phase_mode=0, plasma=0, plasma_a=0.0,
 )
 DISP_ANISO, DISP_ISO = 0, 1
-PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z = 0, 1, 2, 3
+PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL = 0, 1, 2, 3, 4
 RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT = 0, 1, 2, 3
 RAY_MAXSTEPS, RAY_NAN, RAY_STIFF, RAY_LAMBDA_END = 4, 5, 6, 7
 
@@ -139,6 +139,10 @@ def lib():
         L.or_trace_backward.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                         u8p, ip, ctypes.c_int]
+        L.or_backward_points.restype = None
+        L.or_backward_points.argtypes = [dp, dp, ctypes.c_long, dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, dp, u8p, ip,
+                                         ctypes.c_int]
         L.or_dp5_tableau.restype = None
         L.or_dp5_tableau.argtypes = [dp, dp, dp, dp, dp, dp]
         L.or_dp5_linear.restype = ctypes.c_long
@@ -313,3 +317,17 @@ def trace_backward(star, opts, nx, ny, incl, dist_over_R=1e4, bmax_over_R=50.0, 
                             float(dist_over_R), float(bmax_over_R), float(Lc_cut_km), _dp(img),
                             _u8(st), _ip(nc), nthreads or default_threads())
     return img, st, nc
+
+
+def backward_points(star, opts, b, incl, dist_over_R=1e4, Lc_cut_km=0.0, nthreads=None):
+    """Backward integrand at plane points b (n, 2) in units of R: dP/dOmega per
+    unit plane area [W / sr / R^2]; returns (value, status, ncross)."""
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 2)
+    n = b.shape[0]
+    v = np.zeros(n)
+    st = np.zeros(n, dtype=np.uint8)
+    nc = np.zeros(n, dtype=np.int32)
+    lib().or_backward_points(_dp(star), _dp(opts), n, _dp(b), float(incl), float(dist_over_R),
+                             float(Lc_cut_km), _dp(v), _u8(st), _ip(nc),
+                             nthreads or default_threads())
+    return v, st, nc

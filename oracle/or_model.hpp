@@ -34,7 +34,7 @@ constexpr double GM_SUN_KM = 1.4766250;           // G M_sun / c^2 [km], IAU 201
 
 // Model switches (test models exist so that closed forms can pin the tracer).
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
-enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3 };
+enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4 };
 enum { METRIC_FULL = 0, METRIC_FLAT = 1 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
@@ -125,6 +125,11 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma 
     case PLASMA_VACUUM: return T(0.0);
     case PLASMA_HOMOG: return T(s.plasma_a);
     case PLASMA_LINEAR_Z: return s.plasma_a * x[2];
+    case PLASMA_RADIAL: {
+      // spherical test profile a (R / r)^3
+      T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+      return s.plasma_a / (r2 * sqrt(r2));
+    }
     default: break;
   }
   // Goldreich-Julian: n_e = 2 |Omega . B| / e (Eq. GJDensity, charge sign

@@ -274,6 +274,9 @@ struct StepHook {
   virtual ~StepHook() {}
 };
 
+// Largest displacement of one step, as a fraction of the distance to the centre.
+constexpr double STEP_REACH = 0.5;
+
 static int trace_ray(const Star& s, const double m[3], double omega_inf, double y[6],
                      const TraceOpts& o, long* nacc_out, long* nrej_out, double* lam_out,
                      StepHook* hook = nullptr) {
@@ -293,6 +296,13 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
   double K[7][6], ynew[6], err[6];
   while (true) {
     if (nacc >= o.max_steps || nacc + nrej >= 4 * o.max_steps) { status = RAY_MAXSTEPS; break; }
+    // A step may move the ray by at most half its distance from the centre:
+    // far from the star the medium is nearly uniform and the error estimate
+    // alone would let one step carry the ray across the star and its plasma,
+    // which no stage of that step samples.
+    const double v2 = f0[0] * f0[0] + f0[1] * f0[1] + f0[2] * f0[2];
+    const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    if (h * h * v2 > STEP_REACH * STEP_REACH * r2) h = STEP_REACH * std::sqrt(r2 / v2);
     bool clipped = false;
     if (o.lambda_max > 0.0 && lam + h >= o.lambda_max) { h = o.lambda_max - lam; clipped = true; }
     dp5_step(f, y, f0, h, ynew, err, K);
@@ -655,6 +665,17 @@ void or_trace_forward(const double* sp, const double* topt, long n, double* stat
   });
 }
 
+// The frequency-integrated axion phase-space density at the line centre,
+// int domega omega^2 f_a [eV^3], and the traced omega_inf / m_a.
+static double backward_fa(const Star& s, double* omega_inf) {
+  using units::PI;
+  const double v0 = s.v0;
+  *omega_inf = std::sqrt(1.0 + v0 * v0);                       // line centre / m_a
+  const double k0 = v0 * s.ma_eV, w0 = *omega_inf * s.ma_eV;   // [eV]
+  return (s.fa_model == FA_DELTA) ? w0 * s.n_inf / (4.0 * PI * k0)
+                                  : w0 * s.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
+}
+
 // Backward image: ny x nx pixels (row-major, y index slow), value = the pixel's
 // contribution to dP/dOmega [W / sr] (frequency integrated over the line),
 // plus status and the number of crossings counted per pixel.  The star's
@@ -662,14 +683,10 @@ void or_trace_forward(const double* sp, const double* topt, long n, double* stat
 void or_trace_backward(const double* sp, const double* topt, int nx, int ny, double incl,
                        double dist_over_R, double bmax_over_R, double Lc_cut_km, double* image,
                        unsigned char* status, int* ncross, int nthreads) {
-  using units::PI;
   Star s = make_star(sp);
   TraceOpts o = make_opts(topt);
-  const double v0 = s.v0;
-  const double omega_inf = std::sqrt(1.0 + v0 * v0);          // line centre / m_a
-  const double k0 = v0 * s.ma_eV, w0 = omega_inf * s.ma_eV;   // [eV]
-  const double Fa = (s.fa_model == FA_DELTA) ? w0 * s.n_inf / (4.0 * PI * k0)
-                                             : w0 * s.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
+  double omega_inf;
+  const double Fa = backward_fa(s, &omega_inf);
   const double dbx = 2.0 * bmax_over_R / nx, dby = 2.0 * bmax_over_R / ny;   // units of R
   const double area_eV = (dbx * s.R_inv_eV) * (dby * s.R_inv_eV);          // [eV^-2]
   const double EV2_W = units::EV_J / units::HBAR_EV_S;
@@ -682,6 +699,27 @@ void or_trace_backward(const double* sp, const double* topt, int nx, int ny, dou
     backward_pixel(s, o, incl, dist_over_R, bx, by, omega_inf, Lc_cut_km, &v, &status[p], &nc);
     image[p] = area_eV * Fa * v * EV2_W;
     if (ncross) ncross[p] = nc;
+  });
+}
+
+// The backward integrand at arbitrary plane points (bx, by) = b[2i], b[2i+1]
+// (units of R): dP/dOmega per unit plane area, [W / sr / R^2], so that a
+// quadrature over the plane in units of R gives dP/dOmega.
+void or_backward_points(const double* sp, const double* topt, long n, const double* b,
+                        double incl, double dist_over_R, double Lc_cut_km, double* value,
+                        unsigned char* status, int* ncross, int nthreads) {
+  Star s = make_star(sp);
+  TraceOpts o = make_opts(topt);
+  double omega_inf;
+  const double Fa = backward_fa(s, &omega_inf);
+  const double unit = s.R_inv_eV * s.R_inv_eV * Fa * units::EV_J / units::HBAR_EV_S;
+  parallel_for(n, nthreads, [&](long i) {
+    double v;
+    int nc;
+    backward_pixel(s, o, incl, dist_over_R, b[2 * i], b[2 * i + 1], omega_inf, Lc_cut_km, &v,
+                   &status[i], &nc);
+    value[i] = unit * v;
+    if (ncross) ncross[i] = nc;
   });
 }
 
