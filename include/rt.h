@@ -71,7 +71,10 @@ enum { RT_FA_MAXWELL = 0, RT_FA_DELTA = 1 };
 enum { RT_WEIGHT_PAG = 0 };
 enum { RT_METRIC_FULL = 0, RT_METRIC_FLAT = 1 };
 enum { RT_PHASE_FIXED = 0, RT_PHASE_UNIFORM = 1 };
-enum { RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3 };
+enum {
+  RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3,
+  RT_PLASMA_RADIAL = 4
+};
 enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
 
 /*
@@ -93,7 +96,8 @@ enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
  *   prop_metric    RT_METRIC_FULL, or RT_METRIC_FLAT (M = 0 in propagation only)
  *   phase_mode     RT_PHASE_FIXED or RT_PHASE_UNIFORM (psi = 2 pi u5 per sample)
  *   plasma         RT_PLASMA_GJ; the others are analytic test media
- *   plasma_a       omega_p^2 / m_a^2 (HOMOG) or its gradient d/d(z/R) (LINEAR_Z)
+ *   plasma_a       omega_p^2 / m_a^2 (HOMOG), its gradient d/d(z/R) (LINEAR_Z), or
+ *                  its value at r = R of the spherical profile a (R/r)^3 (RADIAL)
  */
 typedef struct {
   double M_sun, R_km, B0_G, P_s, theta_m_rad, psi_rad, m_a_eV, g_agg_GeVinv, rho_dm_GeV_cm3,

@@ -115,7 +115,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
   if (p->phase_mode != RT_PHASE_FIXED && p->phase_mode != RT_PHASE_UNIFORM)
     return fail(RT_EUNSUPPORTED, "unknown phase_mode %d", p->phase_mode);
-  if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_LINEAR_Z)
+  if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_RADIAL)
     return fail(RT_EUNSUPPORTED, "unknown plasma %d", p->plasma);
 
   rt_star* s = new (std::nothrow) rt_star;
@@ -156,6 +156,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     case RT_PLASMA_GJ: s->wp2_surface_max = h.cp * 0.5 * (3.0 + std::fabs(h.cos_tm)); break;
     case RT_PLASMA_HOMOG: s->wp2_surface_max = p->plasma_a; break;
     case RT_PLASMA_LINEAR_Z: s->wp2_surface_max = std::fabs(p->plasma_a) * 1e30; break;
+    case RT_PLASMA_RADIAL: s->wp2_surface_max = p->plasma_a; break;
     default: s->wp2_surface_max = 0.0; break;
   }
   s->empty = !(s->wp2_surface_max > 1.0);

@@ -42,7 +42,7 @@ struct StarDev {
 };
 
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
-enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3 };
+enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 enum {
@@ -151,6 +151,12 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
   } else if (c.plasma == PLASMA_LINEAR_Z) {
     P = c.pa * x2;
     dP2 = c.pa;
+  } else if (c.plasma == PLASMA_RADIAL) {
+    P = c.pa * ir2 * ir;
+    const T m3 = T(-3) * P * ir;
+    dP0 = m3 * n0;
+    dP1 = m3 * n1;
+    dP2 = m3 * n2;
   }
   if (c.disp == DISP_ISO) {
     gx0 += dP0;
@@ -218,6 +224,8 @@ __device__ __forceinline__ T ham_value(const RayConst<T>& c, const T* x, const T
     P = c.pa;
   } else if (c.plasma == PLASMA_LINEAR_Z) {
     P = c.pa * x[2];
+  } else if (c.plasma == PLASMA_RADIAL) {
+    P = c.pa * ir * ir * ir;
   }
   if (c.disp == DISP_ISO) return H + P;
   const T ib = rt_rsqrt(T(3) * mu * mu + T(1));
@@ -226,6 +234,12 @@ __device__ __forceinline__ T ham_value(const RayConst<T>& c, const T* x, const T
   const T Kp = (T(3) * mu * kr - km + T(2) * mu * kr * (sA - T(1))) * ib;
   return H + P - P * A * Kp * Kp * c.iW2;
 }
+
+// Largest displacement of one integration step, as a fraction of the distance
+// to the centre: far from the star the medium is nearly uniform and the
+// embedded error estimate alone would let one step carry a ray across the star
+// and its plasma, which no stage of that step samples.
+constexpr double STEP_REACH = 0.5;
 
 // Dormand-Prince 5(4) coefficients (Dormand & Prince 1980) and the
 // continuous extension of Hairer, Norsett & Wanner (Sec. II.6).

@@ -42,7 +42,7 @@ inline Cnt rt_rcp(Cnt v) { g_t.flops += 1; g_t.special += 1; return Cnt(1.0 / v.
 
 extern "C" rt_status rt_flops_per_step(int32_t dispersion, int32_t plasma, double* out4) {
   if (!out4) return RT_EINVAL;
-  if (dispersion < 0 || dispersion > 1 || plasma < 0 || plasma > 3) return RT_EINVAL;
+  if (dispersion < 0 || dispersion > 1 || plasma < 0 || plasma > 4) return RT_EINVAL;
   rtk::RayConst<Cnt> c;
   c.rs = 0.4; c.cp = 4000.0; c.pa = 0.1; c.W2 = 1.0; c.iW2 = 1.0;
   c.m0 = 0.3; c.m1 = 0.1; c.m2 = 0.9; c.sig = 1.0; c.disp = dispersion; c.plasma = plasma;

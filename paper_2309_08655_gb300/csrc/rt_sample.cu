@@ -81,6 +81,12 @@ __device__ __forceinline__ void line_plasma(const Line& L, double r, double& P, 
     }
     case PLASMA_HOMOG: P = L.pa; dP = 0.0; break;
     case PLASMA_LINEAR_Z: P = L.pa * r * L.nz; dP = L.pa * L.nz; break;
+    case PLASMA_RADIAL: {
+      const double ir = 1.0 / r;
+      P = L.pa * ir * ir * ir;
+      dP = -3.0 * P * ir;
+      break;
+    }
     default: P = 0.0; dP = 0.0; break;
   }
 }

@@ -155,6 +155,12 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
   if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
   bool clipped = false;
   double h = L.h;
+  {
+    // displacement of one step at most STEP_REACH x the distance to the centre
+    const double v2 = L.f0[0] * L.f0[0] + L.f0[1] * L.f0[1] + L.f0[2] * L.f0[2];
+    const double r2 = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
+    if (h * h * v2 > STEP_REACH * STEP_REACH * r2) h = STEP_REACH * sqrt(r2 / v2);
+  }
   if (p.lambda_max > 0.0 && L.lam + h >= p.lambda_max) {
     h = p.lambda_max - L.lam;
     clipped = true;
@@ -451,6 +457,8 @@ struct CrossingHook {
       P = c.pa;
     } else if (c.plasma == PLASMA_LINEAR_Z) {
       P = c.pa * y[2];
+    } else if (c.plasma == PLASMA_RADIAL) {
+      P = c.pa * ir * ir * ir;
     }
     const double bb = 3.0 * mu * mu + 1.0;
     const double km = y[3] * c.m0 + y[4] * c.m1 + y[5] * c.m2;
@@ -576,6 +584,7 @@ __device__ void load_pixel(const BackParams& bp, int64_t p, Lane& L) {
   if (L.c.plasma == PLASMA_GJ) P = L.c.cp * ir * ir * ir * fabs(3.0 * n2 * mu - L.c.m2);
   else if (L.c.plasma == PLASMA_HOMOG) P = L.c.pa;
   else if (L.c.plasma == PLASMA_LINEAR_Z) P = L.c.pa * L.y[2];
+  else if (L.c.plasma == PLASMA_RADIAL) P = L.c.pa * ir * ir * ir;
   // H(s) = -W2/A + s^2 + P - P A (s Kd)^2 / W2, Kd = d . bhat (orthonormal)
   const double bn = rsqrt(3.0 * mu * mu + 1.0);
   const double Kd = (3.0 * mu * dn - (-(L.c.m0 * o[0] + L.c.m2 * o[2]))) * bn;

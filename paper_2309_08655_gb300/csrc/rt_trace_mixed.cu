@@ -192,11 +192,23 @@ __device__ __forceinline__ void dense_x(const LaneM& L, float h, float th, const
 // the FP64 pass, else the final status.
 __device__ int advance_m(const TraceParams& p, LaneM& L) {
   if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
-  const float h = L.h;
   const float rtol = (float)p.rtol, atol = (float)p.atol;
   float yf[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) yf[i] = (float)L.y[i];
+  float h = L.h;
+  {
+    // displacement of one step at most STEP_REACH x the distance to the centre
+    float v2 = 0.0f, r2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float vi = 2.0f * yf[3 + i] + L.f0[i];
+      v2 += vi * vi;
+      r2 += yf[i] * yf[i];
+    }
+    if (h * h * v2 > (float)(STEP_REACH * STEP_REACH) * r2)
+      h = (float)STEP_REACH * sqrtf(r2 / v2);
+  }
   // stage derivatives: R (position, small part) and K (momentum), j = 1..7
   float R1[3], R2[3], R3[3], R4[3], R5[3], R6[3], R7[3];
   float K1[3], K2[3], K3[3], K4[3], K5[3], K6[3], K7[3];

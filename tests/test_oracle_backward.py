@@ -1,0 +1,146 @@
+"""Pins of the oracle's backward image-plane estimator (Sec. 2.1, Eq.
+BackPower; every crossing, Sec. 5.1.3) against things the mathematics fixes:
+
+* Liouville's theorem: the backward dP/dOmega integrated over the observer's
+  sphere equals the total power of the forward Monte-Carlo (escaped rays),
+  two estimators that share only the Hamiltonian and Psi (pin 9 of the test
+  plan, here to the Monte-Carlo error).  The test medium is the spherical
+  profile omega_p^2 = a m_a^2 (R/r)^3 with isotropic dispersion and an aligned
+  dipole: ray geometry is spherically symmetric (Psi alone depends on the
+  direction), so dP/dOmega is smooth in the inclination and the image is a
+  disc whose rim -- where the two crossings of a grazing ray merge and
+  1/|dg/dl| diverges like (b_rim - b)^-1/2 -- is handled exactly by the
+  substitution b = b_rim (1 - s^2) before Gauss-Legendre quadrature.
+* A closed form: flat space (M = 0), radial ray through the centre.  The ray
+  slows to |k| = v0 m_a at omega_p = m_a (r_c = a^(1/3) R), reflects just
+  inside and leaves on the same line, crossing twice at r_c with |k_r| = v0;
+  there dg/dl = 3 |k_r| / (W r_c), dt/dl = 2 W and Psi follows from the
+  dipole at r_c o with k parallel to n.
+* Consistency of the pixel grid with the point evaluator, the mirror symmetry
+  of an aligned rotator, and the conversion-length cut only removing
+  crossings.
+"""
+import math
+
+import numpy as np
+import pytest
+
+C_KMS = 299792.458
+HBARC_EV_KM = 1.973269804e-10
+HBAR_EV_S = 6.582119569e-16
+EV_J = 1.602176634e-19
+
+
+def _radial_star(oracle, **kw):
+    base = dict(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5, dispersion=1,
+                fa_model=1, plasma=oracle.PLASMA_RADIAL, plasma_a=8.0)
+    base.update(kw)
+    return oracle.star_vector(**base)
+
+
+def _rim(oracle, sv, opts, incl, phi):
+    """Largest b on the ray (b cos phi, b sin phi) that still crosses."""
+    lo, hi = 0.0, 6.0
+    for _ in range(44):
+        mid = 0.5 * (lo + hi)
+        _, _, nc = oracle.backward_points(sv, opts, [[mid * math.cos(phi), mid * math.sin(phi)]],
+                                          incl)
+        if nc[0] > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_liouville_forward_equals_backward_total(oracle):
+    sv = _radial_star(oracle)
+    opts = oracle.trace_opts(rtol=1e-10)
+    # forward: total power of the escaped rays
+    n = 60000
+    u = np.random.default_rng(11).random((6, n))
+    st, w, s = oracle.sample(sv, u)
+    oracle.trace_forward(sv, opts, st, s)
+    esc = s == oracle.RAY_ESCAPED
+    P_fwd = w[esc].sum()
+    sigma = (w * esc).std() * math.sqrt(n)
+    assert esc.mean() > 0.99
+    # backward: int dOmega dP/dOmega, axisymmetric in the observer azimuth
+    xs, ws = np.polynomial.legendre.leggauss(20)
+    xs, ws = 0.5 * (xs + 1.0), 0.5 * ws
+    ci, wi = np.polynomial.legendre.leggauss(8)
+    nphi = 12
+    phis = (np.arange(nphi) + 0.5) * 2.0 * math.pi / nphi
+    rim = _rim(oracle, sv, opts, 1.0, 0.0)
+    # spherically symmetric geometry: the same rim in every direction (to the
+    # resolution of the crossing search, which misses a pair of crossings
+    # closer together than a sixteenth of a step)
+    assert abs(_rim(oracle, sv, opts, 0.3, 2.0) - rim) < 1e-6
+    total = 0.0
+    for c, wc in zip(ci, wi):
+        pts, wts = [], []
+        for p in phis:
+            b = rim * (1.0 - xs ** 2)
+            pts.append(np.stack([b * math.cos(p), b * math.sin(p)], 1))
+            wts.append(b * 2.0 * rim * xs * ws * (2.0 * math.pi / nphi))
+        v, _, nc = oracle.backward_points(sv, opts, np.concatenate(pts), math.acos(c))
+        assert np.all(nc == 2)
+        total += wc * np.sum(v * np.concatenate(wts))
+    P_back = 2.0 * math.pi * total
+    assert abs(P_back / P_fwd - 1.0) < 5.0 * sigma / P_fwd + 2e-3, (P_back, P_fwd, sigma)
+
+
+@pytest.mark.parametrize("incl", [0.5, 1.2])
+def test_flat_radial_ray_closed_form(oracle, incl):
+    v0_kms, theta_m = 3000.0, 0.3
+    sv = _radial_star(oracle, M_sun=0.0, v0_kms=v0_kms, theta_m=theta_m)
+    v, st, nc = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10), [[0.0, 0.0]], incl)
+    assert st[0] == oracle.RAY_ESCAPED and nc[0] == 2
+    v0 = v0_kms / C_KMS
+    W = math.sqrt(1.0 + v0 * v0)
+    r_c, m_a, R_km = 2.0, 1e-5, 10.0
+    R_eV = R_km / HBARC_EV_KM
+    hbarc_cm = HBARC_EV_KM * 1e5
+    B0 = 1e14 * math.sqrt((1e-7 / EV_J) * hbarc_cm ** 3 / (4.0 * math.pi))   # [eV^2]
+    g = 1e-12 * 1e-9
+    n_inf = 0.45 * 1e9 * hbarc_cm ** 3 / m_a
+    mu = math.sin(theta_m) * math.sin(incl) + math.cos(theta_m) * math.cos(incl)   # m . o
+    # |B|^2 sin^2(k, B) for k along n: (B0/2)^2 r^-6 (1 - mu^2)
+    Psi = 0.5 * math.pi * g * g * (0.5 * B0 / r_c ** 3) ** 2 * (1.0 - mu * mu) * (W * m_a)
+    dt_over_dg = (2.0 * W) / (3.0 * v0 / (W * r_c)) * R_eV / m_a          # [eV^-2]
+    Fa = W * m_a * n_inf / (4.0 * math.pi * v0 * m_a)                       # delta f_a
+    expect = 2.0 * Psi * dt_over_dg * Fa * R_eV ** 2 * EV_J / HBAR_EV_S    # [W / sr / R^2]
+    assert abs(v[0] / expect - 1.0) < 1e-8, (v[0], expect)
+
+
+def test_pixel_grid_equals_points(oracle):
+    sv = _radial_star(oracle, dispersion=0, theta_m=0.4, psi=0.3)
+    opts = oracle.trace_opts(rtol=1e-10)
+    nx, ny, bmax, incl = 7, 5, 2.0, 0.8
+    img, st, nc = oracle.trace_backward(sv, opts, nx, ny, incl, 1e4, bmax)
+    dbx, dby = 2 * bmax / nx, 2 * bmax / ny
+    bx = -bmax + (np.arange(nx) + 0.5) * dbx
+    by = -bmax + (np.arange(ny) + 0.5) * dby
+    B = np.stack(np.meshgrid(bx, by), -1).reshape(-1, 2)
+    v, st2, nc2 = oracle.backward_points(sv, opts, B, incl)
+    np.testing.assert_array_equal(st.ravel(), st2)
+    np.testing.assert_array_equal(nc.ravel(), nc2)
+    np.testing.assert_allclose(img.ravel(), v * dbx * dby, rtol=1e-14, atol=0)
+    assert (nc > 0).mean() > 0.3
+
+
+def test_aligned_image_mirror_symmetric_and_cut(oracle):
+    """Aligned Goldreich-Julian star: the configuration is symmetric under
+    y -> -y, and so is the image; a conversion-length cut only drops
+    crossings."""
+    from paper_2309_08655_gb300 import inputs as I
+    kw = I.star_config0()
+    kw.update(m_a_eV=1e-5)
+    sv = oracle.star_vector(**kw)
+    opts = oracle.trace_opts(rtol=1e-10)
+    img, st, nc = oracle.trace_backward(sv, opts, 12, 12, 0.9, 1e4, 2.0)
+    assert (nc > 0).any()
+    np.testing.assert_allclose(img, img[::-1, :], rtol=1e-9, atol=0)
+    np.testing.assert_array_equal(nc, nc[::-1, :])
+    img2, st2, nc2 = oracle.trace_backward(sv, opts, 12, 12, 0.9, 1e4, 2.0, Lc_cut_km=0.5)
+    assert np.all(nc2 <= nc) and np.all(img2 <= img * (1 + 1e-12))
+    assert nc2.sum() < nc.sum()
