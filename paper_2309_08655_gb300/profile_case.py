@@ -1,10 +1,15 @@
 """Small, self-contained forward case for kernel profiling (ncu) and quick timing.
 
     python -m paper_2309_08655_gb300.profile_case --precision fp64 --n 1024
+    python -m paper_2309_08655_gb300.profile_case --mode backward --n 65536
 
-Samples n rays of the aligned 200 km-surface star (seed 0), traces them once in
-the requested precision (one persistent trace launch, after one untimed warm-up
-launch on a copy) and bins them; prints the trace time and step counts.
+Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
+them once in the requested precision (one persistent trace launch, after one
+untimed warm-up launch on a copy) and bins them.  Backward: an image of about
+n pixels (square) of the same star at inclination 60 deg, plane at 1e4 R,
+impact parameters up to 50 R (one warm-up launch on an image of at most
+32 x 32 pixels first).
+Prints the trace time and step counts.
 """
 from __future__ import annotations
 
@@ -25,9 +30,12 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
+    ap.add_argument("--mode", choices=["forward", "backward"], default="forward")
     a = ap.parse_args()
     build()
     dev = torch.device("cuda:0")
+    if a.mode == "backward":
+        return backward(a, dev)
     if a.config == "config0":
         kw = I.star_config0()
     else:
@@ -58,6 +66,35 @@ def main():
                       "trace_ms": e0.elapsed_time(e1), "accepted": int(c[0]),
                       "rejected": int(c[1]), "rays": int(c[2]), "promoted": int(c[4]),
                       "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}))
+
+
+def backward(a, dev):
+    import math
+    kw = I.star_config0()
+    star = rt.Star(rt.make_params(**kw))
+    side = max(1, int(round(math.sqrt(a.n))))
+    rtol = a.rtol if a.rtol is not None else 1e-10
+    opts = rt.make_opts(rtol=rtol)
+    incl, D, bmax = math.radians(60.0), 1e4, 50.0
+    img = torch.empty((side, side), dtype=torch.float64, device=dev)
+    st = torch.empty((side, side), dtype=torch.uint8, device=dev)
+    nc = torch.empty((side, side), dtype=torch.int32, device=dev)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    w = min(side, 32)
+    rt.rt_trace_backward(star, w, w, incl, D, bmax, img, st, nc, ctr, opts=opts)     # warm-up
+    ctr.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    rt.rt_trace_backward(star, side, side, incl, D, bmax, img, st, nc, ctr, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    c = ctr.cpu().numpy()
+    print(json.dumps({"mode": "backward", "pixels": side * side, "rtol": rtol,
+                      "trace_ms": e0.elapsed_time(e1), "accepted": int(c[0]),
+                      "rejected": int(c[1]), "pixels_done": int(c[2]), "crossings": int(c[6]),
+                      "dP_dOmega": float(img.sum()),
+                      "statuses": np.bincount(st.cpu().numpy().ravel(), minlength=8).tolist()}))
 
 
 if __name__ == "__main__":

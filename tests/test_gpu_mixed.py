@@ -1,6 +1,17 @@
 """Mixed-precision tracing (FP32 stages, FP64 state, FP64 promotion) against
-the FP64 oracle: end points within 1e-6 relative on the well-conditioned set,
-binned flux within 1e-4 relative L1, statuses and promotion accounting."""
+the FP64 oracle: end points on the well-conditioned set, binned flux within
+1e-4 relative L1, statuses and promotion accounting.
+
+Conditioning.  Every FP32 stage evaluation carries a relative rounding error
+of a few eps32 = 6e-8 of its derivative, so a step's momentum increment is off
+by ~eps32 of itself and the end point by ~eps32 x (total variation of k along
+the ray) x kappa, where kappa is the ray's amplification of a perturbation.
+kappa is measured with the oracle: the largest relative end-point change over
+two random relative perturbations of the initial state of size 1e-9, divided
+by 1e-9.  On rays with kappa <= 10 the mixed end points must agree with the
+FP64 oracle (rtol 1e-10) to 1e-6 for 99 % of the rays and to 1e-5 for all
+(measured on GB300: p99 6e-7 / 7e-7, max 4e-6 / 3e-6 at rtol 1e-8).
+"""
 import numpy as np
 import pytest
 
@@ -22,11 +33,20 @@ def _built():
     assert torch.cuda.is_available()
 
 
+def _kappa(oracle, sv, st0, s0, ref, sref, eps=1e-9):
+    kap = np.zeros(st0.shape[1])
+    for seed in (1, 2):
+        p = G.perturbed(st0, eps, seed)
+        sp = s0.copy()
+        oracle.trace_forward(sv, oracle.trace_opts(rtol=1e-10), p, sp)
+        kap = np.maximum(kap, G.rel_state_diff(p, ref) / eps)
+        kap[sp != sref] = np.inf
+    return kap
+
+
 def _run(oracle, kw, u):
     sv = oracle.star_vector(**kw)
     st0, w0, s0 = oracle.sample(sv, u)
-    # FP32 stages perturb each step by ~1e-8 of its increment: the comparison at
-    # 1e-6 is defined on rays whose end point is insensitive to rounding
     ref, sref, good, spread = G.well_conditioned(oracle, sv, st0, s0, 1e-10)
     star = rt.Star(rt.make_params(**kw))
     st_d = torch.from_numpy(st0.copy()).cuda()
@@ -37,7 +57,7 @@ def _run(oracle, kw, u):
 
 
 @pytest.mark.parametrize("which", ["config0", "misaligned"])
-def test_mixed_endpoints_within_1e6(oracle, which):
+def test_mixed_endpoints_on_well_conditioned_rays(oracle, which):
     if which == "config0":
         kw = I.star_config0()
         u = I.sample_uniforms(0, 2048)
@@ -48,15 +68,13 @@ def test_mixed_endpoints_within_1e6(oracle, which):
     traced = s0 == oracle.RAY_READY
     assert not np.any(s_g == 8)            # no ray left in the internal promoted state
     assert (s_g[traced] == sref[traced]).mean() > 0.99
-    g = good & traced & (s_g == sref)
-    assert g.sum() > 0.05 * traced.sum()
+    kap = _kappa(oracle, sv, st0, s0, ref, sref)
+    g = (kap <= 10) & traced & (s_g == sref)
+    assert g.sum() > 0.6 * traced.sum()
     d = G.rel_state_diff(st_g[:, g], ref[:, g])
-    # FP32 stages leave an error floor ~ eps32 x (total variation of k): rays
-    # that reflect many times near the star accumulate more; the 1e-6 bar holds
-    # for 99 % of the well-conditioned rays, the worst stay below 1e-4
-    assert np.median(d) < 5e-7
+    assert np.median(d) < 2e-7
     assert np.percentile(d, 99) < 1e-6, np.sort(d)[-20:]
-    assert d.max() < 1e-4, np.sort(d)[-5:]
+    assert d.max() < 1e-5, np.sort(d)[-5:]
     assert ctr[2] == traced.sum()          # every ray finished exactly once
     assert ctr[4] <= traced.sum()
 
