@@ -1,19 +1,25 @@
-"""Benchmark of the forward hot path on the production-size workload.
+"""Benchmark of the hot path on the production-size workload.
 
 Workload (one "step"): 16 sub-batches x 65536 forward rays on a misaligned
 magnetar-like rotator (B0 = 1.6e14 G, P = 3.76 s, theta_m = 30 deg,
 M = 1.5 Msun, R = 11 km), axion masses log-uniform in [1e-6, 5e-3] eV (one per
 sub-batch, seed 1), rotation phase uniform per ray: conversion-surface
-sampling (FP64) -> Dormand-Prince 5(4) trace to r = 1000 R at rtol 1e-10 ->
-fixed-point binning into 64 x 32 x 128 (theta, phi, frequency) bins per
-sub-batch.  Inputs are synthetic (SplitMix64 uniforms) and resident in HBM
-when the timed region starts; the L2 is flushed (256 MiB write) before every
-timed step.
+sampling (FP64) -> Dormand-Prince 5(4) trace to r = 1000 R (FP64 at rtol
+1e-10, and mixed FP32/FP64 at rtol 1e-8) -> fixed-point binning into
+64 x 32 x 128 (theta, phi, frequency) bins per sub-batch.  Inputs are
+synthetic (SplitMix64 uniforms) and resident in HBM when the timed region
+starts; the L2 is flushed (256 MiB write) before every timed step.
 
-Reported: accepted ray-steps/s (value), rays/s, the roofline of the trace
-kernel (FP64 ALU), an end-to-end number through the C ABI with host buffers,
-and the oracle timed on the host cores.  ``--impl reference`` times the
-oracle alone (the CPU reference arm) on a bounded sample of the same workload.
+Reported: accepted ray-steps/s (value) of the fastest precision whose binned
+flux is within 1e-6 (relative L1) of the FP64 oracle run on the same
+uniforms, rays/s, the roofline of the trace kernel (FP64 or FP32 ALU), an
+end-to-end number through the C ABI with host buffers, the oracle timed on
+the host cores (cpu_baseline: the whole workload), and two further legs: the
+backward image plane (1024 x 1024 pixels at 60 deg, impact parameters to
+50 R, with oracle-checked pixels) and the adjoint gradient of a smoothed line
+flux (2^18 rays; adjoint/forward time ratio, checkpoint memory).
+``--impl reference`` times the oracle alone (the CPU reference arm) on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -55,6 +61,8 @@ def _args():
                          "workload, which also gives the flux error against the oracle)")
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the backward image-plane measurement")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint (gradient) measurement")
     return ap.parse_args()
 
 
@@ -359,6 +367,9 @@ def run_ours(args):
     back = None
     if not args.no_backward:
         back = _backward_leg(args, dev, stream, fl, rank)
+    adj = None
+    if not args.no_adjoint:
+        adj = _adjoint_leg(args, dev)
     if rank != 0:
         return
     H = res[head]
@@ -378,7 +389,8 @@ def run_ours(args):
         "fp64": res["fp64"], "mixed": res["mixed"],
         "mixed_vs_fp64_rays_per_s": res["mixed"]["rays_per_s"] / res["fp64"]["rays_per_s"],
         "backward": back,
-        "adjoint_forward_ratio": None,
+        "adjoint_forward_ratio": adj["adjoint_forward_ratio"] if adj else None,
+        "adjoint": adj,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
@@ -386,6 +398,55 @@ def run_ours(args):
         "clocks": clk,
     }
     print(json.dumps(line))
+
+
+def _adjoint_leg(args, dev):
+    """Differentiable trace: 2^18 forward rays on the misaligned magnetar-like
+    star at m_a = 1e-5 eV; the line flux toward inclination 1.1 rad smoothed
+    with a von Mises-Fisher kernel one theta-bin wide (kappa = (64/pi)^2) and
+    its gradient with respect to (m_a, B0, theta_m, M, R, inclination) by the
+    adjoint (rt_flux_gradient).  Times one forward (sample + trace + functional)
+    and one gradient after a warm-up of each on a smaller sample."""
+    import numpy as np
+    import torch
+
+    from paper_2309_08655_gb300 import flux
+    from paper_2309_08655_gb300 import inputs as I
+    from paper_2309_08655_gb300 import rt
+    kw = I.stars_config1()[0]
+    kw.update(m_a_eV=1e-5)
+    n = 1 << 18
+    kappa = (64.0 / math.pi) ** 2
+    p = torch.tensor([kw["m_a_eV"], kw["B0_G"], kw["theta_m"], kw["M_sun"], kw["R_km"], 1.1],
+                     dtype=torch.float64)
+    u = torch.from_numpy(I.sample_uniforms(4000, n)).to(dev)
+    grad = torch.empty(6, dtype=torch.float64, device=dev)
+    F2 = torch.empty(1, dtype=torch.float64, device=dev)
+    uw = u[:, :4096].contiguous()
+    Fw, nw, sw, iw, ow = flux.flux_forward(p, kw, uw, kappa)
+    rt.rt_flux_gradient(sw, 4096, uw, nw, iw, kappa, grad, F2, opts=ow)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F, nacc, star, incl, opts = flux.flux_forward(p, kw, u, kappa)
+    torch.cuda.synchronize()
+    t_f = time.perf_counter() - t0
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    t0 = time.perf_counter()
+    nbytes = rt.rt_flux_gradient(star, n, u, nacc, incl, kappa, grad, F2, counters=ctr,
+                                 opts=opts)
+    torch.cuda.synchronize()
+    t_g = time.perf_counter() - t0
+    g = grad.cpu().numpy()
+    c = ctr.cpu().numpy()
+    return {"workload": "adjoint_2^18_rays_ma1e-5_incl1.1_vmf_one_theta_bin",
+            "precision": "fp64", "rays": n, "F_W_per_sr": float(F.cpu()[0]),
+            "grad": dict(zip(flux.PARAM_NAMES, [float(x) for x in g])),
+            "t_forward_s": t_f, "t_gradient_s": t_g, "adjoint_forward_ratio": t_g / t_f,
+            "checkpoint_MiB": nbytes / 2 ** 20, "replayed_attempts": int(c[0]),
+            "rays_left_out": int(c[4]),
+            "fp32_vs_fp64_gradient_error": None,
+            "note": "the adjoint runs in FP64 only; timings include sampling, both "
+                    "replays and the dual-number Jacobian products"}
 
 
 def _backward_leg(args, dev, stream, fl, rank):

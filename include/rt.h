@@ -261,6 +261,57 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
                             int64_t* d_counters, const rt_trace_opts* opts, void* stream);
 
 /*
+ * Line-flux functional and its adjoint gradient.  The paper differentiates
+ * nothing; this is a service for fitting its model (a reading):
+ *   F = sum_i w_i K(khat_i . o),  K(mu) = C exp(kappa (mu - 1)),
+ *   C = kappa / (2 pi (1 - exp(-2 kappa)))  (von Mises-Fisher kernel, unit mass),
+ * over the ESCAPED rays i with weights w_i (Sec. 4.2, Eq. PowerCurved) and
+ * khat_i the static orthonormal-frame momentum direction at r = r_out
+ * (the direction rt_bin_spectrum bins, Sec. 2.2); o = (sin i, 0, cos i).
+ * F is in W/sr: the line flux toward o smoothed over ~1/sqrt(kappa) rad.
+ *
+ * rt_flux_value - F over already traced rays (state, weight and status as
+ *   rt_trace_forward leaves them).  d_F_ray: out, n per-ray terms; d_F: out,
+ *   their sum (fixed summation order: deterministic).
+ *
+ * rt_flux_gradient - dF/dp for p = (m_a [eV], B0 [G], theta_m [rad], M [Msun],
+ *   R [km], inclination [rad]) by reverse-mode differentiation of sampling and
+ *   the FP64 integrator, at the star's parameters, for the n samples drawn
+ *   from d_uniforms (RT_UNIFORM_ROWS x n, as rt_sample_conversion_surface)
+ *   and traced with opts (RT_PREC_FP64, lambda_max 0).  Each ray is
+ *   re-integrated with a checkpoint every 32 accepted steps (d_nacc, the
+ *   accepted steps per ray of the forward rt_trace_forward run with the same
+ *   opts, sizes the checkpoint store), then swept backwards segment by
+ *   segment, each segment re-integrated from its checkpoint: the discrete
+ *   adjoint of each Dormand-Prince step (Jacobian-vector products of the
+ *   analytic right-hand side by forward-mode dual numbers), the saltation
+ *   jump where the Goldreich-Julian branch switches on the null cone, and the
+ *   escape point's implicit dependence on the parameters.  The derivatives
+ *   of the initial state and the weight come from the sampling code in dual
+ *   numbers (the resonance root by the implicit function theorem).  Status,
+ *   escape and the number of steps are held fixed (the gradient of the
+ *   discrete scheme at frozen decisions).
+ *     d_grad     out: 6 float64, dF/dp
+ *     d_F        out: 1 float64, F recomputed by the adjoint's replay
+ *     d_status   out (may be NULL): n final statuses of the replay
+ *     d_counters in/out (may be NULL): [0] replayed step attempts, [2] rays,
+ *                [4] rays left out (replay longer than d_nacc allows)
+ *     ckpt_bytes out (host, may be NULL): bytes of checkpoint storage used
+ *   Needs RT_PLASMA_GJ, M_sun > 0 and B0_G > 0.  Synchronous: allocates the
+ *   checkpoint store (sum over rays of (nacc/32 + 2) x 104 B), segment
+ *   scratch (2.5 KB per resident thread: about 100 MB on GB300) and 69 B per
+ *   ray, and frees them before returning; RT_ENOMEM if that fails.
+ */
+rt_status rt_flux_value(const rt_star* star, int64_t n, const double* d_state,
+                        const double* d_weight, const uint8_t* d_status, double incl_rad,
+                        double kappa, double* d_F_ray, double* d_F, void* stream);
+rt_status rt_flux_gradient(const rt_star* star, int64_t n, const double* d_uniforms,
+                           const int32_t* d_nacc, double incl_rad, double kappa,
+                           const rt_trace_opts* opts, double* d_grad, double* d_F,
+                           uint8_t* d_status, int64_t* d_counters, int64_t* ckpt_bytes,
+                           void* stream);
+
+/*
  * Batches: many stars (different B0, P, misalignment, m_a, ...) traced in ONE
  * persistent launch whose global queue spans all of them, so the long rays of
  * one star overlap with the bulk of the others.  counts[s] rays of star s

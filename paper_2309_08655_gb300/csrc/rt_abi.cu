@@ -349,6 +349,171 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   return RT_OK;
 }
 
+static double vmf_norm(double kappa) {
+  return kappa / (2.0 * PI * -std::expm1(-2.0 * kappa));
+}
+
+rt_status rt_flux_value(const rt_star* s, int64_t n, const double* d_state,
+                        const double* d_weight, const uint8_t* d_status, double incl_rad,
+                        double kappa, double* d_F_ray, double* d_F, void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
+  if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
+    return fail(RT_EINVAL, "need finite incl_rad and 0 < kappa < inf");
+  rt_status st;
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_weight, "d_weight")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_F_ray, "d_F_ray")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_F, "d_F")) != RT_OK) return st;
+  cudaError_t e = rtk::launch_flux_value(s->d, n, d_state, d_weight, d_status, incl_rad, kappa,
+                                         vmf_norm(kappa), d_F_ray, d_F, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "flux value kernel");
+  return RT_OK;
+}
+
+rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms,
+                           const int32_t* d_nacc, double incl_rad, double kappa,
+                           const rt_trace_opts* o, double* d_grad, double* d_F,
+                           uint8_t* d_status, int64_t* d_counters, int64_t* ckpt_bytes,
+                           void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (o->precision != RT_PREC_FP64)
+    return fail(RT_EUNSUPPORTED, "rt_flux_gradient supports RT_PREC_FP64 only");
+  if (o->lambda_max != 0.0) return fail(RT_EUNSUPPORTED, "lambda_max must be 0");
+  if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
+    return fail(RT_EINVAL, "need finite incl_rad and 0 < kappa < inf");
+  if ((st = check_dev_ptr(d_uniforms, "d_uniforms")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_grad, "d_grad")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_F, "d_F")) != RT_OK) return st;
+  if (d_status && (st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
+  const rt_star_params& p = s->p;
+  const rtk::StarDev& h = s->h;
+  if (p.plasma != RT_PLASMA_GJ) return fail(RT_EUNSUPPORTED, "the gradient needs RT_PLASMA_GJ");
+  if (!(p.M_sun > 0) || !(p.B0_G > 0))
+    return fail(RT_EINVAL, "the gradient needs M_sun > 0 and B0_G > 0");
+  typedef rtk::Dual<rtk::NSAMP_TANGENTS> D5;
+  rtk::AdjLaunch a;
+  // sampling constants with their derivatives (m_a, B0, theta_m, M, R): each a
+  // monomial in the parameters (rt_init_star)
+  D5 c;
+  c = D5(h.rs);
+  c.d[rtk::PAR_M] = h.rs / p.M_sun;
+  c.d[rtk::PAR_R] = -h.rs / p.R_km;
+  a.sc.rs = c;
+  c = D5(h.cp);
+  c.d[rtk::PAR_MA] = -2.0 * h.cp / p.m_a_eV;
+  c.d[rtk::PAR_B0] = h.cp / p.B0_G;
+  a.sc.cp = c;
+  c = D5(h.sin_tm);
+  c.d[rtk::PAR_THM] = h.cos_tm;
+  a.sc.sin_tm = c;
+  c = D5(h.cos_tm);
+  c.d[rtk::PAR_THM] = -h.sin_tm;
+  a.sc.cos_tm = c;
+  c = D5(h.B0_eV2);
+  c.d[rtk::PAR_B0] = h.B0_eV2 / p.B0_G;
+  a.sc.B0_eV2 = c;
+  c = D5(h.R_eV);
+  c.d[rtk::PAR_R] = h.R_eV / p.R_km;
+  a.sc.R_eV = c;
+  c = D5(h.n_inf);
+  c.d[rtk::PAR_MA] = -h.n_inf / p.m_a_eV;
+  a.sc.n_inf = c;
+  c = D5(h.ma_eV);
+  c.d[rtk::PAR_MA] = 1.0;
+  a.sc.ma_eV = c;
+  a.sc.v0 = h.v0;
+  a.sc.psi_fixed = h.psi_fixed;
+  a.sc.plasma_a = h.plasma_a;
+  a.sc.g_eV = h.g_eV;
+  a.sc.w_unit = h.w_unit;
+  a.sc.disp = h.dispersion;
+  a.sc.plasma = h.plasma;
+  a.sc.fa_model = h.fa_model;
+  a.sc.phase_mode = h.phase_mode;
+  a.star = &h;
+  const bool flat = (p.prop_metric == RT_METRIC_FLAT);
+  a.drsp_dM = flat ? 0.0 : h.rs / p.M_sun;
+  a.drsp_dR = flat ? 0.0 : -h.rs / p.R_km;
+  a.dcp_dma = -2.0 * h.cp / p.m_a_eV;
+  a.dcp_dB0 = h.cp / p.B0_G;
+  a.incl = incl_rad;
+  a.kappa = kappa;
+  a.knorm = vmf_norm(kappa);
+  a.rtol = o->rtol;
+  a.atol = o->atol;
+  a.r_out = o->r_out_over_R;
+  a.r_capture = o->r_capture_over_R;
+  a.max_steps = o->max_steps;
+  a.n = n;
+  a.u = d_uniforms;
+  a.grad = d_grad;
+  a.F = d_F;
+  a.counters = d_counters;
+  a.queue = s->d_queue;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = rtk::adjoint_grid(&a.grid, &a.block);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint occupancy");
+  // scratch: checkpoint offsets, checkpoints, segment records, per-ray results
+  int64_t* off = nullptr;
+  double *ck = nullptr, *seg = nullptr, *Fr = nullptr, *Gr = nullptr;
+  uint8_t* stt = nullptr;
+  int32_t* flg = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(off);
+    cudaFree(ck);
+    cudaFree(seg);
+    cudaFree(Fr);
+    cudaFree(Gr);
+    if (!d_status) cudaFree(stt);
+    cudaFree(flg);
+  };
+  int64_t total = 0;
+  const size_t seg_n = (size_t)a.grid * a.block * rtk::CK * 10;
+  if ((e = cudaMalloc(&off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&seg, seg_n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&Fr, n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&Gr, (size_t)rtk::NPARAMS * n * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&flg, n * sizeof(int32_t))) != cudaSuccess ||
+      (!d_status && (e = cudaMalloc(&stt, n)) != cudaSuccess)) {
+    cleanup();
+    return (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "adjoint scratch allocation failed")
+                                            : cuda_fail(e, "cudaMalloc");
+  }
+  if (d_status) stt = d_status;
+  if ((e = rtk::launch_ck_offsets(d_nacc, n, off, cs)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, cs)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(cs)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "checkpoint offsets");
+  }
+  if ((e = cudaMalloc(&ck, (size_t)total * rtk::CKREC * sizeof(double))) != cudaSuccess) {
+    cleanup();
+    return (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "checkpoint allocation failed")
+                                            : cuda_fail(e, "cudaMalloc");
+  }
+  if (ckpt_bytes) *ckpt_bytes = total * rtk::CKREC * (int64_t)sizeof(double);
+  a.ck_off = off;
+  a.ck = ck;
+  a.seg = seg;
+  a.F_ray = Fr;
+  a.G_ray = Gr;
+  a.status = stt;
+  a.flags = flg;
+  e = rtk::launch_adjoint(a, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
+  return RT_OK;
+}
+
 rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
                           const double* d_weight, const uint8_t* d_status, int32_t nth,
                           int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,

@@ -1,0 +1,767 @@
+// Reverse-mode (adjoint) gradient of a smooth line-flux functional through
+// sampling and the FP64 integrator.
+//
+// Functional (a reading: the paper differentiates nothing; the functional is
+// the line flux toward an observer, smoothed on the sphere):
+//   F = sum_i w_i K(khat_i . o),  K(mu) = C exp(kappa (mu - 1)),
+//   C = kappa / (2 pi (1 - exp(-2 kappa)))   (von Mises-Fisher, unit mass),
+// over ESCAPED rays, khat_i the static orthonormal-frame momentum direction at
+// the escape point r = r_out, o = (sin i, 0, cos i).  Parameters p = (m_a
+// [eV], B0 [G], theta_m [rad], M [Msun], R [km], i [rad]).
+//
+// dF/dp = sum_i [ K dw_i/dp + w_i K' dmu_i/dp ], where mu_i depends on p through
+// the initial state y0(p) and the constants q = (r_s/R, omega_p^2 coefficient,
+// magnetic axis m) of the ray equations.  Per ray:
+//  * y0, w and their p-derivatives come from the sampling code instantiated
+//    with 5-tangent dual numbers (the root's derivative by the implicit
+//    function theorem);
+//  * the trajectory is replayed from checkpoints stored every CK accepted
+//    steps, each segment re-integrated (bitwise the same steps) and swept
+//    backwards step by step: the discrete adjoint of a Dormand-Prince step at
+//    its accepted step size, with J^T v of the right-hand side f = Omega grad H
+//    obtained from one forward-mode product, J^T v = Omega J (Omega v), and the
+//    q-derivatives from the same dual evaluation;
+//  * where the Goldreich-Julian branch switches on the null cone c(x) = 0
+//    (the right-hand side jumps there), the saltation matrix
+//    S = I + (f_new - f_old) grad c^T / (grad c . f_old) is applied, together
+//    with the shift of the crossing with the magnetic axis;
+//  * the escape point is the continuous extension at the theta* where
+//    |x| = r_out, differentiated with theta* implicit.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_dual.cuh"
+#include "rt_integrator.cuh"
+#include "rt_internal.h"
+#include "rt_sample_core.cuh"
+
+namespace rtk {
+
+// dual-number overloads used by the sampling core (argument-dependent lookup)
+template <int N>
+__device__ __forceinline__ double val(const Dual<N>& x) {
+  return x.v;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> tabs(const Dual<N>& x) {
+  return dabs(x);
+}
+template <int N>
+__device__ __forceinline__ Dual<N> root_of(double r, const Dual<N>& G, double dGdr) {
+  Dual<N> o(r);
+#pragma unroll
+  for (int k = 0; k < N; ++k) o.d[k] = -G.d[k] / dGdr;
+  return o;
+}
+
+namespace {
+
+using sampling::SampConst;
+using sampling::SampOut;
+using sampling::sample_core;
+
+typedef Dual<6> D6;
+
+constexpr int SEGREC = 10;   // y[6], h, sig, flags, spare
+enum { FL_FLIP_BEFORE = 1, FL_FLIP_AFTER = 2, FL_ESCAPE = 4 };
+
+struct AdjParams {
+  SampConst<Dual<NSAMP_TANGENTS>> sc;
+  SampConst<double> scv;
+  double R_km, ma_eV, rs_prop, cp, plasma_a, cos_tm, sin_tm;
+  int dispersion, plasma;
+  double drsp_dM, drsp_dR, dcp_dma, dcp_dB0;
+  double incl, kappa, knorm;
+  double rtol, atol, r_out, r_capture;
+  int max_steps;
+  int64_t n;
+  const double* u;
+  const int64_t* ck_off;
+  double* ck;
+  double* seg;
+  double* F_ray;
+  double* G_ray;
+  uint8_t* status;
+  int32_t* flags;
+  int64_t* counters;
+  unsigned long long* queue;
+};
+
+// J^T v and v . df/dq at y (q = rs, cp, m0, m1, m2), from one dual evaluation.
+__device__ __noinline__ void rhs_vjp(const RayConst<double>& c, const double* y, const double* v,
+                                     double* out, double* qbar) {
+  RayConst<D6> cd;
+  cd.rs = D6::var(c.rs, 1);
+  cd.cp = D6::var(c.cp, 2);
+  cd.pa = D6(c.pa);
+  cd.W2 = D6(c.W2);
+  cd.iW2 = D6(c.iW2);
+  cd.m0 = D6::var(c.m0, 3);
+  cd.m1 = D6::var(c.m1, 4);
+  cd.m2 = D6::var(c.m2, 5);
+  cd.sig = D6(c.sig);
+  cd.disp = c.disp;
+  cd.plasma = c.plasma;
+  // u = Omega v = (v_k, -v_x)
+  D6 yd[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    yd[j] = D6(y[j]);
+    yd[j].d[0] = v[3 + j];
+    yd[3 + j] = D6(y[3 + j]);
+    yd[3 + j].d[0] = -v[j];
+  }
+  D6 f[6];
+  ham_rhs<D6>(cd, yd[0], yd[1], yd[2], yd[3], yd[4], yd[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+  // J^T v = Omega (J u) = ((Ju)_k, -(Ju)_x)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    out[j] = f[3 + j].d[0];
+    out[3 + j] = -f[j].d[0];
+  }
+#pragma unroll
+  for (int m = 1; m < 6; ++m) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += v[j] * f[j].d[m];
+    qbar[m - 1] += s;
+  }
+}
+
+// Adjoint of a branch switch at y from sig_old to -sig_old:
+// ybar <- S^T ybar, and the crossing's dependence on the magnetic axis.
+__device__ void saltation(RayConst<double> c, const double* y, double sig_old, double* ybar,
+                          double* qbar) {
+  double fo[6], fn[6];
+  c.sig = sig_old;
+  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]);
+  c.sig = -sig_old;
+  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], fn[0], fn[1], fn[2], fn[3], fn[4], fn[5]);
+  // c(x) = 3 z (m.x) - m_z |x|^2 (the sign of Omega . B)
+  const double mx = c.m0 * y[0] + c.m1 * y[1] + c.m2 * y[2];
+  const double gc0 = 3.0 * y[2] * c.m0 - 2.0 * c.m2 * y[0];
+  const double gc1 = 3.0 * y[2] * c.m1 - 2.0 * c.m2 * y[1];
+  const double gc2 = 3.0 * mx + 3.0 * y[2] * c.m2 - 2.0 * c.m2 * y[2];
+  const double den = gc0 * fo[0] + gc1 * fo[1] + gc2 * fo[2];
+  if (den == 0.0) return;
+  double num = 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) num += (fn[j] - fo[j]) * ybar[j];
+  const double s = num / den;
+  ybar[0] += s * gc0;
+  ybar[1] += s * gc1;
+  ybar[2] += s * gc2;
+  const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+  qbar[2] += s * 3.0 * y[2] * y[0];
+  qbar[3] += s * 3.0 * y[2] * y[1];
+  qbar[4] += s * (3.0 * y[2] * y[2] - r2);
+}
+
+// Discrete adjoint of one accepted Dormand-Prince step from y with step h.
+// ybar: in, the adjoint at the step's end (unused when escape); out, at y.
+// Escape: the step ends at the theta* of the continuous extension where
+// |x| = r_out, and ybar_e is the adjoint there.
+__device__ void step_adjoint(const RayConst<double>& c, const double* y, double h, bool escape,
+                             double r_out, const double* ybar_e, double* ybar, double* qbar) {
+  double K[7][6], Y[6][6], t[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Y[0][i] = y[i];
+  rhs64(c, Y[0], K[0]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Y[1][i] = y[i] + h * (DP::a21 * K[0][i]);
+  rhs64(c, Y[1], K[1]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Y[2][i] = y[i] + h * (DP::a31 * K[0][i] + DP::a32 * K[1][i]);
+  rhs64(c, Y[2], K[2]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    Y[3][i] = y[i] + h * (DP::a41 * K[0][i] + DP::a42 * K[1][i] + DP::a43 * K[2][i]);
+  rhs64(c, Y[3], K[3]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    Y[4][i] = y[i] + h * (DP::a51 * K[0][i] + DP::a52 * K[1][i] + DP::a53 * K[2][i] +
+                          DP::a54 * K[3][i]);
+  rhs64(c, Y[4], K[4]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    Y[5][i] = y[i] + h * (DP::a61 * K[0][i] + DP::a62 * K[1][i] + DP::a63 * K[2][i] +
+                          DP::a64 * K[3][i] + DP::a65 * K[4][i]);
+  rhs64(c, Y[5], K[5]);
+  double yn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    yn[i] = y[i] + h * (DP::b1 * K[0][i] + DP::b3 * K[2][i] + DP::b4 * K[3][i] +
+                        DP::b5 * K[4][i] + DP::b6 * K[5][i]);
+  double kb[7][6], ynb[6], yb[6];
+#pragma unroll
+  for (int s = 0; s < 7; ++s)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) kb[s][i] = 0.0;
+  if (escape) {
+    rhs64(c, yn, K[6]);
+    double r2v[6], r3[6], r4[6], r5[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      r2v[i] = yn[i] - y[i];
+      r3[i] = h * K[0][i] - r2v[i];
+      r4[i] = r2v[i] - h * K[6][i] - r3[i];
+      r5[i] = h * (DP::d1 * K[0][i] + DP::d3 * K[2][i] + DP::d4 * K[3][i] + DP::d5 * K[4][i] +
+                   DP::d6 * K[5][i] + DP::d7 * K[6][i]);
+    }
+    // the same bisection as the forward step
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double xd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        xd[i] = y[i] + mid * (r2v[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+      const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+      if (rd < r_out) lo = mid; else hi = mid;
+    }
+    const double th = 0.5 * (lo + hi);
+    const double al = th, be = th * (1.0 - th), ga = th * th * (1.0 - th),
+                 de = th * th * (1.0 - th) * (1.0 - th);
+    const double dal = 1.0, dbe = 1.0 - 2.0 * th, dga = 2.0 * th - 3.0 * th * th,
+                 dde = 2.0 * th * (1.0 - th) * (1.0 - th) - 2.0 * th * th * (1.0 - th);
+    double xe[3], dD[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      dD[i] = dal * r2v[i] + dbe * r3[i] + dga * r4[i] + dde * r5[i];
+      if (i < 3) xe[i] = y[i] + al * r2v[i] + be * r3[i] + ga * r4[i] + de * r5[i];
+    }
+    double s = 0.0, cth = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s += ybar_e[i] * dD[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cth += 2.0 * xe[i] * dD[i];
+    double yt[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yt[i] = ybar_e[i] - ((i < 3) ? (s / cth) * 2.0 * xe[i] : 0.0);
+    double r2b[6], r3b[6], r4b[6], r5b[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      r2b[i] = al * yt[i];
+      r3b[i] = be * yt[i];
+      r4b[i] = ga * yt[i];
+      r5b[i] = de * yt[i];
+      yb[i] = yt[i];
+      kb[0][i] += h * DP::d1 * r5b[i];
+      kb[2][i] += h * DP::d3 * r5b[i];
+      kb[3][i] += h * DP::d4 * r5b[i];
+      kb[4][i] += h * DP::d5 * r5b[i];
+      kb[5][i] += h * DP::d6 * r5b[i];
+      kb[6][i] += h * DP::d7 * r5b[i];
+      r2b[i] += r4b[i];
+      kb[6][i] -= h * r4b[i];
+      r3b[i] -= r4b[i];
+      kb[0][i] += h * r3b[i];
+      r2b[i] -= r3b[i];
+      ynb[i] = r2b[i];
+      yb[i] -= r2b[i];
+    }
+    rhs_vjp(c, yn, kb[6], t, qbar);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ynb[i] += t[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      ynb[i] = ybar[i];
+      yb[i] = 0.0;
+    }
+  }
+  // yn = y + h sum b_j k_j
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    yb[i] += ynb[i];
+    kb[0][i] += h * DP::b1 * ynb[i];
+    kb[2][i] += h * DP::b3 * ynb[i];
+    kb[3][i] += h * DP::b4 * ynb[i];
+    kb[4][i] += h * DP::b5 * ynb[i];
+    kb[5][i] += h * DP::b6 * ynb[i];
+  }
+  // stages, last to first: k_s = f(Y_s), Y_s = y + h sum_j a_sj k_j
+  const double A[6][5] = {{0, 0, 0, 0, 0},
+                          {DP::a21, 0, 0, 0, 0},
+                          {DP::a31, DP::a32, 0, 0, 0},
+                          {DP::a41, DP::a42, DP::a43, 0, 0},
+                          {DP::a51, DP::a52, DP::a53, DP::a54, 0},
+                          {DP::a61, DP::a62, DP::a63, DP::a64, DP::a65}};
+  for (int s = 5; s >= 0; --s) {
+    double Yb[6];
+    rhs_vjp(c, Y[s], kb[s], Yb, qbar);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      yb[i] += Yb[i];
+      for (int j = 0; j < s; ++j) kb[j][i] += h * A[s][j] * Yb[i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) ybar[i] = yb[i];
+}
+
+// K(mu) at a scaled state, in the operation order of flux_kernel_value.
+__device__ double flux_K(const double* x, const double* k, double rs, double si, double ci,
+                         double kappa, double knorm) {
+  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  double n[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) n[j] = x[j] / r;
+  const double A = 1.0 - rs / r;
+  const double kn = n[0] * k[0] + n[1] * k[1] + n[2] * k[2];
+  const double cr = (sqrt(A) - 1.0) * kn;
+  double ko[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) ko[j] = k[j] + cr * n[j];
+  const double kk = 1.0 / sqrt(ko[0] * ko[0] + ko[1] * ko[1] + ko[2] * ko[2]);
+  const double mu = (ko[0] * si + ko[2] * ci) * kk;
+  return knorm * exp(kappa * (mu - 1.0));
+}
+
+// The functional's integrand at the escape point and its gradient with
+// respect to the state and r_s (w and the observer direction held fixed).
+__device__ double flux_kernel_value(const AdjParams& P, const double* y, double w, double* ybar,
+                                    double* rsbar, double* dmu_dincl, double* Kout) {
+  typedef Dual<7> D7;
+  D7 x[3], k[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    x[j] = D7::var(y[j], j);
+    k[j] = D7::var(y[3 + j], 3 + j);
+  }
+  const D7 rs = D7::var(P.rs_prop, 6);
+  const D7 r = rt_sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  D7 n[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) n[j] = x[j] / r;
+  const D7 A = D7(1.0) - rs / r;
+  const D7 kn = n[0] * k[0] + n[1] * k[1] + n[2] * k[2];
+  const D7 cr = (rt_sqrt(A) - D7(1.0)) * kn;
+  D7 ko[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) ko[j] = k[j] + cr * n[j];
+  const D7 kk = rt_rsqrt(ko[0] * ko[0] + ko[1] * ko[1] + ko[2] * ko[2]);
+  double si, ci;
+  sincos(P.incl, &si, &ci);
+  const D7 mu = (ko[0] * D7(si) + ko[2] * D7(ci)) * kk;
+  const double K = P.knorm * exp(P.kappa * (mu.v - 1.0));
+  *Kout = K;
+  const double g = w * K * P.kappa;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) ybar[j] = g * mu.d[j];
+  *rsbar = g * mu.d[6];
+  *dmu_dincl = (ko[0].v * ci - ko[2].v * si) * kk.v;
+  return w * K;
+}
+
+__device__ void store_ck(double* ck, const Lane& L) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) ck[j] = L.y[j];
+  ck[6] = L.h;
+  ck[7] = L.h_resume;
+  ck[8] = L.c.sig;
+  ck[9] = L.last_rej ? 1.0 : 0.0;
+  ck[10] = L.switching ? 1.0 : 0.0;
+  ck[11] = (double)L.na;
+  ck[12] = (double)L.nr;
+}
+
+__device__ void load_ck(const double* ck, Lane& L) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) L.y[j] = ck[j];
+  L.h = ck[6];
+  L.h_resume = ck[7];
+  L.c.sig = ck[8];
+  L.last_rej = ck[9] != 0.0;
+  L.switching = ck[10] != 0.0;
+  L.na = (int)ck[11];
+  L.nr = (int)ck[12];
+  rhs64(L.c, L.y, L.f0);
+}
+
+// Records every accepted step of a segment replay.
+struct RecHook {
+  double* seg;
+  int nrec, cap;
+  bool pend_flip;
+  __device__ void on_accept(const Lane& L, const double* y, const double*, const double*,
+                            const double*, const double*, const double*, const double*,
+                            const double*, double h) {
+    if (nrec < cap) {
+      double* r = seg + (int64_t)nrec * SEGREC;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) r[j] = y[j];
+      r[6] = h;
+      r[7] = L.c.sig;
+      r[8] = pend_flip ? (double)FL_FLIP_BEFORE : 0.0;
+    }
+    pend_flip = false;
+    ++nrec;
+  }
+};
+
+__device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long long* steps) {
+  const int64_t n = P.n;
+  double u[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) u[j] = P.u[j * n + i];
+  SampOut<Dual<NSAMP_TANGENTS>> so;
+  sample_core(P.sc, u, (double)n, so);
+  // values exactly as the sampling kernel computes them
+  SampOut<double> sv;
+  sample_core(P.scv, u, (double)n, sv);
+  double G[NPARAMS];
+#pragma unroll
+  for (int k = 0; k < NPARAMS; ++k) G[k] = 0.0;
+  P.flags[i] = 0;
+  if (!sv.ok || !so.ok) {
+    P.F_ray[i] = 0.0;
+    for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = 0.0;
+    P.status[i] = RAY_NO_ROOT;
+    return;
+  }
+  // the initial lane exactly as the forward trace loads it from the state
+  Lane L;
+  const double iR = 1.0 / P.R_km, im = 1.0 / P.ma_eV;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    L.y[j] = (sv.x[j] * P.R_km) * iR;
+    L.y[3 + j] = (sv.k[j] * P.ma_eV) * im;
+  }
+  const double om = 1.0 + sv.delta;
+  double sps, cps;
+  sincos(sv.psi, &sps, &cps);
+  L.R_km = P.R_km;
+  L.ma_eV = P.ma_eV;
+  L.c.rs = P.rs_prop;
+  L.c.cp = P.cp;
+  L.c.pa = P.plasma_a;
+  L.c.W2 = om * om;
+  L.c.iW2 = 1.0 / (om * om);
+  L.c.m0 = P.sin_tm * cps;
+  L.c.m1 = P.sin_tm * sps;
+  L.c.m2 = P.cos_tm;
+  L.c.disp = P.dispersion;
+  L.c.plasma = P.plasma;
+  L.c.sig = gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]);
+  L.switching = false;
+  L.h_resume = 0.0;
+  rhs64(L.c, L.y, L.f0);
+  L.h = initial_step(L.c, L.y, L.f0, P.rtol, P.atol, 1e30);
+  L.lam = 0.0;
+  L.na = 0;
+  L.nr = 0;
+  L.last_rej = false;
+  TraceParams tp;
+  tp.rtol = P.rtol;
+  tp.atol = P.atol;
+  tp.r_out = P.r_out;
+  tp.lambda_max = 0.0;
+  tp.r_capture = P.r_capture;
+  tp.max_steps = P.max_steps;
+  // forward replay with a checkpoint every CK accepted steps
+  const int64_t c0 = P.ck_off[i];
+  const int64_t cmax = P.ck_off[i + 1] - c0;
+  double* ck = P.ck + c0 * CKREC;
+  int64_t nck = 0;
+  if (nck < cmax) store_ck(ck, L);
+  ++nck;
+  NoHook nh;
+  int st;
+  for (;;) {
+    const int na0 = L.na;
+    st = advance(tp, L, nh);
+    if (st >= 0) break;
+    if (L.na != na0 && L.na % CK == 0) {
+      if (nck < cmax) store_ck(ck + nck * CKREC, L);
+      ++nck;
+    }
+  }
+  const int na_final = L.na;
+  *steps += na_final + L.nr;
+  P.status[i] = (uint8_t)st;
+  if (nck > cmax) {
+    P.flags[i] = 1;   // more steps than the forward pass: no gradient
+    if (P.counters) atomicAdd((unsigned long long*)&P.counters[CTR_PROMOTED], 1ull);
+    P.F_ray[i] = 0.0;
+    for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = 0.0;
+    return;
+  }
+  if (st != RAY_ESCAPED) {
+    P.F_ray[i] = 0.0;
+    for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = 0.0;
+    return;
+  }
+  // functional at the escape point
+  double ybar[6], qbar[5] = {0, 0, 0, 0, 0}, rsb, dmu_di;
+  const double w = sv.w;
+  double Kv;
+  const double Fi = flux_kernel_value(P, L.y, w, ybar, &rsb, &dmu_di, &Kv);
+  qbar[0] += rsb;
+  double ybar_e[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) ybar_e[j] = ybar[j];
+  // reverse sweep over the segments
+  const int last_seg = (na_final - 1) / CK;
+  for (int sgi = last_seg; sgi >= 0; --sgi) {
+    load_ck(ck + (int64_t)sgi * CKREC, L);
+    const int end_na = (sgi == last_seg) ? na_final : (sgi + 1) * CK;
+    RecHook rh;
+    rh.seg = seg;
+    rh.nrec = 0;
+    rh.cap = CK;
+    rh.pend_flip = false;
+    int st2 = -1;
+    while (L.na < end_na) {
+      const int na0 = L.na;
+      const double sig0 = L.c.sig;
+      st2 = advance(tp, L, rh);
+      if (L.na == na0) {
+        if (L.c.sig != sig0) rh.pend_flip = true;   // switched at the current point
+      } else if (st2 < 0 && L.c.sig != sig0 && rh.nrec <= CK) {
+        seg[(int64_t)(rh.nrec - 1) * SEGREC + 8] += (double)FL_FLIP_AFTER;
+      }
+      if (st2 >= 0) break;
+    }
+    if (st2 >= 0 && rh.nrec >= 1 && rh.nrec <= CK)
+      seg[(int64_t)(rh.nrec - 1) * SEGREC + 8] += (double)FL_ESCAPE;
+    const int nrec = rh.nrec < CK ? rh.nrec : CK;
+    for (int j = nrec - 1; j >= 0; --j) {
+      const double* r = seg + (int64_t)j * SEGREC;
+      const int fl = (int)r[8];
+      RayConst<double> cj = L.c;
+      cj.sig = r[7];
+      double y[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) y[q] = r[q];
+      if (fl & FL_FLIP_AFTER) {
+        // the branch switched at the end of this step: undo at y_{n+1}
+        double yn[6];
+        // y_{n+1} is the next record's start, or the next checkpoint's state
+        if (j + 1 < nrec) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) yn[q] = seg[(int64_t)(j + 1) * SEGREC + q];
+        } else {
+          const double* nx = ck + (int64_t)(sgi + 1) * CKREC;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) yn[q] = nx[q];
+        }
+        saltation(cj, yn, r[7], ybar, qbar + 0);
+      }
+      step_adjoint(cj, y, r[6], (fl & FL_ESCAPE) != 0, P.r_out, ybar_e, ybar, qbar);
+      if (fl & FL_FLIP_BEFORE) saltation(cj, y, -r[7], ybar, qbar);
+    }
+  }
+  // assemble dF/dp for this ray
+  double dmdth[3] = {P.cos_tm * cps, P.cos_tm * sps, -P.sin_tm};
+#pragma unroll
+  for (int k = 0; k < NSAMP_TANGENTS; ++k) {
+    double g = Kv * so.w.d[k];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g += ybar[j] * so.x[j].d[k] + ybar[3 + j] * so.k[j].d[k];
+    G[k] = g;
+  }
+  G[PAR_MA] += qbar[1] * P.dcp_dma;
+  G[PAR_B0] += qbar[1] * P.dcp_dB0;
+  G[PAR_THM] += qbar[2] * dmdth[0] + qbar[3] * dmdth[1] + qbar[4] * dmdth[2];
+  G[PAR_M] += qbar[0] * P.drsp_dM;
+  G[PAR_R] += qbar[0] * P.drsp_dR;
+  G[PAR_INCL] = w * Kv * P.kappa * dmu_di;
+  P.F_ray[i] = Fi;
+  for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = G[k];
+}
+
+__global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double* seg = P.seg + tid * (int64_t)CK * SEGREC;
+  long long steps = 0, rays = 0;
+  for (;;) {
+    const int64_t i = (int64_t)atomicAdd(P.queue, 1ull);
+    if (i >= P.n) break;
+    adjoint_ray(P, i, seg, &steps);
+    ++rays;
+  }
+  if (P.counters) {
+    atomicAdd((unsigned long long*)&P.counters[CTR_ACC], (unsigned long long)steps);
+    atomicAdd((unsigned long long*)&P.counters[CTR_RAYS], (unsigned long long)rays);
+  }
+}
+
+// The functional over already traced rays: F_ray[i] = w_i K(mu_i).
+__global__ void flux_value_kernel(const StarDev* sd, int64_t n, const double* state,
+                                  const double* weight, const uint8_t* status, double incl,
+                                  double kappa, double knorm, double* F_ray) {
+  const StarDev& s = *sd;
+  double si, ci;
+  sincos(incl, &si, &ci);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (status[i] != RAY_ESCAPED) {
+      F_ray[i] = 0.0;
+      continue;
+    }
+    const double iR = 1.0 / s.R_km, im = 1.0 / s.ma_eV;
+    double x[3], k[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      x[j] = state[j * n + i] * iR;
+      k[j] = state[(3 + j) * n + i] * im;
+    }
+    F_ray[i] = weight[i] * flux_K(x, k, s.rs_prop, si, ci, kappa, knorm);
+  }
+}
+
+// Deterministic sums of rows of an (nrow x n) array: one block per row, each
+// thread a strided partial sum in a fixed order, then a fixed-shape tree.
+__global__ void row_sums_kernel(const double* a, int64_t n, double* out) {
+  __shared__ double sh[256];
+  const int row = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += a[row * n + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[row] = sh[0];
+}
+
+// Checkpoint counts per ray from the forward step counts, and their exclusive
+// prefix sum (one block; fixed order).
+__global__ void ck_offsets_kernel(const int32_t* nacc, int64_t n, int64_t* off) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int64_t chunk = (n + T - 1) / T;
+  const int64_t b = (int64_t)t * chunk, e = (b + chunk < n) ? b + chunk : n;
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += (int64_t)(nacc[i] / CK) + 2;
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t acc = 0;
+    for (int q = 0; q < T; ++q) {
+      const int64_t v = part[q];
+      part[q] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  int64_t acc = part[t];
+  for (int64_t i = b; i < e; ++i) {
+    off[i] = acc;
+    acc += (int64_t)(nacc[i] / CK) + 2;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* state,
+                              const double* weight, const uint8_t* status, double incl,
+                              double kappa, double knorm, double* F_ray, double* F_total,
+                              cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (n + 255) / 256;
+  if (grid > (int64_t)nsm * 8) grid = (int64_t)nsm * 8;
+  flux_value_kernel<<<(unsigned)grid, 256, 0, stream>>>(d_star, n, state, weight, status, incl,
+                                                        kappa, knorm, F_ray);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_sums_kernel<<<1, 256, 0, stream>>>(F_ray, n, F_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ck_offsets(const int32_t* nacc, int64_t n, int64_t* off, cudaStream_t stream) {
+  ck_offsets_kernel<<<1, 1024, 0, stream>>>(nacc, n, off);
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_grid(int* grid, int* block) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *block = 64;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel, *block, 0);
+  if (e != cudaSuccess) return e;
+  *grid = nsm * (occ > 0 ? occ : 1);
+  return cudaSuccess;
+}
+
+cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
+  AdjParams P;
+  P.sc = a.sc;
+  {
+    const auto& d = a.sc;
+    SampConst<double>& v = P.scv;
+    v.rs = d.rs.v;
+    v.cp = d.cp.v;
+    v.sin_tm = d.sin_tm.v;
+    v.cos_tm = d.cos_tm.v;
+    v.B0_eV2 = d.B0_eV2.v;
+    v.R_eV = d.R_eV.v;
+    v.n_inf = d.n_inf.v;
+    v.ma_eV = d.ma_eV.v;
+    v.v0 = d.v0;
+    v.psi_fixed = d.psi_fixed;
+    v.plasma_a = d.plasma_a;
+    v.g_eV = d.g_eV;
+    v.w_unit = d.w_unit;
+    v.disp = d.disp;
+    v.plasma = d.plasma;
+    v.fa_model = d.fa_model;
+    v.phase_mode = d.phase_mode;
+  }
+  P.R_km = a.star->R_km;
+  P.ma_eV = a.star->ma_eV;
+  P.rs_prop = a.star->rs_prop;
+  P.cp = a.star->cp;
+  P.plasma_a = a.star->plasma_a;
+  P.cos_tm = a.star->cos_tm;
+  P.sin_tm = a.star->sin_tm;
+  P.dispersion = a.star->dispersion;
+  P.plasma = a.star->plasma;
+  P.drsp_dM = a.drsp_dM;
+  P.drsp_dR = a.drsp_dR;
+  P.dcp_dma = a.dcp_dma;
+  P.dcp_dB0 = a.dcp_dB0;
+  P.incl = a.incl;
+  P.kappa = a.kappa;
+  P.knorm = a.knorm;
+  P.rtol = a.rtol;
+  P.atol = a.atol;
+  P.r_out = a.r_out;
+  P.r_capture = a.r_capture;
+  P.max_steps = a.max_steps;
+  P.n = a.n;
+  P.u = a.u;
+  P.ck_off = a.ck_off;
+  P.ck = a.ck;
+  P.seg = a.seg;
+  P.F_ray = a.F_ray;
+  P.G_ray = a.G_ray;
+  P.status = a.status;
+  P.flags = a.flags;
+  P.counters = a.counters;
+  P.queue = a.queue;
+  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  adjoint_kernel<<<a.grid, a.block, 0, stream>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_sums_kernel<<<NPARAMS, 256, 0, stream>>>(a.G_ray, a.n, a.grad);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_sums_kernel<<<1, 256, 0, stream>>>(a.F_ray, a.n, a.F);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

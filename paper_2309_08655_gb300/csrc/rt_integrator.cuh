@@ -1,0 +1,246 @@
+// The FP64 Dormand-Prince 5(4) integrator of Hamilton's equations (Eq.
+// Hamilton) shared by the forward, backward and adjoint kernels: the lane
+// state of one ray, the step-size controller, and one step attempt with the
+// null-cone branch switching, the step-reach bound and the escape event.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_device.cuh"
+#include "rt_internal.h"
+
+namespace rtk {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ void rhs64(const RayConst<double>& c, const double* y, double* f) {
+  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+}
+
+__device__ __forceinline__ double step_factor(double err, bool accepted, bool last_rej) {
+  double fac = (err > 0.0) ? 0.9 * pow(err, -0.2) : 5.0;
+  fac = fmin(5.0, fmax(0.2, fac));
+  if (!accepted || last_rej) fac = fmin(fac, 1.0);
+  return fac;
+}
+
+// Hairer's two-evaluation initial step (order 5).
+__device__ double initial_step(const RayConst<double>& c, const double* y0, const double* f0,
+                               double rtol, double atol, double hmax) {
+  double dnf = 0.0, dny = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double sk = atol + rtol * fabs(y0[i]);
+    dnf += (f0[i] / sk) * (f0[i] / sk);
+    dny += (y0[i] / sk) * (y0[i] / sk);
+  }
+  double h = (dnf <= 1e-10 || dny <= 1e-10) ? 1e-6 : sqrt(dny / dnf) * 0.01;
+  h = fmin(h, hmax);
+  double y1[6], f1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y1[i] = y0[i] + h * f0[i];
+  rhs64(c, y1, f1);
+  double der2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double sk = atol + rtol * fabs(y0[i]);
+    der2 += ((f1[i] - f0[i]) / sk) * ((f1[i] - f0[i]) / sk);
+  }
+  der2 = sqrt(der2) / h;
+  const double der12 = fmax(fabs(der2), sqrt(dnf));
+  const double h1 = (der12 <= 1e-15) ? fmax(1e-6, h * 1e-3) : pow(0.01 / der12, 0.2);
+  return fmin(fmin(100.0 * h, h1), hmax);
+}
+
+struct Lane {
+  RayConst<double> c;
+  double y[6], f0[6];
+  double h, lam;
+  int na, nr;
+  bool last_rej;
+  bool switching;      // the current attempt ends just past a null-cone crossing
+  double h_resume;     // step size to resume with after that crossing
+  double R_km, ma_eV;
+};
+
+// The Goldreich-Julian density |2 Omega . B / e| has a kink on the null cone
+// Omega . B = 0 (Eq. GJDensity): dk/dlambda jumps there, which an embedded
+// error estimate cannot resolve inside a step.  Each step integrates the
+// smooth continuation of the side it starts on (c.sig); when an accepted step
+// ends on the other side, the crossing is located on the continuous extension,
+// the step is redone to end just past it, and the side is switched there.
+constexpr double SWITCH_MIN_FRACTION = 1e-6;
+constexpr double SWITCH_OVERSHOOT = 1e-10;
+
+// Observer of accepted steps (forward tracing needs none).
+struct NoHook {
+  __device__ __forceinline__ void on_accept(const Lane&, const double*, const double*,
+                                            const double*, const double*, const double*,
+                                            const double*, const double*, const double*,
+                                            double) {}
+};
+
+// One attempted Dormand-Prince step.  Returns -1 to continue, else the final
+// ray status.  hook.on_accept sees every accepted step (start, end, stages).
+template <class Hook>
+__device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
+  if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
+  bool clipped = false;
+  double h = L.h;
+  {
+    // displacement of one step at most STEP_REACH x the distance to the centre
+    const double v2 = L.f0[0] * L.f0[0] + L.f0[1] * L.f0[1] + L.f0[2] * L.f0[2];
+    const double r2 = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
+    if (h * h * v2 > STEP_REACH * STEP_REACH * r2) h = STEP_REACH * sqrt(r2 / v2);
+  }
+  if (p.lambda_max > 0.0 && L.lam + h >= p.lambda_max) {
+    h = p.lambda_max - L.lam;
+    clipped = true;
+  }
+  const double* y = L.y;
+  const double* k1 = L.f0;
+  double t[6], k2[6], k3[6], k4[6], k5[6], k6[6], k7[6], yn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (DP::a21 * k1[i]);
+  rhs64(L.c, t, k2);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t[i] = y[i] + h * (DP::a31 * k1[i] + DP::a32 * k2[i]);
+  rhs64(L.c, t, k3);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a41 * k1[i] + DP::a42 * k2[i] + DP::a43 * k3[i]);
+  rhs64(L.c, t, k4);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a51 * k1[i] + DP::a52 * k2[i] + DP::a53 * k3[i] + DP::a54 * k4[i]);
+  rhs64(L.c, t, k5);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    t[i] = y[i] + h * (DP::a61 * k1[i] + DP::a62 * k2[i] + DP::a63 * k3[i] + DP::a64 * k4[i] +
+                       DP::a65 * k5[i]);
+  rhs64(L.c, t, k6);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    yn[i] = y[i] + h * (DP::b1 * k1[i] + DP::b3 * k3[i] + DP::b4 * k4[i] + DP::b5 * k5[i] +
+                        DP::b6 * k6[i]);
+  rhs64(L.c, yn, k7);
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double e = h * (DP::e1 * k1[i] + DP::e3 * k3[i] + DP::e4 * k4[i] + DP::e5 * k5[i] +
+                          DP::e6 * k6[i] + DP::e7 * k7[i]);
+    const double sc = p.atol + p.rtol * fmax(fabs(y[i]), fabs(yn[i]));
+    s += (e / sc) * (e / sc);
+  }
+  const double en = sqrt(s / 6.0);
+  if (!isfinite(en)) {
+    ++L.nr;
+    L.h = h * 0.2;
+    L.last_rej = true;
+    return (L.h < 1e-12) ? RAY_NAN : -1;
+  }
+  const bool gj = (L.c.plasma == PLASMA_GJ);
+  if (en <= 1.0 && gj && !L.switching &&
+      L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, yn[0], yn[1], yn[2]) < 0.0) {
+    // the step crossed the null cone: largest th with the start side on the
+    // continuous extension (bisection), then redo the step to end just past it
+    double r3[3], r4[3], r5[3], r2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r2[i] = yn[i] - y[i];
+      r3[i] = h * k1[i] - r2[i];
+      r4[i] = r2[i] - h * k7[i] - r3[i];
+      r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
+                   DP::d6 * k6[i] + DP::d7 * k7[i]);
+    }
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      double xd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        xd[i] = y[i] + mid * (r2[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+      if (L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, xd[0], xd[1], xd[2]) >= 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    ++L.nr;
+    if (lo < SWITCH_MIN_FRACTION) {
+      L.c.sig = -L.c.sig;             // already at the cone: switch here
+      rhs64(L.c, L.y, L.f0);
+      L.h = h;
+    } else {
+      L.h_resume = h;
+      L.h = h * lo * (1.0 + SWITCH_OVERSHOOT);
+      L.switching = true;
+    }
+    return -1;
+  }
+  if (en <= 1.0) {
+    ++L.na;
+    hook.on_accept(L, y, yn, k1, k3, k4, k5, k6, k7, h);
+    const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+    if (rnew >= p.r_out) {
+      // locate |x(th)| = r_out on the continuous extension by bisection
+      double r3[6], r4[6], r5[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const double r2 = yn[i] - y[i];
+        r3[i] = h * k1[i] - r2;
+        r4[i] = r2 - h * k7[i] - r3[i];
+        r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
+                     DP::d6 * k6[i] + DP::d7 * k7[i]);
+        t[i] = r2;
+      }
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double xd[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          xd[i] = y[i] + mid * (t[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+        const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+        if (rd < p.r_out) lo = mid; else hi = mid;
+      }
+      const double th = 0.5 * (lo + hi);
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        yn[i] = y[i] + th * (t[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+#pragma unroll
+      for (int i = 0; i < 6; ++i) L.y[i] = yn[i];
+      L.lam += th * h;
+      return RAY_ESCAPED;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      L.y[i] = yn[i];
+      L.f0[i] = k7[i];
+    }
+    L.lam += h;
+    if (rnew <= p.r_capture) return RAY_CAPTURED;
+    if (clipped) return RAY_LAMBDA_END;
+    if (gj && L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]) < 0.0) {
+      L.c.sig = -L.c.sig;             // past the cone: continue on the other side
+      rhs64(L.c, L.y, L.f0);
+    }
+    if (L.switching) {
+      L.h = L.h_resume;
+      L.switching = false;
+    } else {
+      L.h = h * step_factor(en, true, L.last_rej);
+    }
+    L.last_rej = false;
+    return -1;
+  }
+  ++L.nr;
+  L.h = h * step_factor(en, false, L.last_rej);
+  L.last_rej = true;
+  return (L.h < 1e-12) ? RAY_STIFF : -1;
+}
+
+}  // namespace
+}  // namespace rtk

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include "rt_device.cuh"
+#include "rt_dual.cuh"
+#include "rt_sample_core.cuh"
 
 namespace rtk {
 
@@ -84,6 +86,44 @@ struct BackLaunch {
   unsigned long long* queue;
 };
 cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream);
+
+// Adjoint of the line-flux functional (rt_adjoint.cu).  Parameters, in
+// order: m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad];
+// the first NSAMP_TANGENTS move the sampling.
+enum { PAR_MA = 0, PAR_B0, PAR_THM, PAR_M, PAR_R, PAR_INCL, NPARAMS };
+constexpr int NSAMP_TANGENTS = 5;
+constexpr int CK = 32;        // accepted steps per checkpoint
+constexpr int CKREC = 13;     // doubles per checkpoint: y, h, h_resume, sig, flags, counts
+
+struct AdjLaunch {
+  const StarDev* star;                          // host descriptor
+  sampling::SampConst<Dual<NSAMP_TANGENTS>> sc;  // sampling constants with p-tangents
+  double drsp_dM, drsp_dR, dcp_dma, dcp_dB0;
+  double incl, kappa, knorm;
+  double rtol, atol, r_out, r_capture;
+  int max_steps;
+  int64_t n;
+  const double* u;
+  const int64_t* ck_off;
+  double* ck;
+  double* seg;
+  double* F_ray;
+  double* G_ray;
+  uint8_t* status;
+  int32_t* flags;
+  int64_t* counters;
+  unsigned long long* queue;
+  double* grad;    // NPARAMS
+  double* F;       // 1
+  int grid, block;
+};
+cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* state,
+                              const double* weight, const uint8_t* status, double incl,
+                              double kappa, double knorm, double* F_ray, double* F_total,
+                              cudaStream_t stream);
+cudaError_t launch_ck_offsets(const int32_t* nacc, int64_t n, int64_t* off, cudaStream_t stream);
+cudaError_t adjoint_grid(int* grid, int* block);
+cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream);
 
 // Sets the thread-local message returned by rt_last_error().
 void set_last_error(const char* msg);

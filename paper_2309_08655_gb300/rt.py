@@ -83,6 +83,13 @@ def lib():
         L.rt_flops_per_step.restype = ctypes.c_int
         L.rt_flops_per_step.argtypes = [ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_double)]
+        L.rt_flux_value.restype = ctypes.c_int
+        L.rt_flux_value.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double,
+                                    ctypes.c_double, _vp, _vp, _vp]
+        L.rt_flux_gradient.restype = ctypes.c_int
+        L.rt_flux_gradient.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(rt_trace_opts), _vp, _vp,
+                                       _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
         L.rt_count_status.restype = ctypes.c_int
         L.rt_count_status.argtypes = [ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
         L.rt_init_batch.restype = ctypes.c_int
@@ -249,6 +256,26 @@ def rt_flops_per_step(dispersion: int, plasma: int) -> list[float]:
     return list(out)
 
 
+def rt_flux_value(star: Star, n, state, weight, status, incl_rad, kappa, F_ray, F,
+                  stream=None) -> int:
+    return _check(lib().rt_flux_value(star.handle, int(n), _ptr(state), _ptr(weight),
+                                      _ptr(status), float(incl_rad), float(kappa), _ptr(F_ray),
+                                      _ptr(F), _stream(stream)))
+
+
+def rt_flux_gradient(star: Star, n, uniforms, nacc, incl_rad, kappa, grad, F, status=None,
+                     counters=None, opts: rt_trace_opts | None = None, stream=None) -> int:
+    """Returns the checkpoint bytes used."""
+    if opts is None:
+        opts = make_opts()
+    nbytes = ctypes.c_int64(0)
+    _check(lib().rt_flux_gradient(star.handle, int(n), _ptr(uniforms), _ptr(nacc),
+                                  float(incl_rad), float(kappa), ctypes.byref(opts), _ptr(grad),
+                                  _ptr(F), _ptr(status), _ptr(counters), ctypes.byref(nbytes),
+                                  _stream(stream)))
+    return int(nbytes.value)
+
+
 def rt_count_status(n, status, stream=None) -> tuple[int, list[int]]:
     counts = (ctypes.c_int64 * RAY_NSTATUS)()
     st = _check(lib().rt_count_status(int(n), _ptr(status), counts, _stream(stream)),
@@ -324,4 +351,4 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_trace_forward", "rt_bin_spectrum", "rt_count_status", "rt_last_error",
             "rt_version", "rt_init_batch", "rt_destroy_batch", "rt_sample_batch",
             "rt_trace_batch", "rt_bin_batch", "rt_trace_backward", "rt_bin_spectrum_noalloc",
-            "rt_flops_per_step"]
+            "rt_flops_per_step", "rt_flux_value", "rt_flux_gradient"]

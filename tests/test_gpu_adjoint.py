@@ -1,0 +1,154 @@
+"""Adjoint gradient of the smoothed line flux (rt_flux_gradient, behind
+torch.autograd.Function) against central finite differences of the GPU
+forward pipeline and of the FP64 oracle (the CPU reference gradient).
+
+Finite differences use a relative step of 1e-6 (absolute 1e-6 rad for the
+angles) at rtol 1e-12, so that the step-size controller's discrete decisions
+move F by much less than the difference quotient resolves.  The adjoint is
+the exact gradient of the discrete scheme at frozen decisions; the bar is
+1e-5 relative per component (1e-4 against the oracle, whose F differs from
+the GPU's only by rounding but is evaluated with its own root finder).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2309_08655_gb300 import flux  # noqa: E402
+from paper_2309_08655_gb300 import inputs as I  # noqa: E402
+from paper_2309_08655_gb300 import rt  # noqa: E402
+
+from . import gpu_util as G  # noqa: E402
+
+KAPPA = 4.0
+RTOL_FD = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2309_08655_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _base():
+    """The misaligned magnetar-like star (B0 = 1.6e14 G, P = 3.76 s, 30 deg,
+    1.5 Msun, 11 km) at m_a = 1e-5 eV, rotation phase uniform per ray."""
+    kw = I.stars_config1()[0]
+    kw.update(m_a_eV=1e-5)
+    return kw
+
+
+def _p0(kw, incl=1.1):
+    return torch.tensor([kw["m_a_eV"], kw["B0_G"], kw["theta_m"], kw["M_sun"], kw["R_km"], incl],
+                        dtype=torch.float64)
+
+
+def _steps(p):
+    h = 1e-6 * np.abs(p.numpy())
+    h[2] = h[5] = 1e-6
+    return h
+
+
+def _fd(fn, p, h):
+    g = np.zeros(6)
+    for k in range(6):
+        e = torch.zeros(6, dtype=torch.float64)
+        e[k] = h[k]
+        g[k] = (fn(p + e) - fn(p - e)) / (2.0 * h[k])
+    return g
+
+
+def _oracle_F(oracle, base, p, u, kappa, rtol):
+    kw = dict(base)
+    kw.update(m_a_eV=float(p[0]), B0_G=float(p[1]), theta_m=float(p[2]), M_sun=float(p[3]),
+              R_km=float(p[4]))
+    incl = float(p[5])
+    sv = oracle.star_vector(**kw)
+    st, w, s = oracle.sample(sv, u)
+    oracle.trace_forward(sv, oracle.trace_opts(rtol=rtol), st, s)
+    esc = s == oracle.RAY_ESCAPED
+    rs = oracle.star_constants(sv)["rs_over_R"]
+    x = st[:3, esc] / kw["R_km"]
+    k = st[3:6, esc] / kw["m_a_eV"]
+    r = np.sqrt((x * x).sum(0))
+    n = x / r
+    A = 1.0 - rs / r
+    kn = (n * k).sum(0)
+    ko = k + (np.sqrt(A) - 1.0) * kn * n
+    mu = (ko[0] * math.sin(incl) + ko[2] * math.cos(incl)) / np.sqrt((ko * ko).sum(0))
+    C = kappa / (2.0 * math.pi * -math.expm1(-2.0 * kappa))
+    return float((w[esc] * C * np.exp(kappa * (mu - 1.0))).sum())
+
+
+def test_adjoint_matches_finite_differences():
+    kw = _base()
+    n = 2048
+    u = torch.from_numpy(I.sample_uniforms(4, n)).to(G.dev())
+    p = _p0(kw).requires_grad_(True)
+    F = flux.line_flux(p, kw, u, KAPPA)
+    F.backward()
+    g_adj = p.grad.numpy().copy()
+    assert math.isfinite(float(F.detach())) and float(F.detach()) > 0
+
+    def Fgpu(q):
+        return float(flux.flux_forward(q, kw, u, KAPPA, rtol=RTOL_FD)[0].cpu()[0])
+
+    pd = p.detach()
+    g_fd = _fd(Fgpu, pd, _steps(pd))
+    rel = np.abs(g_adj - g_fd) / np.maximum(np.abs(g_fd), 1e-300)
+    assert np.all(np.isfinite(g_adj))
+    assert np.all(rel < 1e-5), (g_adj, g_fd, rel)
+
+
+def test_adjoint_replay_reproduces_forward_value():
+    kw = _base()
+    n = 1024
+    u = torch.from_numpy(I.sample_uniforms(5, n)).to(G.dev())
+    p = _p0(kw, incl=0.7)
+    F, nacc, star, incl, opts = flux.flux_forward(p, kw, u, KAPPA)
+    grad = torch.empty(6, dtype=torch.float64, device=G.dev())
+    F2 = torch.empty(1, dtype=torch.float64, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    nbytes = rt.rt_flux_gradient(star, n, u, nacc, incl, KAPPA, grad, F2, counters=ctr,
+                                 opts=opts)
+    torch.cuda.synchronize()
+    # the same rays and steps; the functional is summed from per-ray terms that
+    # the two kernels round differently (FMA contraction)
+    assert abs(float(F2.cpu()[0]) - float(F.cpu()[0])) <= 1e-13 * abs(float(F.cpu()[0]))
+    c = ctr.cpu().numpy()
+    assert c[2] == n and c[4] == 0
+    assert nbytes > 0
+
+
+def test_adjoint_matches_oracle_reference_gradient(oracle):
+    kw = _base()
+    n = 512
+    u_np = I.sample_uniforms(6, n)
+    u = torch.from_numpy(u_np).to(G.dev())
+    p = _p0(kw, incl=1.3).requires_grad_(True)
+    F = flux.line_flux(p, kw, u, KAPPA)
+    F.backward()
+    g_adj = p.grad.numpy()
+    pd = p.detach()
+    F_or = _oracle_F(oracle, kw, pd.numpy(), u_np, KAPPA, 1e-10)
+    assert abs(F_or - float(F.detach())) <= 1e-9 * abs(F_or)
+    g_or = _fd(lambda q: _oracle_F(oracle, kw, q.numpy(), u_np, KAPPA, RTOL_FD), pd, _steps(pd))
+    rel = np.abs(g_adj - g_or) / np.maximum(np.abs(g_or), 1e-300)
+    assert np.all(rel < 1e-4), (g_adj, g_or, rel)
+
+
+def test_gradient_rejects_unsupported_models():
+    kw = _base()
+    kw.update(plasma=4, plasma_a=8.0)      # the spherical test medium
+    star = rt.Star(rt.make_params(**kw))
+    n = 16
+    u = torch.from_numpy(I.sample_uniforms(7, n)).to(G.dev())
+    nacc = torch.zeros(n, dtype=torch.int32, device=G.dev())
+    g = torch.empty(6, dtype=torch.float64, device=G.dev())
+    F = torch.empty(1, dtype=torch.float64, device=G.dev())
+    with pytest.raises(rt.RtError):
+        rt.rt_flux_gradient(star, n, u, nacc, 1.0, KAPPA, g, F)
