@@ -63,6 +63,8 @@ def _args():
                     help="skip the backward image-plane measurement")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the 256-instance uneven batch measurement")
     return ap.parse_args()
 
 
@@ -370,6 +372,9 @@ def run_ours(args):
     adj = None
     if not args.no_adjoint:
         adj = _adjoint_leg(args, dev)
+    uneven = None
+    if not args.no_uneven:
+        uneven = _uneven_leg(args, dev)
     if rank != 0:
         return
     H = res[head]
@@ -391,6 +396,7 @@ def run_ours(args):
         "backward": back,
         "adjoint_forward_ratio": adj["adjoint_forward_ratio"] if adj else None,
         "adjoint": adj,
+        "uneven_batch": uneven,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
@@ -398,6 +404,96 @@ def run_ours(args):
         "clocks": clk,
     }
     print(json.dumps(line))
+
+
+def _uneven_leg(args, dev):
+    """256 star/axion instances with ray counts log-uniform in [1e3, 1e6]:
+    the 128 forward instances in one persistent launch (mixed precision,
+    launch shape from the autotuner, sample -> trace -> bin captured in one
+    CUDA graph), the 128 backward images (FP64) on a second stream.  Latency
+    of an instance = GPU global-timer stamp of its last ray or pixel minus the
+    start of the first launch."""
+    import numpy as np
+    import torch
+
+    from paper_2309_08655_gb300 import inputs as I
+    from paper_2309_08655_gb300 import rt
+    insts = I.instances_config3()
+    fwd = [x for x in insts if x["mode"] == "forward"]
+    bwd = [x for x in insts if x["mode"] == "backward"]
+    stars = [rt.Star(rt.make_params(**x["star"])) for x in fwd]
+    counts = [x["n"] for x in fwd]
+    batch = rt.Batch(stars, counts)
+    N = batch.N
+    u = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [I.sample_uniforms(x["seed"], x["n"]) for x in fwd], axis=1))).to(dev)
+    st = torch.empty((8, N), dtype=torch.float64, device=dev)
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    s = torch.empty(N, dtype=torch.uint8, device=dev)
+    nth, nph, nnu = NBINS
+    hist = torch.empty((len(fwd), nth, nph, nnu), dtype=torch.float64, device=dev)
+    oor = torch.empty(len(fwd), dtype=torch.float64, device=dev)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    ts_f = torch.zeros(1 + len(fwd), dtype=torch.int64, device=dev)
+    opts_f = rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED, timestamps=ts_f)
+    rt.rt_sample_batch(batch, u, st, w, s)
+    tune = rt.rt_batch_autotune(batch, st, s, opts_f, rays_per_star=256)
+    graph = rt.Graph(batch, u, st, w, s, ctr, opts_f, nth, nph, nnu, 0.0, 9.0, hist, oor)
+    # backward images: one star each, bmax from the largest conversion radius
+    bstars, bopts, bufs = [], [], []
+    ts_b = torch.zeros(2 * len(bwd), dtype=torch.int64, device=dev)
+    ctr_b = torch.zeros(8, dtype=torch.int64, device=dev)
+    for j, x in enumerate(bwd):
+        sb = rt.Star(rt.make_params(**x["star"]))
+        r_max = max((2.0 * sb.info()["wp2_coef"]) ** (1.0 / 3.0), 1.5)
+        side = x["side"]
+        img = torch.empty((side, side), dtype=torch.float64, device=dev)
+        stt = torch.empty((side, side), dtype=torch.uint8, device=dev)
+        bstars.append((sb, side, x["incl"], 1.3 * r_max))
+        bopts.append(rt.make_opts(rtol=1e-10, timestamps=ts_b[2 * j:2 * j + 2]))
+        bufs.append((img, stt))
+    s2 = torch.cuda.Stream()
+    # warm-up: one replay of the forward graph
+    graph.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for j in range(len(bwd)):
+        rt.rt_timestamps_reset(ts_b[2 * j:2 * j + 2], 1)
+    ctr_b.zero_()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    e0.record()
+    s2.wait_event(e0)
+    graph.launch()
+    with torch.cuda.stream(s2):
+        for (sb, side, incl, bmax), o, (img, stt) in zip(bstars, bopts, bufs):
+            rt.rt_trace_backward(sb, side, side, incl, 1e4, bmax, img, stt, None, ctr_b, opts=o,
+                                 stream=s2)
+    torch.cuda.current_stream().wait_stream(s2)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    t_wall = time.perf_counter() - t_wall
+    tf = ts_f.cpu().numpy().astype(np.int64)
+    tb = ts_b.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    c, cb = ctr.cpu().numpy(), ctr_b.cpu().numpy()
+    t0 = min(int(tf[0]), int(tb[:, 0].min()))
+    lat = [(int(tf[1 + k]) - t0) / 1e6 for k in range(len(fwd)) if tf[1 + k] > 0]
+    lat += [(int(tb[j, 1]) - t0) / 1e6 for j in range(len(bwd)) if tb[j, 1] > 0]
+    lat = np.array(lat)
+    steps = float(c[0] + cb[0])
+    return {"workload": "uneven_256_instances_128fwd_128bwd", "instances": len(insts),
+            "forward_rays": int(N), "backward_pixels": int(sum(b[1] ** 2 for b in bstars)),
+            "empty_forward_instances": int(sum(1 for x in stars if x.info()["empty"])),
+            "precision": {"forward": "mixed (rtol 1e-8)", "backward": "fp64 (rtol 1e-10)"},
+            "autotuned": {"block": tune["block"], "blocks_per_sm": tune["blocks_per_sm"],
+                          "candidates": len(tune["candidates_ms"])},
+            "graph": "forward sample -> trace -> bin replayed from one CUDA graph",
+            "seconds": t, "wall_seconds": t_wall, "ray_steps_per_s": steps / t,
+            "accepted_steps": steps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p90": float(np.percentile(lat, 90)), "max": float(lat.max()),
+                           "instances_timed": int(lat.size)}}
 
 
 def _adjoint_leg(args, dev):

@@ -117,13 +117,25 @@ typedef struct {
  *   r_capture_over_R  capture radius (1 = stellar surface)
  *   precision         RT_PREC_FP64 or RT_PREC_MIXED
  *   max_steps         bound on accepted steps per ray
- *   block             threads per block of the persistent kernel (0 = auto)
+ *   block             threads per block of the persistent kernel (0 = auto, or
+ *                     the batch's autotuned value, rt_batch_autotune)
  *   blocks_per_sm     resident blocks per SM for the persistent grid (0 = auto)
+ *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
+ *                     that the kernels stamp with the GPU's nanosecond global
+ *                     timer: [0] the earliest start of a tracing launch (min),
+ *                     [1 + s] the moment the last ray (pixel) of instance s
+ *                     finished (max; s = the star's index in a batch, 0 for a
+ *                     single star or an image).  Reset with rt_timestamps_reset;
+ *                     per-instance latency = [1 + s] - [0].
  */
 typedef struct {
   double rtol, atol, r_out_over_R, lambda_max, r_capture_over_R;
   int32_t precision, max_steps, block, blocks_per_sm;
+  uint64_t* timestamps;
 } rt_trace_opts;
+
+/* rt_timestamps_reset - [0] = UINT64_MAX, [1..n_instances] = 0, on stream. */
+rt_status rt_timestamps_reset(uint64_t* d_timestamps, int32_t n_instances, void* stream);
 
 typedef struct rt_star rt_star; /* opaque, library-owned */
 
@@ -343,6 +355,43 @@ rt_status rt_bin_batch(rt_batch* batch, const double* d_state, const double* d_w
                        const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
                        double nu_lo, double nu_hi, double* d_hist, double* d_out_of_range,
                        void* stream);
+
+/*
+ * CUDA graph of one batch step.  rt_batch_graph_create captures, on a stream
+ * of its own, exactly what rt_sample_batch, rt_trace_batch (with d_counters
+ * and opts) and rt_bin_batch enqueue for these buffers -- plus a reset of
+ * d_counters (may be NULL) and of opts->timestamps (if set) -- and
+ * instantiates it (host, synchronous; the launch shape is fixed at capture,
+ * so autotune first).  rt_graph_launch replays it on `stream` (the buffers'
+ * contents at replay time are used).  The graph holds the batch's handles:
+ * destroy it before them.
+ */
+typedef struct rt_graph rt_graph;
+rt_status rt_batch_graph_create(rt_batch* batch, const double* d_uniforms, double* d_state,
+                                double* d_weight, uint8_t* d_status, int64_t* d_counters,
+                                const rt_trace_opts* opts, int32_t nth, int32_t nph, int32_t nnu,
+                                double nu_lo, double nu_hi, double* d_hist,
+                                double* d_out_of_range, rt_graph** out);
+rt_status rt_graph_launch(rt_graph* graph, void* stream);
+void rt_graph_destroy(rt_graph* graph);
+
+/*
+ * rt_batch_autotune - choose the trace kernel's launch shape (threads per
+ * block, resident blocks per SM) for this batch and opts->precision by timing
+ * every candidate the kernel's register budget allows on a sample: the first
+ * rays_per_star sampled rays of every star (d_state/d_status as left by
+ * rt_sample_batch; they are copied, not modified).  One warm-up run, then one
+ * timed run per candidate (CUDA events).  The choice is stored in the batch
+ * and used by rt_trace_batch whenever opts->block == 0.  Synchronous;
+ * allocates and frees scratch for the sample.
+ *   block_out, bps_out, ms_out (host, may be NULL): the winner and its time
+ *   ncand_out (may be NULL): candidates timed; cand_ms (may be NULL): their
+ *   times in ms, at most cand_cap of them
+ */
+rt_status rt_batch_autotune(rt_batch* batch, const double* d_state, const uint8_t* d_status,
+                            const rt_trace_opts* opts, int32_t rays_per_star, int32_t* block_out,
+                            int32_t* bps_out, double* ms_out, int32_t* ncand_out, double* cand_ms,
+                            int32_t cand_cap, void* stream);
 
 /*
  * rt_bin_spectrum_noalloc - rt_bin_spectrum for callers that cannot allocate

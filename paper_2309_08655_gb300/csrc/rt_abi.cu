@@ -275,6 +275,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.nrej = d_nrej;
   p.counters = d_counters;
   p.queue = s->d_queue;
+  p.ts = (unsigned long long*)o->timestamps;
   p.rtol = o->rtol;
   p.atol = o->atol;
   p.r_out = o->r_out_over_R;
@@ -344,6 +345,7 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   b.ncross = d_ncross;
   b.counters = d_counters;
   b.queue = s->d_queue;
+  b.ts = (unsigned long long*)o->timestamps;
   cudaError_t e = rtk::launch_backward(b, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward kernel");
   return RT_OK;
@@ -591,6 +593,8 @@ struct rt_batch {
   size_t bins_per_star = 0;
   int device = 0;
   bool all_empty = true;
+  int tuned_block[2] = {0, 0};        // autotuned launch shape per precision (0 = default)
+  int tuned_bps[2] = {0, 0};
 };
 
 extern "C" {
@@ -700,6 +704,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.nrej = d_nrej;
   p.counters = d_counters;
   p.queue = b->d_queue;
+  p.ts = (unsigned long long*)o->timestamps;
   p.rtol = o->rtol;
   p.atol = o->atol;
   p.r_out = o->r_out_over_R;
@@ -707,19 +712,49 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
+  const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
+  const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
+  const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];
   cudaError_t e;
   if (o->precision == RT_PREC_MIXED) {
-    e = rtk::launch_trace_mixed(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    e = rtk::launch_trace_mixed(p, blk, bps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
     p.claim_status = rtk::RAY_PROMOTED;
     e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
     return RT_OK;
   }
-  e = rtk::launch_trace_fp64(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+  e = rtk::launch_trace_fp64(p, blk, bps, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "trace kernel");
   return RT_OK;
 }
+
+}  // extern "C"
+
+// The batch's binning scratch, grown when a larger histogram is requested
+// (synchronises the stream before freeing the old one).
+static rt_status ensure_batch_bins(rt_batch* b, int32_t nth, int32_t nph, int32_t nnu,
+                                   void* stream) {
+  const size_t per = rtk::bin_scratch_entries(nth, nph, nnu);
+  if (per <= b->bins_per_star) return RT_OK;
+  if (b->d_bins) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(b->d_bins);
+    b->d_bins = nullptr;
+    b->bins_per_star = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, per * b->stars.size() * sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RT_ENOMEM, "cannot allocate the batch binning scratch");
+  }
+  b->d_bins = (long long*)p;
+  b->bins_per_star = per;
+  return RT_OK;
+}
+
+extern "C" {
 
 rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weight,
                        const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
@@ -737,24 +772,8 @@ rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weigh
   }
   if ((st = check_dev_ptr(d_hist, "d_hist")) != RT_OK) return st;
   if ((st = check_dev_ptr(d_oor, "d_out_of_range")) != RT_OK) return st;
-  const size_t per = rtk::bin_scratch_entries(nth, nph, nnu);
   const size_t nst = b->stars.size();
-  if (per > b->bins_per_star) {
-    if (b->d_bins) {
-      cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-      cudaFree(b->d_bins);
-      b->d_bins = nullptr;
-      b->bins_per_star = 0;
-    }
-    void* p = nullptr;
-    if (cudaMalloc(&p, per * nst * sizeof(long long)) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(RT_ENOMEM, "cannot allocate the batch binning scratch");
-    }
-    b->d_bins = (long long*)p;
-    b->bins_per_star = per;
-  }
+  if ((st = ensure_batch_bins(b, nth, nph, nnu, stream)) != RT_OK) return st;
   const size_t nbins = (size_t)nth * nph * nnu;
   for (size_t s = 0; s < nst; ++s) {
     const int64_t o = b->off[s], cnt = b->off[s + 1] - o;
@@ -778,6 +797,230 @@ rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weigh
     cudaError_t e = rtk::launch_bin(p, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "bin kernels");
   }
+  return RT_OK;
+}
+
+rt_status rt_timestamps_reset(uint64_t* d_ts, int32_t n_instances, void* stream) {
+  if (n_instances < 1) return fail(RT_EINVAL, "n_instances must be >= 1");
+  rt_status st;
+  if ((st = check_dev_ptr(d_ts, "d_timestamps")) != RT_OK) return st;
+  cudaError_t e = rtk::launch_ts_reset((unsigned long long*)d_ts, n_instances,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "timestamp reset");
+  return RT_OK;
+}
+
+struct rt_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+rt_status rt_batch_graph_create(rt_batch* b, const double* d_u, double* d_state,
+                                double* d_weight, uint8_t* d_status, int64_t* d_counters,
+                                const rt_trace_opts* o, int32_t nth, int32_t nph, int32_t nnu,
+                                double nu_lo, double nu_hi, double* d_hist, double* d_oor,
+                                rt_graph** out) {
+  if (!out) return fail(RT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  if (b->N == 0) return fail(RT_EINVAL, "empty batch");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
+  if ((st = ensure_batch_bins(b, nth, nph, nnu, nullptr)) != RT_OK) return st;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  // sample -> trace -> bin, as the individual calls would enqueue them
+  st = RT_OK;
+  if (d_counters) {
+    e = cudaMemsetAsync(d_counters, 0, RT_COUNTERS * sizeof(int64_t), cs);
+    if (e != cudaSuccess) st = cuda_fail(e, "counter reset");
+  }
+  if (st == RT_OK && o->timestamps) st = rt_timestamps_reset(o->timestamps,
+                                                             (int32_t)b->stars.size(), cs);
+  if (st == RT_OK) {
+    st = rt_sample_batch(b, d_u, d_state, d_weight, d_status, cs);
+    if (st == RT_EEMPTY_SURFACE) st = RT_OK;
+  }
+  if (st == RT_OK) st = rt_trace_batch(b, d_state, d_status, nullptr, nullptr, d_counters, o, cs);
+  if (st == RT_OK)
+    st = rt_bin_batch(b, d_state, d_weight, d_status, nth, nph, nnu, nu_lo, nu_hi, d_hist,
+                      d_oor, cs);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (st != RT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  rt_graph* r = new (std::nothrow) rt_graph;
+  if (!r) {
+    cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    return fail(RT_ENOMEM, "host allocation failed");
+  }
+  r->graph = g;
+  r->exec = x;
+  cudaGetDevice(&r->device);
+  *out = r;
+  return RT_OK;
+}
+
+rt_status rt_graph_launch(rt_graph* g, void* stream) {
+  if (!g) return fail(RT_EINVAL, "graph is NULL");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return RT_OK;
+}
+
+void rt_graph_destroy(rt_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d_status,
+                            const rt_trace_opts* o, int32_t rays_per_star, int32_t* block_out,
+                            int32_t* bps_out, double* ms_out, int32_t* ncand_out,
+                            double* cand_ms, int32_t cand_cap, void* stream) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if (rays_per_star < 1) return fail(RT_EINVAL, "rays_per_star must be >= 1");
+  if (b->N == 0) return fail(RT_EINVAL, "empty batch");
+  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  const bool mixed = (o->precision == RT_PREC_MIXED);
+  const size_t nst = b->stars.size();
+  // the first rays_per_star rays of every star, in a batch of their own
+  std::vector<int64_t> off(nst + 1, 0);
+  for (size_t s = 0; s < nst; ++s) {
+    const int64_t cnt = b->off[s + 1] - b->off[s];
+    off[s + 1] = off[s] + (cnt < rays_per_star ? cnt : rays_per_star);
+  }
+  const int64_t M = off[nst];
+  if (M == 0) return fail(RT_EINVAL, "no rays to tune on");
+  cudaStream_t cs = (cudaStream_t)stream;
+  void* blk = nullptr;
+  const size_t bytes = 256 + 2 * (size_t)RT_STATE_ROWS * M * sizeof(double) + 2 * (size_t)M +
+                       (nst + 1) * sizeof(int64_t) + 64;
+  cudaError_t e = cudaMalloc(&blk, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RT_ENOMEM, "autotune scratch allocation failed");
+  }
+  char* q = (char*)blk;
+  unsigned long long* queue = (unsigned long long*)q;
+  double* st0 = (double*)(q + 256);
+  double* st1 = st0 + (size_t)RT_STATE_ROWS * M;
+  uint8_t* s0 = (uint8_t*)(st1 + (size_t)RT_STATE_ROWS * M);
+  uint8_t* s1 = s0 + M;
+  int64_t* doff = (int64_t*)(((uintptr_t)(s1 + M) + 7) & ~(uintptr_t)7);
+  for (size_t s = 0; s < nst && e == cudaSuccess; ++s) {
+    const int64_t m = off[s + 1] - off[s];
+    if (m == 0) continue;
+    for (int r = 0; r < RT_STATE_ROWS && e == cudaSuccess; ++r)
+      e = cudaMemcpyAsync(st0 + r * M + off[s], d_state + r * b->N + b->off[s],
+                          m * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s0 + off[s], d_status + b->off[s], m, cudaMemcpyDeviceToDevice, cs);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(doff, off.data(), (nst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                        cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return cuda_fail(e, "autotune gather");
+  }
+  rtk::TraceParams p;
+  p.stars = b->d_stars;
+  p.nstars = (int)nst;
+  p.offsets = doff;
+  p.n = M;
+  p.state = st1;
+  p.status = s1;
+  p.nacc = nullptr;
+  p.nrej = nullptr;
+  p.counters = nullptr;
+  p.queue = queue;
+  p.ts = nullptr;
+  p.rtol = o->rtol;
+  p.atol = o->atol;
+  p.r_out = o->r_out_over_R;
+  p.lambda_max = o->lambda_max;
+  p.r_capture = o->r_capture_over_R;
+  p.max_steps = o->max_steps;
+  // candidates: block sizes the kernel's launch bounds allow, every resident count
+  std::vector<std::pair<int, int>> cand;
+  const int blocks[3] = {mixed ? 64 : 32, mixed ? 128 : 64, mixed ? 256 : 128};
+  for (int bi = 0; bi < 3; ++bi) {
+    int occ = 0;
+    e = mixed ? rtk::occupancy_mixed(blocks[bi], &occ) : rtk::occupancy_fp64(blocks[bi], &occ);
+    if (e != cudaSuccess) break;
+    for (int k = 1; k <= occ; ++k) cand.push_back({blocks[bi], k});
+  }
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  auto run = [&](int block, int bps, float* ms) -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(st1, st0, (size_t)RT_STATE_ROWS * M * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, cs);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(s1, s0, M, cudaMemcpyDeviceToDevice, cs);
+    if (r == cudaSuccess) r = cudaEventRecord(ev0, cs);
+    p.claim_status = rtk::RAY_READY;
+    if (r == cudaSuccess)
+      r = mixed ? rtk::launch_trace_mixed(p, block, bps, cs) : rtk::launch_trace_fp64(p, block, bps, cs);
+    if (r == cudaSuccess && mixed) {
+      p.claim_status = rtk::RAY_PROMOTED;
+      r = rtk::launch_trace_fp64(p, 0, 0, cs);
+    }
+    if (r == cudaSuccess) r = cudaEventRecord(ev1, cs);
+    if (r == cudaSuccess) r = cudaEventSynchronize(ev1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, ev0, ev1);
+    return r;
+  };
+  int best_b = 0, best_k = 0;
+  float best = 3.0e38f, ms = 0.0f;
+  if (e == cudaSuccess && !cand.empty()) e = run(cand[0].first, cand[0].second, &ms);   // warm-up
+  int nc = 0;
+  for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+    e = run(cand[c].first, cand[c].second, &ms);
+    if (e != cudaSuccess) break;
+    if (cand_ms && nc < cand_cap) cand_ms[nc] = ms;
+    ++nc;
+    if (ms < best) {
+      best = ms;
+      best_b = cand[c].first;
+      best_k = cand[c].second;
+    }
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  cudaFree(blk);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
+  const int pi = mixed ? 1 : 0;
+  b->tuned_block[pi] = best_b;
+  b->tuned_bps[pi] = best_k;
+  if (block_out) *block_out = best_b;
+  if (bps_out) *bps_out = best_k;
+  if (ms_out) *ms_out = best;
+  if (ncand_out) *ncand_out = nc;
   return RT_OK;
 }
 

@@ -113,7 +113,8 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
   const T ir2 = ir * ir;
   const T A = T(1) - c.rs * ir;
   const T Am1 = -c.rs * ir;
-  const T iA = rt_rcp(A);
+  const T qA = rt_rsqrt(A);                    // one special for 1/A, sqrt(A), 1/sqrt(A)
+  const T iA = qA * qA;
   const T W = c.W2 * iA;                       // omega^2
   const T kr = n0 * k0 + n1 * k1 + n2 * k2;    // n.k
   // metric part: H_g = -W2/A + k.k + (A-1) kr^2
@@ -166,7 +167,7 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
     // anisotropic term H_a = P - P A Kp^2 / W2 with Kp = U / |b|,
     // U = k.b + (sqrt(A) - 1) (n.k)(n.b), n.b = 2 mu, |b|^2 = 3 mu^2 + 1
     const T ib = rt_rsqrt(T(3) * mu * mu + T(1));
-    const T sA = rt_sqrt(A);
+    const T sA = A * qA;
     const T km = k0 * c.m0 + k1 * c.m1 + k2 * c.m2;
     const T U = T(3) * mu * kr - km + T(2) * mu * kr * (sA - T(1));
     const T Kp = U * ib;
@@ -183,7 +184,7 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
     const T ib3 = ib * ib * ib;
     const T a1 = ib * opsA * kr - T(3) * mu * U * ib3;
     const T a2 = ib * opsA * mu;
-    const T a3 = ib * mu * kr * c.rs * ir2 * rt_rcp(sA);
+    const T a3 = ib * mu * kr * c.rs * ir2 * qA;
     const T a1r = a1 * ir, a2r = a2 * ir;
     const T an = a3 - a1r * mu - a2r * kr;
     const T dK0 = a1r * c.m0 + a2r * k0 + an * n0;
@@ -233,6 +234,13 @@ __device__ __forceinline__ T ham_value(const RayConst<T>& c, const T* x, const T
   const T km = k[0] * c.m0 + k[1] * c.m1 + k[2] * c.m2;
   const T Kp = (T(3) * mu * kr - km + T(2) * mu * kr * (sA - T(1))) * ib;
   return H + P - P * A * Kp * Kp * c.iW2;
+}
+
+// Nanosecond global timer of the GPU (for per-instance completion times).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 // Largest displacement of one integration step, as a fraction of the distance

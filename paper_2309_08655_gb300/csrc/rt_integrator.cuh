@@ -182,8 +182,8 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
   if (en <= 1.0) {
     ++L.na;
     hook.on_accept(L, y, yn, k1, k3, k4, k5, k6, k7, h);
-    const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
-    if (rnew >= p.r_out) {
+    const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
+    if (rnew2 >= p.r_out * p.r_out) {
       // locate |x(th)| = r_out on the continuous extension by bisection
       double r3[6], r4[6], r5[6];
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
       L.f0[i] = k7[i];
     }
     L.lam += h;
-    if (rnew <= p.r_capture) return RAY_CAPTURED;
+    if (rnew2 <= p.r_capture * p.r_capture) return RAY_CAPTURED;
     if (clipped) return RAY_LAMBDA_END;
     if (gj && L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]) < 0.0) {
       L.c.sig = -L.c.sig;             // past the cone: continue on the other side

@@ -24,6 +24,7 @@ struct TraceParams {
   double rtol, atol, r_out, lambda_max, r_capture;
   int max_steps;
   int claim_status;           // rays with this status are traced (READY, or PROMOTED)
+  unsigned long long* ts;     // optional: [0] launch start (min), [1 + star] last finish (max)
 };
 
 // Per-call counters (int64): accepted steps, rejected steps, rays finished,
@@ -66,6 +67,9 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
                                cudaStream_t stream);
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
+// Resident blocks per SM of the trace kernels at a block size.
+cudaError_t occupancy_fp64(int block, int* occ);
+cudaError_t occupancy_mixed(int block, int* occ);
 
 // Backward image-plane tracing (one ray per pixel, ny x nx row-major).
 struct BackLaunch {
@@ -84,8 +88,10 @@ struct BackLaunch {
   int32_t* ncross;
   int64_t* counters;
   unsigned long long* queue;
+  unsigned long long* ts;     // optional: [0] start (min), [1] last pixel finished (max)
 };
 cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream);
+cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream);
 
 // Adjoint of the line-flux functional (rt_adjoint.cu).  Parameters, in
 // order: m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad];

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   Lane L;
   long long acc = 0, rej = 0, traced = 0, esc = 0;
   int na0 = 0, nr0 = 0;   // steps a resumed ray had already taken in FP32
+  if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   for (;;) {
     const bool need = (ray == -1);
     const unsigned mneed = __ballot_sync(FULL, need);
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       const int st = advance(p, L, nh);
       if (st >= 0) {
         store_lane(p, ray, L, st);
+        if (p.ts) atomicMax(p.ts + 1 + find_star(p, ray), global_ns());
         acc += L.na - na0;
         rej += L.nr - nr0;
         traced += 1;
@@ -172,6 +174,7 @@ struct BackParams {
   unsigned long long* queue;
   double rtol, atol, r_capture;
   int max_steps;
+  unsigned long long* ts;
 };
 
 __device__ __forceinline__ double crossing_g(const RayConst<double>& c, double W,
@@ -385,10 +388,12 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   tp.lambda_max = 0.0;
   tp.r_capture = bp.r_capture;
   tp.max_steps = bp.max_steps;
+  tp.ts = nullptr;
   int64_t pix = -1;
   Lane L;
   CrossingHook hk;
   long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0;
+  if (bp.ts && threadIdx.x == 0) atomicMin(bp.ts, global_ns());
   for (;;) {
     const bool need = (pix == -1);
     const unsigned mneed = __ballot_sync(FULL, need);
@@ -422,6 +427,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
       const int st = advance(tp, L, hk);
       if (st >= 0) {
         bp.image[pix] = bp.img_scale * hk.sum;
+        if (bp.ts) atomicMax(bp.ts + 1, global_ns());
         bp.status[pix] = (uint8_t)st;
         if (bp.ncross) bp.ncross[pix] = hk.ncross - hk.ncut;
         acc += L.na;
@@ -478,6 +484,7 @@ cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream) {
   bp.rtol = b.rtol;
   bp.atol = b.atol;
   bp.r_capture = b.r_capture;
+  bp.ts = b.ts;
   bp.max_steps = b.max_steps;
   const int block = 128;
   int occ = 0;
@@ -492,6 +499,21 @@ cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   backward_kernel<<<(unsigned)grid, block, 0, stream>>>(bp);
   return cudaGetLastError();
+}
+
+namespace {
+__global__ void ts_reset_kernel(unsigned long long* ts, int n) {
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) ts[i] = (i == 0) ? ~0ull : 0ull;
+}
+}  // namespace
+
+cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream) {
+  ts_reset_kernel<<<1, 256, 0, stream>>>(ts, n);
+  return cudaGetLastError();
+}
+
+cudaError_t occupancy_fp64(int block, int* occ) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, trace_fp64_kernel, block, 0);
 }
 
 cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,

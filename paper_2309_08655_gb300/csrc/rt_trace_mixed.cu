@@ -336,8 +336,8 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   if (en <= 1.0f) {
     ++L.na;
     L.noisy_rej = 0;
-    const double rnew = sqrt(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
-    if (rnew >= p.r_out) {
+    const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
+    if (rnew2 >= p.r_out * p.r_out) {
       // locate |x(th)| = r_out on the continuous extension
       float lo = 0.0f, hi = 1.0f;
       for (int it = 0; it < 60; ++it) {
@@ -367,7 +367,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
     for (int i = 0; i < 6; ++i) L.y[i] = yn[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i) L.f0[i] = fn[i];
-    if (rnew <= p.r_capture) return RAY_CAPTURED;
+    if (rnew2 <= p.r_capture * p.r_capture) return RAY_CAPTURED;
     if (gj && L.c.sig * side_md(L.md, L.y[0], L.y[1], L.y[2]) < 0.0f) {
       L.c.sig = -L.c.sig;             // past the cone: continue on the other side
       rhs32c(L.c, L.md, L.y, t + 3, L.f0);
@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
   int64_t ray = -1;
   LaneM L;
   long long acc = 0, rej = 0, traced = 0, esc = 0, promoted = 0;
+  if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   for (;;) {
     const bool need = (ray == -1);
     const unsigned mneed = __ballot_sync(FULL, need);
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
       const int st = advance_m(p, L);
       if (st >= 0) {
         store_lane_m(p, ray, L, st);
+        if (p.ts && st != RAY_PROMOTED) atomicMax(p.ts + 1 + find_star_m(p, ray), global_ns());
         acc += L.na;
         rej += L.nr;
         if (st == RAY_PROMOTED) {
@@ -451,6 +453,10 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
 }
 
 }  // namespace
+
+cudaError_t occupancy_mixed(int block, int* occ) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, trace_mixed_kernel, block, 0);
+}
 
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
                                cudaStream_t stream) {

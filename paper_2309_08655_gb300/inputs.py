@@ -83,3 +83,31 @@ def stars_config1(seed: int = 1, nsub: int = 16) -> list[dict]:
 CONFIG1 = dict(name="forward_misaligned_16x65536", nsub=16, n_per_sub=1 << 16, seed=1,
                rtol=1e-10, rtol_mixed=1e-8, r_out_over_R=1000.0, max_steps=100000, nth=64,
                nph=32, nnu=128, nu_lo=0.0, nu_hi=9.0)
+
+
+def instances_config3(seed: int = 3, n: int = 256) -> list[dict]:
+    """Uneven batch of star/axion configurations: B0 log-uniform in
+    [1e12, 1e15] G, P uniform in [0.1, 10] s, misalignment uniform in
+    [0, 90] deg, m_a log-uniform in [1e-6, 5e-3] eV, M = 1.4 Msun, R = 10 km;
+    ray counts log-uniform in [1e3, 1e6]; odd instances are backward images
+    (side ceil(sqrt(N)), observer direction uniform on the sphere), even ones
+    forward batches with a uniform rotation phase per ray."""
+    u = uniforms(seed, 1 << 41, 7 * n).reshape(n, 7)
+    out = []
+    for i in range(n):
+        v = u[i]
+        B0 = math.exp(math.log(1e12) + v[0] * (math.log(1e15) - math.log(1e12)))
+        P = 0.1 + v[1] * (10.0 - 0.1)
+        th = v[2] * 0.5 * math.pi
+        ma = math.exp(math.log(1e-6) + v[3] * (math.log(5e-3) - math.log(1e-6)))
+        N = int(round(math.exp(math.log(1e3) + v[4] * (math.log(1e6) - math.log(1e3)))))
+        star = star_config0()
+        star.update(M_sun=1.4, R_km=10.0, B0_G=B0, P_s=P, theta_m=th, m_a_eV=ma,
+                    phase_mode=1 if i % 2 == 0 else 0, psi=2.0 * math.pi * v[6])
+        inst = dict(star=star, n=N, mode="backward" if i % 2 else "forward",
+                    seed=seed * 100000 + i)
+        if i % 2:
+            inst["side"] = int(math.ceil(math.sqrt(N)))
+            inst["incl"] = math.acos(1.0 - 2.0 * v[5])
+        out.append(inst)
+    return out

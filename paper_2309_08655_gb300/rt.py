@@ -40,7 +40,8 @@ class rt_star_params(ctypes.Structure):
 class rt_trace_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in [
         "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
-        (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm"]]
+        (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm"]] + [
+        ("timestamps", ctypes.c_void_p)]
 
 
 _lib = None
@@ -90,6 +91,24 @@ def lib():
         L.rt_flux_gradient.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(rt_trace_opts), _vp, _vp,
                                        _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+        L.rt_timestamps_reset.restype = ctypes.c_int
+        L.rt_timestamps_reset.argtypes = [_vp, ctypes.c_int32, _vp]
+        L.rt_batch_graph_create.restype = ctypes.c_int
+        L.rt_batch_graph_create.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp,
+                                            ctypes.POINTER(rt_trace_opts), ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                            ctypes.c_double, _vp, _vp, ctypes.POINTER(_vp)]
+        L.rt_graph_launch.restype = ctypes.c_int
+        L.rt_graph_launch.argtypes = [_vp, _vp]
+        L.rt_graph_destroy.restype = None
+        L.rt_graph_destroy.argtypes = [_vp]
+        L.rt_batch_autotune.restype = ctypes.c_int
+        L.rt_batch_autotune.argtypes = [_vp, _vp, _vp, ctypes.POINTER(rt_trace_opts),
+                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _vp]
         L.rt_count_status.restype = ctypes.c_int
         L.rt_count_status.argtypes = [ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
         L.rt_init_batch.restype = ctypes.c_int
@@ -153,7 +172,8 @@ def make_params(**kw) -> rt_star_params:
 
 
 def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capture_over_R=1.0,
-              precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0) -> rt_trace_opts:
+              precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0,
+              timestamps=None) -> rt_trace_opts:
     o = rt_trace_opts()
     o.rtol = rtol
     o.atol = rtol if atol is None else atol
@@ -164,6 +184,7 @@ def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capt
     o.max_steps = max_steps
     o.block = block
     o.blocks_per_sm = blocks_per_sm
+    o.timestamps = _ptr(timestamps)
     return o
 
 
@@ -276,6 +297,67 @@ def rt_flux_gradient(star: Star, n, uniforms, nacc, incl_rad, kappa, grad, F, st
     return int(nbytes.value)
 
 
+def rt_timestamps_reset(timestamps, n_instances, stream=None) -> int:
+    return _check(lib().rt_timestamps_reset(_ptr(timestamps), int(n_instances), _stream(stream)))
+
+
+class Graph:
+    """Owning wrapper of an ``rt_graph`` (a captured sample -> trace -> bin step)."""
+
+    def __init__(self, batch, uniforms, state, weight, status, counters, opts, nth, nph, nnu,
+                 nu_lo, nu_hi, hist, out_of_range):
+        h = _vp()
+        _check(lib().rt_batch_graph_create(batch.handle, _ptr(uniforms), _ptr(state),
+                                           _ptr(weight), _ptr(status), _ptr(counters),
+                                           ctypes.byref(opts), int(nth), int(nph), int(nnu),
+                                           float(nu_lo), float(nu_hi), _ptr(hist),
+                                           _ptr(out_of_range), ctypes.byref(h)))
+        self.handle = h
+        self.keep = (batch, opts)      # the graph refers to both
+
+    def launch(self, stream=None) -> int:
+        return _check(lib().rt_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rt_batch_graph_create(batch, uniforms, state, weight, status, counters, opts, nth, nph, nnu,
+                          nu_lo, nu_hi, hist, out_of_range) -> Graph:
+    return Graph(batch, uniforms, state, weight, status, counters, opts, nth, nph, nnu, nu_lo,
+                 nu_hi, hist, out_of_range)
+
+
+def rt_graph_launch(graph: Graph, stream=None) -> int:
+    return graph.launch(stream)
+
+
+def rt_graph_destroy(graph: Graph) -> None:
+    graph.close()
+
+
+def rt_batch_autotune(batch, state, status, opts, rays_per_star=2048, stream=None) -> dict:
+    blk = ctypes.c_int32(0)
+    bps = ctypes.c_int32(0)
+    ms = ctypes.c_double(0.0)
+    nc = ctypes.c_int32(0)
+    cand = (ctypes.c_double * 64)()
+    _check(lib().rt_batch_autotune(batch.handle, _ptr(state), _ptr(status), ctypes.byref(opts),
+                                   int(rays_per_star), ctypes.byref(blk), ctypes.byref(bps),
+                                   ctypes.byref(ms), ctypes.byref(nc), cand, 64,
+                                   _stream(stream)))
+    return {"block": blk.value, "blocks_per_sm": bps.value, "ms": ms.value,
+            "candidates_ms": list(cand)[:min(nc.value, 64)]}
+
+
 def rt_count_status(n, status, stream=None) -> tuple[int, list[int]]:
     counts = (ctypes.c_int64 * RAY_NSTATUS)()
     st = _check(lib().rt_count_status(int(n), _ptr(status), counts, _stream(stream)),
@@ -351,4 +433,5 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_trace_forward", "rt_bin_spectrum", "rt_count_status", "rt_last_error",
             "rt_version", "rt_init_batch", "rt_destroy_batch", "rt_sample_batch",
             "rt_trace_batch", "rt_bin_batch", "rt_trace_backward", "rt_bin_spectrum_noalloc",
-            "rt_flops_per_step", "rt_flux_value", "rt_flux_gradient"]
+            "rt_flops_per_step", "rt_flux_value", "rt_flux_gradient", "rt_timestamps_reset",
+            "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune"]
