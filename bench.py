@@ -222,6 +222,7 @@ def run_ours(args):
     from paper_2309_08655_gb300 import build as B
     from paper_2309_08655_gb300 import inputs as I
     from paper_2309_08655_gb300 import rt
+    from paper_2309_08655_gb300 import shard
 
     ws, rank, local = _dist()
     if not torch.cuda.is_available():
@@ -239,7 +240,7 @@ def run_ours(args):
     stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
     batch = rt.Batch(stars, [nper] * nsub)
     # weak scaling: every rank traces its own seeded copy of the workload
-    seeds = [cfg["seed"] * 1000 + j + 100000 * rank for j in range(nsub)]
+    seeds = shard.rank_seeds(cfg["seed"], nsub, rank)
     u_host = torch.from_numpy(np.ascontiguousarray(
         np.concatenate([I.sample_uniforms(sd, nper) for sd in seeds], axis=1))).pin_memory()
     u = u_host.to(dev)
@@ -295,15 +296,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        T = sum(t_steps)
-        acc_all, rays_all = c_sum[0], c_sum[2]
-        if ws > 1:
-            tt = torch.tensor([T], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            T = float(tt[0])
-            cs = torch.tensor([c_sum[0], c_sum[2]], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(cs)
-            acc_all, rays_all = float(cs[0]), float(cs[1])
+        T, acc_all, rays_all = shard.reduce_totals(sum(t_steps), c_sum[0], c_sum[2], dev)
         attempts = (c_sum[0] + c_sum[1]) / args.steps
         rays_launch = c_sum[2] / args.steps
         promoted_attempts = c_sum[5] / args.steps
@@ -365,15 +358,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_e2e.append(time.perf_counter() - t0)
         acc_e2e += float(ctr[0])
-    e2e_val = acc_e2e / sum(t_e2e)
+    t_e2e_all, acc_e2e, _ = shard.reduce_totals(sum(t_e2e), acc_e2e, 0.0, dev)
+    e2e_val = acc_e2e / t_e2e_all
+    # the further legs run on a single GPU only (a scaling run times the main step)
     back = None
-    if not args.no_backward:
+    if ws == 1 and not args.no_backward:
         back = _backward_leg(args, dev, stream, fl, rank)
     adj = None
-    if not args.no_adjoint:
+    if ws == 1 and not args.no_adjoint:
         adj = _adjoint_leg(args, dev)
     uneven = None
-    if not args.no_uneven:
+    if ws == 1 and not args.no_uneven:
         uneven = _uneven_leg(args, dev)
     if rank != 0:
         return
