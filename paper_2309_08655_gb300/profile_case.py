@@ -2,6 +2,7 @@
 
     python -m paper_2309_08655_gb300.profile_case --precision fp64 --n 1024
     python -m paper_2309_08655_gb300.profile_case --mode backward --n 65536
+    python -m paper_2309_08655_gb300.profile_case --mode adjoint --n 4096
 
 Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
 them once in the requested precision (one persistent trace launch, after one
@@ -9,7 +10,9 @@ untimed warm-up launch on a copy) and bins them.  Backward: an image of about
 n pixels (square) of the same star at inclination 60 deg, plane at 1e4 R,
 impact parameters up to 50 R (one warm-up launch on an image of at most
 32 x 32 pixels first).
-Prints the trace time and step counts.
+Adjoint: n rays of the misaligned magnetar-like star at m_a = 1e-5 eV, the
+smoothed line flux toward 1.1 rad (kappa 4) and its gradient (one warm-up
+gradient on 256 rays first).  Prints the trace time and step counts.
 """
 from __future__ import annotations
 
@@ -30,12 +33,14 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
-    ap.add_argument("--mode", choices=["forward", "backward"], default="forward")
+    ap.add_argument("--mode", choices=["forward", "backward", "adjoint"], default="forward")
     a = ap.parse_args()
     build()
     dev = torch.device("cuda:0")
     if a.mode == "backward":
         return backward(a, dev)
+    if a.mode == "adjoint":
+        return adjoint(a, dev)
     if a.config == "config0":
         kw = I.star_config0()
     else:
@@ -95,6 +100,31 @@ def backward(a, dev):
                       "rejected": int(c[1]), "pixels_done": int(c[2]), "crossings": int(c[6]),
                       "dP_dOmega": float(img.sum()),
                       "statuses": np.bincount(st.cpu().numpy().ravel(), minlength=8).tolist()}))
+
+
+def adjoint(a, dev):
+    from . import flux
+    kw = I.stars_config1()[0]
+    kw.update(m_a_eV=1e-5)
+    p = torch.tensor([kw["m_a_eV"], kw["B0_G"], kw["theta_m"], kw["M_sun"], kw["R_km"], 1.1],
+                     dtype=torch.float64)
+    grad = torch.empty(6, dtype=torch.float64, device=dev)
+    F2 = torch.empty(1, dtype=torch.float64, device=dev)
+    uw = torch.from_numpy(I.sample_uniforms(4, 256)).to(dev)
+    Fw, nw, sw, iw, ow = flux.flux_forward(p, kw, uw, 4.0)
+    rt.rt_flux_gradient(sw, 256, uw, nw, iw, 4.0, grad, F2, opts=ow)      # warm-up
+    u = torch.from_numpy(I.sample_uniforms(4, a.n)).to(dev)
+    F, nacc, star, incl, opts = flux.flux_forward(p, kw, u, 4.0)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    nb = rt.rt_flux_gradient(star, a.n, u, nacc, incl, 4.0, grad, F2, counters=ctr, opts=opts)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "adjoint", "rays": a.n, "gradient_ms": e0.elapsed_time(e1),
+                      "replayed_attempts": int(ctr.cpu()[0]), "checkpoint_bytes": nb,
+                      "F": float(F.cpu()[0]), "grad": grad.cpu().tolist()}))
 
 
 if __name__ == "__main__":
