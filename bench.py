@@ -48,6 +48,26 @@ SMS, CLK = 152, 2.070e9
 PEAK_FP64 = SMS * 4 * CLK
 PEAK_FP32 = SMS * 256 * CLK
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace launch
+# of this workload, from a single-pass ncu launch list of
+# `bench.py --steps 1 --warmup 3 --no-cpu-baseline --no-backward --no-adjoint
+# --no-uneven`, valid for the kernel sources with the given SHA-256 prefix
+# (reported as null once they change).  Writes stay in L2 during the launch.
+TRAFFIC = {
+    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu"), "ed1b264d47d5e841", 35.91e6),
+    "mixed": (("rt_device.cuh", "rt_trace_mixed.cu"), "cb241f2535c0a607", 36.36e6),
+}
+
+
+def _traffic(prec):
+    import hashlib
+    files, digest, nbytes = TRAFFIC[prec]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2309_08655_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest()[:16] == digest else None
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -305,14 +325,14 @@ def run_ours(args):
             flops = attempts * fl[1] + rays_launch * fl[2]
             roof = {"kernel": "trace_fp64_kernel", "bound": "alu", "achieved": flops / t_tr / 1e12,
                     "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP64, "traffic": None,
+                    "frac": flops / t_tr / PEAK_FP64, "traffic": _traffic("fp64"),
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
         else:
             flops = (attempts - promoted_attempts) * fl[1] + rays_launch * fl[2]
             roof = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)",
                     "bound": "alu", "achieved": flops / t_tr / 1e12,
                     "peak": PEAK_FP32 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP32, "traffic": None,
+                    "frac": flops / t_tr / PEAK_FP32, "traffic": _traffic("mixed"),
                     "peak_source": "derived: 152 SMs x 256 FP32 flop/clk x 2070 MHz",
                     "promoted_rays_per_step": c_sum[4] / args.steps,
                     "promoted_fp64_attempts_per_step": promoted_attempts}
