@@ -217,8 +217,8 @@ __device__ void step_adjoint(const RayConst<double>& c, const double* y, double 
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         xd[i] = y[i] + mid * (r2v[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-      const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
-      if (rd < r_out) lo = mid; else hi = mid;
+      const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+      if (rd2 < r_out * r_out) lo = mid; else hi = mid;
     }
     const double th = 0.5 * (lo + hi);
     const double al = th, be = th * (1.0 - th), ga = th * th * (1.0 - th),

@@ -18,8 +18,23 @@ __device__ __forceinline__ void rhs64(const RayConst<double>& c, const double* y
   ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
 }
 
+// err^(-1/5) to within an ulp or two: a single-precision estimate refined by
+// two Newton steps on y^-5 = err, y <- y (6 - err y^5) / 5 (quadratic
+// convergence: 1e-7, 1e-14, rounding).  Used where the result is clamped to
+// [0.2, 5] after the factor 0.9, i.e. for err in [1.9e-4, 1.9e3].
+__device__ __forceinline__ double pow_m1_5(double err) {
+  double y = (double)exp2f(-0.2f * log2f((float)err));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double y2 = y * y;
+    y = y * (1.2 - 0.2 * err * (y2 * y2 * y));
+  }
+  return y;
+}
+
 __device__ __forceinline__ double step_factor(double err, bool accepted, bool last_rej) {
-  double fac = (err > 0.0) ? 0.9 * pow(err, -0.2) : 5.0;
+  // outside [1e-6, 1e6] the clamp below decides: 0.9 err^-0.2 > 5 or < 0.2
+  double fac = (err > 1e6) ? 0.0 : (err >= 1e-6) ? 0.9 * pow_m1_5(err) : 5.0;
   fac = fmin(5.0, fmax(0.2, fac));
   if (!accepted || last_rej) fac = fmin(fac, 1.0);
   return fac;
@@ -154,18 +169,44 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
       r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
                    DP::d6 * k6[i] + DP::d7 * k7[i]);
     }
-    double lo = 0.0, hi = 1.0;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
+    // largest th with the start side on the continuous extension: Illinois
+    // (regula falsi with halving) on s(th) = sig (3 z (m.x) - m_z |x|^2), whose
+    // sign is the side, bracketed on [0, 1]; a bisection step whenever the
+    // bracket did not halve, to the last representable th
+    const double sgn = L.c.sig;
+    auto side_val = [&](double th) {
       double xd[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        xd[i] = y[i] + mid * (r2[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-      if (L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, xd[0], xd[1], xd[2]) >= 0.0)
+        xd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+      const double mx = L.c.m0 * xd[0] + L.c.m1 * xd[1] + L.c.m2 * xd[2];
+      const double rr = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+      return sgn * (3.0 * xd[2] * mx - L.c.m2 * rr);
+    };
+    double lo = 0.0, hi = 1.0;
+    double flo = side_val(0.0), fhi = side_val(1.0);
+    if (!(flo >= 0.0)) flo = 0.0;                  // the start is on its own side
+    if (!(fhi < 0.0)) fhi = -1e-300;
+    int last = 0;
+    double width = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double mid = (lo * fhi - hi * flo) / (fhi - flo);
+      if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
+      if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (it & 1) width = hi - lo;
+      const double fm = side_val(mid);
+      if (fm >= 0.0) {
         lo = mid;
-      else
+        flo = fm;
+        if (last > 0) fhi *= 0.5;
+        last = 1;
+      } else {
         hi = mid;
+        fhi = fm;
+        if (last < 0) flo *= 0.5;
+        last = -1;
+      }
     }
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
@@ -203,8 +244,8 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
 #pragma unroll
         for (int i = 0; i < 3; ++i)
           xd[i] = y[i] + mid * (t[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-        const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
-        if (rd < p.r_out) lo = mid; else hi = mid;
+        const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+        if (rd2 < p.r_out * p.r_out) lo = mid; else hi = mid;
       }
       const double th = 0.5 * (lo + hi);
 #pragma unroll

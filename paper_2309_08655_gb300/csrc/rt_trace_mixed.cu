@@ -345,8 +345,8 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
         if (mid <= lo || mid >= hi) break;
         double xd[3];
         dense_x(L, h, mid, sR, r3, r4, r5, xd);
-        const double rd = sqrt(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
-        if (rd < p.r_out) lo = mid; else hi = mid;
+        const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+        if (rd2 < p.r_out * p.r_out) lo = mid; else hi = mid;
       }
       const float th = 0.5f * (lo + hi);
       double xd[3];
