@@ -54,19 +54,22 @@ PEAK_FP32 = SMS * 256 * CLK
 # --no-uneven`, valid for the kernel sources with the given SHA-256 prefix
 # (reported as null once they change).  Writes stay in L2 during the launch.
 TRAFFIC = {
-    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu"), "ed1b264d47d5e841", 35.91e6),
-    "mixed": (("rt_device.cuh", "rt_trace_mixed.cu"), "cb241f2535c0a607", 36.36e6),
+    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu"), "ec0274833a6ff00c",
+             {1: 35.5e6, 3: 141.2e6}),
+    "mixed": (("rt_device.cuh", "rt_trace_mixed.cu"), "b83e6145461ffe2a",
+              {1: 36.4e6, 3: 131.0e6}),
 }
 
 
-def _traffic(prec):
+def _traffic(prec, steps_per_launch=1):
     import hashlib
-    files, digest, nbytes = TRAFFIC[prec]
+    files, digest, by_steps = TRAFFIC[prec]
+    nbytes = by_steps.get(steps_per_launch)
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2309_08655_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return nbytes if h.hexdigest()[:16] == digest else None
+    return nbytes if (nbytes is not None and h.hexdigest()[:16] == digest) else None
 
 
 def _args():
@@ -406,7 +409,7 @@ def run_ours(args):
             peak, kern = PEAK_FP32, "trace_mixed_kernel (+ FP64 pass for promoted rays)"
         roof = dict(res[prec]["roofline"])
         roof.update({"kernel": kern, "achieved": flops / t_tr / 1e12, "frac": flops / t_tr / peak,
-                     "traffic": None, "attempts_per_launch": attempts,
+                     "traffic": _traffic(prec, K), "attempts_per_launch": attempts,
                      "trace_ms_per_launch": 1e3 * t_tr, "steps_per_launch": K})
         hp = P.hist.cpu().numpy()
         same = all(np.array_equal(hp[k * nsub:(k + 1) * nsub], hists[prec]) for k in range(K))

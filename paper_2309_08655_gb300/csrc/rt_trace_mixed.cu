@@ -50,6 +50,23 @@ __device__ __forceinline__ void rhs32c(const RayConst<float>& c, const double* m
                              f[0], f[1], f[2], f[3], f[4], f[5], F);
 }
 
+// The same at a stage point x0 + d given in FP32 (xf = x0 + d rounded), with
+// F expanded about the step's start x0: F(x0 + d) = F0 + gF.d + 3 d_z (m.d)
+// - m_z |d|^2, F0 and gF = grad F(x0) formed once per step in FP64.  The FP32
+// terms carry an absolute error ~ eps32 |x| |d|, as the FP64 evaluation at a
+// point whose increment d went through FP32 does.
+__device__ __forceinline__ void rhs32s(const RayConst<float>& c, float F0, const float* gF,
+                                       const float* xf, const float* d, const float* kf,
+                                       float* f) {
+  const float md = c.m0 * d[0] + c.m1 * d[1] + c.m2 * d[2];
+  const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const float F = F0 + (gF[0] * d[0] + gF[1] * d[1] + gF[2] * d[2]) +
+                  (3.0f * d[2] * md - c.m2 * dd);
+  const float r2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
+  ham_rhs<float, true, true>(c, xf[0], xf[1], xf[2], kf[0], kf[1], kf[2], f[0], f[1], f[2], f[3],
+                             f[4], f[5], F * __frcp_rn(r2));
+}
+
 __device__ __forceinline__ float side_md(const double* md, double x0, double x1, double x2) {
   return (float)gj_side<double>(md[0], md[1], md[2], x0, x1, x2);
 }
@@ -217,16 +234,26 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
     R1[i] = L.f0[i];
     K1[i] = L.f0[3 + i];
   }
-  float t[6], f[6], dks[3];
-  double xs[3];
+  // null-cone factor F = 3 z (m.x) - m_z |x|^2 and its gradient at the start, FP64
+  float F0 = 0.0f, gF[3] = {0.0f, 0.0f, 0.0f};
+  if (L.c.plasma == PLASMA_GJ) {
+    const double mx = L.md[0] * L.y[0] + L.md[1] * L.y[1] + L.md[2] * L.y[2];
+    const double r2d = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
+    F0 = (float)(3.0 * L.y[2] * mx - L.md[2] * r2d);
+    gF[0] = (float)(3.0 * L.y[2] * L.md[0] - 2.0 * L.md[2] * L.y[0]);
+    gF[1] = (float)(3.0 * L.y[2] * L.md[1] - 2.0 * L.md[2] * L.y[1]);
+    gF[2] = (float)(3.0 * mx + 3.0 * L.y[2] * L.md[2] - 2.0 * L.md[2] * L.y[2]);
+  }
+  float t[6], f[6], dks[3], dx[3], xs[3];
 #define RT_STAGE(Rout, Kout, cj, SUMR, SUMK)                                          \
   {                                                                                   \
     _Pragma("unroll") for (int i = 0; i < 3; ++i) {                                   \
       dks[i] = h * (SUMK);                                                            \
-      xs[i] = L.y[i] + (double)(2.0f * h * (float)(cj) * yf[3 + i] + h * (SUMR));     \
+      dx[i] = 2.0f * h * (float)(cj) * yf[3 + i] + h * (SUMR);                        \
+      xs[i] = yf[i] + dx[i];                                                          \
       t[3 + i] = yf[3 + i] + dks[i];                                                  \
     }                                                                                 \
-    rhs32c(L.c, L.md, xs, t + 3, f);                                                  \
+    rhs32s(L.c, F0, gF, xs, dx, t + 3, f);                                            \
     _Pragma("unroll") for (int i = 0; i < 3; ++i) {                                   \
       Rout[i] = 2.0f * dks[i] + f[i];                                                 \
       Kout[i] = f[3 + i];                                                             \
@@ -265,7 +292,9 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   float fn[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) t[i] = (float)yn[i];
-  rhs32c(L.c, L.md, yn, t + 3, fn);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dx[i] = 2.0f * h * yf[3 + i] + sR[i];
+  rhs32s(L.c, F0, gF, t, dx, t + 3, fn);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     R7[i] = 2.0f * dK[i] + fn[i];
