@@ -120,6 +120,13 @@ typedef struct {
  *   block             threads per block of the persistent kernel (0 = auto, or
  *                     the batch's autotuned value, rt_batch_autotune)
  *   blocks_per_sm     resident blocks per SM for the persistent grid (0 = auto)
+ *   tail              0: FP64 tracing parks the rays of warps left with at most 5
+ *                     rays once the queue has drained and continues them six lanes
+ *                     per ray (one lane per state component); results agree with
+ *                     the one-lane-per-ray path to rounding.  1: one lane per ray
+ *                     throughout.  The handle owns the park buffer (allocated on
+ *                     first use, 5.4 MB on GB300).
+ *   reserved          must be 0
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),
@@ -130,7 +137,7 @@ typedef struct {
  */
 typedef struct {
   double rtol, atol, r_out_over_R, lambda_max, r_capture_over_R;
-  int32_t precision, max_steps, block, blocks_per_sm;
+  int32_t precision, max_steps, block, blocks_per_sm, tail, reserved;
   uint64_t* timestamps;
 } rt_trace_opts;
 

@@ -77,6 +77,8 @@ struct rt_star {
   int device = 0;
   double wp2_surface_max = 0.0;
   bool empty = false;
+  double* d_park = nullptr;     // tail-mode park buffer (allocated on first use)
+  int64_t park_cap = 0;
 };
 
 extern "C" {
@@ -191,6 +193,7 @@ void rt_destroy_star(rt_star* s) {
   if (cur != s->device) cudaSetDevice(s->device);
   if (s->d_bins) cudaFree(s->d_bins);
   if (s->d_queue) cudaFree(s->d_queue);
+  if (s->d_park) cudaFree(s->d_park);
   if (cur != s->device) cudaSetDevice(cur);
   delete s;
 }
@@ -232,6 +235,36 @@ rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double
   return s->empty ? RT_EEMPTY_SURFACE : RT_OK;
 }
 
+// The tail-mode park buffer: two counters, then park_capacity entries.
+static rt_status ensure_park(double** buf, int64_t* cap) {
+  if (*buf) return RT_OK;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t c = rtk::park_capacity(nsm > 0 ? nsm : 1);
+  void* p = nullptr;
+  if (cudaMalloc(&p, 256 + (size_t)c * rtk::PARKREC * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RT_ENOMEM, "cannot allocate the tail-mode park buffer");
+  }
+  *buf = (double*)p;
+  *cap = c;
+  return RT_OK;
+}
+
+static void set_park(rtk::TraceParams& p, double* buf, int64_t cap, const rt_trace_opts* o) {
+  if (o->tail == 0 && buf) {
+    p.park_count = (unsigned long long*)buf;
+    p.park_next = p.park_count + 1;
+    p.park = buf + 32;           // after the 256-byte counter block
+    p.park_cap = cap;
+  } else {
+    p.park = nullptr;
+    p.park_count = p.park_next = nullptr;
+    p.park_cap = 0;
+  }
+}
+
 static rt_status check_opts(const rt_trace_opts* o) {
   if (!o) return fail(RT_EINVAL, "opts is NULL");
   if (!(o->rtol > 0 && o->rtol < 1) || !(o->atol > 0 && o->atol < 1))
@@ -246,6 +279,8 @@ static rt_status check_opts(const rt_trace_opts* o) {
   if (o->precision != RT_PREC_FP64 && o->precision != RT_PREC_MIXED)
     return fail(RT_EINVAL, "unknown precision %d", o->precision);
   if (o->block < 0 || o->blocks_per_sm < 0) return fail(RT_EINVAL, "negative launch parameter");
+  if (o->tail != 0 && o->tail != 1) return fail(RT_EINVAL, "tail must be 0 or 1");
+  if (o->reserved != 0) return fail(RT_EINVAL, "reserved must be 0");
   return RT_OK;
 }
 
@@ -276,6 +311,13 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.counters = d_counters;
   p.queue = s->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
+  if (o->tail == 0 && o->lambda_max == 0.0) {
+    rt_star* sm = const_cast<rt_star*>(s);
+    if ((st = ensure_park(&sm->d_park, &sm->park_cap)) != RT_OK) return st;
+    set_park(p, sm->d_park, sm->park_cap, o);
+  } else {
+    set_park(p, nullptr, 0, o);
+  }
   p.rtol = o->rtol;
   p.atol = o->atol;
   p.r_out = o->r_out_over_R;
@@ -595,6 +637,8 @@ struct rt_batch {
   bool all_empty = true;
   int tuned_block[2] = {0, 0};        // autotuned launch shape per precision (0 = default)
   int tuned_bps[2] = {0, 0};
+  double* d_park = nullptr;           // tail-mode park buffer (allocated on first use)
+  int64_t park_cap = 0;
 };
 
 extern "C" {
@@ -649,6 +693,7 @@ void rt_destroy_batch(rt_batch* b) {
   if (cur != b->device) cudaSetDevice(b->device);
   if (b->d_bins) cudaFree(b->d_bins);
   if (b->d_queue) cudaFree(b->d_queue);
+  if (b->d_park) cudaFree(b->d_park);
   if (cur != b->device) cudaSetDevice(cur);
   delete b;
 }
@@ -705,6 +750,12 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.counters = d_counters;
   p.queue = b->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
+  if (o->tail == 0 && o->lambda_max == 0.0) {
+    if ((st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
+    set_park(p, b->d_park, b->park_cap, o);
+  } else {
+    set_park(p, nullptr, 0, o);
+  }
   p.rtol = o->rtol;
   p.atol = o->atol;
   p.r_out = o->r_out_over_R;
@@ -829,6 +880,7 @@ rt_status rt_batch_graph_create(rt_batch* b, const double* d_u, double* d_state,
   if ((st = check_opts(o)) != RT_OK) return st;
   if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
   if ((st = ensure_batch_bins(b, nth, nph, nnu, nullptr)) != RT_OK) return st;
+  if (o->tail == 0 && (st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
@@ -960,6 +1012,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   p.counters = nullptr;
   p.queue = queue;
   p.ts = nullptr;
+  set_park(p, nullptr, 0, o);
   p.rtol = o->rtol;
   p.atol = o->atol;
   p.r_out = o->r_out_over_R;

@@ -461,6 +461,7 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
   tp.r_capture = P.r_capture;
   tp.max_steps = P.max_steps;
   tp.ts = nullptr;
+  tp.park = nullptr;
   // forward replay with a checkpoint every CK accepted steps
   const int64_t c0 = P.ck_off[i];
   const int64_t cmax = P.ck_off[i + 1] - c0;

@@ -25,7 +25,17 @@ struct TraceParams {
   int max_steps;
   int claim_status;           // rays with this status are traced (READY, or PROMOTED)
   unsigned long long* ts;     // optional: [0] launch start (min), [1 + star] last finish (max)
+  // tail mode (FP64): rays of warps left with <= PARK_LIVE_MAX rays once the
+  // queue has drained are parked here and continued six lanes per ray
+  double* park;               // park_cap entries of PARKREC doubles (NULL: no parking)
+  unsigned long long* park_count;
+  unsigned long long* park_next;
+  int64_t park_cap;
 };
+constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lambda
+constexpr int PARK_LIVE_MAX = 5;
+// Park capacity that covers any persistent grid on the device.
+inline int64_t park_capacity(int nsm) { return (int64_t)nsm * (2048 / 32) * PARK_LIVE_MAX; }
 
 // Per-call counters (int64): accepted steps, rejected steps, rays finished,
 // rays escaped, rays promoted from FP32 to FP64, FP64 steps of promoted rays,
@@ -66,6 +76,7 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
                               cudaStream_t stream);
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
                                cudaStream_t stream);
+cudaError_t launch_tail_fp64(const TraceParams& p, cudaStream_t stream);
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
 // Resident blocks per SM of the trace kernels at a block size.
 cudaError_t occupancy_fp64(int block, int* occ);

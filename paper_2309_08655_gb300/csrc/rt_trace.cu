@@ -111,6 +111,31 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
     }
     const unsigned live = __ballot_sync(FULL, ray != -2);
     if (live == 0) break;
+    if (p.park) {
+      // the queue has drained and this warp holds few rays: park them for the
+      // six-lanes-per-ray tail kernel (the complete integrator state)
+      const unsigned has = __ballot_sync(FULL, ray >= 0);
+      const unsigned drained = __ballot_sync(FULL, ray == -2);
+      if (drained && has && __popc(has) <= PARK_LIVE_MAX && ray >= 0) {
+        const unsigned long long slot = atomicAdd(p.park_count, 1ull);
+        if (slot < (unsigned long long)p.park_cap) {
+          double* pe = p.park + slot * PARKREC;
+#pragma unroll
+          for (int j = 0; j < 6; ++j) pe[j] = L.y[j];
+          pe[6] = L.h;
+          pe[7] = L.h_resume;
+          pe[8] = L.c.sig;
+          pe[9] = (double)((L.last_rej ? 1 : 0) | (L.switching ? 2 : 0));
+          pe[10] = (double)L.na;
+          pe[11] = (double)L.nr;
+          pe[12] = (double)ray;
+          pe[13] = L.lam;
+          acc += L.na - na0;
+          rej += L.nr - nr0;
+          ray = -2;
+        }
+      }
+    }
     if (ray >= 0) {
       NoHook nh;
       const int st = advance(p, L, nh);
@@ -389,6 +414,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   tp.r_capture = bp.r_capture;
   tp.max_steps = bp.max_steps;
   tp.ts = nullptr;
+  tp.park = nullptr;
   int64_t pix = -1;
   Lane L;
   CrossingHook hk;
@@ -540,8 +566,14 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
   if (grid < 1) grid = 1;
   e = cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
+  if (p.park) {
+    e = cudaMemsetAsync(p.park_count, 0, 2 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+  }
   trace_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(p);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !p.park) return e;
+  return launch_tail_fp64(p, stream);
 }
 
 }  // namespace rtk

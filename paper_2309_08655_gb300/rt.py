@@ -40,7 +40,8 @@ class rt_star_params(ctypes.Structure):
 class rt_trace_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in [
         "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
-        (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm"]] + [
+        (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm", "tail",
+                                      "reserved"]] + [
         ("timestamps", ctypes.c_void_p)]
 
 
@@ -173,7 +174,7 @@ def make_params(**kw) -> rt_star_params:
 
 def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capture_over_R=1.0,
               precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0,
-              timestamps=None) -> rt_trace_opts:
+              timestamps=None, tail=0) -> rt_trace_opts:
     o = rt_trace_opts()
     o.rtol = rtol
     o.atol = rtol if atol is None else atol
@@ -184,6 +185,8 @@ def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capt
     o.max_steps = max_steps
     o.block = block
     o.blocks_per_sm = blocks_per_sm
+    o.tail = tail
+    o.reserved = 0
     o.timestamps = _ptr(timestamps)
     return o
 

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layouts_match_header():
     # 10 doubles, 8 int32, 1 double / 5 doubles, 4 int32 (no padding surprises)
     assert ctypes.sizeof(rt.rt_star_params) == 10 * 8 + 8 * 4 + 8
-    assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 4 * 4 + 8   # + the timestamps pointer
+    assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 6 * 4 + 8   # + the timestamps pointer
     assert rt.rt_star_params.plasma_a.offset == 112
 
 

@@ -1,7 +1,9 @@
 """Batched persistent launch over several stars with uneven ray counts: the
 batch path (one sampling pass per star, ONE trace launch over all stars, per
-star histograms) reproduces the single-star path bit for bit in FP64, and
-agrees with the oracle on the sampled states."""
+star histograms) reproduces the single-star path bit for bit in FP64 with one
+lane per ray throughout (tail = 1), and to rounding with the six-lane tail
+mode (which rays are parked depends on the launch), and agrees with the
+oracle on the sampled states."""
 import numpy as np
 import pytest
 
@@ -32,7 +34,8 @@ def _setup():
     return stars_kw, counts, us
 
 
-def test_batch_equals_single_star_path_bitwise(oracle):
+@pytest.mark.parametrize("tail", [1, 0])
+def test_batch_equals_single_star_path(oracle, tail):
     stars_kw, counts, us = _setup()
     dev = torch.device("cuda:0")
     N = sum(counts)
@@ -44,7 +47,7 @@ def test_batch_equals_single_star_path_bitwise(oracle):
     s = torch.empty(N, dtype=torch.uint8, device=dev)
     assert rt.rt_sample_batch(batch, u_all, st, w, s) == rt.RT_OK
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
-    rt.rt_trace_batch(batch, st, s, counters=ctr, opts=rt.make_opts(rtol=1e-10))
+    rt.rt_trace_batch(batch, st, s, counters=ctr, opts=rt.make_opts(rtol=1e-10, tail=tail))
     hist = torch.empty((len(stars),) + NB, dtype=torch.float64, device=dev)
     oor = torch.empty(len(stars), dtype=torch.float64, device=dev)
     rt.rt_bin_batch(batch, st, w, s, *NB, 0.0, 9.0, hist, oor)
@@ -54,13 +57,24 @@ def test_batch_equals_single_star_path_bitwise(oracle):
     traced = 0
     for j, kw in enumerate(stars_kw):
         star, st1, w1, s1, _ = G.gpu_sample(kw, us[j])
-        G.gpu_trace(star, st1, s1, rtol=1e-10)
+        G.gpu_trace(star, st1, s1, rtol=1e-10, tail=tail)
         h1 = G.gpu_bin(star, st1, w1, s1, *NB)[0]
         a, b = off[j], off[j + 1]
-        assert np.array_equal(st_b[:, a:b], st1.cpu().numpy())
-        assert np.array_equal(s_b[a:b], s1.cpu().numpy())
         assert np.array_equal(w_b[a:b], w1.cpu().numpy())
-        assert np.array_equal(h_b[j], h1)
+        if tail == 1:
+            assert np.array_equal(st_b[:, a:b], st1.cpu().numpy())
+            assert np.array_equal(s_b[a:b], s1.cpu().numpy())
+            assert np.array_equal(h_b[j], h1)
+        else:
+            s1n = s1.cpu().numpy()
+            same = s_b[a:b] == s1n
+            assert same.mean() > 0.99
+            tr = same & (s1n != rt.RAY_NO_ROOT)
+            if tr.any():
+                d = G.rel_state_diff(st_b[:, a:b][:, tr], st1.cpu().numpy()[:, tr])
+                assert np.median(d) < 1e-12
+            if h1.sum() > 0:
+                assert np.abs(h_b[j] - h1).sum() / h1.sum() < 1e-4
         traced += int((s1.cpu().numpy() != rt.RAY_NO_ROOT).sum())
         # sampled states agree with the oracle
         so, wo, sto = oracle.sample(oracle.star_vector(**kw), us[j])
