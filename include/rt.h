@@ -123,9 +123,10 @@ typedef struct {
  *   tail              0: FP64 tracing parks the rays of warps left with at most 5
  *                     rays once the queue has drained and continues them six lanes
  *                     per ray (one lane per state component); results agree with
- *                     the one-lane-per-ray path to rounding.  1: one lane per ray
+ *                     the one-lane-per-ray path to rounding.  2-31: the same with
+ *                     that many rays as the threshold.  1: one lane per ray
  *                     throughout.  The handle owns the park buffer (allocated on
- *                     first use, 5.4 MB on GB300).
+ *                     first use, 33 MB on GB300).
  *   reserved          must be 0
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global

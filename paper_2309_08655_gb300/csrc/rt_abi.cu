@@ -253,11 +253,12 @@ static rt_status ensure_park(double** buf, int64_t* cap) {
 }
 
 static void set_park(rtk::TraceParams& p, double* buf, int64_t cap, const rt_trace_opts* o) {
-  if (o->tail == 0 && buf) {
+  if (o->tail != 1 && buf) {
     p.park_count = (unsigned long long*)buf;
     p.park_next = p.park_count + 1;
     p.park = buf + 32;           // after the 256-byte counter block
     p.park_cap = cap;
+    p.park_live = (o->tail == 0) ? rtk::PARK_LIVE_MAX : o->tail;
   } else {
     p.park = nullptr;
     p.park_count = p.park_next = nullptr;
@@ -279,7 +280,7 @@ static rt_status check_opts(const rt_trace_opts* o) {
   if (o->precision != RT_PREC_FP64 && o->precision != RT_PREC_MIXED)
     return fail(RT_EINVAL, "unknown precision %d", o->precision);
   if (o->block < 0 || o->blocks_per_sm < 0) return fail(RT_EINVAL, "negative launch parameter");
-  if (o->tail != 0 && o->tail != 1) return fail(RT_EINVAL, "tail must be 0 or 1");
+  if (o->tail < 0 || o->tail > 31) return fail(RT_EINVAL, "tail must be in [0, 31]");
   if (o->reserved != 0) return fail(RT_EINVAL, "reserved must be 0");
   return RT_OK;
 }
@@ -311,7 +312,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.counters = d_counters;
   p.queue = s->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail == 0 && o->lambda_max == 0.0) {
+  if (o->tail != 1 && o->lambda_max == 0.0) {
     rt_star* sm = const_cast<rt_star*>(s);
     if ((st = ensure_park(&sm->d_park, &sm->park_cap)) != RT_OK) return st;
     set_park(p, sm->d_park, sm->park_cap, o);
@@ -750,7 +751,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.counters = d_counters;
   p.queue = b->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail == 0 && o->lambda_max == 0.0) {
+  if (o->tail != 1 && o->lambda_max == 0.0) {
     if ((st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
     set_park(p, b->d_park, b->park_cap, o);
   } else {
@@ -880,7 +881,7 @@ rt_status rt_batch_graph_create(rt_batch* b, const double* d_u, double* d_state,
   if ((st = check_opts(o)) != RT_OK) return st;
   if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
   if ((st = ensure_batch_bins(b, nth, nph, nnu, nullptr)) != RT_OK) return st;
-  if (o->tail == 0 && (st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
+  if (o->tail != 1 && (st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");

@@ -31,11 +31,13 @@ struct TraceParams {
   unsigned long long* park_count;
   unsigned long long* park_next;
   int64_t park_cap;
+  int park_live;              // park when a drained warp holds at most this many rays
 };
 constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lambda
 constexpr int PARK_LIVE_MAX = 5;
-// Park capacity that covers any persistent grid on the device.
-inline int64_t park_capacity(int nsm) { return (int64_t)nsm * (2048 / 32) * PARK_LIVE_MAX; }
+// Park capacity that covers any persistent grid on the device (up to 31 rays
+// per warp).
+inline int64_t park_capacity(int nsm) { return (int64_t)nsm * (2048 / 32) * 31; }
 
 // Per-call counters (int64): accepted steps, rejected steps, rays finished,
 // rays escaped, rays promoted from FP32 to FP64, FP64 steps of promoted rays,

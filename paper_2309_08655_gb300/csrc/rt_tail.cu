@@ -75,35 +75,30 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp)
     P = c.pa * ir2 * ir;
     dPj = -3.0 * P * ir * nj;
   }
+  // the anisotropic scalars both kinds of component use, once
+  const bool aniso = (c.disp != DISP_ISO);
+  double ib = 0.0, sA = 0.0, U = 0.0, Kp = 0.0, fac = 0.0, opsA = 0.0;
+  if (aniso) {
+    ib = rsqrt(3.0 * mu * mu + 1.0);
+    sA = A * qA;
+    const double km = k0 * c.m0 + k1 * c.m1 + k2 * c.m2;
+    U = 3.0 * mu * kr - km + 2.0 * mu * kr * (sA - 1.0);
+    Kp = U * ib;
+    fac = P * A * Kp * c.iW2;
+    opsA = 1.0 + 2.0 * sA;
+  }
   if (comp < 3) {
     double g = 2.0 * (kj + Am1 * kr * nj);
-    if (c.disp != DISP_ISO) {
-      const double ib = rsqrt(3.0 * mu * mu + 1.0);
-      const double sA = A * qA;
-      const double km = k0 * c.m0 + k1 * c.m1 + k2 * c.m2;
-      const double U = 3.0 * mu * kr - km + 2.0 * mu * kr * (sA - 1.0);
-      const double Kp = U * ib;
-      const double fac = P * A * Kp * c.iW2;
-      const double c1 = mu * (1.0 + 2.0 * sA);
-      const double g2 = -2.0 * fac * ib;
-      g += g2 * (c1 * nj - mj);
-    }
+    if (aniso) g += (-2.0 * fac * ib) * (mu * opsA * nj - mj);
     return g;
   }
   const double cA = (W * iA + kr * kr) * c.rs * ir2;
   const double ckr = 2.0 * Am1 * kr * ir;
   double gx = cA * nj + ckr * (kj - kr * nj);
-  if (c.disp == DISP_ISO) {
+  if (!aniso) {
     gx += dPj;
   } else {
-    const double ib = rsqrt(3.0 * mu * mu + 1.0);
-    const double sA = A * qA;
-    const double km = k0 * c.m0 + k1 * c.m1 + k2 * c.m2;
-    const double U = 3.0 * mu * kr - km + 2.0 * mu * kr * (sA - 1.0);
-    const double Kp = U * ib;
     const double Kp2iW2 = Kp * Kp * c.iW2;
-    const double fac = P * A * Kp * c.iW2;
-    const double opsA = 1.0 + 2.0 * sA;
     const double ib3 = ib * ib * ib;
     const double a1 = ib * opsA * kr - 3.0 * mu * U * ib3;
     const double a2 = ib * opsA * mu;

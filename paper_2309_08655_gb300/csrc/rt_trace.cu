@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       // six-lanes-per-ray tail kernel (the complete integrator state)
       const unsigned has = __ballot_sync(FULL, ray >= 0);
       const unsigned drained = __ballot_sync(FULL, ray == -2);
-      if (drained && has && __popc(has) <= PARK_LIVE_MAX && ray >= 0) {
+      if (drained && has && __popc(has) <= p.park_live && ray >= 0) {
         const unsigned long long slot = atomicAdd(p.park_count, 1ull);
         if (slot < (unsigned long long)p.park_cap) {
           double* pe = p.park + slot * PARKREC;
