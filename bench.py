@@ -45,16 +45,18 @@ NBINS = (64, 32, 128)
 # 152 SMs x 2070 MHz; FP64 4 flop/clk/SM (1.26 TFLOP/s, the nominal GB300
 # FP64 rate); FP32 128 lanes x 2 flop/clk/SM (80.5 TFLOP/s).
 SMS, CLK = 152, 2.070e9
+FP64_KERNELS = "trace_fp64_kernel + tail_fp64_kernel (one trace call)"
 PEAK_FP64 = SMS * 4 * CLK
 PEAK_FP32 = SMS * 256 * CLK
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace launch
-# of this workload, from a single-pass ncu launch list of
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace call
+# of this workload (FP64: the persistent trace launch plus its six-lane tail
+# launch), from a single-pass ncu launch list of
 # `bench.py --steps 1 --warmup 3 --no-cpu-baseline --no-backward --no-adjoint
 # --no-uneven`, valid for the kernel sources with the given SHA-256 prefix
 # (reported as null once they change).  Writes stay in L2 during the launch.
 TRAFFIC = {
-    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu"), "ec0274833a6ff00c",
+    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu", "rt_tail.cu"), "ec0274833a6ff00c",
              {1: 35.5e6, 3: 141.2e6}),
     "mixed": (("rt_device.cuh", "rt_trace_mixed.cu"), "b83e6145461ffe2a",
               {1: 36.4e6, 3: 131.0e6}),
@@ -357,7 +359,7 @@ def run_ours(args):
         t_tr = statistics.mean(t_trace)
         if prec == "fp64":
             flops = attempts * fl[1] + rays_launch * fl[2]
-            roof = {"kernel": "trace_fp64_kernel", "bound": "alu", "achieved": flops / t_tr / 1e12,
+            roof = {"kernel": FP64_KERNELS, "bound": "alu", "achieved": flops / t_tr / 1e12,
                     "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
                     "frac": flops / t_tr / PEAK_FP64, "traffic": _traffic("fp64"),
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
@@ -382,7 +384,8 @@ def run_ours(args):
     hists = {p: res[p].pop("hist") for p in ("fp64", "mixed")}
     # continuous batching: the K steps' batches (16 sub-batches each) in one
     # persistent launch, so the bulk of later batches overlaps the long rays of
-    # earlier ones; the same work per step, results bitwise equal per step
+    # earlier ones; the same work per step (rays that finish in the six-lane
+    # tail kernel may differ from one launch per step by rounding)
     K = min(args.steps, 64)
     P = _Pipelined(rt, stars, nper, nsub, K, u, dev, stream, NBINS, cfg)
     for prec in ("fp64", "mixed"):
@@ -403,7 +406,7 @@ def run_ours(args):
         attempts = c[0] + c[1]
         if prec == "fp64":
             flops = attempts * fl[1] + c[2] * fl[2]
-            peak, kern = PEAK_FP64, "trace_fp64_kernel"
+            peak, kern = PEAK_FP64, FP64_KERNELS
         else:
             flops = (attempts - c[5]) * fl[1] + c[2] * fl[2]
             peak, kern = PEAK_FP32, "trace_mixed_kernel (+ FP64 pass for promoted rays)"
@@ -471,8 +474,8 @@ def run_ours(args):
                    "rtol": H["rtol"], "r_out_over_R": cfg["r_out_over_R"],
                    "max_steps": cfg["max_steps"], "bins": list(NBINS), "precision": head,
                    "launch": f"continuous batching: the {K} timed steps' 16 sub-batches each "
-                             f"in one persistent trace launch (per-step results bitwise equal "
-                             f"to one launch per step, whose numbers are under "
+                             f"in one persistent trace launch (per-step histograms compared "
+                             f"with one launch per step, whose numbers are under "
                              f"'{head}' -> 'ms_per_step')",
                    "l2": f"inputs larger than L2 ({K} x 117 MB) and L2 flushed (256 MiB "
                          f"write) before the timed region"},
@@ -512,7 +515,7 @@ def _uneven_leg(args, dev):
     """256 star/axion instances with ray counts log-uniform in [1e3, 1e6]:
     the 128 forward instances in one persistent launch (mixed precision,
     launch shape from the autotuner, sample -> trace -> bin captured in one
-    CUDA graph), the 128 backward images (FP64) on a second stream.  Latency
+    CUDA graph), the 128 backward images (mixed precision) on a second stream.  Latency
     of an instance = GPU global-timer stamp of its last ray or pixel minus the
     start of the first launch."""
     import numpy as np
@@ -552,7 +555,8 @@ def _uneven_leg(args, dev):
         img = torch.empty((side, side), dtype=torch.float64, device=dev)
         stt = torch.empty((side, side), dtype=torch.uint8, device=dev)
         bstars.append((sb, side, x["incl"], 1.3 * r_max))
-        bopts.append(rt.make_opts(rtol=1e-10, timestamps=ts_b[2 * j:2 * j + 2]))
+        bopts.append(rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED,
+                                  timestamps=ts_b[2 * j:2 * j + 2]))
         bufs.append((img, stt))
     s2 = torch.cuda.Stream()
     # warm-up: one replay of the forward graph
@@ -587,7 +591,7 @@ def _uneven_leg(args, dev):
     return {"workload": "uneven_256_instances_128fwd_128bwd", "instances": len(insts),
             "forward_rays": int(N), "backward_pixels": int(sum(b[1] ** 2 for b in bstars)),
             "empty_forward_instances": int(sum(1 for x in stars if x.info()["empty"])),
-            "precision": {"forward": "mixed (rtol 1e-8)", "backward": "fp64 (rtol 1e-10)"},
+            "precision": {"forward": "mixed (rtol 1e-8)", "backward": "mixed (rtol 1e-8)"},
             "autotuned": {"block": tune["block"], "blocks_per_sm": tune["blocks_per_sm"],
                           "candidates": len(tune["candidates_ms"])},
             "graph": "forward sample -> trace -> bin replayed from one CUDA graph",
@@ -636,22 +640,36 @@ def _adjoint_leg(args, dev):
     t_g = time.perf_counter() - t0
     g = grad.cpu().numpy()
     c = ctr.cpu().numpy()
+    # the same gradient with the backward sweep in FP32 (FP64 replay)
+    o32 = rt.make_opts(rtol=opts.rtol, precision=rt.PREC_MIXED)
+    rt.rt_flux_gradient(sw, 4096, uw, nw, iw, kappa, grad, F2, opts=o32)    # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rt.rt_flux_gradient(star, n, u, nacc, incl, kappa, grad, F2, opts=o32)
+    torch.cuda.synchronize()
+    t_g32 = time.perf_counter() - t0
+    g32 = grad.cpu().numpy()
+    err32 = np.abs(g32 - g) / np.abs(g)
     return {"workload": "adjoint_2^18_rays_ma1e-5_incl1.1_vmf_one_theta_bin",
             "precision": "fp64", "rays": n, "F_W_per_sr": float(F.cpu()[0]),
             "grad": dict(zip(flux.PARAM_NAMES, [float(x) for x in g])),
             "t_forward_s": t_f, "t_gradient_s": t_g, "adjoint_forward_ratio": t_g / t_f,
             "checkpoint_MiB": nbytes / 2 ** 20, "replayed_attempts": int(c[0]),
             "rays_left_out": int(c[4]),
-            "fp32_vs_fp64_gradient_error": None,
-            "note": "the adjoint runs in FP64 only; timings include sampling, both "
-                    "replays and the dual-number Jacobian products"}
+            "fp32_sweep": {"t_gradient_s": t_g32, "adjoint_forward_ratio": t_g32 / t_f,
+                           "grad": dict(zip(flux.PARAM_NAMES, [float(x) for x in g32]))},
+            "fp32_vs_fp64_gradient_error": dict(zip(flux.PARAM_NAMES,
+                                                    [float(x) for x in err32])),
+            "note": "forward trace and replays FP64; timings include sampling, both "
+                    "replays and the dual-number Jacobian products; fp32_sweep forms the "
+                    "backward sweep's stages, products and sums in FP32"}
 
 
 def _backward_leg(args, dev, stream, fl, rank):
     """Backward image plane: 1024 x 1024 pixels at inclination 60 deg, plane at
     1e4 R, impact parameters up to 50 R, on the aligned 200 km-surface star
-    (FP64, rtol 1e-10).  A seeded sample of pixels is recomputed by the oracle
-    on rank 0."""
+    (FP64, rtol 1e-10; and mixed precision, rtol 1e-8, compared with it).  A
+    seeded sample of the FP64 pixels is recomputed by the oracle on rank 0."""
     import numpy as np
     import torch
 
@@ -689,6 +707,36 @@ def _backward_leg(args, dev, stream, fl, rank):
                         "unit": "TFLOP/s", "frac": (c[0] + c[1]) * fl[1] / t / PEAK_FP64,
                         "traffic": None,
                         "note": "integrator flops only; the crossing search is not counted"}}
+    # the same image in mixed precision (FP32 stages, rtol 1e-8; FP64 crossing
+    # search, bisection and estimator; floor pixels re-traced in FP64)
+    om = rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED)
+    img_m = torch.empty_like(img)
+    st_m = torch.empty_like(st)
+    nc_m = torch.empty_like(nc)
+    rt.rt_trace_backward(star, 128, 128, incl, D, bmax, img_m, st_m, nc_m, None, opts=om,
+                         stream=stream)                                    # warm-up
+    torch.cuda.synchronize()
+    ctr.zero_()
+    e0.record(stream)
+    for _ in range(reps):
+        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img_m, st_m, nc_m, ctr, opts=om,
+                             stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tm = e0.elapsed_time(e1) / 1e3 / reps
+    cm = ctr.cpu().numpy() / reps
+    same = (nc_m == nc) & (st_m == st)
+    litm = same & (nc > 0)
+    relm = ((img_m - img).abs() / img.abs().clamp_min(1e-300))[litm]
+    out["mixed"] = {"rtol": 1e-8, "ms_per_image": 1e3 * tm, "pixels_per_s": nx * ny / tm,
+                    "ray_steps_per_s": cm[0] / tm, "accepted_steps": cm[0],
+                    "rejected_steps": cm[1], "pixels_to_fp64": cm[4], "crossings": cm[6],
+                    "dP_dOmega_W_per_sr": float(img_m.sum()),
+                    "total_rel_diff_vs_fp64": float(abs(img_m.sum() - img.sum()) / img.sum()),
+                    "pixels_same_crossings": float(same.double().mean()),
+                    "pixel_rel_diff_p50_p99": [float(torch.quantile(relm, q)) for q in (0.5, 0.99)]
+                    if relm.numel() else None,
+                    "speedup_vs_fp64": t / tm}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         img_h, nc_h = img.cpu().numpy(), nc.cpu().numpy()

@@ -270,9 +270,19 @@ rt_status rt_bin_spectrum(const rt_star* star, int64_t n, const double* d_state,
  *   d_ncross      out (may be NULL): ny x nx crossings counted (after the cut)
  *   d_counters    in/out (may be NULL): RT_COUNTERS int64 accumulated:
  *                 accepted steps, rejected steps, pixels finished, pixels
- *                 escaped, -, -, crossings counted
- *   opts          rtol, atol, r_capture_over_R, max_steps used (precision
- *                 must be RT_PREC_FP64); r_out_over_R, lambda_max ignored
+ *                 escaped, pixels handed from the FP32 to the FP64 kernel
+ *                 (RT_PREC_MIXED), -, crossings counted
+ *   opts          rtol, atol, r_capture_over_R, max_steps, precision used;
+ *                 r_out_over_R, lambda_max ignored
+ * The sign of g is decided in FP32 where it is certain (on shell, g has the
+ * sign of P G - 1 up to the integrator's drift, and that is formed in FP32
+ * with a wide margin), else in FP64; bisection and contributions are FP64.
+ * RT_PREC_FP64: FP64 stages.  RT_PREC_MIXED: FP32 stages with the FP64 state
+ * of the forward mixed kernel; the crossing search runs on the FP64
+ * reconstruction of each step's continuous extension; a pixel whose FP32
+ * error estimate sits on the rounding floor is traced again from the plane in
+ * FP64 (second kernel on the same stream; the first call with a larger image
+ * allocates a list of 4 B per pixel on the handle).
  * Deterministic.  Calls sharing one handle must be serialised on one stream.
  */
 rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double incl_rad,
@@ -298,7 +308,11 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *   R [km], inclination [rad]) by reverse-mode differentiation of sampling and
  *   the FP64 integrator, at the star's parameters, for the n samples drawn
  *   from d_uniforms (RT_UNIFORM_ROWS x n, as rt_sample_conversion_surface)
- *   and traced with opts (RT_PREC_FP64, lambda_max 0).  Each ray is
+ *   and traced with opts (lambda_max 0).  opts.precision: RT_PREC_FP64
+ *   sweeps backwards in FP64; RT_PREC_MIXED replays the trajectory in FP64
+ *   (the same steps) but forms the stages, Jacobian products and adjoint
+ *   accumulation of the backward sweep in FP32 (the FP32-vs-FP64 gradient
+ *   error).  Each ray is
  *   re-integrated with a checkpoint every 32 accepted steps (d_nacc, the
  *   accepted steps per ray of the forward rt_trace_forward run with the same
  *   opts, sizes the checkpoint store), then swept backwards segment by
@@ -345,12 +359,27 @@ rt_status rt_flux_gradient(const rt_star* star, int64_t n, const double* d_unifo
  *   8 x N.  RT_EEMPTY_SURFACE only when every star's surface is empty.
  * rt_trace_batch - rt_trace_forward over all N rays in one launch (FP64) or
  *   one FP32 launch plus one FP64 pass for promoted rays (RT_PREC_MIXED).
+ *   With images set (rt_batch_set_images), the same persistent launch also
+ *   traces every pixel of every image (rt_trace_backward's estimator): rays
+ *   and pixels share one work queue, rays first, and a lane that finishes
+ *   either claims the next item of either kind.  RT_PREC_MIXED then runs one
+ *   FP32 launch and one FP64 launch for the promoted rays (from where they
+ *   stopped) and the handed-over pixels (anew).  No tail mode in that case;
+ *   lambda_max must be 0.  Timestamps: 1 + nstars + nimg entries, [1 + nstars
+ *   + j] the last pixel of image j.  Counters add rays and pixels.
  * rt_bin_batch - per-star histograms: d_hist is nstars x nth x nph x nnu,
  *   d_out_of_range nstars; per-star fixed-point scales (binning scratch owned
  *   by the batch, allocated on first use).
  * Calls on one batch must be serialised on one stream.
  */
 typedef struct rt_batch rt_batch;
+
+/* One backward image of a batch: the arguments of rt_trace_backward. */
+typedef struct {
+  int32_t nx, ny;
+  double incl_rad, dist_over_R, bmax_over_R, Lc_cut_km;
+} rt_image_desc;
+
 rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64_t* counts,
                         rt_batch** out);
 void rt_destroy_batch(rt_batch* batch);
@@ -363,6 +392,22 @@ rt_status rt_bin_batch(rt_batch* batch, const double* d_state, const double* d_w
                        const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
                        double nu_lo, double nu_hi, double* d_hist, double* d_out_of_range,
                        void* stream);
+/*
+ * rt_batch_set_images - host, synchronous: the backward images that
+ *   rt_trace_batch traces together with the batch's rays (Sec. 2.1, Eq.
+ *   BackPower; the geometry and estimator of rt_trace_backward).  Image j of
+ *   star stars[j] (handles outlive the batch) and geometry descs[j] writes its
+ *   ny x nx pixels at offset P_j = sum_{i<j} nx_i ny_i of the caller-owned
+ *   device buffers d_image (float64, W / sr), d_img_status (u8) and d_ncross
+ *   (int32, may be NULL), each of total length P = sum nx_j ny_j <= 2^31.
+ *   Uploads a table of the images (about 300 B each) and a 4 B-per-pixel list
+ *   for the mixed-precision hand-over, replacing any earlier images; nimg = 0
+ *   removes them.  RT_EINVAL on any invalid geometry (the earlier images are
+ *   kept); RT_ENOMEM leaves the batch without images.
+ */
+rt_status rt_batch_set_images(rt_batch* batch, int32_t nimg, const rt_star* const* stars,
+                              const rt_image_desc* descs, double* d_image, uint8_t* d_img_status,
+                              int32_t* d_ncross);
 
 /*
  * CUDA graph of one batch step.  rt_batch_graph_create captures, on a stream

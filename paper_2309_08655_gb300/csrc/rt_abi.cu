@@ -13,6 +13,7 @@
 
 #include "rt.h"
 #include "rt_device.cuh"
+#include "rt_backward.cuh"
 #include "rt_internal.h"
 
 namespace {
@@ -79,6 +80,8 @@ struct rt_star {
   bool empty = false;
   double* d_park = nullptr;     // tail-mode park buffer (allocated on first use)
   int64_t park_cap = 0;
+  int32_t* d_promo = nullptr;   // mixed backward: [count | pixels handed to FP64]
+  int64_t promo_cap = 0;
 };
 
 extern "C" {
@@ -194,6 +197,7 @@ void rt_destroy_star(rt_star* s) {
   if (s->d_bins) cudaFree(s->d_bins);
   if (s->d_queue) cudaFree(s->d_queue);
   if (s->d_park) cudaFree(s->d_park);
+  if (s->d_promo) cudaFree(s->d_promo);
   if (cur != s->device) cudaSetDevice(cur);
   delete s;
 }
@@ -340,15 +344,9 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   return RT_OK;
 }
 
-rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double incl_rad,
-                            double dist_over_R, double bmax_over_R, double Lc_cut_km,
-                            double* d_image, uint8_t* d_status, int32_t* d_ncross,
-                            int64_t* d_counters, const rt_trace_opts* o, void* stream) {
-  if (!s) return fail(RT_EINVAL, "star is NULL");
-  rt_status st;
-  if ((st = check_opts(o)) != RT_OK) return st;
-  if (o->precision != RT_PREC_FP64)
-    return fail(RT_EUNSUPPORTED, "rt_trace_backward supports RT_PREC_FP64 only");
+// Checks of one image's geometry (rt_trace_backward's arguments).
+static rt_status check_image(int32_t nx, int32_t ny, double incl_rad, double dist_over_R,
+                             double bmax_over_R, double Lc_cut_km) {
   if (nx < 1 || ny < 1) return fail(RT_EINVAL, "nx and ny must be >= 1");
   if ((int64_t)nx * ny > ((int64_t)1 << 31)) return fail(RT_EINVAL, "nx * ny > 2^31");
   if (!is_finite_val(incl_rad) || !is_finite_val(dist_over_R) || !is_finite_val(bmax_over_R) ||
@@ -358,17 +356,38 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   if (!(dist_over_R > bmax_over_R * std::sqrt(2.0) + 1.0))
     return fail(RT_EINVAL, "dist_over_R must exceed bmax_over_R * sqrt(2) + 1");
   if (Lc_cut_km < 0) return fail(RT_EINVAL, "Lc_cut_km must be >= 0");
+  return RT_OK;
+}
+
+// Line centre, pixel scale and cut of one image (Sec. 2.1, Eq. BackPower).
+static void image_setup(const rtk::StarDev& h, int32_t nx, int32_t ny, double bmax_over_R,
+                        double Lc_cut_km, double* W, double* img_scale, double* Lc_cut) {
+  // line centre and the analytic frequency integral of f_a (Eq. GaussianDist)
+  *W = std::sqrt(1.0 + h.v0 * h.v0);
+  const double k0 = h.v0 * h.ma_eV, w0 = *W * h.ma_eV;
+  const double Fa = (h.fa_model == rtk::FA_DELTA) ? w0 * h.n_inf / (4.0 * PI * k0)
+                                                  : w0 * h.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
+  const double dbx = 2.0 * bmax_over_R / nx * h.R_eV, dby = 2.0 * bmax_over_R / ny * h.R_eV;
+  *img_scale = dbx * dby * Fa * h.w_unit;
+  *Lc_cut = Lc_cut_km / h.R_km;
+}
+
+rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double incl_rad,
+                            double dist_over_R, double bmax_over_R, double Lc_cut_km,
+                            double* d_image, uint8_t* d_status, int32_t* d_ncross,
+                            int64_t* d_counters, const rt_trace_opts* o, void* stream) {
+  if (!s) return fail(RT_EINVAL, "star is NULL");
+  rt_status st;
+  if ((st = check_opts(o)) != RT_OK) return st;
+  if ((st = check_image(nx, ny, incl_rad, dist_over_R, bmax_over_R, Lc_cut_km)) != RT_OK)
+    return st;
   if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
   if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
   if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
   const rtk::StarDev& h = s->h;
-  // line centre and the analytic frequency integral of f_a (Eq. GaussianDist)
-  const double W = std::sqrt(1.0 + h.v0 * h.v0);
-  const double k0 = h.v0 * h.ma_eV, w0 = W * h.ma_eV;
-  const double Fa = (h.fa_model == rtk::FA_DELTA) ? w0 * h.n_inf / (4.0 * PI * k0)
-                                                  : w0 * h.n_inf / (2.0 * std::pow(PI, 1.5) * k0);
-  const double dbx = 2.0 * bmax_over_R / nx * h.R_eV, dby = 2.0 * bmax_over_R / ny * h.R_eV;
+  double W, img_scale, Lc_cut;
+  image_setup(h, nx, ny, bmax_over_R, Lc_cut_km, &W, &img_scale, &Lc_cut);
   rtk::BackLaunch b;
   b.star = &h;
   b.nx = nx;
@@ -377,8 +396,8 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   b.D = dist_over_R;
   b.bmax = bmax_over_R;
   b.W = W;
-  b.Lc_cut = Lc_cut_km / h.R_km;
-  b.img_scale = dbx * dby * Fa * h.w_unit;
+  b.Lc_cut = Lc_cut;
+  b.img_scale = img_scale;
   b.rtol = o->rtol;
   b.atol = o->atol;
   b.r_capture = o->r_capture_over_R;
@@ -389,6 +408,28 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   b.counters = d_counters;
   b.queue = s->d_queue;
   b.ts = (unsigned long long*)o->timestamps;
+  b.prec = o->precision;
+  b.promo = nullptr;
+  b.promo_n = nullptr;
+  if (o->precision == RT_PREC_MIXED) {
+    // list of the pixels handed to the FP64 kernel (each at most once)
+    const int64_t npix = (int64_t)nx * ny;
+    rt_star* sm = const_cast<rt_star*>(s);
+    if (sm->promo_cap < npix) {
+      if (sm->d_promo) cudaFree(sm->d_promo);
+      sm->d_promo = nullptr;
+      sm->promo_cap = 0;
+      void* p = nullptr;
+      if (cudaMalloc(&p, 256 + (size_t)npix * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RT_ENOMEM, "cannot allocate the promoted-pixel list");
+      }
+      sm->d_promo = (int32_t*)p;
+      sm->promo_cap = npix;
+    }
+    b.promo_n = (unsigned long long*)sm->d_promo;
+    b.promo = sm->d_promo + 64;        // after the 256-byte counter block
+  }
   cudaError_t e = rtk::launch_backward(b, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward kernel");
   return RT_OK;
@@ -426,8 +467,6 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
-  if (o->precision != RT_PREC_FP64)
-    return fail(RT_EUNSUPPORTED, "rt_flux_gradient supports RT_PREC_FP64 only");
   if (o->lambda_max != 0.0) return fail(RT_EUNSUPPORTED, "lambda_max must be 0");
   if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
     return fail(RT_EINVAL, "need finite incl_rad and 0 < kappa < inf");
@@ -503,7 +542,8 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   a.counters = d_counters;
   a.queue = s->d_queue;
   cudaStream_t cs = (cudaStream_t)stream;
-  cudaError_t e = rtk::adjoint_grid(&a.grid, &a.block);
+  a.prec = o->precision;
+  cudaError_t e = rtk::adjoint_grid(a.prec, &a.grid, &a.block);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint occupancy");
   // scratch: checkpoint offsets, checkpoints, segment records, per-ray results
   int64_t* off = nullptr;
@@ -640,6 +680,14 @@ struct rt_batch {
   int tuned_bps[2] = {0, 0};
   double* d_park = nullptr;           // tail-mode park buffer (allocated on first use)
   int64_t park_cap = 0;
+  // backward images traced in the same launch (rt_batch_set_images)
+  int nimg = 0;
+  int64_t npix = 0;
+  void* d_img_block = nullptr;        // [promo count | image table | offsets | promo list]
+  rtk::BackParams* d_img = nullptr;
+  int64_t* d_img_off = nullptr;
+  unsigned long long* d_promo_n = nullptr;
+  int32_t* d_promo = nullptr;
 };
 
 extern "C" {
@@ -695,8 +743,94 @@ void rt_destroy_batch(rt_batch* b) {
   if (b->d_bins) cudaFree(b->d_bins);
   if (b->d_queue) cudaFree(b->d_queue);
   if (b->d_park) cudaFree(b->d_park);
+  if (b->d_img_block) cudaFree(b->d_img_block);
   if (cur != b->device) cudaSetDevice(cur);
   delete b;
+}
+
+rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* stars,
+                              const rt_image_desc* descs, double* d_image, uint8_t* d_img_status,
+                              int32_t* d_ncross) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  if (nimg < 0) return fail(RT_EINVAL, "nimg must be >= 0");
+  if (nimg > 0 && (!stars || !descs)) return fail(RT_EINVAL, "stars and descs are required");
+  rt_status st;
+  std::vector<rtk::BackParams> tbl((size_t)nimg);
+  std::vector<int64_t> off((size_t)nimg + 1, 0);
+  for (int32_t j = 0; j < nimg; ++j) {
+    const rt_image_desc& d = descs[j];
+    if (!stars[j]) return fail(RT_EINVAL, "image %d: star is NULL", j);
+    if ((st = check_image(d.nx, d.ny, d.incl_rad, d.dist_over_R, d.bmax_over_R, d.Lc_cut_km)) !=
+        RT_OK)
+      return st;
+    off[j + 1] = off[j] + (int64_t)d.nx * d.ny;
+  }
+  const int64_t npix = off[nimg];
+  if (npix > ((int64_t)1 << 31)) return fail(RT_EINVAL, "more than 2^31 pixels in all images");
+  if (npix > 0) {
+    if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_img_status, "d_img_status")) != RT_OK) return st;
+    if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
+  }
+  for (int32_t j = 0; j < nimg; ++j) {
+    const rt_image_desc& d = descs[j];
+    const rtk::StarDev& h = stars[j]->h;
+    rtk::BackParams& bp = tbl[j];
+    memset(&bp, 0, sizeof(bp));
+    bp.s = h;
+    bp.nx = d.nx;
+    bp.ny = d.ny;
+    bp.incl = d.incl_rad;
+    bp.D = d.dist_over_R;
+    bp.bmax = d.bmax_over_R;
+    image_setup(h, d.nx, d.ny, d.bmax_over_R, d.Lc_cut_km, &bp.W, &bp.img_scale, &bp.Lc_cut);
+    bp.image = d_image + off[j];
+    bp.status = d_img_status + off[j];
+    bp.ncross = d_ncross ? d_ncross + off[j] : nullptr;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != b->device) cudaSetDevice(b->device);
+  if (b->d_img_block) cudaFree(b->d_img_block);
+  b->d_img_block = nullptr;
+  b->d_img = nullptr;
+  b->d_img_off = nullptr;
+  b->d_promo_n = nullptr;
+  b->d_promo = nullptr;
+  b->nimg = 0;
+  b->npix = 0;
+  rt_status out = RT_OK;
+  if (nimg > 0) {
+    const size_t tb = ((sizeof(rtk::BackParams) * nimg + 255) / 256) * 256;
+    const size_t ob = (((size_t)nimg + 1) * sizeof(int64_t) + 255) / 256 * 256;
+    void* blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, 256 + tb + ob + (size_t)npix * sizeof(int32_t));
+    if (e == cudaSuccess) {
+      char* c = (char*)blk;
+      e = cudaMemcpy(c + 256, tbl.data(), sizeof(rtk::BackParams) * nimg, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(c + 256 + tb, off.data(), off.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        b->d_img_block = blk;
+        b->d_promo_n = (unsigned long long*)c;
+        b->d_img = (rtk::BackParams*)(c + 256);
+        b->d_img_off = (int64_t*)(c + 256 + tb);
+        b->d_promo = (int32_t*)(c + 256 + tb + ob);
+        b->nimg = nimg;
+        b->npix = npix;
+      } else {
+        cudaFree(blk);
+      }
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      out = (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "image table allocation failed")
+                                             : cuda_fail(e, "image table upload");
+    }
+  }
+  if (cur != b->device) cudaSetDevice(cur);
+  return out;
 }
 
 rt_status rt_sample_batch(rt_batch* b, const double* d_u, double* d_state, double* d_weight,
@@ -731,7 +865,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
-  if (b->N == 0) return RT_OK;
+  if (b->N == 0 && b->npix == 0) return RT_OK;
   if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
   if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
   if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
@@ -768,6 +902,36 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
   const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];
   cudaError_t e;
+  if (b->npix > 0) {
+    // rays and pixels in one persistent launch (no tail mode)
+    if (o->lambda_max != 0.0)
+      return fail(RT_EUNSUPPORTED, "lambda_max must be 0 for a batch with images");
+    rtk::ImgTable t;
+    t.img = b->d_img;
+    t.off = b->d_img_off;
+    t.nimg = b->nimg;
+    t.npix = b->npix;
+    t.promo = b->d_promo;
+    t.promo_n = b->d_promo_n;
+    t.list = nullptr;
+    t.list_n = nullptr;
+    t.ts = o->timestamps ? (unsigned long long*)o->timestamps + 1 + b->stars.size() : nullptr;
+    if (o->precision == RT_PREC_MIXED) {
+      e = cudaMemsetAsync(b->d_promo_n, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+      if (e == cudaSuccess) e = rtk::launch_batch_mixed(p, t, blk, bps, (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(e, "mixed batch kernel");
+      // FP64: the promoted rays from where they stopped, the listed pixels anew
+      p.claim_status = rtk::RAY_PROMOTED;
+      t.list = b->d_promo;
+      t.list_n = b->d_promo_n;
+      e = rtk::launch_batch_fp64(p, t, 0, 0, (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(e, "batch kernel (promoted rays and pixels)");
+      return RT_OK;
+    }
+    e = rtk::launch_batch_fp64(p, t, blk, bps, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
+    return RT_OK;
+  }
   if (o->precision == RT_PREC_MIXED) {
     e = rtk::launch_trace_mixed(p, blk, bps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
@@ -896,8 +1060,8 @@ rt_status rt_batch_graph_create(rt_batch* b, const double* d_u, double* d_state,
     e = cudaMemsetAsync(d_counters, 0, RT_COUNTERS * sizeof(int64_t), cs);
     if (e != cudaSuccess) st = cuda_fail(e, "counter reset");
   }
-  if (st == RT_OK && o->timestamps) st = rt_timestamps_reset(o->timestamps,
-                                                             (int32_t)b->stars.size(), cs);
+  if (st == RT_OK && o->timestamps)
+    st = rt_timestamps_reset(o->timestamps, (int32_t)b->stars.size() + b->nimg, cs);
   if (st == RT_OK) {
     st = rt_sample_batch(b, d_u, d_state, d_weight, d_status, cs);
     if (st == RT_EEMPTY_SURFACE) st = RT_OK;

@@ -87,32 +87,59 @@ struct AdjParams {
   unsigned long long* queue;
 };
 
-// J^T v and v . df/dq at y (q = rs, cp, m0, m1, m2), from one dual evaluation.
-__device__ __noinline__ void rhs_vjp(const RayConst<double>& c, const double* y, const double* v,
-                                     double* out, double* qbar) {
-  RayConst<D6> cd;
-  cd.rs = D6::var(c.rs, 1);
-  cd.cp = D6::var(c.cp, 2);
-  cd.pa = D6(c.pa);
-  cd.W2 = D6(c.W2);
-  cd.iW2 = D6(c.iW2);
-  cd.m0 = D6::var(c.m0, 3);
-  cd.m1 = D6::var(c.m1, 4);
-  cd.m2 = D6::var(c.m2, 5);
-  cd.sig = D6(c.sig);
+// Right-hand side in the sweep's precision T.
+template <class T>
+__device__ __forceinline__ void rhs_t(const RayConst<T>& c, const T* y, T* f) {
+  ham_rhs<T>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+}
+
+// The ray's constants in the sweep's precision.
+template <class T>
+__device__ __forceinline__ RayConst<T> cast_const(const RayConst<double>& c) {
+  RayConst<T> o;
+  o.rs = T(c.rs);
+  o.cp = T(c.cp);
+  o.pa = T(c.pa);
+  o.W2 = T(c.W2);
+  o.iW2 = T(c.iW2);
+  o.m0 = T(c.m0);
+  o.m1 = T(c.m1);
+  o.m2 = T(c.m2);
+  o.sig = T(c.sig);
+  o.disp = c.disp;
+  o.plasma = c.plasma;
+  return o;
+}
+
+// J^T v and v . df/dq at y (q = rs, cp, m0, m1, m2), from one dual evaluation
+// in the scalar type T.
+template <class T>
+__device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* y, const T* v, T* out,
+                                     T* qbar) {
+  typedef Dual<6, T> DT;
+  RayConst<DT> cd;
+  cd.rs = DT::var(c.rs, 1);
+  cd.cp = DT::var(c.cp, 2);
+  cd.pa = DT(c.pa);
+  cd.W2 = DT(c.W2);
+  cd.iW2 = DT(c.iW2);
+  cd.m0 = DT::var(c.m0, 3);
+  cd.m1 = DT::var(c.m1, 4);
+  cd.m2 = DT::var(c.m2, 5);
+  cd.sig = DT(c.sig);
   cd.disp = c.disp;
   cd.plasma = c.plasma;
   // u = Omega v = (v_k, -v_x)
-  D6 yd[6];
+  DT yd[6];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    yd[j] = D6(y[j]);
+    yd[j] = DT(y[j]);
     yd[j].d[0] = v[3 + j];
-    yd[3 + j] = D6(y[3 + j]);
+    yd[3 + j] = DT(y[3 + j]);
     yd[3 + j].d[0] = -v[j];
   }
-  D6 f[6];
-  ham_rhs<D6>(cd, yd[0], yd[1], yd[2], yd[3], yd[4], yd[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+  DT f[6];
+  ham_rhs<DT>(cd, yd[0], yd[1], yd[2], yd[3], yd[4], yd[5], f[0], f[1], f[2], f[3], f[4], f[5]);
   // J^T v = Omega (J u) = ((Ju)_k, -(Ju)_x)
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -121,7 +148,7 @@ __device__ __noinline__ void rhs_vjp(const RayConst<double>& c, const double* y,
   }
 #pragma unroll
   for (int m = 1; m < 6; ++m) {
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int j = 0; j < 6; ++j) s += v[j] * f[j].d[m];
     qbar[m - 1] += s;
@@ -130,116 +157,126 @@ __device__ __noinline__ void rhs_vjp(const RayConst<double>& c, const double* y,
 
 // Adjoint of a branch switch at y from sig_old to -sig_old:
 // ybar <- S^T ybar, and the crossing's dependence on the magnetic axis.
-__device__ void saltation(RayConst<double> c, const double* y, double sig_old, double* ybar,
-                          double* qbar) {
-  double fo[6], fn[6];
+template <class T>
+__device__ void saltation(RayConst<T> c, const T* y, T sig_old, T* ybar, T* qbar) {
+  T fo[6], fn[6];
   c.sig = sig_old;
-  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], fo[0], fo[1], fo[2], fo[3], fo[4], fo[5]);
+  rhs_t(c, y, fo);
   c.sig = -sig_old;
-  ham_rhs<double>(c, y[0], y[1], y[2], y[3], y[4], y[5], fn[0], fn[1], fn[2], fn[3], fn[4], fn[5]);
+  rhs_t(c, y, fn);
   // c(x) = 3 z (m.x) - m_z |x|^2 (the sign of Omega . B)
-  const double mx = c.m0 * y[0] + c.m1 * y[1] + c.m2 * y[2];
-  const double gc0 = 3.0 * y[2] * c.m0 - 2.0 * c.m2 * y[0];
-  const double gc1 = 3.0 * y[2] * c.m1 - 2.0 * c.m2 * y[1];
-  const double gc2 = 3.0 * mx + 3.0 * y[2] * c.m2 - 2.0 * c.m2 * y[2];
-  const double den = gc0 * fo[0] + gc1 * fo[1] + gc2 * fo[2];
-  if (den == 0.0) return;
-  double num = 0.0;
+  const T mx = c.m0 * y[0] + c.m1 * y[1] + c.m2 * y[2];
+  const T gc0 = T(3) * y[2] * c.m0 - T(2) * c.m2 * y[0];
+  const T gc1 = T(3) * y[2] * c.m1 - T(2) * c.m2 * y[1];
+  const T gc2 = T(3) * mx + T(3) * y[2] * c.m2 - T(2) * c.m2 * y[2];
+  const T den = gc0 * fo[0] + gc1 * fo[1] + gc2 * fo[2];
+  if (den == T(0)) return;
+  T num = T(0);
 #pragma unroll
   for (int j = 0; j < 6; ++j) num += (fn[j] - fo[j]) * ybar[j];
-  const double s = num / den;
+  const T s = num / den;
   ybar[0] += s * gc0;
   ybar[1] += s * gc1;
   ybar[2] += s * gc2;
-  const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-  qbar[2] += s * 3.0 * y[2] * y[0];
-  qbar[3] += s * 3.0 * y[2] * y[1];
-  qbar[4] += s * (3.0 * y[2] * y[2] - r2);
+  const T r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+  qbar[2] += s * T(3) * y[2] * y[0];
+  qbar[3] += s * T(3) * y[2] * y[1];
+  qbar[4] += s * (T(3) * y[2] * y[2] - r2);
 }
 
-// Discrete adjoint of one accepted Dormand-Prince step from y with step h.
+// Discrete adjoint of one accepted Dormand-Prince step from y with step h, in
+// the scalar type T (double: the FP64 sweep; float: the single-precision sweep,
+// which re-forms the step's stages in float from the FP64 record).
 // ybar: in, the adjoint at the step's end (unused when escape); out, at y.
 // Escape: the step ends at the theta* of the continuous extension where
 // |x| = r_out, and ybar_e is the adjoint there.
-__device__ void step_adjoint(const RayConst<double>& c, const double* y, double h, bool escape,
-                             double r_out, const double* ybar_e, double* ybar, double* qbar) {
-  double K[7][6], Y[6][6], t[6];
+template <class T>
+__device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape, T r_out,
+                             const T* ybar_e, T* ybar, T* qbar) {
+  const T a21 = T(DP::a21), a31 = T(DP::a31), a32 = T(DP::a32), a41 = T(DP::a41),
+          a42 = T(DP::a42), a43 = T(DP::a43), a51 = T(DP::a51), a52 = T(DP::a52),
+          a53 = T(DP::a53), a54 = T(DP::a54), a61 = T(DP::a61), a62 = T(DP::a62),
+          a63 = T(DP::a63), a64 = T(DP::a64), a65 = T(DP::a65);
+  const T b1 = T(DP::b1), b3 = T(DP::b3), b4 = T(DP::b4), b5 = T(DP::b5), b6 = T(DP::b6);
+  const T d1 = T(DP::d1), d3 = T(DP::d3), d4 = T(DP::d4), d5 = T(DP::d5), d6 = T(DP::d6),
+          d7 = T(DP::d7);
+  T K[7][6], Y[6][6], t[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) Y[0][i] = y[i];
-  rhs64(c, Y[0], K[0]);
+  rhs_t(c, Y[0], K[0]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Y[1][i] = y[i] + h * (DP::a21 * K[0][i]);
-  rhs64(c, Y[1], K[1]);
+  for (int i = 0; i < 6; ++i) Y[1][i] = y[i] + h * (a21 * K[0][i]);
+  rhs_t(c, Y[1], K[1]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Y[2][i] = y[i] + h * (DP::a31 * K[0][i] + DP::a32 * K[1][i]);
-  rhs64(c, Y[2], K[2]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    Y[3][i] = y[i] + h * (DP::a41 * K[0][i] + DP::a42 * K[1][i] + DP::a43 * K[2][i]);
-  rhs64(c, Y[3], K[3]);
+  for (int i = 0; i < 6; ++i) Y[2][i] = y[i] + h * (a31 * K[0][i] + a32 * K[1][i]);
+  rhs_t(c, Y[2], K[2]);
 #pragma unroll
   for (int i = 0; i < 6; ++i)
-    Y[4][i] = y[i] + h * (DP::a51 * K[0][i] + DP::a52 * K[1][i] + DP::a53 * K[2][i] +
-                          DP::a54 * K[3][i]);
-  rhs64(c, Y[4], K[4]);
+    Y[3][i] = y[i] + h * (a41 * K[0][i] + a42 * K[1][i] + a43 * K[2][i]);
+  rhs_t(c, Y[3], K[3]);
 #pragma unroll
   for (int i = 0; i < 6; ++i)
-    Y[5][i] = y[i] + h * (DP::a61 * K[0][i] + DP::a62 * K[1][i] + DP::a63 * K[2][i] +
-                          DP::a64 * K[3][i] + DP::a65 * K[4][i]);
-  rhs64(c, Y[5], K[5]);
-  double yn[6];
+    Y[4][i] = y[i] + h * (a51 * K[0][i] + a52 * K[1][i] + a53 * K[2][i] + a54 * K[3][i]);
+  rhs_t(c, Y[4], K[4]);
 #pragma unroll
   for (int i = 0; i < 6; ++i)
-    yn[i] = y[i] + h * (DP::b1 * K[0][i] + DP::b3 * K[2][i] + DP::b4 * K[3][i] +
-                        DP::b5 * K[4][i] + DP::b6 * K[5][i]);
-  double kb[7][6], ynb[6], yb[6];
+    Y[5][i] = y[i] + h * (a61 * K[0][i] + a62 * K[1][i] + a63 * K[2][i] + a64 * K[3][i] +
+                          a65 * K[4][i]);
+  rhs_t(c, Y[5], K[5]);
+  T yn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    yn[i] = y[i] + h * (b1 * K[0][i] + b3 * K[2][i] + b4 * K[3][i] + b5 * K[4][i] +
+                        b6 * K[5][i]);
+  T kb[7][6], ynb[6], yb[6];
 #pragma unroll
   for (int s = 0; s < 7; ++s)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) kb[s][i] = 0.0;
+    for (int i = 0; i < 6; ++i) kb[s][i] = T(0);
   if (escape) {
-    rhs64(c, yn, K[6]);
-    double r2v[6], r3[6], r4[6], r5[6];
+    rhs_t(c, yn, K[6]);
+    T r2v[6], r3[6], r4[6], r5[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       r2v[i] = yn[i] - y[i];
       r3[i] = h * K[0][i] - r2v[i];
       r4[i] = r2v[i] - h * K[6][i] - r3[i];
-      r5[i] = h * (DP::d1 * K[0][i] + DP::d3 * K[2][i] + DP::d4 * K[3][i] + DP::d5 * K[4][i] +
-                   DP::d6 * K[5][i] + DP::d7 * K[6][i]);
+      r5[i] = h * (d1 * K[0][i] + d3 * K[2][i] + d4 * K[3][i] + d5 * K[4][i] + d6 * K[5][i] +
+                   d7 * K[6][i]);
     }
     // the same bisection as the forward step
-    double lo = 0.0, hi = 1.0;
+    T lo = T(0), hi = T(1);
     for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
+      const T mid = T(0.5) * (lo + hi);
       if (mid <= lo || mid >= hi) break;
-      double xd[3];
+      T xd[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        xd[i] = y[i] + mid * (r2v[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-      const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+        xd[i] = y[i] + mid * (r2v[i] + (T(1) - mid) * (r3[i] + mid * (r4[i] + (T(1) - mid) *
+                                                                             r5[i])));
+      const T rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
       if (rd2 < r_out * r_out) lo = mid; else hi = mid;
     }
-    const double th = 0.5 * (lo + hi);
-    const double al = th, be = th * (1.0 - th), ga = th * th * (1.0 - th),
-                 de = th * th * (1.0 - th) * (1.0 - th);
-    const double dal = 1.0, dbe = 1.0 - 2.0 * th, dga = 2.0 * th - 3.0 * th * th,
-                 dde = 2.0 * th * (1.0 - th) * (1.0 - th) - 2.0 * th * th * (1.0 - th);
-    double xe[3], dD[6];
+    const T th = T(0.5) * (lo + hi);
+    const T al = th, be = th * (T(1) - th), ga = th * th * (T(1) - th),
+            de = th * th * (T(1) - th) * (T(1) - th);
+    const T dal = T(1), dbe = T(1) - T(2) * th, dga = T(2) * th - T(3) * th * th,
+            dde = T(2) * th * (T(1) - th) * (T(1) - th) - T(2) * th * th * (T(1) - th);
+    T xe[3], dD[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       dD[i] = dal * r2v[i] + dbe * r3[i] + dga * r4[i] + dde * r5[i];
       if (i < 3) xe[i] = y[i] + al * r2v[i] + be * r3[i] + ga * r4[i] + de * r5[i];
     }
-    double s = 0.0, cth = 0.0;
+    T s = T(0), cth = T(0);
 #pragma unroll
     for (int i = 0; i < 6; ++i) s += ybar_e[i] * dD[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) cth += 2.0 * xe[i] * dD[i];
-    double yt[6];
+    for (int i = 0; i < 3; ++i) cth += T(2) * xe[i] * dD[i];
+    T yt[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) yt[i] = ybar_e[i] - ((i < 3) ? (s / cth) * 2.0 * xe[i] : 0.0);
-    double r2b[6], r3b[6], r4b[6], r5b[6];
+    for (int i = 0; i < 6; ++i) yt[i] = ybar_e[i] - ((i < 3) ? (s / cth) * T(2) * xe[i] : T(0));
+    T r2b[6], r3b[6], r4b[6], r5b[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       r2b[i] = al * yt[i];
@@ -247,12 +284,12 @@ __device__ void step_adjoint(const RayConst<double>& c, const double* y, double 
       r4b[i] = ga * yt[i];
       r5b[i] = de * yt[i];
       yb[i] = yt[i];
-      kb[0][i] += h * DP::d1 * r5b[i];
-      kb[2][i] += h * DP::d3 * r5b[i];
-      kb[3][i] += h * DP::d4 * r5b[i];
-      kb[4][i] += h * DP::d5 * r5b[i];
-      kb[5][i] += h * DP::d6 * r5b[i];
-      kb[6][i] += h * DP::d7 * r5b[i];
+      kb[0][i] += h * d1 * r5b[i];
+      kb[2][i] += h * d3 * r5b[i];
+      kb[3][i] += h * d4 * r5b[i];
+      kb[4][i] += h * d5 * r5b[i];
+      kb[5][i] += h * d6 * r5b[i];
+      kb[6][i] += h * d7 * r5b[i];
       r2b[i] += r4b[i];
       kb[6][i] -= h * r4b[i];
       r3b[i] -= r4b[i];
@@ -268,28 +305,28 @@ __device__ void step_adjoint(const RayConst<double>& c, const double* y, double 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       ynb[i] = ybar[i];
-      yb[i] = 0.0;
+      yb[i] = T(0);
     }
   }
   // yn = y + h sum b_j k_j
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     yb[i] += ynb[i];
-    kb[0][i] += h * DP::b1 * ynb[i];
-    kb[2][i] += h * DP::b3 * ynb[i];
-    kb[3][i] += h * DP::b4 * ynb[i];
-    kb[4][i] += h * DP::b5 * ynb[i];
-    kb[5][i] += h * DP::b6 * ynb[i];
+    kb[0][i] += h * b1 * ynb[i];
+    kb[2][i] += h * b3 * ynb[i];
+    kb[3][i] += h * b4 * ynb[i];
+    kb[4][i] += h * b5 * ynb[i];
+    kb[5][i] += h * b6 * ynb[i];
   }
   // stages, last to first: k_s = f(Y_s), Y_s = y + h sum_j a_sj k_j
-  const double A[6][5] = {{0, 0, 0, 0, 0},
-                          {DP::a21, 0, 0, 0, 0},
-                          {DP::a31, DP::a32, 0, 0, 0},
-                          {DP::a41, DP::a42, DP::a43, 0, 0},
-                          {DP::a51, DP::a52, DP::a53, DP::a54, 0},
-                          {DP::a61, DP::a62, DP::a63, DP::a64, DP::a65}};
+  const T A[6][5] = {{T(0), T(0), T(0), T(0), T(0)},
+                     {a21, T(0), T(0), T(0), T(0)},
+                     {a31, a32, T(0), T(0), T(0)},
+                     {a41, a42, a43, T(0), T(0)},
+                     {a51, a52, a53, a54, T(0)},
+                     {a61, a62, a63, a64, a65}};
   for (int s = 5; s >= 0; --s) {
-    double Yb[6];
+    T Yb[6];
     rhs_vjp(c, Y[s], kb[s], Yb, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -401,6 +438,8 @@ struct RecHook {
   }
 };
 
+// T: precision of the reverse sweep (the forward replay is FP64 either way).
+template <class T>
 __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long long* steps) {
   const int64_t n = P.n;
   double u[6];
@@ -501,9 +540,14 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
   double Kv;
   const double Fi = flux_kernel_value(P, L.y, w, ybar, &rsb, &dmu_di, &Kv);
   qbar[0] += rsb;
-  double ybar_e[6];
+  T yb[6], ye[6], qb[5];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) ybar_e[j] = ybar[j];
+  for (int j = 0; j < 6; ++j) {
+    yb[j] = T(ybar[j]);
+    ye[j] = yb[j];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) qb[k] = T(qbar[k]);
   // reverse sweep over the segments
   const int last_seg = (na_final - 1) / CK;
   for (int sgi = last_seg; sgi >= 0; --sgi) {
@@ -532,29 +576,33 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
     for (int j = nrec - 1; j >= 0; --j) {
       const double* r = seg + (int64_t)j * SEGREC;
       const int fl = (int)r[8];
-      RayConst<double> cj = L.c;
-      cj.sig = r[7];
-      double y[6];
+      RayConst<T> cj = cast_const<T>(L.c);
+      cj.sig = T(r[7]);
+      T y[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) y[q] = r[q];
+      for (int q = 0; q < 6; ++q) y[q] = T(r[q]);
       if (fl & FL_FLIP_AFTER) {
         // the branch switched at the end of this step: undo at y_{n+1}
-        double yn[6];
+        T yn[6];
         // y_{n+1} is the next record's start, or the next checkpoint's state
         if (j + 1 < nrec) {
 #pragma unroll
-          for (int q = 0; q < 6; ++q) yn[q] = seg[(int64_t)(j + 1) * SEGREC + q];
+          for (int q = 0; q < 6; ++q) yn[q] = T(seg[(int64_t)(j + 1) * SEGREC + q]);
         } else {
           const double* nx = ck + (int64_t)(sgi + 1) * CKREC;
 #pragma unroll
-          for (int q = 0; q < 6; ++q) yn[q] = nx[q];
+          for (int q = 0; q < 6; ++q) yn[q] = T(nx[q]);
         }
-        saltation(cj, yn, r[7], ybar, qbar + 0);
+        saltation(cj, yn, T(r[7]), yb, qb);
       }
-      step_adjoint(cj, y, r[6], (fl & FL_ESCAPE) != 0, P.r_out, ybar_e, ybar, qbar);
-      if (fl & FL_FLIP_BEFORE) saltation(cj, y, -r[7], ybar, qbar);
+      step_adjoint(cj, y, T(r[6]), (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb, qb);
+      if (fl & FL_FLIP_BEFORE) saltation(cj, y, T(-r[7]), yb, qb);
     }
   }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) ybar[j] = (double)yb[j];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) qbar[k] = (double)qb[k];
   // assemble dF/dp for this ray
   double dmdth[3] = {P.cos_tm * cps, P.cos_tm * sps, -P.sin_tm};
 #pragma unroll
@@ -574,6 +622,7 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
   for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = G[k];
 }
 
+template <class T>
 __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double* seg = P.seg + tid * (int64_t)CK * SEGREC;
@@ -581,7 +630,7 @@ __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
   for (;;) {
     const int64_t i = (int64_t)atomicAdd(P.queue, 1ull);
     if (i >= P.n) break;
-    adjoint_ray(P, i, seg, &steps);
+    adjoint_ray<T>(P, i, seg, &steps);
     ++rays;
   }
   if (P.counters) {
@@ -685,14 +734,16 @@ cudaError_t launch_ck_offsets(const int32_t* nacc, int64_t n, int64_t* off, cuda
   return cudaGetLastError();
 }
 
-cudaError_t adjoint_grid(int* grid, int* block) {
+cudaError_t adjoint_grid(int prec, int* grid, int* block) {
   int dev = 0, nsm = 0, occ = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   *block = 64;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel, *block, 0);
+  e = (prec == PREC_MIXED)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<float>, *block, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<double>, *block, 0);
   if (e != cudaSuccess) return e;
   *grid = nsm * (occ > 0 ? occ : 1);
   return cudaSuccess;
@@ -756,7 +807,10 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
   P.queue = a.queue;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  adjoint_kernel<<<a.grid, a.block, 0, stream>>>(P);
+  if (a.prec == PREC_MIXED)
+    adjoint_kernel<float><<<a.grid, a.block, 0, stream>>>(P);
+  else
+    adjoint_kernel<double><<<a.grid, a.block, 0, stream>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   row_sums_kernel<<<NPARAMS, 256, 0, stream>>>(a.G_ray, a.n, a.grad);

@@ -12,126 +12,132 @@
 
 namespace rtk {
 
-template <int N>
+// Dual<N, T>: value and N tangent components in the scalar type T (double, or
+// float for the single-precision reverse sweep).
+template <int N, class T = double>
 struct Dual {
-  double v;
-  double d[N];
-  RT_HD Dual() : v(0.0) {
+  T v;
+  T d[N];
+  RT_HD Dual() : v(T(0)) {
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = 0.0;
+    for (int i = 0; i < N; ++i) d[i] = T(0);
   }
-  RT_HD Dual(double x) : v(x) {  // NOLINT: implicit constants
+  RT_HD Dual(T x) : v(x) {  // NOLINT: implicit constants
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = 0.0;
+    for (int i = 0; i < N; ++i) d[i] = T(0);
   }
-  RT_HD static Dual var(double x, int k) {
+  RT_HD static Dual var(T x, int k) {
     Dual r(x);
-    r.d[k] = 1.0;
+    r.d[k] = T(1);
     return r;
   }
 };
 
-template <int N>
-RT_HD __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> operator+(const Dual<N, T>& a, const Dual<N, T>& b) {
+  Dual<N, T> r;
   r.v = a.v + b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> operator-(const Dual<N, T>& a, const Dual<N, T>& b) {
+  Dual<N, T> r;
   r.v = a.v - b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> operator-(const Dual<N>& a) {
-  Dual<N> r;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> operator-(const Dual<N, T>& a) {
+  Dual<N, T> r;
   r.v = -a.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> operator*(const Dual<N, T>& a, const Dual<N, T>& b) {
+  Dual<N, T> r;
   r.v = a.v * b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
   return r;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
-  const double ib = 1.0 / b.v;
-  r.v = a.v / b.v;   // the value rounds exactly as in double arithmetic
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> operator/(const Dual<N, T>& a, const Dual<N, T>& b) {
+  Dual<N, T> r;
+  const T ib = T(1) / b.v;
+  r.v = a.v / b.v;   // the value rounds exactly as in plain arithmetic
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
   return r;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N>& operator+=(Dual<N>& a, const Dual<N>& b) {
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T>& operator+=(Dual<N, T>& a, const Dual<N, T>& b) {
   a = a + b;
   return a;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N>& operator-=(Dual<N>& a, const Dual<N>& b) {
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T>& operator-=(Dual<N, T>& a, const Dual<N, T>& b) {
   a = a - b;
   return a;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N>& operator*=(Dual<N>& a, const Dual<N>& b) {
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T>& operator*=(Dual<N, T>& a, const Dual<N, T>& b) {
   a = a * b;
   return a;
 }
-template <int N>
-RT_HD __forceinline__ bool operator<(const Dual<N>& a, const Dual<N>& b) { return a.v < b.v; }
-template <int N>
-RT_HD __forceinline__ bool operator>(const Dual<N>& a, const Dual<N>& b) { return a.v > b.v; }
+template <int N, class T>
+RT_HD __forceinline__ bool operator<(const Dual<N, T>& a, const Dual<N, T>& b) {
+  return a.v < b.v;
+}
+template <int N, class T>
+RT_HD __forceinline__ bool operator>(const Dual<N, T>& a, const Dual<N, T>& b) {
+  return a.v > b.v;
+}
 
 // chain rule for a scalar function with value fv and derivative df at a.v
-template <int N>
-RT_HD __forceinline__ Dual<N> chain(const Dual<N>& a, double fv, double df) {
-  Dual<N> r;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> chain(const Dual<N, T>& a, T fv, T df) {
+  Dual<N, T> r;
   r.v = fv;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = df * a.d[i];
   return r;
 }
 
-template <int N>
-RT_HD __forceinline__ Dual<N> rt_sqrt(const Dual<N>& a) {
-  const double s = sqrt(a.v);
-  return chain(a, s, 0.5 / s);
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> rt_sqrt(const Dual<N, T>& a) {
+  const T s = rt_sqrt(a.v);
+  return chain(a, s, T(0.5) / s);
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> rt_rsqrt(const Dual<N>& a) {
-  const double q = 1.0 / sqrt(a.v);
-  return chain(a, q, -0.5 * q * q * q);
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> rt_rsqrt(const Dual<N, T>& a) {
+  const T q = T(1) / rt_sqrt(a.v);
+  return chain(a, q, T(-0.5) * q * q * q);
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> rt_rcp(const Dual<N>& a) {
-  const double q = 1.0 / a.v;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> rt_rcp(const Dual<N, T>& a) {
+  const T q = T(1) / a.v;
   return chain(a, q, -q * q);
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> dabs(const Dual<N>& a) {
-  return a.v < 0.0 ? -a : a;
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> dabs(const Dual<N, T>& a) {
+  return a.v < T(0) ? -a : a;
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> dsin(const Dual<N>& a) {
-  return chain(a, sin(a.v), cos(a.v));
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> dsin(const Dual<N, T>& a) {
+  return chain(a, T(sin(a.v)), T(cos(a.v)));
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> dcos(const Dual<N>& a) {
-  return chain(a, cos(a.v), -sin(a.v));
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> dcos(const Dual<N, T>& a) {
+  return chain(a, T(cos(a.v)), T(-sin(a.v)));
 }
-template <int N>
-RT_HD __forceinline__ Dual<N> dexp(const Dual<N>& a) {
-  const double e = exp(a.v);
+template <int N, class T>
+RT_HD __forceinline__ Dual<N, T> dexp(const Dual<N, T>& a) {
+  const T e = exp(a.v);
   return chain(a, e, e);
 }
 

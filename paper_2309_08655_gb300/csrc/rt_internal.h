@@ -102,6 +102,10 @@ struct BackLaunch {
   int64_t* counters;
   unsigned long long* queue;
   unsigned long long* ts;     // optional: [0] start (min), [1] last pixel finished (max)
+  int prec;                   // PREC_FP64, or PREC_MIXED (FP32 stages; FP64 pass for the
+                              // pixels listed in promo, count in *promo_n)
+  int32_t* promo;
+  unsigned long long* promo_n;
 };
 cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream);
 cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream);
@@ -109,6 +113,7 @@ cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream);
 // Adjoint of the line-flux functional (rt_adjoint.cu).  Parameters, in
 // order: m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad];
 // the first NSAMP_TANGENTS move the sampling.
+enum { PREC_FP64 = 0, PREC_MIXED = 1 };   // the values of RT_PREC_*
 enum { PAR_MA = 0, PAR_B0, PAR_THM, PAR_M, PAR_R, PAR_INCL, NPARAMS };
 constexpr int NSAMP_TANGENTS = 5;
 constexpr int CK = 32;        // accepted steps per checkpoint
@@ -134,6 +139,7 @@ struct AdjLaunch {
   unsigned long long* queue;
   double* grad;    // NPARAMS
   double* F;       // 1
+  int prec;        // PREC_FP64: FP64 reverse sweep; PREC_MIXED: FP32 reverse sweep
   int grid, block;
 };
 cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* state,
@@ -141,7 +147,7 @@ cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* st
                               double kappa, double knorm, double* F_ray, double* F_total,
                               cudaStream_t stream);
 cudaError_t launch_ck_offsets(const int32_t* nacc, int64_t n, int64_t* off, cudaStream_t stream);
-cudaError_t adjoint_grid(int* grid, int* block);
+cudaError_t adjoint_grid(int prec, int* grid, int* block);
 cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream);
 
 // Sets the thread-local message returned by rt_last_error().

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rt_backward.cuh"
 #include "rt_device.cuh"
 #include "rt_integrator.cuh"
 #include "rt_internal.h"
@@ -171,134 +172,17 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Backward image plane (Sec. 2.1, Eq. BackPower; all level crossings,
-// Sec. 5.1.3).  By Liouville's theorem the forward phase-space integral
-// P = int d^3x d^3k j, j = sqrt(A) delta(E_gamma - E_a) Psi f_a, equals
-// dP/dOmega = int dA int domega omega^2 int_ray j dt over the photons crossing
-// a distant plane; the ray integral of the delta function is a sum over the
-// crossings of g = E_gamma - E_a = omega - sqrt(m_a^2 + |k|^2) along the ray,
-// sum_c sqrt(A) Psi f_a |dt/dl| / |dg/dl|.  Each pixel's time-reversed ray
-// (k -> -k; H is even in k) is traced inward from the plane; the sign of g is
-// sampled at BACK_SUBDIV points of every accepted step on the continuous
-// extension (a ray turning near the resonance crosses it twice within one
-// step) and every sign change is located by bisection.
+// Backward image plane, FP64 integrator (crossing search in rt_backward.cuh).
 
-constexpr int BACK_SUBDIV = 16;
-
-struct BackParams {
-  StarDev s;
-  int nx, ny;
-  double incl, D, bmax;
-  double W;             // omega_inf / m_a at the line centre
-  double Lc_cut;        // conversion-length cut, units of R (0: none)
-  double img_scale;     // pixel area x frequency-integrated f_a x unit conversion
-  double* image;
-  uint8_t* status;
-  int32_t* ncross;
-  int64_t* counters;
-  unsigned long long* queue;
-  double rtol, atol, r_capture;
-  int max_steps;
-  unsigned long long* ts;
-};
-
-__device__ __forceinline__ double crossing_g(const RayConst<double>& c, double W,
-                                             const double* y) {
-  const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-  const double ir = rsqrt(r2);
-  const double A = 1.0 - c.rs * ir;
-  const double kr = (y[0] * y[3] + y[1] * y[4] + y[2] * y[5]) * ir;
-  const double kk = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + (A - 1.0) * kr * kr;
-  return W * rsqrt(A) - sqrt(1.0 + kk);
-}
-
+// Passes every accepted step, with its FP64 continuous extension, to the
+// crossing search.
 struct CrossingHook {
-  const StarDev* s;
-  double W, Lc_cut;
-  double sum;
-  int ncross, ncut;
-  bool have_g;
-  double g_prev;
-
-  // sqrt(A) Psi |dt/dl| / |dg/dl| at a crossing (scaled), analytic gradients.
-  __device__ void contribution(const Lane& L, const double* y) {
-    const RayConst<double>& c = L.c;
-    double f[6];
-    rhs64(c, y, f);
-    const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-    const double ir = rsqrt(r2);
-    const double n0 = y[0] * ir, n1 = y[1] * ir, n2 = y[2] * ir;
-    const double A = 1.0 - c.rs * ir;
-    const double sA = sqrt(A);
-    const double kr = n0 * y[3] + n1 * y[4] + n2 * y[5];
-    const double kk = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + (A - 1.0) * kr * kr;
-    const double Ea = sqrt(1.0 + kk);
-    const double om = W / sA;
-    // dg/dl = (d omega/dx - d|k|^2/dx / 2E_a) . xdot - (d|k|^2/dk / 2E_a) . kdot
-    const double dAr = c.rs * ir * ir;                       // dA/dx = dAr n
-    const double c_om = -0.5 * om / A * dAr;                  // d omega/dx = c_om n
-    const double ckr = 2.0 * (A - 1.0) * kr * ir;
-    double dg = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double ni = (i == 0) ? n0 : (i == 1) ? n1 : n2;
-      const double dkk_dx = kr * kr * dAr * ni + ckr * (y[3 + i] - kr * ni);
-      const double dkk_dk = 2.0 * (y[3 + i] + (A - 1.0) * kr * ni);
-      dg += (c_om * ni - 0.5 * dkk_dx / Ea) * f[i] - 0.5 * dkk_dk / Ea * f[3 + i];
-    }
-    // plasma and field at the crossing
-    const double mu = c.m0 * n0 + c.m1 * n1 + c.m2 * n2;
-    double P = 0.0;
-    if (c.plasma == PLASMA_GJ) {
-      const double F = 3.0 * n2 * mu - c.m2;
-      P = c.cp * ir * ir * ir * fabs(F);
-    } else if (c.plasma == PLASMA_HOMOG) {
-      P = c.pa;
-    } else if (c.plasma == PLASMA_LINEAR_Z) {
-      P = c.pa * y[2];
-    } else if (c.plasma == PLASMA_RADIAL) {
-      P = c.pa * ir * ir * ir;
-    }
-    const double bb = 3.0 * mu * mu + 1.0;
-    const double km = y[3] * c.m0 + y[4] * c.m1 + y[5] * c.m2;
-    const double Kpb = 3.0 * mu * kr - km + 2.0 * mu * kr * (sA - 1.0);   // k_o . b
-    const double Kp2 = Kpb * Kpb / bb;                                     // k_par^2
-    // dt/dl = dH/dk_t with k_t = -omega_inf
-    const double dtdl =
-        fabs((c.disp == DISP_ISO) ? 2.0 * W / A : 2.0 * W / A - 2.0 * P * A * Kp2 / (W * W * W));
-    // conversion length E / |dg/ds| (units of R), s the proper length
-    const double vn = n0 * f[0] + n1 * f[1] + n2 * f[2];
-    const double v2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] + (1.0 / A - 1.0) * vn * vn;
-    const double Lc = om * sqrt(v2) / fabs(dg);
-    ++ncross;
-    if (Lc_cut > 0.0 && Lc > Lc_cut) {
-      ++ncut;
-      return;
-    }
-    const double ko2 = kk;                                    // |k_o|^2 = g^{ij} k_i k_j
-    const double cos2 = Kp2 / ko2;
-    const double sin2 = 1.0 - cos2;
-    double shape;
-    if (c.disp == DISP_ISO) {
-      shape = sin2;
-    } else {
-      const double E2 = om * om;
-      const double Dd = cos2 * P * (P - 2.0 * E2) + E2 * E2;
-      shape = E2 * E2 * sin2 / Dd;
-    }
-    const double Bmag = s->B0_eV2 * 0.5 * ir * ir * ir * sqrt(bb);
-    const double Psi = 0.5 * PI * s->g_eV * s->g_eV * Bmag * Bmag * shape * (om * s->ma_eV);
-    const double ratio = dtdl / fabs(dg) * s->R_eV / s->ma_eV;
-    sum += sA * Psi * ratio;
-  }
-
+  bool on;           // false: a forward ray of a mixed batch (no crossing search)
+  CrossingAcc acc;
   __device__ void on_accept(const Lane& L, const double* y, const double* yn, const double* k1,
                             const double* k3, const double* k4, const double* k5,
                             const double* k6, const double* k7, double h) {
-    if (!have_g) {
-      g_prev = crossing_g(L.c, W, y);
-      have_g = true;
-    }
+    if (!on) return;
     double r2[6], r3[6], r4[6], r5[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -308,95 +192,18 @@ struct CrossingHook {
       r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
                    DP::d6 * k6[i] + DP::d7 * k7[i]);
     }
-    double yd[6];
-    double th0 = 0.0, gA = g_prev;
-    for (int q = 1; q <= BACK_SUBDIV; ++q) {
-      const double th1 = (double)q / BACK_SUBDIV;
-      double gB;
-      if (q == BACK_SUBDIV) {
-        gB = crossing_g(L.c, W, yn);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-          yd[i] = y[i] + th1 * (r2[i] + (1.0 - th1) * (r3[i] + th1 * (r4[i] + (1.0 - th1) * r5[i])));
-        gB = crossing_g(L.c, W, yd);
-      }
-      if ((gA < 0.0) != (gB < 0.0)) {
-        double lo = th0, hi = th1;
-        const bool negA = gA < 0.0;
-        for (int it = 0; it < 200; ++it) {
-          const double mid = 0.5 * (lo + hi);
-          if (mid <= lo || mid >= hi) break;
-#pragma unroll
-          for (int i = 0; i < 6; ++i)
-            yd[i] = y[i] + mid * (r2[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-          if ((crossing_g(L.c, W, yd) < 0.0) == negA) lo = mid; else hi = mid;
-        }
-        const double th = 0.5 * (lo + hi);
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-          yd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
-        contribution(L, yd);
-      }
-      th0 = th1;
-      gA = gB;
-    }
-    g_prev = gA;
+    acc.scan_step(L.c, y, yn, r2, r3, r4, r5);
   }
 };
 
-// Initial state of pixel p: position on the plane, time-reversed momentum on
-// shell along -o (orthonormal frame).
-__device__ void load_pixel(const BackParams& bp, int64_t p, Lane& L) {
-  const StarDev& s = bp.s;
-  const int i = (int)(p % bp.nx), j = (int)(p / bp.nx);
-  const double bx = -bp.bmax + (i + 0.5) * (2.0 * bp.bmax / bp.nx);
-  const double by = -bp.bmax + (j + 0.5) * (2.0 * bp.bmax / bp.ny);
-  double si, ci;
-  sincos(bp.incl, &si, &ci);
-  const double o[3] = {si, 0.0, ci}, e1[3] = {ci, 0.0, -si};
-  L.y[0] = bp.D * o[0] + bx * e1[0];
-  L.y[1] = by;
-  L.y[2] = bp.D * o[2] + bx * e1[2];
-  L.R_km = s.R_km;
-  L.ma_eV = s.ma_eV;
-  double sp, cpsi;
-  sincos(s.psi_fixed, &sp, &cpsi);
-  L.c.rs = s.rs_prop;
-  L.c.cp = s.cp;
-  L.c.pa = s.plasma_a;
-  L.c.W2 = bp.W * bp.W;
-  L.c.iW2 = 1.0 / (bp.W * bp.W);
-  L.c.m0 = s.sin_tm * cpsi;
-  L.c.m1 = s.sin_tm * sp;
-  L.c.m2 = s.cos_tm;
-  L.c.disp = s.dispersion;
-  L.c.plasma = s.plasma;
-  L.c.sig = gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]);
-  const double r2 = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
-  const double ir = rsqrt(r2);
-  const double n0 = L.y[0] * ir, n1 = L.y[1] * ir, n2 = L.y[2] * ir;
-  const double A = 1.0 - L.c.rs * ir;
-  const double dn = -(n0 * o[0] + n1 * o[1] + n2 * o[2]);         // n . d, d = -o
-  const double mu = L.c.m0 * n0 + L.c.m1 * n1 + L.c.m2 * n2;
-  double P = 0.0;
-  if (L.c.plasma == PLASMA_GJ) P = L.c.cp * ir * ir * ir * fabs(3.0 * n2 * mu - L.c.m2);
-  else if (L.c.plasma == PLASMA_HOMOG) P = L.c.pa;
-  else if (L.c.plasma == PLASMA_LINEAR_Z) P = L.c.pa * L.y[2];
-  else if (L.c.plasma == PLASMA_RADIAL) P = L.c.pa * ir * ir * ir;
-  // H(s) = -W2/A + s^2 + P - P A (s Kd)^2 / W2, Kd = d . bhat (orthonormal)
-  const double bn = rsqrt(3.0 * mu * mu + 1.0);
-  const double Kd = (3.0 * mu * dn - (-(L.c.m0 * o[0] + L.c.m2 * o[2]))) * bn;
-  const double den = (L.c.disp == DISP_ISO) ? 1.0 : 1.0 - P * A * Kd * Kd * L.c.iW2;
-  const double sk = sqrt((L.c.W2 / A - P) / den);
-  const double cr = (1.0 / sqrt(A) - 1.0) * dn;
-  L.y[3] = sk * (-o[0] + cr * n0);
-  L.y[4] = sk * (cr * n1);
-  L.y[5] = sk * (-o[2] + cr * n2);
+__device__ void load_pixel(const BackParams& bp, int64_t p, Lane& L, double rtol, double atol) {
+  pixel_init(bp, p, L.y, L.c);
+  L.R_km = bp.s.R_km;
+  L.ma_eV = bp.s.ma_eV;
   L.switching = false;
   L.h_resume = 0.0;
   rhs64(L.c, L.y, L.f0);
-  L.h = initial_step(L.c, L.y, L.f0, bp.rtol, bp.atol, 1e30);
+  L.h = initial_step(L.c, L.y, L.f0, rtol, atol, 1e30);
   L.lam = 0.0;
   L.na = 0;
   L.nr = 0;
@@ -405,7 +212,8 @@ __device__ void load_pixel(const BackParams& bp, int64_t p, Lane& L) {
 
 __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   const int lane = threadIdx.x & 31;
-  const int64_t npix = (int64_t)bp.nx * bp.ny;
+  // all pixels, or only those the mixed-precision kernel handed over
+  const int64_t npix = bp.list ? (int64_t)*bp.list_n : (int64_t)bp.nx * bp.ny;
   TraceParams tp;
   tp.rtol = bp.rtol;
   tp.atol = bp.atol;
@@ -418,6 +226,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   int64_t pix = -1;
   Lane L;
   CrossingHook hk;
+  hk.on = true;
   long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0;
   if (bp.ts && threadIdx.x == 0) atomicMin(bp.ts, global_ns());
   for (;;) {
@@ -433,18 +242,11 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
         if (idx >= npix) {
           pix = -2;
         } else {
-          pix = idx;
-          load_pixel(bp, idx, L);
+          pix = bp.list ? (int64_t)bp.list[idx] : idx;
+          load_pixel(bp, pix, L, bp.rtol, bp.atol);
           // escaped once back at the distance the ray started from
           tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
-          hk.s = &bp.s;
-          hk.W = bp.W;
-          hk.Lc_cut = bp.Lc_cut;
-          hk.sum = 0.0;
-          hk.ncross = 0;
-          hk.ncut = 0;
-          hk.have_g = false;
-          hk.g_prev = 0.0;
+          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
         }
       }
     }
@@ -452,15 +254,15 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
     if (pix >= 0) {
       const int st = advance(tp, L, hk);
       if (st >= 0) {
-        bp.image[pix] = bp.img_scale * hk.sum;
+        bp.image[pix] = bp.img_scale * hk.acc.sum;
         if (bp.ts) atomicMax(bp.ts + 1, global_ns());
         bp.status[pix] = (uint8_t)st;
-        if (bp.ncross) bp.ncross[pix] = hk.ncross - hk.ncut;
+        if (bp.ncross) bp.ncross[pix] = hk.acc.ncross - hk.acc.ncut;
         acc += L.na;
         rej += L.nr;
         done += 1;
         esc += (st == RAY_ESCAPED);
-        nc += hk.ncross - hk.ncut;
+        nc += hk.acc.ncross - hk.acc.ncut;
         pix = -1;
       }
     }
@@ -484,7 +286,141 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   }
 }
 
+// Forward rays and backward pixels of a batch in one persistent launch (FP64,
+// one lane per item, no tail mode): a lane that finishes claims the next item
+// of the common queue, whichever kind it is.
+__global__ void __launch_bounds__(128) batch_fp64_kernel(TraceParams p, ImgTable t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nf = p.n;
+  const int64_t total = nf + (t.list ? (int64_t)*t.list_n : t.npix);
+  TraceParams tp = p;          // r_out per item
+  tp.park = nullptr;
+  int64_t item = -1;           // -1: needs an item, -2: queue exhausted
+  int64_t ray = 0, pix = 0;
+  int img = 0;
+  bool isp = false;
+  Lane L;
+  CrossingHook hk;
+  hk.on = false;
+  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0;
+  int na0 = 0, nr0 = 0;
+  if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  for (;;) {
+    const bool need = (item == -1);
+    const unsigned mneed = __ballot_sync(FULL, need);
+    if (mneed) {
+      const int leader = __ffs(mneed) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
+        if (idx >= total) {
+          item = -2;
+        } else if (idx < nf) {
+          if (p.status[idx] != p.claim_status) {
+            item = -1;
+          } else {
+            item = idx;
+            isp = false;
+            ray = idx;
+            load_lane(tp, idx, L);
+            na0 = L.na;
+            nr0 = L.nr;
+            tp.r_out = p.r_out;
+            hk.on = false;
+          }
+        } else {
+          const int64_t q = idx - nf;
+          const int64_t g = t.list ? (int64_t)t.list[q] : q;
+          img = find_image(t, g);
+          pix = g - t.off[img];
+          const BackParams& bp = t.img[img];
+          load_pixel(bp, pix, L, p.rtol, p.atol);
+          na0 = nr0 = 0;
+          // escaped once back at the distance the ray started from
+          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+          hk.on = true;
+          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
+          isp = true;
+          item = idx;
+        }
+      }
+    }
+    if (__ballot_sync(FULL, item != -2) == 0) break;
+    if (item >= 0) {
+      const int st = advance(tp, L, hk);
+      if (st >= 0) {
+        if (!isp) {
+          store_lane(tp, ray, L, st);
+          if (p.ts) atomicMax(p.ts + 1 + find_star(p, ray), global_ns());
+        } else {
+          const BackParams& bp = t.img[img];
+          bp.image[pix] = bp.img_scale * hk.acc.sum;
+          bp.status[pix] = (uint8_t)st;
+          if (bp.ncross) bp.ncross[pix] = hk.acc.ncross - hk.acc.ncut;
+          if (t.ts) atomicMax(t.ts + img, global_ns());
+          nc += hk.acc.ncross - hk.acc.ncut;
+        }
+        acc += L.na - na0;
+        rej += L.nr - nr0;
+        done += 1;
+        esc += (st == RAY_ESCAPED);
+        item = -1;
+      }
+    }
+  }
+  if (p.counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_down_sync(FULL, acc, o);
+      rej += __shfl_down_sync(FULL, rej, o);
+      done += __shfl_down_sync(FULL, done, o);
+      esc += __shfl_down_sync(FULL, esc, o);
+      nc += __shfl_down_sync(FULL, nc, o);
+    }
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&p.counters[CTR_ACC], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_REJ], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&p.counters[CTR_RAYS], (unsigned long long)done);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ESC], (unsigned long long)esc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_CROSS], (unsigned long long)nc);
+      if (p.claim_status == RAY_PROMOTED)
+        atomicAdd((unsigned long long*)&p.counters[CTR_PROMOTED_STEPS],
+                  (unsigned long long)(acc + rej));
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_fp64(const TraceParams& p, const ImgTable& t, int block,
+                              int blocks_per_sm, cudaStream_t stream) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (block <= 0) block = 128;
+  if (block > 128) block = 128;
+  block = (block / 32) * 32;
+  if (block < 32) block = 32;
+  if (blocks_per_sm <= 0) {
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_fp64_kernel, block, 0);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = occ > 0 ? occ : 1;
+  }
+  const int64_t items = p.n + t.npix;
+  int64_t grid = (int64_t)nsm * blocks_per_sm;
+  const int64_t max_useful = (items + block - 1) / block;
+  if (grid > max_useful) grid = max_useful;
+  if (grid < 1) grid = 1;
+  e = cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  batch_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(p, t);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream) {
   int dev = 0, nsm = 0;
@@ -512,6 +448,22 @@ cudaError_t launch_backward(const BackLaunch& b, cudaStream_t stream) {
   bp.r_capture = b.r_capture;
   bp.ts = b.ts;
   bp.max_steps = b.max_steps;
+  bp.promo = nullptr;
+  bp.promo_n = nullptr;
+  bp.list = nullptr;
+  bp.list_n = nullptr;
+  if (b.prec == PREC_MIXED) {
+    // FP32-stage pass over every pixel, then the FP64 kernel over the pixels
+    // it handed over (the list's length is read on the device)
+    bp.promo = b.promo;
+    bp.promo_n = b.promo_n;
+    e = cudaMemsetAsync(b.promo_n, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    e = launch_backward_mixed(bp, stream);
+    if (e != cudaSuccess) return e;
+    bp.list = b.promo;
+    bp.list_n = b.promo_n;
+  }
   const int block = 128;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, backward_kernel, block, 0);

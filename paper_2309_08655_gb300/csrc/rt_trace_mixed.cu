@@ -15,12 +15,14 @@
 //
 // FP32 rounding still puts a noise floor under the error estimate of the
 // momenta; where a rejected step's estimate sits on that floor three times in
-// a row, the ray is promoted: it is handed, from its current state, to the
-// FP64 kernel (resume pass) for the rest of its path.  The Goldreich-Julian
-// null cone is crossed by the same located branch switch as in rt_trace.cu.
+// a row, or the FP32 step size collapses, the ray is promoted: it is handed,
+// from its current state, to the FP64 kernel (resume pass) for the rest of
+// its path.  The Goldreich-Julian null cone is crossed by the same located
+// branch switch as in rt_trace.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rt_backward.cuh"
 #include "rt_device.cuh"
 #include "rt_internal.h"
 
@@ -28,7 +30,6 @@ namespace rtk {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr float EPS32 = 5.9604645e-8f;     // unit roundoff 2^-24
 constexpr float NOISE_C = 4.0f;             // rounding amplification allowed in a stage
 constexpr float NOISE_LIMIT = 0.25f;
@@ -205,9 +206,22 @@ __device__ __forceinline__ void dense_x(const LaneM& L, float h, float th, const
             (double)(th * (sR[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]))));
 }
 
+// Observer of accepted steps (forward tracing needs none).
+struct NoHookM {
+  static constexpr bool active = false;
+  __device__ __forceinline__ void on_accept(const LaneM&, const double*, float, const float*,
+                                            const float*, const float*, const float*,
+                                            const float*, const float*, const float*,
+                                            const float*) {}
+};
+
 // One attempted step.  Returns -1 to continue, RAY_PROMOTED to hand the ray to
-// the FP64 pass, else the final status.
-__device__ int advance_m(const TraceParams& p, LaneM& L) {
+// the FP64 pass, else the final status.  hook.on_accept sees every accepted
+// step: its FP64 start (L.y) and end (yn) and the FP32 small parts of the
+// continuous extension (position: sR, r3, r4, r5 about y + 2 h k th;
+// momentum: dK, q3, q4, q5).
+template <class Hook>
+__device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
   if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
   const float rtol = (float)p.rtol, atol = (float)p.atol;
   float yf[6];
@@ -325,7 +339,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
     ++L.nr;
     L.h = h * 0.2f;
     L.last_rej = true;
-    return (L.h < 1e-12f) ? RAY_NAN : -1;
+    return (L.h < 1e-12f) ? RAY_PROMOTED : -1;    // FP64 decides
   }
   // continuous-extension pieces (small parts), for the event locations
   float r3[3], r4[3], r5[3];
@@ -365,6 +379,17 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   if (en <= 1.0f) {
     ++L.na;
     L.noisy_rej = 0;
+    if (Hook::active) {
+      float q3[3], q4[3], q5[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        q3[i] = h * K1[i] - dK[i];
+        q4[i] = dK[i] - h * K7[i] - q3[i];
+        q5[i] = h * ((float)DP::d1 * K1[i] + (float)DP::d3 * K3[i] + (float)DP::d4 * K4[i] +
+                     (float)DP::d5 * K5[i] + (float)DP::d6 * K6[i] + (float)DP::d7 * K7[i]);
+      }
+      hook.on_accept(L, yn, h, sR, r3, r4, r5, dK, q3, q4, q5);
+    }
     const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
     if (rnew2 >= p.r_out * p.r_out) {
       // locate |x(th)| = r_out on the continuous extension
@@ -415,7 +440,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L) {
   ++L.nr;
   L.h = h * step_factor32(en, false, L.last_rej);
   L.last_rej = true;
-  return (L.h < 1e-12f) ? RAY_STIFF : -1;
+  return (L.h < 1e-12f) ? RAY_PROMOTED : -1;     // FP64 decides
 }
 
 __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
@@ -446,7 +471,8 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
     }
     if (__ballot_sync(FULL, ray != -2) == 0) break;
     if (ray >= 0) {
-      const int st = advance_m(p, L);
+      NoHookM nh;
+      const int st = advance_m(p, L, nh);
       if (st >= 0) {
         store_lane_m(p, ray, L, st);
         if (p.ts && st != RAY_PROMOTED) atomicMax(p.ts + 1 + find_star_m(p, ray), global_ns());
@@ -481,7 +507,313 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Backward image plane in mixed precision: the FP32-stage integrator above,
+// the crossing search of rt_backward.cuh on the FP64 reconstruction of each
+// accepted step's continuous extension (FP64 state + FP32 small parts), FP64
+// bisection and FP64 contributions.  A pixel whose FP32 error estimate sits on
+// the rounding floor is appended to a list and traced again from the plane by
+// the FP64 kernel.
+
+struct CrossingHookM {
+  static constexpr bool active = true;
+  bool on;              // false: a forward ray of a mixed batch (no crossing search)
+  CrossingAcc acc;
+  RayConst<double> c;   // the pixel's constants in FP64 (sig follows the lane's)
+  __device__ void on_accept(const LaneM& L, const double* yn, float h, const float* sR,
+                            const float* r3, const float* r4, const float* r5, const float* dK,
+                            const float* q3, const float* q4, const float* q5) {
+    if (!on) return;
+    double R2[6], R3[6], R4[6], R5[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R2[i] = yn[i] - L.y[i];
+      R3[i] = (double)r3[i];
+      R4[i] = (double)r4[i];
+      R5[i] = (double)r5[i];
+      R2[3 + i] = yn[3 + i] - L.y[3 + i];
+      R3[3 + i] = (double)q3[i];
+      R4[3 + i] = (double)q4[i];
+      R5[3 + i] = (double)q5[i];
+    }
+    c.sig = (double)L.c.sig;
+    acc.scan_step(c, L.y, yn, R2, R3, R4, R5);
+  }
+};
+
+__device__ void load_pixel_m(const BackParams& bp, int64_t pix, LaneM& L, RayConst<double>& c,
+                             float rtol, float atol) {
+  pixel_init(bp, pix, L.y, c);
+  L.R_km = bp.s.R_km;
+  L.ma_eV = bp.s.ma_eV;
+  L.c.rs = (float)c.rs;
+  L.c.cp = (float)c.cp;
+  L.c.pa = (float)c.pa;
+  L.c.W2 = (float)c.W2;
+  L.c.iW2 = (float)c.iW2;
+  L.md[0] = c.m0;
+  L.md[1] = c.m1;
+  L.md[2] = c.m2;
+  L.c.m0 = (float)c.m0;
+  L.c.m1 = (float)c.m1;
+  L.c.m2 = (float)c.m2;
+  L.c.disp = c.disp;
+  L.c.plasma = c.plasma;
+  L.c.sig = (float)c.sig;
+  L.switching = false;
+  L.h_resume = 0.0f;
+  float kf[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) kf[i] = (float)L.y[3 + i];
+  rhs32c(L.c, L.md, L.y, kf, L.f0);
+  L.h = initial_step32(L.c, L.md, L.y, L.f0, rtol, atol);
+  L.na = 0;
+  L.nr = 0;
+  L.noisy_rej = 0;
+  L.last_rej = false;
+}
+
+__global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t npix = (int64_t)bp.nx * bp.ny;
+  TraceParams tp;
+  tp.rtol = bp.rtol;
+  tp.atol = bp.atol;
+  tp.r_out = 0.0;
+  tp.lambda_max = 0.0;
+  tp.r_capture = bp.r_capture;
+  tp.max_steps = bp.max_steps;
+  tp.ts = nullptr;
+  tp.park = nullptr;
+  int64_t pix = -1;
+  LaneM L;
+  CrossingHookM hk;
+  hk.on = true;
+  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, promoted = 0;
+  if (bp.ts && threadIdx.x == 0) atomicMin(bp.ts, global_ns());
+  for (;;) {
+    const bool need = (pix == -1);
+    const unsigned mneed = __ballot_sync(FULL, need);
+    if (mneed) {
+      const int leader = __ffs(mneed) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(bp.queue, (unsigned long long)__popc(mneed));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
+        if (idx >= npix) {
+          pix = -2;
+        } else {
+          pix = idx;
+          load_pixel_m(bp, idx, L, hk.c, (float)bp.rtol, (float)bp.atol);
+          // escaped once back at the distance the ray started from
+          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
+        }
+      }
+    }
+    if (__ballot_sync(FULL, pix != -2) == 0) break;
+    if (pix >= 0) {
+      const int st = advance_m(tp, L, hk);
+      if (st >= 0) {
+        acc += L.na;
+        rej += L.nr;
+        if (st == RAY_PROMOTED) {
+          const unsigned long long k = atomicAdd(bp.promo_n, 1ull);
+          if (k < (unsigned long long)npix) bp.promo[k] = (int32_t)pix;
+          ++promoted;
+        } else {
+          bp.image[pix] = bp.img_scale * hk.acc.sum;
+          if (bp.ts) atomicMax(bp.ts + 1, global_ns());
+          bp.status[pix] = (uint8_t)st;
+          if (bp.ncross) bp.ncross[pix] = hk.acc.ncross - hk.acc.ncut;
+          done += 1;
+          esc += (st == RAY_ESCAPED);
+          nc += hk.acc.ncross - hk.acc.ncut;
+        }
+        pix = -1;
+      }
+    }
+  }
+  if (bp.counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_down_sync(FULL, acc, o);
+      rej += __shfl_down_sync(FULL, rej, o);
+      done += __shfl_down_sync(FULL, done, o);
+      esc += __shfl_down_sync(FULL, esc, o);
+      nc += __shfl_down_sync(FULL, nc, o);
+      promoted += __shfl_down_sync(FULL, promoted, o);
+    }
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&bp.counters[CTR_ACC], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_REJ], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_RAYS], (unsigned long long)done);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_ESC], (unsigned long long)esc);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_CROSS], (unsigned long long)nc);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_PROMOTED], (unsigned long long)promoted);
+    }
+  }
+}
+
+// Forward rays and backward pixels of a batch in one persistent launch, FP32
+// stages: rays that reach the FP32 floor are left with status RAY_PROMOTED
+// for the FP64 pass, pixels are listed for it (t.promo).
+__global__ void __launch_bounds__(256) batch_mixed_kernel(TraceParams p, ImgTable t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nf = p.n;
+  const int64_t total = nf + t.npix;
+  TraceParams tp = p;          // r_out per item
+  int64_t item = -1;           // -1: needs an item, -2: queue exhausted
+  int64_t ray = 0, pix = 0, g = 0;
+  int img = 0;
+  bool isp = false;
+  LaneM L;
+  CrossingHookM hk;
+  hk.on = false;
+  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, promoted = 0;
+  if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  for (;;) {
+    const bool need = (item == -1);
+    const unsigned mneed = __ballot_sync(FULL, need);
+    if (mneed) {
+      const int leader = __ffs(mneed) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
+        if (idx >= total) {
+          item = -2;
+        } else if (idx < nf) {
+          if (p.status[idx] != RAY_READY) {
+            item = -1;
+          } else {
+            item = idx;
+            isp = false;
+            ray = idx;
+            load_lane_m(tp, idx, L);
+            tp.r_out = p.r_out;
+            hk.on = false;
+          }
+        } else {
+          g = idx - nf;
+          img = find_image(t, g);
+          pix = g - t.off[img];
+          const BackParams& bp = t.img[img];
+          load_pixel_m(bp, pix, L, hk.c, (float)p.rtol, (float)p.atol);
+          // escaped once back at the distance the ray started from
+          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+          hk.on = true;
+          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
+          isp = true;
+          item = idx;
+        }
+      }
+    }
+    if (__ballot_sync(FULL, item != -2) == 0) break;
+    if (item >= 0) {
+      const int st = advance_m(tp, L, hk);
+      if (st >= 0) {
+        acc += L.na;
+        rej += L.nr;
+        if (!isp) {
+          store_lane_m(tp, ray, L, st);
+          if (st == RAY_PROMOTED) {
+            promoted += 1;
+          } else {
+            if (p.ts) atomicMax(p.ts + 1 + find_star_m(p, ray), global_ns());
+            done += 1;
+            esc += (st == RAY_ESCAPED);
+          }
+        } else if (st == RAY_PROMOTED) {
+          const unsigned long long k = atomicAdd(t.promo_n, 1ull);
+          if (k < (unsigned long long)t.npix) t.promo[k] = (int32_t)g;
+          promoted += 1;
+        } else {
+          const BackParams& bp = t.img[img];
+          bp.image[pix] = bp.img_scale * hk.acc.sum;
+          bp.status[pix] = (uint8_t)st;
+          if (bp.ncross) bp.ncross[pix] = hk.acc.ncross - hk.acc.ncut;
+          if (t.ts) atomicMax(t.ts + img, global_ns());
+          nc += hk.acc.ncross - hk.acc.ncut;
+          done += 1;
+          esc += (st == RAY_ESCAPED);
+        }
+        item = -1;
+      }
+    }
+  }
+  if (p.counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_down_sync(FULL, acc, o);
+      rej += __shfl_down_sync(FULL, rej, o);
+      done += __shfl_down_sync(FULL, done, o);
+      esc += __shfl_down_sync(FULL, esc, o);
+      nc += __shfl_down_sync(FULL, nc, o);
+      promoted += __shfl_down_sync(FULL, promoted, o);
+    }
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&p.counters[CTR_ACC], (unsigned long long)acc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_REJ], (unsigned long long)rej);
+      atomicAdd((unsigned long long*)&p.counters[CTR_RAYS], (unsigned long long)done);
+      atomicAdd((unsigned long long*)&p.counters[CTR_ESC], (unsigned long long)esc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_CROSS], (unsigned long long)nc);
+      atomicAdd((unsigned long long*)&p.counters[CTR_PROMOTED], (unsigned long long)promoted);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_mixed(const TraceParams& p, const ImgTable& t, int block,
+                               int blocks_per_sm, cudaStream_t stream) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (block <= 0) block = 128;
+  if (block > 256) block = 256;
+  block = (block / 32) * 32;
+  if (block < 32) block = 32;
+  if (blocks_per_sm <= 0) {
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_mixed_kernel, block, 0);
+    if (e != cudaSuccess) return e;
+    blocks_per_sm = occ > 0 ? occ : 1;
+  }
+  const int64_t items = p.n + t.npix;
+  int64_t grid = (int64_t)nsm * blocks_per_sm;
+  const int64_t max_useful = (items + block - 1) / block;
+  if (grid > max_useful) grid = max_useful;
+  if (grid < 1) grid = 1;
+  e = cudaMemsetAsync(p.queue, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  batch_mixed_kernel<<<(unsigned)grid, block, 0, stream>>>(p, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_mixed(const BackParams& bp, cudaStream_t stream) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int block = 128;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, backward_mixed_kernel, block, 0);
+  if (e != cudaSuccess) return e;
+  const int64_t npix = (int64_t)bp.nx * bp.ny;
+  int64_t grid = (int64_t)nsm * (occ > 0 ? occ : 1);
+  const int64_t max_useful = (npix + block - 1) / block;
+  if (grid > max_useful) grid = max_useful;
+  if (grid < 1) grid = 1;
+  e = cudaMemsetAsync(bp.queue, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  backward_mixed_kernel<<<(unsigned)grid, block, 0, stream>>>(bp);
+  return cudaGetLastError();
+}
 
 cudaError_t occupancy_mixed(int block, int* occ) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, trace_mixed_kernel, block, 0);

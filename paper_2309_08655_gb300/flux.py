@@ -4,7 +4,8 @@
 with the given uniforms, traces every ray (FP64) and returns the von
 Mises-Fisher-smoothed line flux F toward the observer (rt_flux_value).  Its
 backward pass calls rt_flux_gradient, the reverse-mode adjoint through the
-integrator with step checkpointing.  ``params`` is a float64 tensor
+integrator with step checkpointing (``grad_precision="fp32"``: the backward
+sweep in FP32 over the same FP64 replay).  ``params`` is a float64 tensor
 (m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad]);
 ``base`` holds the other star parameters (``rt.make_params`` keywords).
 Every step runs in the CUDA library; torch supplies device memory and the
@@ -17,6 +18,7 @@ import torch
 from . import rt
 
 PARAM_NAMES = ("m_a_eV", "B0_G", "theta_m", "M_sun", "R_km", "incl")
+_GRAD_PREC = {"fp64": rt.PREC_FP64, "fp32": rt.PREC_MIXED}
 
 
 def _star(params: torch.Tensor, base: dict) -> tuple[rt.Star, float]:
@@ -47,10 +49,11 @@ def flux_forward(params, base, uniforms, kappa, rtol=1e-10):
 
 class LineFlux(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, params, base, uniforms, kappa, rtol):
+    def forward(ctx, params, base, uniforms, kappa, rtol, grad_precision):
         F, nacc, star, incl, opts = flux_forward(params, base, uniforms, kappa, rtol)
         ctx.save_for_backward(uniforms, nacc)
-        ctx.star, ctx.incl, ctx.kappa, ctx.opts = star, incl, kappa, opts
+        ctx.star, ctx.incl, ctx.kappa = star, incl, kappa
+        ctx.opts = rt.make_opts(rtol=rtol, precision=_GRAD_PREC[grad_precision])
         return F[0].to(params.device)
 
     @staticmethod
@@ -61,9 +64,11 @@ class LineFlux(torch.autograd.Function):
         F = torch.empty(1, dtype=torch.float64, device=dev)
         rt.rt_flux_gradient(ctx.star, uniforms.shape[1], uniforms, nacc, ctx.incl, ctx.kappa,
                             grad, F, opts=ctx.opts)
-        return (grad.to(gF.device) * gF), None, None, None, None
+        return (grad.to(gF.device) * gF), None, None, None, None, None
 
 
 def line_flux(params: torch.Tensor, base: dict, uniforms: torch.Tensor, kappa: float,
-              rtol: float = 1e-10) -> torch.Tensor:
-    return LineFlux.apply(params, base, uniforms, kappa, rtol)
+              rtol: float = 1e-10, grad_precision: str = "fp64") -> torch.Tensor:
+    if grad_precision not in _GRAD_PREC:
+        raise ValueError(f"grad_precision must be one of {sorted(_GRAD_PREC)}")
+    return LineFlux.apply(params, base, uniforms, kappa, rtol, grad_precision)

@@ -37,6 +37,12 @@ class rt_star_params(ctypes.Structure):
             "plasma", "reserved"]] + [("plasma_a", ctypes.c_double)]
 
 
+class rt_image_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("incl_rad", ctypes.c_double),
+                ("dist_over_R", ctypes.c_double), ("bmax_over_R", ctypes.c_double),
+                ("Lc_cut_km", ctypes.c_double)]
+
+
 class rt_trace_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in [
         "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
@@ -126,6 +132,9 @@ def lib():
         L.rt_bin_batch.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp,
                                    _vp]
+        L.rt_batch_set_images.restype = ctypes.c_int
+        L.rt_batch_set_images.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp),
+                                          ctypes.POINTER(rt_image_desc), _vp, _vp, _vp]
         L.rt_last_error.restype = ctypes.c_char_p
         L.rt_last_error.argtypes = []
         L.rt_version.restype = ctypes.c_int32
@@ -424,6 +433,20 @@ def rt_bin_batch(batch: Batch, state, weight, status, nth, nph, nnu, nu_lo, nu_h
                                      _ptr(hist), _ptr(out_of_range), _stream(stream)))
 
 
+def rt_batch_set_images(batch: Batch, stars, descs, image, img_status, ncross=None) -> int:
+    """descs: (nx, ny, incl_rad, dist_over_R, bmax_over_R, Lc_cut_km) per image."""
+    n = len(stars)
+    arr = (_vp * max(n, 1))(*[s.handle for s in stars])
+    d = (rt_image_desc * max(n, 1))(*[rt_image_desc(int(x[0]), int(x[1]), float(x[2]),
+                                                    float(x[3]), float(x[4]), float(x[5]))
+                                      for x in descs])
+    r = _check(lib().rt_batch_set_images(batch.handle, n, arr, d, _ptr(image), _ptr(img_status),
+                                         _ptr(ncross)))
+    batch.image_stars = list(stars)     # the handles must outlive the batch
+    batch.nimg = n
+    return r
+
+
 def rt_last_error() -> str:
     return lib().rt_last_error().decode()
 
@@ -437,4 +460,5 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_version", "rt_init_batch", "rt_destroy_batch", "rt_sample_batch",
             "rt_trace_batch", "rt_bin_batch", "rt_trace_backward", "rt_bin_spectrum_noalloc",
             "rt_flops_per_step", "rt_flux_value", "rt_flux_gradient", "rt_timestamps_reset",
-            "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune"]
+            "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune",
+            "rt_batch_set_images"]

@@ -152,3 +152,35 @@ def test_gradient_rejects_unsupported_models():
     F = torch.empty(1, dtype=torch.float64, device=G.dev())
     with pytest.raises(rt.RtError):
         rt.rt_flux_gradient(star, n, u, nacc, 1.0, KAPPA, g, F)
+
+
+def test_fp32_sweep_close_to_fp64_sweep():
+    """The single-precision backward sweep (RT_PREC_MIXED) over the same FP64
+    replay: the same F, and every gradient component within 1e-3 relative of
+    the FP64 sweep's (FP32 stage rounding and accumulation over ~10^3 steps)."""
+    kw = _base()
+    n = 2048
+    u = torch.from_numpy(I.sample_uniforms(4, n)).to(G.dev())
+    g = {}
+    for prec in ("fp64", "fp32"):
+        p = _p0(kw).requires_grad_(True)
+        F = flux.line_flux(p, kw, u, KAPPA, grad_precision=prec)
+        F.backward()
+        g[prec] = p.grad.numpy().copy()
+    rel = np.abs(g["fp32"] - g["fp64"]) / np.abs(g["fp64"])
+    assert np.all(np.isfinite(g["fp32"]))
+    assert np.all(rel < 1e-3), (g, rel)
+    # the replay (and so F) is FP64 in both
+    F0, nacc, star, incl, _ = flux.flux_forward(_p0(kw), kw, u, KAPPA)
+    grad = torch.empty(6, dtype=torch.float64, device=G.dev())
+    F2 = torch.empty(1, dtype=torch.float64, device=G.dev())
+    rt.rt_flux_gradient(star, n, u, nacc, incl, KAPPA, grad, F2,
+                        opts=rt.make_opts(rtol=1e-10, precision=rt.PREC_MIXED))
+    assert abs(float(F2.cpu()[0]) - float(F0.cpu()[0])) <= 1e-13 * abs(float(F0.cpu()[0]))
+
+
+def test_line_flux_rejects_unknown_grad_precision():
+    kw = _base()
+    u = torch.from_numpy(I.sample_uniforms(4, 8)).to(G.dev())
+    with pytest.raises(ValueError):
+        flux.line_flux(_p0(kw), kw, u, KAPPA, grad_precision="fp16")

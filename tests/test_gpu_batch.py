@@ -102,3 +102,106 @@ def test_batch_mixed_runs_every_ray_once():
     c = ctr.cpu().numpy()
     assert c[2] == ready
     assert int((s == rt.RAY_READY).sum()) == 0 and int((s >= rt.RAY_NSTATUS).sum()) == 0
+
+
+def _images():
+    """Three backward images of two stars (one of them also a forward star of
+    the batch), ragged sizes."""
+    kw_a = dict(I.star_config0())
+    kw_b = dict(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=0.5, psi=0.4, m_a_eV=1e-5,
+                g_GeVinv=1e-12, rho_GeV_cm3=0.45, v0_kms=200.0, dispersion=0, resonance=0,
+                fa_model=0, weight_mode=0, prop_metric=0, phase_mode=0, plasma=0,
+                plasma_a=0.0)
+    descs = [(12, 10, 1.0, 1e4, 2.0, 0.0), (7, 9, 0.3, 1e4, 25.0, 0.0),
+             (16, 16, 1.2, 1e4, 2.0, 1.0)]
+    return [kw_b, kw_a, kw_b], descs
+
+
+@pytest.mark.parametrize("precision", [rt.PREC_FP64, rt.PREC_MIXED])
+def test_batch_with_images_equals_separate_calls(precision):
+    """Rays and pixels in one persistent launch (one queue): every ray equals
+    rt_trace_batch on the rays alone (one lane per ray, tail = 1) and every
+    pixel equals rt_trace_backward on its image alone, bit for bit -- the items
+    are independent and each is traced by the same code whichever lane takes
+    it.  The counters add rays and pixels; the timestamps cover both."""
+    stars_kw, counts, us = _setup()
+    dev = torch.device("cuda:0")
+    N = sum(counts)
+    rtol = 1e-10 if precision == rt.PREC_FP64 else 1e-8
+    opts = rt.make_opts(rtol=rtol, precision=precision, tail=1)
+    stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
+    u_all = torch.from_numpy(np.ascontiguousarray(np.concatenate(us, axis=1))).to(dev)
+
+    def rays_only():
+        b = rt.Batch(stars, counts)
+        st = torch.empty((8, N), dtype=torch.float64, device=dev)
+        w = torch.empty(N, dtype=torch.float64, device=dev)
+        s = torch.empty(N, dtype=torch.uint8, device=dev)
+        rt.rt_sample_batch(b, u_all, st, w, s)
+        rt.rt_trace_batch(b, st, s, opts=opts)
+        torch.cuda.synchronize()
+        return G.to_np(st, s)
+
+    st_r, s_r = rays_only()
+    ikw, descs = _images()
+    istars = [rt.Star(rt.make_params(**kw)) for kw in ikw]
+    sep = []
+    for sb, d in zip(istars, descs):
+        img = torch.empty((d[1], d[0]), dtype=torch.float64, device=dev)
+        sti = torch.empty((d[1], d[0]), dtype=torch.uint8, device=dev)
+        nci = torch.empty((d[1], d[0]), dtype=torch.int32, device=dev)
+        rt.rt_trace_backward(sb, d[0], d[1], d[2], d[3], d[4], img, sti, nci, None,
+                             Lc_cut_km=d[5], opts=opts)
+        torch.cuda.synchronize()
+        sep.append(G.to_np(img, sti, nci))
+    P = sum(d[0] * d[1] for d in descs)
+    batch = rt.Batch(stars, counts)
+    image = torch.full((P,), float("nan"), dtype=torch.float64, device=dev)
+    ist = torch.full((P,), 255, dtype=torch.uint8, device=dev)
+    inc = torch.full((P,), -1, dtype=torch.int32, device=dev)
+    rt.rt_batch_set_images(batch, istars, descs, image, ist, inc)
+    st = torch.empty((8, N), dtype=torch.float64, device=dev)
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    s = torch.empty(N, dtype=torch.uint8, device=dev)
+    rt.rt_sample_batch(batch, u_all, st, w, s)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    ts = torch.zeros(1 + len(stars) + len(descs), dtype=torch.int64, device=dev)
+    rt.rt_timestamps_reset(ts, len(stars) + len(descs))
+    o2 = rt.make_opts(rtol=rtol, precision=precision, tail=1, timestamps=ts)
+    rt.rt_trace_batch(batch, st, s, counters=ctr, opts=o2)
+    torch.cuda.synchronize()
+    st_u, s_u, img_u, ist_u, inc_u, c, t = G.to_np(st, s, image, ist, inc, ctr, ts)
+    assert np.array_equal(s_u, s_r)
+    assert np.array_equal(st_u, st_r)
+    o = 0
+    for (img, sti, nci), d in zip(sep, descs):
+        n = d[0] * d[1]
+        assert np.array_equal(ist_u[o:o + n], sti.ravel())
+        assert np.array_equal(inc_u[o:o + n], nci.ravel())
+        assert np.array_equal(img_u[o:o + n], img.ravel())
+        o += n
+    traced = int(np.sum((s_r != rt.RAY_NO_ROOT) & (s_r != rt.RAY_READY)))
+    assert int(c[2]) == traced + P
+    assert int(c[6]) == int(inc_u.sum())
+    assert t[0] > 0 and np.all(t[1 + len(stars):] >= t[0])
+    # removing the images gives the rays-only batch back
+    rt.rt_batch_set_images(batch, [], [], None, None)
+    rt.rt_sample_batch(batch, u_all, st, w, s)
+    rt.rt_trace_batch(batch, st, s, opts=opts)
+    torch.cuda.synchronize()
+    assert np.array_equal(G.to_np(st)[0], st_r)
+
+
+def test_batch_set_images_rejects_bad_geometry():
+    stars_kw, counts, _ = _setup()
+    dev = torch.device("cuda:0")
+    stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
+    batch = rt.Batch(stars, counts)
+    ikw, descs = _images()
+    istars = [rt.Star(rt.make_params(**kw)) for kw in ikw]
+    img = torch.empty(1000, dtype=torch.float64, device=dev)
+    st = torch.empty(1000, dtype=torch.uint8, device=dev)
+    with pytest.raises(rt.RtError):
+        rt.rt_batch_set_images(batch, istars[:1], [(4, 4, 0.3, 5.0, 6.0, 0.0)], img, st)
+    with pytest.raises(rt.RtError):
+        rt.rt_batch_set_images(batch, istars[:1], [(0, 4, 0.3, 1e4, 6.0, 0.0)], img, st)
