@@ -513,11 +513,13 @@ def _plain(o):
 
 def _uneven_leg(args, dev):
     """256 star/axion instances with ray counts log-uniform in [1e3, 1e6]:
-    the 128 forward instances in one persistent launch (mixed precision,
-    launch shape from the autotuner, sample -> trace -> bin captured in one
-    CUDA graph), the 128 backward images (mixed precision) on a second stream.  Latency
-    of an instance = GPU global-timer stamp of its last ray or pixel minus the
-    start of the first launch."""
+    the 128 forward instances (rays) and the 128 backward images (pixels) in
+    ONE persistent launch with one work queue (mixed precision, rtol 1e-8,
+    plus the FP64 pass for promoted rays and pixels), sample -> trace -> bin
+    captured in one CUDA graph.  Latency of an instance = GPU global-timer
+    stamp of its last ray or pixel minus the start of the launch.  The
+    autotuner's shape is recorded for the rays-only launch of the same
+    forward instances (also timed, for comparison)."""
     import numpy as np
     import torch
 
@@ -539,64 +541,60 @@ def _uneven_leg(args, dev):
     hist = torch.empty((len(fwd), nth, nph, nnu), dtype=torch.float64, device=dev)
     oor = torch.empty(len(fwd), dtype=torch.float64, device=dev)
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
-    ts_f = torch.zeros(1 + len(fwd), dtype=torch.int64, device=dev)
-    opts_f = rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED, timestamps=ts_f)
+    nts = len(fwd) + len(bwd)
+    ts = torch.zeros(1 + nts, dtype=torch.int64, device=dev)
+    opts = rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED, timestamps=ts)
     rt.rt_sample_batch(batch, u, st, w, s)
-    tune = rt.rt_batch_autotune(batch, st, s, opts_f, rays_per_star=256)
-    graph = rt.Graph(batch, u, st, w, s, ctr, opts_f, nth, nph, nnu, 0.0, 9.0, hist, oor)
-    # backward images: one star each, bmax from the largest conversion radius
-    bstars, bopts, bufs = [], [], []
-    ts_b = torch.zeros(2 * len(bwd), dtype=torch.int64, device=dev)
-    ctr_b = torch.zeros(8, dtype=torch.int64, device=dev)
-    for j, x in enumerate(bwd):
-        sb = rt.Star(rt.make_params(**x["star"]))
-        r_max = max((2.0 * sb.info()["wp2_coef"]) ** (1.0 / 3.0), 1.5)
-        side = x["side"]
-        img = torch.empty((side, side), dtype=torch.float64, device=dev)
-        stt = torch.empty((side, side), dtype=torch.uint8, device=dev)
-        bstars.append((sb, side, x["incl"], 1.3 * r_max))
-        bopts.append(rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED,
-                                  timestamps=ts_b[2 * j:2 * j + 2]))
-        bufs.append((img, stt))
-    s2 = torch.cuda.Stream()
-    # warm-up: one replay of the forward graph
-    graph.launch()
+    tune = rt.rt_batch_autotune(batch, st, s, opts, rays_per_star=256)
+    # rays only (the autotuned launch), for comparison
+    graph_f = rt.Graph(batch, u, st, w, s, ctr, opts, nth, nph, nnu, 0.0, 9.0, hist, oor)
+    graph_f.launch()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for j in range(len(bwd)):
-        rt.rt_timestamps_reset(ts_b[2 * j:2 * j + 2], 1)
-    ctr_b.zero_()
+    e0.record()
+    graph_f.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    t_rays_only = e0.elapsed_time(e1) / 1e3
+    # backward images: one star each, bmax from the largest conversion radius
+    bstars, descs = [], []
+    for x in bwd:
+        sb = rt.Star(rt.make_params(**x["star"]))
+        r_max = max((2.0 * sb.info()["wp2_coef"]) ** (1.0 / 3.0), 1.5)
+        bstars.append(sb)
+        descs.append((x["side"], x["side"], x["incl"], 1e4, 1.3 * r_max, 0.0))
+    P = sum(d[0] * d[1] for d in descs)
+    image = torch.empty(P, dtype=torch.float64, device=dev)
+    ist = torch.empty(P, dtype=torch.uint8, device=dev)
+    rt.rt_batch_set_images(batch, bstars, descs, image, ist)
+    graph = rt.Graph(batch, u, st, w, s, ctr, opts, nth, nph, nnu, 0.0, 9.0, hist, oor)
+    graph.launch()                                     # warm-up
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     e0.record()
-    s2.wait_event(e0)
     graph.launch()
-    with torch.cuda.stream(s2):
-        for (sb, side, incl, bmax), o, (img, stt) in zip(bstars, bopts, bufs):
-            rt.rt_trace_backward(sb, side, side, incl, 1e4, bmax, img, stt, None, ctr_b, opts=o,
-                                 stream=s2)
-    torch.cuda.current_stream().wait_stream(s2)
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     t_wall = time.perf_counter() - t_wall
-    tf = ts_f.cpu().numpy().astype(np.int64)
-    tb = ts_b.cpu().numpy().astype(np.int64).reshape(-1, 2)
-    c, cb = ctr.cpu().numpy(), ctr_b.cpu().numpy()
-    t0 = min(int(tf[0]), int(tb[:, 0].min()))
-    lat = [(int(tf[1 + k]) - t0) / 1e6 for k in range(len(fwd)) if tf[1 + k] > 0]
-    lat += [(int(tb[j, 1]) - t0) / 1e6 for j in range(len(bwd)) if tb[j, 1] > 0]
-    lat = np.array(lat)
-    steps = float(c[0] + cb[0])
+    tt = ts.cpu().numpy().astype(np.int64)
+    c = ctr.cpu().numpy()
+    t0 = int(tt[0])
+    lat = np.array([(int(tt[1 + k]) - t0) / 1e6 for k in range(nts) if tt[1 + k] > 0])
+    steps = float(c[0])
     return {"workload": "uneven_256_instances_128fwd_128bwd", "instances": len(insts),
-            "forward_rays": int(N), "backward_pixels": int(sum(b[1] ** 2 for b in bstars)),
+            "forward_rays": int(N), "backward_pixels": int(P),
             "empty_forward_instances": int(sum(1 for x in stars if x.info()["empty"])),
-            "precision": {"forward": "mixed (rtol 1e-8)", "backward": "mixed (rtol 1e-8)"},
-            "autotuned": {"block": tune["block"], "blocks_per_sm": tune["blocks_per_sm"],
-                          "candidates": len(tune["candidates_ms"])},
-            "graph": "forward sample -> trace -> bin replayed from one CUDA graph",
+            "precision": "mixed (rtol 1e-8), FP64 pass for promoted rays and pixels",
+            "launch": "rays and pixels of all 256 instances in one persistent launch, "
+                      "one queue; sample -> trace -> bin replayed from one CUDA graph",
+            "autotuned_rays_only": {"block": tune["block"],
+                                    "blocks_per_sm": tune["blocks_per_sm"],
+                                    "candidates": len(tune["candidates_ms"]),
+                                    "seconds_rays_only": t_rays_only},
             "seconds": t, "wall_seconds": t_wall, "ray_steps_per_s": steps / t,
-            "accepted_steps": steps,
+            "accepted_steps": steps, "items_finished": int(c[2]),
+            "promoted_to_fp64": int(c[4]),
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
                            "p90": float(np.percentile(lat, 90)), "max": float(lat.max()),
                            "instances_timed": int(lat.size)}}

@@ -916,9 +916,11 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
     t.list = nullptr;
     t.list_n = nullptr;
     t.ts = o->timestamps ? (unsigned long long*)o->timestamps + 1 + b->stars.size() : nullptr;
+    // the autotuned shape is the rays-only kernel's: explicit shapes only
+    const int ublk = o->block > 0 ? o->block : 0, ubps = o->block > 0 ? o->blocks_per_sm : 0;
     if (o->precision == RT_PREC_MIXED) {
       e = cudaMemsetAsync(b->d_promo_n, 0, sizeof(unsigned long long), (cudaStream_t)stream);
-      if (e == cudaSuccess) e = rtk::launch_batch_mixed(p, t, blk, bps, (cudaStream_t)stream);
+      if (e == cudaSuccess) e = rtk::launch_batch_mixed(p, t, ublk, ubps, (cudaStream_t)stream);
       if (e != cudaSuccess) return cuda_fail(e, "mixed batch kernel");
       // FP64: the promoted rays from where they stopped, the listed pixels anew
       p.claim_status = rtk::RAY_PROMOTED;
@@ -928,7 +930,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
       if (e != cudaSuccess) return cuda_fail(e, "batch kernel (promoted rays and pixels)");
       return RT_OK;
     }
-    e = rtk::launch_batch_fp64(p, t, blk, bps, (cudaStream_t)stream);
+    e = rtk::launch_batch_fp64(p, t, ublk, ubps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
     return RT_OK;
   }

@@ -269,26 +269,19 @@ struct CrossingAcc {
     sum += sA * Psi * ratio;
   }
 
-  // One accepted step from y to yn with the continuous extension
-  // y + th (r2 + (1 - th) (r3 + th (r4 + (1 - th) r5))) (FP64 pieces): the
-  // sign of g at BACK_SUBDIV points (screened in FP32), every sign change
-  // located by FP64 bisection and its contribution added.
-  __device__ void scan_step(const RayConst<double>& c, const double* y, const double* yn,
-                            const double* r2, const double* r3, const double* r4,
-                            const double* r5) {
+  // One accepted step from y to yn with the continuous extension x(th): the
+  // sign of g at BACK_SUBDIV points, screened in FP32 on the pieces p2..p5 of
+  // x(th) - y = th (p2 + (1 - th) (p3 + th (p4 + (1 - th) p5))) about y32,
+  // evaluated in FP64 at dense64(th, x) where the screen leaves it open, every
+  // sign change located by FP64 bisection on dense64 and its contribution
+  // added.
+  template <class Dense64>
+  __device__ void scan(const RayConst<double>& c, const double* y, const double* yn,
+                       const Screen& sc, const float* y32, const float* p2, const float* p3,
+                       const float* p4, const float* p5, Dense64& dense64) {
     if (!have_g) {
       neg_prev = crossing_g(c, W, y) < 0.0;
       have_g = true;
-    }
-    const Screen sc = make_screen(c, y);
-    float y32[6], p2[6], p3[6], p4[6], p5[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      y32[i] = (float)y[i];
-      p2[i] = (float)r2[i];
-      p3[i] = (float)r3[i];
-      p4[i] = (float)r4[i];
-      p5[i] = (float)r5[i];
     }
     double yd[6];
     double th0 = 0.0;
@@ -314,9 +307,7 @@ struct CrossingAcc {
       } else if (q == BACK_SUBDIV) {
         negB = crossing_g(c, W, yn) < 0.0;
       } else {
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-          yd[i] = y[i] + th1 * (r2[i] + (1.0 - th1) * (r3[i] + th1 * (r4[i] + (1.0 - th1) * r5[i])));
+        dense64(th1, yd);
         negB = crossing_g(c, W, yd) < 0.0;
       }
       if (negA != negB) {
@@ -324,21 +315,39 @@ struct CrossingAcc {
         for (int it = 0; it < 200; ++it) {
           const double mid = 0.5 * (lo + hi);
           if (mid <= lo || mid >= hi) break;
-#pragma unroll
-          for (int i = 0; i < 6; ++i)
-            yd[i] = y[i] + mid * (r2[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
+          dense64(mid, yd);
           if ((crossing_g(c, W, yd) < 0.0) == negA) lo = mid; else hi = mid;
         }
-        const double th = 0.5 * (lo + hi);
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-          yd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+        dense64(0.5 * (lo + hi), yd);
         contribution(c, yd);
       }
       th0 = th1;
       negA = negB;
     }
     neg_prev = negA;
+  }
+
+  // The same from the FP64 pieces y + th (r2 + (1 - th) (r3 + th (r4 + (1 - th)
+  // r5))) of the FP64 integrator.
+  __device__ void scan_step(const RayConst<double>& c, const double* y, const double* yn,
+                            const double* r2, const double* r3, const double* r4,
+                            const double* r5) {
+    const Screen sc = make_screen(c, y);
+    float y32[6], p2[6], p3[6], p4[6], p5[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      y32[i] = (float)y[i];
+      p2[i] = (float)r2[i];
+      p3[i] = (float)r3[i];
+      p4[i] = (float)r4[i];
+      p5[i] = (float)r5[i];
+    }
+    auto dense64 = [&](double th, double* yd) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        yd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+    };
+    scan(c, y, yn, sc, y32, p2, p3, p4, p5, dense64);
   }
 };
 

@@ -209,17 +209,18 @@ __device__ __forceinline__ void dense_x(const LaneM& L, float h, float th, const
 // Observer of accepted steps (forward tracing needs none).
 struct NoHookM {
   static constexpr bool active = false;
-  __device__ __forceinline__ void on_accept(const LaneM&, const double*, float, const float*,
+  __device__ __forceinline__ void on_accept(const LaneM&, const double*, const float*, float,
+                                            float, const float*, const float*, const float*,
                                             const float*, const float*, const float*,
-                                            const float*, const float*, const float*,
-                                            const float*) {}
+                                            const float*, const float*, const float*) {}
 };
 
 // One attempted step.  Returns -1 to continue, RAY_PROMOTED to hand the ray to
 // the FP64 pass, else the final status.  hook.on_accept sees every accepted
-// step: its FP64 start (L.y) and end (yn) and the FP32 small parts of the
-// continuous extension (position: sR, r3, r4, r5 about y + 2 h k th;
-// momentum: dK, q3, q4, q5).
+// step: its FP64 start (L.y) and end (yn), the start in FP32 (yf), the step,
+// the null-cone factor and its gradient at the start (F0, gF), and the FP32
+// small parts of the continuous extension (position: sR, r3, r4, r5 about
+// y + 2 h k th; momentum: dK, q3, q4, q5).
 template <class Hook>
 __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
   if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
@@ -388,7 +389,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
         q5[i] = h * ((float)DP::d1 * K1[i] + (float)DP::d3 * K3[i] + (float)DP::d4 * K4[i] +
                      (float)DP::d5 * K5[i] + (float)DP::d6 * K6[i] + (float)DP::d7 * K7[i]);
       }
-      hook.on_accept(L, yn, h, sR, r3, r4, r5, dK, q3, q4, q5);
+      hook.on_accept(L, yn, yf, h, F0, gF, sR, r3, r4, r5, dK, q3, q4, q5);
     }
     const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
     if (rnew2 >= p.r_out * p.r_out) {
@@ -520,24 +521,51 @@ struct CrossingHookM {
   bool on;              // false: a forward ray of a mixed batch (no crossing search)
   CrossingAcc acc;
   RayConst<double> c;   // the pixel's constants in FP64 (sig follows the lane's)
-  __device__ void on_accept(const LaneM& L, const double* yn, float h, const float* sR,
-                            const float* r3, const float* r4, const float* r5, const float* dK,
-                            const float* q3, const float* q4, const float* q5) {
+  __device__ void on_accept(const LaneM& L, const double* yn, const float* yf, float h, float F0,
+                            const float* gF, const float* sR, const float* r3, const float* r4,
+                            const float* r5, const float* dK, const float* q3, const float* q4,
+                            const float* q5) {
     if (!on) return;
-    double R2[6], R3[6], R4[6], R5[6];
+    c.sig = (double)L.c.sig;
+    // the screen from the step's own FP32 constants, null-cone factor and pieces
+    Screen sc;
+    sc.rs = L.c.rs;
+    sc.cp = L.c.cp;
+    sc.pa = L.c.pa;
+    sc.iW2 = L.c.iW2;
+    sc.m0 = L.c.m0;
+    sc.m1 = L.c.m1;
+    sc.m2 = L.c.m2;
+    sc.sig = L.c.sig;
+    sc.disp = L.c.disp;
+    sc.plasma = L.c.plasma;
+    sc.F0 = F0;
+    sc.gF[0] = gF[0];
+    sc.gF[1] = gF[1];
+    sc.gF[2] = gF[2];
+    float p2[6], p3[6], p4[6], p5[6];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R2[i] = yn[i] - L.y[i];
-      R3[i] = (double)r3[i];
-      R4[i] = (double)r4[i];
-      R5[i] = (double)r5[i];
-      R2[3 + i] = yn[3 + i] - L.y[3 + i];
-      R3[3 + i] = (double)q3[i];
-      R4[3 + i] = (double)q4[i];
-      R5[3 + i] = (double)q5[i];
+      p2[i] = 2.0f * h * yf[3 + i] + sR[i];
+      p3[i] = r3[i];
+      p4[i] = r4[i];
+      p5[i] = r5[i];
+      p2[3 + i] = dK[i];
+      p3[3 + i] = q3[i];
+      p4[3 + i] = q4[i];
+      p5[3 + i] = q5[i];
     }
-    c.sig = (double)L.c.sig;
-    acc.scan_step(c, L.y, yn, R2, R3, R4, R5);
+    // FP64 points of the continuous extension: FP64 start and increment, FP32
+    // small parts
+    const double* y = L.y;
+    auto dense64 = [&](double th, double* yd) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        yd[i] = y[i] + th * ((yn[i] - y[i]) +
+                             (1.0 - th) * ((double)p3[i] +
+                                           th * ((double)p4[i] + (1.0 - th) * (double)p5[i])));
+    };
+    acc.scan(c, L.y, yn, sc, yf, p2, p3, p4, p5, dense64);
   }
 };
 

@@ -8,8 +8,8 @@ Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
 them once in the requested precision (one persistent trace launch, after one
 untimed warm-up launch on a copy) and bins them.  Backward: an image of about
 n pixels (square) of the same star at inclination 60 deg, plane at 1e4 R,
-impact parameters up to 50 R (one warm-up launch on an image of at most
-32 x 32 pixels first).
+impact parameters up to 50 R, in the requested precision (one warm-up launch
+on an image of at most 32 x 32 pixels first).
 Adjoint: n rays of the misaligned magnetar-like star at m_a = 1e-5 eV, the
 smoothed line flux toward 1.1 rad (kappa 4) and its gradient (one warm-up
 gradient on 256 rays first).  Prints the trace time and step counts.
@@ -78,8 +78,9 @@ def backward(a, dev):
     kw = I.star_config0()
     star = rt.Star(rt.make_params(**kw))
     side = max(1, int(round(math.sqrt(a.n))))
-    rtol = a.rtol if a.rtol is not None else 1e-10
-    opts = rt.make_opts(rtol=rtol)
+    prec = rt.PREC_FP64 if a.precision == "fp64" else rt.PREC_MIXED
+    rtol = a.rtol if a.rtol is not None else (1e-10 if prec == rt.PREC_FP64 else 1e-8)
+    opts = rt.make_opts(rtol=rtol, precision=prec)
     incl, D, bmax = math.radians(60.0), 1e4, 50.0
     img = torch.empty((side, side), dtype=torch.float64, device=dev)
     st = torch.empty((side, side), dtype=torch.uint8, device=dev)
@@ -95,7 +96,8 @@ def backward(a, dev):
     e1.record()
     torch.cuda.synchronize()
     c = ctr.cpu().numpy()
-    print(json.dumps({"mode": "backward", "pixels": side * side, "rtol": rtol,
+    print(json.dumps({"mode": "backward", "precision": a.precision, "pixels": side * side,
+                      "rtol": rtol, "promoted": int(c[4]),
                       "trace_ms": e0.elapsed_time(e1), "accepted": int(c[0]),
                       "rejected": int(c[1]), "pixels_done": int(c[2]), "crossings": int(c[6]),
                       "dP_dOmega": float(img.sum()),
