@@ -77,7 +77,7 @@ def _traffic(prec, steps_per_launch=1):
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,6 +88,8 @@ def _args():
                     help="skip the backward image-plane measurement")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-twisted", action="store_true",
+                    help="skip the twisted-magnetosphere (Eq. neMag) workload")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 256-instance uneven batch measurement")
     return ap.parse_args()
@@ -461,6 +463,9 @@ def run_ours(args):
     uneven = None
     if ws == 1 and not args.no_uneven:
         uneven = _uneven_leg(args, dev)
+    twisted = None
+    if ws == 1 and not args.no_twisted:
+        twisted = _twisted_leg(args, dev, stream)
     if rank != 0:
         return
     H = res[head]
@@ -488,6 +493,7 @@ def run_ours(args):
         "adjoint_forward_ratio": adj["adjoint_forward_ratio"] if adj else None,
         "adjoint": adj,
         "uneven_batch": uneven,
+        "twisted_magnetosphere": twisted,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
@@ -509,6 +515,56 @@ def _plain(o):
     if isinstance(o, np.ndarray):
         return o.tolist()
     raise TypeError(type(o).__name__)
+
+
+def _twisted_leg(args, dev, stream):
+    """The benchmark's 16 x 65536-ray step with the twisted magnetar density
+    of Sec. 6 (Eq. neMag) in place of Goldreich-Julian: model M2's charge
+    multiplicity lambda = 20 with twist psi = 0.2 (plasma_a = 4), open field
+    lines excised.  Every sub-batch mass (1e-6 .. 5e-3 eV) then has a
+    conversion surface.  One launch per step, FP64 and mixed precision."""
+    import numpy as np
+    import torch
+
+    from paper_2309_08655_gb300 import inputs as I
+    from paper_2309_08655_gb300 import rt
+    cfg = I.CONFIG1
+    nsub, nper = cfg["nsub"], cfg["n_per_sub"]
+    N = nsub * nper
+    kws = I.stars_config1(cfg["seed"], nsub)
+    for kw in kws:
+        kw.update(plasma=rt.PLASMA_TWISTED, plasma_a=4.0)
+    stars = [rt.Star(rt.make_params(**kw)) for kw in kws]
+    batch = rt.Batch(stars, [nper] * nsub)
+    u = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [I.sample_uniforms(cfg["seed"] * 1000 + j, nper) for j in range(nsub)], axis=1))).to(dev)
+    st = torch.empty((8, N), dtype=torch.float64, device=dev)
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    s = torch.empty(N, dtype=torch.uint8, device=dev)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": "forward_misaligned_16x65536_twisted_lambda20_psi0.2",
+           "empty_sub_batches": int(sum(1 for x in stars if x.info()["empty"]))}
+    for name, prec, rtol in (("fp64", rt.PREC_FP64, cfg["rtol"]),
+                             ("mixed", rt.PREC_MIXED, cfg["rtol_mixed"])):
+        opts = rt.make_opts(rtol=rtol, r_out_over_R=cfg["r_out_over_R"], precision=prec,
+                            max_steps=cfg["max_steps"])
+        rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
+        rt.rt_trace_batch(batch, st, s, None, None, None, opts, stream=stream)   # warm-up
+        torch.cuda.synchronize()
+        ctr.zero_()
+        e0.record(stream)
+        rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
+        rt.rt_trace_batch(batch, st, s, None, None, ctr, opts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        c = ctr.cpu().numpy()
+        out[name] = {"rtol": rtol, "ms_per_step": 1e3 * t, "ray_steps_per_s": c[0] / t,
+                     "rays_per_s": c[2] / t, "accepted_steps": int(c[0]),
+                     "rays_traced": int(c[2]), "promoted": int(c[4]),
+                     "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}
+    return out
 
 
 def _uneven_leg(args, dev):

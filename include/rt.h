@@ -73,7 +73,7 @@ enum { RT_METRIC_FULL = 0, RT_METRIC_FLAT = 1 };
 enum { RT_PHASE_FIXED = 0, RT_PHASE_UNIFORM = 1 };
 enum {
   RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3,
-  RT_PLASMA_RADIAL = 4
+  RT_PLASMA_RADIAL = 4, RT_PLASMA_TWISTED = 5
 };
 enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
 
@@ -95,9 +95,16 @@ enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
  *   weight_mode    RT_WEIGHT_PAG (conversion probability, Eq. CPAnisoCurved)
  *   prop_metric    RT_METRIC_FULL, or RT_METRIC_FLAT (M = 0 in propagation only)
  *   phase_mode     RT_PHASE_FIXED or RT_PHASE_UNIFORM (psi = 2 pi u5 per sample)
- *   plasma         RT_PLASMA_GJ; the others are analytic test media
- *   plasma_a       omega_p^2 / m_a^2 (HOMOG), its gradient d/d(z/R) (LINEAR_Z), or
- *                  its value at r = R of the spherical profile a (R/r)^3 (RADIAL)
+ *   plasma         RT_PLASMA_GJ (Eq. GJDensity), RT_PLASMA_TWISTED (the twisted
+ *                  magnetar magnetosphere of Sec. 6, Eq. neMag: n_e = lambda psi
+ *                  sin^2(theta) B0 (R/r)^3 / (e r), theta the magnetic colatitude,
+ *                  dipole field kept for B; no conversion on open field lines,
+ *                  r / sin^2(theta) >= c / Omega: such samples get RT_RAY_NO_ROOT
+ *                  and weight 0); the others are analytic test media
+ *   plasma_a       TWISTED: lambda psi (charge multiplicity x twist angle [rad],
+ *                  > 0); omega_p^2 / m_a^2 (HOMOG), its gradient d/d(z/R)
+ *                  (LINEAR_Z), or its value at r = R of the spherical profile
+ *                  a (R/r)^3 (RADIAL)
  */
 typedef struct {
   double M_sun, R_km, B0_G, P_s, theta_m_rad, psi_rad, m_a_eV, g_agg_GeVinv, rho_dm_GeV_cm3,

@@ -43,7 +43,7 @@ STAR_DEFAULTS = dict(
     fa_model=0, weight_mode=0, prop_metric=0, phase_mode=0, plasma=0, plasma_a=0.0,
 )
 DISP_ANISO, DISP_ISO = 0, 1
-PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL = 0, 1, 2, 3, 4
+PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL, PLASMA_TWISTED = range(6)
 RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT = 0, 1, 2, 3
 RAY_MAXSTEPS, RAY_NAN, RAY_STIFF, RAY_LAMBDA_END = 4, 5, 6, 7
 

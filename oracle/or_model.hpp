@@ -34,7 +34,10 @@ constexpr double GM_SUN_KM = 1.4766250;           // G M_sun / c^2 [km], IAU 201
 
 // Model switches (test models exist so that closed forms can pin the tracer).
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
-enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4 };
+enum {
+  PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4,
+  PLASMA_TWISTED = 5
+};
 enum { METRIC_FULL = 0, METRIC_FLAT = 1 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
@@ -61,6 +64,7 @@ struct Star {
   double R_inv_eV;  // R in eV^-1
   double n_inf;     // asymptotic axion number density [eV^3]
   double g_eV;      // coupling [eV^-1]
+  double r_lc;      // light-cylinder radius c / Omega, units of R
 };
 
 inline Star make_star(const double* p) {
@@ -85,6 +89,7 @@ inline Star make_star(const double* p) {
   s.R_inv_eV = s.R_km / HBARC_EV_KM;
   s.n_inf = s.rho * 1e9 * hbarc_cm * hbarc_cm * hbarc_cm / s.ma_eV;
   s.g_eV = s.g_GeV * 1e-9;
+  s.r_lc = C_KM_S * s.P_s / (2.0 * PI) / s.R_km;
   return s;
 }
 
@@ -129,6 +134,20 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma 
       // spherical test profile a (R / r)^3
       T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
       return s.plasma_a / (r2 * sqrt(r2));
+    }
+    case PLASMA_TWISTED: {
+      // twisted magnetar magnetosphere (Sec. 6, Eq. neMag): the current of a
+      // globally twisted dipole, j = (psi sin^2 theta / r) B, with charge
+      // multiplicity lambda over the minimal density 2|j|/e, and |B| taken as
+      // B0 (R/r)^3:  n_e = lambda psi sin^2(theta) B0 (R/r)^3 / (e r),
+      // theta the colatitude from the magnetic axis; omega_p^2 = e^2 n_e / m_e.
+      T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+      T cos_t = (m[0] * x[0] + m[1] * x[1] + m[2] * x[2]) / r;
+      T sin2 = 1.0 - cos_t * cos_t;
+      T r_eV = r * s.R_inv_eV;                              // [eV^-1]
+      T n_e = s.plasma_a * sin2 * s.B0_eV2 / (r * r * r) / (s.e_hl * r_eV);   // [eV^3]
+      T wp2 = s.e_hl * s.e_hl * n_e / units::ME_EV;         // [eV^2]
+      return wp2 / (s.ma_eV * s.ma_eV);
     }
     default: break;
   }

@@ -112,8 +112,8 @@ static T resonance_h(const Star& s, const double m[3], const double n[3], const 
 // Root of h on (1, inf) (units of R): h(1) > 0 is required (the photon is
 // heavier than the axion at the surface); the bracket is widened by doubling
 // until h < 0 and then bisected to the last representable digit.  h is
-// monotone along the radial line for the Goldreich-Julian profile outside the
-// surface, so the root is unique.
+// monotone along the radial line for the Goldreich-Julian and the twisted
+// profiles outside the surface, so the root is unique.
 static bool resonance_root(const Star& s, const double m[3], const double n[3],
                            const double khat[3], double omega_inf, double* r_out) {
   double lo = 1.0;
@@ -173,6 +173,15 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
   if (!resonance_root(s, m, n, khat, omega_inf, &r)) {
     *status = RAY_NO_ROOT;
     return;
+  }
+  if (s.plasma == PLASMA_TWISTED) {
+    // no conversion on open field lines (Sec. 6): the dipole field line through
+    // the point, r / sin^2(theta) = L, reaches the light cylinder (L >= c / Omega)
+    const double cos_t = n[0] * m[0] + n[1] * m[1] + n[2] * m[2];
+    if (r / (1.0 - cos_t * cos_t) >= s.r_lc) {
+      *status = RAY_NO_ROOT;
+      return;
+    }
   }
   // derivative dh/dr along the leaf (dual numbers)
   double E, K2, wp2, cos2;

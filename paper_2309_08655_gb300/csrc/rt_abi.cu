@@ -120,8 +120,10 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
   if (p->phase_mode != RT_PHASE_FIXED && p->phase_mode != RT_PHASE_UNIFORM)
     return fail(RT_EUNSUPPORTED, "unknown phase_mode %d", p->phase_mode);
-  if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_RADIAL)
+  if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_TWISTED)
     return fail(RT_EUNSUPPORTED, "unknown plasma %d", p->plasma);
+  if (p->plasma == RT_PLASMA_TWISTED && !(p->plasma_a > 0))
+    return fail(RT_EINVAL, "RT_PLASMA_TWISTED needs plasma_a = lambda psi > 0");
 
   rt_star* s = new (std::nothrow) rt_star;
   if (!s) return fail(RT_ENOMEM, "host allocation failed");
@@ -138,6 +140,14 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
   const double B0_eV2 =
       p->B0_G * std::sqrt((1e-7 / EV_J) * hbarc_cm * hbarc_cm * hbarc_cm / (4.0 * PI));
   h.cp = e_hl * omega_eV * B0_eV2 / ME_EV / (p->m_a_eV * p->m_a_eV);
+  if (p->plasma == RT_PLASMA_TWISTED) {
+    // twisted magnetosphere (Eq. neMag): n_e = lambda psi sin^2(theta) B0 (R/r)^3
+    // / (e r), omega_p^2 / m_a^2 = cp sin^2(theta) (R/r)^4 with
+    // cp = e lambda psi B0 / (R m_e m_a^2) (Heaviside-Lorentz natural units)
+    h.cp = e_hl * p->plasma_a * B0_eV2 / (p->R_km / HBARC_EV_KM) / ME_EV /
+           (p->m_a_eV * p->m_a_eV);
+  }
+  h.rlc = C_KM_S * p->P_s / (2.0 * PI * p->R_km);
   h.plasma_a = p->plasma_a;
   h.cos_tm = std::cos(p->theta_m_rad);
   h.sin_tm = std::sin(p->theta_m_rad);
@@ -162,6 +172,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     case RT_PLASMA_HOMOG: s->wp2_surface_max = p->plasma_a; break;
     case RT_PLASMA_LINEAR_Z: s->wp2_surface_max = std::fabs(p->plasma_a) * 1e30; break;
     case RT_PLASMA_RADIAL: s->wp2_surface_max = p->plasma_a; break;
+    case RT_PLASMA_TWISTED: s->wp2_surface_max = h.cp; break;     // sin^2 = 1
     default: s->wp2_surface_max = 0.0; break;
   }
   s->empty = !(s->wp2_surface_max > 1.0);
@@ -515,6 +526,7 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   a.sc.v0 = h.v0;
   a.sc.psi_fixed = h.psi_fixed;
   a.sc.plasma_a = h.plasma_a;
+  a.sc.rlc = h.rlc;
   a.sc.g_eV = h.g_eV;
   a.sc.w_unit = h.w_unit;
   a.sc.disp = h.dispersion;

@@ -766,6 +766,7 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
     v.v0 = d.v0;
     v.psi_fixed = d.psi_fixed;
     v.plasma_a = d.plasma_a;
+    v.rlc = d.rlc;
     v.g_eV = d.g_eV;
     v.w_unit = d.w_unit;
     v.disp = d.disp;

@@ -160,6 +160,10 @@ __device__ __forceinline__ int screen_sign(const Screen& s, const float* x, cons
     dP = 1e-6f * fabsf(P);
   } else if (s.plasma == PLASMA_RADIAL) {
     P = s.pa * ir * ir * ir;
+  } else if (s.plasma == PLASMA_TWISTED) {
+    const float mu = (s.m0 * x[0] + s.m1 * x[1] + s.m2 * x[2]) * ir;
+    P = s.cp * (1.0f - mu * mu) * ir * ir * ir * ir;
+    dP = 1e-6f * fabsf(P);
   }
   float G = 1.0f, t = 0.0f;
   if (s.disp != DISP_ISO) {
@@ -235,6 +239,8 @@ struct CrossingAcc {
       P = c.pa * y[2];
     } else if (c.plasma == PLASMA_RADIAL) {
       P = c.pa * ir * ir * ir;
+    } else if (c.plasma == PLASMA_TWISTED) {
+      P = c.cp * (1.0 - mu * mu) * ir * ir * ir * ir;
     }
     const double bb = 3.0 * mu * mu + 1.0;
     const double km = y[3] * c.m0 + y[4] * c.m1 + y[5] * c.m2;
@@ -389,6 +395,7 @@ __device__ __forceinline__ void pixel_init(const BackParams& bp, int64_t p, doub
   else if (c.plasma == PLASMA_HOMOG) P = c.pa;
   else if (c.plasma == PLASMA_LINEAR_Z) P = c.pa * y[2];
   else if (c.plasma == PLASMA_RADIAL) P = c.pa * ir * ir * ir;
+  else if (c.plasma == PLASMA_TWISTED) P = c.cp * (1.0 - mu * mu) * ir * ir * ir * ir;
   // H(s) = -W2/A + s^2 + P - P A (s Kd)^2 / W2, Kd = d . bhat (orthonormal)
   const double bn = rsqrt(3.0 * mu * mu + 1.0);
   const double Kd = (3.0 * mu * dn - (-(c.m0 * o[0] + c.m2 * o[2]))) * bn;

@@ -38,11 +38,15 @@ struct StarDev {
   double g_eV;        // coupling [eV^-1]
   double n_inf;       // asymptotic axion number density [eV^3]
   double w_unit;      // 1 eV^2 of power in W
+  double rlc;         // light-cylinder radius / R (open field lines of the twisted model)
   int32_t dispersion, plasma, fa_model, phase_mode;
 };
 
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
-enum { PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4 };
+enum {
+  PLASMA_GJ = 0, PLASMA_VACUUM = 1, PLASMA_HOMOG = 2, PLASMA_LINEAR_Z = 3, PLASMA_RADIAL = 4,
+  PLASMA_TWISTED = 5
+};
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 enum {
@@ -158,6 +162,17 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
     dP0 = m3 * n0;
     dP1 = m3 * n1;
     dP2 = m3 * n2;
+  } else if (c.plasma == PLASMA_TWISTED) {
+    // twisted magnetosphere (Eq. neMag): P = cp (1 - mu^2) r^-4, so
+    // dP = cp r^-5 (-2 mu (m - mu n) - 4 (1 - mu^2) n) = cp r^-5 (-2 mu m + (6 mu^2 - 4) n)
+    const T ir4 = ir2 * ir2;
+    P = c.cp * (T(1) - mu * mu) * ir4;
+    const T q = c.cp * ir4 * ir;
+    const T am = T(-2) * q * mu;
+    const T an = q * (T(6) * mu * mu - T(4));
+    dP0 = am * c.m0 + an * n0;
+    dP1 = am * c.m1 + an * n1;
+    dP2 = am * c.m2 + an * n2;
   }
   if (c.disp == DISP_ISO) {
     gx0 += dP0;
@@ -227,6 +242,8 @@ __device__ __forceinline__ T ham_value(const RayConst<T>& c, const T* x, const T
     P = c.pa * x[2];
   } else if (c.plasma == PLASMA_RADIAL) {
     P = c.pa * ir * ir * ir;
+  } else if (c.plasma == PLASMA_TWISTED) {
+    P = c.cp * (T(1) - mu * mu) * ir * ir * ir * ir;
   }
   if (c.disp == DISP_ISO) return H + P;
   const T ib = rt_rsqrt(T(3) * mu * mu + T(1));

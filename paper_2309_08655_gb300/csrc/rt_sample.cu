@@ -27,6 +27,7 @@ __global__ void sample_kernel(SampleParams p) {
   c.v0 = s.v0;
   c.psi_fixed = s.psi_fixed;
   c.plasma_a = s.plasma_a;
+  c.rlc = s.rlc;
   c.g_eV = s.g_eV;
   c.w_unit = s.w_unit;
   c.disp = s.dispersion;

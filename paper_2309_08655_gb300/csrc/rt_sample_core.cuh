@@ -88,6 +88,12 @@ __device__ __forceinline__ void line_plasma(const Line& L, double r, double& P, 
       dP = -3.0 * P * ir;
       break;
     }
+    case PLASMA_TWISTED: {
+      const double ir = 1.0 / r;
+      P = L.PR * ir * ir * ir * ir;
+      dP = -4.0 * P * ir;
+      break;
+    }
     default: P = 0.0; dP = 0.0; break;
   }
 }
@@ -116,6 +122,7 @@ template <class T>
 struct SampConst {
   T rs, cp, sin_tm, cos_tm, B0_eV2, R_eV, n_inf, ma_eV;
   double v0, psi_fixed, plasma_a, g_eV, w_unit;
+  double rlc;     // light-cylinder radius / R (twisted model: open field lines excluded)
   int disp, plasma, fa_model, phase_mode;
 };
 
@@ -150,6 +157,12 @@ __device__ __forceinline__ void line_plasma_t(int plasma, const T& PR, double pa
       const T ir = rt_rcp(r);
       P = T(pa) * ir * ir * ir;
       dP = T(-3.0) * P * ir;
+      break;
+    }
+    case PLASMA_TWISTED: {
+      const T ir = rt_rcp(r);
+      P = PR * ir * ir * ir * ir;
+      dP = T(-4.0) * P * ir;
       break;
     }
     default: P = T(0.0); dP = T(0.0); break;
@@ -189,7 +202,10 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
   const T kb = T(q0) * b0 + T(q1) * b1 + T(q2) * b2;
   const T c2 = kb * kb / bb;
   const T s2 = T(1.0) - c2;
-  const T PR = s.cp * tabs(T(3.0) * T(n2) * mu - m2);
+  // the angular factor of P along the radial line: Goldreich-Julian
+  // |3 n_z (m.n) - m_z|; twisted magnetosphere sin^2 of the magnetic colatitude
+  const T PR = (s.plasma == PLASMA_TWISTED) ? s.cp * (T(1.0) - mu * mu)
+                                            : s.cp * tabs(T(3.0) * T(n2) * mu - m2);
   Line L;
   L.disp = s.disp;
   L.plasma = s.plasma;
@@ -223,6 +239,12 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
     const bool done = fabs(rn - r) <= 1e-16 * r || hi - lo <= 4e-16 * hi;
     r = rn;
     if (done) break;
+  }
+  // twisted magnetosphere: no conversion on open field lines, the dipole
+  // lines r / sin^2(theta) = L that reach the light cylinder (L >= r_LC)
+  if (s.plasma == PLASMA_TWISTED && r >= s.rlc * (1.0 - val(mu) * val(mu))) {
+    o.ok = false;
+    return;
   }
   // G in the working type at the root, for the root's dependence on the constants
   double dGr;

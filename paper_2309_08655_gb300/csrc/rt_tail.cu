@@ -74,6 +74,11 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp)
   } else if (c.plasma == PLASMA_RADIAL) {
     P = c.pa * ir2 * ir;
     dPj = -3.0 * P * ir * nj;
+  } else if (c.plasma == PLASMA_TWISTED) {
+    const double ir4 = ir2 * ir2;
+    P = c.cp * (1.0 - mu * mu) * ir4;
+    const double q = c.cp * ir4 * ir;
+    dPj = (-2.0 * q * mu) * mj + (q * (6.0 * mu * mu - 4.0)) * nj;
   }
   // the anisotropic scalars both kinds of component use, once
   const bool aniso = (c.disp != DISP_ISO);

@@ -187,3 +187,91 @@ def test_empty_surface_gives_no_roots(oracle):
     u = np.random.default_rng(3).random((6, 256))
     st, w, status = oracle.sample(star, u)
     assert np.all(status == oracle.RAY_NO_ROOT) and np.all(w == 0)
+
+
+# --- twisted magnetar magnetosphere (Sec. 6, Eq. neMag) ----------------------
+
+
+def _n_e_cm3(wp2, m_a):
+    """n_e [cm^-3] from omega_p^2 / m_a^2: n_e = omega_p^2 m_e / e^2 (e^2 = 4 pi alpha)."""
+    alpha = 7.2973525693e-3
+    hbarc_cm = 1.973269804e-10 * 1e5
+    n_ev3 = wp2 * m_a ** 2 * 510998.95 / (4 * np.pi * alpha)
+    return n_ev3 / hbarc_cm ** 3
+
+
+def test_twisted_density_matches_paper_estimate(oracle):
+    rows = np.loadtxt(os.path.join(GOLDEN, "twisted_density.txt"), ndmin=2)
+    for lam, psi, B0, R, n_paper, prec, ratio_paper, lprec in rows:
+        m_a = 1e-4
+        star = oracle.star_vector(R_km=R, B0_G=B0, P_s=3.76, m_a_eV=m_a, plasma=5,
+                                  plasma_a=lam * psi)
+        # on the magnetic equator (sin^2 theta = 1) of the surface, aligned rotator
+        x = np.array([[R], [0.0], [0.0]])
+        n_e = _n_e_cm3(oracle.plasma_freq2(star, x)[0], m_a)
+        assert abs(n_e / n_paper - 1) < prec, n_e
+        # against the Goldreich-Julian density at the pole of the same star
+        gj = oracle.star_vector(R_km=R, B0_G=B0, P_s=3.76, m_a_eV=m_a)
+        n_gj = _n_e_cm3(oracle.plasma_freq2(gj, np.array([[0.0], [0.0], [R]]))[0], m_a)
+        assert abs(np.log10(n_e / n_gj / (lam * ratio_paper))) < lprec, n_e / n_gj
+
+
+def test_twisted_density_angular_and_radial_structure(oracle):
+    """omega_p^2 = c sin^2(theta_mag) (R/r)^4, linear in lambda psi and B0,
+    1/m_a^2, independent of the rotation period, following the magnetic axis."""
+    R = 11.0
+    base = dict(R_km=R, B0_G=1.6e14, P_s=3.76, m_a_eV=1e-3, plasma=5, plasma_a=0.2)
+    star = oracle.star_vector(**base)
+    th = np.linspace(0.0, np.pi, 37)
+    r = np.array([1.0, 1.7, 4.2]) * R
+    pts = np.concatenate([np.stack([rr * np.sin(th), np.zeros_like(th), rr * np.cos(th)])
+                          for rr in r], axis=1)
+    wp2 = oracle.plasma_freq2(star, pts)
+    c = oracle.plasma_freq2(star, np.array([[R], [0.0], [0.0]]))[0]
+    rr = np.repeat(r, th.size)
+    tt = np.tile(th, r.size)
+    assert np.allclose(wp2, c * np.sin(tt) ** 2 * (R / rr) ** 4, rtol=1e-12, atol=1e-14 * c)
+    for k, f in (("plasma_a", 3.0), ("B0_G", 2.5), ("m_a_eV", 0.5), ("P_s", 7.0)):
+        kw = dict(base)
+        kw[k] = base[k] * f
+        c2 = oracle.plasma_freq2(oracle.star_vector(**kw), np.array([[R], [0.0], [0.0]]))[0]
+        expect = {"plasma_a": f, "B0_G": f, "m_a_eV": 1 / f ** 2, "P_s": 1.0}[k]
+        assert np.isclose(c2 / c, expect, rtol=1e-13), k
+    # misaligned: zero on the magnetic axis at phase psi, maximal across it
+    tm, ph = 0.5, 2.0
+    s2 = oracle.star_vector(**dict(base, theta_m=tm))
+    mh = np.array([np.sin(tm) * np.cos(ph), np.sin(tm) * np.sin(ph), np.cos(tm)])
+    assert oracle.plasma_freq2(s2, (2 * R * mh)[:, None], ph)[0] < 1e-14 * c
+    e = np.cross(mh, [0.0, 0.0, 1.0])
+    e /= np.linalg.norm(e)
+    assert np.isclose(oracle.plasma_freq2(s2, (2 * R * e)[:, None], ph)[0], c / 16, rtol=1e-12)
+
+
+def test_twisted_open_field_lines_are_excluded(oracle):
+    """Samples whose conversion point lies on an open field line (the dipole
+    line r / sin^2 theta = L reaching the light cylinder, L >= c / Omega) get
+    no resonance and weight 0; all others are kept unchanged."""
+    from paper_2309_08655_gb300 import inputs as I
+    R = 10.0
+    base = dict(R_km=R, B0_G=1e14, m_a_eV=1e-3, plasma=5, plasma_a=0.2, theta_m=0.3,
+                psi=0.7)
+    u = I.sample_uniforms(77, 4000)
+    slow = oracle.star_vector(**dict(base, P_s=10.0))          # r_LC ~ 4.8e4 R
+    fast = oracle.star_vector(**dict(base, P_s=4.5e-4))        # r_LC ~ 2.1 R
+    st_s, w_s, s_s = oracle.sample(slow, u)
+    st_f, w_f, s_f = oracle.sample(fast, u)
+    r_lc = 299792.458 * 4.5e-4 / (2 * np.pi) / R
+    mh = np.array([np.sin(0.3) * np.cos(0.7), np.sin(0.3) * np.sin(0.7), np.cos(0.3)])
+    ok = s_s == oracle.RAY_READY
+    assert ok.sum() > 1000
+    x = st_s[:3] / R
+    r = np.linalg.norm(x, axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):     # r = 0 where no root
+        cos_t = (mh[:, None] * x).sum(0) / r
+        L = r / (1 - cos_t ** 2)
+    assert np.any(ok & (L >= r_lc)) and np.any(ok & (L < r_lc))
+    open_ = ok & (L >= r_lc)
+    assert np.all(s_f[open_] == oracle.RAY_NO_ROOT) and np.all(w_f[open_] == 0.0)
+    keep = ok & (L < r_lc)
+    assert np.all(s_f[keep] == oracle.RAY_READY)
+    assert np.array_equal(st_f[:, keep], st_s[:, keep]) and np.array_equal(w_f[keep], w_s[keep])

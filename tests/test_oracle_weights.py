@@ -138,3 +138,64 @@ def test_binning_conserves_escaped_weight_and_edges(oracle):
     assert hist[63, 31, 14] == 4.0         # theta = pi -> last bin, phi wraps below 2 pi
     assert hist[int(1.0 / (np.pi / 64)), int(3.0 / (2 * np.pi / 32)), 127] == 8.0
     assert hist[int(2.0 / (np.pi / 64)), int(5.0 / (2 * np.pi / 32)), int(4.0 / (9 / 128))] == 16.0
+
+
+def _iso_power_quadrature_twisted(oracle, star_kw):
+    """The same reduction for the twisted magnetosphere (Sec. 6, Eq. neMag):
+    omega_p^2 = C sin^2(th) (R/r)^4 on an aligned rotator, resonance surface
+    r0(th) = (C sin^2 th / m_a^2)^(1/4), |d_r omega_p^2| = 4 m_a^2 / r0, and no
+    conversion where r0 / sin^2 th >= c / Omega (open field lines)."""
+    star = oracle.star_vector(**star_kw)
+    c = oracle.star_constants(star)
+    m = star_kw["m_a_eV"]
+    R = star_kw["R_km"] / HBARC_EV_KM
+    rs = c["rs_over_R"]
+    coef = oracle.plasma_freq2(star, np.array([[star_kw["R_km"]], [0.0], [0.0]]))[0]
+    B0 = c["B0_eV2"]
+    g = star_kw.get("g_GeVinv", 1e-12) * 1e-9
+    n_inf = c["n_inf_eV3"]
+    k0 = m * star_kw.get("v0_kms", 200.0) / C_KM_S
+    r_lc = C_KM_S * star_kw["P_s"] / (2 * np.pi) / star_kw["R_km"]
+
+    def I_k(r_over_R):
+        A = 1 - rs / r_over_R
+
+        def f(kinf):
+            k = np.sqrt((m * m + kinf * kinf) / A - m * m)
+            E2 = (m * m + kinf * kinf) / A
+            return (k * kinf / A) * E2 * np.exp(-(kinf / k0) ** 2)
+
+        val, _ = integrate.quad(f, 0, 12 * k0, epsrel=1e-11, epsabs=0, limit=200)
+        return n_inf * val / (np.pi * k0 * k0) ** 1.5
+
+    def integrand(th):
+        s2 = np.sin(th) ** 2
+        r0 = (coef * s2) ** 0.25
+        if r0 <= 1.0 or r0 / s2 >= r_lc:
+            return 0.0
+        Bmag = 0.5 * B0 / r0**3 * np.sqrt(3 * np.cos(th) ** 2 + 1)
+        dwp2 = 4 * m * m / (r0 * R)
+        return np.sin(th) * (r0 * R) ** 2 * Bmag**2 * I_k(r0) / dwp2
+
+    tot, _ = integrate.quad(integrand, 0, np.pi, epsrel=1e-9, limit=400)
+    P = (8 * np.pi / 3) * np.pi * g * g * 2 * np.pi * tot
+    return P * EV_J / HBAR_EV_S
+
+
+@pytest.mark.parametrize("P_s", [3.76, 5.8e-4])
+def test_isotropic_twisted_power_matches_surface_quadrature(oracle, P_s):
+    """Twisted magnetar density, isotropic dispersion: the Monte-Carlo total of
+    the oracle's weights against the surface quadrature, with the light
+    cylinder far away (3.76 s) and cutting the surface (0.58 ms: r_LC = 2.5 R
+    against a surface at 1.6 R on the magnetic equator)."""
+    kw = dict(M_sun=1.5, R_km=11.0, B0_G=1.6e14, P_s=P_s, m_a_eV=1e-3, dispersion=1,
+              plasma=5, plasma_a=0.2)
+    star = oracle.star_vector(**kw)
+    n = 40000
+    u = np.random.default_rng(22).random((6, n))
+    st, w, status = oracle.sample(star, u)
+    W = w * n
+    mc, sig = W.mean(), W.std() / np.sqrt(n)
+    quad = _iso_power_quadrature_twisted(oracle, kw)
+    assert sig / mc < 0.05
+    assert abs(mc - quad) < 4 * sig, (mc, quad, sig)
