@@ -96,6 +96,40 @@ struct NoHook {
                                             double) {}
 };
 
+// The last th in [0, 1] on the non-negative side of side_val, given
+// side_val(0) = flo >= 0 > fhi = side_val(1): Illinois (regula falsi that
+// halves the retained end's value), with a bisection step whenever the
+// bracket did not halve over two steps, run to the last representable th.
+// Returns lo (side_val >= 0); *hi_out the first th past it.
+template <class S>
+__device__ __forceinline__ double last_nonneg(S& side_val, double flo, double fhi,
+                                              double* hi_out) {
+  double lo = 0.0, hi = 1.0;
+  int last = 0;
+  double width = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = (lo * fhi - hi * flo) / (fhi - flo);
+    if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (it & 1) width = hi - lo;
+    const double fm = side_val(mid);
+    if (fm >= 0.0) {
+      lo = mid;
+      flo = fm;
+      if (last > 0) fhi *= 0.5;
+      last = 1;
+    } else {
+      hi = mid;
+      fhi = fm;
+      if (last < 0) flo *= 0.5;
+      last = -1;
+    }
+  }
+  *hi_out = hi;
+  return lo;
+}
+
 // One attempted Dormand-Prince step.  Returns -1 to continue, else the final
 // ray status.  hook.on_accept sees every accepted step (start, end, stages).
 template <class Hook>
@@ -183,31 +217,11 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
       const double rr = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
       return sgn * (3.0 * xd[2] * mx - L.c.m2 * rr);
     };
-    double lo = 0.0, hi = 1.0;
     double flo = side_val(0.0), fhi = side_val(1.0);
     if (!(flo >= 0.0)) flo = 0.0;                  // the start is on its own side
     if (!(fhi < 0.0)) fhi = -1e-300;
-    int last = 0;
-    double width = 1.0;
-    for (int it = 0; it < 200; ++it) {
-      double mid = (lo * fhi - hi * flo) / (fhi - flo);
-      if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
-      if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (it & 1) width = hi - lo;
-      const double fm = side_val(mid);
-      if (fm >= 0.0) {
-        lo = mid;
-        flo = fm;
-        if (last > 0) fhi *= 0.5;
-        last = 1;
-      } else {
-        hi = mid;
-        fhi = fm;
-        if (last < 0) flo *= 0.5;
-        last = -1;
-      }
-    }
+    double hi;
+    const double lo = last_nonneg(side_val, flo, fhi, &hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;             // already at the cone: switch here
@@ -225,7 +239,7 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
     hook.on_accept(L, y, yn, k1, k3, k4, k5, k6, k7, h);
     const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
     if (rnew2 >= p.r_out * p.r_out) {
-      // locate |x(th)| = r_out on the continuous extension by bisection
+      // locate |x(th)| = r_out on the continuous extension
       double r3[6], r4[6], r5[6];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -236,17 +250,22 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
                      DP::d6 * k6[i] + DP::d7 * k7[i]);
         t[i] = r2;
       }
-      double lo = 0.0, hi = 1.0;
-      for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
+      // r_out^2 - |x(th)|^2 changes sign on [0, 1]: Illinois to the last
+      // representable th (the root to rounding, in ~10 evaluations)
+      const double ro2 = p.r_out * p.r_out;
+      auto inside = [&](double th) {
         double xd[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
-          xd[i] = y[i] + mid * (t[i] + (1.0 - mid) * (r3[i] + mid * (r4[i] + (1.0 - mid) * r5[i])));
-        const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
-        if (rd2 < p.r_out * p.r_out) lo = mid; else hi = mid;
-      }
+          xd[i] = y[i] + th * (t[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+        return ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+      };
+      double flo = ro2 - (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+      if (!(flo >= 0.0)) flo = 0.0;
+      double fhi = ro2 - rnew2;
+      if (!(fhi < 0.0)) fhi = -1e-300;
+      double hi;
+      const double lo = last_nonneg(inside, flo, fhi, &hi);
       const double th = 0.5 * (lo + hi);
 #pragma unroll
       for (int i = 0; i < 6; ++i)

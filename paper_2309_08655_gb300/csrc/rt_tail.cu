@@ -242,16 +242,20 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
     ++L.na;
     const double rnew2 = ynf[0] * ynf[0] + ynf[1] * ynf[1] + ynf[2] * ynf[2];
     if (rnew2 >= p.r_out * p.r_out) {
-      double lo = 0.0, hi = 1.0;
-      for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
+      // |x(th)| = r_out on the continuous extension: Illinois, as advance()
+      const double ro2 = p.r_out * p.r_out;
+      auto inside = [&](double th) {
         double xd[6];
-        gather6(gm, base, y + mid * (r2c + (1.0 - mid) * (r3c + mid * (r4c + (1.0 - mid) * r5c))),
+        gather6(gm, base, y + th * (r2c + (1.0 - th) * (r3c + th * (r4c + (1.0 - th) * r5c))),
                 xd);
-        const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
-        if (rd2 < p.r_out * p.r_out) lo = mid; else hi = mid;
-      }
+        return ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+      };
+      double flo = ro2 - (yfull[0] * yfull[0] + yfull[1] * yfull[1] + yfull[2] * yfull[2]);
+      if (!(flo >= 0.0)) flo = 0.0;
+      double fhi = ro2 - rnew2;
+      if (!(fhi < 0.0)) fhi = -1e-300;
+      double hi;
+      const double lo = last_nonneg(inside, flo, fhi, &hi);
       const double th = 0.5 * (lo + hi);
       L.yc = y + th * (r2c + (1.0 - th) * (r3c + th * (r4c + (1.0 - th) * r5c)));
       L.lam += th * h;

@@ -393,15 +393,36 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
     }
     const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
     if (rnew2 >= p.r_out * p.r_out) {
-      // locate |x(th)| = r_out on the continuous extension
+      // locate |x(th)| = r_out on the continuous extension: Illinois on
+      // r_out^2 - |x(th)|^2 (FP64 values), th in FP32 to its last bit
+      const double ro2 = p.r_out * p.r_out;
       float lo = 0.0f, hi = 1.0f;
-      for (int it = 0; it < 60; ++it) {
-        const float mid = 0.5f * (lo + hi);
+      double flo = ro2 - (L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+      if (!(flo >= 0.0)) flo = 0.0;
+      double fhi = ro2 - rnew2;
+      if (!(fhi < 0.0)) fhi = -1e-300;
+      int last = 0;
+      float width = 1.0f;
+      for (int it = 0; it < 100; ++it) {
+        float mid = (float)(((double)lo * fhi - (double)hi * flo) / (fhi - flo));
+        if ((it & 1) && hi - lo > 0.5f * width) mid = 0.5f * (lo + hi);
+        if (!(mid > lo && mid < hi)) mid = 0.5f * (lo + hi);
         if (mid <= lo || mid >= hi) break;
+        if (it & 1) width = hi - lo;
         double xd[3];
         dense_x(L, h, mid, sR, r3, r4, r5, xd);
-        const double rd2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
-        if (rd2 < p.r_out * p.r_out) lo = mid; else hi = mid;
+        const double fm = ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+        if (fm >= 0.0) {
+          lo = mid;
+          flo = fm;
+          if (last > 0) fhi *= 0.5;
+          last = 1;
+        } else {
+          hi = mid;
+          fhi = fm;
+          if (last < 0) flo *= 0.5;
+          last = -1;
+        }
       }
       const float th = 0.5f * (lo + hi);
       double xd[3];
