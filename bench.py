@@ -46,20 +46,22 @@ NBINS = (64, 32, 128)
 # FP64 rate); FP32 128 lanes x 2 flop/clk/SM (80.5 TFLOP/s).
 SMS, CLK = 152, 2.070e9
 FP64_KERNELS = "trace_fp64_kernel + tail_fp64_kernel (one trace call)"
+LC_CUT_KM = 1.0      # backward IR cut on the conversion length (Sec. 4.4)
 PEAK_FP64 = SMS * 4 * CLK
 PEAK_FP32 = SMS * 256 * CLK
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace call
-# of this workload (FP64: the persistent trace launch plus its six-lane tail
-# launch), from a single-pass ncu launch list of
-# `bench.py --steps 1 --warmup 3 --no-cpu-baseline --no-backward --no-adjoint
-# --no-uneven`, valid for the kernel sources with the given SHA-256 prefix
-# (reported as null once they change).  Writes stay in L2 during the launch.
+# of this workload, one step per launch (1) and eight steps per launch (8)
+# (FP64: the persistent trace launch plus its six-lane tail launch; mixed: the
+# FP32 launch plus the FP64 pass and its tail), from a single-pass ncu launch
+# list of `bench.py --steps 8 --warmup 1 --no-cpu-baseline --no-backward
+# --no-adjoint --no-uneven --no-twisted`, valid for the kernel sources with the
+# given SHA-256 prefix (reported as null once they change).
 TRAFFIC = {
-    "fp64": (("rt_device.cuh", "rt_integrator.cuh", "rt_trace.cu", "rt_tail.cu"), "ec0274833a6ff00c",
-             {1: 35.5e6, 3: 141.2e6}),
-    "mixed": (("rt_device.cuh", "rt_trace_mixed.cu"), "b83e6145461ffe2a",
-              {1: 36.4e6, 3: 131.0e6}),
+    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "c14a6817cb338f4c",
+             {1: 38.2e6, 8: 475.0e6}),
+    "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_trace_mixed.cu'),
+              "67c453ced2a2e156", {1: 36.7e6, 8: 442.5e6}),
 }
 
 
@@ -722,8 +724,11 @@ def _adjoint_leg(args, dev):
 def _backward_leg(args, dev, stream, fl, rank):
     """Backward image plane: 1024 x 1024 pixels at inclination 60 deg, plane at
     1e4 R, impact parameters up to 50 R, on the aligned 200 km-surface star
-    (FP64, rtol 1e-10; and mixed precision, rtol 1e-8, compared with it).  A
-    seeded sample of the FP64 pixels is recomputed by the oracle on rank 0."""
+    (FP64, rtol 1e-10; and mixed precision, rtol 1e-8, compared with it), with
+    the paper's IR cut on the conversion length (L_c <= 1 km, Sec. 4.4): it
+    drops the near-tangent crossings whose 1/|dg/dl| diverges, which would let
+    a handful of pixels carry percents of the total.  A seeded sample of the
+    FP64 pixels is recomputed by the oracle on rank 0."""
     import numpy as np
     import torch
 
@@ -738,7 +743,8 @@ def _backward_leg(args, dev, stream, fl, rank):
     st = torch.empty((ny, nx), dtype=torch.uint8, device=dev)
     nc = torch.empty((ny, nx), dtype=torch.int32, device=dev)
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
-    rt.rt_trace_backward(star, 128, 128, incl, D, bmax, img, st, nc, ctr, opts=opts,
+    rt.rt_trace_backward(star, 128, 128, incl, D, bmax, img, st, nc, ctr,
+                         Lc_cut_km=LC_CUT_KM, opts=opts,
                          stream=stream)                                    # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = max(1, min(args.steps, 2))
@@ -746,13 +752,14 @@ def _backward_leg(args, dev, stream, fl, rank):
     ctr.zero_()
     e0.record(stream)
     for _ in range(reps):
-        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img, st, nc, ctr, opts=opts,
+        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img, st, nc, ctr,
+                         Lc_cut_km=LC_CUT_KM, opts=opts,
                              stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     c = ctr.cpu().numpy() / reps
-    out = {"workload": "backward_image_1024x1024_incl60_b50R", "precision": "fp64",
+    out = {"workload": "backward_image_1024x1024_incl60_b50R_Lc1km", "precision": "fp64",
            "ms_per_image": 1e3 * t, "pixels_per_s": nx * ny / t,
            "ray_steps_per_s": c[0] / t, "accepted_steps": c[0], "rejected_steps": c[1],
            "crossings": c[6], "dP_dOmega_W_per_sr": float(img.sum()),
@@ -767,13 +774,15 @@ def _backward_leg(args, dev, stream, fl, rank):
     img_m = torch.empty_like(img)
     st_m = torch.empty_like(st)
     nc_m = torch.empty_like(nc)
-    rt.rt_trace_backward(star, 128, 128, incl, D, bmax, img_m, st_m, nc_m, None, opts=om,
+    rt.rt_trace_backward(star, 128, 128, incl, D, bmax, img_m, st_m, nc_m, None,
+                         Lc_cut_km=LC_CUT_KM, opts=om,
                          stream=stream)                                    # warm-up
     torch.cuda.synchronize()
     ctr.zero_()
     e0.record(stream)
     for _ in range(reps):
-        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img_m, st_m, nc_m, ctr, opts=om,
+        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img_m, st_m, nc_m, ctr,
+                         Lc_cut_km=LC_CUT_KM, opts=om,
                              stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -803,7 +812,7 @@ def _backward_leg(args, dev, stream, fl, rank):
         b = np.stack([-bmax + (i + 0.5) * db, -bmax + (j + 0.5) * db], 1)
         t0 = time.perf_counter()
         v, _, nco = oracle.backward_points(oracle.star_vector(**kw), oracle.trace_opts(rtol=1e-10),
-                                           b, incl, D)
+                                           b, incl, D, Lc_cut_km=LC_CUT_KM)
         t_or = time.perf_counter() - t0
         ref = v * db * db
         got = img_h.ravel()[pick]
