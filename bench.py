@@ -753,8 +753,7 @@ def _backward_leg(args, dev, stream, fl, rank):
     e0.record(stream)
     for _ in range(reps):
         rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img, st, nc, ctr,
-                         Lc_cut_km=LC_CUT_KM, opts=opts,
-                             stream=stream)
+                             Lc_cut_km=LC_CUT_KM, opts=opts, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
@@ -782,8 +781,7 @@ def _backward_leg(args, dev, stream, fl, rank):
     e0.record(stream)
     for _ in range(reps):
         rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img_m, st_m, nc_m, ctr,
-                         Lc_cut_km=LC_CUT_KM, opts=om,
-                             stream=stream)
+                             Lc_cut_km=LC_CUT_KM, opts=om, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
     tm = e0.elapsed_time(e1) / 1e3 / reps
