@@ -319,7 +319,8 @@ def trace_backward(star, opts, nx, ny, incl, dist_over_R=1e4, bmax_over_R=50.0, 
     return img, st, nc
 
 
-def backward_points(star, opts, b, incl, dist_over_R=1e4, Lc_cut_km=0.0, nthreads=None):
+def backward_points(star, opts, b, incl, dist_over_R=1e4, Lc_cut_km=0.0, nthreads=None,
+                    variant: str = "strict"):
     """Backward integrand at plane points b (n, 2) in units of R: dP/dOmega per
     unit plane area [W / sr / R^2]; returns (value, status, ncross)."""
     b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 2)
@@ -327,7 +328,8 @@ def backward_points(star, opts, b, incl, dist_over_R=1e4, Lc_cut_km=0.0, nthread
     v = np.zeros(n)
     st = np.zeros(n, dtype=np.uint8)
     nc = np.zeros(n, dtype=np.int32)
-    lib().or_backward_points(_dp(star), _dp(opts), n, _dp(b), float(incl), float(dist_over_R),
+    L = lib() if variant == "strict" else lib_contracted()
+    L.or_backward_points(_dp(star), _dp(opts), n, _dp(b), float(incl), float(dist_over_R),
                              float(Lc_cut_km), _dp(v), _u8(st), _ip(nc),
                              nthreads or default_threads())
     return v, st, nc

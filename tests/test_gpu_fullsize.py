@@ -1,0 +1,272 @@
+"""Parity at the benchmark's full sizes, in the launch configurations that
+bench.py times, on sampled outputs that the FP64 oracle recomputes one by one.
+
+* 16 x 65536 forward rays (misaligned magnetar-like rotator, 16 axion masses),
+  two steps' batches in one persistent launch (continuous batching) in FP64
+  and in mixed precision: a seeded sample of rays plus the longest ones,
+  re-sampled and re-traced by the oracle from their own uniforms.
+* The 1024 x 1024 backward image at 60 deg (FP64 and mixed): a seeded sample
+  of lit and unlit pixels recomputed by the oracle.
+* The 256 uneven instances (forward batches and backward images in one
+  launch, mixed precision, replayed from a CUDA graph): every item finished
+  once, and sampled rays and pixels against the oracle.
+* The 2^18-ray adjoint gradient against central finite differences of the
+  GPU forward pipeline.
+
+Tolerances are those of the small-size tests: FP64 end points 1e-10 and
+pixels 1e-8 where the oracle's strict and FMA-contracted builds agree (the
+well-conditioned set); mixed precision p90 1e-5 (end points) / 1e-4 (pixels);
+gradient 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2309_08655_gb300 import inputs as I  # noqa: E402
+from paper_2309_08655_gb300 import rt  # noqa: E402
+
+from . import gpu_util as G  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2309_08655_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def _oracle_rays(oracle, kws, seeds, picks, nper, rtol):
+    """The oracle's own sample and trace of the picked rays (index within the
+    batch of nsub x nper), strict and contracted builds."""
+    out = []
+    for i in picks:
+        j, q = divmod(int(i), nper)
+        sv = oracle.star_vector(**kws[j])
+        u = I.sample_uniforms(seeds[j], 1, first=q)
+        st, _, s = oracle.sample(sv, u)
+        a, sa = st.copy(), s.copy()
+        oracle.trace_forward(sv, oracle.trace_opts(rtol=rtol), a, sa)
+        b, sb = st.copy(), s.copy()
+        oracle.trace_forward(sv, oracle.trace_opts(rtol=rtol), b, sb, variant="contracted")
+        out.append((a[:, 0], sa[0], b[:, 0], sb[0], s[0]))
+    return out
+
+
+@pytest.mark.parametrize("precision", [rt.PREC_FP64, rt.PREC_MIXED])
+def test_forward_full_size_continuous_batching(oracle, precision):
+    cfg = I.CONFIG1
+    nsub, nper, K = cfg["nsub"], cfg["n_per_sub"], 2
+    kws = I.stars_config1(cfg["seed"], nsub)
+    seeds = [cfg["seed"] * 1000 + j for j in range(nsub)]
+    stars = [rt.Star(rt.make_params(**kw)) for kw in kws]
+    batch = rt.Batch(stars * K, [nper] * (nsub * K))
+    N = nsub * nper
+    u = np.concatenate([I.sample_uniforms(sd, nper) for sd in seeds], axis=1)
+    ud = torch.from_numpy(np.ascontiguousarray(np.tile(u, (1, K)))).cuda()
+    st = torch.empty((8, K * N), dtype=torch.float64, device=G.dev())
+    w = torch.empty(K * N, dtype=torch.float64, device=G.dev())
+    s = torch.empty(K * N, dtype=torch.uint8, device=G.dev())
+    nacc = torch.zeros(K * N, dtype=torch.int32, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    mixed = precision == rt.PREC_MIXED
+    rtol = cfg["rtol_mixed"] if mixed else cfg["rtol"]
+    opts = rt.make_opts(rtol=rtol, r_out_over_R=cfg["r_out_over_R"], precision=precision,
+                        max_steps=cfg["max_steps"])
+    rt.rt_sample_batch(batch, ud, st, w, s)
+    rt.rt_trace_batch(batch, st, s, nacc, None, ctr, opts)
+    torch.cuda.synchronize()
+    st_g, s_g, na = G.to_np(st, s, nacc)
+    # both copies of the batch traced every ray once, to the same statuses
+    traced = s_g[:N] != rt.RAY_NO_ROOT
+    assert int(ctr.cpu()[2]) == 2 * traced.sum()
+    assert (s_g[:N] == s_g[N:]).mean() > 0.9999
+    rng = np.random.default_rng(11)
+    cand = np.flatnonzero(traced)
+    picks = np.concatenate([rng.choice(cand, 40, replace=False),
+                            cand[np.argsort(na[:N][cand])[-3:]]])
+    ref = _oracle_rays(oracle, kws, seeds, picks, nper, cfg["rtol"])
+    dev_ok, dev_all = [], []
+    for k, i in enumerate(picks):
+        a, sa, b, sb, s0 = ref[k]
+        for copy in range(K):
+            g = st_g[:, copy * N + i]
+            sg = s_g[copy * N + i]
+            dx = np.linalg.norm(g[:3] - a[:3]) / np.linalg.norm(a[:3])
+            dk = np.linalg.norm(g[3:6] - a[3:6]) / np.linalg.norm(a[3:6])
+            spread = max(np.linalg.norm(b[:3] - a[:3]) / np.linalg.norm(a[:3]),
+                         np.linalg.norm(b[3:6] - a[3:6]) / np.linalg.norm(a[3:6]))
+            if sg == sa:
+                dev_all.append(max(dx, dk))
+                if sa == sb and spread <= 1e-12:
+                    dev_ok.append(max(dx, dk))
+            if not mixed:
+                assert sg == sa or sa != sb or spread > 1e-12, (i, sg, sa)
+    assert len(dev_all) >= 0.9 * K * len(picks)
+    assert len(dev_ok) >= 0.5 * K * len(picks)
+    if mixed:
+        assert np.percentile(dev_all, 90) < 1e-5
+    else:
+        assert max(dev_ok) < 1e-10, max(dev_ok)
+
+
+def test_backward_full_size_image(oracle):
+    kw = I.star_config0()
+    star = rt.Star(rt.make_params(**kw))
+    nx = ny = 1024
+    incl, D, bmax = math.radians(60.0), 1e4, 50.0
+    res = {}
+    for prec, rtol in ((rt.PREC_FP64, 1e-10), (rt.PREC_MIXED, 1e-8)):
+        img = torch.empty((ny, nx), dtype=torch.float64, device=G.dev())
+        st = torch.empty((ny, nx), dtype=torch.uint8, device=G.dev())
+        nc = torch.empty((ny, nx), dtype=torch.int32, device=G.dev())
+        ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+        rt.rt_trace_backward(star, nx, ny, incl, D, bmax, img, st, nc, ctr,
+                             opts=rt.make_opts(rtol=rtol, precision=prec))
+        torch.cuda.synchronize()
+        res[prec] = G.to_np(img, st, nc, ctr)
+    ig, sg, ng, cg = res[rt.PREC_FP64]
+    assert int(cg[2]) == nx * ny and int(cg[6]) == int(ng.sum())
+    rng = np.random.default_rng(60)
+    lit = np.flatnonzero(ng.ravel() > 0)
+    pick = np.concatenate([rng.choice(lit, 48, replace=False),
+                           rng.choice(nx * ny, 16, replace=False)])
+    j, i = np.divmod(pick, nx)
+    db = 2.0 * bmax / nx
+    b = np.stack([-bmax + (i + 0.5) * db, -bmax + (j + 0.5) * db], 1)
+    sv = oracle.star_vector(**kw)
+    va, sa, na = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10), b, incl, D)
+    ref = va * db * db
+    # the contracted build of the same source: the well-conditioned pixels
+    vb, sb, nb = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10), b, incl, D,
+                                        variant="contracted")
+    got = ig.ravel()[pick]
+    scale = np.maximum(np.abs(ref), 1e-300)
+    good = (sa == sb) & (na == nb) & (np.abs(va - vb) / np.maximum(np.abs(va), 1e-300) <= 1e-10)
+    assert good.mean() > 0.8
+    assert np.array_equal(ng.ravel()[pick][good], na[good])
+    assert (np.abs(got - ref) / scale)[good].max() <= 1e-8
+    # mixed precision against the FP64 image on the same pixels
+    im, sm, nm, cm = res[rt.PREC_MIXED]
+    same = (nm == ng) & (sm == sg)
+    assert same.mean() > 0.9999
+    litm = same & (ng > 0)
+    rel = np.abs(im[litm] - ig[litm]) / np.abs(ig[litm])
+    assert np.percentile(rel, 90) <= 1e-4
+    assert abs(im[same].sum() - ig[same].sum()) <= 1e-3 * ig[same].sum()
+
+
+def test_uneven_instances_one_launch(oracle):
+    """The 256 instances as bench.py runs them: 128 forward batches and 128
+    backward images of different stars in one mixed-precision launch, replayed
+    from a CUDA graph.  Every ray and pixel ends once; sampled rays and pixels
+    of a few instances agree with the FP64 oracle to the mixed tolerance."""
+    insts = I.instances_config3()
+    fwd = [x for x in insts if x["mode"] == "forward"]
+    bwd = [x for x in insts if x["mode"] == "backward"]
+    stars = [rt.Star(rt.make_params(**x["star"])) for x in fwd]
+    counts = [x["n"] for x in fwd]
+    batch = rt.Batch(stars, counts)
+    N = batch.N
+    u = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [I.sample_uniforms(x["seed"], x["n"]) for x in fwd], axis=1))).cuda()
+    st = torch.empty((8, N), dtype=torch.float64, device=G.dev())
+    w = torch.empty(N, dtype=torch.float64, device=G.dev())
+    s = torch.empty(N, dtype=torch.uint8, device=G.dev())
+    hist = torch.empty((len(fwd), 16, 8, 32), dtype=torch.float64, device=G.dev())
+    oor = torch.empty(len(fwd), dtype=torch.float64, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    bstars, descs = [], []
+    for x in bwd:
+        sb = rt.Star(rt.make_params(**x["star"]))
+        r_max = max((2.0 * sb.info()["wp2_coef"]) ** (1.0 / 3.0), 1.5)
+        bstars.append(sb)
+        descs.append((x["side"], x["side"], x["incl"], 1e4, 1.3 * r_max, 0.0))
+    P = sum(d[0] * d[1] for d in descs)
+    image = torch.empty(P, dtype=torch.float64, device=G.dev())
+    ist = torch.empty(P, dtype=torch.uint8, device=G.dev())
+    inc = torch.empty(P, dtype=torch.int32, device=G.dev())
+    rt.rt_batch_set_images(batch, bstars, descs, image, ist, inc)
+    opts = rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED)
+    graph = rt.Graph(batch, u, st, w, s, ctr, opts, 16, 8, 32, 0.0, 9.0, hist, oor)
+    graph.launch()
+    torch.cuda.synchronize()
+    st_g, s_g, img, ist_g, inc_g, c = G.to_np(st, s, image, ist, inc, ctr)
+    traced = (s_g != rt.RAY_NO_ROOT).sum()
+    assert int(c[2]) == traced + P
+    assert np.all(np.isin(s_g, [rt.RAY_ESCAPED, rt.RAY_CAPTURED, rt.RAY_NO_ROOT,
+                                rt.RAY_MAXSTEPS]))
+    assert np.all(np.isin(ist_g, [rt.RAY_ESCAPED, rt.RAY_CAPTURED, rt.RAY_MAXSTEPS]))
+    assert int(c[6]) == int(inc_g.sum())
+    # sampled rays of the three largest non-empty forward instances
+    off = np.concatenate([[0], np.cumsum(counts)])
+    order = [k for k in np.argsort(counts)[::-1] if not stars[k].info()["empty"]][:3]
+    rng = np.random.default_rng(3)
+    devs, nsame, ntot = [], 0, 0
+    for k in order:
+        idx = np.flatnonzero(s_g[off[k]:off[k + 1]] != rt.RAY_NO_ROOT)
+        sv = oracle.star_vector(**fwd[k]["star"])
+        for q in rng.choice(idx, min(8, idx.size), replace=False):
+            u1 = I.sample_uniforms(fwd[k]["seed"], 1, first=int(q))
+            so, _, s0 = oracle.sample(sv, u1)
+            oracle.trace_forward(sv, oracle.trace_opts(rtol=1e-10), so, s0)
+            g = st_g[:, off[k] + q]
+            ntot += 1
+            if s0[0] == s_g[off[k] + q]:
+                nsame += 1
+                devs.append(max(np.linalg.norm(g[:3] - so[:3, 0]) / np.linalg.norm(so[:3, 0]),
+                                np.linalg.norm(g[3:6] - so[3:6, 0]) / np.linalg.norm(so[3:6, 0])))
+    assert nsame >= 0.9 * ntot
+    assert np.percentile(devs, 90) < 1e-5
+    # sampled lit pixels of the three largest images
+    poff = np.concatenate([[0], np.cumsum([d[0] * d[1] for d in descs])])
+    rels = []
+    for jj in np.argsort([d[0] for d in descs])[::-1][:3]:
+        d = descs[jj]
+        nx = d[0]
+        lit = np.flatnonzero(inc_g[poff[jj]:poff[jj + 1]] > 0)
+        if lit.size == 0:
+            continue
+        pick = rng.choice(lit, min(8, lit.size), replace=False)
+        yy, xx = np.divmod(pick, nx)
+        db = 2.0 * d[4] / nx
+        b = np.stack([-d[4] + (xx + 0.5) * db, -d[4] + (yy + 0.5) * db], 1)
+        sv = oracle.star_vector(**bwd[jj]["star"])
+        v, _, nco = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10), b, d[2], d[3])
+        got = img[poff[jj] + pick]
+        eq = nco == inc_g[poff[jj] + pick]
+        rels.extend((np.abs(got - v * db * db) / np.abs(v * db * db))[eq & (v != 0)])
+    assert len(rels) >= 8
+    assert np.percentile(rels, 90) < 1e-4
+
+
+def test_adjoint_full_size_matches_central_differences():
+    """The 2^18-ray gradient of the smoothed line flux (bench.py's adjoint
+    workload: m_a = 1e-5 eV, inclination 1.1 rad, kappa one theta-bin) against
+    central differences of the GPU forward pipeline at rtol 1e-12."""
+    from paper_2309_08655_gb300 import flux
+    kw = I.stars_config1()[0]
+    kw.update(m_a_eV=1e-5)
+    n = 1 << 18
+    kappa = (64.0 / math.pi) ** 2
+    p = torch.tensor([kw["m_a_eV"], kw["B0_G"], kw["theta_m"], kw["M_sun"], kw["R_km"], 1.1],
+                     dtype=torch.float64)
+    u = torch.from_numpy(I.sample_uniforms(4000, n)).cuda()
+    q = p.clone().requires_grad_(True)
+    F = flux.line_flux(q, kw, u, kappa)
+    F.backward()
+    g = q.grad.numpy()
+    hs = 1e-6 * np.abs(p.numpy())
+    hs[2] = hs[5] = 1e-6
+    g_fd = np.zeros(6)
+    for k in range(6):
+        e = torch.zeros(6, dtype=torch.float64)
+        e[k] = hs[k]
+        Fp = float(flux.flux_forward(p + e, kw, u, kappa, rtol=1e-12)[0].cpu()[0])
+        Fm = float(flux.flux_forward(p - e, kw, u, kappa, rtol=1e-12)[0].cpu()[0])
+        g_fd[k] = (Fp - Fm) / (2.0 * hs[k])
+    rel = np.abs(g - g_fd) / np.abs(g_fd)
+    assert np.all(rel < 1e-5), (g, g_fd, rel)
