@@ -98,6 +98,11 @@ def lib_contracted():
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                         ctypes.POINTER(ctypes.c_uint8),
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.or_backward_points.restype = None
+        L.or_backward_points.argtypes = [dp, dp, ctypes.c_long, dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, dp,
+                                         ctypes.POINTER(ctypes.c_uint8),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         _lib_contracted = L
     return _lib_contracted
 
