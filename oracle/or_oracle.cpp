@@ -109,6 +109,25 @@ static T resonance_h(const Star& s, const double m[3], const double n[3], const 
   return Eg - Ea;
 }
 
+// h = E_gamma - E_a at a point x (units of R) of the leaf selected by (khat,
+// omega_inf): the local axion momentum is |k| khat with |k|^2 = omega_inf^2 / A
+// - m_a^2 there.  Its gradient (dual numbers over x) is the normal of the
+// conversion surface.
+template <class T>
+static T resonance_h_at(const Star& s, const double m[3], const double khat[3],
+                        double omega_inf, const T x[3]) {
+  T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  T A = 1.0 - s.rs / r;
+  T K2 = omega_inf * omega_inf / A - 1.0;
+  T Ea = sqrt(1.0 + K2);
+  T wp2 = plasma_freq2(s, m, x);
+  T B[3];
+  dipole_field(m, x, B);
+  T Bn = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  T kb = (khat[0] * B[0] + khat[1] * B[1] + khat[2] * B[2]) / Bn;
+  return photon_energy(s.dispersion, K2, wp2, kb * kb) - Ea;
+}
+
 // Root of h on (1, inf) (units of R): h(1) > 0 is required (the photon is
 // heavier than the axion at the surface); the bracket is widened by doubling
 // until h < 0 and then bisected to the last representable digit.  h is
@@ -220,9 +239,24 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
   const double mom = kloc_eV * kinf_eV / A;
   const double tdil = std::sqrt(A);
   const double fa_over_pdf = s.n_inf / (4.0 * PI * kinf_eV * kinf_eV);
-  const double W = vol * mom * tdil * Psi * fa_over_pdf / dhdr_eV * (4.0 * PI) * (4.0 * PI);
+  // the weight per unit of Psi (the conversion probability's numerator)
+  const double W1 = vol * mom * tdil * fa_over_pdf / dhdr_eV * (4.0 * PI) * (4.0 * PI);
   const double EV2_W = units::EV_J / units::HBAR_EV_S;  // 1 eV^2 of power in W
-  *w = W / (double)N * EV2_W;
+  *w = W1 * Psi / (double)N * EV2_W;
+  if (s.weight_mode == WEIGHT_UNIT_P) {
+    // conversion probability set to one (Sec. 5.1, Fig. flatiso right panel):
+    // divide by P_agamma = Psi / |k . dE| (Eq. CPAnisoCurved), with dE the
+    // proper-frame gradient of h = E_gamma - E_a, the normal of the surface
+    Dual<3> xd[3];
+    for (int i = 0; i < 3; ++i) xd[i] = Dual<3>::var(x[i], i);
+    Dual<3> hx = resonance_h_at<Dual<3>>(s, m, khat, omega_inf, xd);
+    double g[3] = {hx.d[0], hx.d[1], hx.d[2]};           // d h / d(x/R), units m_a
+    const double gn = g[0] * n[0] + g[1] * n[1] + g[2] * n[2];
+    double kg = 0.0;                                      // khat . proper gradient
+    for (int i = 0; i < 3; ++i) kg += khat[i] * (g[i] + (std::sqrt(A) - 1.0) * gn * n[i]);
+    const double kdE = kloc_eV * std::fabs(kg) * s.ma_eV / s.R_inv_eV;   // [eV^3]
+    *w = W1 * kdE / (double)N * EV2_W;
+  }
   // initial photon phase-space point: orthonormal k = |k| khat, covariant
   // Cartesian components k = k_o + (1/sqrt(A) - 1)(n.k_o) n
   double ko[3] = {kloc * khat[0], kloc * khat[1], kloc * khat[2]};

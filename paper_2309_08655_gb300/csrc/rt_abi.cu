@@ -114,7 +114,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unsupported resonance mode %d", p->resonance);
   if (p->fa_model != RT_FA_MAXWELL && p->fa_model != RT_FA_DELTA)
     return fail(RT_EUNSUPPORTED, "unknown fa_model %d", p->fa_model);
-  if (p->weight_mode != RT_WEIGHT_PAG)
+  if (p->weight_mode != RT_WEIGHT_PAG && p->weight_mode != RT_WEIGHT_UNIT_P)
     return fail(RT_EUNSUPPORTED, "unsupported weight_mode %d", p->weight_mode);
   if (p->prop_metric != RT_METRIC_FULL && p->prop_metric != RT_METRIC_FLAT)
     return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
@@ -164,6 +164,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
   h.plasma = p->plasma;
   h.fa_model = p->fa_model;
   h.phase_mode = p->phase_mode;
+  h.weight_mode = p->weight_mode;
   // Largest omega_p^2 / m_a^2 on the surface: max over n of
   // |3 n_z (m.n) - cos th_m| = (3 + |cos th_m|) / 2 (eigenvalues of the
   // symmetrised z m^T).  A kinematic resonance needs omega_p > m_a somewhere.
@@ -393,6 +394,8 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   if ((st = check_image(nx, ny, incl_rad, dist_over_R, bmax_over_R, Lc_cut_km)) != RT_OK)
     return st;
   if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
+  if (s->p.weight_mode != RT_WEIGHT_PAG)
+    return fail(RT_EUNSUPPORTED, "rt_trace_backward needs RT_WEIGHT_PAG");
   if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
   if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
@@ -490,6 +493,8 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   const rt_star_params& p = s->p;
   const rtk::StarDev& h = s->h;
   if (p.plasma != RT_PLASMA_GJ) return fail(RT_EUNSUPPORTED, "the gradient needs RT_PLASMA_GJ");
+  if (p.weight_mode != RT_WEIGHT_PAG)
+    return fail(RT_EUNSUPPORTED, "the gradient needs RT_WEIGHT_PAG");
   if (!(p.M_sun > 0) || !(p.B0_G > 0))
     return fail(RT_EINVAL, "the gradient needs M_sun > 0 and B0_G > 0");
   typedef rtk::Dual<rtk::NSAMP_TANGENTS> D5;
@@ -772,6 +777,8 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
   for (int32_t j = 0; j < nimg; ++j) {
     const rt_image_desc& d = descs[j];
     if (!stars[j]) return fail(RT_EINVAL, "image %d: star is NULL", j);
+    if (stars[j]->p.weight_mode != RT_WEIGHT_PAG)
+      return fail(RT_EUNSUPPORTED, "image %d: backward images need RT_WEIGHT_PAG", j);
     if ((st = check_image(d.nx, d.ny, d.incl_rad, d.dist_over_R, d.bmax_over_R, d.Lc_cut_km)) !=
         RT_OK)
       return st;

@@ -773,6 +773,7 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
     v.plasma = d.plasma;
     v.fa_model = d.fa_model;
     v.phase_mode = d.phase_mode;
+    v.weight_mode = d.weight_mode;
   }
   P.R_km = a.star->R_km;
   P.ma_eV = a.star->ma_eV;

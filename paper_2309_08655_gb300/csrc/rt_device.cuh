@@ -40,6 +40,7 @@ struct StarDev {
   double w_unit;      // 1 eV^2 of power in W
   double rlc;         // light-cylinder radius / R (open field lines of the twisted model)
   int32_t dispersion, plasma, fa_model, phase_mode;
+  int32_t weight_mode;  // WEIGHT_PAG or WEIGHT_UNIT_P
 };
 
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
@@ -48,6 +49,7 @@ enum {
   PLASMA_TWISTED = 5
 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
+enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 enum {
   RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,

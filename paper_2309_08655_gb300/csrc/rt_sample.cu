@@ -34,6 +34,7 @@ __global__ void sample_kernel(SampleParams p) {
   c.plasma = s.plasma;
   c.fa_model = s.fa_model;
   c.phase_mode = s.phase_mode;
+  c.weight_mode = s.weight_mode;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double u[6];

@@ -30,7 +30,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "rt_device.cuh"
+#include "rt_dual.cuh"
 
 namespace rtk {
 namespace sampling {
@@ -124,6 +127,7 @@ struct SampConst {
   double v0, psi_fixed, plasma_a, g_eV, w_unit;
   double rlc;     // light-cylinder radius / R (twisted model: open field lines excluded)
   int disp, plasma, fa_model, phase_mode;
+  int weight_mode;
 };
 
 template <class T>
@@ -167,6 +171,46 @@ __device__ __forceinline__ void line_plasma_t(int plasma, const T& PR, double pa
     }
     default: P = T(0.0); dP = T(0.0); break;
   }
+}
+
+// Gradient of G (units 1/R) at the point x (units of R) of the leaf selected by
+// (khat = q, W2 = omega_inf^2): the header's G with the angular factors and
+// A evaluated at x itself (dual numbers over x).  Along the radial line it is
+// G' of the root search; across it, the tilt of the conversion surface.
+__device__ __forceinline__ void grad_G(const SampConst<double>& s, double m0, double m1,
+                                       double m2, const double* q, double W2, const double* x,
+                                       double* g) {
+  typedef Dual<3> D3;
+  D3 X[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) X[i] = D3::var(x[i], i);
+  const D3 r = rt_sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+  const D3 ir = D3(1.0) / r;
+  const D3 n0 = X[0] * ir, n1 = X[1] * ir, n2 = X[2] * ir;
+  const D3 mu = D3(m0) * n0 + D3(m1) * n1 + D3(m2) * n2;
+  const D3 A = D3(1.0) - D3(s.rs) * ir;
+  const D3 K2 = D3(W2) / A - D3(1.0);
+  D3 P(0.0);
+  switch (s.plasma) {
+    case PLASMA_GJ: P = D3(s.cp) * ir * ir * ir * dabs(D3(3.0) * n2 * mu - D3(m2)); break;
+    case PLASMA_TWISTED: P = D3(s.cp) * (D3(1.0) - mu * mu) * ir * ir * ir * ir; break;
+    case PLASMA_HOMOG: P = D3(s.plasma_a); break;
+    case PLASMA_LINEAR_Z: P = D3(s.plasma_a) * X[2]; break;
+    case PLASMA_RADIAL: P = D3(s.plasma_a) * ir * ir * ir; break;
+    default: break;
+  }
+  D3 G;
+  if (s.disp == DISP_ISO) {
+    G = P - D3(1.0);
+  } else {
+    const D3 b0 = D3(3.0) * mu * n0 - D3(m0), b1 = D3(3.0) * mu * n1 - D3(m1),
+             b2 = D3(3.0) * mu * n2 - D3(m2);
+    const D3 kb = D3(q[0]) * b0 + D3(q[1]) * b1 + D3(q[2]) * b2;
+    const D3 s2 = D3(1.0) - kb * kb / (D3(3.0) * mu * mu + D3(1.0));
+    G = P * (D3(1.0) + K2 * s2) - (D3(1.0) + K2);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) g[i] = G.d[i];
 }
 
 // One sample from its six uniforms (the sample coordinates and the weight
@@ -270,15 +314,17 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
   const T K2 = T(L.W2) / A - T(1.0);
   const T E2 = T(1.0) + K2;
   const T E = rt_sqrt(E2);
-  T dhdr, shape;
+  T dhdr, shape, hden;   // hden: dh = dG / hden
   if (s.disp == DISP_ISO) {
     dhdr = dP / (T(2.0) * E);
+    hden = T(2.0) * E;
     shape = s2;
   } else {
     const T dK2 = -T(L.W2) * s.rs / (rT * rT * A * A);
     const T dG = dP * (T(1.0) + K2 * s2) + P * s2 * dK2 - dK2;
     const T ym = K2 * P * c2 / E2;
     dhdr = dG / (T(2.0) * E * (E2 - ym));
+    hden = T(2.0) * E * (E2 - ym);
     const T D = c2 * P * (P - T(2.0) * E2) + E2 * E2;
     shape = E2 * E2 * s2 / D;
   }
@@ -288,8 +334,30 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
   const T Psi = T(0.5 * PI * s.g_eV * s.g_eV) * Bmag * Bmag * shape * (E * s.ma_eV);
   const T r_eV = rT * s.R_eV;
   const T dh_eV = tabs(dhdr) * s.ma_eV / s.R_eV;
-  const T W = T(4.0 * PI) * r_eV * r_eV * (kloc / T(kinf)) * s.n_inf * Psi / (A * dh_eV);
-  o.w = W / T(nsamp) * T(s.w_unit);
+  // the weight per unit of Psi (the conversion probability's numerator)
+  const T W1 = T(4.0 * PI) * r_eV * r_eV * (kloc / T(kinf)) * s.n_inf / (A * dh_eV);
+  o.w = W1 * Psi / T(nsamp) * T(s.w_unit);
+  if constexpr (std::is_same<T, double>::value) {
+    if (s.weight_mode == WEIGHT_UNIT_P) {
+      // conversion probability set to one (Sec. 5.1): divide by
+      // P_agamma = Psi / |k . dE| (Eq. CPAnisoCurved), dE the proper-frame
+      // gradient of h = E_gamma - E_a; dh = dG / (2 E (E^2 - y_minus)) (as h')
+      const double q[3] = {q0, q1, q2};
+      const double xr[3] = {rT * n0, rT * n1, rT * n2};
+      double g[3];
+      grad_G(s, m0, m1, m2, q, L.W2, xr, g);
+      const double gn = g[0] * n0 + g[1] * n1 + g[2] * n2;
+      const double sA = sqrt(A);
+      double kg = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double ni = (i == 0) ? n0 : (i == 1) ? n1 : n2;
+        kg += q[i] * (g[i] + (sA - 1.0) * gn * ni);
+      }
+      const double kdE = kloc * s.ma_eV * fabs(kg / hden) * s.ma_eV / s.R_eV;   // [eV^3]
+      o.w = W1 * kdE / nsamp * s.w_unit;
+    }
+  }
   // photon phase-space point: orthonormal k = |k| khat; covariant Cartesian
   // k = k_o + (1/sqrt(A) - 1) (n.k_o) n
   const T nko = kloc * T(n0 * q0 + n1 * q1 + n2 * q2);

@@ -258,3 +258,39 @@ def test_tail_mode_matches_one_lane_per_ray(oracle, which):
     assert G.rel_state_diff(st_a[:, g], ref[:, g]).max() < 1e-10
     assert c_a[2] == c_b[2] == traced.sum()          # every ray finished once
     assert abs(int(c_a[0]) - int(c_b[0])) <= 0.01 * int(c_b[0])
+
+
+@pytest.mark.parametrize("which", ["misaligned_gj", "twisted_iso", "flat_sphere"])
+def test_unit_probability_weights(oracle, which):
+    """RT_WEIGHT_UNIT_P (conversion probability set to one): the same samples
+    as the default mode, weights against the oracle's to 1e-11; the oracle
+    differentiates h = E_gamma - E_a by dual numbers, the GPU dG by dual
+    numbers and divides by the same factor as for h'."""
+    if which == "misaligned_gj":
+        kw = I.stars_config1()[5]
+    elif which == "twisted_iso":
+        kw = I.star_config0()
+        kw.update(M_sun=1.5, R_km=11.0, B0_G=1.6e14, P_s=3.76, theta_m=0.5, m_a_eV=1e-3,
+                  phase_mode=1, plasma=rt.PLASMA_TWISTED, plasma_a=0.2, dispersion=1)
+    else:
+        kw = I.star_config0()
+        kw.update(M_sun=0.0, m_a_eV=1e-5, plasma=rt.PLASMA_RADIAL, plasma_a=8.0, dispersion=1)
+    kw = dict(kw, weight_mode=rt.WEIGHT_UNIT_P)
+    u = I.sample_uniforms(500, 2048)
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, u)
+    st_g, w_g, s_g = G.to_np(st_d, w_d, s_d)
+    st_o, w_o, s_o = oracle.sample(_star_vec(oracle, kw), u)
+    assert np.array_equal(s_g, s_o)
+    ok = s_o == oracle.RAY_READY
+    assert ok.sum() > 200
+    assert G.rel_state_diff(st_g[:, ok], st_o[:, ok]).max() < 1e-12
+    assert np.abs(w_g[ok] / w_o[ok] - 1).max() < 1e-11
+    # the default mode samples the same states with other weights
+    _, st_p, w_p, s_p, _ = G.gpu_sample(dict(kw, weight_mode=rt.WEIGHT_PAG), u)
+    assert np.array_equal(G.to_np(s_p)[0], s_g)
+    assert not np.allclose(G.to_np(w_p)[0][ok], w_g[ok])
+    # the backward tracer and the gradient need the conversion probability
+    img = torch.empty((2, 2), dtype=torch.float64, device=G.dev())
+    st2 = torch.empty((2, 2), dtype=torch.uint8, device=G.dev())
+    with pytest.raises(rt.RtError):
+        rt.rt_trace_backward(star, 2, 2, 0.3, 1e4, 3.0, img, st2)

@@ -199,3 +199,34 @@ def test_isotropic_twisted_power_matches_surface_quadrature(oracle, P_s):
     quad = _iso_power_quadrature_twisted(oracle, kw)
     assert sig / mc < 0.05
     assert abs(mc - quad) < 4 * sig, (mc, quad, sig)
+
+
+def test_unit_probability_weights_give_the_axion_flux_through_the_surface(oracle):
+    """With the conversion probability set to one (weight_mode 1), the power is
+    the axion energy flux through the conversion surface, int dSigma int d^3k
+    f_a |cos theta_n| v_a omega = int dSigma n_inf <|k| |cos|>.  Flat space
+    (M = 0), isotropic dispersion and the spherical test medium a (R/r)^3 make
+    the surface the sphere r0 = a^(1/3) R, so the total is
+    4 pi r0^2 n_inf <|k|> / 2 with <|k|> = 2 k0 / sqrt(pi) for the Maxwellian."""
+    kw = dict(M_sun=0.0, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5, dispersion=1,
+              plasma=4, plasma_a=8.0, weight_mode=1)
+    star = oracle.star_vector(**kw)
+    c = oracle.star_constants(star)
+    n = 40000
+    u = np.random.default_rng(23).random((6, n))
+    st, w, status = oracle.sample(star, u)
+    assert np.all(status == oracle.RAY_READY)
+    W = w * n
+    mc, sig = W.mean(), W.std() / np.sqrt(n)
+    m = kw["m_a_eV"]
+    r0 = 2.0 * kw["R_km"] / HBARC_EV_KM                      # a^(1/3) = 2, in eV^-1
+    k0 = m * 200.0 / C_KM_S
+    P = 4 * np.pi * r0 ** 2 * c["n_inf_eV3"] * k0 / np.sqrt(np.pi) * EV_J / HBAR_EV_S
+    assert sig / mc < 0.02
+    assert abs(mc - P) < 4 * sig, (mc, P, sig)
+    # the per-sample weight is |k cos| per unit of the surface-and-momentum
+    # measure: independent of B0 and the coupling, unlike the default weights
+    st2, w2, _ = oracle.sample(oracle.star_vector(**dict(kw, B0_G=3e14, g_GeVinv=5e-12)), u)
+    assert np.array_equal(w2, w)
+    _, w_pag, _ = oracle.sample(oracle.star_vector(**dict(kw, weight_mode=0)), u)
+    assert not np.allclose(w_pag, w)
