@@ -39,8 +39,13 @@ __device__ __forceinline__ int find_star_t(const TraceParams& p, int64_t i) {
 }
 
 // Component c (0-2: dx_c/dl, 3-5: dk_{c-3}/dl) of ham_rhs at the full state y.
-// The scalar prefix is evaluated by every lane; the component tail by index.
-__device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp) {
+// The scalar prefix is evaluated by every lane, except that its three dot
+// products and its two independent reciprocal square roots are spread over
+// the group's lanes (one FP64 instruction sequence for all, then shuffles:
+// the same operations and operands, so the same results); the component tail
+// by index.
+__device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp, unsigned gm,
+                           int base) {
   const double x0 = y[0], x1 = y[1], x2 = y[2], k0 = y[3], k1 = y[4], k2 = y[5];
   const double r2 = x0 * x0 + x1 * x1 + x2 * x2;
   const double ir = rsqrt(r2);
@@ -48,15 +53,26 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp)
   const double ir2 = ir * ir;
   const double A = 1.0 - c.rs * ir;
   const double Am1 = -c.rs * ir;
-  const double qA = rsqrt(A);
+  const int j = comp < 3 ? comp : comp - 3;
+  // n.k (lane 0), m.n (lane 1), k.m (lane 2) in one pass
+  const double a0 = j == 0 ? n0 : (j == 1 ? c.m0 : k0);
+  const double a1 = j == 0 ? n1 : (j == 1 ? c.m1 : k1);
+  const double a2 = j == 0 ? n2 : (j == 1 ? c.m2 : k2);
+  const double b0 = j == 0 ? k0 : (j == 1 ? n0 : c.m0);
+  const double b1 = j == 0 ? k1 : (j == 1 ? n1 : c.m1);
+  const double b2 = j == 0 ? k2 : (j == 1 ? n2 : c.m2);
+  const double dot = a0 * b0 + a1 * b1 + a2 * b2;
+  const double kr = __shfl_sync(gm, dot, base);
+  const double mu = __shfl_sync(gm, dot, base + 1);
+  const double km = __shfl_sync(gm, dot, base + 2);
+  // 1/sqrt(A) (lanes 0-2) and 1/sqrt(3 mu^2 + 1) (lanes 3-5) in one pass
+  const double rq = rsqrt(comp < 3 ? A : 3.0 * mu * mu + 1.0);
+  const double qA = __shfl_sync(gm, rq, base);
   const double iA = qA * qA;
   const double W = c.W2 * iA;
-  const double kr = n0 * k0 + n1 * k1 + n2 * k2;
-  const int j = comp < 3 ? comp : comp - 3;
   const double nj = j == 0 ? n0 : (j == 1 ? n1 : n2);
   const double kj = j == 0 ? k0 : (j == 1 ? k1 : k2);
   const double mj = j == 0 ? c.m0 : (j == 1 ? c.m1 : c.m2);
-  const double mu = c.m0 * n0 + c.m1 * n1 + c.m2 * n2;
   double P = 0.0, dPj = 0.0;
   if (c.plasma == PLASMA_GJ) {
     const double F = 3.0 * n2 * mu - c.m2;
@@ -84,9 +100,8 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp)
   const bool aniso = (c.disp != DISP_ISO);
   double ib = 0.0, sA = 0.0, U = 0.0, Kp = 0.0, fac = 0.0, opsA = 0.0;
   if (aniso) {
-    ib = rsqrt(3.0 * mu * mu + 1.0);
+    ib = __shfl_sync(gm, rq, base + 3);
     sA = A * qA;
-    const double km = k0 * c.m0 + k1 * c.m1 + k2 * c.m2;
     U = 3.0 * mu * kr - km + 2.0 * mu * kr * (sA - 1.0);
     Kp = U * ib;
     fac = P * A * Kp * c.iW2;
@@ -156,21 +171,21 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
   const double y = L.yc;
   double K1 = L.f0c, K2, K3, K4, K5, K6, K7;
   gather6(gm, base, y + h * (DP::a21 * K1), t);
-  K2 = rhs_comp(L.c, t, cc);
+  K2 = rhs_comp(L.c, t, cc, gm, base);
   gather6(gm, base, y + h * (DP::a31 * K1 + DP::a32 * K2), t);
-  K3 = rhs_comp(L.c, t, cc);
+  K3 = rhs_comp(L.c, t, cc, gm, base);
   gather6(gm, base, y + h * (DP::a41 * K1 + DP::a42 * K2 + DP::a43 * K3), t);
-  K4 = rhs_comp(L.c, t, cc);
+  K4 = rhs_comp(L.c, t, cc, gm, base);
   gather6(gm, base, y + h * (DP::a51 * K1 + DP::a52 * K2 + DP::a53 * K3 + DP::a54 * K4), t);
-  K5 = rhs_comp(L.c, t, cc);
+  K5 = rhs_comp(L.c, t, cc, gm, base);
   gather6(gm, base,
           y + h * (DP::a61 * K1 + DP::a62 * K2 + DP::a63 * K3 + DP::a64 * K4 + DP::a65 * K5),
           t);
-  K6 = rhs_comp(L.c, t, cc);
+  K6 = rhs_comp(L.c, t, cc, gm, base);
   const double yn = y + h * (DP::b1 * K1 + DP::b3 * K3 + DP::b4 * K4 + DP::b5 * K5 + DP::b6 * K6);
   double ynf[6];
   gather6(gm, base, yn, ynf);
-  K7 = rhs_comp(L.c, ynf, cc);
+  K7 = rhs_comp(L.c, ynf, cc, gm, base);
   const double e = h * (DP::e1 * K1 + DP::e3 * K3 + DP::e4 * K4 + DP::e5 * K5 + DP::e6 * K6 +
                         DP::e7 * K7);
   const double sc = p.atol + p.rtol * fmax(fabs(y), fabs(yn));
@@ -229,7 +244,7 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;
-      L.f0c = rhs_comp(L.c, yfull, cc);
+      L.f0c = rhs_comp(L.c, yfull, cc, gm, base);
       L.h = h;
     } else {
       L.h_resume = h;
@@ -268,7 +283,7 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
     if (clipped) return RAY_LAMBDA_END;
     if (gj && L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, ynf[0], ynf[1], ynf[2]) < 0.0) {
       L.c.sig = -L.c.sig;
-      L.f0c = rhs_comp(L.c, ynf, cc);
+      L.f0c = rhs_comp(L.c, ynf, cc, gm, base);
     }
     if (L.switching) {
       L.h = L.h_resume;
@@ -336,7 +351,7 @@ __global__ void __launch_bounds__(128) tail_fp64_kernel(TraceParams p) {
         L.c.sig = sig;
         double yfull[6];
         gather6(gm, base, L.yc, yfull);
-        L.f0c = rhs_comp(L.c, yfull, cc);
+        L.f0c = rhs_comp(L.c, yfull, cc, gm, base);
         na0 = L.na;
         nr0 = L.nr;
         have = true;
