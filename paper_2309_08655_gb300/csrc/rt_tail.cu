@@ -42,8 +42,8 @@ __device__ __forceinline__ int find_star_t(const TraceParams& p, int64_t i) {
 // The scalar prefix is evaluated by every lane, except that its three dot
 // products and its two independent reciprocal square roots are spread over
 // the group's lanes (one FP64 instruction sequence for all, then shuffles:
-// the same operations and operands, so the same results); the component tail
-// by index.
+// the same operations and operands, so the same results); each lane then
+// takes its component from coefficients that all lanes form.
 __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp, unsigned gm,
                            int base) {
   const double x0 = y[0], x1 = y[1], x2 = y[2], k0 = y[3], k1 = y[4], k2 = y[5];
@@ -107,17 +107,17 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp,
     fac = P * A * Kp * c.iW2;
     opsA = 1.0 + 2.0 * sA;
   }
-  if (comp < 3) {
-    double g = 2.0 * (kj + Am1 * kr * nj);
-    if (aniso) g += (-2.0 * fac * ib) * (mu * opsA * nj - mj);
-    return g;
-  }
+  // Both kinds of component as out = al k_j + be n_j + ga m_j (+ dP_j one_m):
+  // every lane forms both coefficient sets (no divergence), then takes its own.
+  // position (c < 3): dH/dk_j = 2 (k_j + (A-1) kr n_j) - 2 fac ib (mu opsA n_j - m_j)
+  const double gk_be = 2.0 * Am1 * kr - 2.0 * fac * ib * mu * opsA;
+  const double gk_ga = 2.0 * fac * ib;
+  // momentum (c >= 3): -dH/dx_j, dH/dx_j = cA n_j + ckr (k_j - kr n_j)
+  //   + dP_j one_m + cdA n_j - 2 fac (a1r m_j + a2r k_j + an n_j)
   const double cA = (W * iA + kr * kr) * c.rs * ir2;
   const double ckr = 2.0 * Am1 * kr * ir;
-  double gx = cA * nj + ckr * (kj - kr * nj);
-  if (!aniso) {
-    gx += dPj;
-  } else {
+  double gx_al = ckr, gx_be = cA - ckr * kr, gx_ga = 0.0, one_m = 1.0;
+  if (aniso) {
     const double Kp2iW2 = Kp * Kp * c.iW2;
     const double ib3 = ib * ib * ib;
     const double a1 = ib * opsA * kr - 3.0 * mu * U * ib3;
@@ -125,12 +125,19 @@ __device__ double rhs_comp(const RayConst<double>& c, const double* y, int comp,
     const double a3 = ib * mu * kr * c.rs * ir2 * qA;
     const double a1r = a1 * ir, a2r = a2 * ir;
     const double an = a3 - a1r * mu - a2r * kr;
-    const double dKj = a1r * mj + a2r * kj + an * nj;
-    const double one_m = 1.0 - A * Kp2iW2;
+    one_m = 1.0 - A * Kp2iW2;
     const double cdA = -P * Kp2iW2 * c.rs * ir2;
-    gx += dPj * one_m + cdA * nj - 2.0 * fac * dKj;
+    const double m2f = -2.0 * fac;
+    gx_al += m2f * a2r;
+    gx_be += cdA + m2f * an;
+    gx_ga = m2f * a1r;
   }
-  return -gx;
+  const bool pos = comp < 3;
+  const double al = pos ? 2.0 : -gx_al;
+  const double be = pos ? gk_be : -gx_be;
+  const double ga = pos ? gk_ga : -gx_ga;
+  const double dp = pos ? 0.0 : -dPj * one_m;
+  return al * kj + be * nj + ga * mj + dp;
 }
 
 // Group state: lane c of a group owns component c; the rest is replicated.
