@@ -294,3 +294,23 @@ def test_unit_probability_weights(oracle, which):
     st2 = torch.empty((2, 2), dtype=torch.uint8, device=G.dev())
     with pytest.raises(rt.RtError):
         rt.rt_trace_backward(star, 2, 2, 0.3, 1e4, 3.0, img, st2)
+
+
+@pytest.mark.parametrize("dispersion", [0, 1])
+def test_flat_propagation_mode(oracle, dispersion):
+    """App. B's first approximation (RT_METRIC_FLAT): photons start with the
+    momenta of the curved-space resonance but propagate with M = 0 in
+    Hamilton's equations.  End points against the oracle's same mode (1e-10 on
+    the well-conditioned set), and they differ from the curved propagation."""
+    kw = dict(I.star_config0(), prop_metric=1, dispersion=dispersion)
+    u = I.sample_uniforms(600, 1024)
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _trace_parity(oracle, kw, u, rtol=1e-10)
+    traced = s0 == oracle.RAY_READY
+    assert (s_g[traced] == sref[traced]).mean() > 0.99
+    g = good & traced & (s_g == sref)
+    assert g.sum() > 0.3 * traced.sum()
+    assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+    cur = _trace_parity(oracle, dict(kw, prop_metric=0), u, rtol=1e-10)
+    esc = traced & (s_g == rt.RAY_ESCAPED) & (cur[6] == rt.RAY_ESCAPED)
+    assert esc.sum() > 100
+    assert np.median(G.rel_state_diff(st_g[:, esc], cur[5][:, esc])) > 1e-6

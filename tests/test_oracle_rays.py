@@ -235,3 +235,25 @@ def test_brute_force_rk4_richardson(oracle):
     good &= np.abs(b[:6] - a[:6]).max(axis=0) / 15 / scale < 1e-10
     assert good.sum() >= 8
     assert err[good].max() < 1e-11, err[good]
+
+
+def test_flat_propagation_keeps_vacuum_rays_straight(oracle):
+    """With M > 0 in the initial conditions but flat propagation (App. B) and
+    no plasma, H = -W^2 + |k|^2 and a ray is the straight line x + 2 k l with
+    constant k, whatever the mass."""
+    star = oracle.star_vector(M_sun=1.4, R_km=10.0, m_a_eV=1e-5, plasma=1, prop_metric=1,
+                              dispersion=1)
+    x0 = np.array([3.0, -2.0, 5.0]) * 10.0                  # km
+    k0 = np.array([0.3, 0.4, -0.1]) * 1e-5                  # eV, covariant
+    st = np.zeros((8, 1))
+    st[:3, 0] = x0
+    st[3:6, 0] = k0
+    st[6, 0] = 0.0
+    s = np.zeros(1, dtype=np.uint8)
+    lam = 2.0
+    oracle.trace_forward(star, oracle.trace_opts(rtol=1e-12, lambda_max=lam, r_out_over_R=1e6),
+                         st, s)
+    assert s[0] == oracle.RAY_LAMBDA_END
+    xs = x0 / 10.0 + 2.0 * (k0 / 1e-5) * lam
+    assert np.allclose(st[:3, 0] / 10.0, xs, rtol=1e-12, atol=1e-12)
+    assert np.allclose(st[3:6, 0], k0, rtol=1e-13, atol=0)
