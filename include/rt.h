@@ -68,7 +68,7 @@ enum {
 enum { RT_DISP_ANISO = 0, RT_DISP_ISO = 1 };
 enum { RT_RES_KINEMATIC = 0 };
 enum { RT_FA_MAXWELL = 0, RT_FA_DELTA = 1 };
-enum { RT_WEIGHT_PAG = 0, RT_WEIGHT_UNIT_P = 1 };
+enum { RT_WEIGHT_PAG = 0, RT_WEIGHT_UNIT_P = 1, RT_WEIGHT_RENORM = 2 };
 enum { RT_METRIC_FULL = 0, RT_METRIC_FLAT = 1 };
 enum { RT_PHASE_FIXED = 0, RT_PHASE_UNIFORM = 1 };
 enum {
@@ -96,8 +96,11 @@ enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
  *                  RT_WEIGHT_UNIT_P (the probability set to one, Sec. 5.1: each
  *                  weight divided by P_agamma = Psi / |k . dE|, dE the proper-frame
  *                  gradient of E_gamma - E_a, i.e. the axion energy flux through
- *                  the conversion surface; forward sampling only -- the backward
- *                  tracer and the gradient reject it)
+ *                  the conversion surface), or RT_WEIGHT_RENORM (that, times
+ *                  R_i = (1 cm^-3 / n_a(r_i)) (m_a / |k_a|) / sqrt(1 - r_s / r_i) of
+ *                  Eq. reweight, n_a = n_inf k_c / k0 the focused density of
+ *                  Sec. 4.3); forward sampling only -- the backward tracer and
+ *                  the gradient reject both)
  *   prop_metric    RT_METRIC_FULL, or RT_METRIC_FLAT (M = 0 in propagation only)
  *   phase_mode     RT_PHASE_FIXED or RT_PHASE_UNIFORM (psi = 2 pi u5 per sample)
  *   plasma         RT_PLASMA_GJ (Eq. GJDensity), RT_PLASMA_TWISTED (the twisted

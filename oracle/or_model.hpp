@@ -40,7 +40,7 @@ enum {
 };
 enum { METRIC_FULL = 0, METRIC_FLAT = 1 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
-enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1 };
+enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1, WEIGHT_RENORM = 2 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 
 // Parameter vector layout shared with the Python wrapper of the oracle.

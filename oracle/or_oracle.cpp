@@ -243,7 +243,7 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
   const double W1 = vol * mom * tdil * fa_over_pdf / dhdr_eV * (4.0 * PI) * (4.0 * PI);
   const double EV2_W = units::EV_J / units::HBAR_EV_S;  // 1 eV^2 of power in W
   *w = W1 * Psi / (double)N * EV2_W;
-  if (s.weight_mode == WEIGHT_UNIT_P) {
+  if (s.weight_mode == WEIGHT_UNIT_P || s.weight_mode == WEIGHT_RENORM) {
     // conversion probability set to one (Sec. 5.1, Fig. flatiso right panel):
     // divide by P_agamma = Psi / |k . dE| (Eq. CPAnisoCurved), with dE the
     // proper-frame gradient of h = E_gamma - E_a, the normal of the surface
@@ -256,6 +256,17 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
     for (int i = 0; i < 3; ++i) kg += khat[i] * (g[i] + (std::sqrt(A) - 1.0) * gn * n[i]);
     const double kdE = kloc_eV * std::fabs(kg) * s.ma_eV / s.R_inv_eV;   // [eV^3]
     *w = W1 * kdE / (double)N * EV2_W;
+    if (s.weight_mode == WEIGHT_RENORM) {
+      // Eq. reweight: R_i = (1 cm^-3 / n_a(r_i)) (m_a / |k_a(r_i)|) / sqrt(1 - r_s / r_i),
+      // with the focused density of the monochromatic distribution (Sec. 4.3),
+      // n_a = n_inf k_c / k0, k_c^2 = k0^2 + 2 G M m_a^2 / r
+      const double hbarc_cm = units::HBARC_EV_KM * 1e5;
+      const double per_cm3 = hbarc_cm * hbarc_cm * hbarc_cm;           // 1 cm^-3 in eV^3
+      const double k0 = s.v0 * s.ma_eV;
+      const double kc = std::sqrt(k0 * k0 + s.ma_eV * s.ma_eV * s.rs / r);
+      const double n_a = s.n_inf * kc / k0;
+      *w *= (per_cm3 / n_a) * (s.ma_eV / kloc_eV) / std::sqrt(A);
+    }
   }
   // initial photon phase-space point: orthonormal k = |k| khat, covariant
   // Cartesian components k = k_o + (1/sqrt(A) - 1)(n.k_o) n

@@ -114,7 +114,8 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unsupported resonance mode %d", p->resonance);
   if (p->fa_model != RT_FA_MAXWELL && p->fa_model != RT_FA_DELTA)
     return fail(RT_EUNSUPPORTED, "unknown fa_model %d", p->fa_model);
-  if (p->weight_mode != RT_WEIGHT_PAG && p->weight_mode != RT_WEIGHT_UNIT_P)
+  if (p->weight_mode != RT_WEIGHT_PAG && p->weight_mode != RT_WEIGHT_UNIT_P &&
+      p->weight_mode != RT_WEIGHT_RENORM)
     return fail(RT_EUNSUPPORTED, "unsupported weight_mode %d", p->weight_mode);
   if (p->prop_metric != RT_METRIC_FULL && p->prop_metric != RT_METRIC_FLAT)
     return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
@@ -532,6 +533,7 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   a.sc.psi_fixed = h.psi_fixed;
   a.sc.plasma_a = h.plasma_a;
   a.sc.rlc = h.rlc;
+  a.sc.per_cm3 = rtk::PER_CM3_EV3;
   a.sc.g_eV = h.g_eV;
   a.sc.w_unit = h.w_unit;
   a.sc.disp = h.dispersion;

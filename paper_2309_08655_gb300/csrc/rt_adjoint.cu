@@ -774,6 +774,7 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
     v.fa_model = d.fa_model;
     v.phase_mode = d.phase_mode;
     v.weight_mode = d.weight_mode;
+    v.per_cm3 = d.per_cm3;
   }
   P.R_km = a.star->R_km;
   P.ma_eV = a.star->ma_eV;

@@ -23,6 +23,8 @@
 namespace rtk {
 
 constexpr double PI = 3.14159265358979323846;
+// 1 cm^-3 in eV^3: (hbar c)^3 with hbar c = 1.973269804e-5 eV cm (CODATA 2018)
+constexpr double PER_CM3_EV3 = 1.973269804e-5 * 1.973269804e-5 * 1.973269804e-5;
 
 // Per-star constants (device copy built by rt_init_star).
 struct StarDev {
@@ -49,7 +51,7 @@ enum {
   PLASMA_TWISTED = 5
 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
-enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1 };
+enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1, WEIGHT_RENORM = 2 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
 enum {
   RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,

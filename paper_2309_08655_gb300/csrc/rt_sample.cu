@@ -35,6 +35,7 @@ __global__ void sample_kernel(SampleParams p) {
   c.fa_model = s.fa_model;
   c.phase_mode = s.phase_mode;
   c.weight_mode = s.weight_mode;
+  c.per_cm3 = PER_CM3_EV3;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double u[6];

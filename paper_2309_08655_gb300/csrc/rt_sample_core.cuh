@@ -126,6 +126,7 @@ struct SampConst {
   T rs, cp, sin_tm, cos_tm, B0_eV2, R_eV, n_inf, ma_eV;
   double v0, psi_fixed, plasma_a, g_eV, w_unit;
   double rlc;     // light-cylinder radius / R (twisted model: open field lines excluded)
+  double per_cm3; // 1 cm^-3 in eV^3 (the renormalised weights)
   int disp, plasma, fa_model, phase_mode;
   int weight_mode;
 };
@@ -338,7 +339,7 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
   const T W1 = T(4.0 * PI) * r_eV * r_eV * (kloc / T(kinf)) * s.n_inf / (A * dh_eV);
   o.w = W1 * Psi / T(nsamp) * T(s.w_unit);
   if constexpr (std::is_same<T, double>::value) {
-    if (s.weight_mode == WEIGHT_UNIT_P) {
+    if (s.weight_mode == WEIGHT_UNIT_P || s.weight_mode == WEIGHT_RENORM) {
       // conversion probability set to one (Sec. 5.1): divide by
       // P_agamma = Psi / |k . dE| (Eq. CPAnisoCurved), dE the proper-frame
       // gradient of h = E_gamma - E_a; dh = dG / (2 E (E^2 - y_minus)) (as h')
@@ -356,6 +357,13 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
       }
       const double kdE = kloc * s.ma_eV * fabs(kg / hden) * s.ma_eV / s.R_eV;   // [eV^3]
       o.w = W1 * kdE / nsamp * s.w_unit;
+      if (s.weight_mode == WEIGHT_RENORM) {
+        // Eq. reweight: x (1 cm^-3 / n_a(r)) (m_a / |k_a|) / sqrt(1 - r_s / r), the
+        // focused density of the monochromatic distribution n_inf k_c / k0,
+        // k_c^2 = k0^2 + m_a^2 r_s / r (Sec. 4.3)
+        const double kc_over_k0 = sqrt(s.v0 * s.v0 + s.rs / rT) / s.v0;
+        o.w *= (s.per_cm3 / (s.n_inf * kc_over_k0)) / kloc / sA;
+      }
     }
   }
   // photon phase-space point: orthonormal k = |k| khat; covariant Cartesian

@@ -23,7 +23,7 @@ RAY_NSTATUS = 8
 PREC_FP64, PREC_MIXED = 0, 1
 (PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL,
  PLASMA_TWISTED) = range(6)
-WEIGHT_PAG, WEIGHT_UNIT_P = 0, 1
+WEIGHT_PAG, WEIGHT_UNIT_P, WEIGHT_RENORM = 0, 1, 2
 
 
 class RtError(RuntimeError):

@@ -260,10 +260,12 @@ def test_tail_mode_matches_one_lane_per_ray(oracle, which):
     assert abs(int(c_a[0]) - int(c_b[0])) <= 0.01 * int(c_b[0])
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("which", ["misaligned_gj", "twisted_iso", "flat_sphere"])
-def test_unit_probability_weights(oracle, which):
-    """RT_WEIGHT_UNIT_P (conversion probability set to one): the same samples
-    as the default mode, weights against the oracle's to 1e-11; the oracle
+def test_unit_probability_weights(oracle, which, mode):
+    """RT_WEIGHT_UNIT_P (conversion probability set to one) and
+    RT_WEIGHT_RENORM (times R_i of Eq. reweight): the same samples as the
+    default mode, weights against the oracle's to 1e-11; the oracle
     differentiates h = E_gamma - E_a by dual numbers, the GPU dG by dual
     numbers and divides by the same factor as for h'."""
     if which == "misaligned_gj":
@@ -275,7 +277,7 @@ def test_unit_probability_weights(oracle, which):
     else:
         kw = I.star_config0()
         kw.update(M_sun=0.0, m_a_eV=1e-5, plasma=rt.PLASMA_RADIAL, plasma_a=8.0, dispersion=1)
-    kw = dict(kw, weight_mode=rt.WEIGHT_UNIT_P)
+    kw = dict(kw, weight_mode=mode)
     u = I.sample_uniforms(500, 2048)
     star, st_d, w_d, s_d, code = G.gpu_sample(kw, u)
     st_g, w_g, s_g = G.to_np(st_d, w_d, s_d)

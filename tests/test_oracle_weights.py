@@ -230,3 +230,52 @@ def test_unit_probability_weights_give_the_axion_flux_through_the_surface(oracle
     assert np.array_equal(w2, w)
     _, w_pag, _ = oracle.sample(oracle.star_vector(**dict(kw, weight_mode=0)), u)
     assert not np.allclose(w_pag, w)
+
+
+def test_renormalised_weights_count_surface_crossings(oracle):
+    """weight_mode 2 (Eq. reweight): the unit-probability weight times
+    R_i = (1 cm^-3 / n_a(r_i)) (m_a / |k_a|) / sqrt(1 - r_s / r_i).  In flat
+    space (n_a = n_inf, A = 1) the product no longer depends on the axion
+    speed: the total is 4 pi r0^2 m_a (1 cm^-3) <|cos|> = 2 pi r0^2 m_a cm^-3
+    on the sphere r0 = a^(1/3) R, for any velocity distribution."""
+    hbarc_cm = HBARC_EV_KM * 1e5
+    for fa_model, v0 in ((0, 200.0), (0, 600.0), (1, 200.0)):
+        kw = dict(M_sun=0.0, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5, dispersion=1,
+                  plasma=4, plasma_a=8.0, weight_mode=2, fa_model=fa_model, v0_kms=v0)
+        star = oracle.star_vector(**kw)
+        n = 40000
+        u = np.random.default_rng(24).random((6, n))
+        st, w, status = oracle.sample(star, u)
+        W = w * n
+        mc, sig = W.mean(), W.std() / np.sqrt(n)
+        r0 = 2.0 * kw["R_km"] / HBARC_EV_KM
+        P = 2 * np.pi * r0 ** 2 * kw["m_a_eV"] * hbarc_cm ** 3 * EV_J / HBAR_EV_S
+        assert sig / mc < 0.02
+        assert abs(mc - P) < 4 * sig, (fa_model, v0, mc, P, sig)
+
+
+def test_renormalised_weights_in_curved_space(oracle):
+    """With M > 0 the factor uses the focused density n_inf k_c / k0,
+    k_c^2 = k0^2 + m_a^2 r_s / r (Sec. 4.3), the sample's own local momentum
+    and the redshift; checked sample by sample against the unit weights."""
+    kw = dict(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5, dispersion=0)
+    u = np.random.default_rng(25).random((6, 2000))
+    st1, w1, s1 = oracle.sample(oracle.star_vector(**dict(kw, weight_mode=1)), u)
+    st2, w2, s2 = oracle.sample(oracle.star_vector(**dict(kw, weight_mode=2)), u)
+    assert np.array_equal(s1, s2) and np.array_equal(st1, st2)
+    ok = s1 == oracle.RAY_READY
+    c = oracle.star_constants(oracle.star_vector(**kw))
+    R = 10.0
+    r = np.linalg.norm(st1[:3, ok], axis=0) / R
+    A = 1 - c["rs_over_R"] / r
+    m = 1e-5
+    # |k_a| from the covariant state: k_o = k + (sqrt(A) - 1)(n.k) n
+    n = st1[:3, ok] / (r * R)
+    k = st1[3:6, ok]
+    kn = (n * k).sum(0)
+    ko = k + (np.sqrt(A) - 1) * kn * n
+    ka = np.linalg.norm(ko, axis=0)
+    k0 = m * 200.0 / C_KM_S
+    kc = np.sqrt(k0 ** 2 + m ** 2 * c["rs_over_R"] / r)
+    Ri = (HBARC_EV_KM * 1e5) ** 3 / (c["n_inf_eV3"] * kc / k0) * (m / ka) / np.sqrt(A)
+    assert np.allclose(w2[ok], w1[ok] * Ri, rtol=1e-12)
