@@ -35,13 +35,15 @@ _HDR = ["or_dual.hpp", "or_model.hpp", "or_dopri.hpp"]
 STAR_KEYS = [
     "M_sun", "R_km", "B0_G", "P_s", "theta_m", "psi", "m_a_eV", "g_GeVinv",
     "rho_GeV_cm3", "v0_kms", "dispersion", "resonance", "fa_model", "weight_mode",
-    "prop_metric", "phase_mode", "plasma", "plasma_a",
+    "prop_metric", "phase_mode", "plasma", "plasma_a", "rotation",
 ]
 STAR_DEFAULTS = dict(
     M_sun=1.0, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=0.0, psi=0.0, m_a_eV=1e-5,
     g_GeVinv=1e-12, rho_GeV_cm3=0.45, v0_kms=200.0, dispersion=0, resonance=0,
     fa_model=0, weight_mode=0, prop_metric=0, phase_mode=0, plasma=0, plasma_a=0.0,
+    rotation=0,
 )
+ROTATION_SNAPSHOT, ROTATION_RIGID = 0, 1
 DISP_ANISO, DISP_ISO = 0, 1
 PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL, PLASMA_TWISTED = range(6)
 RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT = 0, 1, 2, 3

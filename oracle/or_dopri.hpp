@@ -42,16 +42,17 @@ struct DP5 {
                                   69997945.0 / 29380423.0};
 };
 
-// One trial step from (y, f0 = f(y)) with step h.  Writes the 5th-order
+// One trial step from (y, f0 = f(y)) with step h, for a state of N
+// components (N = 6: x, k; N = 8: x, k, t, k_t).  Writes the 5th-order
 // solution, the local error estimate (5th minus 4th order) and all stages
 // (stage 7 is f(y_new), reused as the next step's first stage).
-template <class F>
-inline void dp5_step(F& f, const double y[6], const double f0[6], double h, double ynew[6],
-                     double err[6], double K[7][6]) {
-  for (int i = 0; i < 6; ++i) K[0][i] = f0[i];
-  double ys[6];
+template <class F, int N>
+inline void dp5_step(F& f, const double* y, const double* f0, double h, double* ynew,
+                     double* err, double (*K)[N]) {
+  for (int i = 0; i < N; ++i) K[0][i] = f0[i];
+  double ys[N];
   for (int s = 1; s < 7; ++s) {
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < N; ++i) {
       double acc = 0.0;
       for (int j = 0; j < s; ++j) acc += DP5::a[s][j] * K[j][i];
       ys[i] = y[i] + h * acc;
@@ -59,7 +60,7 @@ inline void dp5_step(F& f, const double y[6], const double f0[6], double h, doub
     f(ys, K[s]);
   }
   // stage 7 was evaluated at the 5th-order solution (row 7 of a equals b)
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < N; ++i) {
     double acc5 = 0.0, acce = 0.0;
     for (int j = 0; j < 7; ++j) {
       acc5 += DP5::b[j] * K[j][i];
@@ -71,9 +72,10 @@ inline void dp5_step(F& f, const double y[6], const double f0[6], double h, doub
 }
 
 // Dense output on [lambda_n, lambda_n + h] at fraction th in [0, 1].
-inline void dp5_dense(const double y[6], const double ynew[6], const double K[7][6], double h,
-                      double th, double out[6]) {
-  for (int i = 0; i < 6; ++i) {
+template <int N>
+inline void dp5_dense(const double* y, const double* ynew, const double (*K)[N], double h,
+                      double th, double* out) {
+  for (int i = 0; i < N; ++i) {
     double r1 = y[i];
     double r2 = ynew[i] - y[i];
     double r3 = h * K[0][i] - r2;
@@ -85,7 +87,10 @@ inline void dp5_dense(const double y[6], const double ynew[6], const double K[7]
   }
 }
 
-// RMS norm of the error, scaled by atol + rtol * max(|y|, |ynew|).
+// RMS norm of the error, scaled by atol + rtol * max(|y|, |ynew|), over the
+// six phase-space components x, k: with the eight-component state of a
+// rotating magnetosphere the clock t and k_t follow the step sequence that
+// x and k choose.
 inline double dp5_error_norm(const double y[6], const double ynew[6], const double err[6],
                              double rtol, double atol) {
   double s = 0.0;
@@ -105,9 +110,10 @@ inline double dp5_step_factor(double err, bool accepted, bool last_rejected) {
   return fac;
 }
 
-// Initial step: the two-evaluation heuristic (order 5) of Hairer et al.
-template <class F>
-inline double dp5_initial_step(F& f, const double y0[6], const double f0[6], double rtol,
+// Initial step: the two-evaluation heuristic (order 5) of Hairer et al.,
+// with the norms over x, k (as the error norm).
+template <int N = 6, class F>
+inline double dp5_initial_step(F& f, const double* y0, const double* f0, double rtol,
                                double atol, double hmax) {
   double dnf = 0.0, dny = 0.0;
   for (int i = 0; i < 6; ++i) {
@@ -117,8 +123,8 @@ inline double dp5_initial_step(F& f, const double y0[6], const double f0[6], dou
   }
   double h = (dnf <= 1e-10 || dny <= 1e-10) ? 1e-6 : std::sqrt(dny / dnf) * 0.01;
   h = std::fmin(h, hmax);
-  double y1[6], f1[6];
-  for (int i = 0; i < 6; ++i) y1[i] = y0[i] + h * f0[i];
+  double y1[N], f1[N];
+  for (int i = 0; i < N; ++i) y1[i] = y0[i] + h * f0[i];
   f(y1, f1);
   double der2 = 0.0;
   for (int i = 0; i < 6; ++i) {

@@ -12,6 +12,8 @@ namespace orc {
 
 using std::fabs;
 using std::sqrt;
+using std::sin;
+using std::cos;
 
 template <int N>
 struct Dual {
@@ -58,6 +60,20 @@ template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
 // |a|: derivative sign(a) * a' (the kink at a = 0 is a set of measure zero).
 template <int N> inline Dual<N> fabs(const Dual<N>& a) {
   return a.v < 0.0 ? -a : a;
+}
+
+// sin and cos (the rotation phase of a rotating magnetic axis, Eq. GJDensity).
+template <int N> inline Dual<N> sin(const Dual<N>& a) {
+  Dual<N> r; r.v = std::sin(a.v);
+  const double c = std::cos(a.v);
+  for (int i = 0; i < N; ++i) r.d[i] = c * a.d[i];
+  return r;
+}
+template <int N> inline Dual<N> cos(const Dual<N>& a) {
+  Dual<N> r; r.v = std::cos(a.v);
+  const double sn = std::sin(a.v);
+  for (int i = 0; i < N; ++i) r.d[i] = -sn * a.d[i];
+  return r;
 }
 
 inline double value(double x) { return x; }

@@ -42,18 +42,23 @@ enum { METRIC_FULL = 0, METRIC_FLAT = 1 };
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1, WEIGHT_RENORM = 2 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
+// Snapshot: the plasma frozen at the emission phase for the whole flight, so
+// k_t is conserved (the reading of Sec. 5 used for every figure of the paper).
+// Rigid: the magnetosphere keeps rotating while the photon flies (the time
+// dependence that Eq. GJDensity writes through cos(Omega t)); k_t evolves.
+enum { ROTATION_SNAPSHOT = 0, ROTATION_RIGID = 1 };
 
 // Parameter vector layout shared with the Python wrapper of the oracle.
 enum {
   SP_M_SUN = 0, SP_R_KM, SP_B0_G, SP_P_S, SP_THETA_M, SP_PSI, SP_MA_EV, SP_G_GEV,
   SP_RHO_GEV_CM3, SP_V0_KMS, SP_DISPERSION, SP_RESONANCE, SP_FA_MODEL, SP_WEIGHT_MODE,
-  SP_PROP_METRIC, SP_PHASE_MODE, SP_PLASMA, SP_PLASMA_A, SP_COUNT
+  SP_PROP_METRIC, SP_PHASE_MODE, SP_PLASMA, SP_PLASMA_A, SP_ROTATION, SP_COUNT
 };
 
 struct Star {
   // physical inputs
   double M_sun, R_km, B0_G, P_s, theta_m, psi, ma_eV, g_GeV, rho, v0_kms;
-  int dispersion, resonance, fa_model, weight_mode, prop_metric, phase_mode, plasma;
+  int dispersion, resonance, fa_model, weight_mode, prop_metric, phase_mode, plasma, rotation;
   double plasma_a;
   // derived
   double rs;        // r_s / R (geometry of the initial conditions)
@@ -66,6 +71,7 @@ struct Star {
   double n_inf;     // asymptotic axion number density [eV^3]
   double g_eV;      // coupling [eV^-1]
   double r_lc;      // light-cylinder radius c / Omega, units of R
+  double omega_R;   // Omega R / c: rotation rate per unit of t (t in units of R / c)
 };
 
 inline Star make_star(const double* p) {
@@ -78,6 +84,7 @@ inline Star make_star(const double* p) {
   s.fa_model = (int)p[SP_FA_MODEL]; s.weight_mode = (int)p[SP_WEIGHT_MODE];
   s.prop_metric = (int)p[SP_PROP_METRIC]; s.phase_mode = (int)p[SP_PHASE_MODE];
   s.plasma = (int)p[SP_PLASMA]; s.plasma_a = p[SP_PLASMA_A];
+  s.rotation = (int)p[SP_ROTATION];
   s.rs = 2.0 * s.M_sun * GM_SUN_KM / s.R_km;
   s.rs_prop = (s.prop_metric == METRIC_FLAT) ? 0.0 : s.rs;
   s.e_hl = std::sqrt(4.0 * PI * ALPHA);
@@ -91,22 +98,24 @@ inline Star make_star(const double* p) {
   s.n_inf = s.rho * 1e9 * hbarc_cm * hbarc_cm * hbarc_cm / s.ma_eV;
   s.g_eV = s.g_GeV * 1e-9;
   s.r_lc = C_KM_S * s.P_s / (2.0 * PI) / s.R_km;
+  s.omega_R = 1.0 / s.r_lc;
   return s;
 }
 
 // Magnetic axis at rotation phase psi (misalignment theta_m from the z axis,
 // which is the rotation axis; Sec. 5, below Eq. GJDensity).
-inline void magnetic_axis(const Star& s, double psi, double m[3]) {
-  m[0] = std::sin(s.theta_m) * std::cos(psi);
-  m[1] = std::sin(s.theta_m) * std::sin(psi);
-  m[2] = std::cos(s.theta_m);
+template <class T>
+inline void magnetic_axis(const Star& s, T psi, T m[3]) {
+  m[0] = std::sin(s.theta_m) * cos(psi);
+  m[1] = std::sin(s.theta_m) * sin(psi);
+  m[2] = T(std::cos(s.theta_m));
 }
 
 // Dipole field in the static orthonormal frame, in units of B0, at the point
 // x (units of R): B = (1/2) r^-3 [3 (m.n) n - m]; |B| = B0 at the magnetic pole
 // of the surface.
-template <class T>
-inline void dipole_field(const double m[3], const T x[3], T B[3]) {
+template <class T, class M>
+inline void dipole_field(const M m[3], const T x[3], T B[3]) {
   T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   T n[3] = {x[0] / r, x[1] / r, x[2] / r};
   T mu = n[0] * m[0] + n[1] * m[1] + n[2] * m[2];
@@ -125,8 +134,8 @@ inline int gj_branch(const double m[3], const double x[3]) {
 // omega_p^2 / m_a^2 at x (units of R).  sigma = 0 evaluates |n_e|; sigma = +-1
 // evaluates sigma * n_e, the smooth continuation of one side of the null cone
 // (used inside an integration step, see trace_ray).
-template <class T>
-inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma = 0) {
+template <class T, class M>
+inline T plasma_freq2(const Star& s, const M m[3], const T x[3], int sigma = 0) {
   switch (s.plasma) {
     case PLASMA_VACUUM: return T(0.0);
     case PLASMA_HOMOG: return T(s.plasma_a);
@@ -165,8 +174,8 @@ inline T plasma_freq2(const Star& s, const double m[3], const T x[3], int sigma 
 
 // The photon Hamiltonian H(x, k) / m_a^2 with k_t = -omega_inf fixed (static
 // snapshot of the plasma, so dk_t/dlambda = 0).
-template <class T, class W = double>
-inline T hamiltonian(const Star& s, const double m[3], W omega_inf, const T x[3],
+template <class T, class W = double, class M = double>
+inline T hamiltonian(const Star& s, const M m[3], W omega_inf, const T x[3],
                      const T k[3], int sigma = 0) {
   T r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
   T n[3] = {x[0] / r, x[1] / r, x[2] / r};
@@ -220,6 +229,33 @@ inline void rhs(const Star& s, const double m[3], double omega_inf, const double
     dy[i] = H.d[3 + i];
     dy[3 + i] = -H.d[i];
   }
+}
+
+// Rigidly rotating magnetosphere: the magnetic axis turns about z,
+// m(t) = m(psi0 + Omega t), while the photon flies, so the Hamiltonian
+// depends on the coordinate time t and the state is the full canonical pair
+// (x^mu, k_mu) of Eq. Hamilton: y = (x, k, t, k_t), eight components, with
+// omega_inf = -k_t no longer a constant.  Derivatives by dual numbers in all
+// eight: dx/dl = dH/dk, dk/dl = -dH/dx, dt/dl = dH/dk_t, dk_t/dl = -dH/dt.
+inline void rhs_rotating(const Star& s, double psi0, const double y[8], double dy[8],
+                         int sigma = 0) {
+  typedef Dual<8> D;
+  D x[3], k[3];
+  for (int i = 0; i < 3; ++i) {
+    x[i] = D::var(y[i], i);
+    k[i] = D::var(y[3 + i], 3 + i);
+  }
+  const D t = D::var(y[6], 6);
+  const D kt = D::var(y[7], 7);
+  D m[3];
+  magnetic_axis(s, psi0 + s.omega_R * t, m);
+  D H = hamiltonian(s, m, -kt, x, k, sigma);
+  for (int i = 0; i < 3; ++i) {
+    dy[i] = H.d[3 + i];
+    dy[3 + i] = -H.d[i];
+  }
+  dy[6] = H.d[7];
+  dy[7] = -H.d[6];
 }
 
 }  // namespace orc

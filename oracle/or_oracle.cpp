@@ -431,6 +431,124 @@ static int trace_ray(const Star& s, const double m[3], double omega_inf, double 
 }
 
 // ---------------------------------------------------------------------------
+// Forward tracing through a rigidly rotating magnetosphere (Eq. GJDensity with
+// its cos(Omega t) kept during the flight; Eq. Hamilton for all four canonical
+// pairs).  The same integrator and events as trace_ray on the eight-component
+// state y = (x, k, t, k_t) of rhs_rotating; the null cone Omega . B = 0 now
+// turns with the star, so its side is taken with the axis at the point's own t.
+
+struct RotRHS {
+  const Star* s;
+  double psi0;
+  int sigma = 0;
+  void operator()(const double y[8], double dy[8]) { rhs_rotating(*s, psi0, y, dy, sigma); }
+};
+
+static int gj_branch_at(const Star& s, double psi0, const double y[8]) {
+  double m[3];
+  magnetic_axis(s, psi0 + s.omega_R * y[6], m);
+  return gj_branch(m, y);
+}
+
+static int trace_ray_rotating(const Star& s, double psi0, double y[8], const TraceOpts& o,
+                              long* nacc_out, long* nrej_out, double* lam_out) {
+  RotRHS f{&s, psi0};
+  const bool gj = (s.plasma == PLASMA_GJ);
+  if (gj) f.sigma = gj_branch_at(s, psi0, y);
+  double f0[8];
+  f(y, f0);
+  double lam = 0.0;
+  double hmax = (o.lambda_max > 0.0) ? o.lambda_max : 1e30;
+  double h = dp5_initial_step<8>(f, y, f0, o.rtol, o.atol, hmax);
+  long nacc = 0, nrej = 0;
+  bool last_rej = false, switching = false;
+  double h_resume = 0.0;
+  int status = RAY_MAXSTEPS;
+  double K[7][8], ynew[8], err[8], yd[8];
+  while (true) {
+    if (nacc >= o.max_steps || nacc + nrej >= 4 * o.max_steps) { status = RAY_MAXSTEPS; break; }
+    const double v2 = f0[0] * f0[0] + f0[1] * f0[1] + f0[2] * f0[2];
+    const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    if (h * h * v2 > STEP_REACH * STEP_REACH * r2) h = STEP_REACH * std::sqrt(r2 / v2);
+    bool clipped = false;
+    if (o.lambda_max > 0.0 && lam + h >= o.lambda_max) { h = o.lambda_max - lam; clipped = true; }
+    dp5_step(f, y, f0, h, ynew, err, K);
+    double en = dp5_error_norm(y, ynew, err, o.rtol, o.atol);
+    if (!std::isfinite(en)) {
+      ++nrej;
+      h *= 0.2;
+      last_rej = true;
+      if (h < 1e-12) { status = RAY_NAN; break; }
+      continue;
+    }
+    if (en <= 1.0) {
+      if (gj && !switching && f.sigma * gj_branch_at(s, psi0, ynew) < 0) {
+        // the accepted step crossed the (turning) null cone: largest th whose
+        // point is on the start side, by bisection on the continuous extension
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 200; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          dp5_dense(y, ynew, K, h, mid, yd);
+          if (f.sigma * gj_branch_at(s, psi0, yd) >= 0) lo = mid; else hi = mid;
+        }
+        ++nrej;
+        if (lo < SWITCH_MIN_FRACTION) {
+          f.sigma = -f.sigma;
+          f(y, f0);
+        } else {
+          h_resume = h;
+          h = h * lo * (1.0 + SWITCH_OVERSHOOT);
+          switching = true;
+        }
+        continue;
+      }
+      ++nacc;
+      double rnew = norm3(ynew);
+      if (rnew >= o.r_out) {
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 200; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          dp5_dense(y, ynew, K, h, mid, yd);
+          if (norm3(yd) < o.r_out) lo = mid; else hi = mid;
+        }
+        double th = 0.5 * (lo + hi);
+        dp5_dense(y, ynew, K, h, th, yd);
+        for (int i = 0; i < 8; ++i) y[i] = yd[i];
+        lam += th * h;
+        status = RAY_ESCAPED;
+        break;
+      }
+      for (int i = 0; i < 8; ++i) { y[i] = ynew[i]; f0[i] = K[6][i]; }
+      lam += h;
+      if (rnew <= o.r_capture) { status = RAY_CAPTURED; break; }
+      if (clipped) { status = RAY_LAMBDA_END; break; }
+      if (gj && f.sigma * gj_branch_at(s, psi0, y) < 0) {
+        f.sigma = -f.sigma;
+        f(y, f0);
+      }
+      if (switching) {
+        h = h_resume;
+        switching = false;
+      } else {
+        h *= dp5_step_factor(en, true, last_rej);
+      }
+      last_rej = false;
+    } else {
+      ++nrej;
+      h *= dp5_step_factor(en, false, last_rej);
+      last_rej = true;
+      if (h < 1e-12) { status = RAY_STIFF; break; }
+    }
+  }
+  *nacc_out = nacc;
+  *nrej_out = nrej;
+  if (lam_out) *lam_out = lam;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
 // Backward image-plane estimator (Sec. 2.1, Eq. BackPower; every level
 // crossing along the worldline contributes, Sec. 5.1.3).
 //
@@ -711,7 +829,22 @@ void or_trace_forward(const double* sp, const double* topt, long n, double* stat
     load_ray(s, state, n, i, y, &om, m);
     long na = 0, nr = 0;
     double l = 0.0;
-    status[i] = (unsigned char)trace_ray(s, m, om, y, o, &na, &nr, &l);
+    if (s.rotation == ROTATION_RIGID) {
+      // the clock starts at the emission phase: t = 0, psi(0) = state row 7;
+      // on return row 6 holds the final omega_inf / m_a - 1 = -k_t - 1 and
+      // row 7 the rotation phase psi0 + Omega t at the end point
+      const double psi0 = state[7 * n + i];
+      double y8[8];
+      for (int c = 0; c < 6; ++c) y8[c] = y[c];
+      y8[6] = 0.0;
+      y8[7] = -om;
+      status[i] = (unsigned char)trace_ray_rotating(s, psi0, y8, o, &na, &nr, &l);
+      for (int c = 0; c < 6; ++c) y[c] = y8[c];
+      state[6 * n + i] = -y8[7] - 1.0;
+      state[7 * n + i] = psi0 + s.omega_R * y8[6];
+    } else {
+      status[i] = (unsigned char)trace_ray(s, m, om, y, o, &na, &nr, &l);
+    }
     store_ray(s, state, n, i, y);
     if (nacc) nacc[i] = (int)na;
     if (nrej) nrej[i] = (int)nr;
