@@ -71,6 +71,7 @@ enum { RT_FA_MAXWELL = 0, RT_FA_DELTA = 1 };
 enum { RT_WEIGHT_PAG = 0, RT_WEIGHT_UNIT_P = 1, RT_WEIGHT_RENORM = 2 };
 enum { RT_METRIC_FULL = 0, RT_METRIC_FLAT = 1 };
 enum { RT_PHASE_FIXED = 0, RT_PHASE_UNIFORM = 1 };
+enum { RT_ROTATION_SNAPSHOT = 0, RT_ROTATION_RIGID = 1 };
 enum {
   RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3,
   RT_PLASMA_RADIAL = 4, RT_PLASMA_TWISTED = 5
@@ -113,12 +114,24 @@ enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
  *                  > 0); omega_p^2 / m_a^2 (HOMOG), its gradient d/d(z/R)
  *                  (LINEAR_Z), or its value at r = R of the spherical profile
  *                  a (R/r)^3 (RADIAL)
+ *   rotation       RT_ROTATION_SNAPSHOT: the magnetosphere frozen at the emission
+ *                  phase for the whole flight, k_t conserved.  RT_ROTATION_RIGID:
+ *                  it keeps turning about z at Omega = 2 pi / P_s while the photon
+ *                  flies (the cos(Omega t) of Eq. GJDensity), so k_t evolves (Eq.
+ *                  Hamilton for all four canonical pairs) and the line is Doppler
+ *                  shifted; sampling is unchanged (the snapshot at emission).
+ *                  rt_trace_forward traces it in RT_PREC_FP64 only (one lane per
+ *                  ray throughout), and on return state row 6 holds the final
+ *                  omega_inf / m_a - 1 and row 7 the rotation phase psi0 + Omega t
+ *                  at the end point.  The backward tracer, the gradient and
+ *                  batches reject it (RT_EUNSUPPORTED).  Before this field existed
+ *                  it was reserved and ignored; 0 keeps that behaviour.
  */
 typedef struct {
   double M_sun, R_km, B0_G, P_s, theta_m_rad, psi_rad, m_a_eV, g_agg_GeVinv, rho_dm_GeV_cm3,
       v0_kms;
   int32_t dispersion, resonance, fa_model, weight_mode, prop_metric, phase_mode, plasma,
-      reserved;
+      rotation;
   double plasma_a;
 } rt_star_params;
 

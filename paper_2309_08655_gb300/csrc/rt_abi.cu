@@ -119,6 +119,8 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unsupported weight_mode %d", p->weight_mode);
   if (p->prop_metric != RT_METRIC_FULL && p->prop_metric != RT_METRIC_FLAT)
     return fail(RT_EUNSUPPORTED, "unknown prop_metric %d", p->prop_metric);
+  if (p->rotation != RT_ROTATION_SNAPSHOT && p->rotation != RT_ROTATION_RIGID)
+    return fail(RT_EUNSUPPORTED, "unknown rotation %d", p->rotation);
   if (p->phase_mode != RT_PHASE_FIXED && p->phase_mode != RT_PHASE_UNIFORM)
     return fail(RT_EUNSUPPORTED, "unknown phase_mode %d", p->phase_mode);
   if (p->plasma < RT_PLASMA_GJ || p->plasma > RT_PLASMA_TWISTED)
@@ -166,6 +168,7 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
   h.fa_model = p->fa_model;
   h.phase_mode = p->phase_mode;
   h.weight_mode = p->weight_mode;
+  h.rotation = p->rotation;
   // Largest omega_p^2 / m_a^2 on the surface: max over n of
   // |3 n_z (m.n) - cos th_m| = (3 + |cos th_m|) / 2 (eigenvalues of the
   // symmetrised z m^T).  A kinematic resonance needs omega_p > m_a somewhere.
@@ -317,6 +320,9 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
   if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
     return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
+  const bool rigid = (s->p.rotation == RT_ROTATION_RIGID);
+  if (rigid && o->precision != RT_PREC_FP64)
+    return fail(RT_EUNSUPPORTED, "a rotating magnetosphere is traced in RT_PREC_FP64 only");
   rtk::TraceParams p;
   p.stars = s->d;
   p.nstars = 1;
@@ -329,7 +335,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.counters = d_counters;
   p.queue = s->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail != 1 && o->lambda_max == 0.0) {
+  if (o->tail != 1 && o->lambda_max == 0.0 && !rigid) {
     rt_star* sm = const_cast<rt_star*>(s);
     if ((st = ensure_park(&sm->d_park, &sm->park_cap)) != RT_OK) return st;
     set_park(p, sm->d_park, sm->park_cap, o);
@@ -344,6 +350,11 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
   cudaError_t e;
+  if (rigid) {
+    e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rotating-magnetosphere trace kernel");
+    return RT_OK;
+  }
   if (o->precision == RT_PREC_MIXED) {
     e = rtk::launch_trace_mixed(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
@@ -397,6 +408,8 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
   if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
   if (s->p.weight_mode != RT_WEIGHT_PAG)
     return fail(RT_EUNSUPPORTED, "rt_trace_backward needs RT_WEIGHT_PAG");
+  if (s->p.rotation != RT_ROTATION_SNAPSHOT)
+    return fail(RT_EUNSUPPORTED, "rt_trace_backward needs RT_ROTATION_SNAPSHOT");
   if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
   if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
@@ -496,6 +509,8 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   if (p.plasma != RT_PLASMA_GJ) return fail(RT_EUNSUPPORTED, "the gradient needs RT_PLASMA_GJ");
   if (p.weight_mode != RT_WEIGHT_PAG)
     return fail(RT_EUNSUPPORTED, "the gradient needs RT_WEIGHT_PAG");
+  if (p.rotation != RT_ROTATION_SNAPSHOT)
+    return fail(RT_EUNSUPPORTED, "the gradient needs RT_ROTATION_SNAPSHOT");
   if (!(p.M_sun > 0) || !(p.B0_G > 0))
     return fail(RT_EINVAL, "the gradient needs M_sun > 0 and B0_G > 0");
   typedef rtk::Dual<rtk::NSAMP_TANGENTS> D5;
@@ -725,6 +740,10 @@ rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64
       delete b;
       return fail(RT_EINVAL, "star %d is NULL or has a negative count", s);
     }
+    if (stars[s]->p.rotation != RT_ROTATION_SNAPSHOT) {
+      delete b;
+      return fail(RT_EUNSUPPORTED, "star %d: batches need RT_ROTATION_SNAPSHOT", s);
+    }
     b->stars.push_back(stars[s]);
     table[s] = stars[s]->h;
     b->off[s + 1] = b->off[s] + counts[s];
@@ -781,6 +800,8 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
     if (!stars[j]) return fail(RT_EINVAL, "image %d: star is NULL", j);
     if (stars[j]->p.weight_mode != RT_WEIGHT_PAG)
       return fail(RT_EUNSUPPORTED, "image %d: backward images need RT_WEIGHT_PAG", j);
+    if (stars[j]->p.rotation != RT_ROTATION_SNAPSHOT)
+      return fail(RT_EUNSUPPORTED, "image %d: backward images need RT_ROTATION_SNAPSHOT", j);
     if ((st = check_image(d.nx, d.ny, d.incl_rad, d.dist_over_R, d.bmax_over_R, d.Lc_cut_km)) !=
         RT_OK)
       return st;

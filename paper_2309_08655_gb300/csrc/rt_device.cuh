@@ -42,7 +42,8 @@ struct StarDev {
   double w_unit;      // 1 eV^2 of power in W
   double rlc;         // light-cylinder radius / R (open field lines of the twisted model)
   int32_t dispersion, plasma, fa_model, phase_mode;
-  int32_t weight_mode;  // WEIGHT_PAG or WEIGHT_UNIT_P
+  int32_t weight_mode;  // WEIGHT_PAG, WEIGHT_UNIT_P or WEIGHT_RENORM
+  int32_t rotation;     // ROTATION_SNAPSHOT or ROTATION_RIGID (rt_trace_rot.cu)
 };
 
 enum { DISP_ANISO = 0, DISP_ISO = 1 };
@@ -53,6 +54,7 @@ enum {
 enum { FA_MAXWELL = 0, FA_DELTA = 1 };
 enum { WEIGHT_PAG = 0, WEIGHT_UNIT_P = 1, WEIGHT_RENORM = 2 };
 enum { PHASE_FIXED = 0, PHASE_UNIFORM = 1 };
+enum { ROTATION_SNAPSHOT = 0, ROTATION_RIGID = 1 };
 enum {
   RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,
   RAY_NAN = 5, RAY_STIFF = 6, RAY_LAMBDA_END = 7,
@@ -108,13 +110,15 @@ RT_HD __forceinline__ T gj_side(const T m0, const T m1, const T m2, const T x0, 
 
 // dx/dl = dH/dk, dk/dl = -dH/dx (Eq. Hamilton), analytic.  With XCORR the
 // position derivative is returned without its flat-space part 2k (the caller
-// then adds 2k itself, in higher precision).  (Host-callable only for the
-// flop-counting scalar of rt_flops.cu.)
-template <class T, bool XCORR = false, bool FIN = false>
+// then adds 2k itself, in higher precision).  With DW also *dw = dH/dW2, the
+// derivative with respect to omega_inf^2 = k_t^2 (for a Hamiltonian in which
+// k_t evolves).  (Host-callable only for the flop-counting scalar of
+// rt_flops.cu.)
+template <class T, bool XCORR = false, bool FIN = false, bool DW = false>
 RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
                                         const T x2, const T k0, const T k1, const T k2, T& dx0,
                                         T& dx1, T& dx2, T& dk0, T& dk1, T& dk2,
-                                        const T F_in = T(0)) {
+                                        const T F_in = T(0), T* dw = nullptr) {
   const T r2 = x0 * x0 + x1 * x1 + x2 * x2;
   const T ir = rt_rsqrt(r2);
   const T n0 = x0 * ir, n1 = x1 * ir, n2 = x2 * ir;
@@ -182,6 +186,7 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
     gx0 += dP0;
     gx1 += dP1;
     gx2 += dP2;
+    if (DW) *dw = -iA;                            // d(-W2/A)/dW2
   } else {
     // anisotropic term H_a = P - P A Kp^2 / W2 with Kp = U / |b|,
     // U = k.b + (sqrt(A) - 1) (n.k)(n.b), n.b = 2 mu, |b|^2 = 3 mu^2 + 1
@@ -213,6 +218,7 @@ RT_HD __forceinline__ void ham_rhs(const RayConst<T>& c, const T x0, const T x1,
     const T one_m = T(1) - A * Kp2iW2;
     const T cdA = -P * Kp2iW2 * c.rs * ir2;
     const T m2f = T(-2) * fac;
+    if (DW) *dw = Kp2iW2 * P * A * c.iW2 - iA;    // d(-W2/A - P A Kp^2/W2)/dW2
     gx0 += dP0 * one_m + cdA * n0 + m2f * dK0;
     gx1 += dP1 * one_m + cdA * n1 + m2f * dK1;
     gx2 += dP2 * one_m + cdA * n2 + m2f * dK2;

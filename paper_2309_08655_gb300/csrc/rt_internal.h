@@ -74,6 +74,9 @@ struct BinParams {
 };
 
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t stream);
+// Forward tracing through a rigidly rotating magnetosphere (rt_trace_rot.cu).
+cudaError_t launch_trace_rot(const TraceParams& p, int block, int blocks_per_sm,
+                             cudaStream_t stream);
 cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,
                               cudaStream_t stream);
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,

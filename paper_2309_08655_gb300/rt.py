@@ -24,6 +24,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 (PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL,
  PLASMA_TWISTED) = range(6)
 WEIGHT_PAG, WEIGHT_UNIT_P, WEIGHT_RENORM = 0, 1, 2
+ROTATION_SNAPSHOT, ROTATION_RIGID = 0, 1
 
 
 class RtError(RuntimeError):
@@ -37,7 +38,7 @@ class rt_star_params(ctypes.Structure):
         "M_sun", "R_km", "B0_G", "P_s", "theta_m_rad", "psi_rad", "m_a_eV", "g_agg_GeVinv",
         "rho_dm_GeV_cm3", "v0_kms"]] + [(k, ctypes.c_int32) for k in [
             "dispersion", "resonance", "fa_model", "weight_mode", "prop_metric", "phase_mode",
-            "plasma", "reserved"]] + [("plasma_a", ctypes.c_double)]
+            "plasma", "rotation"]] + [("plasma_a", ctypes.c_double)]
 
 
 class rt_image_desc(ctypes.Structure):

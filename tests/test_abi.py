@@ -38,6 +38,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(rt.rt_star_params) == 10 * 8 + 8 * 4 + 8
     assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 6 * 4 + 8   # + the timestamps pointer
     assert rt.rt_star_params.plasma_a.offset == 112
+    assert rt.rt_star_params.rotation.offset == 108
 
 
 def test_version_and_error_paths_without_gpu(L):
@@ -52,6 +53,10 @@ def test_version_and_error_paths_without_gpu(L):
         rt.Star(rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5,
                                dispersion=7))
     assert e.value.status == rt.RT_EUNSUPPORTED
+    with pytest.raises(rt.RtError) as e:
+        rt.Star(rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5,
+                               rotation=2))
+    assert e.value.status == rt.RT_EUNSUPPORTED and "rotation" in str(e.value)
     st = L.rt_trace_forward(None, 10, None, None, None, None, None, None, None)
     assert st == rt.RT_EINVAL
     st = L.rt_init_star(None, ctypes.byref(ctypes.c_void_p()))

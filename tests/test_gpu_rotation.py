@@ -1,0 +1,133 @@
+"""Parity of the rotating-magnetosphere forward path (the cos(Omega t) of Eq.
+GJDensity kept during the flight; Eq. Hamilton on (x, k, t, k_t)) with the
+oracle's eight-component integration, through the C ABI.
+
+Tolerances as the static forward tests: end points 1e-10 relative on the
+well-conditioned set (oracle strict vs contracted within 1e-12), statuses
+>= 99 %, and over all rays deviations of the size of the oracle's own spread.
+The frequency row (omega_inf / m_a - 1) moves by up to ~1e-4 (the Doppler
+shift Omega Delta L_z) and carries the end point's relative error: 1e-12
+absolute on the well-conditioned set.  The end phase psi0 + Omega t
+(Omega t ~ 0.2 rad at r_out = 1000 R for P = 1 s): 1e-10 rad.  Binned flux
+1e-4 relative L1 on a frequency axis wide enough for the Doppler-broadened
+line.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2309_08655_gb300 import inputs as I  # noqa: E402
+from paper_2309_08655_gb300 import rt  # noqa: E402
+
+from . import gpu_util as G  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2309_08655_gb300.build import build
+    build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _star(theta_m=0.6, plasma=rt.PLASMA_GJ, **kw):
+    base = dict(M_sun=1.0, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=theta_m, m_a_eV=1e-5,
+                phase_mode=1, plasma=plasma, rotation=rt.ROTATION_RIGID)
+    if plasma == rt.PLASMA_TWISTED:
+        base.update(m_a_eV=1e-3, B0_G=1.6e14, P_s=3.76, plasma_a=4.0)
+    base.update(kw)
+    return base
+
+
+def _wR(kw):
+    return 2 * math.pi / kw["P_s"] * kw["R_km"] / 299792.458
+
+
+def _Lz(st, kw):
+    return (st[0] * st[4] - st[1] * st[3]) / (kw["R_km"] * kw["m_a_eV"])
+
+
+@pytest.mark.parametrize("case", ["gj_misaligned", "gj_aligned", "twisted_misaligned"])
+def test_rotating_trace_parity(oracle, case):
+    kw = {"gj_misaligned": _star(0.6), "gj_aligned": _star(0.0),
+          "twisted_misaligned": _star(math.radians(30.0), rt.PLASMA_TWISTED)}[case]
+    sv = oracle.star_vector(**kw)
+    u = I.sample_uniforms(410 + len(case), 2048)
+    st0, w0, s0 = oracle.sample(sv, u)
+    ref, sref, good, spread = G.well_conditioned(oracle, sv, st0, s0, 1e-10)
+    star = rt.Star(rt.make_params(**kw))
+    st_d = torch.from_numpy(st0.copy()).cuda()
+    s_d = torch.from_numpy(s0.copy()).cuda()
+    nacc, nrej, ctr = G.gpu_trace(star, st_d, s_d, rtol=1e-10)
+    st_g, s_g, na = G.to_np(st_d, s_d, nacc)
+    ctr = ctr.cpu().numpy()
+    traced = s0 == oracle.RAY_READY
+    assert traced.sum() > 500
+    assert (s_g[traced] == sref[traced]).mean() > 0.99
+    g = good & traced & (s_g == sref)
+    assert g.sum() > 0.2 * traced.sum()
+    assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+    assert np.abs(st_g[6, g] - ref[6, g]).max() < 1e-12
+    assert np.abs(st_g[7, g] - ref[7, g]).max() < 1e-10
+    m = traced & (s_g == sref)
+    dev_all = G.rel_state_diff(st_g[:, m], ref[:, m])
+    for q in (50, 90, 99):
+        assert np.percentile(dev_all, q) <= 10 * np.percentile(spread[m], q) + 1e-12, q
+    assert ctr[2] == traced.sum() and ctr[0] == na.sum()
+    assert ctr[3] == (s_g == rt.RAY_ESCAPED).sum()
+    # the corotating energy omega - Omega L_z is conserved on every escaped ray
+    esc = traced & (s_g == rt.RAY_ESCAPED)
+    dJ = (st_g[6, esc] - st0[6, esc]) - _wR(kw) * (_Lz(st_g[:, esc], kw) - _Lz(st0[:, esc], kw))
+    assert np.abs(dJ).max() < 1e-10
+    d_om = np.abs(st_g[6, esc] - st0[6, esc])
+    if case == "gj_aligned":
+        assert d_om.max() < 1e-15          # axisymmetric: no Doppler shift
+    else:
+        assert d_om.max() > 1e-6           # the turning plasma shifts the line
+    # binned flux on a frequency axis that holds the Doppler-broadened line
+    y_max = 1.5 * max(d_om.max(), 1e-9) / (0.5 * (200.0 / 299792.458) ** 2) + 10.0
+    w_d = torch.from_numpy(w0.copy()).cuda()
+    hist, _, _, oor = G.gpu_bin(star, st_d, w_d, s_d, nu_lo=-y_max, nu_hi=y_max)
+    h_o, _ = oracle.bin_rays(sv, ref, w0, sref, nu_lo=-y_max, nu_hi=y_max)
+    assert np.abs(hist - h_o).sum() / h_o.sum() < 1e-4
+
+
+def test_aligned_rotating_trace_is_the_static_trace():
+    kw = _star(0.0)
+    u = I.sample_uniforms(420, 2048)
+    st_d, w_d, s_d = None, None, None
+    out = {}
+    for rot in (rt.ROTATION_SNAPSHOT, rt.ROTATION_RIGID):
+        k = dict(kw, rotation=rot)
+        star, st_d, w_d, s_d, code = G.gpu_sample(k, u)
+        assert code == rt.RT_OK
+        st0 = st_d.cpu().numpy()
+        G.gpu_trace(star, st_d, s_d, rtol=1e-10, tail=1)
+        out[rot] = G.to_np(st_d, s_d) + [st0]
+    (a, sa, a0), (b, sb, b0) = out[rt.ROTATION_SNAPSHOT], out[rt.ROTATION_RIGID]
+    assert np.array_equal(a0, b0)                      # sampling ignores the switch
+    assert (sa == sb).mean() > 0.999
+    m = (sa == sb) & (sa == rt.RAY_ESCAPED)
+    d = G.rel_state_diff(b[:, m], a[:, m])
+    assert np.median(d) < 1e-13 and np.percentile(d, 90) < 1e-11
+
+
+def test_rotating_magnetosphere_rejections():
+    kw = _star(0.6)
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, I.sample_uniforms(421, 256))
+    n = st_d.shape[1]
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_forward(star, n, st_d, s_d, opts=rt.make_opts(rtol=1e-8,
+                                                                  precision=rt.PREC_MIXED))
+    assert e.value.status == rt.RT_EUNSUPPORTED
+    img = torch.empty((4, 4), dtype=torch.float64, device=G.dev())
+    ist = torch.empty((4, 4), dtype=torch.uint8, device=G.dev())
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_backward(star, 4, 4, 1.0, 1e4, 50.0, img, ist)
+    assert e.value.status == rt.RT_EUNSUPPORTED
+    with pytest.raises(rt.RtError) as e:
+        rt.Batch([star], [n])
+    assert e.value.status == rt.RT_EUNSUPPORTED
