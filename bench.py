@@ -92,6 +92,8 @@ def _args():
                     help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-twisted", action="store_true",
                     help="skip the twisted-magnetosphere (Eq. neMag) workload")
+    ap.add_argument("--no-rotating", action="store_true",
+                    help="skip the rigidly rotating magnetosphere workload")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 256-instance uneven batch measurement")
     return ap.parse_args()
@@ -468,6 +470,9 @@ def run_ours(args):
     twisted = None
     if ws == 1 and not args.no_twisted:
         twisted = _twisted_leg(args, dev, stream)
+    rotating = None
+    if ws == 1 and not args.no_rotating:
+        rotating = _rotating_leg(args, dev, stream)
     if rank != 0:
         return
     H = res[head]
@@ -496,6 +501,7 @@ def run_ours(args):
         "adjoint": adj,
         "uneven_batch": uneven,
         "twisted_magnetosphere": twisted,
+        "rotating_magnetosphere": rotating,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
@@ -567,6 +573,60 @@ def _twisted_leg(args, dev, stream):
                      "rays_traced": int(c[2]), "promoted": int(c[4]),
                      "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}
     return out
+
+
+def _rotating_leg(args, dev, stream):
+    """The benchmark's 16 x 65536-ray step with the magnetosphere turning
+    while the photons fly (the cos(Omega t) of Eq. GJDensity kept during the
+    flight, Eq. Hamilton on x, k, t, k_t): one batch, FP64, one launch per
+    step.  Reports the speed and the Doppler shift of the escaping photons in
+    units of the natural line width v0^2 / 2."""
+    import numpy as np
+    import torch
+
+    from paper_2309_08655_gb300 import inputs as I
+    from paper_2309_08655_gb300 import rt
+    cfg = I.CONFIG1
+    nsub, nper = cfg["nsub"], cfg["n_per_sub"]
+    N = nsub * nper
+    kws = I.stars_config1(cfg["seed"], nsub)
+    for kw in kws:
+        kw.update(rotation=rt.ROTATION_RIGID)
+    stars = [rt.Star(rt.make_params(**kw)) for kw in kws]
+    batch = rt.Batch(stars, [nper] * nsub)
+    u = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [I.sample_uniforms(cfg["seed"] * 1000 + j, nper) for j in range(nsub)], axis=1))).to(dev)
+    st = torch.empty((8, N), dtype=torch.float64, device=dev)
+    w = torch.empty(N, dtype=torch.float64, device=dev)
+    s = torch.empty(N, dtype=torch.uint8, device=dev)
+    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+    opts = rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
+                        max_steps=cfg["max_steps"])
+    rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
+    delta0 = st[6].clone()
+    rt.rt_trace_batch(batch, st, s, None, None, None, opts, stream=stream)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
+    rt.rt_trace_batch(batch, st, s, None, None, ctr, opts, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    c = ctr.cpu().numpy()
+    status = s.cpu().numpy()
+    esc = status == rt.RAY_ESCAPED
+    width = 0.5 * (kws[0].get("v0_kms", 200.0) / 299792.458) ** 2
+    shift = np.abs((st[6] - delta0).cpu().numpy()[esc]) / width
+    return {"workload": "forward_misaligned_16x65536_rotating", "precision": "fp64",
+            "rtol": cfg["rtol"], "ms_per_step": 1e3 * t, "ray_steps_per_s": c[0] / t,
+            "rays_per_s": c[2] / t, "accepted_steps": int(c[0]), "rejected_steps": int(c[1]),
+            "rays_traced": int(c[2]),
+            "statuses": np.bincount(status, minlength=8).tolist(),
+            "doppler_shift_in_line_widths_p50_p90_max": [float(np.percentile(shift, 50)),
+                                                         float(np.percentile(shift, 90)),
+                                                         float(shift.max())],
+            "launch": "one persistent launch per step (one lane per ray, no tail mode)"}
 
 
 def _uneven_leg(args, dev):

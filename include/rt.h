@@ -123,8 +123,9 @@ enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
  *                  rt_trace_forward traces it in RT_PREC_FP64 only (one lane per
  *                  ray throughout), and on return state row 6 holds the final
  *                  omega_inf / m_a - 1 and row 7 the rotation phase psi0 + Omega t
- *                  at the end point.  The backward tracer, the gradient and
- *                  batches reject it (RT_EUNSUPPORTED).  Before this field existed
+ *                  at the end point.  The backward tracer, backward images
+ *                  and the gradient reject it (RT_EUNSUPPORTED); a batch takes
+ *                  it when all its stars do.  Before this field existed
  *                  it was reserved and ignored; 0 keeps that behaviour.
  */
 typedef struct {
@@ -381,7 +382,10 @@ rt_status rt_flux_gradient(const rt_star* star, int64_t n, const double* d_unifo
  * N = sum(counts), in star order (SoA row stride N).
  *
  * rt_init_batch - host; allocates a device star table, the offsets and a
- *   queue counter.  The star handles must outlive the batch.
+ *   queue counter.  The star handles must outlive the batch.  All stars share
+ *   one rotation mode (RT_EUNSUPPORTED otherwise); a batch of
+ *   RT_ROTATION_RIGID stars is traced by the rotating-magnetosphere kernel
+ *   (FP64 only, no images, no autotuner).
  * rt_sample_batch - rt_sample_conversion_surface for every star on its range
  *   (each star's weights normalised by its own count); u is 6 x N, state
  *   8 x N.  RT_EEMPTY_SURFACE only when every star's surface is empty.

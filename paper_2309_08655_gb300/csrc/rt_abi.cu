@@ -710,6 +710,7 @@ struct rt_batch {
   size_t bins_per_star = 0;
   int device = 0;
   bool all_empty = true;
+  bool rigid = false;                 // every star RT_ROTATION_RIGID (rt_trace_rot.cu)
   int tuned_block[2] = {0, 0};        // autotuned launch shape per precision (0 = default)
   int tuned_bps[2] = {0, 0};
   double* d_park = nullptr;           // tail-mode park buffer (allocated on first use)
@@ -740,15 +741,16 @@ rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64
       delete b;
       return fail(RT_EINVAL, "star %d is NULL or has a negative count", s);
     }
-    if (stars[s]->p.rotation != RT_ROTATION_SNAPSHOT) {
+    if (stars[s]->p.rotation != stars[0]->p.rotation) {
       delete b;
-      return fail(RT_EUNSUPPORTED, "star %d: batches need RT_ROTATION_SNAPSHOT", s);
+      return fail(RT_EUNSUPPORTED, "star %d: a batch cannot mix rotation modes", s);
     }
     b->stars.push_back(stars[s]);
     table[s] = stars[s]->h;
     b->off[s + 1] = b->off[s] + counts[s];
     b->all_empty = b->all_empty && stars[s]->empty;
   }
+  b->rigid = (stars[0]->p.rotation == RT_ROTATION_RIGID);
   b->N = b->off[nstars];
   cudaGetDevice(&b->device);
   const size_t tbl = sizeof(rtk::StarDev) * nstars, offb = sizeof(int64_t) * (nstars + 1);
@@ -915,6 +917,8 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
   if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
     return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
+  if (b->rigid && o->precision != RT_PREC_FP64)
+    return fail(RT_EUNSUPPORTED, "a rotating magnetosphere is traced in RT_PREC_FP64 only");
   rtk::TraceParams p;
   p.stars = b->d_stars;
   p.nstars = (int)b->stars.size();
@@ -927,7 +931,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.counters = d_counters;
   p.queue = b->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail != 1 && o->lambda_max == 0.0) {
+  if (o->tail != 1 && o->lambda_max == 0.0 && !b->rigid) {
     if ((st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
     set_park(p, b->d_park, b->park_cap, o);
   } else {
@@ -944,6 +948,11 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
   const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];
   cudaError_t e;
+  if (b->rigid) {   // no images: rt_batch_set_images rejects rotating stars
+    e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rotating-magnetosphere trace kernel");
+    return RT_OK;
+  }
   if (b->npix > 0) {
     // rays and pixels in one persistent launch (no tail mode)
     if (o->lambda_max != 0.0)
@@ -1164,6 +1173,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   if ((st = check_opts(o)) != RT_OK) return st;
   if (rays_per_star < 1) return fail(RT_EINVAL, "rays_per_star must be >= 1");
   if (b->N == 0) return fail(RT_EINVAL, "empty batch");
+  if (b->rigid) return fail(RT_EUNSUPPORTED, "the autotuner needs RT_ROTATION_SNAPSHOT stars");
   if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
   if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
   const bool mixed = (o->precision == RT_PREC_MIXED);

@@ -3,10 +3,13 @@
     python -m paper_2309_08655_gb300.profile_case --precision fp64 --n 1024
     python -m paper_2309_08655_gb300.profile_case --mode backward --n 65536
     python -m paper_2309_08655_gb300.profile_case --mode adjoint --n 4096
+    python -m paper_2309_08655_gb300.profile_case --config config1 --rotating --n 65536
 
 Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
 them once in the requested precision (one persistent trace launch, after one
-untimed warm-up launch on a copy) and bins them.  Backward: an image of about
+untimed warm-up launch on a copy) and bins them; --rotating keeps the
+magnetosphere turning during the flight (FP64 only).  config1 is the
+misaligned magnetar-like star of the largest sub-batch mass.  Backward: an image of about
 n pixels (square) of the same star at inclination 60 deg, plane at 1e4 R,
 impact parameters up to 50 R, in the requested precision (one warm-up launch
 on an image of at most 32 x 32 pixels first).
@@ -34,6 +37,7 @@ def main():
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
     ap.add_argument("--mode", choices=["forward", "backward", "adjoint"], default="forward")
+    ap.add_argument("--rotating", action="store_true")
     a = ap.parse_args()
     build()
     dev = torch.device("cuda:0")
@@ -45,6 +49,8 @@ def main():
         kw = I.star_config0()
     else:
         kw = I.stars_config1()[15]
+    if a.rotating:
+        kw.update(rotation=rt.ROTATION_RIGID)
     u = torch.from_numpy(I.sample_uniforms(0, a.n)).to(dev)
     star = rt.Star(rt.make_params(**kw))
     st = torch.empty((8, a.n), dtype=torch.float64, device=dev)

@@ -128,6 +128,46 @@ def test_rotating_magnetosphere_rejections():
     with pytest.raises(rt.RtError) as e:
         rt.rt_trace_backward(star, 4, 4, 1.0, 1e4, 50.0, img, ist)
     assert e.value.status == rt.RT_EUNSUPPORTED
+    snap = rt.Star(rt.make_params(**dict(kw, rotation=rt.ROTATION_SNAPSHOT)))
     with pytest.raises(rt.RtError) as e:
-        rt.Batch([star], [n])
+        rt.Batch([star, snap], [n, n])                 # rotation modes cannot mix
+    assert e.value.status == rt.RT_EUNSUPPORTED
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_batch_set_images(rt.Batch([snap], [n]), [star],
+                               [(4, 4, 1.0, 1e4, 50.0, 0.0)], img, ist)
+    assert e.value.status == rt.RT_EUNSUPPORTED
+
+
+def test_rotating_batch_equals_single_star_calls():
+    kws = [_star(0.3, m_a_eV=1e-5), _star(1.2, m_a_eV=2e-5, P_s=0.5),
+           _star(math.radians(30.0), rt.PLASMA_TWISTED)]
+    counts = [700, 0, 900]
+    kws.insert(1, _star(0.8, m_a_eV=1.5e-5))
+    counts.insert(1, 500)
+    stars = [rt.Star(rt.make_params(**k)) for k in kws]
+    u = np.concatenate([I.sample_uniforms(430 + j, c) for j, c in enumerate(counts)], axis=1)
+    N = u.shape[1]
+    batch = rt.Batch(stars, counts)
+    ud = torch.from_numpy(np.ascontiguousarray(u)).to(G.dev())
+    st = torch.empty((8, N), dtype=torch.float64, device=G.dev())
+    w = torch.empty(N, dtype=torch.float64, device=G.dev())
+    s = torch.empty(N, dtype=torch.uint8, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    rt.rt_sample_batch(batch, ud, st, w, s)
+    rt.rt_trace_batch(batch, st, s, None, None, ctr, rt.make_opts(rtol=1e-10))
+    torch.cuda.synchronize()
+    st_b, s_b = G.to_np(st, s)
+    o = 0
+    for star, c, j in zip(stars, counts, range(len(counts))):
+        if c == 0:
+            continue
+        _, st1, _, s1, _ = G.gpu_sample(kws[j], u[:, o:o + c])
+        G.gpu_trace(star, st1, s1, rtol=1e-10)
+        a, sa = G.to_np(st1, s1)
+        assert np.array_equal(sa, s_b[o:o + c])
+        assert np.array_equal(a, st_b[:, o:o + c])     # same kernel, same arithmetic
+        o += c
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace_batch(batch, st, s, None, None, None,
+                          rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED))
     assert e.value.status == rt.RT_EUNSUPPORTED
