@@ -25,6 +25,8 @@ PREC_FP64, PREC_MIXED = 0, 1
  PLASMA_TWISTED) = range(6)
 WEIGHT_PAG, WEIGHT_UNIT_P, WEIGHT_RENORM = 0, 1, 2
 ROTATION_SNAPSHOT, ROTATION_RIGID = 0, 1
+DISP_ANISO, DISP_ISO = 0, 1
+METRIC_FULL, METRIC_FLAT = 0, 1
 
 
 class RtError(RuntimeError):

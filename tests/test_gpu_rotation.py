@@ -171,3 +171,75 @@ def test_rotating_batch_equals_single_star_calls():
         rt.rt_trace_batch(batch, st, s, None, None, None,
                           rt.make_opts(rtol=1e-8, precision=rt.PREC_MIXED))
     assert e.value.status == rt.RT_EUNSUPPORTED
+
+
+def _parity(oracle, kw, u, rtol=1e-10, **topt):
+    sv = oracle.star_vector(**kw)
+    st0, w0, s0 = oracle.sample(sv, u)
+    ref, sref, good, spread = G.well_conditioned(oracle, sv, st0, s0, rtol, **topt)
+    star = rt.Star(rt.make_params(**kw))
+    st_d = torch.from_numpy(st0.copy()).cuda()
+    s_d = torch.from_numpy(s0.copy()).cuda()
+    nacc, nrej, ctr = G.gpu_trace(star, st_d, s_d, rtol=rtol, **topt)
+    st_g, s_g, na = G.to_np(st_d, s_d, nacc)
+    return st0, s0, ref, sref, good, st_g, s_g, na, ctr.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 257])
+def test_rotating_ragged_sizes(oracle, n):
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _parity(
+        oracle, _star(0.6), I.sample_uniforms(440, n, first=300))
+    traced = s0 == 0
+    assert ctr[2] == traced.sum()                      # every lane of the ragged tail ran
+    assert (s_g[traced] == sref[traced]).mean() >= (0.95 if n > 30 else 1.0)
+    g = good & traced & (s_g == sref)
+    if g.any():
+        assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+        assert np.abs(st_g[6, g] - ref[6, g]).max() < 1e-12
+
+
+def test_rotating_step_bound_and_lambda_end_match_oracle(oracle):
+    u = I.sample_uniforms(441, 256)
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _parity(oracle, _star(0.6), u, max_steps=40)
+    traced = s0 == 0
+    assert np.array_equal(s_g[traced], sref[traced])
+    assert (s_g == rt.RAY_MAXSTEPS).sum() > 10
+    g = good & traced
+    assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+    # lambda_max: every ray stops at the same worldline parameter, mid-flight
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _parity(oracle, _star(0.6), u,
+                                                           lambda_max=5.0)
+    assert (s_g[traced] == rt.RAY_LAMBDA_END).mean() > 0.5
+    assert np.array_equal(s_g[traced], sref[traced])
+    g = good & traced
+    assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+    assert np.abs(st_g[7, g] - ref[7, g]).max() < 1e-10
+
+
+def test_rotating_zero_rays_and_empty_surface():
+    kw = _star(0.6)
+    star = rt.Star(rt.make_params(**kw))
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert rt.rt_trace_forward(star, 0, e, e) == rt.RT_OK
+    star2, st, w, s, code = G.gpu_sample(dict(kw, m_a_eV=1e-3), I.sample_uniforms(442, 300))
+    assert code == rt.RT_EEMPTY_SURFACE
+    nacc, nrej, ctr = G.gpu_trace(star2, st, s)
+    assert int(ctr[2]) == 0 and bool((s == rt.RAY_NO_ROOT).all())
+
+
+@pytest.mark.parametrize("variant", ["iso", "flat", "unit_p"])
+def test_rotating_model_variants(oracle, variant):
+    extra = {"iso": dict(dispersion=rt.DISP_ISO), "flat": dict(prop_metric=rt.METRIC_FLAT),
+             "unit_p": dict(weight_mode=rt.WEIGHT_UNIT_P)}[variant]
+    kw = _star(0.9, **extra)
+    st0, s0, ref, sref, good, st_g, s_g, na, ctr = _parity(oracle, kw,
+                                                           I.sample_uniforms(443, 512))
+    traced = s0 == 0
+    assert traced.sum() > 100
+    # flat propagation starts off shell (H != 0, App. B); with the plasma turning, a
+    # few such rays see dt/dl < 0 and a collapsing omega and end STIFF (oracle too)
+    assert (s_g[traced] == sref[traced]).mean() > (0.98 if variant == "flat" else 0.99)
+    g = good & traced & (s_g == sref)
+    assert g.sum() > 0.2 * traced.sum()
+    assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
+    assert np.abs(st_g[6, g] - ref[6, g]).max() < 1e-12
