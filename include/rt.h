@@ -77,6 +77,7 @@ enum {
   RT_PLASMA_RADIAL = 4, RT_PLASMA_TWISTED = 5
 };
 enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
+enum { RT_CLAIM_COST = 0, RT_CLAIM_INDEX = 1 };
 
 /*
  * Star, plasma and axion parameters (Sec. 5 fiducials; Eq. GJDensity).
@@ -156,7 +157,13 @@ typedef struct {
  *                     that many rays as the threshold.  1: one lane per ray
  *                     throughout.  The handle owns the park buffer (allocated on
  *                     first use, 33 MB on GB300).
- *   reserved          must be 0
+ *   claim_order       RT_CLAIM_COST (0): the FP64 forward kernels claim rays by
+ *                     predicted cost -- first those that start within 1e-3 rad,
+ *                     then 1e-2 rad, of the Goldreich-Julian null cone (the rays
+ *                     that can be guided along it for tens of thousands of
+ *                     steps), then the rest -- so that the longest rays run from
+ *                     the start of the launch; results do not depend on it.
+ *                     RT_CLAIM_INDEX (1): in index order.
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),
@@ -167,7 +174,7 @@ typedef struct {
  */
 typedef struct {
   double rtol, atol, r_out_over_R, lambda_max, r_capture_over_R;
-  int32_t precision, max_steps, block, blocks_per_sm, tail, reserved;
+  int32_t precision, max_steps, block, blocks_per_sm, tail, claim_order;
   uint64_t* timestamps;
 } rt_trace_opts;
 

@@ -301,7 +301,8 @@ static rt_status check_opts(const rt_trace_opts* o) {
     return fail(RT_EINVAL, "unknown precision %d", o->precision);
   if (o->block < 0 || o->blocks_per_sm < 0) return fail(RT_EINVAL, "negative launch parameter");
   if (o->tail < 0 || o->tail > 31) return fail(RT_EINVAL, "tail must be in [0, 31]");
-  if (o->reserved != 0) return fail(RT_EINVAL, "reserved must be 0");
+  if (o->claim_order != RT_CLAIM_COST && o->claim_order != RT_CLAIM_INDEX)
+    return fail(RT_EINVAL, "unknown claim_order %d", o->claim_order);
   return RT_OK;
 }
 
@@ -349,6 +350,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
+  p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST) ? 1 : 0;
   cudaError_t e;
   if (rigid) {
     e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
@@ -944,6 +946,9 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
+  // cost-ordered claims for the FP64 rays-only launches (not with images)
+  p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST && b->npix == 0)
+                ? 1 : 0;
   const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
   const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
   const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];

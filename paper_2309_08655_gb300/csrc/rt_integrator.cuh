@@ -88,6 +88,31 @@ struct Lane {
 constexpr double SWITCH_MIN_FRACTION = 1e-6;
 constexpr double SWITCH_OVERSHOOT = 1e-10;
 
+// Cost bucket of ray i for the cost-ordered claim (TraceParams::order): the
+// angular distance d of its start point from the Goldreich-Julian null cone
+// F = 3 n_z (m.n) - m_z = 0, d = |F| / |grad_n F| (the gradient on the unit
+// sphere); bucket 0 for d < 1e-3, 1 for d < 1e-2, 2 otherwise (and for every
+// other plasma).  Rays guided along the cone for thousands of steps start
+// within d < 1e-2 of it.
+__device__ __forceinline__ int cost_bucket(const StarDev& s, const double* state, int64_t n,
+                                           int64_t i) {
+  if (s.plasma != PLASMA_GJ) return COST_BUCKETS - 1;
+  const double x0 = state[i], x1 = state[n + i], x2 = state[2 * n + i];
+  double sp, cpsi;
+  sincos(state[7 * n + i], &sp, &cpsi);
+  const double m0 = s.sin_tm * cpsi, m1 = s.sin_tm * sp, m2 = s.cos_tm;
+  const double ir = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
+  const double n0 = x0 * ir, n1 = x1 * ir, n2 = x2 * ir;
+  const double mu = m0 * n0 + m1 * n1 + m2 * n2;
+  const double F = 3.0 * n2 * mu - m2;
+  // grad_n F = 3 (mu e_z + n_z m) minus its radial part 6 mu n_z n
+  const double c = 6.0 * mu * n2;
+  const double g0 = 3.0 * n2 * m0 - c * n0, g1 = 3.0 * n2 * m1 - c * n1,
+               g2 = 3.0 * (mu + n2 * m2) - c * n2;
+  const double F2 = F * F, G2 = g0 * g0 + g1 * g1 + g2 * g2;
+  return (F2 < 1e-6 * G2) ? 0 : (F2 < 1e-4 * G2) ? 1 : 2;
+}
+
 // Observer of accepted steps (forward tracing needs none).
 struct NoHook {
   __device__ __forceinline__ void on_accept(const Lane&, const double*, const double*,

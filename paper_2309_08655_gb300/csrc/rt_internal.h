@@ -32,7 +32,14 @@ struct TraceParams {
   unsigned long long* park_next;
   int64_t park_cap;
   int park_live;              // park when a drained warp holds at most this many rays
+  // claim order of the FP64 forward kernels: 0 = by index; 1 = by predicted
+  // cost -- COST_BUCKETS passes over the queue, the first taking the rays that
+  // start closest to the Goldreich-Julian null cone (the ones that can be
+  // guided along it for tens of thousands of steps), so that the longest rays
+  // run from the start of the launch instead of after the bulk
+  int order = 0;
 };
+constexpr int COST_BUCKETS = 3;
 constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lambda
 constexpr int PARK_LIVE_MAX = 5;
 // Park capacity that covers any persistent grid on the device (up to 31 rays

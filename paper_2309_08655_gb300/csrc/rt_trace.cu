@@ -87,6 +87,9 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   Lane L;
   long long acc = 0, rej = 0, traced = 0, esc = 0;
   int na0 = 0, nr0 = 0;   // steps a resumed ray had already taken in FP32
+  // the queue: one pass over the rays, or COST_BUCKETS passes (pass b claims
+  // the rays of cost bucket b)
+  const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   for (;;) {
     const bool need = (ray == -1);
@@ -98,13 +101,16 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       base = __shfl_sync(FULL, base, leader);
       if (need) {
         const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        if (idx >= p.n) {
+        const int pass = p.order ? (int)(idx / p.n) : 0;
+        const int64_t i = idx - (int64_t)pass * p.n;
+        if (idx >= nq) {
           ray = -2;
-        } else if (p.status[idx] != p.claim_status) {
+        } else if (p.status[i] != p.claim_status ||
+                   (p.order && cost_bucket(p.stars[find_star(p, i)], p.state, p.n, i) != pass)) {
           ray = -1;
         } else {
-          ray = idx;
-          load_lane(p, idx, L);
+          ray = i;
+          load_lane(p, i, L);
           na0 = L.na;
           nr0 = L.nr;
         }

@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(128) trace_rot_kernel(TraceParams p) {
   int64_t ray = -1;   // -1: needs a ray, -2: queue exhausted
   RotLane L;
   long long acc = 0, rej = 0, traced = 0, esc = 0;
+  const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;   // cost-ordered passes
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   for (;;) {
     const bool need = (ray == -1);
@@ -333,13 +334,16 @@ __global__ void __launch_bounds__(128) trace_rot_kernel(TraceParams p) {
       base = __shfl_sync(FULL, base, leader);
       if (need) {
         const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        if (idx >= p.n) {
+        const int pass = p.order ? (int)(idx / p.n) : 0;
+        const int64_t i = idx - (int64_t)pass * p.n;
+        if (idx >= nq) {
           ray = -2;
-        } else if (p.status[idx] != p.claim_status) {
+        } else if (p.status[i] != p.claim_status ||
+                   (p.order && cost_bucket(p.stars[star_of(p, i)], p.state, p.n, i) != pass)) {
           ray = -1;
         } else {
-          ray = idx;
-          load_rot(p, idx, L);
+          ray = i;
+          load_rot(p, i, L);
         }
       }
     }

@@ -21,6 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EEMPTY_SURFACE", "EPARTIAL",
  RAY_LAMBDA_END) = range(8)
 RAY_NSTATUS = 8
 PREC_FP64, PREC_MIXED = 0, 1
+CLAIM_COST, CLAIM_INDEX = 0, 1
 (PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL,
  PLASMA_TWISTED) = range(6)
 WEIGHT_PAG, WEIGHT_UNIT_P, WEIGHT_RENORM = 0, 1, 2
@@ -53,7 +54,7 @@ class rt_trace_opts(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in [
         "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
         (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm", "tail",
-                                      "reserved"]] + [
+                                      "claim_order"]] + [
         ("timestamps", ctypes.c_void_p)]
 
 
@@ -189,7 +190,7 @@ def make_params(**kw) -> rt_star_params:
 
 def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capture_over_R=1.0,
               precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0,
-              timestamps=None, tail=0) -> rt_trace_opts:
+              timestamps=None, tail=0, claim_order=0) -> rt_trace_opts:
     o = rt_trace_opts()
     o.rtol = rtol
     o.atol = rtol if atol is None else atol
@@ -201,7 +202,7 @@ def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capt
     o.block = block
     o.blocks_per_sm = blocks_per_sm
     o.tail = tail
-    o.reserved = 0
+    o.claim_order = claim_order
     o.timestamps = _ptr(timestamps)
     return o
 

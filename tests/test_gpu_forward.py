@@ -316,3 +316,20 @@ def test_flat_propagation_mode(oracle, dispersion):
     esc = traced & (s_g == rt.RAY_ESCAPED) & (cur[6] == rt.RAY_ESCAPED)
     assert esc.sum() > 100
     assert np.median(G.rel_state_diff(st_g[:, esc], cur[5][:, esc])) > 1e-6
+
+
+def test_claim_order_does_not_change_results():
+    # the star of the benchmark whose rays include the longest null-cone rays
+    kw = I.stars_config1()[15]
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, I.sample_uniforms(500, 8192))
+    out = {}
+    for order in (rt.CLAIM_COST, rt.CLAIM_INDEX):
+        st, s = st_d.clone(), s_d.clone()
+        nacc, nrej, ctr = G.gpu_trace(star, st, s, rtol=1e-10, tail=1, claim_order=order)
+        out[order] = G.to_np(st, s, nacc, nrej, ctr)
+    a, b = out[rt.CLAIM_COST], out[rt.CLAIM_INDEX]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)                 # one lane per ray: bitwise
+    with pytest.raises(rt.RtError) as e:
+        G.gpu_trace(star, st_d.clone(), s_d.clone(), claim_order=2)
+    assert e.value.status == rt.RT_EINVAL

@@ -249,3 +249,15 @@ def test_rotating_model_variants(oracle, variant):
     else:
         assert d.max() < 1e-10
         assert np.abs(st_g[6, g] - ref[6, g]).max() < 1e-12
+
+
+def test_rotating_claim_order_does_not_change_results():
+    kw = _star(math.radians(30.0), m_a_eV=1.06e-6, B0_G=1.6e14, P_s=3.76, M_sun=1.5, R_km=11.0)
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, I.sample_uniforms(444, 4096))
+    out = {}
+    for order in (rt.CLAIM_COST, rt.CLAIM_INDEX):
+        st, s = st_d.clone(), s_d.clone()
+        nacc, nrej, ctr = G.gpu_trace(star, st, s, rtol=1e-10, claim_order=order)
+        out[order] = G.to_np(st, s, nacc, nrej, ctr)
+    for x, y in zip(out[rt.CLAIM_COST], out[rt.CLAIM_INDEX]):
+        assert np.array_equal(x, y)
