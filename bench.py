@@ -76,6 +76,9 @@ def _traffic(prec, steps_per_launch=1):
     return nbytes if (nbytes is not None and h.hexdigest()[:16] == digest) else None
 
 
+CLAIM = {"index": 0, "cost": 1}
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -92,6 +95,8 @@ def _args():
                     help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-twisted", action="store_true",
                     help="skip the twisted-magnetosphere (Eq. neMag) workload")
+    ap.add_argument("--claim-order", choices=["index", "cost"], default="index",
+                    help="order in which the FP64 kernels claim rays (rt_trace_opts.claim_order)")
     ap.add_argument("--no-rotating", action="store_true",
                     help="skip the rigidly rotating magnetosphere workload")
     ap.add_argument("--no-uneven", action="store_true",
@@ -317,7 +322,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     opts = {
         "fp64": rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
-                             precision=rt.PREC_FP64, max_steps=cfg["max_steps"]),
+                             precision=rt.PREC_FP64, max_steps=cfg["max_steps"],
+                             claim_order=CLAIM[args.claim_order]),
         "mixed": rt.make_opts(rtol=cfg["rtol_mixed"], r_out_over_R=cfg["r_out_over_R"],
                               precision=rt.PREC_MIXED, max_steps=cfg["max_steps"]),
     }
@@ -489,6 +495,7 @@ def run_ours(args):
                              f"in one persistent trace launch (per-step histograms compared "
                              f"with one launch per step, whose numbers are under "
                              f"'{head}' -> 'ms_per_step')",
+                   "claim_order": args.claim_order,
                    "l2": f"inputs larger than L2 ({K} x 117 MB) and L2 flushed (256 MiB "
                          f"write) before the timed region"},
         "rays_per_s": HP["rays_per_s"],
@@ -601,7 +608,7 @@ def _rotating_leg(args, dev, stream):
     s = torch.empty(N, dtype=torch.uint8, device=dev)
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
     opts = rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
-                        max_steps=cfg["max_steps"])
+                        max_steps=cfg["max_steps"], claim_order=CLAIM[args.claim_order])
     rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
     delta0 = st[6].clone()
     rt.rt_trace_batch(batch, st, s, None, None, None, opts, stream=stream)   # warm-up

@@ -77,7 +77,7 @@ enum {
   RT_PLASMA_RADIAL = 4, RT_PLASMA_TWISTED = 5
 };
 enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
-enum { RT_CLAIM_COST = 0, RT_CLAIM_INDEX = 1 };
+enum { RT_CLAIM_INDEX = 0, RT_CLAIM_COST = 1 };
 
 /*
  * Star, plasma and axion parameters (Sec. 5 fiducials; Eq. GJDensity).
@@ -157,13 +157,17 @@ typedef struct {
  *                     that many rays as the threshold.  1: one lane per ray
  *                     throughout.  The handle owns the park buffer (allocated on
  *                     first use, 33 MB on GB300).
- *   claim_order       RT_CLAIM_COST (0): the FP64 forward kernels claim rays by
+ *   claim_order       RT_CLAIM_INDEX (0): rays are claimed in index order.
+ *                     RT_CLAIM_COST (1): the FP64 forward kernels claim rays by
  *                     predicted cost -- first those that start within 1e-3 rad,
  *                     then 1e-2 rad, of the Goldreich-Julian null cone (the rays
  *                     that can be guided along it for tens of thousands of
  *                     steps), then the rest -- so that the longest rays run from
- *                     the start of the launch; results do not depend on it.
- *                     RT_CLAIM_INDEX (1): in index order.
+ *                     the start of the launch.  A ray's arithmetic does not
+ *                     depend on the order, but which rays end in the tail kernel
+ *                     (whose results agree with one lane per ray to rounding)
+ *                     then varies from run to run: bitwise reproducible only
+ *                     with tail = 1.
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),
@@ -240,7 +244,7 @@ rt_status rt_sample_conversion_surface(const rt_star* star, int64_t n, const dou
  *              promoted rays in FP64, 2 reserved
  *   opts       integration options (host pointer, read during the call)
  * RT_PREC_FP64: every stage in FP64; deterministic (bitwise identical outputs
- * for identical inputs).  RT_PREC_MIXED: the stages and their combinations run
+ * for identical inputs) with the default claim order.  RT_PREC_MIXED: the stages and their combinations run
  * in FP32 and the state accumulates in FP64; where the FP32 rounding floor of
  * the embedded error estimate reaches a quarter of the tolerance on a rejected
  * step, the ray continues in FP64 from that point (a second kernel on the same

@@ -21,7 +21,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EEMPTY_SURFACE", "EPARTIAL",
  RAY_LAMBDA_END) = range(8)
 RAY_NSTATUS = 8
 PREC_FP64, PREC_MIXED = 0, 1
-CLAIM_COST, CLAIM_INDEX = 0, 1
+CLAIM_INDEX, CLAIM_COST = 0, 1
 (PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL,
  PLASMA_TWISTED) = range(6)
 WEIGHT_PAG, WEIGHT_UNIT_P, WEIGHT_RENORM = 0, 1, 2
