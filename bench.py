@@ -95,7 +95,7 @@ def _args():
                     help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-twisted", action="store_true",
                     help="skip the twisted-magnetosphere (Eq. neMag) workload")
-    ap.add_argument("--claim-order", choices=["index", "cost"], default="index",
+    ap.add_argument("--claim-order", choices=["index", "cost"], default="cost",
                     help="order in which the FP64 kernels claim rays (rt_trace_opts.claim_order)")
     ap.add_argument("--no-rotating", action="store_true",
                     help="skip the rigidly rotating magnetosphere workload")
