@@ -55,20 +55,23 @@ PEAK_FP32 = SMS * 256 * CLK
 # (FP64: the persistent trace launch plus its six-lane tail launch; mixed: the
 # FP32 launch plus the FP64 pass and its tail), from a single-pass ncu launch
 # list of `bench.py --steps 8 --warmup 1 --no-cpu-baseline --no-backward
-# --no-adjoint --no-uneven --no-twisted`, valid for the kernel sources with the
-# given SHA-256 prefix (reported as null once they change).
+# --no-adjoint --no-uneven --no-twisted --no-rotating` (cost-ordered claims),
+# valid for the kernel sources with the given SHA-256 prefix (reported as null
+# once they change).
 TRAFFIC = {
-    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "370b5adfb1c2553c",
-             {1: 38.2e6, 8: 475.8e6}),
+    # (steps per launch, claim order) -> DRAM bytes of the trace call
+    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "efe2066294217b38",
+             {(1, "cost"): 38.1e6, (8, "cost"): 774.7e6}),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_trace_mixed.cu'),
-              "0ad0080c3e28b4e2", {1: 36.6e6, 8: 447.3e6}),
+              "b1c2a672c2db62a0", {(1, "cost"): 36.6e6, (8, "cost"): 447.0e6,
+                                   (1, "index"): 36.6e6, (8, "index"): 447.0e6}),
 }
 
 
-def _traffic(prec, steps_per_launch=1):
+def _traffic(prec, steps_per_launch=1, claim="cost"):
     import hashlib
     files, digest, by_steps = TRAFFIC[prec]
-    nbytes = by_steps.get(steps_per_launch)
+    nbytes = by_steps.get((steps_per_launch, claim))
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2309_08655_gb300", "csrc", f), "rb") as fh:
@@ -373,14 +376,14 @@ def run_ours(args):
             flops = attempts * fl[1] + rays_launch * fl[2]
             roof = {"kernel": FP64_KERNELS, "bound": "alu", "achieved": flops / t_tr / 1e12,
                     "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP64, "traffic": _traffic("fp64"),
+                    "frac": flops / t_tr / PEAK_FP64, "traffic": _traffic("fp64", 1, args.claim_order),
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
         else:
             flops = (attempts - promoted_attempts) * fl[1] + rays_launch * fl[2]
             roof = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)",
                     "bound": "alu", "achieved": flops / t_tr / 1e12,
                     "peak": PEAK_FP32 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP32, "traffic": _traffic("mixed"),
+                    "frac": flops / t_tr / PEAK_FP32, "traffic": _traffic("mixed", 1, args.claim_order),
                     "peak_source": "derived: 152 SMs x 256 FP32 flop/clk x 2070 MHz",
                     "promoted_rays_per_step": c_sum[4] / args.steps,
                     "promoted_fp64_attempts_per_step": promoted_attempts}
@@ -424,7 +427,7 @@ def run_ours(args):
             peak, kern = PEAK_FP32, "trace_mixed_kernel (+ FP64 pass for promoted rays)"
         roof = dict(res[prec]["roofline"])
         roof.update({"kernel": kern, "achieved": flops / t_tr / 1e12, "frac": flops / t_tr / peak,
-                     "traffic": _traffic(prec, K), "attempts_per_launch": attempts,
+                     "traffic": _traffic(prec, K, args.claim_order), "attempts_per_launch": attempts,
                      "trace_ms_per_launch": 1e3 * t_tr, "steps_per_launch": K})
         hp = P.hist.cpu().numpy()
         same = all(np.array_equal(hp[k * nsub:(k + 1) * nsub], hists[prec]) for k in range(K))
