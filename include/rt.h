@@ -163,11 +163,13 @@ typedef struct {
  *                     then 1e-2 rad, of the Goldreich-Julian null cone (the rays
  *                     that can be guided along it for tens of thousands of
  *                     steps), then the rest -- so that the longest rays run from
- *                     the start of the launch.  A ray's arithmetic does not
- *                     depend on the order, but which rays end in the tail kernel
- *                     (whose results agree with one lane per ray to rounding)
- *                     then varies from run to run: bitwise reproducible only
- *                     with tail = 1.
+ *                     the start of the launch.  In tail mode (tail != 1) the
+ *                     rays within 1e-3 rad (up to 8192 per call, nearest first)
+ *                     are traced six lanes per ray from the start on a few SMs
+ *                     of their own (the express lane), and the others one lane
+ *                     per ray without parking; results agree with index order
+ *                     to rounding and are bitwise reproducible (unless more
+ *                     than 8192 rays qualify).  Not with images in a batch.
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),

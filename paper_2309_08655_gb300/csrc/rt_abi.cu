@@ -263,7 +263,9 @@ static rt_status ensure_park(double** buf, int64_t* cap) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int64_t c = rtk::park_capacity(nsm > 0 ? nsm : 1);
   void* p = nullptr;
-  if (cudaMalloc(&p, 256 + (size_t)c * rtk::PARKREC * sizeof(double)) != cudaSuccess) {
+  // [256 B counters | c park records | express area]
+  if (cudaMalloc(&p, 256 + (size_t)c * rtk::PARKREC * sizeof(double) + rtk::express_bytes()) !=
+      cudaSuccess) {
     cudaGetLastError();
     return fail(RT_ENOMEM, "cannot allocate the tail-mode park buffer");
   }
@@ -284,6 +286,22 @@ static void set_park(rtk::TraceParams& p, double* buf, int64_t cap, const rt_tra
     p.park_count = p.park_next = nullptr;
     p.park_cap = 0;
   }
+}
+
+// The express area after the park records (cost-ordered FP64 tracing with a
+// park buffer): the bucket-0 rays are traced six lanes per ray from the start.
+static void set_express(rtk::TraceParams& p) {
+  if (!p.order || !p.park) {
+    p.xrec = nullptr;
+    return;
+  }
+  char* x = (char*)(p.park + p.park_cap * rtk::PARKREC);
+  p.xcount = (unsigned long long*)x;
+  p.xslot = (int*)(x + 64);
+  p.xcand = (unsigned long long*)(x + 64 + rtk::XSLOTS * sizeof(int));
+  p.xrec = (double*)(x + 64 + rtk::XSLOTS * sizeof(int) +
+                     (size_t)rtk::XCAP * 2 * sizeof(unsigned long long));
+  p.xcap = rtk::XCAP;
 }
 
 static rt_status check_opts(const rt_trace_opts* o) {
@@ -351,6 +369,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
   p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST) ? 1 : 0;
+  set_express(p);
   cudaError_t e;
   if (rigid) {
     e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
@@ -949,6 +968,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   // cost-ordered claims for the FP64 rays-only launches (not with images)
   p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST && b->npix == 0)
                 ? 1 : 0;
+  set_express(p);
   const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
   const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
   const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];

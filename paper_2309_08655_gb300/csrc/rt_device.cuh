@@ -58,7 +58,8 @@ enum { ROTATION_SNAPSHOT = 0, ROTATION_RIGID = 1 };
 enum {
   RAY_READY = 0, RAY_ESCAPED = 1, RAY_CAPTURED = 2, RAY_NO_ROOT = 3, RAY_MAXSTEPS = 4,
   RAY_NAN = 5, RAY_STIFF = 6, RAY_LAMBDA_END = 7,
-  RAY_PROMOTED = 8   // internal: handed from the FP32 pass to the FP64 pass
+  RAY_PROMOTED = 8,  // internal: handed from the FP32 pass to the FP64 pass
+  RAY_EXPRESS = 9    // internal: traced by the express groups of the FP64 launch
 };
 
 // (The host branches exist for host-side instantiation in tests of the formula.)

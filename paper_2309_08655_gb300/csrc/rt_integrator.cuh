@@ -88,15 +88,13 @@ struct Lane {
 constexpr double SWITCH_MIN_FRACTION = 1e-6;
 constexpr double SWITCH_OVERSHOOT = 1e-10;
 
-// Cost bucket of ray i for the cost-ordered claim (TraceParams::order): the
-// angular distance d of its start point from the Goldreich-Julian null cone
-// F = 3 n_z (m.n) - m_z = 0, d = |F| / |grad_n F| (the gradient on the unit
-// sphere); bucket 0 for d < 1e-3, 1 for d < 1e-2, 2 otherwise (and for every
-// other plasma).  Rays guided along the cone for thousands of steps start
-// within d < 1e-2 of it.
-__device__ __forceinline__ int cost_bucket(const StarDev& s, const double* state, int64_t n,
-                                           int64_t i) {
-  if (s.plasma != PLASMA_GJ) return COST_BUCKETS - 1;
+// Squared angular distance of ray i's start point from the Goldreich-Julian
+// null cone F = 3 n_z (m.n) - m_z = 0, (F / |grad_n F|)^2 (the gradient on
+// the unit sphere); 1e300 for the other plasmas.  Rays guided along the cone for
+// thousands of steps start within 1e-2 rad of it.
+__device__ __forceinline__ double cone_dist2(const StarDev& s, const double* state, int64_t n,
+                                             int64_t i) {
+  if (s.plasma != PLASMA_GJ) return 1e300;
   const double x0 = state[i], x1 = state[n + i], x2 = state[2 * n + i];
   double sp, cpsi;
   sincos(state[7 * n + i], &sp, &cpsi);
@@ -109,8 +107,15 @@ __device__ __forceinline__ int cost_bucket(const StarDev& s, const double* state
   const double c = 6.0 * mu * n2;
   const double g0 = 3.0 * n2 * m0 - c * n0, g1 = 3.0 * n2 * m1 - c * n1,
                g2 = 3.0 * (mu + n2 * m2) - c * n2;
-  const double F2 = F * F, G2 = g0 * g0 + g1 * g1 + g2 * g2;
-  return (F2 < 1e-6 * G2) ? 0 : (F2 < 1e-4 * G2) ? 1 : 2;
+  return (F * F) / (g0 * g0 + g1 * g1 + g2 * g2);
+}
+
+// Cost bucket for the cost-ordered claim (TraceParams::order): 0 for a start
+// within 1e-3 rad of the null cone, 1 within 1e-2 rad, 2 otherwise.
+__device__ __forceinline__ int cost_bucket(const StarDev& s, const double* state, int64_t n,
+                                           int64_t i) {
+  const double d2 = cone_dist2(s, state, n, i);
+  return (d2 < 1e-6) ? 0 : (d2 < 1e-4) ? 1 : 2;
 }
 
 // Observer of accepted steps (forward tracing needs none).

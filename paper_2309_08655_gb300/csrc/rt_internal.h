@@ -38,10 +38,28 @@ struct TraceParams {
   // guided along it for tens of thousands of steps), so that the longest rays
   // run from the start of the launch instead of after the bulk
   int order = 0;
+  // express lane (cost-ordered FP64 tracing in tail mode): the rays of cost
+  // bucket 0, ranked by their distance from the null cone, become park records
+  // that six-lane groups of the first block on each of the first SMs continue
+  // from the start of the launch, while the other blocks trace the rest one
+  // lane per ray (without parking); the tail launch takes any record left over
+  double* xrec = nullptr;               // xcap records of PARKREC doubles
+  unsigned long long* xcount = nullptr;  // [0] candidates found, [1] next record
+  int* xslot = nullptr;                 // per-SM arrival counter (XSLOTS ints)
+  unsigned long long* xcand = nullptr;   // xcap (key, ray) pairs
+  int64_t xcap = 0;
 };
 constexpr int COST_BUCKETS = 3;
 constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lambda
 constexpr int PARK_LIVE_MAX = 5;
+constexpr int XSLOTS = 256;            // per-SM counters (more than any GPU's SMs)
+constexpr int64_t XCAP = 8192;         // express records per launch
+constexpr int XRAYS_PER_SM = 20;       // four warps of five six-lane groups
+// bytes of the express area: counters, per-SM slots, candidates, records
+inline size_t express_bytes() {
+  return 64 + XSLOTS * sizeof(int) + (size_t)XCAP * 2 * sizeof(unsigned long long) +
+         (size_t)XCAP * PARKREC * sizeof(double);
+}
 // Park capacity that covers any persistent grid on the device (up to 31 rays
 // per warp).
 inline int64_t park_capacity(int nsm) { return (int64_t)nsm * (2048 / 32) * 31; }

@@ -11,6 +11,7 @@
 #include "rt_device.cuh"
 #include "rt_integrator.cuh"
 #include "rt_internal.h"
+#include "rt_tail.cuh"
 
 namespace rtk {
 
@@ -81,6 +82,63 @@ __device__ void store_lane(const TraceParams& p, int64_t i, const Lane& L, int s
   if (p.nrej) p.nrej[i] = L.nr;
 }
 
+// Express lane, step 1: the READY rays of cost bucket 0 as (key, ray) pairs,
+// key = the bits of the squared null-cone distance (ordered as the distance).
+__global__ void express_select_kernel(TraceParams p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (p.status[i] != RAY_READY) continue;
+    const double d2 = cone_dist2(p.stars[find_star(p, i)], p.state, p.n, i);
+    if (!(d2 < 1e-6)) continue;                     // cost bucket 0 only
+    const unsigned long long slot = atomicAdd(p.xcount, 1ull);
+    if (slot < (unsigned long long)p.xcap) {
+      p.xcand[2 * slot] = (unsigned long long)__double_as_longlong(d2);
+      p.xcand[2 * slot + 1] = (unsigned long long)i;
+    }
+  }
+}
+
+// Express lane, step 2: candidate k goes to record slot rank(k) (ascending
+// distance, ties by ray index: nearest the cone first) as a fresh park record
+// (the start of load_lane), and its ray leaves the queue (RAY_EXPRESS).
+__global__ void express_rank_kernel(TraceParams p) {
+  const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
+                                   ? *p.xcount : (unsigned long long)p.xcap;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = p.xcand[2 * k], ray = p.xcand[2 * k + 1];
+    unsigned long long rank = 0;
+    for (unsigned long long j = 0; j < K; ++j) {
+      const unsigned long long kj = p.xcand[2 * j], rj = p.xcand[2 * j + 1];
+      rank += (kj < key || (kj == key && rj < ray)) ? 1ull : 0ull;
+    }
+    Lane L;
+    load_lane(p, (int64_t)ray, L);
+    double* pe = p.xrec + rank * PARKREC;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) pe[j] = L.y[j];
+    pe[6] = L.h;
+    pe[7] = 0.0;
+    pe[8] = L.c.sig;
+    pe[9] = 0.0;
+    pe[10] = 0.0;
+    pe[11] = 0.0;
+    pe[12] = (double)ray;
+    pe[13] = 0.0;
+    p.status[ray] = RAY_EXPRESS;
+  }
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// Wait of an express SM's other blocks: 20 us naps, at most ~20 s, then on.
+constexpr int XWAIT_NS = 20000;
+constexpr int XWAIT_MAX = 1000000;
+
 __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   const int lane = threadIdx.x & 31;
   int64_t ray = -1;   // -1: needs a ray, -2: queue exhausted
@@ -91,6 +149,38 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   // the rays of cost bucket b)
   const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  if (p.xrec) {
+    // express lane: the first block on each of the first ceil(K / 20) SMs
+    // (at most an eighth of them) continues the K express records six lanes
+    // per ray from the start; the SM's other blocks nap until every record is
+    // claimed, so that each express warp has its sub-partition to itself
+    const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
+                                     ? *p.xcount : (unsigned long long)p.xcap;
+    __shared__ int role;
+    if (threadIdx.x == 0) {
+      int nsm = 1;
+      asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+      unsigned long long xs = (K + XRAYS_PER_SM - 1) / XRAYS_PER_SM;
+      const unsigned long long cap = (unsigned long long)(nsm / 8 > 0 ? nsm / 8 : 1);
+      if (xs > cap) xs = cap;
+      const unsigned sm = sm_id();
+      role = (sm < xs && sm < (unsigned)XSLOTS) ? atomicAdd(p.xslot + sm, 1) : -1;
+    }
+    __syncthreads();
+    if (role == 0) {
+      GroupCounts gc;
+      tail_groups(p, p.xrec, K, p.xcount + 1, gc);
+      acc += gc.acc;
+      rej += gc.rej;
+      traced += gc.traced;
+      esc += gc.esc;
+    } else if (role > 0) {
+      for (int it = 0; it < XWAIT_MAX; ++it) {
+        if (*(volatile unsigned long long*)(p.xcount + 1) >= K) break;
+        __nanosleep(XWAIT_NS);
+      }
+    }
+  }
   for (;;) {
     const bool need = (ray == -1);
     const unsigned mneed = __ballot_sync(FULL, need);
@@ -528,7 +618,23 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
     e = cudaMemsetAsync(p.park_count, 0, 2 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
   }
-  trace_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(p);
+  TraceParams q = p;
+  if (p.xrec) {
+    // express lane: select and rank the bucket-0 rays; the persistent launch
+    // then traces the rest one lane per ray without parking
+    e = cudaMemsetAsync(p.xcount, 0, 64 + XSLOTS * sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const int64_t sel_grid = (p.n + 255) / 256 < (int64_t)nsm * 8 ? (p.n + 255) / 256
+                                                                   : (int64_t)nsm * 8;
+    express_select_kernel<<<(unsigned)(sel_grid > 0 ? sel_grid : 1), 256, 0, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    express_rank_kernel<<<(unsigned)((XCAP + 127) / 128), 128, 0, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    q.park = nullptr;
+  }
+  trace_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(q);
   e = cudaGetLastError();
   if (e != cudaSuccess || !p.park) return e;
   return launch_tail_fp64(p, stream);

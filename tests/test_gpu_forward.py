@@ -333,3 +333,48 @@ def test_claim_order_does_not_change_results():
     with pytest.raises(rt.RtError) as e:
         G.gpu_trace(star, st_d.clone(), s_d.clone(), claim_order=2)
     assert e.value.status == rt.RT_EINVAL
+
+
+def test_express_lane_matches_index_order(oracle):
+    # cost order in tail mode: the rays nearest the null cone run six lanes per
+    # ray from the start (express lane), the others one lane per ray
+    kw = I.stars_config1()[15]
+    u = I.sample_uniforms(501, 16384)
+    sv = oracle.star_vector(**kw)
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, u)
+    out = {}
+    for name, order in (("cost", rt.CLAIM_COST), ("cost_again", rt.CLAIM_COST),
+                        ("index", rt.CLAIM_INDEX)):
+        st, s = st_d.clone(), s_d.clone()
+        nacc, nrej, ctr = G.gpu_trace(star, st, s, rtol=1e-10, claim_order=order)
+        out[name] = G.to_np(st, s, nacc, ctr)
+    a, b, c = out["cost"], out["cost_again"], out["index"]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)                    # reproducible
+    traced = s_d.cpu().numpy() == rt.RAY_READY
+    assert a[3][2] == traced.sum() == c[3][2]          # every ray traced once
+    assert (a[1][traced] == c[1][traced]).mean() > 0.999
+    m = traced & (a[1] == c[1]) & (a[1] == rt.RAY_ESCAPED)
+    d = G.rel_state_diff(a[0][:, m], c[0][:, m])
+    assert np.median(d) < 1e-13 and np.percentile(d, 99) < 1e-9
+    # the express rays themselves against the oracle
+    st0 = st_d.cpu().numpy()
+    x = st0[:3] / kw["R_km"]
+    r = np.linalg.norm(x, axis=0)
+    tm = kw["theta_m"]
+    mvec = np.array([np.sin(tm) * np.cos(st0[7]), np.sin(tm) * np.sin(st0[7]),
+                     np.full(st0.shape[1], np.cos(tm))])
+    n = x / np.where(r > 0, r, 1)
+    mu = (mvec * n).sum(0)
+    F = 3 * n[2] * mu - mvec[2]
+    cc = 6 * mu * n[2]
+    g = np.array([3 * n[2] * mvec[0] - cc * n[0], 3 * n[2] * mvec[1] - cc * n[1],
+                  3 * (mu + n[2] * mvec[2]) - cc * n[2]])
+    dist = np.abs(F) / np.maximum(np.linalg.norm(g, axis=0), 1e-300)
+    near = np.where(traced & (dist < 1e-3))[0]
+    assert near.size > 5
+    ref, sref, good, spread = G.well_conditioned(oracle, sv, st0[:, near].copy(),
+                                                 s_d.cpu().numpy()[near].copy(), 1e-10)
+    gsel = good & (sref == a[1][near])
+    if gsel.any():
+        assert G.rel_state_diff(a[0][:, near][:, gsel], ref[:, gsel]).max() < 1e-10
