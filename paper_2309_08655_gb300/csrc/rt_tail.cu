@@ -17,15 +17,17 @@ namespace {
 __global__ void __launch_bounds__(128) tail_fp64_kernel(TraceParams p) {
   const int lane = threadIdx.x & 31;
   GroupCounts gc;
-  if (p.xrec) {
+  if (p.xrec) {   // express records that no express group claimed
     const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
                                      ? *p.xcount : (unsigned long long)p.xcap;
-    tail_groups(p, p.xrec, K, p.xcount + 1, gc);
+    const unsigned long long S = express_sms(K) < K ? express_sms(K) : K;
+    tail_groups(p, p.xrec, 0, S, p.xcount + 2, GROUPS_PER_WARP, gc);
+    tail_groups(p, p.xrec, S, K, p.xcount + 1, GROUPS_PER_WARP, gc);
   }
   const unsigned long long nparked = *p.park_count < (unsigned long long)p.park_cap
                                          ? *p.park_count
                                          : (unsigned long long)p.park_cap;
-  tail_groups(p, p.park, nparked, p.park_next, gc);
+  tail_groups(p, p.park, 0, nparked, p.park_next, GROUPS_PER_WARP, gc);
   if (p.counters && (lane % GROUP) == 0 && lane / GROUP < GROUPS_PER_WARP) {
     atomicAdd((unsigned long long*)&p.counters[CTR_ACC], (unsigned long long)gc.acc);
     atomicAdd((unsigned long long*)&p.counters[CTR_REJ], (unsigned long long)gc.rej);

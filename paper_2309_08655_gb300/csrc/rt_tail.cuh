@@ -315,14 +315,17 @@ struct GroupCounts {
 };
 
 // Six-lane groups of the calling warp continue parked rays: records
-// [*next, nrec) of recs (PARKREC doubles each: y[6], h, h_resume, sig, flags,
-// na, nr, ray, lambda), claimed one per group with an atomic on *next, until
-// none is left.  Every lane of the warp must call it.
-__device__ void tail_groups(const TraceParams& p, const double* recs, unsigned long long nrec,
-                            unsigned long long* next, GroupCounts& cnt) {
+// lo + e of recs (PARKREC doubles each: y[6], h, h_resume, sig, flags, na, nr,
+// ray, lambda), e = 0, 1, ... claimed one per group with an atomic on *next,
+// while lo + e < hi.  ngroups (1 to GROUPS_PER_WARP) groups of the warp take
+// part: one group per warp keeps a ray's attempts free of the other groups'
+// divergent branches.  Every lane of the warp must call it.
+__device__ void tail_groups(const TraceParams& p, const double* recs, unsigned long long lo,
+                            unsigned long long hi, unsigned long long* next, int ngroups,
+                            GroupCounts& cnt) {
   const int lane = threadIdx.x & 31;
   const int g = lane / GROUP, cc = lane % GROUP;
-  const bool in_group = g < GROUPS_PER_WARP;
+  const bool in_group = g < ngroups && g < GROUPS_PER_WARP;
   const int base = g * GROUP;
   const unsigned gm = in_group ? (0x3Fu << base) : 0u;
   GLane L;
@@ -331,9 +334,9 @@ __device__ void tail_groups(const TraceParams& p, const double* recs, unsigned l
   for (;;) {
     if (in_group && !have && !done) {
       unsigned long long e = 0;
-      if (cc == 0) e = atomicAdd(next, 1ull);
+      if (cc == 0) e = lo + atomicAdd(next, 1ull);
       e = __shfl_sync(gm, e, base);
-      if (e >= nrec) {
+      if (e >= hi) {
         done = true;
       } else {
         const double* pe = recs + e * PARKREC;
@@ -393,6 +396,17 @@ __device__ void tail_groups(const TraceParams& p, const double* recs, unsigned l
       }
     }
   }
+}
+
+// The express records' split: the first S (one per express SM) are continued
+// by one group per warp, the rest (S to K) by five; S express SMs, at most an
+// eighth of the device's SM identifiers.
+__device__ __forceinline__ unsigned long long express_sms(unsigned long long K) {
+  int nsm = 1;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+  unsigned long long xs = (K + XRAYS_PER_SM - 1) / XRAYS_PER_SM;
+  const unsigned long long cap = (unsigned long long)(nsm / 8 > 0 ? nsm / 8 : 1);
+  return xs < cap ? xs : cap;
 }
 
 }  // namespace

@@ -150,33 +150,35 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   if (p.xrec) {
-    // express lane: the first block on each of the first ceil(K / 20) SMs
-    // (at most an eighth of them) continues the K express records six lanes
-    // per ray from the start; the SM's other blocks nap until every record is
-    // claimed, so that each express warp has its sub-partition to itself
+    // express lane: the first block on each of the first S SMs continues the
+    // K express records six lanes per ray from the start -- its warp 0 the
+    // first S records (the rays nearest the cone) one group at a time, then,
+    // like its other warps, the rest five groups at a time; the SM's other
+    // blocks nap until every record is claimed, so that each express warp has
+    // its sub-partition to itself
     const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
                                      ? *p.xcount : (unsigned long long)p.xcap;
+    const unsigned long long xs = express_sms(K);
+    const unsigned long long S = xs < K ? xs : K;
     __shared__ int role;
     if (threadIdx.x == 0) {
-      int nsm = 1;
-      asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
-      unsigned long long xs = (K + XRAYS_PER_SM - 1) / XRAYS_PER_SM;
-      const unsigned long long cap = (unsigned long long)(nsm / 8 > 0 ? nsm / 8 : 1);
-      if (xs > cap) xs = cap;
       const unsigned sm = sm_id();
       role = (sm < xs && sm < (unsigned)XSLOTS) ? atomicAdd(p.xslot + sm, 1) : -1;
     }
     __syncthreads();
     if (role == 0) {
       GroupCounts gc;
-      tail_groups(p, p.xrec, K, p.xcount + 1, gc);
+      if ((threadIdx.x >> 5) == 0) tail_groups(p, p.xrec, 0, S, p.xcount + 2, 1, gc);
+      tail_groups(p, p.xrec, S, K, p.xcount + 1, GROUPS_PER_WARP, gc);
       acc += gc.acc;
       rej += gc.rej;
       traced += gc.traced;
       esc += gc.esc;
     } else if (role > 0) {
       for (int it = 0; it < XWAIT_MAX; ++it) {
-        if (*(volatile unsigned long long*)(p.xcount + 1) >= K) break;
+        if (*(volatile unsigned long long*)(p.xcount + 2) >= S &&
+            *(volatile unsigned long long*)(p.xcount + 1) >= K - S)
+          break;
         __nanosleep(XWAIT_NS);
       }
     }
