@@ -164,7 +164,7 @@ typedef struct {
  *                     that can be guided along it for tens of thousands of
  *                     steps), then the rest -- so that the longest rays run from
  *                     the start of the launch.  In tail mode (tail != 1) the
- *                     rays within 1e-3 rad (up to 8192 per call, ranked)
+ *                     rays within 1e-3 rad (up to 8192 per call, nearest first)
  *                     are traced six lanes per ray from the start on a few SMs
  *                     of their own (the express lane), and the others one lane
  *                     per ray without parking; results agree with index order

@@ -82,44 +82,24 @@ __device__ void store_lane(const TraceParams& p, int64_t i, const Lane& L, int s
   if (p.nrej) p.nrej[i] = L.nr;
 }
 
-// Express lane, step 1: the READY rays of cost bucket 0 as (key, ray) pairs.
-// The key ranks them by how long they may stay by the cone: the start's
-// distance d from it, times |cos| of the angle between the momentum and the
-// cone's normal plus 0.1 (a ray that starts moving along the cone is guided
-// longest); key = the bits of (d (|k.g| + 0.1))^2, ordered as the value.
+// Express lane, step 1: the READY rays of cost bucket 0 as (key, ray) pairs,
+// key = the bits of the squared null-cone distance (ordered as the distance).
 __global__ void express_select_kernel(TraceParams p) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (p.status[i] != RAY_READY) continue;
-    const StarDev& s = p.stars[find_star(p, i)];
-    const double d2 = cone_dist2(s, p.state, p.n, i);
+    const double d2 = cone_dist2(p.stars[find_star(p, i)], p.state, p.n, i);
     if (!(d2 < 1e-6)) continue;                     // cost bucket 0 only
-    const int64_t n = p.n;
-    const double x0 = p.state[i], x1 = p.state[n + i], x2 = p.state[2 * n + i];
-    const double k0 = p.state[3 * n + i], k1 = p.state[4 * n + i], k2 = p.state[5 * n + i];
-    double sp, cpsi;
-    sincos(p.state[7 * n + i], &sp, &cpsi);
-    const double m0 = s.sin_tm * cpsi, m1 = s.sin_tm * sp, m2 = s.cos_tm;
-    const double ir = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
-    const double n0 = x0 * ir, n1 = x1 * ir, n2 = x2 * ir;
-    const double mu = m0 * n0 + m1 * n1 + m2 * n2;
-    const double c = 6.0 * mu * n2;
-    const double g0 = 3.0 * n2 * m0 - c * n0, g1 = 3.0 * n2 * m1 - c * n1,
-                 g2 = 3.0 * (mu + n2 * m2) - c * n2;
-    const double kg = fabs(k0 * g0 + k1 * g1 + k2 * g2) *
-                      rsqrt((k0 * k0 + k1 * k1 + k2 * k2) * (g0 * g0 + g1 * g1 + g2 * g2));
-    const double w = kg + 0.1;
-    const double key = d2 * w * w;
     const unsigned long long slot = atomicAdd(p.xcount, 1ull);
     if (slot < (unsigned long long)p.xcap) {
-      p.xcand[2 * slot] = (unsigned long long)__double_as_longlong(key);
+      p.xcand[2 * slot] = (unsigned long long)__double_as_longlong(d2);
       p.xcand[2 * slot + 1] = (unsigned long long)i;
     }
   }
 }
 
 // Express lane, step 2: candidate k goes to record slot rank(k) (ascending
-// key, ties by ray index) as a fresh park record
+// distance, ties by ray index: nearest the cone first) as a fresh park record
 // (the start of load_lane), and its ray leaves the queue (RAY_EXPRESS).
 __global__ void express_rank_kernel(TraceParams p) {
   const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
@@ -172,7 +152,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   if (p.xrec) {
     // express lane: the first block on each of the first S SMs continues the
     // K express records six lanes per ray from the start -- its warp 0 the
-    // first S records (the highest-ranked rays) one group at a time, then,
+    // first S records (the rays nearest the cone) one group at a time, then,
     // like its other warps, the rest five groups at a time; the SM's other
     // blocks nap until every record is claimed, so that each express warp has
     // its sub-partition to itself
