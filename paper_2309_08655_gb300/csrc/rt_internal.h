@@ -54,7 +54,7 @@ constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lam
 constexpr int PARK_LIVE_MAX = 5;
 constexpr int XSLOTS = 256;            // per-SM counters (more than any GPU's SMs)
 constexpr int64_t XCAP = 8192;         // express records per launch
-constexpr int XRAYS_PER_SM = 16;       // one six-lane group in warp 0, five in warps 1-3
+constexpr int XRAYS_PER_SM = 12;       // one six-lane group in warps 0-1, five in 2-3
 // bytes of the express area: counters, per-SM slots, candidates, records
 inline size_t express_bytes() {
   return 64 + XSLOTS * sizeof(int) + (size_t)XCAP * 2 * sizeof(unsigned long long) +

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(128) tail_fp64_kernel(TraceParams p) {
   if (p.xrec) {   // express records that no express group claimed
     const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
                                      ? *p.xcount : (unsigned long long)p.xcap;
-    const unsigned long long S = express_sms(K) < K ? express_sms(K) : K;
+    const unsigned long long S = express_solo(K);
     tail_groups(p, p.xrec, 0, S, p.xcount + 2, GROUPS_PER_WARP, gc);
     tail_groups(p, p.xrec, S, K, p.xcount + 1, GROUPS_PER_WARP, gc);
   }

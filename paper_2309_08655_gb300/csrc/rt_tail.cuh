@@ -398,15 +398,21 @@ __device__ void tail_groups(const TraceParams& p, const double* recs, unsigned l
   }
 }
 
-// The express records' split: the first S (one per express SM) are continued
-// by one group per warp, the rest (S to K) by five; S express SMs, at most an
-// eighth of the device's SM identifiers.
+// Express SMs for K records: XRAYS_PER_SM per SM, at most an eighth of the
+// device's SM identifiers.
 __device__ __forceinline__ unsigned long long express_sms(unsigned long long K) {
   int nsm = 1;
   asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
   unsigned long long xs = (K + XRAYS_PER_SM - 1) / XRAYS_PER_SM;
   const unsigned long long cap = (unsigned long long)(nsm / 8 > 0 ? nsm / 8 : 1);
   return xs < cap ? xs : cap;
+}
+
+// The express records' split: the first S (two per express SM) are continued
+// one group per warp, the rest (S to K) five groups per warp.
+__device__ __forceinline__ unsigned long long express_solo(unsigned long long K) {
+  const unsigned long long S = 2 * express_sms(K);
+  return S < K ? S : K;
 }
 
 }  // namespace

@@ -150,16 +150,16 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
   const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
   if (p.xrec) {
-    // express lane: the first block on each of the first S SMs continues the
-    // K express records six lanes per ray from the start -- its warp 0 the
-    // first S records (the rays nearest the cone) one group at a time, then,
-    // like its other warps, the rest five groups at a time; the SM's other
-    // blocks nap until every record is claimed, so that each express warp has
-    // its sub-partition to itself
+    // express lane: the first block on each of the first xs SMs continues the
+    // K express records six lanes per ray from the start -- its warps 0 and 1
+    // the first S = 2 xs records (the rays nearest the cone) one group at a
+    // time, then, like its other warps, the rest five groups at a time; the
+    // SM's other blocks nap until every record is claimed, so that each
+    // express warp has its sub-partition to itself
     const unsigned long long K = *p.xcount < (unsigned long long)p.xcap
                                      ? *p.xcount : (unsigned long long)p.xcap;
     const unsigned long long xs = express_sms(K);
-    const unsigned long long S = xs < K ? xs : K;
+    const unsigned long long S = express_solo(K);
     __shared__ int role;
     if (threadIdx.x == 0) {
       const unsigned sm = sm_id();
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
     __syncthreads();
     if (role == 0) {
       GroupCounts gc;
-      if ((threadIdx.x >> 5) == 0) tail_groups(p, p.xrec, 0, S, p.xcount + 2, 1, gc);
+      if ((threadIdx.x >> 5) < 2) tail_groups(p, p.xrec, 0, S, p.xcount + 2, 1, gc);
       tail_groups(p, p.xrec, S, K, p.xcount + 1, GROUPS_PER_WARP, gc);
       acc += gc.acc;
       rej += gc.rej;
