@@ -60,11 +60,11 @@ PEAK_FP32 = SMS * 256 * CLK
 # once they change).
 TRAFFIC = {
     # (steps per launch, claim order) -> DRAM bytes of the trace call
-    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "efe2066294217b38",
-             {(1, "cost"): 38.1e6, (8, "cost"): 774.7e6}),
+    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "da695116b94dbdc6",
+             {(1, "cost"): 54.1e6, (8, "cost"): 920.2e6}),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_trace_mixed.cu'),
-              "b1c2a672c2db62a0", {(1, "cost"): 36.6e6, (8, "cost"): 447.0e6,
-                                   (1, "index"): 36.6e6, (8, "index"): 447.0e6}),
+              "e29ca665962e34d0", {(1, "cost"): 36.7e6, (8, "cost"): 445.1e6,
+                                   (1, "index"): 36.7e6, (8, "index"): 445.1e6}),
 }
 
 
@@ -332,7 +332,11 @@ def run_ours(args):
     }
     ev_t = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = {"fp64": nsub + 1 + 3 * nsub, "mixed": nsub + 2 + 3 * nsub}
+    # kernels of one trace call: FP64 cost-ordered = express select + rank +
+    # persistent + tail; FP64 index order = persistent + tail; mixed = FP32 +
+    # FP64 pass + tail.  A pipelined run of K steps: one sampling launch and
+    # three binning launches per star-step, plus one trace call.
+    trace_launches = {"fp64": 4 if args.claim_order == "cost" else 2, "mixed": 3}
 
     def step(prec, uin=None):
         ctr.zero_()
@@ -515,7 +519,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
-        "gpu_launches": launches[head] * K,
+        "gpu_launches": 4 * nsub * K + trace_launches[head],
         "clocks": clk,
     }
     print(json.dumps(line, default=_plain))
