@@ -4,6 +4,7 @@
     python -m paper_2309_08655_gb300.profile_case --mode backward --n 65536
     python -m paper_2309_08655_gb300.profile_case --mode adjoint --n 4096
     python -m paper_2309_08655_gb300.profile_case --config config1 --rotating --n 65536
+    python -m paper_2309_08655_gb300.profile_case --config config1 --claim-order cost --n 65536
 
 Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
 them once in the requested precision (one persistent trace launch, after one
@@ -38,6 +39,7 @@ def main():
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
     ap.add_argument("--mode", choices=["forward", "backward", "adjoint"], default="forward")
     ap.add_argument("--rotating", action="store_true")
+    ap.add_argument("--claim-order", choices=["index", "cost"], default="index")
     a = ap.parse_args()
     build()
     dev = torch.device("cuda:0")
@@ -59,7 +61,8 @@ def main():
     rt.rt_sample_conversion_surface(star, a.n, u, st, w, s)
     prec = rt.PREC_FP64 if a.precision == "fp64" else rt.PREC_MIXED
     rtol = a.rtol if a.rtol is not None else (1e-10 if prec == rt.PREC_FP64 else 1e-8)
-    opts = rt.make_opts(rtol=rtol, precision=prec)
+    opts = rt.make_opts(rtol=rtol, precision=prec,
+                        claim_order=rt.CLAIM_COST if a.claim_order == "cost" else rt.CLAIM_INDEX)
     st0, s0 = st.clone(), s.clone()
     rt.rt_trace_forward(star, a.n, st0, s0, opts=opts)          # warm-up
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
