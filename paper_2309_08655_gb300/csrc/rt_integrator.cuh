@@ -126,8 +126,47 @@ struct NoHook {
                                             double) {}
 };
 
+// The last th in [0, 1] on the non-negative side of side_val, given
+// side_val(0) = flo >= 0 > fhi = side_val(1): Illinois (regula falsi that
+// halves the retained end's value), with a bisection step whenever the
+// bracket did not halve over two steps, run to the last representable th.
+// Returns lo (side_val >= 0); *hi_out the first th past it.  Used for the
+// null-cone crossing, where a step of a ray guided along the cone can hold
+// more than one sign change and the derivative-free search keeps the choice
+// among them a smooth function of the ray (the adjoint and finite differences
+// agree only then).
+template <class S>
+__device__ __forceinline__ double last_nonneg_illinois(S& side_val, double flo, double fhi,
+                                                       double* hi_out) {
+  double lo = 0.0, hi = 1.0;
+  int last = 0;
+  double width = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = (lo * fhi - hi * flo) / (fhi - flo);
+    if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (it & 1) width = hi - lo;
+    const double fm = side_val(mid);
+    if (fm >= 0.0) {
+      lo = mid;
+      flo = fm;
+      if (last > 0) fhi *= 0.5;
+      last = 1;
+    } else {
+      hi = mid;
+      fhi = fm;
+      if (last < 0) flo *= 0.5;
+      last = -1;
+    }
+  }
+  *hi_out = hi;
+  return lo;
+}
+
 // The last th in [0, 1] on the non-negative side of f, given f(0) = flo >= 0 >
-// fhi = f(1), with fd(th, &df) returning f(th) and df/dth: Newton from the
+// fhi = f(1), f monotone there, with fd(th, &df) returning f(th) and df/dth
+// (the escape through r = r_out): Newton from the
 // regula-falsi point, bisection whenever a Newton step leaves the bracket;
 // once the Newton correction is within a few ulps the bracket is closed by
 // stepping one double at a time, so that lo and hi end adjacent -- the same
@@ -240,27 +279,25 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
       r5[i] = h * (DP::d1 * k1[i] + DP::d3 * k3[i] + DP::d4 * k4[i] + DP::d5 * k5[i] +
                    DP::d6 * k6[i] + DP::d7 * k7[i]);
     }
-    // largest th with the start side on the continuous extension, on
-    // s(th) = sig (3 z (m.x) - m_z |x|^2), whose sign is the side, bracketed on
-    // [0, 1], to the last representable th
+    // largest th with the start side on the continuous extension: Illinois
+    // (regula falsi with halving) on s(th) = sig (3 z (m.x) - m_z |x|^2), whose
+    // sign is the side, bracketed on [0, 1]; a bisection step whenever the
+    // bracket did not halve, to the last representable th
     const double sgn = L.c.sig;
-    auto side_val = [&](double th, double* ds) {
-      double xd[3], dd[3];
+    auto side_val = [&](double th) {
+      double xd[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) xd[i] = dense_d(th, y[i], r2[i], r3[i], r4[i], r5[i], &dd[i]);
+      for (int i = 0; i < 3; ++i)
+        xd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
       const double mx = L.c.m0 * xd[0] + L.c.m1 * xd[1] + L.c.m2 * xd[2];
       const double rr = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
-      const double mdx = L.c.m0 * dd[0] + L.c.m1 * dd[1] + L.c.m2 * dd[2];
-      const double xdx = xd[0] * dd[0] + xd[1] * dd[1] + xd[2] * dd[2];
-      *ds = sgn * (3.0 * (dd[2] * mx + xd[2] * mdx) - 2.0 * L.c.m2 * xdx);
       return sgn * (3.0 * xd[2] * mx - L.c.m2 * rr);
     };
-    double dsink;
-    double flo = side_val(0.0, &dsink), fhi = side_val(1.0, &dsink);
+    double flo = side_val(0.0), fhi = side_val(1.0);
     if (!(flo >= 0.0)) flo = 0.0;                  // the start is on its own side
     if (!(fhi < 0.0)) fhi = -1e-300;
     double hi;
-    const double lo = last_nonneg(side_val, flo, fhi, &hi);
+    const double lo = last_nonneg_illinois(side_val, flo, fhi, &hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;             // already at the cone: switch here

@@ -216,28 +216,40 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
                           DP::d7 * K7);
   if (en <= 1.0 && gj && !L.switching &&
       L.c.sig * gj_side<double>(L.c.m0, L.c.m1, L.c.m2, ynf[0], ynf[1], ynf[2]) < 0.0) {
-    // the side function along the continuous extension, to the last
-    // representable th (last_nonneg, as advance())
+    // Illinois on the side function along the continuous extension
     const double sgn = L.c.sig;
-    auto side_val = [&](double th, double* ds) {
-      double dc;
-      const double vc = dense_d(th, y, r2c, r3c, r4c, r5c, &dc);
-      double xd[6], dd[6];
-      gather6(gm, base, vc, xd);
-      gather6(gm, base, dc, dd);
+    auto side_val = [&](double th) {
+      double xd[6];
+      gather6(gm, base, y + th * (r2c + (1.0 - th) * (r3c + th * (r4c + (1.0 - th) * r5c))), xd);
       const double mx = L.c.m0 * xd[0] + L.c.m1 * xd[1] + L.c.m2 * xd[2];
       const double rr = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
-      const double mdx = L.c.m0 * dd[0] + L.c.m1 * dd[1] + L.c.m2 * dd[2];
-      const double xdx = xd[0] * dd[0] + xd[1] * dd[1] + xd[2] * dd[2];
-      *ds = sgn * (3.0 * (dd[2] * mx + xd[2] * mdx) - 2.0 * L.c.m2 * xdx);
       return sgn * (3.0 * xd[2] * mx - L.c.m2 * rr);
     };
-    double dsink;
-    double flo = side_val(0.0, &dsink), fhi = side_val(1.0, &dsink);
+    double lo = 0.0, hi = 1.0;
+    double flo = side_val(0.0), fhi = side_val(1.0);
     if (!(flo >= 0.0)) flo = 0.0;
     if (!(fhi < 0.0)) fhi = -1e-300;
-    double hi;
-    const double lo = last_nonneg(side_val, flo, fhi, &hi);
+    int last = 0;
+    double width = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double mid = (lo * fhi - hi * flo) / (fhi - flo);
+      if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
+      if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (it & 1) width = hi - lo;
+      const double fm = side_val(mid);
+      if (fm >= 0.0) {
+        lo = mid;
+        flo = fm;
+        if (last > 0) fhi *= 0.5;
+        last = 1;
+      } else {
+        hi = mid;
+        fhi = fm;
+        if (last < 0) flo *= 0.5;
+        last = -1;
+      }
+    }
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;

@@ -219,7 +219,7 @@ __device__ int advance_rot(const TraceParams& p, RotLane& L) {
   const bool gj = (L.c.plasma == PLASMA_GJ);
   if (en <= 1.0 && gj && !L.switching && L.c.sig * side_at(L, yn) < 0.0) {
     // the step crossed the turning null cone: the largest th whose point (x,
-    // at its own t) is on the start side, on the continuous
+    // at its own t) is on the start side, by Illinois on the continuous
     // extension; then redo the step to end just past it
     double r2[8], r3[8], r4[8], r5[8];
 #pragma unroll
@@ -231,28 +231,21 @@ __device__ int advance_rot(const TraceParams& p, RotLane& L) {
                    DP::d6 * k6[i] + DP::d7 * k7[i]);
     }
     const double sgn = L.c.sig;
-    auto side_val = [&](double th, double* ds) {
-      double yd[7], dd[7];
-#pragma unroll
-      for (int i = 0; i < 7; ++i) yd[i] = dense_d(th, y[i], r2[i], r3[i], r4[i], r5[i], &dd[i]);
+    auto side_val = [&](double th) {
+      double yd[8];
+      dense(th, yd, r2, r3, r4, r5, 8);
       double sp, cp;
       sincos(L.psi0 + L.Om * yd[6], &sp, &cp);
       const double m0 = L.sin_tm * cp, m1 = L.sin_tm * sp, m2 = L.c.m2;
-      // the axis turns with the point's own t: dm/dth = Omega dt/dth (-m1, m0, 0)
-      const double w = L.Om * dd[6];
       const double mx = m0 * yd[0] + m1 * yd[1] + m2 * yd[2];
       const double rr = yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2];
-      const double dmx = m0 * dd[0] + m1 * dd[1] + m2 * dd[2] + w * (m0 * yd[1] - m1 * yd[0]);
-      const double xdx = yd[0] * dd[0] + yd[1] * dd[1] + yd[2] * dd[2];
-      *ds = sgn * (3.0 * (dd[2] * mx + yd[2] * dmx) - 2.0 * m2 * xdx);
       return sgn * (3.0 * yd[2] * mx - m2 * rr);
     };
-    double dsink;
-    double flo = side_val(0.0, &dsink), fhi = side_val(1.0, &dsink);
+    double flo = side_val(0.0), fhi = side_val(1.0);
     if (!(flo >= 0.0)) flo = 0.0;
     if (!(fhi < 0.0)) fhi = -1e-300;
     double hi;
-    const double lo = last_nonneg(side_val, flo, fhi, &hi);
+    const double lo = last_nonneg_illinois(side_val, flo, fhi, &hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;
