@@ -130,14 +130,10 @@ struct NoHook {
 // side_val(0) = flo >= 0 > fhi = side_val(1): Illinois (regula falsi that
 // halves the retained end's value), with a bisection step whenever the
 // bracket did not halve over two steps, run to the last representable th.
-// Returns lo (side_val >= 0); *hi_out the first th past it.  Used for the
-// null-cone crossing, where a step of a ray guided along the cone can hold
-// more than one sign change and the derivative-free search keeps the choice
-// among them a smooth function of the ray (the adjoint and finite differences
-// agree only then).
+// Returns lo (side_val >= 0); *hi_out the first th past it.
 template <class S>
-__device__ __forceinline__ double last_nonneg_illinois(S& side_val, double flo, double fhi,
-                                                       double* hi_out) {
+__device__ __forceinline__ double last_nonneg(S& side_val, double flo, double fhi,
+                                              double* hi_out) {
   double lo = 0.0, hi = 1.0;
   int last = 0;
   double width = 1.0;
@@ -162,48 +158,6 @@ __device__ __forceinline__ double last_nonneg_illinois(S& side_val, double flo, 
   }
   *hi_out = hi;
   return lo;
-}
-
-// The last th in [0, 1] on the non-negative side of f, given f(0) = flo >= 0 >
-// fhi = f(1), f monotone there, with fd(th, &df) returning f(th) and df/dth
-// (the escape through r = r_out): Newton from the
-// regula-falsi point, bisection whenever a Newton step leaves the bracket;
-// once the Newton correction is within a few ulps the bracket is closed by
-// stepping one double at a time, so that lo and hi end adjacent -- the same
-// pair as bisection to the last representable th, in about a third of the
-// evaluations of a derivative-free search.  Returns lo (f >= 0); *hi_out the
-// first th past it.
-template <class S>
-__device__ __forceinline__ double last_nonneg(S& fd, double flo, double fhi, double* hi_out) {
-  double lo = 0.0, hi = 1.0;
-  double x = flo / (flo - fhi);
-  for (int it = 0; it < 200; ++it) {
-    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-    if (x <= lo || x >= hi) break;            // lo and hi are adjacent doubles
-    double df;
-    const double f = fd(x, &df);
-    if (f >= 0.0) lo = x; else hi = x;
-    const double dx = f / df;
-    if (fabs(dx) <= 4.0 * 2.220446049250313e-16 * x) {
-      x = (f >= 0.0) ? nextafter(x, 2.0) : nextafter(x, -1.0);   // converged: close
-      continue;
-    }
-    x -= dx;                                  // (bisection at the loop head if outside)
-  }
-  *hi_out = hi;
-  return lo;
-}
-
-// Point and derivative of the continuous extension of one component at th:
-// y + th (r2 + (1 - th) (r3 + th (r4 + (1 - th) r5))).
-__device__ __forceinline__ double dense_d(double th, double y, double r2, double r3, double r4,
-                                          double r5, double* d) {
-  const double u = 1.0 - th;
-  const double C = r4 + u * r5;
-  const double B = r3 + th * C;
-  const double A = r2 + u * B;
-  *d = A + th * (u * (C - th * r5) - B);
-  return y + th * A;
 }
 
 // One attempted Dormand-Prince step.  Returns -1 to continue, else the final
@@ -297,7 +251,7 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
     if (!(flo >= 0.0)) flo = 0.0;                  // the start is on its own side
     if (!(fhi < 0.0)) fhi = -1e-300;
     double hi;
-    const double lo = last_nonneg_illinois(side_val, flo, fhi, &hi);
+    const double lo = last_nonneg(side_val, flo, fhi, &hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;             // already at the cone: switch here
@@ -326,14 +280,14 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
                      DP::d6 * k6[i] + DP::d7 * k7[i]);
         t[i] = r2;
       }
-      // r_out^2 - |x(th)|^2 changes sign on [0, 1]: to the last
-      // representable th (the root to rounding)
+      // r_out^2 - |x(th)|^2 changes sign on [0, 1]: Illinois to the last
+      // representable th (the root to rounding, in ~10 evaluations)
       const double ro2 = p.r_out * p.r_out;
-      auto inside = [&](double th, double* df) {
-        double xd[3], dd[3];
+      auto inside = [&](double th) {
+        double xd[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) xd[i] = dense_d(th, y[i], t[i], r3[i], r4[i], r5[i], &dd[i]);
-        *df = -2.0 * (xd[0] * dd[0] + xd[1] * dd[1] + xd[2] * dd[2]);
+        for (int i = 0; i < 3; ++i)
+          xd[i] = y[i] + th * (t[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
         return ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
       };
       double flo = ro2 - (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);

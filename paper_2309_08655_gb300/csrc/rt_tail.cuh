@@ -266,15 +266,12 @@ __device__ int advance_group(const TraceParams& p, GLane& L, int cc, unsigned gm
     ++L.na;
     const double rnew2 = ynf[0] * ynf[0] + ynf[1] * ynf[1] + ynf[2] * ynf[2];
     if (rnew2 >= p.r_out * p.r_out) {
-      // |x(th)| = r_out on the continuous extension, as advance()
+      // |x(th)| = r_out on the continuous extension: Illinois, as advance()
       const double ro2 = p.r_out * p.r_out;
-      auto inside = [&](double th, double* df) {
-        double dc;
-        const double vc = dense_d(th, y, r2c, r3c, r4c, r5c, &dc);
-        double xd[6], dd[6];
-        gather6(gm, base, vc, xd);
-        gather6(gm, base, dc, dd);
-        *df = -2.0 * (xd[0] * dd[0] + xd[1] * dd[1] + xd[2] * dd[2]);
+      auto inside = [&](double th) {
+        double xd[6];
+        gather6(gm, base, y + th * (r2c + (1.0 - th) * (r3c + th * (r4c + (1.0 - th) * r5c))),
+                xd);
         return ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
       };
       double flo = ro2 - (yfull[0] * yfull[0] + yfull[1] * yfull[1] + yfull[2] * yfull[2]);

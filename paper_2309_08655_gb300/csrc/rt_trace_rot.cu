@@ -245,7 +245,7 @@ __device__ int advance_rot(const TraceParams& p, RotLane& L) {
     if (!(flo >= 0.0)) flo = 0.0;
     if (!(fhi < 0.0)) fhi = -1e-300;
     double hi;
-    const double lo = last_nonneg_illinois(side_val, flo, fhi, &hi);
+    const double lo = last_nonneg(side_val, flo, fhi, &hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION) {
       L.c.sig = -L.c.sig;
@@ -272,11 +272,9 @@ __device__ int advance_rot(const TraceParams& p, RotLane& L) {
                      DP::d6 * k6[i] + DP::d7 * k7[i]);
       }
       const double ro2 = p.r_out * p.r_out;
-      auto inside = [&](double th, double* df) {
-        double xd[3], dd[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) xd[i] = dense_d(th, y[i], r2[i], r3[i], r4[i], r5[i], &dd[i]);
-        *df = -2.0 * (xd[0] * dd[0] + xd[1] * dd[1] + xd[2] * dd[2]);
+      auto inside = [&](double th) {
+        double xd[3];
+        dense(th, xd, r2, r3, r4, r5, 3);
         return ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
       };
       double flo = ro2 - (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
