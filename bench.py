@@ -60,10 +60,12 @@ PEAK_FP32 = SMS * 256 * CLK
 # once they change).
 TRAFFIC = {
     # (steps per launch, claim order) -> DRAM bytes of the trace call
-    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu'), "da695116b94dbdc6",
+    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh'),
+             "86200d81649a5107",
              {(1, "cost"): 54.1e6, (8, "cost"): 920.2e6}),
-    "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_trace_mixed.cu'),
-              "e29ca665962e34d0", {(1, "cost"): 36.7e6, (8, "cost"): 445.1e6,
+    "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh',
+               'rt_trace_mixed.cu'),
+              "9a6346c421136f17", {(1, "cost"): 36.7e6, (8, "cost"): 445.1e6,
                                    (1, "index"): 36.7e6, (8, "index"): 445.1e6}),
 }
 
