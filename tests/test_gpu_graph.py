@@ -25,8 +25,10 @@ def _built():
     assert torch.cuda.is_available()
 
 
-def _setup(prec=rt.PREC_FP64, n_per=1024):
+def _setup(prec=rt.PREC_FP64, n_per=1024, rotation=rt.ROTATION_SNAPSHOT):
     kws = I.stars_config1()[:6]          # masses 4e-4 .. 1.4e-6 eV, some surfaces empty
+    for k in kws:
+        k.update(rotation=rotation)
     counts = [n_per, 3 * n_per // 2, n_per // 2, n_per, 7, n_per]   # uneven, one tiny
     stars = [rt.Star(rt.make_params(**k)) for k in kws]
     b = rt.Batch(stars, counts)
@@ -53,10 +55,15 @@ def _direct(b, u, B, opts):
     return {k: v.cpu().numpy().copy() for k, v in B.items()}
 
 
-@pytest.mark.parametrize("prec", [rt.PREC_FP64, rt.PREC_MIXED])
-def test_graph_replay_equals_direct_calls(prec):
-    b, stars, u, B, rtol = _setup(prec)
-    opts = rt.make_opts(rtol=rtol, precision=prec)
+@pytest.mark.parametrize("case", ["fp64", "mixed", "fp64_cost_order", "rotating"])
+def test_graph_replay_equals_direct_calls(case):
+    # cost order: the express lane's selection and ranking are captured too;
+    # rotating: a batch of rigidly rotating magnetospheres (its own kernel)
+    prec = rt.PREC_MIXED if case == "mixed" else rt.PREC_FP64
+    rot = rt.ROTATION_RIGID if case == "rotating" else rt.ROTATION_SNAPSHOT
+    b, stars, u, B, rtol = _setup(prec, rotation=rot)
+    opts = rt.make_opts(rtol=rtol, precision=prec,
+                        claim_order=rt.CLAIM_COST if case == "fp64_cost_order" else rt.CLAIM_INDEX)
     ref = _direct(b, u, B, opts)
     for v in B.values():
         v.fill_(0)
