@@ -302,6 +302,7 @@ static void set_express(rtk::TraceParams& p) {
   p.xrec = (double*)(x + 64 + rtk::XSLOTS * sizeof(int) +
                      (size_t)rtk::XCAP * 2 * sizeof(unsigned long long));
   p.xcap = rtk::XCAP;
+  p.xpark = (p.n >= rtk::XPARK_MIN_RAYS) ? 1 : 0;
 }
 
 static rt_status check_opts(const rt_trace_opts* o) {

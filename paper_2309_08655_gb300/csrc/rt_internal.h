@@ -48,7 +48,12 @@ struct TraceParams {
   int* xslot = nullptr;                 // per-SM arrival counter (XSLOTS ints)
   unsigned long long* xcand = nullptr;   // xcap (key, ray) pairs
   int64_t xcap = 0;
+  // with the express lane the bulk parks its last rays for the tail launch only
+  // in launches long enough that the express lane ends before the bulk (the
+  // tail launch waits for both); shorter ones keep them one lane per ray
+  int xpark = 0;
 };
+constexpr int64_t XPARK_MIN_RAYS = (int64_t)4 << 20;
 constexpr int COST_BUCKETS = 3;
 constexpr int PARKREC = 14;   // y[6], h, h_resume, sig, flags, na, nr, ray, lambda
 constexpr int PARK_LIVE_MAX = 5;

@@ -623,7 +623,7 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
   TraceParams q = p;
   if (p.xrec) {
     // express lane: select and rank the bucket-0 rays; the persistent launch
-    // then traces the rest one lane per ray without parking
+    // then traces the rest one lane per ray, parking only when xpark is set
     e = cudaMemsetAsync(p.xcount, 0, 64 + XSLOTS * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     const int64_t sel_grid = (p.n + 255) / 256 < (int64_t)nsm * 8 ? (p.n + 255) / 256
@@ -634,7 +634,7 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
     express_rank_kernel<<<(unsigned)((XCAP + 127) / 128), 128, 0, stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    q.park = nullptr;
+    if (!p.xpark) q.park = nullptr;
   }
   trace_fp64_kernel<<<(unsigned)grid, block, 0, stream>>>(q);
   e = cudaGetLastError();
