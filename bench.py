@@ -61,12 +61,12 @@ PEAK_FP32 = SMS * 256 * CLK
 TRAFFIC = {
     # (steps per launch, claim order) -> DRAM bytes of the trace call
     "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh'),
-             "86200d81649a5107",
-             {(1, "cost"): 54.1e6, (8, "cost"): 920.2e6}),
+             "0e3654f642f58b55",
+             {(1, "cost"): 54.1e6, (8, "cost"): 925.5e6}),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh',
                'rt_trace_mixed.cu'),
-              "9a6346c421136f17", {(1, "cost"): 36.7e6, (8, "cost"): 445.1e6,
-                                   (1, "index"): 36.7e6, (8, "index"): 445.1e6}),
+              "077aa850c59f317d", {(1, "cost"): 36.7e6, (8, "cost"): 445.9e6,
+                                   (1, "index"): 36.7e6, (8, "index"): 445.9e6}),
 }
 
 

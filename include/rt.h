@@ -167,9 +167,10 @@ typedef struct {
  *                     rays within 1e-3 rad (up to 8192 per call, nearest first)
  *                     are traced six lanes per ray from the start on a few SMs
  *                     of their own (the express lane), and the others one lane
- *                     per ray without parking; results agree with index order
- *                     to rounding and are bitwise reproducible (unless more
- *                     than 8192 rays qualify).  Not with images in a batch.
+ *                     per ray (parking their last rays only in calls of 4M rays
+ *                     or more); results agree with index order to rounding and
+ *                     are bitwise reproducible below 4M rays (unless more than
+ *                     8192 rays qualify).  Not with images in a batch.
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),

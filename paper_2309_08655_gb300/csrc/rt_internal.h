@@ -42,7 +42,8 @@ struct TraceParams {
   // bucket 0, ranked by their distance from the null cone, become park records
   // that six-lane groups of the first block on each of the first SMs continue
   // from the start of the launch, while the other blocks trace the rest one
-  // lane per ray (without parking); the tail launch takes any record left over
+  // lane per ray (parking only when xpark is set); the tail launch takes any
+  // record left over
   double* xrec = nullptr;               // xcap records of PARKREC doubles
   unsigned long long* xcount = nullptr;  // [0] candidates found, [1] next record
   int* xslot = nullptr;                 // per-SM arrival counter (XSLOTS ints)
