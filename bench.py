@@ -41,14 +41,37 @@ if ROOT not in sys.path:
 METRIC = "ray-steps/s & rays/s at 1e-6 rel. flux err; mixed vs FP64; adjoint/forward ratio"
 UNIT = "ray-steps/s"
 NBINS = (64, 32, 128)
-# Nominal GB300 ALU peaks derived from the unit counts and the maximum clock:
-# 152 SMs x 2070 MHz; FP64 4 flop/clk/SM (1.26 TFLOP/s, the nominal GB300
-# FP64 rate); FP32 128 lanes x 2 flop/clk/SM (80.5 TFLOP/s).
+# ALU peaks: measured at the start of every run by rt_measure_alu_peak
+# (independent FMA chains on every SM, CUDA events), which replaces these
+# nominal values derived from the unit counts and the maximum clock (152 SMs x
+# 2070 MHz; FP64 4 flop/clk/SM = 1.26 TFLOP/s; FP32 128 lanes x 2 flop/clk/SM
+# = 80.5 TFLOP/s); both are reported.
 SMS, CLK = 152, 2.070e9
 FP64_KERNELS = "trace_fp64_kernel + tail_fp64_kernel (one trace call)"
 LC_CUT_KM = 0.0      # backward IR cut on the conversion length (Sec. 4.4): none
-PEAK_FP64 = SMS * 4 * CLK
-PEAK_FP32 = SMS * 256 * CLK
+NOMINAL = {"fp64": SMS * 4 * CLK, "fp32": SMS * 256 * CLK}
+PEAK = dict(NOMINAL)
+PEAK_SOURCE = {"fp64": "nominal: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+               "fp32": "nominal: 152 SMs x 256 FP32 flop/clk x 2070 MHz"}
+
+
+def _measure_peaks(rt, stream):
+    """Measured FP64 / FP32 multiply-add rates of this GPU, with the SM clock
+    sampled while they run; they become the roofline denominators."""
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    m = rt.rt_measure_alu_peak(stream=stream)
+    c = clk.stop()
+    PEAK["fp64"], PEAK["fp32"] = m["fp64_flops"], m["fp32_flops"]
+    for k, kk in (("fp64", "fp64_ms"), ("fp32", "fp32_ms")):
+        PEAK_SOURCE[k] = (f"measured on this GPU by rt_measure_alu_peak (8 independent FMA "
+                          f"chains per thread, every SM, one {m[kk]:.0f} ms launch timed with "
+                          f"CUDA events; SM clock median {c['sm_mhz']} MHz); nominal "
+                          f"{NOMINAL[k] / 1e12:.2f} TFLOP/s")
+    return {"fp64_tflops": m["fp64_flops"] / 1e12, "fp32_tflops": m["fp32_flops"] / 1e12,
+            "fp64_ms": m["fp64_ms"], "fp32_ms": m["fp32_ms"], "clocks": c,
+            "nominal_fp64_tflops": NOMINAL["fp64"] / 1e12,
+            "nominal_fp32_tflops": NOMINAL["fp32"] / 1e12}
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace call
 # of this workload, one step per launch (1) and eight steps per launch (8)
@@ -184,10 +207,14 @@ class _Pipelined:
     launch per sub-batch, one persistent trace launch, one binning pass per
     sub-batch."""
 
-    def __init__(self, rt, stars, nper, nsub, K, u, dev, stream, nbins, cfg):
+    def __init__(self, rt, stars, nper, nsub, K, u, dev, stream, nbins, cfg, ws=1):
         import torch
         self.rt, self.stream, self.nbins, self.cfg = rt, stream, nbins, cfg
-        self.batch = rt.Batch(list(stars) * K, [nper] * (nsub * K))
+        self.stars = list(stars) * K
+        self.batch = rt.Batch(self.stars, [nper] * (nsub * K))
+        self.ws, self.nper = ws, nper
+        if ws > 1:        # this rank's share of every star's rays (see run_ours)
+            rt.rt_batch_set_norm(self.batch, [ws * nper] * (nsub * K))
         N = nsub * nper
         self.u = u.repeat(1, K).contiguous()
         f64 = torch.float64
@@ -199,6 +226,8 @@ class _Pipelined:
         self.oor = torch.empty(K * nsub, dtype=f64, device=dev)
         self.ctr = torch.zeros(8, dtype=torch.int64, device=dev)
         self.ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        self.acc = (torch.empty((K * nsub, rt.bin_acc_entries(*nbins)), dtype=torch.int64,
+                                device=dev) if ws > 1 else None)
 
     def run(self, opts):
         rt, cs = self.rt, self.stream
@@ -207,8 +236,16 @@ class _Pipelined:
         self.ev[0].record(cs)
         rt.rt_trace_batch(self.batch, self.st, self.s, None, None, self.ctr, opts, stream=cs)
         self.ev[1].record(cs)
-        rt.rt_bin_batch(self.batch, self.st, self.w, self.s, *self.nbins, self.cfg["nu_lo"],
-                        self.cfg["nu_hi"], self.hist, self.oor, stream=cs)
+        if self.ws > 1:
+            from paper_2309_08655_gb300 import shard
+            ns = len(self.stars)
+            shard.bin_sharded(rt, self.stars, [j * self.nper for j in range(ns + 1)],
+                              self.batch.N, [self.ws * self.nper] * ns, self.st, self.w, self.s,
+                              self.nbins, self.cfg["nu_lo"], self.cfg["nu_hi"], self.acc,
+                              self.hist, self.oor, stream=cs)
+        else:
+            rt.rt_bin_batch(self.batch, self.st, self.w, self.s, *self.nbins, self.cfg["nu_lo"],
+                            self.cfg["nu_hi"], self.hist, self.oor, stream=cs)
 
 
 def _workload():
@@ -312,11 +349,19 @@ def run_ours(args):
     nth, nph, nnu = NBINS
     stars = [rt.Star(rt.make_params(**kw)) for kw in stars_kw]
     batch = rt.Batch(stars, [nper] * nsub)
-    # weak scaling: every rank traces its own seeded copy of the workload
-    seeds = shard.rank_seeds(cfg["seed"], nsub, rank)
-    u_host = torch.from_numpy(np.ascontiguousarray(
-        np.concatenate([I.sample_uniforms(sd, nper) for sd in seeds], axis=1))).pin_memory()
+    # weak scaling: on N ranks every star carries N x 65536 rays, rank r the
+    # contiguous range r (its uniforms, the whole workload's weight
+    # normalisation); the per-star spectra are combined exactly at the end of
+    # each step (int64 all-reduce of the fixed-point sums)
+    first, _ = shard.ray_range(ws * nper, ws, rank)
+    seeds = [cfg["seed"] * 1000 + j for j in range(nsub)]
+    u_host = torch.from_numpy(np.ascontiguousarray(np.concatenate(
+        [I.sample_uniforms(sd, nper, first) for sd in seeds], axis=1))).pin_memory()
     u = u_host.to(dev)
+    if ws > 1:
+        rt.rt_batch_set_norm(batch, [ws * nper] * nsub)
+    acc = torch.empty((nsub, rt.bin_acc_entries(*NBINS)), dtype=torch.int64, device=dev)
+    offsets = [j * nper for j in range(nsub + 1)]
     st = torch.empty((8, N), dtype=torch.float64, device=dev)
     w = torch.empty(N, dtype=torch.float64, device=dev)
     s = torch.empty(N, dtype=torch.uint8, device=dev)
@@ -346,11 +391,16 @@ def run_ours(args):
         ev_t[0].record(stream)
         rt.rt_trace_batch(batch, st, s, None, None, ctr, opts[prec], stream=stream)
         ev_t[1].record(stream)
-        rt.rt_bin_batch(batch, st, w, s, nth, nph, nnu, cfg["nu_lo"], cfg["nu_hi"], hist, oor,
-                        stream=stream)
+        if ws > 1:
+            shard.bin_sharded(rt, stars, offsets, N, [ws * nper] * nsub, st, w, s, NBINS,
+                              cfg["nu_lo"], cfg["nu_hi"], acc, hist, oor, stream=stream)
+        else:
+            rt.rt_bin_batch(batch, st, w, s, nth, nph, nnu, cfg["nu_lo"], cfg["nu_hi"], hist,
+                            oor, stream=stream)
 
     res = {}
     fl = _flops_per_attempt(rt)
+    peaks = _measure_peaks(rt, stream)
     clocks = Clocks(local)
     clocks.start()
     for prec in ("fp64", "mixed"):
@@ -381,16 +431,18 @@ def run_ours(args):
         if prec == "fp64":
             flops = attempts * fl[1] + rays_launch * fl[2]
             roof = {"kernel": FP64_KERNELS, "bound": "alu", "achieved": flops / t_tr / 1e12,
-                    "peak": PEAK_FP64 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP64, "traffic": _traffic("fp64", 1, args.claim_order),
-                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz"}
+                    "peak": PEAK["fp64"] / 1e12, "unit": "TFLOP/s",
+                    "frac": flops / t_tr / PEAK["fp64"],
+                    "traffic": _traffic("fp64", 1, args.claim_order),
+                    "peak_source": PEAK_SOURCE["fp64"]}
         else:
             flops = (attempts - promoted_attempts) * fl[1] + rays_launch * fl[2]
             roof = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)",
                     "bound": "alu", "achieved": flops / t_tr / 1e12,
-                    "peak": PEAK_FP32 / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK_FP32, "traffic": _traffic("mixed", 1, args.claim_order),
-                    "peak_source": "derived: 152 SMs x 256 FP32 flop/clk x 2070 MHz",
+                    "peak": PEAK["fp32"] / 1e12, "unit": "TFLOP/s",
+                    "frac": flops / t_tr / PEAK["fp32"],
+                    "traffic": _traffic("mixed", 1, args.claim_order),
+                    "peak_source": PEAK_SOURCE["fp32"],
                     "promoted_rays_per_step": c_sum[4] / args.steps,
                     "promoted_fp64_attempts_per_step": promoted_attempts}
         roof.update({"flops_per_attempt": fl[1], "attempts_per_launch": attempts,
@@ -408,7 +460,7 @@ def run_ours(args):
     # earlier ones; the same work per step (rays that finish in the six-lane
     # tail kernel may differ from one launch per step by rounding)
     K = min(args.steps, 64)
-    P = _Pipelined(rt, stars, nper, nsub, K, u, dev, stream, NBINS, cfg)
+    P = _Pipelined(rt, stars, nper, nsub, K, u, dev, stream, NBINS, cfg, ws)
     for prec in ("fp64", "mixed"):
         P.run(opts[prec])                   # untimed pass of this path
         torch.cuda.synchronize()
@@ -427,10 +479,10 @@ def run_ours(args):
         attempts = c[0] + c[1]
         if prec == "fp64":
             flops = attempts * fl[1] + c[2] * fl[2]
-            peak, kern = PEAK_FP64, FP64_KERNELS
+            peak, kern = PEAK["fp64"], FP64_KERNELS
         else:
             flops = (attempts - c[5]) * fl[1] + c[2] * fl[2]
-            peak, kern = PEAK_FP32, "trace_mixed_kernel (+ FP64 pass for promoted rays)"
+            peak, kern = PEAK["fp32"], "trace_mixed_kernel (+ FP64 pass for promoted rays)"
         roof = dict(res[prec]["roofline"])
         roof.update({"kernel": kern, "achieved": flops / t_tr / 1e12, "frac": flops / t_tr / peak,
                      "traffic": _traffic(prec, K, args.claim_order), "attempts_per_launch": attempts,
@@ -451,7 +503,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, h_or = _cpu_baseline(stars_kw, cfg, args.cpu_sample)
-        if h_or is not None:
+        if h_or is not None and ws == 1:
             for p in ("fp64", "mixed"):
                 res[p]["flux_l1_vs_oracle"] = l1(hists[p], h_or)
     # headline: the fastest precision whose binned flux is within 1e-6 (relative
@@ -498,6 +550,10 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "rays_per_step": N, "sub_batches": nsub,
+                   "parallelism": ("single GPU" if ws == 1 else
+                                   f"each star's rays split into {ws} contiguous ranges, one per "
+                                   f"rank; per-star int64 fixed-point spectra all-reduced (MAX "
+                                   f"of the largest weight, then SUM) every step"),
                    "rtol": H["rtol"], "r_out_over_R": cfg["r_out_over_R"],
                    "max_steps": cfg["max_steps"], "bins": list(NBINS), "precision": head,
                    "launch": f"continuous batching: the {K} timed steps' 16 sub-batches each "
@@ -519,6 +575,7 @@ def run_ours(args):
         "twisted_magnetosphere": twisted,
         "rotating_magnetosphere": rotating,
         "cpu_baseline": cpu,
+        "alu_peaks": peaks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": u_host.numel() * 8,
                 "d2h_bytes_per_step": hist.numel() * 8},
         "gpu_launches": 4 * nsub * K + trace_launches[head],
@@ -881,8 +938,8 @@ def _backward_leg(args, dev, stream, fl, rank):
            "ray_steps_per_s": c[0] / t, "accepted_steps": c[0], "rejected_steps": c[1],
            "crossings": c[6], "dP_dOmega_W_per_sr": float(img.sum()),
            "roofline": {"kernel": "backward_kernel", "bound": "alu",
-                        "achieved": (c[0] + c[1]) * fl[1] / t / 1e12, "peak": PEAK_FP64 / 1e12,
-                        "unit": "TFLOP/s", "frac": (c[0] + c[1]) * fl[1] / t / PEAK_FP64,
+                        "achieved": (c[0] + c[1]) * fl[1] / t / 1e12, "peak": PEAK["fp64"] / 1e12,
+                        "unit": "TFLOP/s", "frac": (c[0] + c[1]) * fl[1] / t / PEAK["fp64"],
                         "traffic": None,
                         "note": "integrator flops only; the crossing search is not counted"}}
     # the same image in mixed precision (FP32 stages, rtol 1e-8; FP64 crossing

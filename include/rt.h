@@ -233,6 +233,21 @@ rt_status rt_sample_conversion_surface(const rt_star* star, int64_t n, const dou
                                        void* stream);
 
 /*
+ * rt_sample_conversion_surface_part - rt_sample_conversion_surface for one
+ * part of a larger Monte-Carlo sample: the n samples drawn from d_uniforms
+ * are normalised by n_norm (the samples of the whole workload, >= n) instead
+ * of n.  The weights of contiguous parts sampled by different processes (one
+ * GPU each) are then bitwise those of one call over all n_norm samples.  The
+ * paper's tracers run on computing clusters (Sec. 2.4); this is how one
+ * workload's rays are split across GPUs (with rt_bin_part_*).
+ * RT_EINVAL if n_norm < max(n, 1); otherwise as rt_sample_conversion_surface
+ * (rt_sample_conversion_surface is this call with n_norm = n).
+ */
+rt_status rt_sample_conversion_surface_part(const rt_star* star, int64_t n, int64_t n_norm,
+                                            const double* d_uniforms, double* d_state,
+                                            double* d_weight, uint8_t* d_status, void* stream);
+
+/*
  * rt_trace_forward - integrate Hamilton's equations (Eq. Hamilton) of the
  * strong-field Hamiltonian (Eq. StrongBHam) for every ray whose status is
  * RT_RAY_READY, in place, until escape, capture or a bound (Sec. 2.2).
@@ -280,6 +295,45 @@ rt_status rt_bin_spectrum(const rt_star* star, int64_t n, const double* d_state,
                           const double* d_weight, const uint8_t* d_status, int32_t nth,
                           int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,
                           double* d_sky, double* d_spec, double* d_out_of_range, void* stream);
+
+/*
+ * Sharded binning: rt_bin_spectrum split into its three phases around
+ * caller-owned int64 fixed-point sums, so that the sums of several shards
+ * (processes, one GPU each, holding contiguous ranges of one workload's rays;
+ * Sec. 2.4's cluster parallelisation) combine exactly by integer addition.
+ *   d_acc  device int64 array of RT_BIN_ACC_ENTRIES(nth, nph, nnu) entries:
+ *          [0] bit pattern of the largest escaped weight, [1] out-of-range
+ *          sum, then the nth x nph x nnu histogram, the nth x nph sky map and
+ *          the nnu spectrum, all in units of 2^-e.
+ *   rt_bin_part_max         clears d_acc and sets d_acc[0] to the IEEE-754
+ *                           bit pattern of the largest weight among the n
+ *                           rays' ESCAPED ones (0 if none).  Then reduce
+ *                           d_acc[0] with MAX over the shards (for
+ *                           non-negative doubles int64 order is value order).
+ *   rt_bin_part_accumulate  adds the n rays to d_acc[1 ..] with the scale 2^e
+ *                           that the reduced d_acc[0] and n_total (the rays
+ *                           of all shards, >= n) fix; d_state is
+ *                           RT_STATE_ROWS x ld (row stride ld >= n, e.g. one
+ *                           star's slice of a batch).  Then reduce
+ *                           d_acc[1 ..] with SUM over the shards.
+ *   rt_bin_part_finalize    the float64 outputs of rt_bin_spectrum from the
+ *                           reduced sums (the same n_total).
+ * The outputs are bitwise those of rt_bin_spectrum over the n_total rays of
+ * all shards (one shard with all rays: bitwise rt_bin_spectrum).  The three
+ * calls are asynchronous on stream, allocate nothing, and need device memory
+ * of the current device for every array (RT_EINVAL otherwise).
+ */
+#define RT_BIN_ACC_ENTRIES(nth, nph, nnu) \
+  (2 + (int64_t)(nth) * (nph) * (nnu) + (int64_t)(nth) * (nph) + (int64_t)(nnu))
+rt_status rt_bin_part_max(int64_t n, const double* d_weight, const uint8_t* d_status,
+                          int32_t nth, int32_t nph, int32_t nnu, int64_t* d_acc, void* stream);
+rt_status rt_bin_part_accumulate(const rt_star* star, int64_t n, int64_t ld, int64_t n_total,
+                                 const double* d_state, const double* d_weight,
+                                 const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
+                                 double nu_lo, double nu_hi, int64_t* d_acc, void* stream);
+rt_status rt_bin_part_finalize(int32_t nth, int32_t nph, int32_t nnu, int64_t n_total,
+                               const int64_t* d_acc, double* d_hist, double* d_sky,
+                               double* d_spec, double* d_out_of_range, void* stream);
 
 /*
  * rt_trace_backward - image of the axion-induced radio power on a plane far
@@ -431,6 +485,16 @@ rt_status rt_init_batch(const rt_star* const* stars, int32_t nstars, const int64
 void rt_destroy_batch(rt_batch* batch);
 rt_status rt_sample_batch(rt_batch* batch, const double* d_uniforms, double* d_state,
                           double* d_weight, uint8_t* d_status, void* stream);
+/*
+ * rt_batch_set_norm - host: the weight normalisation of each star's samples
+ *   in rt_sample_batch (and in graphs created afterwards): n_norm[s] >=
+ *   counts[s] samples in place of counts[s], as rt_sample_conversion_surface_part
+ *   does for one star, so that batches holding contiguous parts of one
+ *   workload on different GPUs carry the weights of the whole.  NULL restores
+ *   the counts.  RT_EINVAL if some n_norm[s] < max(counts[s], 1) (the earlier
+ *   setting is kept).
+ */
+rt_status rt_batch_set_norm(rt_batch* batch, const int64_t* n_norm);
 rt_status rt_trace_batch(rt_batch* batch, double* d_state, uint8_t* d_status, int32_t* d_nacc,
                          int32_t* d_nrej, int64_t* d_counters, const rt_trace_opts* opts,
                          void* stream);
@@ -507,9 +571,14 @@ rt_status rt_batch_autotune(rt_batch* batch, const double* d_state, const uint8_
  * fixed-point semantics of rt_bin_spectrum.
  *   Limit: 2 + nth*nph*nnu + nth*nph + nnu <= RT_BIN_NOALLOC_MAX_ENTRIES,
  *   else RT_EINVAL (message in rt_last_error()).
+ *   Checks: params must pass rt_init_star's validation, and every array must
+ *   be device (or managed) memory of the current device; RT_EINVAL
+ *   otherwise, before anything is enqueued.
  *   Set-up: the first call on a device looks up the device address of the
  *   array (cudaGetSymbolAddress, with that device current); make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The address is cached for the life of
+ *   the process: after cudaDeviceReset on a device, do not call this entry
+ *   point on that device again in the same process.
  *   Sharing: every call on a device uses the same array; each call clears
  *   the part it uses (an asynchronous memset on `stream`) and leaves its sums
  *   there afterwards.  Calls that overlap on the GPU (different streams, or
@@ -541,6 +610,22 @@ rt_status rt_count_status(int64_t n, const uint8_t* d_status, int64_t* counts, v
  * unknown model switches.
  */
 rt_status rt_flops_per_step(int32_t dispersion, int32_t plasma, double* out4);
+
+/*
+ * rt_measure_alu_peak - measured FP64 and FP32 CUDA-core throughput of the
+ * current device, the denominators of the roofline fractions (the tracing
+ * kernels are bound by the fused multiply-add pipes; the paper reports no
+ * throughput, Sec. 2.4 names only its CPU clusters).  A kernel in which every
+ * thread runs 8 independent chains x <- x b + c (32 multiply-adds per
+ * iteration) on a grid that fills every SM, one warm-up launch and one launch
+ * timed with CUDA events on stream, first in FP64 (iters64 iterations), then
+ * in FP32 (iters32).
+ *   out4  host: [0] FP64 flop/s, [1] FP32 flop/s (a multiply-add counts 2),
+ *         [2] FP64 kernel ms, [3] FP32 kernel ms
+ * Synchronous; allocates and frees a result buffer of 2 KB per SM.  The rate
+ * follows the SM clock of the moment: sample it alongside.
+ */
+rt_status rt_measure_alu_peak(int64_t iters64, int64_t iters32, double* out4, void* stream);
 
 /* Thread-local message describing the last error of this thread. */
 const char* rt_last_error(void);

@@ -119,6 +119,10 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int)
         L.or_sample.restype = ctypes.c_long
         L.or_sample.argtypes = [dp, ctypes.c_long, dp, dp, dp, u8p, ctypes.c_int]
+        L.or_sample_parts.restype = None
+        L.or_sample_parts.argtypes = [dp, ctypes.c_long, dp, dp, ctypes.c_int]
+        L.or_sample_parts_count.restype = ctypes.c_int
+        L.or_sample_parts_count.argtypes = []
         L.or_trace_forward.restype = None
         L.or_trace_forward.argtypes = [dp, dp, ctypes.c_long, dp, u8p, ip, ip, dp, ctypes.c_int]
         L.or_trace_rk4.restype = None
@@ -182,15 +186,36 @@ def star_vector(**kw) -> np.ndarray:
 
 
 def trace_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, max_steps=100000, lambda_max=0.0,
-               r_capture_over_R=1.0) -> np.ndarray:
+               r_capture_over_R=1.0, crossing_grid=0) -> np.ndarray:
+    """crossing_grid: 0 = the exhaustive backward crossing search; n > 0 = a
+    plain sign test at n points per step (a comparison baseline only)."""
     if atol is None:
         atol = rtol
-    return np.array([rtol, atol, r_out_over_R, max_steps, lambda_max, r_capture_over_R],
-                    dtype=np.float64)
+    return np.array([rtol, atol, r_out_over_R, max_steps, lambda_max, r_capture_over_R,
+                     crossing_grid], dtype=np.float64)
 
 
 def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
+
+
+SAMPLE_PARTS = ["ok", "r", "n0", "n1", "n2", "khat0", "khat1", "khat2", "E", "K2", "wp2",
+                "cos2", "Bmag", "dhdr", "gradh0", "gradh1", "gradh2", "Psi", "W1", "w", "A",
+                "kinf", "omega_inf", "shape"]
+
+
+def sample_parts(star: np.ndarray, u: np.ndarray, nthreads: int | None = None) -> dict:
+    """Intermediate quantities of each sample (scaled units: r in R, E and
+    momenta in m_a, dhdr in m_a / R, gradh = dh/d(x/R) in m_a; Bmag [eV^2],
+    Psi [eV^3], w [W]); 'ok' is 0 for samples without a resonance."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.shape[1]
+    L = lib()
+    k = L.or_sample_parts_count()
+    assert k == len(SAMPLE_PARTS)
+    out = np.zeros((n, k))
+    L.or_sample_parts(_dp(star), n, _dp(u), _dp(out), nthreads or default_threads())
+    return {name: out[:, j] for j, name in enumerate(SAMPLE_PARTS)}
 
 
 def sample(star: np.ndarray, u: np.ndarray, nthreads: int | None = None):

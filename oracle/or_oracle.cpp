@@ -29,11 +29,18 @@ enum {
 };
 
 // Trace options vector layout (shared with the Python wrapper of the oracle).
-enum { TO_RTOL = 0, TO_ATOL, TO_R_OUT, TO_MAX_STEPS, TO_LAMBDA_MAX, TO_R_CAPTURE, TO_COUNT };
+// TO_CROSS_GRID selects the backward crossing search: 0 (default) the
+// exhaustive search; n > 0 the plain sign test at n points per step with no
+// extremum search (a comparison baseline for the tests, never the reference).
+enum {
+  TO_RTOL = 0, TO_ATOL, TO_R_OUT, TO_MAX_STEPS, TO_LAMBDA_MAX, TO_R_CAPTURE, TO_CROSS_GRID,
+  TO_COUNT
+};
 
 struct TraceOpts {
   double rtol, atol, r_out, lambda_max, r_capture;
   long max_steps;
+  int cross_grid;
 };
 
 inline TraceOpts make_opts(const double* t) {
@@ -44,6 +51,7 @@ inline TraceOpts make_opts(const double* t) {
   o.max_steps = (long)t[TO_MAX_STEPS];
   o.lambda_max = t[TO_LAMBDA_MAX];
   o.r_capture = t[TO_R_CAPTURE];
+  o.cross_grid = (int)t[TO_CROSS_GRID];
   return o;
 }
 
@@ -166,8 +174,16 @@ static bool resonance_root(const Star& s, const double m[3], const double n[3],
 // sin^2 th_B E (Eq. ProbIsoCurved with its power of E made dimensionally
 // consistent).  Samples: direction n uniform on the sphere, khat uniform on
 // the sphere, |k_inf| from the Maxwellian, and the resonance root r* along n.
+// Intermediate quantities of one sample (the tests evaluate the paper's
+// uncollapsed Eq. PowerCurved from them).
+enum {
+  PT_OK = 0, PT_R, PT_N, PT_KHAT = PT_N + 3, PT_E = PT_KHAT + 3, PT_K2, PT_WP2, PT_COS2, PT_BMAG,
+  PT_DHDR, PT_GRADH, PT_PSI = PT_GRADH + 3, PT_W1, PT_W, PT_A, PT_KINF, PT_OMEGA, PT_SHAPE,
+  PT_COUNT
+};
+
 static void sample_one(const Star& s, const double u[6], long N, double st[8], double* w,
-                       unsigned char* status) {
+                       unsigned char* status, double* parts = nullptr) {
   using units::PI;
   const double ct = 1.0 - 2.0 * u[0];
   const double stt = std::sqrt(std::fmax(0.0, (1.0 - ct) * (1.0 + ct)));
@@ -243,6 +259,30 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
   const double W1 = vol * mom * tdil * fa_over_pdf / dhdr_eV * (4.0 * PI) * (4.0 * PI);
   const double EV2_W = units::EV_J / units::HBAR_EV_S;  // 1 eV^2 of power in W
   *w = W1 * Psi / (double)N * EV2_W;
+  if (parts) {
+    Dual<3> xd[3];
+    for (int i = 0; i < 3; ++i) xd[i] = Dual<3>::var(x[i], i);
+    Dual<3> hx = resonance_h_at<Dual<3>>(s, m, khat, omega_inf, xd);
+    parts[PT_OK] = 1.0;
+    parts[PT_R] = r;
+    for (int i = 0; i < 3; ++i) {
+      parts[PT_N + i] = n[i];
+      parts[PT_KHAT + i] = khat[i];
+      parts[PT_GRADH + i] = hx.d[i];
+    }
+    parts[PT_E] = E;
+    parts[PT_K2] = K2;
+    parts[PT_WP2] = wp2;
+    parts[PT_COS2] = cos2;
+    parts[PT_BMAG] = Bmag;
+    parts[PT_DHDR] = dhdr;
+    parts[PT_PSI] = Psi;
+    parts[PT_W1] = W1;
+    parts[PT_A] = A;
+    parts[PT_KINF] = kinf;
+    parts[PT_OMEGA] = omega_inf;
+    parts[PT_SHAPE] = shape;
+  }
   if (s.weight_mode == WEIGHT_UNIT_P || s.weight_mode == WEIGHT_RENORM) {
     // conversion probability set to one (Sec. 5.1, Fig. flatiso right panel):
     // divide by P_agamma = Psi / |k . dE| (Eq. CPAnisoCurved), with dE the
@@ -277,6 +317,7 @@ static void sample_one(const Star& s, const double u[6], long N, double st[8], d
     st[3 + i] = (ko[i] + (1.0 / std::sqrt(A) - 1.0) * nko * n[i]) * s.ma_eV;
   }
   *status = RAY_READY;
+  if (parts) parts[PT_W] = *w;
 }
 
 // ---------------------------------------------------------------------------
@@ -653,39 +694,108 @@ struct BackwardAcc : StepHook {
     sum += std::sqrt(A) * Psi * ratio;
   }
 
-  int subdiv = 16;      // sign of g sampled at subdiv points of each step
+  // Crossing search (every level crossing along the ray counts, Sec. 5.1.3).
+  // Within one accepted step the ray is the continuous extension x(th), th in
+  // [0, 1].  A crossing is a sign change of g(th).  A ray that grazes the
+  // resonance crosses it twice in quick succession: g then has an extremum
+  // between the two roots and may keep one sign at every sampled th.  So the
+  // step is cut into NSEG equal pieces; on each piece the sign of dg/dth at its
+  // ends (dual numbers through the continuous extension) brackets an extremum
+  // of g, which is located by bisection on the sign of dg/dth.  Between
+  // consecutive break points g is monotone, holds at most one root, and every
+  // sign change there is located by bisection on the sign of g.  Only a piece
+  // holding two extrema of g (1/NSEG of a step) can hide a pair of roots.
+  static constexpr int NSEG = 32;
+  int grid = 0;         // > 0: plain sign test at grid points, no extremum search
+
+  // g and dg/dth at th on the step's continuous extension (the same
+  // polynomial as dp5_dense, evaluated on a dual number in th)
+  void g_slope(const double y[6], const double ynew[6], const double K[7][6], double h,
+               double th, double* g, double* dg) const {
+    typedef Dual<1> D1;
+    const D1 t = D1::var(th, 0);
+    D1 yd[6];
+    for (int i = 0; i < 6; ++i) {
+      const double r2 = ynew[i] - y[i];
+      const double r3 = h * K[0][i] - r2;
+      const double r4 = r2 - h * K[6][i] - r3;
+      double dk = 0.0;
+      for (int j = 0; j < 7; ++j) dk += DP5::d[j] * K[j][i];
+      const double r5 = h * dk;
+      yd[i] = y[i] + t * (r2 + (1.0 - t) * (r3 + t * (r4 + (1.0 - t) * r5)));
+    }
+    const D1 gd = crossing_g<D1>(*s, omega_inf, yd, yd + 3);
+    *g = gd.v;
+    *dg = gd.d[0];
+  }
+
+  // Locates the sign change of g on [lo, hi] (g(lo) < 0 iff negA) and adds
+  // the crossing's contribution.
+  void root(const double y[6], const double ynew[6], const double K[7][6], double h, double lo,
+            double hi, bool negA, int sigma) {
+    double yd[6];
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      dp5_dense(y, ynew, K, h, mid, yd);
+      if ((g_at(yd) < 0.0) == negA) lo = mid; else hi = mid;
+    }
+    dp5_dense(y, ynew, K, h, 0.5 * (lo + hi), yd);
+    contribution(yd, sigma);
+  }
 
   void on_step(const double y[6], const double ynew[6], const double K[7][6], double h,
                int sigma) override {
     if (!have_g) { g_prev = g_at(y); have_g = true; }
-    // A ray that turns near the resonance crosses it twice within a short
-    // stretch; the sign of g is therefore sampled on the continuous extension
-    // at subdiv points per step, and every sign change is located.
     double yd[6];
-    double th0 = 0.0, gA = g_prev;
-    for (int q = 1; q <= subdiv; ++q) {
-      const double th1 = (double)q / subdiv;
-      double gB;
-      if (q == subdiv) {
-        gB = g_at(ynew);
-      } else {
-        dp5_dense(y, ynew, K, h, th1, yd);
-        gB = g_at(yd);
-      }
-      if ((gA < 0.0) != (gB < 0.0)) {
-        double lo = th0, hi = th1;
-        const bool negA = gA < 0.0;
-        for (int it = 0; it < 200; ++it) {
-          double mid = 0.5 * (lo + hi);
-          if (mid <= lo || mid >= hi) break;
-          dp5_dense(y, ynew, K, h, mid, yd);
-          if ((g_at(yd) < 0.0) == negA) lo = mid; else hi = mid;
+    if (grid > 0) {
+      double th0 = 0.0, gA = g_prev;
+      for (int q = 1; q <= grid; ++q) {
+        const double th1 = (double)q / grid;
+        double gB;
+        if (q == grid) {
+          gB = g_at(ynew);
+        } else {
+          dp5_dense(y, ynew, K, h, th1, yd);
+          gB = g_at(yd);
         }
-        dp5_dense(y, ynew, K, h, 0.5 * (lo + hi), yd);
-        contribution(yd, sigma);
+        if ((gA < 0.0) != (gB < 0.0)) root(y, ynew, K, h, th0, th1, gA < 0.0, sigma);
+        th0 = th1;
+        gA = gB;
       }
-      th0 = th1;
+      g_prev = gA;
+      return;
+    }
+    double gA = g_prev, sA, gdum;
+    g_slope(y, ynew, K, h, 0.0, &gdum, &sA);
+    for (int q = 1; q <= NSEG; ++q) {
+      const double thA = (double)(q - 1) / NSEG, thB = (double)q / NSEG;
+      double gB, sB;
+      g_slope(y, ynew, K, h, thB, &gB, &sB);
+      if (q == NSEG) gB = g_at(ynew);
+      // break points of this piece: its ends and the extremum between them
+      double th[3] = {thA, thB, thB}, gv[3] = {gA, gB, gB};
+      int np = 2;
+      if ((sA < 0.0) != (sB < 0.0)) {
+        double lo = thA, hi = thB, gl, sl;
+        const bool negS = sA < 0.0;
+        for (int it = 0; it < 200; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          if (mid <= lo || mid >= hi) break;
+          g_slope(y, ynew, K, h, mid, &gl, &sl);
+          if ((sl < 0.0) == negS) lo = mid; else hi = mid;
+        }
+        const double te = 0.5 * (lo + hi);
+        dp5_dense(y, ynew, K, h, te, yd);
+        th[1] = te;
+        gv[1] = g_at(yd);
+        np = 3;
+      }
+      for (int k = 1; k < np; ++k)
+        if ((gv[k - 1] < 0.0) != (gv[k] < 0.0))
+          root(y, ynew, K, h, th[k - 1], th[k], gv[k - 1] < 0.0, sigma);
       gA = gB;
+      sA = sB;
     }
     g_prev = gA;
   }
@@ -727,6 +837,7 @@ static void backward_pixel(const Star& s, const TraceOpts& base, double incl, do
   acc.m = m;
   acc.omega_inf = omega_inf;
   acc.Lc_cut = Lc_cut_km / s.R_km;
+  acc.grid = base.cross_grid;
   long na, nr;
   double lam;
   *status = (unsigned char)trace_ray(s, m, omega_inf, y, opt, &na, &nr, &lam, &acc);
@@ -812,6 +923,22 @@ long or_sample(const double* sp, long n, const double* u, double* state, double*
   });
   return nroot.load();
 }
+
+// The intermediate quantities of each sample (PT_COUNT doubles per sample,
+// row-major n x PT_COUNT; PT_OK = 0 for samples without a root).
+void or_sample_parts(const double* sp, long n, const double* u, double* parts, int nthreads) {
+  Star s = make_star(sp);
+  parallel_for(n, nthreads, [&](long i) {
+    double ui[6], st[8], w;
+    unsigned char status;
+    for (int c = 0; c < 6; ++c) ui[c] = u[c * n + i];
+    double* pi = parts + i * PT_COUNT;
+    for (int c = 0; c < PT_COUNT; ++c) pi[c] = 0.0;
+    sample_one(s, ui, n, st, &w, &status, pi);
+  });
+}
+
+int or_sample_parts_count(void) { return PT_COUNT; }
 
 // Traces every READY ray in place.  nacc / nrej / lam may be null.
 void or_trace_forward(const double* sp, const double* topt, long n, double* state,

@@ -68,31 +68,11 @@ rt_status check_dev_ptr(const void* p, const char* name) {
 
 void rtk::set_last_error(const char* msg) { g_err = msg; }
 
-struct rt_star {
-  rt_star_params p;
-  rtk::StarDev h;               // host copy of the descriptor
-  rtk::StarDev* d = nullptr;    // device copy
-  unsigned long long* d_queue = nullptr;  // trace work-queue counter (scratch)
-  long long* d_bins = nullptr;  // binning accumulator (scratch)
-  size_t bins_cap = 0;
-  int device = 0;
-  double wp2_surface_max = 0.0;
-  bool empty = false;
-  double* d_park = nullptr;     // tail-mode park buffer (allocated on first use)
-  int64_t park_cap = 0;
-  int32_t* d_promo = nullptr;   // mixed backward: [count | pixels handed to FP64]
-  int64_t promo_cap = 0;
-};
+rt_status rtk::check_device_array(const void* p, const char* name) {
+  return check_dev_ptr(p, name);
+}
 
-extern "C" {
-
-const char* rt_last_error(void) { return g_err.c_str(); }
-
-int32_t rt_version(void) { return 100; }
-
-rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
-  if (out == nullptr) return fail(RT_EINVAL, "out is NULL");
-  *out = nullptr;
+rt_status rtk::check_star_params(const rt_star_params* p) {
   if (p == nullptr) return fail(RT_EINVAL, "params is NULL");
   const double vals[] = {p->M_sun, p->R_km, p->B0_G, p->P_s, p->theta_m_rad, p->psi_rad,
                          p->m_a_eV, p->g_agg_GeVinv, p->rho_dm_GeV_cm3, p->v0_kms,
@@ -127,6 +107,39 @@ rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
     return fail(RT_EUNSUPPORTED, "unknown plasma %d", p->plasma);
   if (p->plasma == RT_PLASMA_TWISTED && !(p->plasma_a > 0))
     return fail(RT_EINVAL, "RT_PLASMA_TWISTED needs plasma_a = lambda psi > 0");
+  return RT_OK;
+}
+
+struct rt_star {
+  rt_star_params p;
+  rtk::StarDev h;               // host copy of the descriptor
+  rtk::StarDev* d = nullptr;    // device copy
+  unsigned long long* d_queue = nullptr;  // trace work-queue counter (scratch)
+  long long* d_bins = nullptr;  // binning accumulator (scratch)
+  size_t bins_cap = 0;
+  int device = 0;
+  double wp2_surface_max = 0.0;
+  bool empty = false;
+  double* d_park = nullptr;     // tail-mode park buffer (allocated on first use)
+  int64_t park_cap = 0;
+  int32_t* d_promo = nullptr;   // mixed backward: [count | pixels handed to FP64]
+  int64_t promo_cap = 0;
+};
+
+const rtk::StarDev& rtk::star_host_desc(const rt_star* s) { return s->h; }
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+int32_t rt_version(void) { return 100; }
+
+rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
+  if (out == nullptr) return fail(RT_EINVAL, "out is NULL");
+  *out = nullptr;
+  const rt_status chk = rtk::check_star_params(p);
+  if (chk != RT_OK) return chk;
+  const double rs = 2.0 * p->M_sun * GM_SUN_KM / p->R_km;
 
   rt_star* s = new (std::nothrow) rt_star;
   if (!s) return fail(RT_ENOMEM, "host allocation failed");
@@ -234,8 +247,16 @@ rt_status rt_star_info(const rt_star* s, double* out) {
 rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double* d_u,
                                        double* d_state, double* d_weight, uint8_t* d_status,
                                        void* stream) {
+  return rt_sample_conversion_surface_part(s, n, n > 0 ? n : 1, d_u, d_state, d_weight, d_status,
+                                           stream);
+}
+
+rt_status rt_sample_conversion_surface_part(const rt_star* s, int64_t n, int64_t n_norm,
+                                            const double* d_u, double* d_state,
+                                            double* d_weight, uint8_t* d_status, void* stream) {
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
+  if (n_norm < n || n_norm < 1) return fail(RT_EINVAL, "need n_norm >= max(n, 1)");
   if (n == 0) return s->empty ? RT_EEMPTY_SURFACE : RT_OK;
   rt_status st;
   if ((st = check_dev_ptr(d_u, "d_uniforms")) != RT_OK) return st;
@@ -246,6 +267,7 @@ rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double
   p.s = s->h;
   p.n = n;
   p.ld = n;
+  p.n_norm = n_norm;
   p.u = d_u;
   p.state = d_state;
   p.weight = d_weight;
@@ -696,9 +718,12 @@ rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
     s->bins_cap = need;
   }
   rtk::BinParams p;
-  p.star = s->d;
+  p.R_km = s->h.R_km;
+  p.rs_prop = s->h.rs_prop;
+  p.v0 = s->h.v0;
   p.n = n;
   p.ld = n;
+  p.n_scale = n;
   p.state = d_state;
   p.weight = d_weight;
   p.status = d_status;
@@ -732,6 +757,7 @@ struct rt_batch {
   size_t bins_per_star = 0;
   int device = 0;
   bool all_empty = true;
+  std::vector<int64_t> norm;          // per-star weight normalisation (empty: the counts)
   bool rigid = false;                 // every star RT_ROTATION_RIGID (rt_trace_rot.cu)
   int tuned_block[2] = {0, 0};        // autotuned launch shape per precision (0 = default)
   int tuned_bps[2] = {0, 0};
@@ -915,6 +941,7 @@ rt_status rt_sample_batch(rt_batch* b, const double* d_u, double* d_state, doubl
     p.s = b->stars[s]->h;
     p.n = cnt;
     p.ld = b->N;
+    p.n_norm = b->norm.empty() ? cnt : b->norm[s];
     p.u = d_u + o;
     p.state = d_state + o;
     p.weight = d_weight + o;
@@ -923,6 +950,21 @@ rt_status rt_sample_batch(rt_batch* b, const double* d_u, double* d_state, doubl
     if (e != cudaSuccess) return cuda_fail(e, "sample kernel");
   }
   return b->all_empty ? RT_EEMPTY_SURFACE : RT_OK;
+}
+
+rt_status rt_batch_set_norm(rt_batch* b, const int64_t* n_norm) {
+  if (!b) return fail(RT_EINVAL, "batch is NULL");
+  if (!n_norm) {
+    b->norm.clear();
+    return RT_OK;
+  }
+  const size_t nst = b->stars.size();
+  for (size_t s = 0; s < nst; ++s)
+    if (n_norm[s] < b->off[s + 1] - b->off[s] || n_norm[s] < 1)
+      return fail(RT_EINVAL, "n_norm[%zu] = %lld is below the star's ray count or 1", s,
+                  (long long)n_norm[s]);
+  b->norm.assign(n_norm, n_norm + nst);
+  return RT_OK;
 }
 
 rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_t* d_nacc,
@@ -1073,9 +1115,12 @@ rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weigh
   for (size_t s = 0; s < nst; ++s) {
     const int64_t o = b->off[s], cnt = b->off[s + 1] - o;
     rtk::BinParams p;
-    p.star = b->d_stars + s;
+    p.R_km = b->stars[s]->h.R_km;
+    p.rs_prop = b->stars[s]->h.rs_prop;
+    p.v0 = b->stars[s]->h.v0;
     p.n = cnt;
     p.ld = b->N;
+    p.n_scale = cnt;
     p.state = d_state + o;
     p.weight = d_weight + o;
     p.status = d_status + o;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rt.h"
 #include "rt_device.cuh"
 #include "rt_dual.cuh"
 #include "rt_sample_core.cuh"
@@ -80,8 +81,10 @@ enum {
 
 struct SampleParams {
   StarDev s;
-  int64_t n;                // samples (the weights are normalised by n)
+  int64_t n;                // samples
   int64_t ld;               // SoA row stride of u and state (>= n)
+  int64_t n_norm;           // the weights are normalised by n_norm (n, or the
+                            // samples of all shards of one workload)
   const double* u;
   double* state;
   double* weight;
@@ -89,9 +92,11 @@ struct SampleParams {
 };
 
 struct BinParams {
-  const StarDev* star;      // device descriptor
+  double R_km, rs_prop, v0; // the star's radius [km], r_s / R of propagation, v0 [c]
   int64_t n;
   int64_t ld;               // SoA row stride of state (>= n)
+  int64_t n_scale;          // ray count that bounds the fixed-point sums (n, or the
+                            // rays of all shards of a sharded binning)
   const double* state;
   const double* weight;
   const uint8_t* status;
@@ -113,7 +118,13 @@ cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,
                                cudaStream_t stream);
 cudaError_t launch_tail_fp64(const TraceParams& p, cudaStream_t stream);
+// Binning: launch_bin = clear p.acc, then the three phases; the phases alone
+// serve the sharded binning (rt_bin_part_*), whose callers reduce p.acc
+// between them.
 cudaError_t launch_bin(const BinParams& p, cudaStream_t stream);
+cudaError_t launch_bin_max(const BinParams& p, cudaStream_t stream);
+cudaError_t launch_bin_accum(const BinParams& p, cudaStream_t stream);
+cudaError_t launch_bin_finalize(const BinParams& p, cudaStream_t stream);
 // Resident blocks per SM of the trace kernels at a block size.
 cudaError_t occupancy_fp64(int block, int* occ);
 cudaError_t occupancy_mixed(int block, int* occ);
@@ -186,6 +197,16 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream);
 
 // Sets the thread-local message returned by rt_last_error().
 void set_last_error(const char* msg);
+
+// Argument checks shared by the entry points (rt_abi.cu); on failure they set
+// the message of rt_last_error() and return RT_EINVAL / RT_EUNSUPPORTED.
+// check_device_array: p is device (or managed) memory of the current device.
+rt_status check_device_array(const void* p, const char* name);
+// check_star_params: the validation of rt_init_star (finite values, R above
+// the Schwarzschild radius, 0 < v0 < c, known model switches, ...).
+rt_status check_star_params(const rt_star_params* p);
+// The host copy of a handle's derived constants.
+const StarDev& star_host_desc(const rt_star* s);
 
 // Number of int64 scratch entries rt_bin_spectrum needs.
 inline size_t bin_scratch_entries(int nth, int nph, int nnu) {

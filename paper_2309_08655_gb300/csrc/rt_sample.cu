@@ -42,7 +42,7 @@ __global__ void sample_kernel(SampleParams p) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) u[j] = p.u[j * ld + i];
     SampOut<double> o;
-    sample_core(c, u, (double)n, o);
+    sample_core(c, u, (double)p.n_norm, o);
     p.state[6 * ld + i] = o.delta;
     p.state[7 * ld + i] = o.psi;
     if (!o.ok) {

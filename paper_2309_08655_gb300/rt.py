@@ -79,6 +79,20 @@ def lib():
         L.rt_star_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
         L.rt_sample_conversion_surface.restype = ctypes.c_int
         L.rt_sample_conversion_surface.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+        L.rt_sample_conversion_surface_part.restype = ctypes.c_int
+        L.rt_sample_conversion_surface_part.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, _vp,
+                                                        _vp, _vp, _vp, _vp]
+        L.rt_bin_part_max.restype = ctypes.c_int
+        L.rt_bin_part_max.argtypes = [ctypes.c_int64, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, _vp, _vp]
+        L.rt_bin_part_accumulate.restype = ctypes.c_int
+        L.rt_bin_part_accumulate.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             _vp, _vp, _vp,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, _vp, _vp]
+        L.rt_bin_part_finalize.restype = ctypes.c_int
+        L.rt_bin_part_finalize.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.rt_trace_forward.restype = ctypes.c_int
         L.rt_trace_forward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp,
                                        ctypes.POINTER(rt_trace_opts), _vp]
@@ -132,6 +146,8 @@ def lib():
         L.rt_destroy_batch.argtypes = [_vp]
         L.rt_sample_batch.restype = ctypes.c_int
         L.rt_sample_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.rt_batch_set_norm.restype = ctypes.c_int
+        L.rt_batch_set_norm.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
         L.rt_trace_batch.restype = ctypes.c_int
         L.rt_trace_batch.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp,
                                      ctypes.POINTER(rt_trace_opts), _vp]
@@ -142,6 +158,9 @@ def lib():
         L.rt_batch_set_images.restype = ctypes.c_int
         L.rt_batch_set_images.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp),
                                           ctypes.POINTER(rt_image_desc), _vp, _vp, _vp]
+        L.rt_measure_alu_peak.restype = ctypes.c_int
+        L.rt_measure_alu_peak.argtypes = [ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_double), _vp]
         L.rt_last_error.restype = ctypes.c_char_p
         L.rt_last_error.argtypes = []
         L.rt_version.restype = ctypes.c_int32
@@ -251,6 +270,40 @@ def rt_sample_conversion_surface(star: Star, n, uniforms, state, weight, status,
     return _check(lib().rt_sample_conversion_surface(
         star.handle, int(n), _ptr(uniforms), _ptr(state), _ptr(weight), _ptr(status),
         _stream(stream)), allow)
+
+
+def rt_sample_conversion_surface_part(star: Star, n, n_norm, uniforms, state, weight, status,
+                                      stream=None, allow_empty=True) -> int:
+    allow = (RT_OK, RT_EEMPTY_SURFACE) if allow_empty else (RT_OK,)
+    return _check(lib().rt_sample_conversion_surface_part(
+        star.handle, int(n), int(n_norm), _ptr(uniforms), _ptr(state), _ptr(weight),
+        _ptr(status), _stream(stream)), allow)
+
+
+def bin_acc_entries(nth, nph, nnu) -> int:
+    """RT_BIN_ACC_ENTRIES: int64 entries of a sharded binning's sums."""
+    return 2 + nth * nph * nnu + nth * nph + nnu
+
+
+def rt_bin_part_max(n, weight, status, nth, nph, nnu, acc, stream=None) -> int:
+    return _check(lib().rt_bin_part_max(int(n), _ptr(weight), _ptr(status), int(nth), int(nph),
+                                        int(nnu), _ptr(acc), _stream(stream)))
+
+
+def rt_bin_part_accumulate(star: Star, n, n_total, state, weight, status, nth, nph, nnu, nu_lo,
+                           nu_hi, acc, ld=None, stream=None) -> int:
+    """ld: row stride of the SoA state (default n)."""
+    return _check(lib().rt_bin_part_accumulate(
+        star.handle, int(n), int(n if ld is None else ld), int(n_total), _ptr(state),
+        _ptr(weight), _ptr(status), int(nth),
+        int(nph), int(nnu), float(nu_lo), float(nu_hi), _ptr(acc), _stream(stream)))
+
+
+def rt_bin_part_finalize(nth, nph, nnu, n_total, acc, hist, sky=None, spec=None,
+                         out_of_range=None, stream=None) -> int:
+    return _check(lib().rt_bin_part_finalize(
+        int(nth), int(nph), int(nnu), int(n_total), _ptr(acc), _ptr(hist), _ptr(sky), _ptr(spec),
+        _ptr(out_of_range), _stream(stream)))
 
 
 def rt_trace_forward(star: Star, n, state, status, nacc=None, nrej=None, counters=None,
@@ -424,6 +477,14 @@ def rt_sample_batch(batch: Batch, uniforms, state, weight, status, stream=None) 
                   (RT_OK, RT_EEMPTY_SURFACE))
 
 
+def rt_batch_set_norm(batch: Batch, n_norm=None) -> int:
+    """Per-star weight normalisation counts (None: the ray counts)."""
+    if n_norm is None:
+        return _check(lib().rt_batch_set_norm(batch.handle, None))
+    arr = (ctypes.c_int64 * len(n_norm))(*[int(v) for v in n_norm])
+    return _check(lib().rt_batch_set_norm(batch.handle, arr))
+
+
 def rt_trace_batch(batch: Batch, state, status, nacc=None, nrej=None, counters=None,
                    opts: rt_trace_opts | None = None, stream=None) -> int:
     if opts is None:
@@ -454,6 +515,14 @@ def rt_batch_set_images(batch: Batch, stars, descs, image, img_status, ncross=No
     return r
 
 
+def rt_measure_alu_peak(iters64=7500, iters32=560000, stream=None) -> dict:
+    """Measured FP64 / FP32 multiply-add throughput of the current GPU (the
+    defaults run each timed kernel for ~0.15 s on a GB300)."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().rt_measure_alu_peak(int(iters64), int(iters32), out, _stream(stream)))
+    return {"fp64_flops": out[0], "fp32_flops": out[1], "fp64_ms": out[2], "fp32_ms": out[3]}
+
+
 def rt_last_error() -> str:
     return lib().rt_last_error().decode()
 
@@ -468,4 +537,6 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_trace_batch", "rt_bin_batch", "rt_trace_backward", "rt_bin_spectrum_noalloc",
             "rt_flops_per_step", "rt_flux_value", "rt_flux_gradient", "rt_timestamps_reset",
             "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune",
-            "rt_batch_set_images"]
+            "rt_batch_set_images", "rt_sample_conversion_surface_part", "rt_bin_part_max",
+            "rt_bin_part_accumulate", "rt_bin_part_finalize", "rt_batch_set_norm",
+            "rt_measure_alu_peak"]

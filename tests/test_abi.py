@@ -67,3 +67,33 @@ def test_objects_are_sm103a():
     # every object is compiled for sm_103a only (one -gencode)
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert os.path.exists(B.library_path())
+
+
+def test_noalloc_rejects_bad_params_and_host_arrays_without_launch(L):
+    """rt_bin_spectrum_noalloc validates the star parameters as rt_init_star
+    does, and every array as device memory of the current device, before
+    anything is enqueued (a host pointer must come back as RT_EINVAL, never
+    reach a kernel)."""
+    import numpy as np
+    vp = ctypes.c_void_p
+    f = L.rt_bin_spectrum_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(rt.rt_star_params), ctypes.c_int64, vp, vp, vp, ctypes.c_int32,
+                  ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp, vp, vp,
+                  vp, vp]
+    host = np.zeros(8 * 16, dtype=np.float64)
+    hp = host.ctypes.data
+    bad = rt.make_params(M_sun=float("nan"), R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5)
+    assert f(ctypes.byref(bad), 16, hp, hp, hp, 4, 4, 4, 0.0, 9.0, hp, None, None, hp,
+             None) == rt.RT_EINVAL
+    assert b"non-finite" in L.rt_last_error()
+    inside = rt.make_params(M_sun=5.0, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5)
+    assert f(ctypes.byref(inside), 16, hp, hp, hp, 4, 4, 4, 0.0, 9.0, hp, None, None, hp,
+             None) == rt.RT_EINVAL                  # R inside the Schwarzschild radius
+    good = rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=1e-5)
+    assert f(ctypes.byref(good), 16, hp, hp, hp, 4, 4, 4, 0.0, 9.0, hp, None, None, hp,
+             None) == rt.RT_EINVAL                  # host arrays
+    assert b"d_state" in L.rt_last_error()
+    assert f(ctypes.byref(good), 0, None, None, None, 4, 4, 4, 0.0, 9.0, hp, None, None, hp,
+             None) == rt.RT_EINVAL                  # host output, no rays
+    assert b"d_hist" in L.rt_last_error()

@@ -2,9 +2,12 @@
 FP64 oracle on the same seeded inputs, through the C ABI.
 
 Tolerances: FP64 end points 1e-10 relative on the well-conditioned set (rays
-whose oracle end point moves by < 100 rtol when rtol is divided by 10); binned
-flux 1e-4 relative L1; sampled states and weights 1e-12 (both sides take the
-same FP64 root, differing only in rounding).
+whose oracle end point moves by at most 1e-12 between the oracle's strict FP64
+build and the same source compiled with FMA contraction -- two equally valid
+FP64 evaluations; 99.6 % of the config-0 rays, so the set must hold at least
+98 % of the traced rays); binned flux 1e-4 relative L1; sampled states and
+weights 1e-12 (both sides take the same FP64 root, differing only in
+rounding).
 """
 import numpy as np
 import pytest
@@ -100,7 +103,7 @@ def test_trace_parity_config0_fp64(oracle):
     assert (s_g[traced] == sref[traced]).mean() > 0.995
     # well-conditioned set (oracle strict vs contracted within 1e-12): 1e-10
     g = good & traced & (s_g == sref)
-    assert g.sum() > 0.2 * traced.sum()
+    assert g.sum() > 0.98 * traced.sum()          # oracle: 99.6 % well-conditioned
     d = G.rel_state_diff(st_g[:, g], ref[:, g])
     assert d.max() < 1e-10, np.sort(d)[-5:]
     # all rays: GPU deviations are of the size of the oracle's own spread

@@ -70,7 +70,7 @@ def test_mixed_endpoints_on_well_conditioned_rays(oracle, which):
     assert (s_g[traced] == sref[traced]).mean() > 0.99
     kap = _kappa(oracle, sv, st0, s0, ref, sref)
     g = (kap <= 10) & traced & (s_g == sref)
-    assert g.sum() > 0.6 * traced.sum()
+    assert g.sum() > 0.74 * traced.sum()          # oracle: 77 % / 81 % with kappa <= 10
     d = G.rel_state_diff(st_g[:, g], ref[:, g])
     assert np.median(d) < 2e-7
     assert np.percentile(d, 99) < 1e-6, np.sort(d)[-20:]

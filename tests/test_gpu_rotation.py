@@ -68,7 +68,7 @@ def test_rotating_trace_parity(oracle, case):
     assert traced.sum() > 500
     assert (s_g[traced] == sref[traced]).mean() > 0.99
     g = good & traced & (s_g == sref)
-    assert g.sum() > 0.2 * traced.sum()
+    assert g.sum() > 0.98 * traced.sum()          # oracle: >= 99.9 % well-conditioned
     assert G.rel_state_diff(st_g[:, g], ref[:, g]).max() < 1e-10
     assert np.abs(st_g[6, g] - ref[6, g]).max() < 1e-12
     assert np.abs(st_g[7, g] - ref[7, g]).max() < 1e-10
@@ -240,7 +240,9 @@ def test_rotating_model_variants(oracle, variant):
     # few such rays see dt/dl < 0 and a collapsing omega and end STIFF (oracle too)
     assert (s_g[traced] == sref[traced]).mean() > (0.98 if variant == "flat" else 0.99)
     g = good & traced & (s_g == sref)
-    assert g.sum() > 0.2 * traced.sum()
+    # oracle: 99.8 % (iso), 100 % (unit_p) well-conditioned; 76 % with flat
+    # propagation, whose off-shell rays amplify rounding
+    assert g.sum() > (0.70 if variant == "flat" else 0.97) * traced.sum()
     d = G.rel_state_diff(st_g[:, g], ref[:, g])
     if variant == "flat":
         # off-shell rays amplify rounding beyond the spread of the two oracle

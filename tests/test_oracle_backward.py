@@ -16,6 +16,14 @@ BackPower; every crossing, Sec. 5.1.3) against things the mathematics fixes:
   inside and leaves on the same line, crossing twice at r_c with |k_r| = v0;
   there dg/dl = 3 |k_r| / (W r_c), dt/dl = 2 W and Psi follows from the
   dipole at r_c o with k parallel to n.
+* A closed form for grazing rays: in flat space the spherical isotropic
+  medium conserves the angular momentum b W of a ray, and r sqrt(W^2 -
+  omega_p^2(r)) grows with r, so the ray reaches the resonance sphere r_c iff
+  b <= b_rim = r_c sqrt(W^2 - 1) / W.  Just inside the rim its two crossings
+  merge at the turning point: both must be counted down to b_rim (1 - 1e-10),
+  none just outside, and the pixel value grows like (b_rim - b)^(-1/2).  A
+  plain sign test at 16 points per step loses the pair already at
+  b_rim (1 - 1e-3).
 * Consistency of the pixel grid with the point evaluator, the mirror symmetry
   of an aligned rotator, and the conversion-length cut only removing
   crossings.
@@ -71,10 +79,8 @@ def test_liouville_forward_equals_backward_total(oracle):
     nphi = 12
     phis = (np.arange(nphi) + 0.5) * 2.0 * math.pi / nphi
     rim = _rim(oracle, sv, opts, 1.0, 0.0)
-    # spherically symmetric geometry: the same rim in every direction (to the
-    # resolution of the crossing search, which misses a pair of crossings
-    # closer together than a sixteenth of a step)
-    assert abs(_rim(oracle, sv, opts, 0.3, 2.0) - rim) < 1e-6
+    # spherically symmetric geometry: the same rim in every direction
+    assert abs(_rim(oracle, sv, opts, 0.3, 2.0) - rim) < 1e-9 * rim
     total = 0.0
     for c, wc in zip(ci, wi):
         pts, wts = [], []
@@ -144,3 +150,29 @@ def test_aligned_image_mirror_symmetric_and_cut(oracle):
     img2, st2, nc2 = oracle.trace_backward(sv, opts, 12, 12, 0.9, 1e4, 2.0, Lc_cut_km=0.5)
     assert np.all(nc2 <= nc) and np.all(img2 <= img * (1 + 1e-12))
     assert nc2.sum() < nc.sum()
+
+
+def test_grazing_pair_counted_to_the_closed_form_rim(oracle):
+    v0_kms = 3000.0
+    sv = _radial_star(oracle, M_sun=0.0, v0_kms=v0_kms)    # a = 8: r_c = 2 R
+    v0 = v0_kms / C_KMS
+    W = math.sqrt(1.0 + v0 * v0)
+    b_rim = 2.0 * math.sqrt(W * W - 1.0) / W
+    eps = 10.0 ** -np.arange(2.0, 11.0)
+    for phi, incl in ((0.0, 0.7), (1.9, 0.2)):
+        c, s = math.cos(phi), math.sin(phi)
+        inside = np.stack([b_rim * (1 - eps) * c, b_rim * (1 - eps) * s], 1)
+        outside = np.stack([b_rim * (1 + eps) * c, b_rim * (1 + eps) * s], 1)
+        opts = oracle.trace_opts(rtol=1e-10)
+        v, st, nc = oracle.backward_points(sv, opts, inside, incl)
+        assert np.all(st == oracle.RAY_ESCAPED)
+        assert np.all(nc == 2), nc
+        # the two merging crossings: value ~ (b_rim - b)^(-1/2)
+        scaled = v * np.sqrt(eps)
+        assert np.all(np.abs(scaled[1:6] / scaled[3] - 1.0) < 3e-3), scaled
+        v2, _, nc2 = oracle.backward_points(sv, opts, outside, incl)
+        assert np.all(nc2 == 0) and np.all(v2 == 0.0)
+        # the comparison baseline loses the pair: the search above is what finds it
+        _, _, nc16 = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10, crossing_grid=16),
+                                            inside, incl)
+        assert (nc16 == 0).sum() >= 5, nc16

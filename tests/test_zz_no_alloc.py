@@ -82,3 +82,30 @@ def test_noalloc_refuses_oversized_histograms(L):
                                      None, x.data_ptr(), None)
     assert code == rt.RT_EINVAL
     assert b"RT_BIN_NOALLOC_MAX_ENTRIES" in L.rt_last_error()
+
+
+def test_noalloc_refuses_host_arrays_and_bad_params(L):
+    """Host memory in place of a device array, or parameters that
+    rt_init_star would refuse, come back as RT_EINVAL before any launch; a
+    correct call right after still matches rt_bin_spectrum."""
+    params = rt.make_params(**I.star_config0())
+    host = np.zeros(8 * 64, dtype=np.float64)
+    hp = host.ctypes.data
+    d = torch.zeros(8 * 64, dtype=torch.float64, device="cuda")
+    s = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    for args in [(hp, d.data_ptr(), s.data_ptr()), (d.data_ptr(), hp, s.data_ptr()),
+                 (d.data_ptr(), d.data_ptr(), host.ctypes.data)]:
+        code = L.rt_bin_spectrum_noalloc(ctypes.byref(params), 64, *args, 4, 4, 4, 0.0, 9.0,
+                                         d.data_ptr(), None, None, d.data_ptr(), None)
+        assert code == rt.RT_EINVAL, L.rt_last_error()
+    code = L.rt_bin_spectrum_noalloc(ctypes.byref(params), 64, d.data_ptr(), d.data_ptr(),
+                                     s.data_ptr(), 4, 4, 4, 0.0, 9.0, hp, None, None,
+                                     d.data_ptr(), None)
+    assert code == rt.RT_EINVAL and b"d_hist" in L.rt_last_error()
+    bad = rt.make_params(**dict(I.star_config0(), v0_kms=4e5))      # faster than light
+    code = L.rt_bin_spectrum_noalloc(ctypes.byref(bad), 64, d.data_ptr(), d.data_ptr(),
+                                     s.data_ptr(), 4, 4, 4, 0.0, 9.0, d.data_ptr(), None, None,
+                                     d.data_ptr(), None)
+    assert code == rt.RT_EINVAL
+    torch.cuda.synchronize()
+    test_noalloc_matches_rt_bin_spectrum_on_two_calls(L)
