@@ -936,7 +936,7 @@ def _backward_leg(args, dev, stream, fl, rank):
     out = {"workload": "backward_image_1024x1024_incl60_b50R", "precision": "fp64",
            "ms_per_image": 1e3 * t, "pixels_per_s": nx * ny / t,
            "ray_steps_per_s": c[0] / t, "accepted_steps": c[0], "rejected_steps": c[1],
-           "crossings": c[6], "dP_dOmega_W_per_sr": float(img.sum()),
+           "crossings": c[6], "extremum_searches": c[5], "dP_dOmega_W_per_sr": float(img.sum()),
            "roofline": {"kernel": "backward_kernel", "bound": "alu",
                         "achieved": (c[0] + c[1]) * fl[1] / t / 1e12, "peak": PEAK["fp64"] / 1e12,
                         "unit": "TFLOP/s", "frac": (c[0] + c[1]) * fl[1] / t / PEAK["fp64"],
@@ -967,6 +967,7 @@ def _backward_leg(args, dev, stream, fl, rank):
     out["mixed"] = {"rtol": 1e-8, "ms_per_image": 1e3 * tm, "pixels_per_s": nx * ny / tm,
                     "ray_steps_per_s": cm[0] / tm, "accepted_steps": cm[0],
                     "rejected_steps": cm[1], "pixels_to_fp64": cm[4], "crossings": cm[6],
+                    "extremum_searches": cm[5],
                     "dP_dOmega_W_per_sr": float(img_m.sum()),
                     "total_rel_diff_vs_fp64": float(abs(img_m.sum() - img.sum()) / img.sum()),
                     "total_rel_diff_same_crossings":

@@ -350,9 +350,13 @@ rt_status rt_bin_part_finalize(int32_t nth, int32_t nph, int32_t nnu, int64_t n_
  * plane along -o with the on-shell momentum at the line centre omega_inf =
  * m_a sqrt(1 + v0^2), is integrated (FP64 DP5(4), opts->rtol/atol,
  * max_steps) until it returns to its starting radius or is captured, and at
- * every sign change of g = E_gamma - E_a = omega - sqrt(m_a^2 + |k|^2) along
- * it (sampled at 16 points of each accepted step on the continuous
- * extension, located by bisection) adds sqrt(A) Psi |dt/dl| / |dg/dl|.
+ * every crossing of g = E_gamma - E_a = omega - sqrt(m_a^2 + |k|^2) = 0
+ * along it adds sqrt(A) Psi |dt/dl| / |dg/dl|.  Crossings are searched on
+ * each accepted step's continuous extension, cut into 16 pieces: a sign
+ * change of g across a piece, and, where the ray grazes the resonance, the
+ * two roots around an extremum of g inside a piece whose ends share a sign
+ * (the extremum bracketed by the slope of g along the step and located by
+ * bisection); every root is located by FP64 bisection.
  * The pixel value is that sum x pixel area x int domega omega^2 f_a
  * (omega_0 n_inf / (2 pi^{3/2} k0) for the Maxwellian, omega_0 n_inf /
  * (4 pi k0) for the monochromatic distribution): dP/dOmega in W / sr.
@@ -368,7 +372,9 @@ rt_status rt_bin_part_finalize(int32_t nth, int32_t nph, int32_t nnu, int64_t n_
  *   d_counters    in/out (may be NULL): RT_COUNTERS int64 accumulated:
  *                 accepted steps, rejected steps, pixels finished, pixels
  *                 escaped, pixels handed from the FP32 to the FP64 kernel
- *                 (RT_PREC_MIXED), -, crossings counted
+ *                 (RT_PREC_MIXED), FP64 extremum searches of the crossing
+ *                 search (pieces where a grazing pair could hide), crossings
+ *                 counted
  *   opts          rtol, atol, r_capture_over_R, max_steps, precision used;
  *                 r_out_over_R, lambda_max ignored
  * The sign of g is decided in FP32 where it is certain (on shell, g has the
@@ -591,6 +597,23 @@ rt_status rt_bin_spectrum_noalloc(const rt_star_params* params, int64_t n, const
                                   int32_t nph, int32_t nnu, double nu_lo, double nu_hi,
                                   double* d_hist, double* d_sky, double* d_spec,
                                   double* d_out_of_range, void* stream);
+
+/*
+ * rt_hamilton_rhs - Hamilton's equations (Eq. Hamilton) of the strong-field
+ * Hamiltonian (Eq. StrongBHam; the model of the star's switches) at n given
+ * photon phase-space points: exactly the right-hand side that the FP64
+ * integrators step with, for checks and for callers that integrate rays
+ * themselves.  The Goldreich-Julian density |2 Omega.B / e| (Eq. GJDensity)
+ * is differentiated on the side of its null cone where the point lies.
+ *   d_state  RT_STATE_ROWS x n, as rt_trace_forward's state (x [km], k [eV],
+ *            delta = omega_inf / m_a - 1, psi)
+ *   d_H      out (may be NULL): n values of H / m_a^2
+ *   d_dydl   out: 6 x n, d(x/R)/dl and d(k/m_a)/dl, rows x0 x1 x2 k0 k1 k2,
+ *            with l the integrators' parameter (H scaled by m_a^2, x by R)
+ * RT_EUNSUPPORTED for RT_ROTATION_RIGID stars.  Asynchronous on stream.
+ */
+rt_status rt_hamilton_rhs(const rt_star* star, int64_t n, const double* d_state, double* d_H,
+                          double* d_dydl, void* stream);
 
 /*
  * rt_count_status - histogram of per-ray status codes (synchronises the

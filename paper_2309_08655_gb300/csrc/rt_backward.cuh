@@ -8,10 +8,16 @@
 // a distant plane; the ray integral of the delta function is a sum over the
 // crossings of g = E_gamma - E_a = omega - sqrt(m_a^2 + |k|^2) along the ray,
 // sum_c sqrt(A) Psi f_a |dt/dl| / |dg/dl|.  Each pixel's time-reversed ray
-// (k -> -k; H is even in k) is traced inward from the plane; the sign of g is
-// sampled at BACK_SUBDIV points of every accepted step on the continuous
-// extension (a ray turning near the resonance crosses it twice within one
-// step) and every sign change is located by bisection.
+// (k -> -k; H is even in k) is traced inward from the plane.  Within each
+// accepted step the ray is the continuous extension y(th), th in [0, 1]; the
+// step is cut into BACK_SUBDIV pieces, and a crossing is either a sign change
+// of g across a piece or, where the ray grazes the resonance, a pair of roots
+// around an extremum of g inside a piece with no sign change at its ends.  The
+// sign of g at the piece ends is screened in FP32 (FP64 where the screen is
+// not certain); the slope of the screened quantity along th, also in FP32,
+// brackets the extrema of g that turn toward zero, and where a tangent-line
+// bound lets such a dip reach zero the extremum is located in FP64 by
+// bisection on the sign of dg/dth.  Every root is located by FP64 bisection.
 
 #pragma once
 #include <cuda_runtime.h>
@@ -23,6 +29,11 @@
 namespace rtk {
 
 constexpr int BACK_SUBDIV = 16;
+// A grazing pair inside a piece needs g near zero there: the slope of the
+// screened N is formed only where |N| < SLOPE_NEAR at an end of the piece
+// (far from the resonance N ~ -1; a smooth dip of N by more than 0.5 within a
+// sixteenth of a step that resolves the ray to rtol does not occur).
+constexpr float SLOPE_NEAR = 0.5f;
 
 struct BackParams {
   StarDev s;
@@ -93,6 +104,35 @@ __device__ __forceinline__ double crossing_g(const RayConst<double>& c, double W
   return W * rsqrt(A) - sqrt(1.0 + kk);
 }
 
+// g and dg/dth at a point y of the continuous extension with y' = dy/dth.
+__device__ __forceinline__ void crossing_g_slope(const RayConst<double>& c, double W,
+                                                 const double* y, const double* yp, double* g,
+                                                 double* dg) {
+  const double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+  const double ir = rsqrt(r2);
+  const double n0 = y[0] * ir, n1 = y[1] * ir, n2 = y[2] * ir;
+  const double A = 1.0 - c.rs * ir;
+  const double kr = n0 * y[3] + n1 * y[4] + n2 * y[5];
+  const double kk = y[3] * y[3] + y[4] * y[4] + y[5] * y[5] + (A - 1.0) * kr * kr;
+  const double Ea = sqrt(1.0 + kk);
+  const double om = W * rsqrt(A);
+  *g = om - Ea;
+  // dg/dx = (d omega / dA - d|k|^2/dA / 2E_a) dA/dx - (d|k|^2/dkr / 2E_a) dkr/dx
+  const double dAr = c.rs * ir * ir;                       // dA/dx = dAr n
+  const double c_om = -0.5 * om / A * dAr;
+  const double ckr = 2.0 * (A - 1.0) * kr * ir;
+  const double iEa = 0.5 / Ea;
+  double d = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double ni = (i == 0) ? n0 : (i == 1) ? n1 : n2;
+    const double dkk_dx = kr * kr * dAr * ni + ckr * (y[3 + i] - kr * ni);
+    const double dkk_dk = 2.0 * (y[3 + i] + (A - 1.0) * kr * ni);
+    d += (c_om * ni - dkk_dx * iEa) * yp[i] - dkk_dk * iEa * yp[3 + i];
+  }
+  *dg = d;
+}
+
 // Sign of g at a sample point, decided in FP32 where it is certain.  g is a
 // difference of two nearly equal terms, but on shell (H = 0)
 //   W^2/A - |k|_g^2 = P G - H,  G = 1 - A Kp^2 / W^2 (anisotropic) or 1,
@@ -136,9 +176,10 @@ __device__ __forceinline__ Screen make_screen(const RayConst<double>& c, const d
 }
 
 // +1 / -1: g > 0 / g < 0 for certain; 0: evaluate g in FP64.  x = x0 + d
-// (FP32), d the displacement from the step start, k the momentum.
+// (FP32), d the displacement from the step start, k the momentum.  *Nout:
+// N = P G - 1 (the screened quantity, of the sign of g up to the drift H).
 __device__ __forceinline__ int screen_sign(const Screen& s, const float* x, const float* d,
-                                           const float* k) {
+                                           const float* k, float* Nout) {
   const float r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
   const float ir = rsqrtf(r2);
   const float A = 1.0f - s.rs * ir;
@@ -178,8 +219,83 @@ __device__ __forceinline__ int screen_sign(const Screen& s, const float* x, cons
   const float PG = P * G;
   const float N = PG - 1.0f;
   const float margin = 0.05f * (1.0f + fabsf(PG)) + dP * fabsf(G) + 1e-5f * fabsf(P) * (1.0f + t);
+  *Nout = N;
   if (!(fabsf(N) > margin)) return 0;      // also NaN
   return N > 0.0f ? 1 : -1;
+}
+
+// dN/dth of the screened N = P G - 1 along the continuous extension, in FP32:
+// x = x0 + d, k, and their th-derivatives xp, kp.  Only its sign is used, to
+// bracket extrema of g between sample points (FP32 suffices on this chip,
+// where FP32 arithmetic is ~64 times cheaper than FP64).
+__device__ __forceinline__ float screen_slope(const Screen& s, const float* x, const float* d,
+                                              const float* k, const float* xp,
+                                              const float* kp) {
+  const float r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const float ir = rsqrtf(r2);
+  const float n0 = x[0] * ir, n1 = x[1] * ir, n2 = x[2] * ir;
+  const float rp = n0 * xp[0] + n1 * xp[1] + n2 * xp[2];          // dr/dth
+  const float lr = rp * ir;                                       // dln r/dth
+  const float A = 1.0f - s.rs * ir;
+  const float mu = s.m0 * n0 + s.m1 * n1 + s.m2 * n2;
+  const float mxp = s.m0 * xp[0] + s.m1 * xp[1] + s.m2 * xp[2];
+  const float mup = (mxp - mu * rp) * ir;                         // d(m.n)/dth
+  float P = 0.0f, Pp = 0.0f;
+  if (s.plasma == PLASMA_GJ) {
+    const float md = s.m0 * d[0] + s.m1 * d[1] + s.m2 * d[2];
+    const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float Fu = s.F0 + (s.gF[0] * d[0] + s.gF[1] * d[1] + s.gF[2] * d[2]) +
+                     (3.0f * d[2] * md - s.m2 * dd);
+    const float Fp = (s.gF[0] + 3.0f * d[2] * s.m0 - 2.0f * s.m2 * d[0]) * xp[0] +
+                     (s.gF[1] + 3.0f * d[2] * s.m1 - 2.0f * s.m2 * d[1]) * xp[1] +
+                     (s.gF[2] + 3.0f * d[2] * s.m2 + 3.0f * md - 2.0f * s.m2 * d[2]) * xp[2];
+    const float pre = s.cp * ir * ir * ir * ir * ir;               // cp r^-5
+    P = pre * Fu * s.sig;
+    Pp = pre * s.sig * (Fp - 5.0f * Fu * lr);
+  } else if (s.plasma == PLASMA_LINEAR_Z) {
+    P = s.pa * x[2];
+    Pp = s.pa * xp[2];
+  } else if (s.plasma == PLASMA_RADIAL) {
+    P = s.pa * ir * ir * ir;
+    Pp = -3.0f * P * lr;
+  } else if (s.plasma == PLASMA_TWISTED) {
+    const float q = s.cp * ir * ir * ir * ir;
+    P = q * (1.0f - mu * mu);
+    Pp = -2.0f * q * mu * mup - 4.0f * P * lr;
+  } else if (s.plasma == PLASMA_HOMOG) {
+    P = s.pa;
+  }
+  if (s.disp == DISP_ISO) return Pp;
+  // G = 1 - t, t = A Kpb^2 iW2 / (3 mu^2 + 1), Kpb = mu kr (1 + 2 sqrt(A)) - m.k
+  const float sA = sqrtf(A);
+  const float Ap = s.rs * ir * lr;                                // dA/dth
+  const float kr = n0 * k[0] + n1 * k[1] + n2 * k[2];
+  const float krp = ((xp[0] - n0 * rp) * k[0] + (xp[1] - n1 * rp) * k[1] +
+                     (xp[2] - n2 * rp) * k[2]) * ir +
+                    n0 * kp[0] + n1 * kp[1] + n2 * kp[2];
+  const float km = s.m0 * k[0] + s.m1 * k[1] + s.m2 * k[2];
+  const float kmp = s.m0 * kp[0] + s.m1 * kp[1] + s.m2 * kp[2];
+  const float Kpb = mu * kr * (1.0f + 2.0f * sA) - km;
+  const float Kpbp = (mup * kr + mu * krp) * (1.0f + 2.0f * sA) + mu * kr * Ap / sA - kmp;
+  const float bb = 3.0f * mu * mu + 1.0f;
+  const float t = A * Kpb * Kpb * s.iW2 / bb;
+  const float tp = s.iW2 * (Ap * Kpb * Kpb + 2.0f * A * Kpb * Kpbp) / bb - t * 6.0f * mu * mup / bb;
+  return Pp * (1.0f - t) - P * tp;
+}
+
+// The continuous extension's displacement d(th) = th (p2 + u (p3 + th (p4 +
+// u p5))), u = 1 - th, and its derivative dd/dth, in FP32.
+__device__ __forceinline__ void dense32(float t, const float* p2, const float* p3,
+                                        const float* p4, const float* p5, float* d, float* dp) {
+  const float u = 1.0f - t;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float Q3 = p4[i] + u * p5[i];
+    const float Q2 = p3[i] + t * Q3;
+    const float Q1 = p2[i] + u * Q2;
+    d[i] = t * Q1;
+    dp[i] = Q1 + t * (u * (Q3 - t * p5[i]) - Q2);
+  }
 }
 
 // Crossing search and estimator of one pixel's ray.
@@ -188,6 +304,7 @@ struct CrossingAcc {
   double W, Lc_cut;
   double sum;
   int ncross, ncut;
+  int nsearch;       // FP64 extremum searches (pieces where a dip could reach zero)
   bool have_g;
   bool neg_prev;     // g < 0 at the end of the previous accepted step
 
@@ -198,6 +315,7 @@ struct CrossingAcc {
     sum = 0.0;
     ncross = 0;
     ncut = 0;
+    nsearch = 0;
     have_g = false;
     neg_prev = false;
   }
@@ -275,12 +393,73 @@ struct CrossingAcc {
     sum += sA * Psi * ratio;
   }
 
-  // One accepted step from y to yn with the continuous extension x(th): the
-  // sign of g at BACK_SUBDIV points, screened in FP32 on the pieces p2..p5 of
-  // x(th) - y = th (p2 + (1 - th) (p3 + th (p4 + (1 - th) p5))) about y32,
-  // evaluated in FP64 at dense64(th, x) where the screen leaves it open, every
-  // sign change located by FP64 bisection on dense64 and its contribution
-  // added.
+  // Locates the sign change of g on [lo, hi] (g(lo) < 0 iff negA) by FP64
+  // bisection on dense64 and adds its contribution.
+  template <class Dense64>
+  __device__ void root(const RayConst<double>& c, double lo, double hi, bool negA,
+                       Dense64& dense64) {
+    double yd[6];
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      dense64(mid, yd, nullptr);
+      if ((crossing_g(c, W, yd) < 0.0) == negA) lo = mid; else hi = mid;
+    }
+    dense64(0.5 * (lo + hi), yd, nullptr);
+    contribution(c, yd);
+  }
+
+  // A piece [a, b] whose ends have the same sign of g (negative iff neg)
+  // while g turns toward zero inside: the extremum is located by FP64
+  // bisection on the sign of dg/dth; if g has the other sign there, the two
+  // roots on either side are located and counted.
+  template <class Dense64>
+  __device__ void graze(const RayConst<double>& c, double a, double b, bool neg,
+                        Dense64& dense64) {
+    double yd[6], yp[6], g, ga, gb;
+    dense64(a, yd, yp);
+    crossing_g_slope(c, W, yd, yp, &g, &ga);
+    dense64(b, yd, yp);
+    crossing_g_slope(c, W, yd, yp, &g, &gb);
+    // a minimum of |g| on the side of neg: g' < 0 then > 0 for g > 0
+    if (neg ? !(ga > 0.0 && gb < 0.0) : !(ga < 0.0 && gb > 0.0)) return;
+    // Illinois (regula falsi with halving of the stale end) on dg/dth
+    double lo = a, hi = b, flo = ga, fhi = gb;
+    int side = 0;
+    for (int it = 0; it < 100 && hi - lo > 1e-13; ++it) {
+      double mid = (lo * fhi - hi * flo) / (fhi - flo);
+      if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+      dense64(mid, yd, yp);
+      double gm;
+      crossing_g_slope(c, W, yd, yp, &g, &gm);
+      if ((gm < 0.0) == (flo < 0.0)) {
+        lo = mid;
+        flo = gm;
+        if (side == -1) fhi *= 0.5;
+        side = -1;
+      } else {
+        hi = mid;
+        fhi = gm;
+        if (side == 1) flo *= 0.5;
+        side = 1;
+      }
+    }
+    const double te = 0.5 * (lo + hi);
+    dense64(te, yd, nullptr);
+    if ((crossing_g(c, W, yd) < 0.0) == neg) return;      // the dip stays on its side
+    root(c, a, te, neg, dense64);
+    root(c, te, b, !neg, dense64);
+  }
+
+  // One accepted step from y to yn with the continuous extension y(th): the
+  // sign of g at BACK_SUBDIV + 1 points, screened in FP32 on the pieces
+  // p2..p5 of y(th) - y = th (p2 + (1 - th) (p3 + th (p4 + (1 - th) p5)))
+  // about y32, evaluated in FP64 at dense64(th) where the screen leaves it
+  // open; every sign change located by FP64 bisection; and between two
+  // samples of one sign, an extremum of g turning toward zero (bracketed by
+  // the FP32 slope of the screened N) searched in FP64 where the two tangent
+  // lines at the samples meet within the screen's margin of zero.
+  // dense64(th, yd, yp) gives the FP64 point and, if yp is set, dy/dth.
   template <class Dense64>
   __device__ void scan(const RayConst<double>& c, const double* y, const double* yn,
                        const Screen& sc, const float* y32, const float* p2, const float* p3,
@@ -292,45 +471,95 @@ struct CrossingAcc {
     double yd[6];
     double th0 = 0.0;
     bool negA = neg_prev;
+    float NA, slA;
+    // pieces whose dip is searched after the loop (bit q - 1), and their sign
+    unsigned dips = 0u, dip_neg = 0u;
+    {
+      float d[6], dp[6], xs[3], ks[3];
+      dense32(0.0f, p2, p3, p4, p5, d, dp);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        xs[i] = y32[i];
+        ks[i] = y32[3 + i];
+      }
+      (void)screen_sign(sc, xs, d, ks, &NA);
+      slA = (fabsf(NA) < SLOPE_NEAR) ? screen_slope(sc, xs, d, ks, dp, dp + 3) : 0.0f;
+    }
     for (int q = 1; q <= BACK_SUBDIV; ++q) {
       const double th1 = (double)q / BACK_SUBDIV;
       const float t = (float)q * (1.0f / BACK_SUBDIV);
-      float d[6], xs[3], ks[3];
+      float d[6], dp[6], xs[3], ks[3];
+      dense32(t, p2, p3, p4, p5, d, dp);
+      if (q == BACK_SUBDIV) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-        d[i] = (q == BACK_SUBDIV)
-                   ? p2[i]
-                   : t * (p2[i] + (1.0f - t) * (p3[i] + t * (p4[i] + (1.0f - t) * p5[i])));
+        for (int i = 0; i < 6; ++i) d[i] = p2[i];          // the step's own increment
+      }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         xs[i] = y32[i] + d[i];
         ks[i] = y32[3 + i] + d[3 + i];
       }
-      const int sg = screen_sign(sc, xs, d, ks);
+      float NB;
+      const int sg = screen_sign(sc, xs, d, ks, &NB);
+      // the slope is needed only where a dip could reach zero: near the
+      // resonance at one end of a piece
+      const bool nearB = fabsf(NB) < SLOPE_NEAR;
+      float slB = 0.0f;
+      if (nearB || fabsf(NA) < SLOPE_NEAR) {
+        if (!(fabsf(NA) < SLOPE_NEAR)) {             // slope at th0 not formed yet
+          float d0[6], dp0[6], x0[3], k0[3];
+          dense32(t - 1.0f / BACK_SUBDIV, p2, p3, p4, p5, d0, dp0);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            x0[i] = y32[i] + d0[i];
+            k0[i] = y32[3 + i] + d0[3 + i];
+          }
+          slA = screen_slope(sc, x0, d0, k0, dp0, dp0 + 3);
+        }
+        slB = screen_slope(sc, xs, d, ks, dp, dp + 3);
+      }
       bool negB;
       if (sg != 0) {
         negB = sg < 0;
       } else if (q == BACK_SUBDIV) {
         negB = crossing_g(c, W, yn) < 0.0;
       } else {
-        dense64(th1, yd);
+        dense64(th1, yd, nullptr);
         negB = crossing_g(c, W, yd) < 0.0;
       }
       if (negA != negB) {
-        double lo = th0, hi = th1;
-        for (int it = 0; it < 200; ++it) {
-          const double mid = 0.5 * (lo + hi);
-          if (mid <= lo || mid >= hi) break;
-          dense64(mid, yd);
-          if ((crossing_g(c, W, yd) < 0.0) == negA) lo = mid; else hi = mid;
+        root(c, th0, th1, negA, dense64);
+      } else {
+        // s N decreasing at th0 and increasing at th1 (s = sign of g): a dip
+        // toward zero between them; the tangent lines at both ends meet at
+        // s N = L, a lower bound of the dip where s N is convex
+        const float sgn = negA ? -1.0f : 1.0f;
+        const float a0 = sgn * NA, a1 = sgn * NB, s0 = sgn * slA, s1 = sgn * slB;
+        if (s0 < 0.0f && s1 > 0.0f) {
+          const float dth = 1.0f / BACK_SUBDIV;
+          float tx = (a1 - a0 - s0 * dth) / (s0 - s1);          // meeting point - th1
+          tx = fminf(0.0f, fmaxf(-dth, tx));
+          const float L = a1 + s1 * tx;
+          const float margin = 0.05f * (2.0f + fabsf(NA) + fabsf(NB));
+          if (!(L > margin)) {
+            dips |= 1u << (q - 1);
+            if (negA) dip_neg |= 1u << (q - 1);
+          }
         }
-        dense64(0.5 * (lo + hi), yd);
-        contribution(c, yd);
       }
       th0 = th1;
       negA = negB;
+      NA = NB;
+      slA = slB;
     }
     neg_prev = negA;
+    nsearch += __popc(dips);
+    while (dips) {
+      const int q = __ffs(dips);                   // piece q: [(q - 1), q] / BACK_SUBDIV
+      dips &= dips - 1u;
+      graze(c, (double)(q - 1) / BACK_SUBDIV, (double)q / BACK_SUBDIV,
+            ((dip_neg >> (q - 1)) & 1u) != 0u, dense64);
+    }
   }
 
   // The same from the FP64 pieces y + th (r2 + (1 - th) (r3 + th (r4 + (1 - th)
@@ -348,10 +577,16 @@ struct CrossingAcc {
       p4[i] = (float)r4[i];
       p5[i] = (float)r5[i];
     }
-    auto dense64 = [&](double th, double* yd) {
+    auto dense64 = [&](double th, double* yd, double* yp) {
+      const double u = 1.0 - th;
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-        yd[i] = y[i] + th * (r2[i] + (1.0 - th) * (r3[i] + th * (r4[i] + (1.0 - th) * r5[i])));
+      for (int i = 0; i < 6; ++i) {
+        const double Q3 = r4[i] + u * r5[i];
+        const double Q2 = r3[i] + th * Q3;
+        const double Q1 = r2[i] + u * Q2;
+        yd[i] = y[i] + th * Q1;
+        if (yp) yp[i] = Q1 + th * (u * (Q3 - th * r5[i]) - Q2);
+      }
     };
     scan(c, y, yn, sc, y32, p2, p3, p4, p5, dense64);
   }

@@ -78,6 +78,8 @@ enum {
   CTR_ACC = 0, CTR_REJ, CTR_RAYS, CTR_ESC, CTR_PROMOTED, CTR_PROMOTED_STEPS, CTR_CROSS,
   CTR_COUNT = 8
 };
+// rt_trace_backward uses slot 5 for its FP64 extremum searches (grazing pairs)
+constexpr int CTR_SEARCH = CTR_PROMOTED_STEPS;
 
 struct SampleParams {
   StarDev s;

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
   Lane L;
   CrossingHook hk;
   hk.on = true;
-  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0;
+  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, srch = 0;
   if (bp.ts && threadIdx.x == 0) atomicMin(bp.ts, global_ns());
   for (;;) {
     const bool need = (pix == -1);
@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
         done += 1;
         esc += (st == RAY_ESCAPED);
         nc += hk.acc.ncross - hk.acc.ncut;
+        srch += hk.acc.nsearch;
         pix = -1;
       }
     }
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
       done += __shfl_down_sync(FULL, done, o);
       esc += __shfl_down_sync(FULL, esc, o);
       nc += __shfl_down_sync(FULL, nc, o);
+      srch += __shfl_down_sync(FULL, srch, o);
     }
     if (lane == 0) {
       atomicAdd((unsigned long long*)&bp.counters[CTR_ACC], (unsigned long long)acc);
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(128) backward_kernel(BackParams bp) {
       atomicAdd((unsigned long long*)&bp.counters[CTR_RAYS], (unsigned long long)done);
       atomicAdd((unsigned long long*)&bp.counters[CTR_ESC], (unsigned long long)esc);
       atomicAdd((unsigned long long*)&bp.counters[CTR_CROSS], (unsigned long long)nc);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_SEARCH], (unsigned long long)srch);
     }
   }
 }

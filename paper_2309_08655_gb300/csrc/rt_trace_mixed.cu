@@ -579,12 +579,16 @@ struct CrossingHookM {
     // FP64 points of the continuous extension: FP64 start and increment, FP32
     // small parts
     const double* y = L.y;
-    auto dense64 = [&](double th, double* yd) {
+    auto dense64 = [&](double th, double* yd, double* yp) {
+      const double u = 1.0 - th;
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-        yd[i] = y[i] + th * ((yn[i] - y[i]) +
-                             (1.0 - th) * ((double)p3[i] +
-                                           th * ((double)p4[i] + (1.0 - th) * (double)p5[i])));
+      for (int i = 0; i < 6; ++i) {
+        const double Q3 = (double)p4[i] + u * (double)p5[i];
+        const double Q2 = (double)p3[i] + th * Q3;
+        const double Q1 = (yn[i] - y[i]) + u * Q2;
+        yd[i] = y[i] + th * Q1;
+        if (yp) yp[i] = Q1 + th * (u * (Q3 - th * (double)p5[i]) - Q2);
+      }
     };
     acc.scan(c, L.y, yn, sc, yf, p2, p3, p4, p5, dense64);
   }
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
   LaneM L;
   CrossingHookM hk;
   hk.on = true;
-  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, promoted = 0;
+  long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, promoted = 0, srch = 0;
   if (bp.ts && threadIdx.x == 0) atomicMin(bp.ts, global_ns());
   for (;;) {
     const bool need = (pix == -1);
@@ -679,6 +683,7 @@ __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
           done += 1;
           esc += (st == RAY_ESCAPED);
           nc += hk.acc.ncross - hk.acc.ncut;
+          srch += hk.acc.nsearch;
         }
         pix = -1;
       }
@@ -692,6 +697,7 @@ __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
       done += __shfl_down_sync(FULL, done, o);
       esc += __shfl_down_sync(FULL, esc, o);
       nc += __shfl_down_sync(FULL, nc, o);
+      srch += __shfl_down_sync(FULL, srch, o);
       promoted += __shfl_down_sync(FULL, promoted, o);
     }
     if (lane == 0) {
@@ -700,6 +706,7 @@ __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
       atomicAdd((unsigned long long*)&bp.counters[CTR_RAYS], (unsigned long long)done);
       atomicAdd((unsigned long long*)&bp.counters[CTR_ESC], (unsigned long long)esc);
       atomicAdd((unsigned long long*)&bp.counters[CTR_CROSS], (unsigned long long)nc);
+      atomicAdd((unsigned long long*)&bp.counters[CTR_SEARCH], (unsigned long long)srch);
       atomicAdd((unsigned long long*)&bp.counters[CTR_PROMOTED], (unsigned long long)promoted);
     }
   }

@@ -158,6 +158,8 @@ def lib():
         L.rt_batch_set_images.restype = ctypes.c_int
         L.rt_batch_set_images.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp),
                                           ctypes.POINTER(rt_image_desc), _vp, _vp, _vp]
+        L.rt_hamilton_rhs.restype = ctypes.c_int
+        L.rt_hamilton_rhs.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
         L.rt_measure_alu_peak.restype = ctypes.c_int
         L.rt_measure_alu_peak.argtypes = [ctypes.c_int64, ctypes.c_int64,
                                           ctypes.POINTER(ctypes.c_double), _vp]
@@ -515,6 +517,11 @@ def rt_batch_set_images(batch: Batch, stars, descs, image, img_status, ncross=No
     return r
 
 
+def rt_hamilton_rhs(star: Star, n, state, H, dydl, stream=None) -> int:
+    return _check(lib().rt_hamilton_rhs(star.handle, int(n), _ptr(state), _ptr(H), _ptr(dydl),
+                                        _stream(stream)))
+
+
 def rt_measure_alu_peak(iters64=7500, iters32=560000, stream=None) -> dict:
     """Measured FP64 / FP32 multiply-add throughput of the current GPU (the
     defaults run each timed kernel for ~0.15 s on a GB300)."""
@@ -539,4 +546,4 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune",
             "rt_batch_set_images", "rt_sample_conversion_surface_part", "rt_bin_part_max",
             "rt_bin_part_accumulate", "rt_bin_part_finalize", "rt_batch_set_norm",
-            "rt_measure_alu_peak"]
+            "rt_measure_alu_peak", "rt_hamilton_rhs"]

@@ -197,3 +197,87 @@ def test_backward_mixed_hands_floor_pixels_to_fp64():
     assert eq.mean() >= int(m[3][4]) / (16 * 16) - 1e-12
     done = np.isin(m[1], [rt.RAY_ESCAPED, rt.RAY_CAPTURED]) & (m[1] == f[1]) & (m[2] == f[2])
     assert abs(m[0][done].sum() - f[0][done].sum()) <= 1e-3 * abs(f[0][done].sum())
+
+
+@pytest.mark.parametrize("precision", [rt.PREC_FP64, rt.PREC_MIXED])
+def test_grazing_pairs_counted_to_the_closed_form_rim(oracle, precision):
+    """Flat space, isotropic spherical medium (omega_p^2 = 8 m_a^2 (R/r)^3):
+    the ray of impact parameter b reaches the resonance sphere r_c = 2 R iff
+    b <= b_rim = r_c sqrt(W^2 - 1) / W (its angular momentum b W is
+    conserved).  Just inside the rim its two crossings merge at the turning
+    point, between two samples of the sign of g: the search must still count
+    both, none just outside, and agree with the oracle's value.  At a
+    relative distance eps from the rim, g peaks at about -eps v0^2 (outside)
+    at the turning point, so the test resolves eps down to 1e-8 in FP64 and
+    1e-4 with FP32 stages (trajectory error ~1e-7); near the rim the pixel
+    value is sensitive to the ray as ~1 / (2 eps), which sets its tolerance."""
+    v0_kms = 30000.0
+    kw = dict(M_sun=0.0, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=0.3, m_a_eV=1e-5,
+              dispersion=1, fa_model=1, plasma=rt.PLASMA_RADIAL, plasma_a=8.0, v0_kms=v0_kms)
+    v0 = v0_kms / 299792.458
+    W = math.sqrt(1.0 + v0 * v0)
+    b_rim = 2.0 * math.sqrt(W * W - 1.0) / W
+    fp64 = precision == rt.PREC_FP64
+    rtol = 1e-10 if fp64 else 1e-8
+    eps_in = [1e-2, 1e-3, 1e-4] + ([1e-5, 1e-6, 1e-7, 1e-8] if fp64 else [])
+    sv = oracle.star_vector(**kw)
+    for eps in eps_in:
+        b = b_rim * (1.0 - eps)
+        # two pixels of a 2 x 1 image, centred at (-b, 0) and (b, 0)
+        img, st, nc, ctr = gpu_backward(kw, 2, 1, 0.7, 1e4, 2.0 * b, rtol=rtol,
+                                        precision=precision)
+        assert np.all(st == rt.RAY_ESCAPED)
+        assert np.all(nc == 2), (eps, nc)
+        if fp64 and eps >= 1e-6:
+            v, _, nco = oracle.backward_points(sv, oracle.trace_opts(rtol=rtol),
+                                               [[-b, 0.0], [b, 0.0]], 0.7)
+            assert np.all(nco == 2)
+            ref = v * (2.0 * b) * (4.0 * b)          # pixel area 2b x 4b
+            assert np.abs(img.ravel() / ref - 1).max() < 2e-10 / eps, (eps, img, ref)
+    for eps in ((1e-2, 1e-5, 1e-8) if fp64 else (1e-2, 1e-3, 1e-4)):
+        img, st, nc, ctr = gpu_backward(kw, 2, 1, 0.7, 1e4, 2.0 * b_rim * (1.0 + eps),
+                                        rtol=rtol, precision=precision)
+        assert np.all(nc == 0) and np.all(img == 0.0)
+
+
+def test_forward_and_backward_agree_at_the_equator_full_resolution():
+    """The paper's forward/backward consistency (Sec. 2.4) at sizes the
+    oracle cannot reach: the config-0 star (aligned Goldreich-Julian,
+    anisotropic), forward dP/dOmega binned over the flat equatorial band
+    87.5 - 92.5 deg from 2^21 rays, against the backward image total averaged
+    over the band's inclinations (four Gauss points in cos over 87.5 - 90 deg,
+    the star being mirror symmetric) at 2048 x 512 pixels over +-12 R.  Both
+    paths are parity-tested against the oracle pixel by pixel and ray by ray;
+    here they must agree with each other within 3 % plus three Monte-Carlo
+    errors (pixel-centre sums resolve the bright rims to ~3 % at this size)."""
+    from paper_2309_08655_gb300 import inputs as I
+    kw = I.star_config0()
+    n = 1 << 21
+    u = I.sample_uniforms(79, n)
+    star, st, w, s, _ = G.gpu_sample(kw, u)
+    G.gpu_trace(star, st, s, rtol=1e-9)
+    st_g, w_g, s_g = G.to_np(st, w, s)
+    esc = s_g == rt.RAY_ESCAPED
+    x = st_g[:3] / kw["R_km"]
+    r = np.linalg.norm(x, axis=0)
+    r[r == 0] = 1.0
+    nv = x / r
+    A = 1.0 - 2.0 * kw["M_sun"] * 1.4766250 / kw["R_km"] / r
+    ko = st_g[3:6] + (np.sqrt(np.clip(A, 1e-12, 1)) - 1) * (nv * st_g[3:6]).sum(0) * nv
+    th = np.degrees(np.arccos(np.clip(ko[2] / np.maximum(np.linalg.norm(ko, axis=0), 1e-300),
+                                      -1, 1)))
+    m = esc & (th >= 87.5) & (th < 92.5)
+    dOm = 2 * math.pi * 2 * math.cos(math.radians(87.5))
+    fwd = w_g[m].sum() / dOm
+    sig = np.std(np.where(m, w_g, 0.0)) * math.sqrt(n) / dOm
+    c, wc = np.polynomial.legendre.leggauss(4)
+    ca, cb = 0.0, math.cos(math.radians(87.5))
+    bwd = 0.0
+    for ci, wi in zip(c, wc):
+        cc = 0.5 * (ca + cb) + 0.5 * (cb - ca) * ci
+        img, st_i, nc, ctr = gpu_backward(kw, 2048, 512, math.acos(cc), 1e4, 12.0, rtol=1e-9)
+        assert not (nc[0].any() or nc[-1].any() or nc[:, 0].any() or nc[:, -1].any())
+        bwd += 0.5 * wi * img.sum()
+    print(f"equatorial band: forward {fwd:.5e} +- {sig:.1e}, backward {bwd:.5e}, "
+          f"ratio {bwd / fwd:.4f}")
+    assert abs(bwd / fwd - 1.0) < 0.03 + 3.0 * sig / fwd, (bwd, fwd, sig)

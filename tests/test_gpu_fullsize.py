@@ -151,9 +151,29 @@ def test_backward_full_size_image(oracle):
     assert good.mean() > 0.8
     assert np.array_equal(ng.ravel()[pick][good], na[good])
     assert (np.abs(got - ref) / scale)[good].max() <= 1e-8
-    # mixed precision against the FP64 image on the same pixels
+    # every pixel lit in either image, and its neighbours (where grazing rays
+    # lie): crossing counts equal to the oracle's exhaustive search, and the
+    # totals over those pixels
     im, sm, nm, cm = res[rt.PREC_MIXED]
+    lit2 = (ng > 0) | (nm > 0)
+    near = lit2.copy()
+    for ax in (0, 1):
+        for sh in (-1, 1):
+            near |= np.roll(lit2, sh, axis=ax)
+    jj, ii = np.nonzero(near)
+    bb = np.stack([-bmax + (ii + 0.5) * db, -bmax + (jj + 0.5) * db], 1)
+    vn, sn, nn = oracle.backward_points(sv, oracle.trace_opts(rtol=1e-10), bb, incl, D)
+    eq = ng[jj, ii] == nn
+    print(f"full-size image: {near.sum()} pixels at or next to the emission, crossing counts "
+          f"equal to the oracle on {eq.mean():.6f}; totals GPU {ig[jj, ii].sum():.6e} "
+          f"oracle {(vn * db * db).sum():.6e}")
+    assert eq.mean() >= 0.9999
+    tot_o = (vn * db * db).sum()
+    assert abs(ig[jj, ii].sum() / tot_o - 1) <= 1e-6
+    # mixed precision against the FP64 image on the same pixels
     same = (nm == ng) & (sm == sg)
+    print(f"mixed vs FP64: equal crossing counts and status on {same.mean():.7f}, "
+          f"image totals {im.sum():.6e} / {ig.sum():.6e}")
     assert same.mean() > 0.9999
     litm = same & (ng > 0)
     rel = np.abs(im[litm] - ig[litm]) / np.abs(ig[litm])
