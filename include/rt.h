@@ -171,6 +171,15 @@ typedef struct {
  *                     or more); results agree with index order to rounding and
  *                     are bitwise reproducible below 4M rays (unless more than
  *                     8192 rays qualify).  Not with images in a batch.
+ *   refill_min        work claiming of the persistent kernels: a warp claims new
+ *                     rays (pixels) from the global queue once at least this many of
+ *                     its lanes are free (1-32; 0 = auto: the batch's autotuned
+ *                     value, else 1 -- refill as soon as any lane is free)
+ *   rays_per_claim    queue entries a lane claims at a time (1-64; 0 = auto, as
+ *                     refill_min); a lane traces its claimed rays one after the
+ *                     other before it claims again.  Neither changes any ray's
+ *                     result with one lane per ray (tail = 1); in tail mode the
+ *                     set of rays that end in the six-lane kernel may change
  *   timestamps        NULL, or a device array of 1 + (number of instances) uint64
  *                     that the kernels stamp with the GPU's nanosecond global
  *                     timer: [0] the earliest start of a tracing launch (min),
@@ -183,6 +192,7 @@ typedef struct {
   double rtol, atol, r_out_over_R, lambda_max, r_capture_over_R;
   int32_t precision, max_steps, block, blocks_per_sm, tail, claim_order;
   uint64_t* timestamps;
+  int32_t refill_min, rays_per_claim;
 } rt_trace_opts;
 
 /* rt_timestamps_reset - [0] = UINT64_MAX, [1..n_instances] = 0, on stream. */
@@ -545,21 +555,31 @@ rt_status rt_graph_launch(rt_graph* graph, void* stream);
 void rt_graph_destroy(rt_graph* graph);
 
 /*
- * rt_batch_autotune - choose the trace kernel's launch shape (threads per
- * block, resident blocks per SM) for this batch and opts->precision by timing
- * every candidate the kernel's register budget allows on a sample: the first
- * rays_per_star sampled rays of every star (d_state/d_status as left by
- * rt_sample_batch; they are copied, not modified).  One warm-up run, then one
- * timed run per candidate (CUDA events).  The choice is stored in the batch
- * and used by rt_trace_batch whenever opts->block == 0.  Synchronous;
- * allocates and frees scratch for the sample.
- *   block_out, bps_out, ms_out (host, may be NULL): the winner and its time
+ * rt_batch_autotune - choose, for this batch and opts->precision, the trace
+ * launch's shape (threads per block, resident blocks per SM), its refill
+ * threshold and its rays per claim (rt_trace_opts.refill_min,
+ * rays_per_claim) by timing candidates on a sample, in three rounds: every
+ * shape the kernel's register budget allows (refill 1, 1 ray per claim), then
+ * refill thresholds 2, 4, 8, 16 at the best shape, then 2, 4, 8 rays per
+ * claim at the best threshold.  The sample: the first rays_per_star sampled
+ * rays of every star (d_state/d_status as left by rt_sample_batch; copied,
+ * not modified) and, when images are set (rt_batch_set_images), a coarse copy
+ * of every image -- the same plane in at most side x side pixels, side =
+ * ceil(sqrt(rays_per_star)), traced into scratch -- so that the launch tuned
+ * is the one rt_trace_batch runs (rays and pixels in one queue).  One warm-up
+ * run, then one timed run per candidate (CUDA events).  The choice is stored
+ * in the batch per precision and per kind of launch (rays only, or with
+ * images) and used by rt_trace_batch for the fields of opts left at 0.
+ * Synchronous; allocates and frees scratch for the sample.
+ *   block_out, bps_out, refill_out, claim_out, ms_out (host, may be NULL):
+ *   the winner and its time
  *   ncand_out (may be NULL): candidates timed; cand_ms (may be NULL): their
- *   times in ms, at most cand_cap of them
+ *   times in ms in the order above, at most cand_cap of them
  */
 rt_status rt_batch_autotune(rt_batch* batch, const double* d_state, const uint8_t* d_status,
                             const rt_trace_opts* opts, int32_t rays_per_star, int32_t* block_out,
-                            int32_t* bps_out, double* ms_out, int32_t* ncand_out, double* cand_ms,
+                            int32_t* bps_out, int32_t* refill_out, int32_t* claim_out,
+                            double* ms_out, int32_t* ncand_out, double* cand_ms,
                             int32_t cand_cap, void* stream);
 
 /*
@@ -653,7 +673,8 @@ rt_status rt_measure_alu_peak(int64_t iters64, int64_t iters32, double* out4, vo
 /* Thread-local message describing the last error of this thread. */
 const char* rt_last_error(void);
 
-/* Library version: major * 10000 + minor * 100 + patch. */
+/* Library version: major * 10000 + minor * 100 + patch (2.0.0: rt_trace_opts
+ * gained refill_min and rays_per_claim, rt_batch_autotune their outputs). */
 int32_t rt_version(void);
 
 #ifdef __cplusplus

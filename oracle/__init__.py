@@ -302,6 +302,29 @@ def star_constants(star):
                 n_inf_eV3=out[4], n_gj_coef_cm3=out[5])
 
 
+def line_flux(star, state, weight, status, incl, kappa):
+    """The smoothed line flux toward o = (sin incl, 0, cos incl) [W / sr]:
+    F = sum over ESCAPED rays of w K(khat . o), K(mu) = C exp(kappa (mu - 1)),
+    C = kappa / (2 pi (1 - exp(-2 kappa))), the von Mises-Fisher kernel of
+    unit mass on the sphere; khat the static orthonormal-frame momentum
+    direction at the end point (the direction binning uses, Sec. 2.2).  The
+    paper differentiates nothing: this is the functional whose gradient the
+    library's adjoint computes, written from its definition."""
+    sv = np.asarray(star, dtype=np.float64)
+    R_km = sv[STAR_KEYS.index("R_km")]
+    rs = 0.0 if sv[STAR_KEYS.index("prop_metric")] == 1 else star_constants(sv)["rs_over_R"]
+    esc = np.asarray(status) == RAY_ESCAPED
+    x = np.asarray(state)[:3, esc] / R_km
+    k = np.asarray(state)[3:6, esc]
+    r = np.sqrt((x * x).sum(0))
+    n = x / r
+    A = 1.0 - rs / r
+    ko = k + (np.sqrt(A) - 1.0) * (n * k).sum(0) * n
+    mu = (ko[0] * np.sin(incl) + ko[2] * np.cos(incl)) / np.sqrt((ko * ko).sum(0))
+    C = kappa / (2.0 * np.pi * -np.expm1(-2.0 * kappa))
+    return float((np.asarray(weight)[esc] * C * np.exp(kappa * (mu - 1.0))).sum())
+
+
 def bin_rays(star, state, weight, status, nth=64, nph=32, nnu=128, nu_lo=0.0, nu_hi=9.0):
     state = np.ascontiguousarray(state, dtype=np.float64)
     weight = np.ascontiguousarray(weight, dtype=np.float64)

@@ -132,7 +132,7 @@ extern "C" {
 
 const char* rt_last_error(void) { return g_err.c_str(); }
 
-int32_t rt_version(void) { return 100; }
+int32_t rt_version(void) { return 20000; }
 
 rt_status rt_init_star(const rt_star_params* p, rt_star** out) {
   if (out == nullptr) return fail(RT_EINVAL, "out is NULL");
@@ -344,7 +344,18 @@ static rt_status check_opts(const rt_trace_opts* o) {
   if (o->tail < 0 || o->tail > 31) return fail(RT_EINVAL, "tail must be in [0, 31]");
   if (o->claim_order != RT_CLAIM_COST && o->claim_order != RT_CLAIM_INDEX)
     return fail(RT_EINVAL, "unknown claim_order %d", o->claim_order);
+  if (o->refill_min < 0 || o->refill_min > 32)
+    return fail(RT_EINVAL, "refill_min must be in [0, 32]");
+  if (o->rays_per_claim < 0 || o->rays_per_claim > 64)
+    return fail(RT_EINVAL, "rays_per_claim must be in [0, 64]");
   return RT_OK;
+}
+
+// The work-claiming knobs of opts (0: the given defaults, e.g. autotuned).
+static void set_claiming(rtk::TraceParams& p, const rt_trace_opts* o, int refill_auto,
+                         int claim_auto) {
+  p.refill_min = o->refill_min > 0 ? o->refill_min : (refill_auto > 0 ? refill_auto : 1);
+  p.claim_size = o->rays_per_claim > 0 ? o->rays_per_claim : (claim_auto > 0 ? claim_auto : 1);
 }
 
 rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t* d_status,
@@ -393,6 +404,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.claim_status = rtk::RAY_READY;
   p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST) ? 1 : 0;
   set_express(p);
+  set_claiming(p, o, 1, 1);
   cudaError_t e;
   if (rigid) {
     e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
@@ -759,8 +771,10 @@ struct rt_batch {
   bool all_empty = true;
   std::vector<int64_t> norm;          // per-star weight normalisation (empty: the counts)
   bool rigid = false;                 // every star RT_ROTATION_RIGID (rt_trace_rot.cu)
-  int tuned_block[2] = {0, 0};        // autotuned launch shape per precision (0 = default)
-  int tuned_bps[2] = {0, 0};
+  // autotuned launch per precision and kind (rays only / with images); 0 = default
+  struct Tuned {
+    int block = 0, bps = 0, refill = 0, claim = 0;
+  } tuned[2][2];
   double* d_park = nullptr;           // tail-mode park buffer (allocated on first use)
   int64_t park_cap = 0;
   // backward images traced in the same launch (rt_batch_set_images)
@@ -771,6 +785,9 @@ struct rt_batch {
   int64_t* d_img_off = nullptr;
   unsigned long long* d_promo_n = nullptr;
   int32_t* d_promo = nullptr;
+  // host copies of the images' geometry and stars (the autotuner's coarse copies)
+  std::vector<rt_image_desc> h_desc;
+  std::vector<const rt_star*> h_img_star;
 };
 
 extern "C" {
@@ -864,6 +881,8 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
     if ((st = check_dev_ptr(d_img_status, "d_img_status")) != RT_OK) return st;
     if (d_ncross && (st = check_dev_ptr(d_ncross, "d_ncross")) != RT_OK) return st;
   }
+  std::vector<rt_image_desc> h_desc(descs, descs + nimg);
+  std::vector<const rt_star*> h_star(stars, stars + nimg);
   for (int32_t j = 0; j < nimg; ++j) {
     const rt_image_desc& d = descs[j];
     const rtk::StarDev& h = stars[j]->h;
@@ -891,6 +910,8 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
   b->d_promo = nullptr;
   b->nimg = 0;
   b->npix = 0;
+  b->h_desc.clear();
+  b->h_img_star.clear();
   rt_status out = RT_OK;
   if (nimg > 0) {
     const size_t tb = ((sizeof(rtk::BackParams) * nimg + 255) / 256) * 256;
@@ -911,6 +932,8 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
         b->d_promo = (int32_t*)(c + 256 + tb + ob);
         b->nimg = nimg;
         b->npix = npix;
+        b->h_desc.swap(h_desc);
+        b->h_img_star.swap(h_star);
       } else {
         cudaFree(blk);
       }
@@ -1013,8 +1036,10 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
                 ? 1 : 0;
   set_express(p);
   const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
-  const int blk = o->block > 0 ? o->block : b->tuned_block[pi];
-  const int bps = o->block > 0 ? o->blocks_per_sm : b->tuned_bps[pi];
+  const rt_batch::Tuned& tu = b->tuned[pi][b->npix > 0 ? 1 : 0];
+  const int blk = o->block > 0 ? o->block : tu.block;
+  const int bps = o->block > 0 ? o->blocks_per_sm : tu.bps;
+  set_claiming(p, o, tu.refill, tu.claim);
   cudaError_t e;
   if (b->rigid) {   // no images: rt_batch_set_images rejects rotating stars
     e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
@@ -1035,21 +1060,20 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
     t.list = nullptr;
     t.list_n = nullptr;
     t.ts = o->timestamps ? (unsigned long long*)o->timestamps + 1 + b->stars.size() : nullptr;
-    // the autotuned shape is the rays-only kernel's: explicit shapes only
-    const int ublk = o->block > 0 ? o->block : 0, ubps = o->block > 0 ? o->blocks_per_sm : 0;
     if (o->precision == RT_PREC_MIXED) {
       e = cudaMemsetAsync(b->d_promo_n, 0, sizeof(unsigned long long), (cudaStream_t)stream);
-      if (e == cudaSuccess) e = rtk::launch_batch_mixed(p, t, ublk, ubps, (cudaStream_t)stream);
+      if (e == cudaSuccess) e = rtk::launch_batch_mixed(p, t, blk, bps, (cudaStream_t)stream);
       if (e != cudaSuccess) return cuda_fail(e, "mixed batch kernel");
       // FP64: the promoted rays from where they stopped, the listed pixels anew
       p.claim_status = rtk::RAY_PROMOTED;
+      p.refill_min = p.claim_size = 1;
       t.list = b->d_promo;
       t.list_n = b->d_promo_n;
       e = rtk::launch_batch_fp64(p, t, 0, 0, (cudaStream_t)stream);
       if (e != cudaSuccess) return cuda_fail(e, "batch kernel (promoted rays and pixels)");
       return RT_OK;
     }
-    e = rtk::launch_batch_fp64(p, t, ublk, ubps, (cudaStream_t)stream);
+    e = rtk::launch_batch_fp64(p, t, blk, bps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
     return RT_OK;
   }
@@ -1057,6 +1081,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
     e = rtk::launch_trace_mixed(p, blk, bps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
     p.claim_status = rtk::RAY_PROMOTED;
+    p.refill_min = p.claim_size = 1;
     e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
     return RT_OK;
@@ -1237,17 +1262,23 @@ void rt_graph_destroy(rt_graph* g) {
 
 rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d_status,
                             const rt_trace_opts* o, int32_t rays_per_star, int32_t* block_out,
-                            int32_t* bps_out, double* ms_out, int32_t* ncand_out,
-                            double* cand_ms, int32_t cand_cap, void* stream) {
+                            int32_t* bps_out, int32_t* refill_out, int32_t* claim_out,
+                            double* ms_out, int32_t* ncand_out, double* cand_ms,
+                            int32_t cand_cap, void* stream) {
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
   if (rays_per_star < 1) return fail(RT_EINVAL, "rays_per_star must be >= 1");
-  if (b->N == 0) return fail(RT_EINVAL, "empty batch");
+  if (b->N == 0 && b->npix == 0) return fail(RT_EINVAL, "empty batch");
   if (b->rigid) return fail(RT_EUNSUPPORTED, "the autotuner needs RT_ROTATION_SNAPSHOT stars");
-  if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
-  if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  if (b->N > 0) {
+    if ((st = check_dev_ptr(d_state, "d_state")) != RT_OK) return st;
+    if ((st = check_dev_ptr(d_status, "d_status")) != RT_OK) return st;
+  }
+  if (b->npix > 0 && o->lambda_max != 0.0)
+    return fail(RT_EUNSUPPORTED, "lambda_max must be 0 for a batch with images");
   const bool mixed = (o->precision == RT_PREC_MIXED);
+  const bool img = (b->npix > 0);
   const size_t nst = b->stars.size();
   // the first rays_per_star rays of every star, in a batch of their own
   std::vector<int64_t> off(nst + 1, 0);
@@ -1256,11 +1287,31 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
     off[s + 1] = off[s] + (cnt < rays_per_star ? cnt : rays_per_star);
   }
   const int64_t M = off[nst];
-  if (M == 0) return fail(RT_EINVAL, "no rays to tune on");
+  // coarse copies of the images: the same planes in at most side x side pixels
+  const int side = (int)std::ceil(std::sqrt((double)rays_per_star));
+  const int nimg = img ? b->nimg : 0;
+  std::vector<rtk::BackParams> tbl((size_t)nimg);
+  std::vector<int64_t> ioff((size_t)nimg + 1, 0);
+  for (int j = 0; j < nimg; ++j) {
+    const rt_image_desc& d = b->h_desc[j];
+    const int nx = d.nx < side ? d.nx : side, ny = d.ny < side ? d.ny : side;
+    ioff[j + 1] = ioff[j] + (int64_t)nx * ny;
+  }
+  const int64_t P = ioff[nimg];
+  if (M + P == 0) return fail(RT_EINVAL, "nothing to tune on");
   cudaStream_t cs = (cudaStream_t)stream;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_st = al((size_t)RT_STATE_ROWS * M * sizeof(double));
+  const size_t b_s = al((size_t)M);
+  const size_t b_off = al((nst + 1) * sizeof(int64_t));
+  const size_t b_tbl = al(sizeof(rtk::BackParams) * (size_t)nimg);
+  const size_t b_ioff = al(((size_t)nimg + 1) * sizeof(int64_t));
+  const size_t b_img = al((size_t)P * sizeof(double));
+  const size_t b_ist = al((size_t)P);
+  const size_t b_promo = al((size_t)(P > 0 ? P : 1) * sizeof(int32_t));
+  const size_t bytes = 256 + 2 * b_st + 2 * b_s + b_off + b_tbl + b_ioff + b_img + b_ist + 256 +
+                       b_promo;
   void* blk = nullptr;
-  const size_t bytes = 256 + 2 * (size_t)RT_STATE_ROWS * M * sizeof(double) + 2 * (size_t)M +
-                       (nst + 1) * sizeof(int64_t) + 64;
   cudaError_t e = cudaMalloc(&blk, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1268,11 +1319,28 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   }
   char* q = (char*)blk;
   unsigned long long* queue = (unsigned long long*)q;
-  double* st0 = (double*)(q + 256);
-  double* st1 = st0 + (size_t)RT_STATE_ROWS * M;
-  uint8_t* s0 = (uint8_t*)(st1 + (size_t)RT_STATE_ROWS * M);
-  uint8_t* s1 = s0 + M;
-  int64_t* doff = (int64_t*)(((uintptr_t)(s1 + M) + 7) & ~(uintptr_t)7);
+  q += 256;
+  double* st0 = (double*)q;
+  q += b_st;
+  double* st1 = (double*)q;
+  q += b_st;
+  uint8_t* s0 = (uint8_t*)q;
+  q += b_s;
+  uint8_t* s1 = (uint8_t*)q;
+  q += b_s;
+  int64_t* doff = (int64_t*)q;
+  q += b_off;
+  rtk::BackParams* d_tbl = (rtk::BackParams*)q;
+  q += b_tbl;
+  int64_t* d_ioff = (int64_t*)q;
+  q += b_ioff;
+  double* d_iimg = (double*)q;
+  q += b_img;
+  uint8_t* d_ist = (uint8_t*)q;
+  q += b_ist;
+  unsigned long long* promo_n = (unsigned long long*)q;
+  q += 256;
+  int32_t* promo = (int32_t*)q;
   for (size_t s = 0; s < nst && e == cudaSuccess; ++s) {
     const int64_t m = off[s + 1] - off[s];
     if (m == 0) continue;
@@ -1285,6 +1353,28 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(doff, off.data(), (nst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                         cs);
+  for (int j = 0; j < nimg; ++j) {
+    const rt_image_desc& d = b->h_desc[j];
+    const rtk::StarDev& h = b->h_img_star[j]->h;
+    rtk::BackParams& bp = tbl[j];
+    memset(&bp, 0, sizeof(bp));
+    bp.s = h;
+    bp.nx = d.nx < side ? d.nx : side;
+    bp.ny = d.ny < side ? d.ny : side;
+    bp.incl = d.incl_rad;
+    bp.D = d.dist_over_R;
+    bp.bmax = d.bmax_over_R;
+    image_setup(h, bp.nx, bp.ny, d.bmax_over_R, d.Lc_cut_km, &bp.W, &bp.img_scale, &bp.Lc_cut);
+    bp.image = d_iimg + ioff[j];
+    bp.status = d_ist + ioff[j];
+    bp.ncross = nullptr;
+  }
+  if (e == cudaSuccess && nimg > 0)
+    e = cudaMemcpyAsync(d_tbl, tbl.data(), sizeof(rtk::BackParams) * nimg,
+                        cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && nimg > 0)
+    e = cudaMemcpyAsync(d_ioff, ioff.data(), ioff.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) {
     cudaFree(blk);
@@ -1309,60 +1399,108 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   p.lambda_max = o->lambda_max;
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
-  // candidates: block sizes the kernel's launch bounds allow, every resident count
+  rtk::ImgTable t;
+  t.img = d_tbl;
+  t.off = d_ioff;
+  t.nimg = nimg;
+  t.npix = P;
+  t.promo = promo;
+  t.promo_n = promo_n;
+  t.list = nullptr;
+  t.list_n = nullptr;
+  t.ts = nullptr;
+  // round 1 candidates: block sizes the kernel's launch bounds allow, every
+  // resident count
   std::vector<std::pair<int, int>> cand;
   const int blocks[3] = {mixed ? 64 : 32, mixed ? 128 : 64, mixed ? 256 : 128};
   for (int bi = 0; bi < 3; ++bi) {
     int occ = 0;
-    e = mixed ? rtk::occupancy_mixed(blocks[bi], &occ) : rtk::occupancy_fp64(blocks[bi], &occ);
+    e = img ? (mixed ? rtk::occupancy_batch_mixed(blocks[bi], &occ)
+                     : rtk::occupancy_batch_fp64(blocks[bi], &occ))
+            : (mixed ? rtk::occupancy_mixed(blocks[bi], &occ)
+                     : rtk::occupancy_fp64(blocks[bi], &occ));
     if (e != cudaSuccess) break;
     for (int k = 1; k <= occ; ++k) cand.push_back({blocks[bi], k});
   }
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ev1);
-  auto run = [&](int block, int bps, float* ms) -> cudaError_t {
-    cudaError_t r = cudaMemcpyAsync(st1, st0, (size_t)RT_STATE_ROWS * M * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, cs);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(s1, s0, M, cudaMemcpyDeviceToDevice, cs);
+  auto run = [&](int block, int bps, int refill, int claim, float* ms) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    if (M > 0) {
+      r = cudaMemcpyAsync(st1, st0, (size_t)RT_STATE_ROWS * M * sizeof(double),
+                          cudaMemcpyDeviceToDevice, cs);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(s1, s0, M, cudaMemcpyDeviceToDevice, cs);
+    }
+    if (r == cudaSuccess && img) r = cudaMemsetAsync(promo_n, 0, sizeof(unsigned long long), cs);
     if (r == cudaSuccess) r = cudaEventRecord(ev0, cs);
     p.claim_status = rtk::RAY_READY;
-    if (r == cudaSuccess)
-      r = mixed ? rtk::launch_trace_mixed(p, block, bps, cs) : rtk::launch_trace_fp64(p, block, bps, cs);
+    p.refill_min = refill;
+    p.claim_size = claim;
+    t.list = nullptr;
+    t.list_n = nullptr;
+    if (r == cudaSuccess) {
+      if (img)
+        r = mixed ? rtk::launch_batch_mixed(p, t, block, bps, cs)
+                  : rtk::launch_batch_fp64(p, t, block, bps, cs);
+      else
+        r = mixed ? rtk::launch_trace_mixed(p, block, bps, cs)
+                  : rtk::launch_trace_fp64(p, block, bps, cs);
+    }
     if (r == cudaSuccess && mixed) {
+      // the FP64 pass over the promoted rays (and the handed-over pixels)
       p.claim_status = rtk::RAY_PROMOTED;
-      r = rtk::launch_trace_fp64(p, 0, 0, cs);
+      p.refill_min = p.claim_size = 1;
+      if (img) {
+        t.list = promo;
+        t.list_n = promo_n;
+        r = rtk::launch_batch_fp64(p, t, 0, 0, cs);
+      } else {
+        r = rtk::launch_trace_fp64(p, 0, 0, cs);
+      }
     }
     if (r == cudaSuccess) r = cudaEventRecord(ev1, cs);
     if (r == cudaSuccess) r = cudaEventSynchronize(ev1);
     if (r == cudaSuccess) r = cudaEventElapsedTime(ms, ev0, ev1);
     return r;
   };
-  int best_b = 0, best_k = 0;
-  float best = 3.0e38f, ms = 0.0f;
-  if (e == cudaSuccess && !cand.empty()) e = run(cand[0].first, cand[0].second, &ms);   // warm-up
+  rt_batch::Tuned best;
+  float best_ms = 3.0e38f, ms = 0.0f;
   int nc = 0;
-  for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
-    e = run(cand[c].first, cand[c].second, &ms);
-    if (e != cudaSuccess) break;
+  auto trial = [&](int block, int bps, int refill, int claim) -> cudaError_t {
+    cudaError_t r = run(block, bps, refill, claim, &ms);
+    if (r != cudaSuccess) return r;
     if (cand_ms && nc < cand_cap) cand_ms[nc] = ms;
     ++nc;
-    if (ms < best) {
-      best = ms;
-      best_b = cand[c].first;
-      best_k = cand[c].second;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.block = block;
+      best.bps = bps;
+      best.refill = refill;
+      best.claim = claim;
     }
-  }
+    return cudaSuccess;
+  };
+  if (e == cudaSuccess && !cand.empty()) e = run(cand[0].first, cand[0].second, 1, 1, &ms);
+  for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c)
+    e = trial(cand[c].first, cand[c].second, 1, 1);
+  const int refills[4] = {2, 4, 8, 16}, claims[3] = {2, 4, 8};
+  const rt_batch::Tuned shape = best;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    e = trial(shape.block, shape.bps, refills[i], 1);
+  const int refill = best.refill;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    e = trial(shape.block, shape.bps, refill, claims[i]);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   cudaFree(blk);
   if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
-  const int pi = mixed ? 1 : 0;
-  b->tuned_block[pi] = best_b;
-  b->tuned_bps[pi] = best_k;
-  if (block_out) *block_out = best_b;
-  if (bps_out) *bps_out = best_k;
-  if (ms_out) *ms_out = best;
+  b->tuned[mixed ? 1 : 0][img ? 1 : 0] = best;
+  if (block_out) *block_out = best.block;
+  if (bps_out) *bps_out = best.bps;
+  if (refill_out) *refill_out = best.refill;
+  if (claim_out) *claim_out = best.claim;
+  if (ms_out) *ms_out = best_ms;
   if (ncand_out) *ncand_out = nc;
   return RT_OK;
 }

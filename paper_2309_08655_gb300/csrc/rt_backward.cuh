@@ -267,7 +267,8 @@ __device__ __forceinline__ float screen_slope(const Screen& s, const float* x, c
   }
   if (s.disp == DISP_ISO) return Pp;
   // G = 1 - t, t = A Kpb^2 iW2 / (3 mu^2 + 1), Kpb = mu kr (1 + 2 sqrt(A)) - m.k
-  const float sA = sqrtf(A);
+  const float rsA = rsqrtf(A);
+  const float sA = A * rsA;
   const float Ap = s.rs * ir * lr;                                // dA/dth
   const float kr = n0 * k[0] + n1 * k[1] + n2 * k[2];
   const float krp = ((xp[0] - n0 * rp) * k[0] + (xp[1] - n1 * rp) * k[1] +
@@ -276,25 +277,29 @@ __device__ __forceinline__ float screen_slope(const Screen& s, const float* x, c
   const float km = s.m0 * k[0] + s.m1 * k[1] + s.m2 * k[2];
   const float kmp = s.m0 * kp[0] + s.m1 * kp[1] + s.m2 * kp[2];
   const float Kpb = mu * kr * (1.0f + 2.0f * sA) - km;
-  const float Kpbp = (mup * kr + mu * krp) * (1.0f + 2.0f * sA) + mu * kr * Ap / sA - kmp;
-  const float bb = 3.0f * mu * mu + 1.0f;
-  const float t = A * Kpb * Kpb * s.iW2 / bb;
-  const float tp = s.iW2 * (Ap * Kpb * Kpb + 2.0f * A * Kpb * Kpbp) / bb - t * 6.0f * mu * mup / bb;
+  const float Kpbp = (mup * kr + mu * krp) * (1.0f + 2.0f * sA) + mu * kr * Ap * rsA - kmp;
+  const float ibb = __fdividef(1.0f, 3.0f * mu * mu + 1.0f);      // only the sign is used
+  const float t = A * Kpb * Kpb * s.iW2 * ibb;
+  const float tp = (s.iW2 * (Ap * Kpb * Kpb + 2.0f * A * Kpb * Kpbp) - t * 6.0f * mu * mup) * ibb;
   return Pp * (1.0f - t) - P * tp;
 }
 
 // The continuous extension's displacement d(th) = th (p2 + u (p3 + th (p4 +
 // u p5))), u = 1 - th, and its derivative dd/dth, in FP32.
 __device__ __forceinline__ void dense32(float t, const float* p2, const float* p3,
-                                        const float* p4, const float* p5, float* d, float* dp) {
+                                        const float* p4, const float* p5, float* d) {
+  const float u = 1.0f - t;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d[i] = t * (p2[i] + u * (p3[i] + t * (p4[i] + u * p5[i])));
+}
+__device__ __forceinline__ void dense32_slope(float t, const float* p2, const float* p3,
+                                              const float* p4, const float* p5, float* dp) {
   const float u = 1.0f - t;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float Q3 = p4[i] + u * p5[i];
     const float Q2 = p3[i] + t * Q3;
-    const float Q1 = p2[i] + u * Q2;
-    d[i] = t * Q1;
-    dp[i] = Q1 + t * (u * (Q3 - t * p5[i]) - Q2);
+    dp[i] = p2[i] + u * Q2 + t * (u * (Q3 - t * p5[i]) - Q2);
   }
 }
 
@@ -475,21 +480,26 @@ struct CrossingAcc {
     // pieces whose dip is searched after the loop (bit q - 1), and their sign
     unsigned dips = 0u, dip_neg = 0u;
     {
-      float d[6], dp[6], xs[3], ks[3];
-      dense32(0.0f, p2, p3, p4, p5, d, dp);
+      const float d[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      float xs[3], ks[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         xs[i] = y32[i];
         ks[i] = y32[3 + i];
       }
       (void)screen_sign(sc, xs, d, ks, &NA);
-      slA = (fabsf(NA) < SLOPE_NEAR) ? screen_slope(sc, xs, d, ks, dp, dp + 3) : 0.0f;
+      slA = 0.0f;
+      if (fabsf(NA) < SLOPE_NEAR) {
+        float dp[6];
+        dense32_slope(0.0f, p2, p3, p4, p5, dp);
+        slA = screen_slope(sc, xs, d, ks, dp, dp + 3);
+      }
     }
     for (int q = 1; q <= BACK_SUBDIV; ++q) {
       const double th1 = (double)q / BACK_SUBDIV;
       const float t = (float)q * (1.0f / BACK_SUBDIV);
-      float d[6], dp[6], xs[3], ks[3];
-      dense32(t, p2, p3, p4, p5, d, dp);
+      float d[6], xs[3], ks[3];
+      dense32(t, p2, p3, p4, p5, d);
       if (q == BACK_SUBDIV) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) d[i] = p2[i];          // the step's own increment
@@ -506,16 +516,20 @@ struct CrossingAcc {
       const bool nearB = fabsf(NB) < SLOPE_NEAR;
       float slB = 0.0f;
       if (nearB || fabsf(NA) < SLOPE_NEAR) {
+        float dp[6];
         if (!(fabsf(NA) < SLOPE_NEAR)) {             // slope at th0 not formed yet
-          float d0[6], dp0[6], x0[3], k0[3];
-          dense32(t - 1.0f / BACK_SUBDIV, p2, p3, p4, p5, d0, dp0);
+          const float t0 = t - 1.0f / BACK_SUBDIV;
+          float d0[6], x0[3], k0[3];
+          dense32(t0, p2, p3, p4, p5, d0);
+          dense32_slope(t0, p2, p3, p4, p5, dp);
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             x0[i] = y32[i] + d0[i];
             k0[i] = y32[3 + i] + d0[3 + i];
           }
-          slA = screen_slope(sc, x0, d0, k0, dp0, dp0 + 3);
+          slA = screen_slope(sc, x0, d0, k0, dp, dp + 3);
         }
+        dense32_slope(t, p2, p3, p4, p5, dp);
         slB = screen_slope(sc, xs, d, ks, dp, dp + 3);
       }
       bool negB;

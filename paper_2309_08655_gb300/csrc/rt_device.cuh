@@ -264,6 +264,46 @@ __device__ __forceinline__ T ham_value(const RayConst<T>& c, const T* x, const T
   return H + P - P * A * Kp * Kp * c.iW2;
 }
 
+// Claiming work from the global queue of a persistent kernel.  item: -1 the
+// lane needs work, -2 the queue is exhausted for it, >= 0 the item in flight.
+// A lane that needs work first takes the next entry of the chunk it claimed
+// last (claim_size consecutive queue entries); the lanes whose chunks are
+// spent claim fresh chunks together -- one atomicAdd per warp -- once at least
+// refill_min of them wait, or at once when no lane of the warp holds an item.
+// take(e) loads queue entry e and returns its item index, or -1 for an entry
+// that is not to be traced.  refill_min = claim_size = 1 claims one entry per
+// waiting lane at every call (a warp refills as soon as any lane is free).
+struct ClaimChunk {
+  int64_t next = 0, end = 0;
+};
+
+template <class Take>
+__device__ __forceinline__ void claim_items(unsigned long long* queue, int64_t nq,
+                                            int refill_min, int claim_size, int64_t& item,
+                                            ClaimChunk& ch, Take&& take) {
+  constexpr unsigned ALL = 0xffffffffu;
+  while (item == -1 && ch.next < ch.end) item = take(ch.next++);
+  const bool need = (item == -1);
+  const unsigned mneed = __ballot_sync(ALL, need);
+  if (!mneed) return;
+  if (__popc(mneed) < refill_min && __ballot_sync(ALL, item >= 0) != 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mneed) - 1;
+  unsigned long long base = 0;
+  if (lane == leader)
+    base = atomicAdd(queue, (unsigned long long)__popc(mneed) * (unsigned long long)claim_size);
+  base = __shfl_sync(ALL, base, leader);
+  if (need) {
+    ch.next = (int64_t)base + (int64_t)__popc(mneed & ((1u << lane) - 1u)) * claim_size;
+    ch.end = ch.next + claim_size < nq ? ch.next + claim_size : nq;
+    if (ch.next >= nq) {
+      item = -2;
+      return;
+    }
+    while (item == -1 && ch.next < ch.end) item = take(ch.next++);
+  }
+}
+
 // Nanosecond global timer of the GPU (for per-instance completion times).
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -132,7 +132,7 @@ struct NoHook {
 // bracket did not halve over two steps, run to the last representable th.
 // Returns lo (side_val >= 0); *hi_out the first th past it.
 template <class S>
-__device__ __forceinline__ double last_nonneg(S& side_val, double flo, double fhi,
+__device__ __forceinline__ double last_nonneg(const S& side_val, double flo, double fhi,
                                               double* hi_out) {
   double lo = 0.0, hi = 1.0;
   int last = 0;

@@ -54,6 +54,10 @@ struct TraceParams {
   // in launches long enough that the express lane ends before the bulk (the
   // tail launch waits for both); shorter ones keep them one lane per ray
   int xpark = 0;
+  // work claiming (claim_items): a warp refills once refill_min lanes wait;
+  // a lane claims claim_size consecutive queue entries at a time
+  int refill_min = 1;
+  int claim_size = 1;
 };
 constexpr int64_t XPARK_MIN_RAYS = (int64_t)4 << 20;
 constexpr int COST_BUCKETS = 3;
@@ -130,6 +134,8 @@ cudaError_t launch_bin_finalize(const BinParams& p, cudaStream_t stream);
 // Resident blocks per SM of the trace kernels at a block size.
 cudaError_t occupancy_fp64(int block, int* occ);
 cudaError_t occupancy_mixed(int block, int* occ);
+cudaError_t occupancy_batch_fp64(int block, int* occ);
+cudaError_t occupancy_batch_mixed(int block, int* occ);
 
 // Backward image-plane tracing (one ray per pixel, ny x nx row-major).
 struct BackLaunch {

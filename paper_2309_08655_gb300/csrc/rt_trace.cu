@@ -183,31 +183,19 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       }
     }
   }
+  ClaimChunk ch;
   for (;;) {
-    const bool need = (ray == -1);
-    const unsigned mneed = __ballot_sync(FULL, need);
-    if (mneed) {
-      const int leader = __ffs(mneed) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
-      base = __shfl_sync(FULL, base, leader);
-      if (need) {
-        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        const int pass = p.order ? (int)(idx / p.n) : 0;
-        const int64_t i = idx - (int64_t)pass * p.n;
-        if (idx >= nq) {
-          ray = -2;
-        } else if (p.status[i] != p.claim_status ||
-                   (p.order && cost_bucket(p.stars[find_star(p, i)], p.state, p.n, i) != pass)) {
-          ray = -1;
-        } else {
-          ray = i;
-          load_lane(p, i, L);
-          na0 = L.na;
-          nr0 = L.nr;
-        }
-      }
-    }
+    claim_items(p.queue, nq, p.refill_min, p.claim_size, ray, ch, [&](int64_t idx) -> int64_t {
+      const int pass = p.order ? (int)(idx / p.n) : 0;
+      const int64_t i = idx - (int64_t)pass * p.n;
+      if (p.status[i] != p.claim_status ||
+          (p.order && cost_bucket(p.stars[find_star(p, i)], p.state, p.n, i) != pass))
+        return -1;
+      load_lane(p, i, L);
+      na0 = L.na;
+      nr0 = L.nr;
+      return i;
+    });
     const unsigned live = __ballot_sync(FULL, ray != -2);
     if (live == 0) break;
     if (p.park) {
@@ -406,48 +394,35 @@ __global__ void __launch_bounds__(128) batch_fp64_kernel(TraceParams p, ImgTable
   long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0;
   int na0 = 0, nr0 = 0;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  ClaimChunk ch;
   for (;;) {
-    const bool need = (item == -1);
-    const unsigned mneed = __ballot_sync(FULL, need);
-    if (mneed) {
-      const int leader = __ffs(mneed) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
-      base = __shfl_sync(FULL, base, leader);
-      if (need) {
-        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        if (idx >= total) {
-          item = -2;
-        } else if (idx < nf) {
-          if (p.status[idx] != p.claim_status) {
-            item = -1;
-          } else {
-            item = idx;
-            isp = false;
-            ray = idx;
-            load_lane(tp, idx, L);
-            na0 = L.na;
-            nr0 = L.nr;
-            tp.r_out = p.r_out;
-            hk.on = false;
-          }
-        } else {
-          const int64_t q = idx - nf;
-          const int64_t g = t.list ? (int64_t)t.list[q] : q;
-          img = find_image(t, g);
-          pix = g - t.off[img];
-          const BackParams& bp = t.img[img];
-          load_pixel(bp, pix, L, p.rtol, p.atol);
-          na0 = nr0 = 0;
-          // escaped once back at the distance the ray started from
-          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
-          hk.on = true;
-          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
-          isp = true;
-          item = idx;
-        }
+    claim_items(p.queue, total, p.refill_min, p.claim_size, item, ch,
+                [&](int64_t idx) -> int64_t {
+      if (idx < nf) {
+        if (p.status[idx] != p.claim_status) return -1;
+        isp = false;
+        ray = idx;
+        load_lane(tp, idx, L);
+        na0 = L.na;
+        nr0 = L.nr;
+        tp.r_out = p.r_out;
+        hk.on = false;
+        return idx;
       }
-    }
+      const int64_t q = idx - nf;
+      const int64_t g = t.list ? (int64_t)t.list[q] : q;
+      img = find_image(t, g);
+      pix = g - t.off[img];
+      const BackParams& bp = t.img[img];
+      load_pixel(bp, pix, L, p.rtol, p.atol);
+      na0 = nr0 = 0;
+      // escaped once back at the distance the ray started from
+      tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+      hk.on = true;
+      hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
+      isp = true;
+      return idx;
+    });
     if (__ballot_sync(FULL, item != -2) == 0) break;
     if (item >= 0) {
       const int st = advance(tp, L, hk);
@@ -593,6 +568,10 @@ cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream) 
 
 cudaError_t occupancy_fp64(int block, int* occ) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, trace_fp64_kernel, block, 0);
+}
+
+cudaError_t occupancy_batch_fp64(int block, int* occ) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_fp64_kernel, block, 0);
 }
 
 cudaError_t launch_trace_fp64(const TraceParams& p, int block, int blocks_per_sm,

@@ -471,26 +471,13 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
   LaneM L;
   long long acc = 0, rej = 0, traced = 0, esc = 0, promoted = 0;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  ClaimChunk ch;
   for (;;) {
-    const bool need = (ray == -1);
-    const unsigned mneed = __ballot_sync(FULL, need);
-    if (mneed) {
-      const int leader = __ffs(mneed) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
-      base = __shfl_sync(FULL, base, leader);
-      if (need) {
-        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        if (idx >= p.n) {
-          ray = -2;
-        } else if (p.status[idx] != RAY_READY) {
-          ray = -1;
-        } else {
-          ray = idx;
-          load_lane_m(p, idx, L);
-        }
-      }
-    }
+    claim_items(p.queue, p.n, p.refill_min, p.claim_size, ray, ch, [&](int64_t idx) -> int64_t {
+      if (p.status[idx] != RAY_READY) return -1;
+      load_lane_m(p, idx, L);
+      return idx;
+    });
     if (__ballot_sync(FULL, ray != -2) == 0) break;
     if (ray >= 0) {
       NoHookM nh;
@@ -729,44 +716,31 @@ __global__ void __launch_bounds__(256) batch_mixed_kernel(TraceParams p, ImgTabl
   hk.on = false;
   long long acc = 0, rej = 0, done = 0, esc = 0, nc = 0, promoted = 0;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  ClaimChunk ch;
   for (;;) {
-    const bool need = (item == -1);
-    const unsigned mneed = __ballot_sync(FULL, need);
-    if (mneed) {
-      const int leader = __ffs(mneed) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(p.queue, (unsigned long long)__popc(mneed));
-      base = __shfl_sync(FULL, base, leader);
-      if (need) {
-        const int64_t idx = (int64_t)base + __popc(mneed & ((1u << lane) - 1u));
-        if (idx >= total) {
-          item = -2;
-        } else if (idx < nf) {
-          if (p.status[idx] != RAY_READY) {
-            item = -1;
-          } else {
-            item = idx;
-            isp = false;
-            ray = idx;
-            load_lane_m(tp, idx, L);
-            tp.r_out = p.r_out;
-            hk.on = false;
-          }
-        } else {
-          g = idx - nf;
-          img = find_image(t, g);
-          pix = g - t.off[img];
-          const BackParams& bp = t.img[img];
-          load_pixel_m(bp, pix, L, hk.c, (float)p.rtol, (float)p.atol);
-          // escaped once back at the distance the ray started from
-          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
-          hk.on = true;
-          hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
-          isp = true;
-          item = idx;
-        }
+    claim_items(p.queue, total, p.refill_min, p.claim_size, item, ch,
+                [&](int64_t idx) -> int64_t {
+      if (idx < nf) {
+        if (p.status[idx] != RAY_READY) return -1;
+        isp = false;
+        ray = idx;
+        load_lane_m(tp, idx, L);
+        tp.r_out = p.r_out;
+        hk.on = false;
+        return idx;
       }
-    }
+      g = idx - nf;
+      img = find_image(t, g);
+      pix = g - t.off[img];
+      const BackParams& bp = t.img[img];
+      load_pixel_m(bp, pix, L, hk.c, (float)p.rtol, (float)p.atol);
+      // escaped once back at the distance the ray started from
+      tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+      hk.on = true;
+      hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
+      isp = true;
+      return idx;
+    });
     if (__ballot_sync(FULL, item != -2) == 0) break;
     if (item >= 0) {
       const int st = advance_m(tp, L, hk);
@@ -873,6 +847,10 @@ cudaError_t launch_backward_mixed(const BackParams& bp, cudaStream_t stream) {
 
 cudaError_t occupancy_mixed(int block, int* occ) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, trace_mixed_kernel, block, 0);
+}
+
+cudaError_t occupancy_batch_mixed(int block, int* occ) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_mixed_kernel, block, 0);
 }
 
 cudaError_t launch_trace_mixed(const TraceParams& p, int block, int blocks_per_sm,

@@ -55,7 +55,8 @@ class rt_trace_opts(ctypes.Structure):
         "rtol", "atol", "r_out_over_R", "lambda_max", "r_capture_over_R"]] + [
         (k, ctypes.c_int32) for k in ["precision", "max_steps", "block", "blocks_per_sm", "tail",
                                       "claim_order"]] + [
-        ("timestamps", ctypes.c_void_p)]
+        ("timestamps", ctypes.c_void_p), ("refill_min", ctypes.c_int32),
+        ("rays_per_claim", ctypes.c_int32)]
 
 
 _lib = None
@@ -134,6 +135,8 @@ def lib():
         L.rt_batch_autotune.argtypes = [_vp, _vp, _vp, ctypes.POINTER(rt_trace_opts),
                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _vp]
@@ -211,7 +214,8 @@ def make_params(**kw) -> rt_star_params:
 
 def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capture_over_R=1.0,
               precision=PREC_FP64, max_steps=100000, block=0, blocks_per_sm=0,
-              timestamps=None, tail=0, claim_order=0) -> rt_trace_opts:
+              timestamps=None, tail=0, claim_order=0, refill_min=0,
+              rays_per_claim=0) -> rt_trace_opts:
     o = rt_trace_opts()
     o.rtol = rtol
     o.atol = rtol if atol is None else atol
@@ -225,6 +229,8 @@ def make_opts(rtol=1e-10, atol=None, r_out_over_R=1000.0, lambda_max=0.0, r_capt
     o.tail = tail
     o.claim_order = claim_order
     o.timestamps = _ptr(timestamps)
+    o.refill_min = refill_min
+    o.rays_per_claim = rays_per_claim
     return o
 
 
@@ -421,14 +427,17 @@ def rt_graph_destroy(graph: Graph) -> None:
 def rt_batch_autotune(batch, state, status, opts, rays_per_star=2048, stream=None) -> dict:
     blk = ctypes.c_int32(0)
     bps = ctypes.c_int32(0)
+    refill = ctypes.c_int32(0)
+    claim = ctypes.c_int32(0)
     ms = ctypes.c_double(0.0)
     nc = ctypes.c_int32(0)
     cand = (ctypes.c_double * 64)()
     _check(lib().rt_batch_autotune(batch.handle, _ptr(state), _ptr(status), ctypes.byref(opts),
                                    int(rays_per_star), ctypes.byref(blk), ctypes.byref(bps),
-                                   ctypes.byref(ms), ctypes.byref(nc), cand, 64,
-                                   _stream(stream)))
-    return {"block": blk.value, "blocks_per_sm": bps.value, "ms": ms.value,
+                                   ctypes.byref(refill), ctypes.byref(claim), ctypes.byref(ms),
+                                   ctypes.byref(nc), cand, 64, _stream(stream)))
+    return {"block": blk.value, "blocks_per_sm": bps.value, "refill_min": refill.value,
+            "rays_per_claim": claim.value, "ms": ms.value,
             "candidates_ms": list(cand)[:min(nc.value, 64)]}
 
 

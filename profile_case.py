@@ -1,10 +1,10 @@
 """Small, self-contained forward case for kernel profiling (ncu) and quick timing.
 
-    python -m paper_2309_08655_gb300.profile_case --precision fp64 --n 1024
-    python -m paper_2309_08655_gb300.profile_case --mode backward --n 65536
-    python -m paper_2309_08655_gb300.profile_case --mode adjoint --n 4096
-    python -m paper_2309_08655_gb300.profile_case --config config1 --rotating --n 65536
-    python -m paper_2309_08655_gb300.profile_case --config config1 --claim-order cost --n 65536
+    python profile_case.py --precision fp64 --n 1024
+    python profile_case.py --mode backward --n 65536
+    python profile_case.py --mode adjoint --n 4096
+    python profile_case.py --config config1 --rotating --n 65536
+    python profile_case.py --config config1 --claim-order cost --n 65536
 
 Forward: samples n rays of the aligned 200 km-surface star (seed 0), traces
 them once in the requested precision (one persistent trace launch, after one
@@ -26,9 +26,9 @@ import json
 import numpy as np
 import torch
 
-from . import inputs as I
-from . import rt
-from .build import build
+from paper_2309_08655_gb300 import inputs as I
+from paper_2309_08655_gb300 import rt
+from paper_2309_08655_gb300.build import build
 
 
 def main():

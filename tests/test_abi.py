@@ -36,13 +36,15 @@ def test_every_declared_symbol_is_exported(L):
 def test_struct_layouts_match_header():
     # 10 doubles, 8 int32, 1 double / 5 doubles, 4 int32 (no padding surprises)
     assert ctypes.sizeof(rt.rt_star_params) == 10 * 8 + 8 * 4 + 8
-    assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 6 * 4 + 8   # + the timestamps pointer
+    # + the timestamps pointer and the two work-claiming knobs after it
+    assert ctypes.sizeof(rt.rt_trace_opts) == 5 * 8 + 6 * 4 + 8 + 2 * 4
+    assert rt.rt_trace_opts.refill_min.offset == 72
     assert rt.rt_star_params.plasma_a.offset == 112
     assert rt.rt_star_params.rotation.offset == 108
 
 
 def test_version_and_error_paths_without_gpu(L):
-    assert rt.rt_version() >= 100
+    assert rt.rt_version() >= 20000
     with pytest.raises(rt.RtError) as e:
         rt.Star(rt.make_params(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, m_a_eV=-1.0))
     assert e.value.status == rt.RT_EINVAL and "m_a_eV" in str(e.value)

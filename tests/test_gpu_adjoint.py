@@ -7,7 +7,8 @@ angles) at rtol 1e-12, so that the step-size controller's discrete decisions
 move F by much less than the difference quotient resolves.  The adjoint is
 the exact gradient of the discrete scheme at frozen decisions; the bar is
 1e-5 relative per component (1e-4 against the oracle, whose F differs from
-the GPU's only by rounding but is evaluated with its own root finder).
+the GPU's only by rounding but is evaluated with its own root finder), also
+at the benchmark's sharp kernel kappa = (64/pi)^2, one theta-bin wide.
 """
 import math
 
@@ -63,25 +64,14 @@ def _fd(fn, p, h):
 
 
 def _oracle_F(oracle, base, p, u, kappa, rtol):
+    """F by the oracle: its own sampling, trace and line-flux functional."""
     kw = dict(base)
     kw.update(m_a_eV=float(p[0]), B0_G=float(p[1]), theta_m=float(p[2]), M_sun=float(p[3]),
               R_km=float(p[4]))
-    incl = float(p[5])
     sv = oracle.star_vector(**kw)
     st, w, s = oracle.sample(sv, u)
     oracle.trace_forward(sv, oracle.trace_opts(rtol=rtol), st, s)
-    esc = s == oracle.RAY_ESCAPED
-    rs = oracle.star_constants(sv)["rs_over_R"]
-    x = st[:3, esc] / kw["R_km"]
-    k = st[3:6, esc] / kw["m_a_eV"]
-    r = np.sqrt((x * x).sum(0))
-    n = x / r
-    A = 1.0 - rs / r
-    kn = (n * k).sum(0)
-    ko = k + (np.sqrt(A) - 1.0) * kn * n
-    mu = (ko[0] * math.sin(incl) + ko[2] * math.cos(incl)) / np.sqrt((ko * ko).sum(0))
-    C = kappa / (2.0 * math.pi * -math.expm1(-2.0 * kappa))
-    return float((w[esc] * C * np.exp(kappa * (mu - 1.0))).sum())
+    return oracle.line_flux(sv, st, w, s, float(p[5]), kappa)
 
 
 def test_adjoint_matches_finite_differences():
@@ -184,3 +174,27 @@ def test_line_flux_rejects_unknown_grad_precision():
     u = torch.from_numpy(I.sample_uniforms(4, 8)).to(G.dev())
     with pytest.raises(ValueError):
         flux.line_flux(_p0(kw), kw, u, KAPPA, grad_precision="fp16")
+
+
+def test_adjoint_matches_oracle_at_the_benchmark_kappa(oracle):
+    """The benchmark's functional: kappa = (64/pi)^2, a kernel one theta-bin
+    (0.05 rad) wide, so each ray's term and its gradient vary 100 times
+    faster with its end direction than at kappa = 4.  4096 rays toward
+    inclination 1.1 rad (the benchmark's), oracle central differences at
+    rtol 1e-12: 1e-4 per component."""
+    kappa = (64.0 / math.pi) ** 2
+    kw = _base()
+    n = 4096
+    u_np = I.sample_uniforms(8, n)
+    u = torch.from_numpy(u_np).to(G.dev())
+    p = _p0(kw, incl=1.1).requires_grad_(True)
+    F = flux.line_flux(p, kw, u, kappa)
+    F.backward()
+    g_adj = p.grad.numpy()
+    pd = p.detach()
+    F_or = _oracle_F(oracle, kw, pd.numpy(), u_np, kappa, 1e-10)
+    assert F_or > 0 and abs(F_or - float(F.detach())) <= 1e-8 * abs(F_or)
+    g_or = _fd(lambda q: _oracle_F(oracle, kw, q.numpy(), u_np, kappa, RTOL_FD), pd, _steps(pd))
+    rel = np.abs(g_adj - g_or) / np.maximum(np.abs(g_or), 1e-300)
+    print("kappa = (64/pi)^2: adjoint", g_adj, "oracle FD", g_or, "rel", rel)
+    assert np.all(rel < 1e-4), (g_adj, g_or, rel)

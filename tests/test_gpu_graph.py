@@ -86,11 +86,54 @@ def test_autotune_choice_is_valid_and_result_invariant():
     tune = rt.rt_batch_autotune(b, B["st"], B["s"], opts, rays_per_star=128)
     assert tune["block"] in (32, 64, 128)
     assert tune["blocks_per_sm"] >= 1
-    assert len(tune["candidates_ms"]) >= 3
+    assert tune["refill_min"] in (1, 2, 4, 8, 16)
+    assert tune["rays_per_claim"] in (1, 2, 4, 8)
+    assert len(tune["candidates_ms"]) >= 3 + 4 + 3       # shapes, thresholds, claim sizes
     assert tune["ms"] == pytest.approx(min(tune["candidates_ms"]))
-    got = _direct(b, u, B, opts)               # opts.block == 0: the tuned shape
+    got = _direct(b, u, B, opts)               # opts fields 0: the tuned launch
     for k in ("st", "s", "hist", "oor", "ctr"):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+
+
+@pytest.mark.parametrize("refill, claim", [(1, 1), (8, 1), (1, 4), (16, 8), (32, 64)])
+def test_refill_threshold_and_claim_size_do_not_change_results(refill, claim):
+    """One lane per ray (tail = 1): every ray's integration is independent of
+    the lane and the moment it is claimed, so any refill threshold and claim
+    size give bitwise the same end states (FP64 and mixed precision)."""
+    for prec in (rt.PREC_FP64, rt.PREC_MIXED):
+        b, stars, u, B, rtol = _setup(prec)
+        ref = _direct(b, u, B, rt.make_opts(rtol=rtol, precision=prec, tail=1))
+        got = _direct(b, u, B, rt.make_opts(rtol=rtol, precision=prec, tail=1,
+                                            refill_min=refill, rays_per_claim=claim))
+        for k in ("st", "s", "hist", "oor", "ctr"):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=(prec, k))
+
+
+def test_autotune_with_images_tunes_the_joint_launch():
+    """With backward images set, the autotuner times rays and (coarse copies
+    of) pixels in one launch and stores the choice for that launch; results of
+    the tuned launch equal those of the default one."""
+    b, stars, u, B, rtol = _setup(rt.PREC_MIXED)
+    kw = dict(M_sun=1.4, R_km=10.0, B0_G=1e14, P_s=1.0, theta_m=0.5, psi=0.4, m_a_eV=1e-5)
+    istars = [rt.Star(rt.make_params(**kw)), rt.Star(rt.make_params(**dict(kw, theta_m=0.2)))]
+    descs = [(40, 30, 1.0, 1e4, 2.0, 0.0), (17, 23, 0.4, 1e4, 2.0, 0.0)]
+    P = sum(d[0] * d[1] for d in descs)
+    img = torch.zeros(P, dtype=torch.float64, device=G.dev())
+    ist = torch.zeros(P, dtype=torch.uint8, device=G.dev())
+    rt.rt_batch_set_images(b, istars, descs, img, ist)
+    opts = rt.make_opts(rtol=rtol, precision=rt.PREC_MIXED)
+    ref = _direct(b, u, B, opts)
+    ref_img = img.cpu().numpy().copy()
+    rt.rt_sample_batch(b, u, B["st"], B["w"], B["s"])
+    tune = rt.rt_batch_autotune(b, B["st"], B["s"], opts, rays_per_star=64)
+    assert tune["block"] in (64, 128, 256) and tune["blocks_per_sm"] >= 1
+    assert tune["refill_min"] in (1, 2, 4, 8, 16) and tune["rays_per_claim"] in (1, 2, 4, 8)
+    img.zero_()
+    got = _direct(b, u, B, opts)
+    for k in ("st", "s", "hist", "oor", "ctr"):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    np.testing.assert_array_equal(img.cpu().numpy(), ref_img)
+    assert ref_img.sum() > 0
 
 
 def test_instance_timestamps():

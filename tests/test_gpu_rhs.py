@@ -8,7 +8,7 @@ differentiates its own smooth continuation), on the conversion surface itself
 (samples of the resonance), and far out; every plasma model and both
 dispersions.  Both sides evaluate the same function in FP64 in different
 ways, so they agree to rounding: 1e-12 relative per block (dx/dl, dk/dl),
-H to 1e-13 of the size of its largest term.
+H to 1e-12 of the size of its largest term.
 """
 import math
 import zlib
@@ -133,7 +133,7 @@ def test_rhs_matches_oracle_dual_numbers(oracle, name):
     rng = np.random.default_rng(zlib.crc32(name.encode()))
     ex, ek, eH = _compare(oracle, kw, _points(kw, rng))
     assert ex.max() < 1e-12 and ek.max() < 1e-12, (ex.max(), ek.max())
-    assert eH.max() < 1e-13, eH.max()
+    assert eH.max() < 1e-12, eH.max()
 
 
 @pytest.mark.parametrize("name", ["gj_aligned_aniso", "gj_misaligned_aniso", "gj_misaligned_iso"])
@@ -142,7 +142,7 @@ def test_rhs_on_both_flanks_of_the_null_cone(oracle, name):
     rng = np.random.default_rng(7)
     ex, ek, eH = _compare(oracle, kw, _null_cone_points(kw, rng))
     assert ex.max() < 1e-12 and ek.max() < 1e-12, (ex.max(), ek.max())
-    assert eH.max() < 1e-13
+    assert eH.max() < 1e-12
 
 
 @pytest.mark.parametrize("name", ["gj_aligned_aniso", "gj_misaligned_aniso", "twisted_aniso"])
