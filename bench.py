@@ -129,6 +129,8 @@ def _args():
                     help="skip the rigidly rotating magnetosphere workload")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 256-instance uneven batch measurement")
+    ap.add_argument("--no-equal-accuracy", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison at equal flux accuracy")
     return ap.parse_args()
 
 
@@ -380,7 +382,8 @@ def run_ours(args):
                              precision=rt.PREC_FP64, max_steps=cfg["max_steps"],
                              claim_order=CLAIM[args.claim_order]),
         "mixed": rt.make_opts(rtol=cfg["rtol_mixed"], r_out_over_R=cfg["r_out_over_R"],
-                              precision=rt.PREC_MIXED, max_steps=cfg["max_steps"]),
+                              precision=rt.PREC_MIXED, max_steps=cfg["max_steps"],
+                              claim_order=CLAIM[args.claim_order]),
     }
     ev_t = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -505,6 +508,11 @@ def run_ours(args):
         return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
 
     res["mixed"]["flux_l1_vs_fp64"] = l1(hists["mixed"], hists["fp64"])
+    equal_acc = None
+    if ws == 1 and not args.no_equal_accuracy:
+        equal_acc = _equal_accuracy(rt, batch, u, st, w, s, hist, oor, ctr, cfg, stream,
+                                    hists["mixed"], res["mixed"]["roofline"]["trace_ms_per_launch"],
+                                    l1)
     # the oracle on the same workload: the CPU baseline and, when it covers the
     # whole workload, the flux error of each precision against it
     cpu = None
@@ -577,6 +585,7 @@ def run_ours(args):
         "roofline": HP["roofline"],
         "fp64": res["fp64"], "mixed": res["mixed"],
         "mixed_vs_fp64_rays_per_s": res["mixed"]["rays_per_s"] / res["fp64"]["rays_per_s"],
+        "mixed_vs_fp64_equal_accuracy": equal_acc,
         "backward": back,
         "adjoint_forward_ratio": adj["adjoint_forward_ratio"] if adj else None,
         "adjoint": adj,
@@ -591,6 +600,51 @@ def run_ours(args):
         "clocks": clk,
     }
     print(json.dumps(line, default=_plain))
+
+
+def _equal_accuracy(rt, batch, u, st, w, s, hist, oor, ctr, cfg, stream, hist_mixed,
+                    ms_mixed, l1):  # ms_mixed: the mixed path's trace call
+    """The mixed path against the plain FP64 path at equal binned-flux
+    accuracy.  Reference: the FP64 flux at rtol 1e-12; the mixed path's
+    distance from it (rtol 1e-8); the FP64 path's distance and time at rtol
+    1e-8, 1e-9, 1e-10; the loosest FP64 rtol at least as close to the
+    reference as the mixed path (the tightest one tried if none is) sets the
+    FP64 time of the ratio.  One launch per step for both, as the mixed
+    path's own timing."""
+    import torch
+    nth, nph, nnu = NBINS
+
+    def run(rtol):
+        o = rt.make_opts(rtol=rtol, r_out_over_R=cfg["r_out_over_R"], precision=rt.PREC_FP64,
+                         max_steps=cfg["max_steps"] * 4, claim_order=CLAIM["cost"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctr.zero_()
+        rt.rt_sample_batch(batch, u, st, w, s, stream=stream)
+        e0.record(stream)
+        rt.rt_trace_batch(batch, st, s, None, None, ctr, o, stream=stream)
+        e1.record(stream)
+        rt.rt_bin_batch(batch, st, w, s, nth, nph, nnu, cfg["nu_lo"], cfg["nu_hi"], hist, oor,
+                        stream=stream)
+        torch.cuda.synchronize()
+        return hist.cpu().numpy().copy(), e0.elapsed_time(e1), int(ctr[0])
+
+    h_ref, t_ref, _ = run(1e-12)
+    d_mixed = l1(hist_mixed, h_ref)
+    rows = []
+    for rtol in (1e-8, 1e-9, 1e-10):
+        h, t, acc = run(rtol)
+        rows.append({"rtol": rtol, "flux_l1_vs_rtol1e-12": l1(h, h_ref), "trace_ms": t,
+                     "accepted_steps": acc})
+    ok = [r for r in rows if r["flux_l1_vs_rtol1e-12"] <= d_mixed]
+    pick = ok[0] if ok else rows[-1]
+    return {"reference": "FP64 rtol 1e-12 binned flux (trace %.0f ms)" % t_ref,
+            "mixed_rtol": cfg["rtol_mixed"], "mixed_flux_l1_vs_rtol1e-12": d_mixed,
+            "mixed_trace_ms": ms_mixed, "fp64": rows,
+            "fp64_rtol_at_equal_accuracy": pick["rtol"],
+            "fp64_at_least_as_accurate": bool(ok),
+            "speedup_mixed_vs_fp64": pick["trace_ms"] / ms_mixed,
+            "launch": "one persistent launch per step, both paths (FP64 cost-ordered claims); "
+                      "times of the trace call (persistent launch and its second pass)"}
 
 
 def _endpoint_errors(ends, or_states, nper):

@@ -158,14 +158,15 @@ typedef struct {
  *                     throughout.  The handle owns the park buffer (allocated on
  *                     first use, 33 MB on GB300).
  *   claim_order       RT_CLAIM_INDEX (0): rays are claimed in index order.
- *                     RT_CLAIM_COST (1): the FP64 forward kernels claim rays by
+ *                     RT_CLAIM_COST (1): the forward kernels (FP64 and the FP32
+ *                     stages of RT_PREC_MIXED) claim rays by
  *                     predicted cost -- first those that start within 1e-3 rad,
  *                     then 1e-2 rad, of the Goldreich-Julian null cone (the rays
  *                     that can be guided along it for tens of thousands of
  *                     steps), then the rest -- so that the longest rays run from
  *                     the start of the launch.  In tail mode (tail != 1) the
  *                     rays within 1e-3 rad (up to 8192 per call, nearest first)
- *                     are traced six lanes per ray from the start on a few SMs
+ *                     of an FP64 call are traced six lanes per ray from the start on a few SMs
  *                     of their own (the express lane), and the others one lane
  *                     per ray (parking their last rays only in calls of 4M rays
  *                     or more); results agree with index order to rounding and
@@ -446,7 +447,7 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *     ckpt_bytes out (host, may be NULL): bytes of checkpoint storage used
  *   Needs RT_PLASMA_GJ, M_sun > 0 and B0_G > 0.  Synchronous: allocates the
  *   checkpoint store (sum over rays of (nacc/32 + 2) x 104 B), segment
- *   scratch (2.5 KB per resident thread: about 100 MB on GB300) and 69 B per
+ *   scratch (13 KB per resident thread: about 500 MB on GB300) and 69 B per
  *   ray, and frees them before returning; RT_ENOMEM if that fails.
  */
 rt_status rt_flux_value(const rt_star* star, int64_t n, const double* d_state,

@@ -402,8 +402,8 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
-  p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST) ? 1 : 0;
-  set_express(p);
+  p.order = (o->claim_order == RT_CLAIM_COST) ? 1 : 0;
+  if (o->precision == RT_PREC_FP64) set_express(p);
   set_claiming(p, o, 1, 1);
   cudaError_t e;
   if (rigid) {
@@ -415,6 +415,8 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
     e = rtk::launch_trace_mixed(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
     p.claim_status = rtk::RAY_PROMOTED;   // FP64 pass over the promoted rays
+    p.order = 0;
+    p.xrec = nullptr;
     e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
     return RT_OK;
@@ -650,7 +652,7 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
     cudaFree(flg);
   };
   int64_t total = 0;
-  const size_t seg_n = (size_t)a.grid * a.block * rtk::CK * 10;
+  const size_t seg_n = (size_t)a.grid * a.block * rtk::CK * rtk::SEGREC;
   if ((e = cudaMalloc(&off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
       (e = cudaMalloc(&seg, seg_n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&Fr, n * sizeof(double))) != cudaSuccess ||
@@ -1031,10 +1033,10 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.r_capture = o->r_capture_over_R;
   p.max_steps = o->max_steps;
   p.claim_status = rtk::RAY_READY;
-  // cost-ordered claims for the FP64 rays-only launches (not with images)
-  p.order = (o->precision == RT_PREC_FP64 && o->claim_order == RT_CLAIM_COST && b->npix == 0)
-                ? 1 : 0;
-  set_express(p);
+  // cost-ordered claims for the rays-only launches (not with images); the
+  // express lane for FP64 ones
+  p.order = (o->claim_order == RT_CLAIM_COST && b->npix == 0) ? 1 : 0;
+  if (o->precision == RT_PREC_FP64) set_express(p);
   const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
   const rt_batch::Tuned& tu = b->tuned[pi][b->npix > 0 ? 1 : 0];
   const int blk = o->block > 0 ? o->block : tu.block;
@@ -1082,6 +1084,8 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
     if (e != cudaSuccess) return cuda_fail(e, "mixed trace kernel");
     p.claim_status = rtk::RAY_PROMOTED;
     p.refill_min = p.claim_size = 1;
+    p.order = 0;
+    p.xrec = nullptr;
     e = rtk::launch_trace_fp64(p, 0, 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "trace kernel (promoted rays)");
     return RT_OK;

@@ -20,7 +20,8 @@
 //    backwards step by step: the discrete adjoint of a Dormand-Prince step at
 //    its accepted step size, with J^T v of the right-hand side f = Omega grad H
 //    obtained from one forward-mode product, J^T v = Omega J (Omega v), and the
-//    q-derivatives from the same dual evaluation;
+//    q-derivatives from the same dual evaluation (q = r_s, the omega_p^2
+//    coefficient, and the magnetic axis along dm/dtheta_m: four tangents);
 //  * where the Goldreich-Julian branch switches on the null cone c(x) = 0
 //    (the right-hand side jumps there), the saltation matrix
 //    S = I + (f_new - f_old) grad c^T / (grad c . f_old) is applied, together
@@ -62,7 +63,9 @@ using sampling::sample_core;
 
 typedef Dual<6> D6;
 
-constexpr int SEGREC = 10;   // y[6], h, sig, flags, spare
+// A segment record's stage derivatives start here (SEGREC, rt_internal.h): the
+// reverse sweep reads them back instead of re-forming the stages.
+constexpr int SEG_K = 10;
 enum { FL_FLIP_BEFORE = 1, FL_FLIP_AFTER = 2, FL_ESCAPE = 4 };
 
 struct AdjParams {
@@ -111,21 +114,30 @@ __device__ __forceinline__ RayConst<T> cast_const(const RayConst<double>& c) {
   return o;
 }
 
-// J^T v and v . df/dq at y (q = rs, cp, m0, m1, m2), from one dual evaluation
-// in the scalar type T.
+// Constants q of the ray equations that the parameters move: r_s / R, the
+// omega_p^2 coefficient, and the misalignment theta_m, which moves the
+// magnetic axis m along dm/dtheta_m (the ray's rotation phase is fixed).
+constexpr int NQ = 3;
+enum { Q_RS = 0, Q_CP, Q_THM };
+
+// J^T v and v . df/dq at y, from one dual evaluation in the scalar type T
+// with 1 + NQ tangents: the direction Omega v, and q (m along dm).
 template <class T>
-__device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* y, const T* v, T* out,
-                                     T* qbar) {
-  typedef Dual<6, T> DT;
+__device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* dm, const T* y, const T* v,
+                                     T* out, T* qbar) {
+  typedef Dual<1 + NQ, T> DT;
   RayConst<DT> cd;
-  cd.rs = DT::var(c.rs, 1);
-  cd.cp = DT::var(c.cp, 2);
+  cd.rs = DT::var(c.rs, 1 + Q_RS);
+  cd.cp = DT::var(c.cp, 1 + Q_CP);
   cd.pa = DT(c.pa);
   cd.W2 = DT(c.W2);
   cd.iW2 = DT(c.iW2);
-  cd.m0 = DT::var(c.m0, 3);
-  cd.m1 = DT::var(c.m1, 4);
-  cd.m2 = DT::var(c.m2, 5);
+  cd.m0 = DT(c.m0);
+  cd.m1 = DT(c.m1);
+  cd.m2 = DT(c.m2);
+  cd.m0.d[1 + Q_THM] = dm[0];
+  cd.m1.d[1 + Q_THM] = dm[1];
+  cd.m2.d[1 + Q_THM] = dm[2];
   cd.sig = DT(c.sig);
   cd.disp = c.disp;
   cd.plasma = c.plasma;
@@ -147,7 +159,7 @@ __device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* y, const T* 
     out[3 + j] = -f[j].d[0];
   }
 #pragma unroll
-  for (int m = 1; m < 6; ++m) {
+  for (int m = 1; m <= NQ; ++m) {
     T s = T(0);
 #pragma unroll
     for (int j = 0; j < 6; ++j) s += v[j] * f[j].d[m];
@@ -158,7 +170,7 @@ __device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* y, const T* 
 // Adjoint of a branch switch at y from sig_old to -sig_old:
 // ybar <- S^T ybar, and the crossing's dependence on the magnetic axis.
 template <class T>
-__device__ void saltation(RayConst<T> c, const T* y, T sig_old, T* ybar, T* qbar) {
+__device__ void saltation(RayConst<T> c, const T* dm, const T* y, T sig_old, T* ybar, T* qbar) {
   T fo[6], fn[6];
   c.sig = sig_old;
   rhs_t(c, y, fo);
@@ -178,10 +190,10 @@ __device__ void saltation(RayConst<T> c, const T* y, T sig_old, T* ybar, T* qbar
   ybar[0] += s * gc0;
   ybar[1] += s * gc1;
   ybar[2] += s * gc2;
+  // the crossing moves with the axis: dc/dm . dm/dtheta_m
   const T r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-  qbar[2] += s * T(3) * y[2] * y[0];
-  qbar[3] += s * T(3) * y[2] * y[1];
-  qbar[4] += s * (T(3) * y[2] * y[2] - r2);
+  qbar[Q_THM] += s * (T(3) * y[2] * y[0] * dm[0] + T(3) * y[2] * y[1] * dm[1] +
+                      (T(3) * y[2] * y[2] - r2) * dm[2]);
 }
 
 // Discrete adjoint of one accepted Dormand-Prince step from y with step h, in
@@ -191,8 +203,9 @@ __device__ void saltation(RayConst<T> c, const T* y, T sig_old, T* ybar, T* qbar
 // Escape: the step ends at the theta* of the continuous extension where
 // |x| = r_out, and ybar_e is the adjoint there.
 template <class T>
-__device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape, T r_out,
-                             const T* ybar_e, T* ybar, T* qbar) {
+__device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
+                             const double* Krec, bool escape, T r_out, const T* ybar_e, T* ybar,
+                             T* qbar) {
   const T a21 = T(DP::a21), a31 = T(DP::a31), a32 = T(DP::a32), a41 = T(DP::a41),
           a42 = T(DP::a42), a43 = T(DP::a43), a51 = T(DP::a51), a52 = T(DP::a52),
           a53 = T(DP::a53), a54 = T(DP::a54), a61 = T(DP::a61), a62 = T(DP::a62),
@@ -200,29 +213,23 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape,
   const T b1 = T(DP::b1), b3 = T(DP::b3), b4 = T(DP::b4), b5 = T(DP::b5), b6 = T(DP::b6);
   const T d1 = T(DP::d1), d3 = T(DP::d3), d4 = T(DP::d4), d5 = T(DP::d5), d6 = T(DP::d6),
           d7 = T(DP::d7);
+  // the stages as the replay formed them (FP64 record, in the sweep's
+  // precision), and the stage inputs Y_s = y + h sum_j a_sj K_j
   T K[7][6], Y[6][6], t[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Y[0][i] = y[i];
-  rhs_t(c, Y[0], K[0]);
+  for (int s = 0; s < 7; ++s)
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Y[1][i] = y[i] + h * (a21 * K[0][i]);
-  rhs_t(c, Y[1], K[1]);
+    for (int i = 0; i < 6; ++i) K[s][i] = T(Krec[6 * s + i]);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) Y[2][i] = y[i] + h * (a31 * K[0][i] + a32 * K[1][i]);
-  rhs_t(c, Y[2], K[2]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 6; ++i) {
+    Y[0][i] = y[i];
+    Y[1][i] = y[i] + h * (a21 * K[0][i]);
+    Y[2][i] = y[i] + h * (a31 * K[0][i] + a32 * K[1][i]);
     Y[3][i] = y[i] + h * (a41 * K[0][i] + a42 * K[1][i] + a43 * K[2][i]);
-  rhs_t(c, Y[3], K[3]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
     Y[4][i] = y[i] + h * (a51 * K[0][i] + a52 * K[1][i] + a53 * K[2][i] + a54 * K[3][i]);
-  rhs_t(c, Y[4], K[4]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
     Y[5][i] = y[i] + h * (a61 * K[0][i] + a62 * K[1][i] + a63 * K[2][i] + a64 * K[3][i] +
                           a65 * K[4][i]);
-  rhs_t(c, Y[5], K[5]);
+  }
   T yn[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i)
@@ -234,7 +241,6 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape,
 #pragma unroll
     for (int i = 0; i < 6; ++i) kb[s][i] = T(0);
   if (escape) {
-    rhs_t(c, yn, K[6]);
     T r2v[6], r3[6], r4[6], r5[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -298,7 +304,7 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape,
       ynb[i] = r2b[i];
       yb[i] -= r2b[i];
     }
-    rhs_vjp(c, yn, kb[6], t, qbar);
+    rhs_vjp(c, dm, yn, kb[6], t, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) ynb[i] += t[i];
   } else {
@@ -327,7 +333,7 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* y, T h, bool escape,
                      {a61, a62, a63, a64, a65}};
   for (int s = 5; s >= 0; --s) {
     T Yb[6];
-    rhs_vjp(c, Y[s], kb[s], Yb, qbar);
+    rhs_vjp(c, dm, Y[s], kb[s], Yb, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       yb[i] += Yb[i];
@@ -417,14 +423,14 @@ __device__ void load_ck(const double* ck, Lane& L) {
   rhs64(L.c, L.y, L.f0);
 }
 
-// Records every accepted step of a segment replay.
+// Records every accepted step of a segment replay, with its stages.
 struct RecHook {
   double* seg;
   int nrec, cap;
   bool pend_flip;
-  __device__ void on_accept(const Lane& L, const double* y, const double*, const double*,
-                            const double*, const double*, const double*, const double*,
-                            const double*, double h) {
+  __device__ void on_accept(const Lane& L, const double* y, const double*, const double* k1,
+                            const double* k2, const double* k3, const double* k4,
+                            const double* k5, const double* k6, const double* k7, double h) {
     if (nrec < cap) {
       double* r = seg + (int64_t)nrec * SEGREC;
 #pragma unroll
@@ -432,6 +438,17 @@ struct RecHook {
       r[6] = h;
       r[7] = L.c.sig;
       r[8] = pend_flip ? (double)FL_FLIP_BEFORE : 0.0;
+      double* K = r + SEG_K;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        K[j] = k1[j];
+        K[6 + j] = k2[j];
+        K[12 + j] = k3[j];
+        K[18 + j] = k4[j];
+        K[24 + j] = k5[j];
+        K[30 + j] = k6[j];
+        K[36 + j] = k7[j];
+      }
     }
     pend_flip = false;
     ++nrec;
@@ -535,19 +552,22 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
     return;
   }
   // functional at the escape point
-  double ybar[6], qbar[5] = {0, 0, 0, 0, 0}, rsb, dmu_di;
+  double ybar[6], qbar[NQ] = {0, 0, 0}, rsb, dmu_di;
   const double w = sv.w;
   double Kv;
   const double Fi = flux_kernel_value(P, L.y, w, ybar, &rsb, &dmu_di, &Kv);
-  qbar[0] += rsb;
-  T yb[6], ye[6], qb[5];
+  qbar[Q_RS] += rsb;
+  const double dmdth[3] = {P.cos_tm * cps, P.cos_tm * sps, -P.sin_tm};
+  T yb[6], ye[6], qb[NQ], dm[3];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     yb[j] = T(ybar[j]);
     ye[j] = yb[j];
   }
 #pragma unroll
-  for (int k = 0; k < 5; ++k) qb[k] = T(qbar[k]);
+  for (int k = 0; k < NQ; ++k) qb[k] = T(qbar[k]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) dm[j] = T(dmdth[j]);
   // reverse sweep over the segments
   const int last_seg = (na_final - 1) / CK;
   for (int sgi = last_seg; sgi >= 0; --sgi) {
@@ -593,18 +613,18 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
 #pragma unroll
           for (int q = 0; q < 6; ++q) yn[q] = T(nx[q]);
         }
-        saltation(cj, yn, T(r[7]), yb, qb);
+        saltation(cj, dm, yn, T(r[7]), yb, qb);
       }
-      step_adjoint(cj, y, T(r[6]), (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb, qb);
-      if (fl & FL_FLIP_BEFORE) saltation(cj, y, T(-r[7]), yb, qb);
+      step_adjoint(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb,
+                   qb);
+      if (fl & FL_FLIP_BEFORE) saltation(cj, dm, y, T(-r[7]), yb, qb);
     }
   }
 #pragma unroll
   for (int j = 0; j < 6; ++j) ybar[j] = (double)yb[j];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) qbar[k] = (double)qb[k];
+  for (int k = 0; k < NQ; ++k) qbar[k] = (double)qb[k];
   // assemble dF/dp for this ray
-  double dmdth[3] = {P.cos_tm * cps, P.cos_tm * sps, -P.sin_tm};
 #pragma unroll
   for (int k = 0; k < NSAMP_TANGENTS; ++k) {
     double g = Kv * so.w.d[k];
@@ -612,11 +632,11 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
     for (int j = 0; j < 3; ++j) g += ybar[j] * so.x[j].d[k] + ybar[3 + j] * so.k[j].d[k];
     G[k] = g;
   }
-  G[PAR_MA] += qbar[1] * P.dcp_dma;
-  G[PAR_B0] += qbar[1] * P.dcp_dB0;
-  G[PAR_THM] += qbar[2] * dmdth[0] + qbar[3] * dmdth[1] + qbar[4] * dmdth[2];
-  G[PAR_M] += qbar[0] * P.drsp_dM;
-  G[PAR_R] += qbar[0] * P.drsp_dR;
+  G[PAR_MA] += qbar[Q_CP] * P.dcp_dma;
+  G[PAR_B0] += qbar[Q_CP] * P.dcp_dB0;
+  G[PAR_THM] += qbar[Q_THM];
+  G[PAR_M] += qbar[Q_RS] * P.drsp_dM;
+  G[PAR_R] += qbar[Q_RS] * P.drsp_dR;
   G[PAR_INCL] = w * Kv * P.kappa * dmu_di;
   P.F_ray[i] = Fi;
   for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = G[k];

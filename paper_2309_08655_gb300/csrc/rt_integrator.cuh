@@ -123,7 +123,7 @@ struct NoHook {
   __device__ __forceinline__ void on_accept(const Lane&, const double*, const double*,
                                             const double*, const double*, const double*,
                                             const double*, const double*, const double*,
-                                            double) {}
+                                            const double*, double) {}
 };
 
 // The last th in [0, 1] on the non-negative side of side_val, given
@@ -266,7 +266,7 @@ __device__ int advance(const TraceParams& p, Lane& L, Hook& hook) {
   }
   if (en <= 1.0) {
     ++L.na;
-    hook.on_accept(L, y, yn, k1, k3, k4, k5, k6, k7, h);
+    hook.on_accept(L, y, yn, k1, k2, k3, k4, k5, k6, k7, h);
     const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
     if (rnew2 >= p.r_out * p.r_out) {
       // locate |x(th)| = r_out on the continuous extension

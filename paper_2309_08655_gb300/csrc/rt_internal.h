@@ -171,6 +171,9 @@ enum { PAR_MA = 0, PAR_B0, PAR_THM, PAR_M, PAR_R, PAR_INCL, NPARAMS };
 constexpr int NSAMP_TANGENTS = 5;
 constexpr int CK = 32;        // accepted steps per checkpoint
 constexpr int CKREC = 13;     // doubles per checkpoint: y, h, h_resume, sig, flags, counts
+// doubles per accepted step of a segment replay: y[6], h, sig, flags, spare,
+// and the step's seven stage derivatives K[7][6]
+constexpr int SEGREC = 10 + 7 * 6;
 
 struct AdjLaunch {
   const StarDev* star;                          // host descriptor

@@ -266,7 +266,7 @@ struct CrossingHook {
   bool on;           // false: a forward ray of a mixed batch (no crossing search)
   CrossingAcc acc;
   __device__ void on_accept(const Lane& L, const double* y, const double* yn, const double* k1,
-                            const double* k3, const double* k4, const double* k5,
+                            const double*, const double* k3, const double* k4, const double* k5,
                             const double* k6, const double* k7, double h) {
     if (!on) return;
     double r2[6], r3[6], r4[6], r5[6];

@@ -471,12 +471,19 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
   LaneM L;
   long long acc = 0, rej = 0, traced = 0, esc = 0, promoted = 0;
   if (p.ts && threadIdx.x == 0) atomicMin(p.ts, global_ns());
+  // one pass over the rays, or COST_BUCKETS passes (cost-ordered claims: the
+  // rays that start nearest the null cone first)
+  const int64_t nq = p.order ? (int64_t)COST_BUCKETS * p.n : p.n;
   ClaimChunk ch;
   for (;;) {
-    claim_items(p.queue, p.n, p.refill_min, p.claim_size, ray, ch, [&](int64_t idx) -> int64_t {
-      if (p.status[idx] != RAY_READY) return -1;
-      load_lane_m(p, idx, L);
-      return idx;
+    claim_items(p.queue, nq, p.refill_min, p.claim_size, ray, ch, [&](int64_t idx) -> int64_t {
+      const int pass = p.order ? (int)(idx / p.n) : 0;
+      const int64_t i = idx - (int64_t)pass * p.n;
+      if (p.status[i] != RAY_READY ||
+          (p.order && cost_bucket(p.stars[find_star_m(p, i)], p.state, p.n, i) != pass))
+        return -1;
+      load_lane_m(p, i, L);
+      return i;
     });
     if (__ballot_sync(FULL, ray != -2) == 0) break;
     if (ray >= 0) {

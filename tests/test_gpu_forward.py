@@ -338,6 +338,24 @@ def test_claim_order_does_not_change_results():
     assert e.value.status == rt.RT_EINVAL
 
 
+def test_claim_order_does_not_change_mixed_results():
+    """Cost-ordered claims in the mixed-precision kernel (FP32 stages): the
+    rays nearest the null cone are claimed first; one lane per ray, every
+    ray's end point, status and step counts are bitwise those of index order
+    (also for the rays handed to the FP64 pass)."""
+    kw = I.stars_config1()[15]
+    star, st_d, w_d, s_d, code = G.gpu_sample(kw, I.sample_uniforms(502, 8192))
+    out = {}
+    for order in (rt.CLAIM_COST, rt.CLAIM_INDEX):
+        st, s = st_d.clone(), s_d.clone()
+        nacc, nrej, ctr = G.gpu_trace(star, st, s, rtol=1e-8, precision=rt.PREC_MIXED, tail=1,
+                                      claim_order=order)
+        out[order] = G.to_np(st, s, nacc, nrej, ctr)
+    a, b = out[rt.CLAIM_COST], out[rt.CLAIM_INDEX]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
 def test_express_lane_matches_index_order(oracle):
     # cost order in tail mode: the rays nearest the null cone run six lanes per
     # ray from the start (express lane), the others one lane per ray
