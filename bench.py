@@ -48,6 +48,10 @@ NBINS = (64, 32, 128)
 # = 80.5 TFLOP/s); both are reported.
 SMS, CLK = 152, 2.070e9
 FP64_KERNELS = "trace_fp64_kernel + tail_fp64_kernel (one trace call)"
+PRECISIONS = ("fp64", "mixed", "df")
+# arithmetic type of each path: FP64; FP32 stages with a double-float state;
+# double-float (pairs of FP32) throughout
+DTYPE = {"fp64": "f64", "mixed": "f32 (state f32x2)", "df": "f32x2"}
 LC_CUT_KM = 0.0      # backward IR cut on the conversion length (Sec. 4.4): none
 NOMINAL = {"fp64": SMS * 4 * CLK, "fp32": SMS * 256 * CLK}
 PEAK = dict(NOMINAL)
@@ -73,35 +77,39 @@ def _measure_peaks(rt, stream):
             "nominal_fp64_tflops": NOMINAL["fp64"] / 1e12,
             "nominal_fp32_tflops": NOMINAL["fp32"] / 1e12}
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one trace call
-# of this workload, one step per launch (1) and eight steps per launch (8)
-# (FP64: the persistent trace launch plus its six-lane tail launch; mixed: the
-# FP32 launch plus the FP64 pass and its tail), from a single-pass ncu launch
-# list of `bench.py --steps 8 --warmup 1 --no-cpu-baseline --no-backward
-# --no-adjoint --no-uneven --no-twisted --no-rotating` (cost-ordered claims),
-# valid for the kernel sources with the given SHA-256 prefix (reported as null
-# once they change).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the trace
+# kernel per traced ray, from one single-pass ncu capture of that kernel alone
+# (one launch, caches flushed by ncu before it) on 2^21 rays of the heaviest
+# benchmark star, cost-ordered claims:
+#   python profile_case.py --config config1 --precision <p> --claim-order cost --n 2097152
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k regex:<kernel> -s 1 -c 1 <the same command>
+# (2^21 rays hold 134 MB of state, more than L2).  The bench scales it by the
+# rays a launch traces; valid for the kernel sources with the given SHA-256
+# prefix (null once they change).
 TRAFFIC = {
-    # (steps per launch, claim order) -> DRAM bytes of the trace call
-    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh'),
-             "0e3654f642f58b55",
-             {(1, "cost"): 54.1e6, (8, "cost"): 925.5e6}),
-    "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_tail.cu', 'rt_tail.cuh',
-               'rt_trace_mixed.cu'),
-              "077aa850c59f317d", {(1, "cost"): 36.7e6, (8, "cost"): 445.9e6,
-                                   (1, "index"): 36.7e6, (8, "index"): 445.9e6}),
+    # precision -> (sources, digest, kernel, bytes per traced ray)
+    "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_internal.h'),
+             None, "trace_fp64_kernel", None),
+    "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_backward.cuh', 'rt_trace_mixed.cu',
+               'rt_internal.h'),
+              None, "trace_mixed_kernel", None),
+    "df": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_df.cuh', 'rt_trace_df.cu', 'rt_internal.h'),
+           None, "trace_df_kernel", None),
 }
 
 
-def _traffic(prec, steps_per_launch=1, claim="cost"):
+def _traffic(prec, rays):
+    """DRAM bytes of the trace kernel for a launch tracing `rays` rays."""
     import hashlib
-    files, digest, by_steps = TRAFFIC[prec]
-    nbytes = by_steps.get((steps_per_launch, claim))
+    files, digest, _, per_ray = TRAFFIC[prec]
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2309_08655_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return nbytes if (nbytes is not None and h.hexdigest()[:16] == digest) else None
+    if per_ray is None or h.hexdigest()[:16] != digest:
+        return None
+    return per_ray * rays
 
 
 CLAIM = {"index": 0, "cost": 1}
@@ -195,13 +203,36 @@ class Clocks:
 
 
 def _flops_per_attempt(rt):
-    L = rt.lib()
-    L.rt_flops_per_step.restype = ctypes.c_int
-    L.rt_flops_per_step.argtypes = [ctypes.c_int32, ctypes.c_int32,
-                                    ctypes.POINTER(ctypes.c_double)]
-    o = (ctypes.c_double * 4)()
-    L.rt_flops_per_step(0, 0, o)
-    return list(o)
+    return rt.rt_flops_per_step(0, 0)
+
+
+def _roofline(prec, fl, fl_df, attempts, rays, promoted_attempts, t):
+    """ALU roofline of one trace call of `t` seconds: counted operations per
+    attempt (and per ray for the initial step) against the measured peak of
+    the pipe that executes them."""
+    if prec == "fp64":
+        flops = attempts * fl[1] + rays * fl[2]
+        r = {"kernel": FP64_KERNELS, "peak": PEAK["fp64"], "peak_source": PEAK_SOURCE["fp64"],
+             "flops_per_attempt": fl[1]}
+    elif prec == "mixed":
+        flops = (attempts - promoted_attempts) * fl[1] + rays * fl[2]
+        r = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)", "peak": PEAK["fp32"],
+             "peak_source": PEAK_SOURCE["fp32"], "flops_per_attempt": fl[1]}
+    else:
+        # the FP32 operations the double-float arithmetic executes; the FP64
+        # operations they stand for reported beside them
+        flops = attempts * fl_df[1] + rays * (2 * fl_df[0] + 600)
+        r = {"kernel": "trace_df_kernel", "peak": PEAK["fp32"], "peak_source": PEAK_SOURCE["fp32"],
+             "flops_per_attempt": fl_df[1],
+             "flops_counted": "FP32 operations of the double-float arithmetic (sum 11, product 10, "
+                              "rsqrt 24; rt_flops_per_step_df)",
+             "fp64_equivalent_flops_per_attempt": fl[1],
+             "fp64_equivalent_tflops": (attempts * fl[1] + rays * fl[2]) / t / 1e12}
+    r.update({"bound": "alu", "achieved": flops / t / 1e12, "unit": "TFLOP/s",
+              "frac": flops / t / r["peak"], "traffic": _traffic(prec, rays),
+              "traffic_kernel": TRAFFIC[prec][2]})
+    r["peak"] = r["peak"] / 1e12
+    return r
 
 
 class _Pipelined:
@@ -384,6 +415,9 @@ def run_ours(args):
         "mixed": rt.make_opts(rtol=cfg["rtol_mixed"], r_out_over_R=cfg["r_out_over_R"],
                               precision=rt.PREC_MIXED, max_steps=cfg["max_steps"],
                               claim_order=CLAIM[args.claim_order]),
+        "df": rt.make_opts(rtol=cfg["rtol"], r_out_over_R=cfg["r_out_over_R"],
+                           precision=rt.PREC_DF, max_steps=cfg["max_steps"],
+                           claim_order=CLAIM[args.claim_order]),
     }
     ev_t = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -391,7 +425,7 @@ def run_ours(args):
     # persistent + tail; FP64 index order = persistent + tail; mixed = FP32 +
     # FP64 pass + tail.  A pipelined run of K steps: one sampling launch and
     # three binning launches per star-step, plus one trace call.
-    trace_launches = {"fp64": 4 if args.claim_order == "cost" else 2, "mixed": 3}
+    trace_launches = {"fp64": 4 if args.claim_order == "cost" else 2, "mixed": 3, "df": 1}
 
     def step(prec, uin=None):
         ctr.zero_()
@@ -408,10 +442,11 @@ def run_ours(args):
 
     res = {}
     fl = _flops_per_attempt(rt)
+    fl_df = rt.rt_flops_per_step_df(0, 0)
     peaks = _measure_peaks(rt, stream)
     clocks = Clocks(local)
     clocks.start()
-    for prec in ("fp64", "mixed"):
+    for prec in PRECISIONS:
         for _ in range(args.warmup):
             step(prec)
         torch.cuda.synchronize()
@@ -436,25 +471,11 @@ def run_ours(args):
         rays_launch = c_sum[2] / args.steps
         promoted_attempts = c_sum[5] / args.steps
         t_tr = statistics.mean(t_trace)
-        if prec == "fp64":
-            flops = attempts * fl[1] + rays_launch * fl[2]
-            roof = {"kernel": FP64_KERNELS, "bound": "alu", "achieved": flops / t_tr / 1e12,
-                    "peak": PEAK["fp64"] / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK["fp64"],
-                    "traffic": _traffic("fp64", 1, args.claim_order),
-                    "peak_source": PEAK_SOURCE["fp64"]}
-        else:
-            flops = (attempts - promoted_attempts) * fl[1] + rays_launch * fl[2]
-            roof = {"kernel": "trace_mixed_kernel (+ FP64 pass for promoted rays)",
-                    "bound": "alu", "achieved": flops / t_tr / 1e12,
-                    "peak": PEAK["fp32"] / 1e12, "unit": "TFLOP/s",
-                    "frac": flops / t_tr / PEAK["fp32"],
-                    "traffic": _traffic("mixed", 1, args.claim_order),
-                    "peak_source": PEAK_SOURCE["fp32"],
-                    "promoted_rays_per_step": c_sum[4] / args.steps,
-                    "promoted_fp64_attempts_per_step": promoted_attempts}
-        roof.update({"flops_per_attempt": fl[1], "attempts_per_launch": attempts,
-                     "trace_ms_per_launch": 1e3 * t_tr})
+        roof = _roofline(prec, fl, fl_df, attempts, rays_launch, promoted_attempts, t_tr)
+        if prec == "mixed":
+            roof.update({"promoted_rays_per_step": c_sum[4] / args.steps,
+                         "promoted_fp64_attempts_per_step": promoted_attempts})
+        roof.update({"attempts_per_launch": attempts, "trace_ms_per_launch": 1e3 * t_tr})
         res[prec] = {"value": acc_all / T, "rays_per_s": rays_all / T,
                      "ms_per_step": 1e3 * T / args.steps, "roofline": roof,
                      "accepted_steps_per_step": c_sum[0] / args.steps,
@@ -463,15 +484,15 @@ def run_ours(args):
                      "hist": hist.cpu().numpy().copy(),
                      "end": (st.cpu().numpy().copy(), s.cpu().numpy().copy()),
                      "statuses": np.bincount(s.cpu().numpy(), minlength=8).tolist()}
-    hists = {p: res[p].pop("hist") for p in ("fp64", "mixed")}
-    ends = {p: res[p].pop("end") for p in ("fp64", "mixed")}
+    hists = {p: res[p].pop("hist") for p in PRECISIONS}
+    ends = {p: res[p].pop("end") for p in PRECISIONS}
     # continuous batching: the K steps' batches (16 sub-batches each) in one
     # persistent launch, so the bulk of later batches overlaps the long rays of
     # earlier ones; the same work per step (rays that finish in the six-lane
     # tail kernel may differ from one launch per step by rounding)
     K = min(args.steps, 64)
     P = _Pipelined(rt, stars, nper, nsub, K, u, dev, stream, NBINS, cfg, ws)
-    for prec in ("fp64", "mixed"):
+    for prec in PRECISIONS:
         P.run(opts[prec])                   # untimed pass of this path
         torch.cuda.synchronize()
         if ws > 1:
@@ -487,16 +508,9 @@ def run_ours(args):
         T, acc_all, rays_all = shard.reduce_totals(e0.elapsed_time(e1) / 1e3, c[0], c[2], dev)
         t_tr = P.ev[0].elapsed_time(P.ev[1]) / 1e3
         attempts = c[0] + c[1]
-        if prec == "fp64":
-            flops = attempts * fl[1] + c[2] * fl[2]
-            peak, kern = PEAK["fp64"], FP64_KERNELS
-        else:
-            flops = (attempts - c[5]) * fl[1] + c[2] * fl[2]
-            peak, kern = PEAK["fp32"], "trace_mixed_kernel (+ FP64 pass for promoted rays)"
-        roof = dict(res[prec]["roofline"])
-        roof.update({"kernel": kern, "achieved": flops / t_tr / 1e12, "frac": flops / t_tr / peak,
-                     "traffic": _traffic(prec, K, args.claim_order), "attempts_per_launch": attempts,
-                     "trace_ms_per_launch": 1e3 * t_tr, "steps_per_launch": K})
+        roof = _roofline(prec, fl, fl_df, attempts, c[2], c[5], t_tr)
+        roof.update({"attempts_per_launch": attempts, "trace_ms_per_launch": 1e3 * t_tr,
+                     "steps_per_launch": K})
         hp = P.hist.cpu().numpy()
         same = all(np.array_equal(hp[k * nsub:(k + 1) * nsub], hists[prec]) for k in range(K))
         res[prec]["pipelined"] = {"value": acc_all / T, "rays_per_s": rays_all / T,
@@ -508,6 +522,7 @@ def run_ours(args):
         return float(np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300))
 
     res["mixed"]["flux_l1_vs_fp64"] = l1(hists["mixed"], hists["fp64"])
+    res["df"]["flux_l1_vs_fp64"] = l1(hists["df"], hists["fp64"])
     equal_acc = None
     if ws == 1 and not args.no_equal_accuracy:
         equal_acc = _equal_accuracy(rt, batch, u, st, w, s, hist, oor, ctr, cfg, stream,
@@ -520,12 +535,12 @@ def run_ours(args):
         or_states = {}
         cpu, h_or = _cpu_baseline(stars_kw, cfg, args.cpu_sample, or_states)
         if h_or is not None and ws == 1:
-            for p in ("fp64", "mixed"):
+            for p in PRECISIONS:
                 res[p]["flux_l1_vs_oracle"] = l1(hists[p], h_or)
             res["mixed"]["endpoint_error_vs_oracle"] = _endpoint_errors(ends, or_states, nper)
     # headline: the fastest precision whose binned flux is within 1e-6 (relative
     # L1) of the FP64 oracle; without the oracle, of the FP64 GPU path
-    ok = [p for p in ("mixed", "fp64")
+    ok = [p for p in PRECISIONS
           if res[p].get("flux_l1_vs_oracle", res[p].get("flux_l1_vs_fp64", 0.0)) <= 1e-6]
     head = min(ok, key=lambda p: res[p]["pipelined"]["ms_per_step"]) if ok else "fp64"
     # end to end through the C ABI with host buffers: H2D of the K steps'
@@ -564,7 +579,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": HP["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": HP["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head],
         "data": "synthetic",
         "config": {"workload": cfg["name"], "rays_per_step": N, "sub_batches": nsub,
                    "parallelism": ("single GPU" if ws == 1 else
@@ -583,8 +598,9 @@ def run_ours(args):
         "rays_per_s": HP["rays_per_s"],
         "flux_l1_vs_oracle": H.get("flux_l1_vs_oracle"),
         "roofline": HP["roofline"],
-        "fp64": res["fp64"], "mixed": res["mixed"],
+        "fp64": res["fp64"], "mixed": res["mixed"], "df": res["df"],
         "mixed_vs_fp64_rays_per_s": res["mixed"]["rays_per_s"] / res["fp64"]["rays_per_s"],
+        "df_vs_fp64_rays_per_s": res["df"]["rays_per_s"] / res["fp64"]["rays_per_s"],
         "mixed_vs_fp64_equal_accuracy": equal_acc,
         "backward": back,
         "adjoint_forward_ratio": adj["adjoint_forward_ratio"] if adj else None,
@@ -605,17 +621,18 @@ def run_ours(args):
 def _equal_accuracy(rt, batch, u, st, w, s, hist, oor, ctr, cfg, stream, hist_mixed,
                     ms_mixed, l1):  # ms_mixed: the mixed path's trace call
     """The mixed path against the plain FP64 path at equal binned-flux
-    accuracy.  Reference: the FP64 flux at rtol 1e-12; the mixed path's
-    distance from it (rtol 1e-8); the FP64 path's distance and time at rtol
-    1e-8, 1e-9, 1e-10; the loosest FP64 rtol at least as close to the
-    reference as the mixed path (the tightest one tried if none is) sets the
-    FP64 time of the ratio.  One launch per step for both, as the mixed
-    path's own timing."""
+    accuracy.  Reference: the FP64 flux at rtol 1e-12.  The FP64 path's
+    distance from it and its time at rtol 1e-8, 1e-9, 1e-10; the mixed path's
+    at its default rtol (the main leg's run) and at rtol 1e-9; the
+    double-float path's at rtol 1e-9 and 1e-10.  For each mixed or
+    double-float row the loosest FP64 rtol at least as close to the reference
+    (the tightest one tried if none is) sets the FP64 time of its ratio.  One
+    launch per step for both, as the mixed path's own timing."""
     import torch
     nth, nph, nnu = NBINS
 
-    def run(rtol):
-        o = rt.make_opts(rtol=rtol, r_out_over_R=cfg["r_out_over_R"], precision=rt.PREC_FP64,
+    def run(rtol, prec):
+        o = rt.make_opts(rtol=rtol, r_out_over_R=cfg["r_out_over_R"], precision=prec,
                          max_steps=cfg["max_steps"] * 4, claim_order=CLAIM["cost"])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ctr.zero_()
@@ -626,24 +643,38 @@ def _equal_accuracy(rt, batch, u, st, w, s, hist, oor, ctr, cfg, stream, hist_mi
         rt.rt_bin_batch(batch, st, w, s, nth, nph, nnu, cfg["nu_lo"], cfg["nu_hi"], hist, oor,
                         stream=stream)
         torch.cuda.synchronize()
-        return hist.cpu().numpy().copy(), e0.elapsed_time(e1), int(ctr[0])
+        return hist.cpu().numpy().copy(), e0.elapsed_time(e1), int(ctr[0]), int(ctr[4])
 
-    h_ref, t_ref, _ = run(1e-12)
-    d_mixed = l1(hist_mixed, h_ref)
+    h_ref, t_ref, _, _ = run(1e-12, rt.PREC_FP64)
     rows = []
     for rtol in (1e-8, 1e-9, 1e-10):
-        h, t, acc = run(rtol)
+        h, t, acc, _ = run(rtol, rt.PREC_FP64)
         rows.append({"rtol": rtol, "flux_l1_vs_rtol1e-12": l1(h, h_ref), "trace_ms": t,
                      "accepted_steps": acc})
-    ok = [r for r in rows if r["flux_l1_vs_rtol1e-12"] <= d_mixed]
-    pick = ok[0] if ok else rows[-1]
+    mixed = [{"rtol": cfg["rtol_mixed"], "flux_l1_vs_rtol1e-12": l1(hist_mixed, h_ref),
+              "trace_ms": ms_mixed}]
+    h, t, acc, promoted = run(1e-9, rt.PREC_MIXED)
+    mixed.append({"rtol": 1e-9, "flux_l1_vs_rtol1e-12": l1(h, h_ref), "trace_ms": t,
+                  "accepted_steps": acc, "promoted_rays": promoted})
+    df = []
+    for rtol in (1e-9, 1e-10):
+        h, t, acc, _ = run(rtol, rt.PREC_DF)
+        df.append({"rtol": rtol, "flux_l1_vs_rtol1e-12": l1(h, h_ref), "trace_ms": t,
+                   "accepted_steps": acc})
+    for m in mixed + df:
+        ok = [r for r in rows if r["flux_l1_vs_rtol1e-12"] <= m["flux_l1_vs_rtol1e-12"]]
+        pick = ok[0] if ok else rows[-1]
+        m.update({"fp64_rtol_at_equal_accuracy": pick["rtol"],
+                  "fp64_at_least_as_accurate": bool(ok),
+                  "speedup_vs_fp64": pick["trace_ms"] / m["trace_ms"]})
     return {"reference": "FP64 rtol 1e-12 binned flux (trace %.0f ms)" % t_ref,
-            "mixed_rtol": cfg["rtol_mixed"], "mixed_flux_l1_vs_rtol1e-12": d_mixed,
-            "mixed_trace_ms": ms_mixed, "fp64": rows,
-            "fp64_rtol_at_equal_accuracy": pick["rtol"],
-            "fp64_at_least_as_accurate": bool(ok),
-            "speedup_mixed_vs_fp64": pick["trace_ms"] / ms_mixed,
-            "launch": "one persistent launch per step, both paths (FP64 cost-ordered claims); "
+            "mixed_rtol": cfg["rtol_mixed"],
+            "mixed_flux_l1_vs_rtol1e-12": mixed[0]["flux_l1_vs_rtol1e-12"],
+            "mixed_trace_ms": ms_mixed, "fp64": rows, "mixed": mixed, "df": df,
+            "fp64_rtol_at_equal_accuracy": mixed[0]["fp64_rtol_at_equal_accuracy"],
+            "fp64_at_least_as_accurate": mixed[0]["fp64_at_least_as_accurate"],
+            "speedup_mixed_vs_fp64": mixed[0]["speedup_vs_fp64"],
+            "launch": "one persistent launch per step, both paths (cost-ordered claims); "
                       "times of the trace call (persistent launch and its second pass)"}
 
 

@@ -76,7 +76,7 @@ enum {
   RT_PLASMA_GJ = 0, RT_PLASMA_VACUUM = 1, RT_PLASMA_HOMOG = 2, RT_PLASMA_LINEAR_Z = 3,
   RT_PLASMA_RADIAL = 4, RT_PLASMA_TWISTED = 5
 };
-enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1 };
+enum { RT_PREC_FP64 = 0, RT_PREC_MIXED = 1, RT_PREC_DF = 2 };
 enum { RT_CLAIM_INDEX = 0, RT_CLAIM_COST = 1 };
 
 /*
@@ -145,7 +145,8 @@ typedef struct {
  *   lambda_max        stop at this worldline parameter (units: R / m_a^2 scaled
  *                     Hamiltonian); 0 = no limit
  *   r_capture_over_R  capture radius (1 = stellar surface)
- *   precision         RT_PREC_FP64 or RT_PREC_MIXED
+ *   precision         RT_PREC_FP64, RT_PREC_MIXED or RT_PREC_DF (forward tracing
+ *                     only: rt_trace_forward, rt_trace_batch without images)
  *   max_steps         bound on accepted steps per ray
  *   block             threads per block of the persistent kernel (0 = auto, or
  *                     the batch's autotuned value, rt_batch_autotune)
@@ -273,11 +274,19 @@ rt_status rt_sample_conversion_surface_part(const rt_star* star, int64_t n, int6
  *              promoted rays in FP64, 2 reserved
  *   opts       integration options (host pointer, read during the call)
  * RT_PREC_FP64: every stage in FP64; deterministic (bitwise identical outputs
- * for identical inputs) with the default claim order.  RT_PREC_MIXED: the stages and their combinations run
- * in FP32 and the state accumulates in FP64; where the FP32 rounding floor of
+ * for identical inputs) with the default claim order.  RT_PREC_MIXED: the
+ * stages and their combinations run in FP32 and the state accumulates in
+ * double-float (two floats, ~48 significant bits; no FP64 arithmetic per
+ * step); where the FP32 rounding floor of
  * the embedded error estimate reaches a quarter of the tolerance on a rejected
  * step, the ray continues in FP64 from that point (a second kernel on the same
  * stream).  Use rtol >= 1e-8 with RT_PREC_MIXED; lambda_max must be 0.
+ * RT_PREC_DF: the FP64 integrator's steps, events and decisions with every
+ * operation in double-float arithmetic on the FP32 pipe (a value is the sum
+ * of two floats, ~48 significant bits; an FP64 operation on this GPU issues
+ * at 1/64 of the FP32 rate): FP64-class results at a fraction of the cost;
+ * one lane per ray (tail ignored), claim_order honoured; lambda_max must be
+ * 0; not for rotating stars.
  * Calls sharing one handle must be serialised on one stream (the handle owns
  * the work-queue counter).
  */
@@ -391,9 +400,9 @@ rt_status rt_bin_part_finalize(int32_t nth, int32_t nph, int32_t nnu, int64_t n_
  * The sign of g is decided in FP32 where it is certain (on shell, g has the
  * sign of P G - 1 up to the integrator's drift, and that is formed in FP32
  * with a wide margin), else in FP64; bisection and contributions are FP64.
- * RT_PREC_FP64: FP64 stages.  RT_PREC_MIXED: FP32 stages with the FP64 state
- * of the forward mixed kernel; the crossing search runs on the FP64
- * reconstruction of each step's continuous extension; a pixel whose FP32
+ * RT_PREC_FP64: FP64 stages.  RT_PREC_MIXED: FP32 stages with the
+ * double-float state of the forward mixed kernel; the crossing search runs on
+ * the FP64 reconstruction of each step's continuous extension; a pixel whose FP32
  * error estimate sits on the rounding floor is traced again from the plane in
  * FP64 (second kernel on the same stream; the first call with a larger image
  * allocates a list of 4 B per pixel on the handle).
@@ -654,6 +663,15 @@ rt_status rt_count_status(int64_t n, const uint8_t* d_status, int64_t* counts, v
  * unknown model switches.
  */
 rt_status rt_flops_per_step(int32_t dispersion, int32_t plasma, double* out4);
+
+/*
+ * rt_flops_per_step_df - the same for RT_PREC_DF, in the FP32 operations the
+ * double-float kernel executes (host only): out2[0] per right-hand side
+ * evaluation, out2[1] per step attempt.  A double-float sum counts 11, a
+ * product 10, a reciprocal square root 24 (rt_df.cuh); FMA = 2.  RT_EINVAL
+ * for unknown model switches.
+ */
+rt_status rt_flops_per_step_df(int32_t dispersion, int32_t plasma, double* out2);
 
 /*
  * rt_measure_alu_peak - measured FP64 and FP32 CUDA-core throughput of the

@@ -16,9 +16,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt_axion.so")
 SOURCES = ["rt_abi.cu", "rt_sample.cu", "rt_trace.cu", "rt_trace_mixed.cu", "rt_bin.cu",
            "rt_flops.cu", "rt_adjoint.cu", "rt_tail.cu", "rt_trace_rot.cu", "rt_peak.cu",
-           "rt_rhs.cu"]
+           "rt_rhs.cu", "rt_trace_df.cu"]
 HEADERS = ["rt_device.cuh", "rt_internal.h", "rt_integrator.cuh", "rt_sample_core.cuh",
-           "rt_dual.cuh", "rt_backward.cuh"]
+           "rt_dual.cuh", "rt_backward.cuh", "rt_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-Xptxas", "-v"]

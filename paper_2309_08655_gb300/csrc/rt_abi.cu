@@ -254,6 +254,7 @@ rt_status rt_sample_conversion_surface(const rt_star* s, int64_t n, const double
 rt_status rt_sample_conversion_surface_part(const rt_star* s, int64_t n, int64_t n_norm,
                                             const double* d_u, double* d_state,
                                             double* d_weight, uint8_t* d_status, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_sample_conversion_surface_part");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
   if (n_norm < n || n_norm < 1) return fail(RT_EINVAL, "need n_norm >= max(n, 1)");
@@ -338,7 +339,8 @@ static rt_status check_opts(const rt_trace_opts* o) {
     return fail(RT_EINVAL, "lambda_max must be finite and >= 0");
   if (o->max_steps <= 0) return fail(RT_EINVAL, "max_steps must be > 0");
   if (o->max_steps > (1 << 28)) return fail(RT_EINVAL, "max_steps too large");
-  if (o->precision != RT_PREC_FP64 && o->precision != RT_PREC_MIXED)
+  if (o->precision != RT_PREC_FP64 && o->precision != RT_PREC_MIXED &&
+      o->precision != RT_PREC_DF)
     return fail(RT_EINVAL, "unknown precision %d", o->precision);
   if (o->block < 0 || o->blocks_per_sm < 0) return fail(RT_EINVAL, "negative launch parameter");
   if (o->tail < 0 || o->tail > 31) return fail(RT_EINVAL, "tail must be in [0, 31]");
@@ -361,6 +363,7 @@ static void set_claiming(rtk::TraceParams& p, const rt_trace_opts* o, int refill
 rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t* d_status,
                            int32_t* d_nacc, int32_t* d_nrej, int64_t* d_counters,
                            const rt_trace_opts* o, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_trace_forward");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
   rt_status st;
@@ -371,7 +374,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
   if (d_nrej && (st = check_dev_ptr(d_nrej, "d_nrej")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
-  if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
+  if (o->precision != RT_PREC_FP64 && o->lambda_max > 0)
     return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
   const bool rigid = (s->p.rotation == RT_ROTATION_RIGID);
   if (rigid && o->precision != RT_PREC_FP64)
@@ -388,7 +391,7 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   p.counters = d_counters;
   p.queue = s->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail != 1 && o->lambda_max == 0.0 && !rigid) {
+  if (o->tail != 1 && o->lambda_max == 0.0 && !rigid && o->precision != RT_PREC_DF) {
     rt_star* sm = const_cast<rt_star*>(s);
     if ((st = ensure_park(&sm->d_park, &sm->park_cap)) != RT_OK) return st;
     set_park(p, sm->d_park, sm->park_cap, o);
@@ -409,6 +412,11 @@ rt_status rt_trace_forward(const rt_star* s, int64_t n, double* d_state, uint8_t
   if (rigid) {
     e = rtk::launch_trace_rot(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "rotating-magnetosphere trace kernel");
+    return RT_OK;
+  }
+  if (o->precision == RT_PREC_DF) {
+    e = rtk::launch_trace_df(p, o->block, o->blocks_per_sm, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "double-float trace kernel");
     return RT_OK;
   }
   if (o->precision == RT_PREC_MIXED) {
@@ -458,9 +466,12 @@ rt_status rt_trace_backward(const rt_star* s, int32_t nx, int32_t ny, double inc
                             double dist_over_R, double bmax_over_R, double Lc_cut_km,
                             double* d_image, uint8_t* d_status, int32_t* d_ncross,
                             int64_t* d_counters, const rt_trace_opts* o, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_trace_backward");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
+  if (o->precision == RT_PREC_DF)
+    return fail(RT_EUNSUPPORTED, "images are traced in RT_PREC_FP64 or RT_PREC_MIXED");
   if ((st = check_image(nx, ny, incl_rad, dist_over_R, bmax_over_R, Lc_cut_km)) != RT_OK)
     return st;
   if ((st = check_dev_ptr(d_image, "d_image")) != RT_OK) return st;
@@ -528,6 +539,7 @@ static double vmf_norm(double kappa) {
 rt_status rt_flux_value(const rt_star* s, int64_t n, const double* d_state,
                         const double* d_weight, const uint8_t* d_status, double incl_rad,
                         double kappa, double* d_F_ray, double* d_F, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_flux_value");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
   if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
@@ -549,11 +561,14 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
                            const rt_trace_opts* o, double* d_grad, double* d_F,
                            uint8_t* d_status, int64_t* d_counters, int64_t* ckpt_bytes,
                            void* stream) {
+  rtk::NvtxRange nvtx_range("rt_flux_gradient");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
   if (o->lambda_max != 0.0) return fail(RT_EUNSUPPORTED, "lambda_max must be 0");
+  if (o->precision == RT_PREC_DF)
+    return fail(RT_EUNSUPPORTED, "the gradient is computed in RT_PREC_FP64 or RT_PREC_MIXED");
   if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
     return fail(RT_EINVAL, "need finite incl_rad and 0 < kappa < inf");
   if ((st = check_dev_ptr(d_uniforms, "d_uniforms")) != RT_OK) return st;
@@ -695,6 +710,7 @@ rt_status rt_bin_spectrum(const rt_star* s_, int64_t n, const double* d_state,
                           const double* d_weight, const uint8_t* d_status, int32_t nth,
                           int32_t nph, int32_t nnu, double nu_lo, double nu_hi, double* d_hist,
                           double* d_sky, double* d_spec, double* d_oor, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_spectrum");
   rt_star* s = const_cast<rt_star*>(s_);
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 0) return fail(RT_EINVAL, "n must be >= 0");
@@ -776,7 +792,7 @@ struct rt_batch {
   // autotuned launch per precision and kind (rays only / with images); 0 = default
   struct Tuned {
     int block = 0, bps = 0, refill = 0, claim = 0;
-  } tuned[2][2];
+  } tuned[3][2];       // [precision: FP64, mixed, double-float][rays only, with images]
   double* d_park = nullptr;           // tail-mode park buffer (allocated on first use)
   int64_t park_cap = 0;
   // backward images traced in the same launch (rt_batch_set_images)
@@ -952,6 +968,7 @@ rt_status rt_batch_set_images(rt_batch* b, int32_t nimg, const rt_star* const* s
 
 rt_status rt_sample_batch(rt_batch* b, const double* d_u, double* d_state, double* d_weight,
                           uint8_t* d_status, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_sample_batch");
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   if (b->N == 0) return RT_OK;
   rt_status st;
@@ -995,6 +1012,7 @@ rt_status rt_batch_set_norm(rt_batch* b, const int64_t* n_norm) {
 rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_t* d_nacc,
                          int32_t* d_nrej, int64_t* d_counters, const rt_trace_opts* o,
                          void* stream) {
+  rtk::NvtxRange nvtx_range("rt_trace_batch");
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
@@ -1004,8 +1022,10 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   if (d_nacc && (st = check_dev_ptr(d_nacc, "d_nacc")) != RT_OK) return st;
   if (d_nrej && (st = check_dev_ptr(d_nrej, "d_nrej")) != RT_OK) return st;
   if (d_counters && (st = check_dev_ptr(d_counters, "d_counters")) != RT_OK) return st;
-  if (o->precision == RT_PREC_MIXED && o->lambda_max > 0)
+  if (o->precision != RT_PREC_FP64 && o->lambda_max > 0)
     return fail(RT_EUNSUPPORTED, "lambda_max is only supported with RT_PREC_FP64");
+  if (o->precision == RT_PREC_DF && b->npix > 0)
+    return fail(RT_EUNSUPPORTED, "a batch with images is traced in RT_PREC_FP64 or RT_PREC_MIXED");
   if (b->rigid && o->precision != RT_PREC_FP64)
     return fail(RT_EUNSUPPORTED, "a rotating magnetosphere is traced in RT_PREC_FP64 only");
   rtk::TraceParams p;
@@ -1020,7 +1040,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   p.counters = d_counters;
   p.queue = b->d_queue;
   p.ts = (unsigned long long*)o->timestamps;
-  if (o->tail != 1 && o->lambda_max == 0.0 && !b->rigid) {
+  if (o->tail != 1 && o->lambda_max == 0.0 && !b->rigid && o->precision != RT_PREC_DF) {
     if ((st = ensure_park(&b->d_park, &b->park_cap)) != RT_OK) return st;
     set_park(p, b->d_park, b->park_cap, o);
   } else {
@@ -1037,7 +1057,7 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
   // express lane for FP64 ones
   p.order = (o->claim_order == RT_CLAIM_COST && b->npix == 0) ? 1 : 0;
   if (o->precision == RT_PREC_FP64) set_express(p);
-  const int pi = (o->precision == RT_PREC_MIXED) ? 1 : 0;
+  const int pi = (o->precision == RT_PREC_MIXED) ? 1 : (o->precision == RT_PREC_DF) ? 2 : 0;
   const rt_batch::Tuned& tu = b->tuned[pi][b->npix > 0 ? 1 : 0];
   const int blk = o->block > 0 ? o->block : tu.block;
   const int bps = o->block > 0 ? o->blocks_per_sm : tu.bps;
@@ -1077,6 +1097,11 @@ rt_status rt_trace_batch(rt_batch* b, double* d_state, uint8_t* d_status, int32_
     }
     e = rtk::launch_batch_fp64(p, t, blk, bps, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel");
+    return RT_OK;
+  }
+  if (o->precision == RT_PREC_DF) {
+    e = rtk::launch_trace_df(p, blk, bps, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "double-float trace kernel");
     return RT_OK;
   }
   if (o->precision == RT_PREC_MIXED) {
@@ -1125,6 +1150,7 @@ extern "C" {
 rt_status rt_bin_batch(rt_batch* b, const double* d_state, const double* d_weight,
                        const uint8_t* d_status, int32_t nth, int32_t nph, int32_t nnu,
                        double nu_lo, double nu_hi, double* d_hist, double* d_oor, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_batch");
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   if (nth < 1 || nph < 1 || nnu < 1) return fail(RT_EINVAL, "bin counts must be >= 1");
   if ((int64_t)nth * nph * nnu > (int64_t)1 << 28) return fail(RT_EINVAL, "too many bins");
@@ -1251,6 +1277,7 @@ rt_status rt_batch_graph_create(rt_batch* b, const double* d_u, double* d_state,
 }
 
 rt_status rt_graph_launch(rt_graph* g, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_graph_launch");
   if (!g) return fail(RT_EINVAL, "graph is NULL");
   cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
@@ -1269,6 +1296,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
                             int32_t* bps_out, int32_t* refill_out, int32_t* claim_out,
                             double* ms_out, int32_t* ncand_out, double* cand_ms,
                             int32_t cand_cap, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_batch_autotune");
   if (!b) return fail(RT_EINVAL, "batch is NULL");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
@@ -1282,7 +1310,10 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   if (b->npix > 0 && o->lambda_max != 0.0)
     return fail(RT_EUNSUPPORTED, "lambda_max must be 0 for a batch with images");
   const bool mixed = (o->precision == RT_PREC_MIXED);
+  const bool df = (o->precision == RT_PREC_DF);
   const bool img = (b->npix > 0);
+  if (df && img)
+    return fail(RT_EUNSUPPORTED, "a batch with images is traced in RT_PREC_FP64 or RT_PREC_MIXED");
   const size_t nst = b->stars.size();
   // the first rays_per_star rays of every star, in a batch of their own
   std::vector<int64_t> off(nst + 1, 0);
@@ -1422,6 +1453,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
     e = img ? (mixed ? rtk::occupancy_batch_mixed(blocks[bi], &occ)
                      : rtk::occupancy_batch_fp64(blocks[bi], &occ))
             : (mixed ? rtk::occupancy_mixed(blocks[bi], &occ)
+               : df  ? rtk::occupancy_trace_df(blocks[bi], &occ)
                      : rtk::occupancy_fp64(blocks[bi], &occ));
     if (e != cudaSuccess) break;
     for (int k = 1; k <= occ; ++k) cand.push_back({blocks[bi], k});
@@ -1449,6 +1481,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
                   : rtk::launch_batch_fp64(p, t, block, bps, cs);
       else
         r = mixed ? rtk::launch_trace_mixed(p, block, bps, cs)
+            : df  ? rtk::launch_trace_df(p, block, bps, cs)
                   : rtk::launch_trace_fp64(p, block, bps, cs);
     }
     if (r == cudaSuccess && mixed) {
@@ -1499,7 +1532,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   if (ev1) cudaEventDestroy(ev1);
   cudaFree(blk);
   if (e != cudaSuccess) return cuda_fail(e, "autotune trial");
-  b->tuned[mixed ? 1 : 0][img ? 1 : 0] = best;
+  b->tuned[mixed ? 1 : df ? 2 : 0][img ? 1 : 0] = best;
   if (block_out) *block_out = best.block;
   if (bps_out) *bps_out = best.bps;
   if (refill_out) *refill_out = best.refill;

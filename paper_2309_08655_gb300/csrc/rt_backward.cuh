@@ -464,16 +464,19 @@ struct CrossingAcc {
   // samples of one sign, an extremum of g turning toward zero (bracketed by
   // the FP32 slope of the screened N) searched in FP64 where the two tangent
   // lines at the samples meet within the screen's margin of zero.
-  // dense64(th, yd, yp) gives the FP64 point and, if yp is set, dy/dth.
+  // dense64(th, yd, yp) gives the FP64 point and, if yp is set, dy/dth.  y
+  // (read only on a ray's first step) and yn may be null: then dense64 at
+  // th = 0 and 1.
   template <class Dense64>
   __device__ void scan(const RayConst<double>& c, const double* y, const double* yn,
                        const Screen& sc, const float* y32, const float* p2, const float* p3,
                        const float* p4, const float* p5, Dense64& dense64) {
+    double yd[6];
     if (!have_g) {
-      neg_prev = crossing_g(c, W, y) < 0.0;
+      if (!y) dense64(0.0, yd, nullptr);
+      neg_prev = crossing_g(c, W, y ? y : yd) < 0.0;
       have_g = true;
     }
-    double yd[6];
     double th0 = 0.0;
     bool negA = neg_prev;
     float NA, slA;
@@ -535,7 +538,7 @@ struct CrossingAcc {
       bool negB;
       if (sg != 0) {
         negB = sg < 0;
-      } else if (q == BACK_SUBDIV) {
+      } else if (q == BACK_SUBDIV && yn) {
         negB = crossing_g(c, W, yn) < 0.0;
       } else {
         dense64(th1, yd, nullptr);

@@ -268,6 +268,7 @@ extern "C" rt_status rt_bin_spectrum_noalloc(const rt_star_params* params, int64
                                              int32_t nnu, double nu_lo, double nu_hi,
                                              double* d_hist, double* d_sky, double* d_spec,
                                              double* d_out_of_range, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_spectrum_noalloc");
   using namespace rtk;
   rt_status st;
   if ((st = check_star_params(params)) != RT_OK) return st;
@@ -362,6 +363,7 @@ rtk::BinParams part_params(int64_t n, int64_t n_total, const double* d_state,
 extern "C" rt_status rt_bin_part_max(int64_t n, const double* d_weight, const uint8_t* d_status,
                                      int32_t nth, int32_t nph, int32_t nnu, int64_t* d_acc,
                                      void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_part_max");
   using namespace rtk;
   rt_status st;
   if (n < 0) return bin_fail(RT_EINVAL, "n must be >= 0");
@@ -381,6 +383,7 @@ extern "C" rt_status rt_bin_part_accumulate(const rt_star* star, int64_t n, int6
                                             const uint8_t* d_status, int32_t nth, int32_t nph,
                                             int32_t nnu, double nu_lo, double nu_hi,
                                             int64_t* d_acc, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_part_accumulate");
   using namespace rtk;
   rt_status st;
   if (!star) return bin_fail(RT_EINVAL, "star is NULL");
@@ -407,6 +410,7 @@ extern "C" rt_status rt_bin_part_accumulate(const rt_star* star, int64_t n, int6
 extern "C" rt_status rt_bin_part_finalize(int32_t nth, int32_t nph, int32_t nnu, int64_t n_total,
                                           const int64_t* d_acc, double* d_hist, double* d_sky,
                                           double* d_spec, double* d_out_of_range, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_bin_part_finalize");
   using namespace rtk;
   rt_status st;
   if (n_total < 0) return bin_fail(RT_EINVAL, "n_total must be >= 0");

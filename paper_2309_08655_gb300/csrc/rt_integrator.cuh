@@ -110,6 +110,21 @@ __device__ __forceinline__ double cone_dist2(const StarDev& s, const double* sta
   return (F * F) / (g0 * g0 + g1 * g1 + g2 * g2);
 }
 
+// Cost-ordered claims and finished rays.  A ray finished in one pass has had
+// its state overwritten, and the cost bucket of its new state may match a
+// later pass.  Stores therefore write the state, fence, then the status
+// (status_after_state), and a claim that read the state for the bucket
+// re-reads the status after a fence (status_still): a claim that saw any of
+// the new state sees the ray finished.
+__device__ __forceinline__ void status_after_state(const TraceParams& p, int64_t i, int st) {
+  __threadfence();
+  p.status[i] = (uint8_t)st;
+}
+__device__ __forceinline__ bool status_still(const TraceParams& p, int64_t i, int want) {
+  __threadfence();
+  return *(volatile const uint8_t*)(p.status + i) == want;
+}
+
 // Cost bucket for the cost-ordered claim (TraceParams::order): 0 for a start
 // within 1e-3 rad of the null cone, 1 within 1e-2 rad, 2 otherwise.
 __device__ __forceinline__ int cost_bucket(const StarDev& s, const double* state, int64_t n,
@@ -131,34 +146,173 @@ struct NoHook {
 // halves the retained end's value), with a bisection step whenever the
 // bracket did not halve over two steps, run to the last representable th.
 // Returns lo (side_val >= 0); *hi_out the first th past it.
-template <class S>
-__device__ __forceinline__ double last_nonneg(const S& side_val, double flo, double fhi,
-                                              double* hi_out) {
-  double lo = 0.0, hi = 1.0;
+// T is the type of th and of the values (double, or float in the mixed
+// kernel); [lo, hi] the starting bracket.
+template <class S, class T>
+__device__ __forceinline__ T last_nonneg(const S& side_val, T flo, T fhi, T* hi_out, T lo = T(0),
+                                         T hi = T(1)) {
   int last = 0;
-  double width = 1.0;
+  T width = hi - lo;
   for (int it = 0; it < 200; ++it) {
-    double mid = (lo * fhi - hi * flo) / (fhi - flo);
-    if ((it & 1) && hi - lo > 0.5 * width) mid = 0.5 * (lo + hi);
-    if (!(mid > lo && mid < hi)) mid = 0.5 * (lo + hi);
+    T mid = (lo * fhi - hi * flo) / (fhi - flo);
+    if ((it & 1) && hi - lo > T(0.5) * width) mid = T(0.5) * (lo + hi);
+    if (!(mid > lo && mid < hi)) mid = T(0.5) * (lo + hi);
     if (mid <= lo || mid >= hi) break;
     if (it & 1) width = hi - lo;
-    const double fm = side_val(mid);
-    if (fm >= 0.0) {
+    const T fm = side_val(mid);
+    if (fm >= T(0)) {
       lo = mid;
       flo = fm;
-      if (last > 0) fhi *= 0.5;
+      if (last > 0) fhi *= T(0.5);
       last = 1;
     } else {
       hi = mid;
       fhi = fm;
-      if (last < 0) flo *= 0.5;
+      if (last < 0) flo *= T(0.5);
       last = -1;
     }
   }
   *hi_out = hi;
   return lo;
 }
+
+// Plain Illinois on the bracket [lo, hi] (side(lo) = flo >= 0 > fhi =
+// side(hi)), updated in place, until it is at most tol x hi wide, stops
+// shrinking, or maxit evaluations were spent.  Superlinear for a simple root;
+// no bisection steps (the caller finishes with last_nonneg if needed).
+template <class S, class T>
+__device__ __forceinline__ void illinois(const S& side, T& lo, T& hi, T& flo, T& fhi, T tol,
+                                         int maxit) {
+  int last = 0;
+  for (int it = 0; it < maxit && hi - lo > tol * hi; ++it) {
+    T mid = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(mid > lo && mid < hi)) mid = T(0.5) * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    const T fm = side(mid);
+    if (fm >= T(0)) {
+      lo = mid;
+      flo = fm;
+      if (last > 0) fhi *= T(0.5);
+      last = 1;
+    } else {
+      hi = mid;
+      fhi = fm;
+      if (last < 0) flo *= T(0.5);
+      last = -1;
+    }
+  }
+}
+
+// Event location on the continuous extension: the last th in [0, 1] on the
+// non-negative side of a function given in FP64 (f64) and, to FP32 rounding,
+// by a cheap FP32 model (f32), with f64(0) = flo >= 0 > fhi = f64(1).  The FP32
+// model's root (plain Illinois to 2^-22 relative) is widened by SEED_WIDEN on
+// each side; FP64 values at the two ends confirm that the root lies inside
+// (else the part of [0, 1] left or right of it holds one), and FP64 Illinois
+// narrows that bracket to SEED_TOL64 relative, far below the 1e-10 relative
+// overshoot of a switch and below the rounding of an escape point.  About six
+// FP64 evaluations where bisection-guarded Illinois from [0, 1] to the last
+// bit takes twenty or more.  Returns lo; *hi_out the end past it.
+constexpr float SEED_TOL32 = 0x1p-22f;
+constexpr double SEED_WIDEN = 0x1p-16;
+constexpr double SEED_TOL64 = 0x1p-44;
+template <class S64, class S32>
+__device__ __forceinline__ double last_nonneg_seeded(const S64& f64, const S32& f32, double flo,
+                                                     double fhi, double* hi_out) {
+  float l = 0.0f, u = 1.0f, fl = (float)flo, fu = (float)fhi;
+  if (!(fl >= 0.0f)) fl = 0.0f;
+  if (!(fu < 0.0f)) fu = -1e-30f;
+  illinois(f32, l, u, fl, fu, SEED_TOL32, 40);
+  double lo = 0.0, hi = 1.0;
+  const double a = fmax(0.0, (double)l - SEED_WIDEN), b = fmin(1.0, (double)u + SEED_WIDEN);
+  const double fa = (a > 0.0) ? f64(a) : flo;
+  if (fa < 0.0) {
+    hi = a;                                        // the root lies left of the FP32 bracket
+    fhi = fa;
+  } else {
+    lo = a;
+    flo = fa;
+    const double fb = (b < 1.0) ? f64(b) : fhi;
+    if (fb >= 0.0) {
+      lo = b;                                      // right of it
+      flo = fb;
+    } else {
+      hi = b;
+      fhi = fb;
+    }
+  }
+  illinois(f64, lo, hi, flo, fhi, SEED_TOL64, 40);
+  if (hi - lo > SEED_TOL64 * hi) return last_nonneg(f64, flo, fhi, hi_out, lo, hi);
+  *hi_out = hi;
+  return lo;
+}
+
+// FP32 model of the null-cone side function sig F(x(th)), F = 3 z (m.x) -
+// m_z |x|^2, along the continuous extension x(th) = y + d(th), d(th) =
+// th (r2 + (1 - th) (r3 + th (r4 + (1 - th) r5))): F(y + d) = F0 + gF.d +
+// 3 d_z (m.d) - m_z |d|^2 with F0 = F(y) from FP64 and gF = grad F(y).
+struct ConeModel32 {
+  float sg, F0, m0, m1, m2, gF[3], r2[3], r3[3], r4[3], r5[3];
+  // y, R2..R5: the first three (position) components
+  template <class T>
+  __device__ __forceinline__ void init(float sig, float F0f, float cm0, float cm1, float cm2,
+                                       const T* y, const T* R2, const T* R3, const T* R4,
+                                       const T* R5) {
+    sg = sig;
+    F0 = F0f;
+    m0 = cm0;
+    m1 = cm1;
+    m2 = cm2;
+    const float y0 = (float)y[0], y1 = (float)y[1], y2 = (float)y[2];
+    const float mx = m0 * y0 + m1 * y1 + m2 * y2;
+    gF[0] = 3.0f * y2 * m0 - 2.0f * m2 * y0;
+    gF[1] = 3.0f * y2 * m1 - 2.0f * m2 * y1;
+    gF[2] = 3.0f * mx + 3.0f * y2 * m2 - 2.0f * m2 * y2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r2[i] = (float)R2[i];
+      r3[i] = (float)R3[i];
+      r4[i] = (float)R4[i];
+      r5[i] = (float)R5[i];
+    }
+  }
+  __device__ __forceinline__ float operator()(float th) const {
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      d[i] = th * (r2[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i])));
+    const float md = m0 * d[0] + m1 * d[1] + m2 * d[2];
+    const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    return sg * (F0 + (gF[0] * d[0] + gF[1] * d[1] + gF[2] * d[2]) + (3.0f * d[2] * md - m2 * dd));
+  }
+};
+
+// FP32 model of r_out^2 - |x(th)|^2 on the same extension: c0 - 2 y.d - |d|^2,
+// c0 = r_out^2 - |y|^2 from FP64.
+struct EscapeModel32 {
+  float c0, y[3], r2[3], r3[3], r4[3], r5[3];
+  template <class T>
+  __device__ __forceinline__ void init(float c0f, const T* yd, const T* R2, const T* R3,
+                                       const T* R4, const T* R5) {
+    c0 = c0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      y[i] = (float)yd[i];
+      r2[i] = (float)R2[i];
+      r3[i] = (float)R3[i];
+      r4[i] = (float)R4[i];
+      r5[i] = (float)R5[i];
+    }
+  }
+  __device__ __forceinline__ float operator()(float th) const {
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      d[i] = th * (r2[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i])));
+    return c0 - (2.0f * (y[0] * d[0] + y[1] * d[1] + y[2] * d[2]) +
+                 (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  }
+};
 
 // One attempted Dormand-Prince step.  Returns -1 to continue, else the final
 // ray status.  hook.on_accept sees every accepted step (start, end, stages).

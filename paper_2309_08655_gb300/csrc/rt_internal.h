@@ -9,7 +9,19 @@
 #include "rt_dual.cuh"
 #include "rt_sample_core.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace rtk {
+
+// NVTX range over a public entry point (the host-side enqueue of its
+// kernels), named after the call, for timeline profilers; without an attached
+// tool a push or pop is a check of one pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TraceParams {
   const StarDev* stars;     // device array of nstars star descriptors
@@ -136,6 +148,10 @@ cudaError_t occupancy_fp64(int block, int* occ);
 cudaError_t occupancy_mixed(int block, int* occ);
 cudaError_t occupancy_batch_fp64(int block, int* occ);
 cudaError_t occupancy_batch_mixed(int block, int* occ);
+// Forward tracing in double-float (rt_trace_df.cu)
+cudaError_t launch_trace_df(const TraceParams& p, int block, int blocks_per_sm,
+                            cudaStream_t stream);
+cudaError_t occupancy_trace_df(int block, int* occ);
 
 // Backward image-plane tracing (one ray per pixel, ny x nx row-major).
 struct BackLaunch {

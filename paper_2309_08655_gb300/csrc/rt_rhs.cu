@@ -51,6 +51,7 @@ __global__ void hamilton_rhs_kernel(StarDev s, int64_t n, const double* state, d
 
 extern "C" rt_status rt_hamilton_rhs(const rt_star* star, int64_t n, const double* d_state,
                                      double* d_H, double* d_dydl, void* stream) {
+  rtk::NvtxRange nvtx_range("rt_hamilton_rhs");
   using namespace rtk;
   if (!star) {
     set_last_error("star is NULL");

@@ -382,8 +382,9 @@ __device__ void tail_groups(const TraceParams& p, const double* recs, unsigned l
         const StarDev& s = p.stars[L.star];
         const int64_t n = p.n;
         p.state[cc * n + L.ray] = (cc < 3) ? L.yc * s.R_km : L.yc * s.ma_eV;
+        __syncwarp(gm);                 // the group's state writes before its status
         if (cc == 0) {
-          p.status[L.ray] = (uint8_t)st;
+          status_after_state(p, L.ray, st);
           if (p.nacc) p.nacc[L.ray] = L.na;
           if (p.nrej) p.nrej[L.ray] = L.nr;
           if (p.ts) atomicMax(p.ts + 1 + L.star, global_ns());

@@ -77,7 +77,7 @@ __device__ void store_lane(const TraceParams& p, int64_t i, const Lane& L, int s
   p.state[3 * n + i] = L.y[3] * L.ma_eV;
   p.state[4 * n + i] = L.y[4] * L.ma_eV;
   p.state[5 * n + i] = L.y[5] * L.ma_eV;
-  p.status[i] = (uint8_t)st;
+  status_after_state(p, i, st);
   if (p.nacc) p.nacc[i] = L.na;
   if (p.nrej) p.nrej[i] = L.nr;
 }
@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(128) trace_fp64_kernel(TraceParams p) {
       const int pass = p.order ? (int)(idx / p.n) : 0;
       const int64_t i = idx - (int64_t)pass * p.n;
       if (p.status[i] != p.claim_status ||
-          (p.order && cost_bucket(p.stars[find_star(p, i)], p.state, p.n, i) != pass))
+          (p.order && (cost_bucket(p.stars[find_star(p, i)], p.state, p.n, i) != pass ||
+                       !status_still(p, i, p.claim_status))))
         return -1;
       load_lane(p, i, L);
       na0 = L.na;

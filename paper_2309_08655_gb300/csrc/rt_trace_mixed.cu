@@ -1,7 +1,10 @@
 // Mixed-precision forward tracing: the Dormand-Prince stages (the analytic
 // right-hand side and the stage combinations) run in FP32 with FP32
-// accumulation of the increments; the ray state is kept in FP64 and receives
-// each accepted increment in FP64.
+// accumulation of the increments; the ray state is kept in double-float (an
+// unevaluated sum of two floats, ~48 significant bits) and receives each
+// accepted increment in double-float arithmetic, so that an attempt runs on
+// the FP32 pipe alone (on this GPU the FP64 pipe, conversions between FP32
+// and FP64 included, has 1/64 of its rate).
 //
 // Increment splitting.  The position derivative is dx/dl = 2k + c(x, k), where
 // the correction c (metric and plasma terms) is small away from the star.  With
@@ -23,6 +26,7 @@
 #include <stdint.h>
 
 #include "rt_backward.cuh"
+#include "rt_df.cuh"
 #include "rt_device.cuh"
 #include "rt_internal.h"
 
@@ -118,10 +122,29 @@ __device__ float initial_step32(const RayConst<float>& c, const double* md, cons
   return fminf(100.0f * h, h1);
 }
 
+// The Goldreich-Julian angular factor F = 3 z (m.x) - m_z |x|^2 in
+// double-float, rounded to FP32 at the end: next to the null cone it is a
+// small difference of O(|x|^2) terms.
+__device__ __forceinline__ float cone_F2(const DF* y, const DF* m) {
+  const DF mx = m[0] * y[0] + m[1] * y[1] + m[2] * y[2];
+  const DF r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+  const DF F = (y[2] * mx) * 3.0f - m[2] * r2;
+  return F.hi + F.lo;
+}
+
+// c(x, k) and dk/dl with the null-cone factor F given: at the state's FP32
+// position xf (the rounding of the double-float state).
+__device__ __forceinline__ void rhs32F(const RayConst<float>& c, float F, const float* xf,
+                                       const float* kf, float* f) {
+  const float r2 = xf[0] * xf[0] + xf[1] * xf[1] + xf[2] * xf[2];
+  ham_rhs<float, true, true>(c, xf[0], xf[1], xf[2], kf[0], kf[1], kf[2], f[0], f[1], f[2], f[3],
+                             f[4], f[5], F * __frcp_rn(r2));
+}
+
 struct LaneM {
   RayConst<float> c;
-  double md[3];        // magnetic axis in FP64 (for the null-cone factor)
-  double y[6];
+  DF m[3];             // magnetic axis in double-float (for the null-cone factor)
+  DF y[6];             // state (x / R, k / m_a) in double-float; y[i].hi is its FP32 rounding
   float f0[6];         // (c, dk/dl) at y (first-same-as-last)
   float h;
   int na, nr;
@@ -148,10 +171,11 @@ __device__ void load_lane_m(const TraceParams& p, int64_t i, LaneM& L) {
   L.R_km = s.R_km;
   L.ma_eV = s.ma_eV;
   const double iR = 1.0 / s.R_km, im = 1.0 / s.ma_eV;
+  double yd[6], md[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    L.y[c] = p.state[c * n + i] * iR;
-    L.y[3 + c] = p.state[(3 + c) * n + i] * im;
+    yd[c] = p.state[c * n + i] * iR;
+    yd[3 + c] = p.state[(3 + c) * n + i] * im;
   }
   const double om = 1.0 + p.state[6 * n + i];
   double sp, cpsi;
@@ -161,22 +185,26 @@ __device__ void load_lane_m(const TraceParams& p, int64_t i, LaneM& L) {
   L.c.pa = (float)s.plasma_a;
   L.c.W2 = (float)(om * om);
   L.c.iW2 = (float)(1.0 / (om * om));
-  L.md[0] = s.sin_tm * cpsi;
-  L.md[1] = s.sin_tm * sp;
-  L.md[2] = s.cos_tm;
-  L.c.m0 = (float)L.md[0];
-  L.c.m1 = (float)L.md[1];
-  L.c.m2 = (float)L.md[2];
+  md[0] = s.sin_tm * cpsi;
+  md[1] = s.sin_tm * sp;
+  md[2] = s.cos_tm;
+  L.c.m0 = (float)md[0];
+  L.c.m1 = (float)md[1];
+  L.c.m2 = (float)md[2];
   L.c.disp = s.dispersion;
   L.c.plasma = s.plasma;
-  L.c.sig = side_md(L.md, L.y[0], L.y[1], L.y[2]);
+  L.c.sig = side_md(md, yd[0], yd[1], yd[2]);
   L.switching = false;
   L.h_resume = 0.0f;
   float kf[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) kf[c] = (float)L.y[3 + c];
-  rhs32c(L.c, L.md, L.y, kf, L.f0);
-  L.h = initial_step32(L.c, L.md, L.y, L.f0, (float)p.rtol, (float)p.atol);
+  for (int c = 0; c < 3; ++c) kf[c] = (float)yd[3 + c];
+  rhs32c(L.c, md, yd, kf, L.f0);
+  L.h = initial_step32(L.c, md, yd, L.f0, (float)p.rtol, (float)p.atol);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) L.y[c] = df_of(yd[c]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) L.m[c] = df_of(md[c]);
   L.na = 0;
   L.nr = 0;
   L.noisy_rej = 0;
@@ -187,37 +215,38 @@ __device__ void store_lane_m(const TraceParams& p, int64_t i, const LaneM& L, in
   const int64_t n = p.n;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    p.state[c * n + i] = L.y[c] * L.R_km;
-    p.state[(3 + c) * n + i] = L.y[3 + c] * L.ma_eV;
+    p.state[c * n + i] = df_d(L.y[c]) * L.R_km;
+    p.state[(3 + c) * n + i] = df_d(L.y[3 + c]) * L.ma_eV;
   }
-  p.status[i] = (uint8_t)st;
+  status_after_state(p, i, st);
   if (p.nacc) p.nacc[i] = L.na;
   if (p.nrej) p.nrej[i] = L.nr;
 }
 
-// Position on the continuous extension at fraction th (FP64 large part + FP32
-// small part).
-__device__ __forceinline__ void dense_x(const LaneM& L, float h, float th, const float* sR,
+// Position on the continuous extension at fraction th of a step from the
+// FP64 state y (FP64 large part + FP32 small part).
+__device__ __forceinline__ void dense_x(const double* y, float h, float th, const float* sR,
                                         const float* r3, const float* r4, const float* r5,
                                         double* xd) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
-    xd[i] = L.y[i] + (double)th * 2.0 * (double)h * L.y[3 + i] +
+    xd[i] = y[i] + (double)th * 2.0 * (double)h * y[3 + i] +
             (double)(th * (sR[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]))));
 }
 
 // Observer of accepted steps (forward tracing needs none).
 struct NoHookM {
   static constexpr bool active = false;
-  __device__ __forceinline__ void on_accept(const LaneM&, const double*, const float*, float,
-                                            float, const float*, const float*, const float*,
+  __device__ __forceinline__ void on_accept(const LaneM&, const DF*, const float*, float, float,
+                                            const float*,
                                             const float*, const float*, const float*,
-                                            const float*, const float*, const float*) {}
+                                            const float*, const float*, const float*,
+                                            const float*, const float*) {}
 };
 
 // One attempted step.  Returns -1 to continue, RAY_PROMOTED to hand the ray to
 // the FP64 pass, else the final status.  hook.on_accept sees every accepted
-// step: its FP64 start (L.y) and end (yn), the start in FP32 (yf), the step,
+// step: its start (L.y) and end (yn) in double-float, the start in FP32 (yf), the step,
 // the null-cone factor and its gradient at the start (F0, gF), and the FP32
 // small parts of the continuous extension (position: sR, r3, r4, r5 about
 // y + 2 h k th; momentum: dK, q3, q4, q5).
@@ -227,7 +256,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
   const float rtol = (float)p.rtol, atol = (float)p.atol;
   float yf[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) yf[i] = (float)L.y[i];
+  for (int i = 0; i < 6; ++i) yf[i] = L.y[i].hi;
   float h = L.h;
   {
     // displacement of one step at most STEP_REACH x the distance to the centre
@@ -249,15 +278,18 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
     R1[i] = L.f0[i];
     K1[i] = L.f0[3 + i];
   }
-  // null-cone factor F = 3 z (m.x) - m_z |x|^2 and its gradient at the start, FP64
-  float F0 = 0.0f, gF[3] = {0.0f, 0.0f, 0.0f};
+  // null-cone factor F = 3 z (m.x) - m_z |x|^2 at the start in double-float
+  // (a small difference of O(|x|^2) terms next to the cone); its gradient gF
+  // and its derivative gL along the straight part 2 h k of the step only
+  // multiply the step's displacement, FP32
+  float F0 = 0.0f, gL = 0.0f, gF[3] = {0.0f, 0.0f, 0.0f};
   if (L.c.plasma == PLASMA_GJ) {
-    const double mx = L.md[0] * L.y[0] + L.md[1] * L.y[1] + L.md[2] * L.y[2];
-    const double r2d = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
-    F0 = (float)(3.0 * L.y[2] * mx - L.md[2] * r2d);
-    gF[0] = (float)(3.0 * L.y[2] * L.md[0] - 2.0 * L.md[2] * L.y[0]);
-    gF[1] = (float)(3.0 * L.y[2] * L.md[1] - 2.0 * L.md[2] * L.y[1]);
-    gF[2] = (float)(3.0 * mx + 3.0 * L.y[2] * L.md[2] - 2.0 * L.md[2] * L.y[2]);
+    F0 = cone_F2(L.y, L.m);
+    const float mxf = L.c.m0 * yf[0] + L.c.m1 * yf[1] + L.c.m2 * yf[2];
+    gF[0] = 3.0f * yf[2] * L.c.m0 - 2.0f * L.c.m2 * yf[0];
+    gF[1] = 3.0f * yf[2] * L.c.m1 - 2.0f * L.c.m2 * yf[1];
+    gF[2] = 3.0f * mxf + 3.0f * yf[2] * L.c.m2 - 2.0f * L.c.m2 * yf[2];
+    gL = 2.0f * h * (gF[0] * yf[3] + gF[1] * yf[4] + gF[2] * yf[5]);
   }
   float t[6], f[6], dks[3], dx[3], xs[3];
 #define RT_STAGE(Rout, Kout, cj, SUMR, SUMK)                                          \
@@ -293,20 +325,20 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
 #undef RT_STAGE
   // 5th-order increments: small position part and momentum
   float sR[3], dK[3];
-  double yn[6];
+  DF yn[6];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     sR[i] = h * ((float)DP::b1 * R1[i] + (float)DP::b3 * R3[i] + (float)DP::b4 * R4[i] +
                  (float)DP::b5 * R5[i] + (float)DP::b6 * R6[i]);
     dK[i] = h * ((float)DP::b1 * K1[i] + (float)DP::b3 * K3[i] + (float)DP::b4 * K4[i] +
                  (float)DP::b5 * K5[i] + (float)DP::b6 * K6[i]);
-    yn[i] = L.y[i] + 2.0 * (double)h * L.y[3 + i] + (double)sR[i];
-    yn[3 + i] = L.y[3 + i] + (double)dK[i];
+    yn[i] = (L.y[i] + L.y[3 + i] * (2.0f * h)) + sR[i];
+    yn[3 + i] = L.y[3 + i] + dK[i];
   }
   // stage 7 at the new point (first-same-as-last)
   float fn[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) t[i] = (float)yn[i];
+  for (int i = 0; i < 6; ++i) t[i] = yn[i].hi;
 #pragma unroll
   for (int i = 0; i < 3; ++i) dx[i] = 2.0f * h * yf[3 + i] + sR[i];
   rhs32s(L.c, F0, gF, t, dx, t + 3, fn);
@@ -314,6 +346,15 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
   for (int i = 0; i < 3; ++i) {
     R7[i] = 2.0f * dK[i] + fn[i];
     K7[i] = fn[3 + i];
+  }
+  // F at the step's end by the same expansion (the side test; the next step
+  // starts from F in FP64, which settles a crossing this test missed)
+  float Fend = 0.0f;
+  if (L.c.plasma == PLASMA_GJ) {
+    const float md = L.c.m0 * dx[0] + L.c.m1 * dx[1] + L.c.m2 * dx[2];
+    const float dd = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    Fend = F0 + (gL + (gF[0] * sR[0] + gF[1] * sR[1] + gF[2] * sR[2])) +
+           (3.0f * dx[2] * md - L.c.m2 * dd);
   }
   // error estimate (sum_j e_j = 0 removes the 2 h k_n part) and its FP32 floor
   float s = 0.0f, snk = 0.0f;
@@ -326,7 +367,7 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
     const float a1 = (float)DP::e1 * v1, a3 = (float)DP::e3 * v3, a4 = (float)DP::e4 * v4;
     const float a5 = (float)DP::e5 * v5, a6 = (float)DP::e6 * v6, a7 = (float)DP::e7 * v7;
     const float e = h * (a1 + a3 + a4 + a5 + a6 + a7);
-    const float sc = atol + rtol * fmaxf(fabsf(yf[i]), fabsf((float)yn[i]));
+    const float sc = atol + rtol * fmaxf(fabsf(yf[i]), fabsf(t[i]));
     s += (e / sc) * (e / sc);
     if (!xp) {
       const float nz = NOISE_C * EPS32 * fabsf(h) *
@@ -355,20 +396,38 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
                    (float)DP::d5 * R5[i] + (float)DP::d6 * R6[i] + (float)DP::d7 * R7[i]);
     }
   }
-  if (en <= 1.0f && gj && !L.switching && L.c.sig * side_md(L.md, yn[0], yn[1], yn[2]) < 0.0f) {
-    // the step crossed the null cone: locate and redo the step to end just past it
+  if (en <= 1.0f && gj && !L.switching && L.c.sig * Fend < 0.0f) {
+    // the step crossed the null cone: locate the crossing on the continuous
+    // extension and redo the step to end just past it.  F along the step by
+    // its expansion about the start, in FP32: with d(th) = th (2 h k + S(th))
+    // (S the small parts), F = F0 + th gL + th gF.S(th) + 3 d_z (m.d) - m_z |d|^2,
+    // F0 and gL from FP64; its rounding, ~eps32 (|F0| + |gL|), moves a
+    // transverse crossing by ~eps32 in th, the resolution of th itself.
+    const float sgn = L.c.sig;
+    auto side_val = [&](float th) {
+      float d[3], gS = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float Si = sR[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]));
+        gS += gF[i] * Si;
+        d[i] = th * (2.0f * h * yf[3 + i] + Si);
+      }
+      const float md = L.c.m0 * d[0] + L.c.m1 * d[1] + L.c.m2 * d[2];
+      const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      return sgn * (F0 + th * (gL + gS) + (3.0f * d[2] * md - L.c.m2 * dd));
+    };
+    float flo = sgn * F0, fhi = sgn * Fend;
+    if (!(flo >= 0.0f)) flo = 0.0f;                 // the start is on its own side
+    if (!(fhi < 0.0f)) fhi = -1e-30f;
+    // plain Illinois to 2^-22 relative (well inside the 1e-6 overshoot), the
+    // guarded form only if that stalls
     float lo = 0.0f, hi = 1.0f;
-    for (int it = 0; it < 40; ++it) {
-      const float mid = 0.5f * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      double xd[3];
-      dense_x(L, h, mid, sR, r3, r4, r5, xd);
-      if (L.c.sig * side_md(L.md, xd[0], xd[1], xd[2]) >= 0.0f) lo = mid; else hi = mid;
-    }
+    illinois(side_val, lo, hi, flo, fhi, SEED_TOL32, 40);
+    if (hi - lo > SEED_TOL32 * hi) lo = last_nonneg(side_val, flo, fhi, &hi, lo, hi);
     ++L.nr;
     if (lo < SWITCH_MIN_FRACTION_M) {
       L.c.sig = -L.c.sig;
-      rhs32c(L.c, L.md, L.y, yf + 3, L.f0);
+      rhs32F(L.c, F0, yf, yf + 3, L.f0);
       L.h = h;
     } else {
       L.h_resume = h;
@@ -391,42 +450,38 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
       }
       hook.on_accept(L, yn, yf, h, F0, gF, sR, r3, r4, r5, dK, q3, q4, q5);
     }
-    const double rnew2 = yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2];
-    if (rnew2 >= p.r_out * p.r_out) {
-      // locate |x(th)| = r_out on the continuous extension: Illinois on
-      // r_out^2 - |x(th)|^2 (FP64 values), th in FP32 to its last bit
+    // escape and capture tests in FP32 (a step that ends within rounding of
+    // r_out escapes at its end point)
+    const float rnew2f = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    if (rnew2f >= (float)(p.r_out * p.r_out)) {
+      // locate |x(th)| = r_out on the continuous extension: r_out^2 - |x(th)|^2
+      // by its FP32 expansion about the start, c0 - 2 y.d - |d|^2 with
+      // c0 = r_out^2 - |y|^2 from FP64 and d(th) = th (2 h k + S(th)); its
+      // rounding moves the root by ~eps32 in th, the resolution of th
       const double ro2 = p.r_out * p.r_out;
+      double y0d[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) y0d[i] = df_d(L.y[i]);
+      double c0d = ro2 - (y0d[0] * y0d[0] + y0d[1] * y0d[1] + y0d[2] * y0d[2]);
+      if (!(c0d >= 0.0)) c0d = 0.0;
+      const float c0 = (float)c0d;
+      auto inside = [&](float th) {
+        float d[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          d[i] = th * (2.0f * h * yf[3 + i] +
+                       (sR[i] + (1.0f - th) * (r3[i] + th * (r4[i] + (1.0f - th) * r5[i]))));
+        return c0 - (2.0f * (yf[0] * d[0] + yf[1] * d[1] + yf[2] * d[2]) +
+                     (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+      };
+      float flo = c0, fhi = inside(1.0f);
+      if (!(fhi < 0.0f)) fhi = -1e-30f;
       float lo = 0.0f, hi = 1.0f;
-      double flo = ro2 - (L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
-      if (!(flo >= 0.0)) flo = 0.0;
-      double fhi = ro2 - rnew2;
-      if (!(fhi < 0.0)) fhi = -1e-300;
-      int last = 0;
-      float width = 1.0f;
-      for (int it = 0; it < 100; ++it) {
-        float mid = (float)(((double)lo * fhi - (double)hi * flo) / (fhi - flo));
-        if ((it & 1) && hi - lo > 0.5f * width) mid = 0.5f * (lo + hi);
-        if (!(mid > lo && mid < hi)) mid = 0.5f * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (it & 1) width = hi - lo;
-        double xd[3];
-        dense_x(L, h, mid, sR, r3, r4, r5, xd);
-        const double fm = ro2 - (xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
-        if (fm >= 0.0) {
-          lo = mid;
-          flo = fm;
-          if (last > 0) fhi *= 0.5;
-          last = 1;
-        } else {
-          hi = mid;
-          fhi = fm;
-          if (last < 0) flo *= 0.5;
-          last = -1;
-        }
-      }
+      illinois(inside, lo, hi, flo, fhi, SEED_TOL32, 40);
+      if (hi - lo > SEED_TOL32 * hi) lo = last_nonneg(inside, flo, fhi, &hi, lo, hi);
       const float th = 0.5f * (lo + hi);
       double xd[3];
-      dense_x(L, h, th, sR, r3, r4, r5, xd);
+      dense_x(y0d, h, th, sR, r3, r4, r5, xd);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const float q3 = h * K1[i] - dK[i];
@@ -434,8 +489,9 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
         const float q5 = h * ((float)DP::d1 * K1[i] + (float)DP::d3 * K3[i] +
                               (float)DP::d4 * K4[i] + (float)DP::d5 * K5[i] +
                               (float)DP::d6 * K6[i] + (float)DP::d7 * K7[i]);
-        L.y[3 + i] += (double)(th * (dK[i] + (1.0f - th) * (q3 + th * (q4 + (1.0f - th) * q5))));
-        L.y[i] = xd[i];
+        L.y[3 + i] = L.y[3 + i] +
+                     th * (dK[i] + (1.0f - th) * (q3 + th * (q4 + (1.0f - th) * q5)));
+        L.y[i] = df_of(xd[i]);
       }
       return RAY_ESCAPED;
     }
@@ -443,10 +499,10 @@ __device__ int advance_m(const TraceParams& p, LaneM& L, Hook& hook) {
     for (int i = 0; i < 6; ++i) L.y[i] = yn[i];
 #pragma unroll
     for (int i = 0; i < 6; ++i) L.f0[i] = fn[i];
-    if (rnew2 <= p.r_capture * p.r_capture) return RAY_CAPTURED;
-    if (gj && L.c.sig * side_md(L.md, L.y[0], L.y[1], L.y[2]) < 0.0f) {
+    if (rnew2f <= (float)(p.r_capture * p.r_capture)) return RAY_CAPTURED;
+    if (gj && L.c.sig * Fend < 0.0f) {
       L.c.sig = -L.c.sig;             // past the cone: continue on the other side
-      rhs32c(L.c, L.md, L.y, t + 3, L.f0);
+      rhs32F(L.c, cone_F2(L.y, L.m), t, t + 3, L.f0);
     }
     if (L.switching) {
       L.h = L.h_resume;
@@ -480,7 +536,8 @@ __global__ void __launch_bounds__(256) trace_mixed_kernel(TraceParams p) {
       const int pass = p.order ? (int)(idx / p.n) : 0;
       const int64_t i = idx - (int64_t)pass * p.n;
       if (p.status[i] != RAY_READY ||
-          (p.order && cost_bucket(p.stars[find_star_m(p, i)], p.state, p.n, i) != pass))
+          (p.order && (cost_bucket(p.stars[find_star_m(p, i)], p.state, p.n, i) != pass ||
+                       !status_still(p, i, RAY_READY))))
         return -1;
       load_lane_m(p, i, L);
       return i;
@@ -536,7 +593,7 @@ struct CrossingHookM {
   bool on;              // false: a forward ray of a mixed batch (no crossing search)
   CrossingAcc acc;
   RayConst<double> c;   // the pixel's constants in FP64 (sig follows the lane's)
-  __device__ void on_accept(const LaneM& L, const double* yn, const float* yf, float h, float F0,
+  __device__ void on_accept(const LaneM& L, const DF* yn, const float* yf, float h, float F0,
                             const float* gF, const float* sR, const float* r3, const float* r4,
                             const float* r5, const float* dK, const float* q3, const float* q4,
                             const float* q5) {
@@ -570,27 +627,37 @@ struct CrossingHookM {
       p4[3 + i] = q4[i];
       p5[3 + i] = q5[i];
     }
-    // FP64 points of the continuous extension: FP64 start and increment, FP32
-    // small parts
-    const double* y = L.y;
+    // FP64 points of the continuous extension: FP64 start and increment (from
+    // the double-float states, formed only where the search needs a point),
+    // FP32 small parts
     auto dense64 = [&](double th, double* yd, double* yp) {
       const double u = 1.0 - th;
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
+        const double y0 = df_d(L.y[i]);
         const double Q3 = (double)p4[i] + u * (double)p5[i];
         const double Q2 = (double)p3[i] + th * Q3;
-        const double Q1 = (yn[i] - y[i]) + u * Q2;
-        yd[i] = y[i] + th * Q1;
+        const double Q1 = (df_d(yn[i]) - y0) + u * Q2;
+        yd[i] = y0 + th * Q1;
         if (yp) yp[i] = Q1 + th * (u * (Q3 - th * (double)p5[i]) - Q2);
       }
     };
-    acc.scan(c, L.y, yn, sc, yf, p2, p3, p4, p5, dense64);
+    // the start in FP64 only for the first step's resonance sign; the end
+    // from the extension at th = 1 where the screen leaves its sign open
+    double y0d[6];
+    if (!acc.have_g) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) y0d[i] = df_d(L.y[i]);
+    }
+    acc.scan(c, acc.have_g ? nullptr : y0d, nullptr, sc, yf, p2, p3, p4, p5, dense64);
   }
 };
 
-__device__ void load_pixel_m(const BackParams& bp, int64_t pix, LaneM& L, RayConst<double>& c,
-                             float rtol, float atol) {
-  pixel_init(bp, pix, L.y, c);
+// Returns the distance of the pixel's start point from the centre.
+__device__ double load_pixel_m(const BackParams& bp, int64_t pix, LaneM& L, RayConst<double>& c,
+                               float rtol, float atol) {
+  double yd[6];
+  pixel_init(bp, pix, yd, c);
   L.R_km = bp.s.R_km;
   L.ma_eV = bp.s.ma_eV;
   L.c.rs = (float)c.rs;
@@ -598,9 +665,7 @@ __device__ void load_pixel_m(const BackParams& bp, int64_t pix, LaneM& L, RayCon
   L.c.pa = (float)c.pa;
   L.c.W2 = (float)c.W2;
   L.c.iW2 = (float)c.iW2;
-  L.md[0] = c.m0;
-  L.md[1] = c.m1;
-  L.md[2] = c.m2;
+  const double md[3] = {c.m0, c.m1, c.m2};
   L.c.m0 = (float)c.m0;
   L.c.m1 = (float)c.m1;
   L.c.m2 = (float)c.m2;
@@ -611,13 +676,18 @@ __device__ void load_pixel_m(const BackParams& bp, int64_t pix, LaneM& L, RayCon
   L.h_resume = 0.0f;
   float kf[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) kf[i] = (float)L.y[3 + i];
-  rhs32c(L.c, L.md, L.y, kf, L.f0);
-  L.h = initial_step32(L.c, L.md, L.y, L.f0, rtol, atol);
+  for (int i = 0; i < 3; ++i) kf[i] = (float)yd[3 + i];
+  rhs32c(L.c, md, yd, kf, L.f0);
+  L.h = initial_step32(L.c, md, yd, L.f0, rtol, atol);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) L.y[i] = df_of(yd[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) L.m[i] = df_of(md[i]);
   L.na = 0;
   L.nr = 0;
   L.noisy_rej = 0;
   L.last_rej = false;
+  return sqrt(yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2]);
 }
 
 __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
@@ -652,9 +722,8 @@ __global__ void __launch_bounds__(256) backward_mixed_kernel(BackParams bp) {
           pix = -2;
         } else {
           pix = idx;
-          load_pixel_m(bp, idx, L, hk.c, (float)bp.rtol, (float)bp.atol);
           // escaped once back at the distance the ray started from
-          tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+          tp.r_out = load_pixel_m(bp, idx, L, hk.c, (float)bp.rtol, (float)bp.atol);
           hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
         }
       }
@@ -740,9 +809,8 @@ __global__ void __launch_bounds__(256) batch_mixed_kernel(TraceParams p, ImgTabl
       img = find_image(t, g);
       pix = g - t.off[img];
       const BackParams& bp = t.img[img];
-      load_pixel_m(bp, pix, L, hk.c, (float)p.rtol, (float)p.atol);
       // escaped once back at the distance the ray started from
-      tp.r_out = sqrt(L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2]);
+      tp.r_out = load_pixel_m(bp, pix, L, hk.c, (float)p.rtol, (float)p.atol);
       hk.on = true;
       hk.acc.reset(&bp.s, bp.W, bp.Lc_cut);
       isp = true;

@@ -149,7 +149,7 @@ __device__ void store_rot(const TraceParams& p, int64_t i, const RotLane& L, int
   p.state[5 * n + i] = L.y[5] * L.ma_eV;
   p.state[6 * n + i] = L.delta0 + (L.y[7] - L.om0);   // omega_inf / m_a - 1 at the end
   p.state[7 * n + i] = L.psi0 + L.Om * L.y[6];        // rotation phase at the end
-  p.status[i] = (uint8_t)st;
+  status_after_state(p, i, st);
   if (p.nacc) p.nacc[i] = L.na;
   if (p.nrej) p.nrej[i] = L.nr;
 }
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(128) trace_rot_kernel(TraceParams p) {
         if (idx >= nq) {
           ray = -2;
         } else if (p.status[i] != p.claim_status ||
-                   (p.order && cost_bucket(p.stars[star_of(p, i)], p.state, p.n, i) != pass)) {
+                   (p.order && (cost_bucket(p.stars[star_of(p, i)], p.state, p.n, i) != pass ||
+                                !status_still(p, i, p.claim_status)))) {
           ray = -1;
         } else {
           ray = i;

@@ -20,7 +20,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EEMPTY_SURFACE", "EPARTIAL",
 (RAY_READY, RAY_ESCAPED, RAY_CAPTURED, RAY_NO_ROOT, RAY_MAXSTEPS, RAY_NAN, RAY_STIFF,
  RAY_LAMBDA_END) = range(8)
 RAY_NSTATUS = 8
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 CLAIM_INDEX, CLAIM_COST = 0, 1
 (PLASMA_GJ, PLASMA_VACUUM, PLASMA_HOMOG, PLASMA_LINEAR_Z, PLASMA_RADIAL,
  PLASMA_TWISTED) = range(6)
@@ -113,6 +113,9 @@ def lib():
         L.rt_flops_per_step.restype = ctypes.c_int
         L.rt_flops_per_step.argtypes = [ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_double)]
+        L.rt_flops_per_step_df.restype = ctypes.c_int
+        L.rt_flops_per_step_df.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double)]
         L.rt_flux_value.restype = ctypes.c_int
         L.rt_flux_value.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double,
                                     ctypes.c_double, _vp, _vp, _vp]
@@ -357,6 +360,12 @@ def rt_flops_per_step(dispersion: int, plasma: int) -> list[float]:
     return list(out)
 
 
+def rt_flops_per_step_df(dispersion: int, plasma: int) -> list[float]:
+    out = (ctypes.c_double * 2)()
+    _check(lib().rt_flops_per_step_df(int(dispersion), int(plasma), out))
+    return list(out)
+
+
 def rt_flux_value(star: Star, n, state, weight, status, incl_rad, kappa, F_ray, F,
                   stream=None) -> int:
     return _check(lib().rt_flux_value(star.handle, int(n), _ptr(state), _ptr(weight),
@@ -555,4 +564,4 @@ EXPORTED = ["rt_init_star", "rt_destroy_star", "rt_star_info", "rt_sample_conver
             "rt_batch_graph_create", "rt_graph_launch", "rt_graph_destroy", "rt_batch_autotune",
             "rt_batch_set_images", "rt_sample_conversion_surface_part", "rt_bin_part_max",
             "rt_bin_part_accumulate", "rt_bin_part_finalize", "rt_batch_set_norm",
-            "rt_measure_alu_peak", "rt_hamilton_rhs"]
+            "rt_measure_alu_peak", "rt_hamilton_rhs", "rt_flops_per_step_df"]

@@ -33,7 +33,7 @@ from paper_2309_08655_gb300.build import build
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df"], default="fp64")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
@@ -59,8 +59,8 @@ def main():
     w = torch.empty(a.n, dtype=torch.float64, device=dev)
     s = torch.empty(a.n, dtype=torch.uint8, device=dev)
     rt.rt_sample_conversion_surface(star, a.n, u, st, w, s)
-    prec = rt.PREC_FP64 if a.precision == "fp64" else rt.PREC_MIXED
-    rtol = a.rtol if a.rtol is not None else (1e-10 if prec == rt.PREC_FP64 else 1e-8)
+    prec = {"fp64": rt.PREC_FP64, "mixed": rt.PREC_MIXED, "df": rt.PREC_DF}[a.precision]
+    rtol = a.rtol if a.rtol is not None else (1e-8 if prec == rt.PREC_MIXED else 1e-10)
     opts = rt.make_opts(rtol=rtol, precision=prec,
                         claim_order=rt.CLAIM_COST if a.claim_order == "cost" else rt.CLAIM_INDEX)
     st0, s0 = st.clone(), s.clone()
@@ -114,7 +114,7 @@ def backward(a, dev):
 
 
 def adjoint(a, dev):
-    from . import flux
+    from paper_2309_08655_gb300 import flux
     kw = I.stars_config1()[0]
     kw.update(m_a_eV=1e-5)
     p = torch.tensor([kw["m_a_eV"], kw["B0_G"], kw["theta_m"], kw["M_sun"], kw["R_km"], 1.1],
