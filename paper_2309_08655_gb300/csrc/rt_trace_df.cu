@@ -63,8 +63,22 @@ __constant__ DF c_E[7] = {DPD::e1, DF(0), DPD::e3, DPD::e4, DPD::e5, DPD::e6, DP
 
 // The right-hand side in double-float, not inlined: at ~1500 instructions a
 // call, six inlined copies per attempt would overflow the instruction cache.
-__device__ __noinline__ void rhs_df(const RayConst<DF>& c, const DF* y, DF* f) {
+// The Goldreich-Julian anisotropic medium (the benchmark's) has a copy with
+// the model switches fixed, free of the other media's branches.
+__device__ __noinline__ void rhs_df_any(const RayConst<DF>& c, const DF* y, DF* f) {
   ham_rhs<DF>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+}
+__device__ __noinline__ void rhs_df_gj_aniso(const RayConst<DF>& c0, const DF* y, DF* f) {
+  RayConst<DF> c = c0;
+  c.plasma = PLASMA_GJ;
+  c.disp = DISP_ANISO;
+  ham_rhs<DF>(c, y[0], y[1], y[2], y[3], y[4], y[5], f[0], f[1], f[2], f[3], f[4], f[5]);
+}
+__device__ __forceinline__ void rhs_df(const RayConst<DF>& c, const DF* y, DF* f) {
+  if (c.plasma == PLASMA_GJ && c.disp == DISP_ANISO)
+    rhs_df_gj_aniso(c, y, f);
+  else
+    rhs_df_any(c, y, f);
 }
 
 // F = 3 z (m.x) - m_z |x|^2, whose sign is the side of the null cone
@@ -236,16 +250,30 @@ __device__ __forceinline__ DF last_nonneg_df(const S& side, DF lo, DF hi, float 
   return lo;
 }
 
-// The event's last th on the non-negative side, seeded by the FP32 model of
-// the side function (model(th), FP32): its root, widened by SEED_WIDEN_D on
-// each side, is checked with the double-float side function, which then
-// narrows the bracket (or the part of [0, 1] left or right of it that holds
-// the root, if the check fails).
+// The event's th, seeded by the FP32 model of the side function (model(th),
+// FP32), whose plain Illinois brackets the root to 2^-22 relative.  Where the
+// double-float side function confirms that bracket (two evaluations), the
+// secant through those two values gives the root to ~1e-14 (the bracket is
+// a few ulp of FP32 wide: curvature ~1e-13, rounding of the values ~1e-14),
+// far inside the 1e-10 relative overshoot of a switch; returned as both ends.
+// Otherwise (a grazing crossing, or the model's rounding moved the root
+// further) the model's root, widened by SEED_WIDEN_D on each side, is checked
+// and the double-float Illinois narrows the bracket (or the part of [0, 1]
+// left or right of it that holds the root).
 template <class S, class M>
 __device__ __forceinline__ DF last_nonneg_seeded_df(const S& side, const M& model, float flo,
                                                     float fhi, DF* hi_out) {
   float l = 0.0f, u = 1.0f, fl = flo, fu = fhi;
   illinois(model, l, u, fl, fu, SEED_TOL32, 40);
+  {
+    const float fa = (l > 0.0f) ? side(DF(l, 0.0f)) : flo;
+    const float fb = (u < 1.0f) ? side(DF(u, 0.0f)) : fhi;
+    if (fa >= 0.0f && fb < 0.0f) {
+      const DF th = DF(l, 0.0f) + (DF(u, 0.0f) - DF(l, 0.0f)) * (fa / (fa - fb));
+      *hi_out = th;
+      return th;
+    }
+  }
   const float W = SEED_WIDEN_D * u + 0x1p-30f;
   const float a = fmaxf(0.0f, l - W), b = fminf(1.0f, u + W);
   DF lo(0), hi(1);
