@@ -90,12 +90,12 @@ def _measure_peaks(rt, stream):
 TRAFFIC = {
     # precision -> (sources, digest, kernel, bytes per traced ray)
     "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_internal.h'),
-             None, "trace_fp64_kernel", None),
+             "2b8c4e13855e2cb9", "trace_fp64_kernel", 334770944 / 2096328),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_backward.cuh', 'rt_trace_mixed.cu',
                'rt_internal.h'),
-              None, "trace_mixed_kernel", None),
+              "26743c2d92e573de", "trace_mixed_kernel", 259265792 / 2096328),
     "df": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_df.cuh', 'rt_trace_df.cu', 'rt_internal.h'),
-           None, "trace_df_kernel", None),
+           "ba15684c868aac3f", "trace_df_kernel", 899023360 / 2096328),
 }
 
 
