@@ -95,7 +95,7 @@ TRAFFIC = {
                'rt_internal.h'),
               "26743c2d92e573de", "trace_mixed_kernel", 259265792 / 2096328),
     "df": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_df.cuh', 'rt_trace_df.cu', 'rt_internal.h'),
-           "ba15684c868aac3f", "trace_df_kernel", 899023360 / 2096328),
+           "fdd95867d784f634", "trace_df_kernel", 391314432 / 2096328),
 }
 
 

@@ -300,17 +300,30 @@ __device__ __forceinline__ DF last_nonneg_seeded_df(const S& side, const M& mode
 // ro2 = r_out^2, rc2 = r_capture^2, tol = (rtol, atol).  Returns -1 to
 // continue, else the final ray status.  (Inlined: a lane passed by reference
 // to a call would live in local memory.)
+__device__ __forceinline__ bool out_of_steps(const TraceParams& p, const LaneD& L) {
+  return L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps;
+}
+
+// The attempt's step: the lane's, limited to a displacement of STEP_REACH x
+// the distance to the centre.
+__device__ __forceinline__ DF attempt_h(const LaneD& L) {
+  DF h = L.h;
+  const DF v2 = L.f0[0] * L.f0[0] + L.f0[1] * L.f0[1] + L.f0[2] * L.f0[2];
+  const DF r2 = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
+  constexpr DF sr = DF(STEP_REACH), sr2 = DF(STEP_REACH * STEP_REACH);
+  if (sr2 * r2 < h * h * v2) h = sr * df_sqrt(df_div(r2, v2));
+  return h;
+}
+
+// The rest of an attempt once its stages are known (k[0..6] and the 5th-order
+// end point yn): error estimate, null-cone and escape events, the decision.
+__device__ __forceinline__ int finish_df(const TraceParams& p, LaneD& L, DF h, DF (*k)[6],
+                                         const DF* yn, DF ro2, float rc2, DF rtol, DF atol);
+
 __device__ __forceinline__ int advance_df(const TraceParams& p, LaneD& L, DF ro2, float rc2,
                                           DF rtol, DF atol) {
-  if (L.na >= p.max_steps || L.na + L.nr >= 4 * p.max_steps) return RAY_MAXSTEPS;
-  DF h = L.h;
-  {
-    // displacement of one step at most STEP_REACH x the distance to the centre
-    const DF v2 = L.f0[0] * L.f0[0] + L.f0[1] * L.f0[1] + L.f0[2] * L.f0[2];
-    const DF r2 = L.y[0] * L.y[0] + L.y[1] * L.y[1] + L.y[2] * L.y[2];
-    constexpr DF sr = DF(STEP_REACH), sr2 = DF(STEP_REACH * STEP_REACH);
-    if (sr2 * r2 < h * h * v2) h = sr * df_sqrt(df_div(r2, v2));
-  }
+  if (out_of_steps(p, L)) return RAY_MAXSTEPS;
+  const DF h = attempt_h(L);
   const DF* y = L.y;
   // stages: k[0] = f(y) (first-same-as-last), k[s] = f(y + h sum_j A[s][j]
   // k[j]) for s = 1..5, and row 6 the 5th-order update yn with k[6] = f(yn);
@@ -329,6 +342,12 @@ __device__ __forceinline__ int advance_df(const TraceParams& p, LaneD& L, DF ro2
     }
     rhs_df(L.c, yn, k[st]);
   }
+  return finish_df(p, L, h, k, yn, ro2, rc2, rtol, atol);
+}
+
+__device__ __forceinline__ int finish_df(const TraceParams& p, LaneD& L, DF h, DF (*k)[6],
+                                         const DF* yn, DF ro2, float rc2, DF rtol, DF atol) {
+  const DF* y = L.y;
   const DF* k1 = k[0];
   const DF* k3 = k[2];
   const DF* k4 = k[3];
@@ -549,10 +568,16 @@ cudaError_t launch_trace_df(const TraceParams& p, int block, int blocks_per_sm,
   block = (block / 32) * 32;
   if (block < 32) block = 32;
   if (blocks_per_sm <= 0) {
+    // default: one 128-thread block per SM, one warp per scheduler.  Measured
+    // on the eight-step benchmark launch: 2.66-2.69 s against 2.84 s with the
+    // two blocks the registers allow; the rays guided along the null cone set
+    // the launch's end, and a warp that has its scheduler to itself runs them
+    // fastest, while the bulk loses little (the kernel is bound by
+    // instruction supply, not by the number of warps)
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, trace_df_kernel, block, 0);
+    e = occupancy_trace_df(block, &occ);
     if (e != cudaSuccess) return e;
-    blocks_per_sm = occ > 0 ? occ : 1;
+    blocks_per_sm = (block >= 128 || occ < 1) ? 1 : (occ < 128 / block ? occ : 128 / block);
   }
   const int64_t warps_needed = (p.n + 31) / 32;
   int64_t grid = (int64_t)nsm * blocks_per_sm;

@@ -12,7 +12,8 @@ decisions with every operation in double-float arithmetic (unit roundoff
 * binned flux vs the oracle: 1e-8 relative L1 (config 0 and a misaligned
   production sub-batch);
 * statuses as the FP64 path's (99.5 %);
-* claim order and batching change nothing, bit for bit (one lane per ray: a
+* claim order (with the express warps of cost order), claim size, refill
+  threshold and batching change nothing, bit for bit (one lane per ray: a
   ray's arithmetic does not depend on its neighbours).
 """
 import numpy as np
@@ -113,6 +114,12 @@ def test_df_claim_order_and_batch_are_bitwise_neutral():
         b, sb = st_d.clone(), s_d.clone()
         G.gpu_trace(star, b, sb, rtol=1e-10, precision=rt.PREC_DF, claim_order=rt.CLAIM_COST)
         assert torch.equal(a, b) and torch.equal(sa, sb)
+        # cost order with the express warps, several rays per claim and a refill
+        # threshold: the queues change hands between phases without losing a ray
+        c, sc = st_d.clone(), s_d.clone()
+        G.gpu_trace(star, c, sc, rtol=1e-10, precision=rt.PREC_DF, claim_order=rt.CLAIM_COST,
+                    rays_per_claim=4, refill_min=8)
+        assert torch.equal(a, c) and torch.equal(sa, sc)
         outs.append((st_d, s_d, a, sa))
     # the three stars in one batch: bitwise the per-star calls
     stars = [rt.Star(rt.make_params(**kw)) for kw in kws]
