@@ -80,7 +80,7 @@ def _measure_peaks(rt, stream):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the trace
 # kernel per traced ray, from one single-pass ncu capture of that kernel alone
 # (one launch, caches flushed by ncu before it) on 2^21 rays of the heaviest
-# benchmark star, cost-ordered claims:
+# benchmark star, cost-ordered claims, default launch shape and refill:
 #   python profile_case.py --config config1 --precision <p> --claim-order cost --n 2097152
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:<kernel> -s 1 -c 1 <the same command>
@@ -90,12 +90,12 @@ def _measure_peaks(rt, stream):
 TRAFFIC = {
     # precision -> (sources, digest, kernel, bytes per traced ray)
     "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_internal.h'),
-             "2b8c4e13855e2cb9", "trace_fp64_kernel", 334770944 / 2096328),
+             "2b8c4e13855e2cb9", "trace_fp64_kernel", 332385536 / 2096328),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_backward.cuh', 'rt_trace_mixed.cu',
                'rt_internal.h'),
-              "26743c2d92e573de", "trace_mixed_kernel", 259265792 / 2096328),
+              "26743c2d92e573de", "trace_mixed_kernel", 250965248 / 2096328),
     "df": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_df.cuh', 'rt_trace_df.cu', 'rt_internal.h'),
-           "fdd95867d784f634", "trace_df_kernel", 391314432 / 2096328),
+           "fdd95867d784f634", "trace_df_kernel", 393602816 / 2096328),
 }
 
 

@@ -176,7 +176,9 @@ typedef struct {
  *   refill_min        work claiming of the persistent kernels: a warp claims new
  *                     rays (pixels) from the global queue once at least this many of
  *                     its lanes are free (1-32; 0 = auto: the batch's autotuned
- *                     value, else 1 -- refill as soon as any lane is free)
+ *                     value, else 8 for RT_PREC_FP64 and 16 for RT_PREC_DF and
+ *                     RT_PREC_MIXED, measured on the benchmark's eight-step
+ *                     launch; 1 refills as soon as any lane is free)
  *   rays_per_claim    queue entries a lane claims at a time (1-64; 0 = auto, as
  *                     refill_min); a lane traces its claimed rays one after the
  *                     other before it claims again.  Neither changes any ray's
