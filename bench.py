@@ -984,24 +984,28 @@ def _adjoint_leg(args, dev):
     F, nacc, star, incl, opts = flux.flux_forward(p, kw, u, kappa)
     torch.cuda.synchronize()
     t_f = time.perf_counter() - t0
-    ctr = torch.zeros(8, dtype=torch.int64, device=dev)
-    t0 = time.perf_counter()
-    nbytes = rt.rt_flux_gradient(star, n, u, nacc, incl, kappa, grad, F2, counters=ctr,
-                                 opts=opts)
-    torch.cuda.synchronize()
-    t_g = time.perf_counter() - t0
-    g = grad.cpu().numpy()
-    c = ctr.cpu().numpy()
-    # the same gradient with the backward sweep in FP32 (FP64 replay)
-    o32 = rt.make_opts(rtol=opts.rtol, precision=rt.PREC_MIXED)
-    rt.rt_flux_gradient(sw, 4096, uw, nw, iw, kappa, grad, F2, opts=o32)    # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rt.rt_flux_gradient(star, n, u, nacc, incl, kappa, grad, F2, opts=o32)
-    torch.cuda.synchronize()
-    t_g32 = time.perf_counter() - t0
-    g32 = grad.cpu().numpy()
+    def run(prec, tape_max_bytes):
+        o = rt.make_opts(rtol=opts.rtol, precision=prec)
+        rt.rt_flux_gradient(sw, 4096, uw, nw, iw, kappa, grad, F2, opts=o,
+                            tape_max_bytes=tape_max_bytes)    # warm-up
+        ctr = torch.zeros(8, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb = rt.rt_flux_gradient(star, n, u, nacc, incl, kappa, grad, F2, counters=ctr, opts=o,
+                                 tape_max_bytes=tape_max_bytes)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, grad.cpu().numpy().copy(), nb, ctr.cpu().numpy()
+
+    # the backward sweep in FP64, double-float and FP32 over the full step tape
+    # (one FP64 replay), and in FP64 over the checkpointed recompute
+    t_g, g, nbytes, c = run(rt.PREC_FP64, -1)
+    t_df, gdf, _, _ = run(rt.PREC_DF, -1)
+    t_g32, g32, _, _ = run(rt.PREC_MIXED, -1)
+    t_ck, gck, nb_ck, _ = run(rt.PREC_FP64, 0)
     err32 = np.abs(g32 - g) / np.abs(g)
+    errdf = np.abs(gdf - g) / np.abs(g)
+    errck = np.abs(gck - g) / np.abs(g)
+    na = nacc.cpu().numpy()
     # the full-size gradient against central finite differences of the GPU
     # forward pipeline (relative step 1e-6, 1e-6 rad for the angles, rtol 1e-12
     # so that the controller's discrete decisions do not move F measurably)
@@ -1018,23 +1022,33 @@ def _adjoint_leg(args, dev):
         g_fd[k] = (Fp - Fm) / (2.0 * hs[k])
     t_fd = time.perf_counter() - t0
     err_fd = np.abs(g - g_fd) / np.abs(g_fd)
+    def named(v):
+        return dict(zip(flux.PARAM_NAMES, [float(x) for x in v]))
+
     return {"workload": "adjoint_2^18_rays_ma1e-5_incl1.1_vmf_one_theta_bin",
-            "precision": "fp64", "rays": n, "F_W_per_sr": float(F.cpu()[0]),
-            "grad": dict(zip(flux.PARAM_NAMES, [float(x) for x in g])),
+            "precision": "fp64 replay, fp64 backward sweep", "rays": n,
+            "F_W_per_sr": float(F.cpu()[0]), "grad": named(g),
             "t_forward_s": t_f, "t_gradient_s": t_g, "adjoint_forward_ratio": t_g / t_f,
-            "checkpoint_MiB": nbytes / 2 ** 20, "replayed_attempts": int(c[0]),
-            "rays_left_out": int(c[4]),
+            "store": "full step tape", "store_MiB": nbytes / 2 ** 20,
+            "forward_steps": {"mean": float(na.mean()), "max": int(na.max())},
+            "replayed_attempts": int(c[0]), "rays_left_out": int(c[4]),
+            "df_sweep": {"t_gradient_s": t_df, "adjoint_forward_ratio": t_df / t_f,
+                         "vs_fp64_sweep_error": named(errdf)},
             "fp32_sweep": {"t_gradient_s": t_g32, "adjoint_forward_ratio": t_g32 / t_f,
-                           "grad": dict(zip(flux.PARAM_NAMES, [float(x) for x in g32]))},
-            "fp32_vs_fp64_gradient_error": dict(zip(flux.PARAM_NAMES,
-                                                    [float(x) for x in err32])),
-            "vs_central_differences": {"relative_error": dict(zip(flux.PARAM_NAMES,
-                                                                  [float(x) for x in err_fd])),
-                                       "seconds": t_fd,
-                                       "note": "12 forward runs at rtol 1e-12, all 2^18 rays"},
-            "note": "forward trace and replays FP64; timings include sampling, both "
-                    "replays and the dual-number Jacobian products; fp32_sweep forms the "
-                    "backward sweep's stages, products and sums in FP32"}
+                           "grad": named(g32)},
+            "fp32_vs_fp64_gradient_error": named(err32),
+            "checkpoints_fp64_sweep": {"t_gradient_s": t_ck, "adjoint_forward_ratio": t_ck / t_f,
+                                       "store_MiB": nb_ck / 2 ** 20,
+                                       "vs_tape_relative_difference": named(errck),
+                                       "note": "a checkpoint every 32 accepted steps and a "
+                                               "replay per segment (the store used when the "
+                                               "tape does not fit)"},
+            "vs_central_differences": {"relative_error": named(err_fd), "seconds": t_fd,
+                                       "note": "12 forward runs at rtol 1e-12, all 2^18 rays; "
+                                               "against the FP64 sweep"},
+            "note": "forward trace and replay FP64; gradient timings include sampling with "
+                    "tangents, the replay onto the tape, the sweep's dual-number Jacobian "
+                    "products and the sums"}
 
 
 def _backward_leg(args, dev, stream, fl, rank):

@@ -145,8 +145,9 @@ typedef struct {
  *   lambda_max        stop at this worldline parameter (units: R / m_a^2 scaled
  *                     Hamiltonian); 0 = no limit
  *   r_capture_over_R  capture radius (1 = stellar surface)
- *   precision         RT_PREC_FP64, RT_PREC_MIXED or RT_PREC_DF (forward tracing
- *                     only: rt_trace_forward, rt_trace_batch without images)
+ *   precision         RT_PREC_FP64, RT_PREC_MIXED or RT_PREC_DF (RT_PREC_DF:
+ *                     rt_trace_forward, rt_trace_batch without images, and the
+ *                     backward sweep of rt_flux_gradient)
  *   max_steps         bound on accepted steps per ray
  *   block             threads per block of the persistent kernel (0 = auto, or
  *                     the batch's autotuned value, rt_batch_autotune)
@@ -433,33 +434,41 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *   R [km], inclination [rad]) by reverse-mode differentiation of sampling and
  *   the FP64 integrator, at the star's parameters, for the n samples drawn
  *   from d_uniforms (RT_UNIFORM_ROWS x n, as rt_sample_conversion_surface)
- *   and traced with opts (lambda_max 0).  opts.precision: RT_PREC_FP64
- *   sweeps backwards in FP64; RT_PREC_MIXED replays the trajectory in FP64
- *   (the same steps) but forms the stages, Jacobian products and adjoint
- *   accumulation of the backward sweep in FP32 (the FP32-vs-FP64 gradient
- *   error).  Each ray is
- *   re-integrated with a checkpoint every 32 accepted steps (d_nacc, the
- *   accepted steps per ray of the forward rt_trace_forward run with the same
- *   opts, sizes the checkpoint store), then swept backwards segment by
- *   segment, each segment re-integrated from its checkpoint: the discrete
- *   adjoint of each Dormand-Prince step (Jacobian-vector products of the
- *   analytic right-hand side by forward-mode dual numbers), the saltation
- *   jump where the Goldreich-Julian branch switches on the null cone, and the
- *   escape point's implicit dependence on the parameters.  The derivatives
- *   of the initial state and the weight come from the sampling code in dual
- *   numbers (the resonance root by the implicit function theorem).  Status,
- *   escape and the number of steps are held fixed (the gradient of the
- *   discrete scheme at frozen decisions).
+ *   and traced with opts (lambda_max 0).  Each ray is re-integrated in FP64
+ *   (the same steps as the forward rt_trace_forward run with the same opts,
+ *   whose accepted steps per ray d_nacc sizes the store) and swept
+ *   backwards: the discrete adjoint of each Dormand-Prince step
+ *   (Jacobian-vector products of the analytic right-hand side by forward-mode
+ *   dual numbers), the saltation jump where the Goldreich-Julian branch
+ *   switches on the null cone, and the escape point's implicit dependence on
+ *   the parameters.  The derivatives of the initial state and the weight come
+ *   from the sampling code in dual numbers (the resonance root by the
+ *   implicit function theorem).  Status, escape and the number of steps are
+ *   held fixed (the gradient of the discrete scheme at frozen decisions).
+ *   Store: the full step tape (every accepted step with its seven stages,
+ *   416 B, plus 424 B per ray) when it fits under tape_max_bytes: one replay
+ *   records the rays, longest first, and a second kernel sweeps them
+ *   backwards; else a checkpoint every 32 accepted steps (sum over rays of
+ *   (nacc/32 + 2) x 104 B) and segment scratch (13 KB per resident thread:
+ *   about 500 MB on GB300), each segment re-integrated from its checkpoint
+ *   before its sweep (one replay more).
+ *   opts.precision sets the arithmetic of the backward sweep (stages, Jacobian
+ *   products, adjoint accumulation), the replay being FP64 always:
+ *   RT_PREC_FP64 FP64; RT_PREC_DF double-float (FP64-class rounding on the
+ *   FP32 pipe); RT_PREC_MIXED FP32 (its error against the FP64 sweep is the
+ *   FP32-vs-FP64 gradient error).
  *     d_grad     out: 6 float64, dF/dp
  *     d_F        out: 1 float64, F recomputed by the adjoint's replay
  *     d_status   out (may be NULL): n final statuses of the replay
- *     d_counters in/out (may be NULL): [0] replayed step attempts, [2] rays,
- *                [4] rays left out (replay longer than d_nacc allows)
- *     ckpt_bytes out (host, may be NULL): bytes of checkpoint storage used
+ *     d_counters in/out (may be NULL): [0] replayed step attempts (first
+ *                replay), [2] rays, [4] rays left out (replay longer than
+ *                d_nacc allows)
+ *     tape_max_bytes  most device bytes the full tape may take (-1: half of
+ *                the free device memory; 0: checkpoints always)
+ *     store_bytes out (host, may be NULL): bytes of the tape or checkpoint store
  *   Needs RT_PLASMA_GJ, M_sun > 0 and B0_G > 0.  Synchronous: allocates the
- *   checkpoint store (sum over rays of (nacc/32 + 2) x 104 B), segment
- *   scratch (13 KB per resident thread: about 500 MB on GB300) and 69 B per
- *   ray, and frees them before returning; RT_ENOMEM if that fails.
+ *   store and 69 B per ray, and frees them before returning; RT_ENOMEM if
+ *   that fails.  Deterministic (fixed-order sums of per-ray terms).
  */
 rt_status rt_flux_value(const rt_star* star, int64_t n, const double* d_state,
                         const double* d_weight, const uint8_t* d_status, double incl_rad,
@@ -467,8 +476,8 @@ rt_status rt_flux_value(const rt_star* star, int64_t n, const double* d_state,
 rt_status rt_flux_gradient(const rt_star* star, int64_t n, const double* d_uniforms,
                            const int32_t* d_nacc, double incl_rad, double kappa,
                            const rt_trace_opts* opts, double* d_grad, double* d_F,
-                           uint8_t* d_status, int64_t* d_counters, int64_t* ckpt_bytes,
-                           void* stream);
+                           uint8_t* d_status, int64_t* d_counters, int64_t tape_max_bytes,
+                           int64_t* store_bytes, void* stream);
 
 /*
  * Batches: many stars (different B0, P, misalignment, m_a, ...) traced in ONE

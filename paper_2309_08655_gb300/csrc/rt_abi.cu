@@ -569,16 +569,14 @@ rt_status rt_flux_value(const rt_star* s, int64_t n, const double* d_state,
 rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms,
                            const int32_t* d_nacc, double incl_rad, double kappa,
                            const rt_trace_opts* o, double* d_grad, double* d_F,
-                           uint8_t* d_status, int64_t* d_counters, int64_t* ckpt_bytes,
-                           void* stream) {
+                           uint8_t* d_status, int64_t* d_counters, int64_t tape_max_bytes,
+                           int64_t* store_bytes, void* stream) {
   rtk::NvtxRange nvtx_range("rt_flux_gradient");
   if (!s) return fail(RT_EINVAL, "star is NULL");
   if (n < 1) return fail(RT_EINVAL, "n must be >= 1");
   rt_status st;
   if ((st = check_opts(o)) != RT_OK) return st;
   if (o->lambda_max != 0.0) return fail(RT_EUNSUPPORTED, "lambda_max must be 0");
-  if (o->precision == RT_PREC_DF)
-    return fail(RT_EUNSUPPORTED, "the gradient is computed in RT_PREC_FP64 or RT_PREC_MIXED");
   if (!is_finite_val(incl_rad) || !(kappa > 0) || !is_finite_val(kappa))
     return fail(RT_EINVAL, "need finite incl_rad and 0 < kappa < inf");
   if ((st = check_dev_ptr(d_uniforms, "d_uniforms")) != RT_OK) return st;
@@ -660,11 +658,22 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
   a.queue = s->d_queue;
   cudaStream_t cs = (cudaStream_t)stream;
   a.prec = o->precision;
-  cudaError_t e = rtk::adjoint_grid(a.prec, &a.grid, &a.block);
-  if (e != cudaSuccess) return cuda_fail(e, "adjoint occupancy");
-  // scratch: checkpoint offsets, checkpoints, segment records, per-ray results
+  a.ck_off = nullptr;
+  a.ck = a.seg = nullptr;
+  a.tape_off = nullptr;
+  a.tape = a.head = nullptr;
+  a.order = nullptr;
+  a.bucket = nullptr;
+  a.grid = a.block = 0;
+  cudaError_t e = cudaSuccess;
+  // scratch: tape or checkpoint offsets, per-ray results; then the full step
+  // tape (with the per-ray heads and the longest-first order) when it fits
+  // under tape_max_bytes, else the checkpoints and the segment records
   int64_t* off = nullptr;
-  double *ck = nullptr, *seg = nullptr, *Fr = nullptr, *Gr = nullptr;
+  double *ck = nullptr, *seg = nullptr, *Fr = nullptr, *Gr = nullptr, *tape = nullptr,
+         *head = nullptr;
+  int64_t* order = nullptr;
+  unsigned long long* bucket = nullptr;
   uint8_t* stt = nullptr;
   int32_t* flg = nullptr;
   auto cleanup = [&]() {
@@ -673,43 +682,87 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
     cudaFree(seg);
     cudaFree(Fr);
     cudaFree(Gr);
+    cudaFree(tape);
+    cudaFree(head);
+    cudaFree(order);
+    cudaFree(bucket);
     if (!d_status) cudaFree(stt);
     cudaFree(flg);
   };
-  int64_t total = 0;
-  const size_t seg_n = (size_t)a.grid * a.block * rtk::CK * rtk::SEGREC;
+  auto alloc_fail = [&](cudaError_t err, const char* what) {
+    cleanup();
+    return (err == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, what)
+                                              : cuda_fail(err, "cudaMalloc");
+  };
   if ((e = cudaMalloc(&off, (n + 1) * sizeof(int64_t))) != cudaSuccess ||
-      (e = cudaMalloc(&seg, seg_n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&Fr, n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&Gr, (size_t)rtk::NPARAMS * n * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&flg, n * sizeof(int32_t))) != cudaSuccess ||
-      (!d_status && (e = cudaMalloc(&stt, n)) != cudaSuccess)) {
-    cleanup();
-    return (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "adjoint scratch allocation failed")
-                                            : cuda_fail(e, "cudaMalloc");
-  }
+      (!d_status && (e = cudaMalloc(&stt, n)) != cudaSuccess))
+    return alloc_fail(e, "adjoint scratch allocation failed");
   if (d_status) stt = d_status;
-  if ((e = rtk::launch_ck_offsets(d_nacc, n, off, cs)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, cs)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(cs)) != cudaSuccess) {
-    cleanup();
-    return cuda_fail(e, "checkpoint offsets");
-  }
-  if ((e = cudaMalloc(&ck, (size_t)total * rtk::CKREC * sizeof(double))) != cudaSuccess) {
-    cleanup();
-    return (e == cudaErrorMemoryAllocation) ? fail(RT_ENOMEM, "checkpoint allocation failed")
-                                            : cuda_fail(e, "cudaMalloc");
-  }
-  if (ckpt_bytes) *ckpt_bytes = total * rtk::CKREC * (int64_t)sizeof(double);
-  a.ck_off = off;
-  a.ck = ck;
-  a.seg = seg;
   a.F_ray = Fr;
   a.G_ray = Gr;
   a.status = stt;
   a.flags = flg;
-  e = rtk::launch_adjoint(a, cs);
+  a.nacc = d_nacc;
+  // the tape's size from the forward step counts
+  int64_t total = 0;
+  if ((e = rtk::launch_tape_offsets(d_nacc, n, off, cs)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, cs)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(cs)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "tape offsets");
+  }
+  const int64_t tape_bytes = total * rtk::SEGREC * (int64_t)sizeof(double) +
+                             n * (rtk::HEADREC * (int64_t)sizeof(double) + 8);
+  int64_t limit = tape_max_bytes;
+  if (limit < 0) {
+    size_t fr = 0, tot = 0;
+    if ((e = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "cudaMemGetInfo");
+    }
+    limit = (int64_t)(fr / 2);
+  }
+  if (tape_bytes <= limit) {
+    if ((e = cudaMalloc(&tape, (size_t)total * rtk::SEGREC * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&head, (size_t)n * rtk::HEADREC * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&order, (size_t)n * sizeof(int64_t))) != cudaSuccess ||
+        (e = cudaMalloc(&bucket, 32 * sizeof(unsigned long long))) != cudaSuccess)
+      return alloc_fail(e, "step tape allocation failed");
+    if (store_bytes) *store_bytes = tape_bytes;
+    a.tape_off = off;
+    a.tape = tape;
+    a.head = head;
+    a.order = order;
+    a.bucket = bucket;
+    e = rtk::launch_adjoint_tape(a, cs);
+  } else {
+    e = rtk::adjoint_grid(a.prec, &a.grid, &a.block);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "adjoint occupancy");
+    }
+    const size_t seg_n = (size_t)a.grid * a.block * rtk::CK * rtk::SEGREC;
+    if ((e = cudaMalloc(&seg, seg_n * sizeof(double))) != cudaSuccess)
+      return alloc_fail(e, "adjoint segment scratch allocation failed");
+    if ((e = rtk::launch_ck_offsets(d_nacc, n, off, cs)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, cs)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(cs)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "checkpoint offsets");
+    }
+    if ((e = cudaMalloc(&ck, (size_t)total * rtk::CKREC * sizeof(double))) != cudaSuccess)
+      return alloc_fail(e, "checkpoint allocation failed");
+    if (store_bytes) *store_bytes = total * rtk::CKREC * (int64_t)sizeof(double);
+    a.ck_off = off;
+    a.ck = ck;
+    a.seg = seg;
+    e = rtk::launch_adjoint(a, cs);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");

@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "rt_df.cuh"
 #include "rt_dual.cuh"
 #include "rt_integrator.cuh"
 #include "rt_internal.h"
@@ -54,6 +55,18 @@ __device__ __forceinline__ Dual<N> root_of(double r, const Dual<N>& G, double dG
   for (int k = 0; k < N; ++k) o.d[k] = -G.d[k] / dGdr;
   return o;
 }
+
+// 1/sqrt of a double-float dual: the value by the series-corrected
+// double-float rsqrt, the derivative -q^3 / 2.
+template <int N>
+__device__ __forceinline__ Dual<N, DF> rt_rsqrt(const Dual<N, DF>& a) {
+  const DF q = rt_rsqrt(a.v);
+  return chain(a, q, DF(-0.5) * (q * q) * q);
+}
+
+__device__ __forceinline__ double dval(double x) { return x; }
+__device__ __forceinline__ double dval(float x) { return (double)x; }
+__device__ __forceinline__ double dval(DF x) { return df_d(x); }
 
 namespace {
 
@@ -88,6 +101,10 @@ struct AdjParams {
   int32_t* flags;
   int64_t* counters;
   unsigned long long* queue;
+  const int64_t* tape_off;
+  double* tape;
+  double* head;
+  const int64_t* order;
 };
 
 // Right-hand side in the sweep's precision T.
@@ -197,8 +214,9 @@ __device__ void saltation(RayConst<T> c, const T* dm, const T* y, T sig_old, T* 
 }
 
 // Discrete adjoint of one accepted Dormand-Prince step from y with step h, in
-// the scalar type T (double: the FP64 sweep; float: the single-precision sweep,
-// which re-forms the step's stages in float from the FP64 record).
+// the scalar type T (double: the FP64 sweep; float: the single-precision
+// sweep; DF: the double-float sweep), from the step's FP64 record (its seven
+// stage derivatives K, as the replay formed them).
 // ybar: in, the adjoint at the step's end (unused when escape); out, at y.
 // Escape: the step ends at the theta* of the continuous extension where
 // |x| = r_out, and ybar_e is the adjoint there.
@@ -206,44 +224,25 @@ template <class T>
 __device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
                              const double* Krec, bool escape, T r_out, const T* ybar_e, T* ybar,
                              T* qbar) {
-  const T a21 = T(DP::a21), a31 = T(DP::a31), a32 = T(DP::a32), a41 = T(DP::a41),
-          a42 = T(DP::a42), a43 = T(DP::a43), a51 = T(DP::a51), a52 = T(DP::a52),
-          a53 = T(DP::a53), a54 = T(DP::a54), a61 = T(DP::a61), a62 = T(DP::a62),
-          a63 = T(DP::a63), a64 = T(DP::a64), a65 = T(DP::a65);
   const T b1 = T(DP::b1), b3 = T(DP::b3), b4 = T(DP::b4), b5 = T(DP::b5), b6 = T(DP::b6);
-  const T d1 = T(DP::d1), d3 = T(DP::d3), d4 = T(DP::d4), d5 = T(DP::d5), d6 = T(DP::d6),
-          d7 = T(DP::d7);
-  // the stages as the replay formed them (FP64 record, in the sweep's
-  // precision), and the stage inputs Y_s = y + h sum_j a_sj K_j
-  T K[7][6], Y[6][6], t[6];
+  T K[7][6], t[6];
 #pragma unroll
   for (int s = 0; s < 7; ++s)
 #pragma unroll
     for (int i = 0; i < 6; ++i) K[s][i] = T(Krec[6 * s + i]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    Y[0][i] = y[i];
-    Y[1][i] = y[i] + h * (a21 * K[0][i]);
-    Y[2][i] = y[i] + h * (a31 * K[0][i] + a32 * K[1][i]);
-    Y[3][i] = y[i] + h * (a41 * K[0][i] + a42 * K[1][i] + a43 * K[2][i]);
-    Y[4][i] = y[i] + h * (a51 * K[0][i] + a52 * K[1][i] + a53 * K[2][i] + a54 * K[3][i]);
-    Y[5][i] = y[i] + h * (a61 * K[0][i] + a62 * K[1][i] + a63 * K[2][i] + a64 * K[3][i] +
-                          a65 * K[4][i]);
-  }
-  T yn[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    yn[i] = y[i] + h * (b1 * K[0][i] + b3 * K[2][i] + b4 * K[3][i] + b5 * K[4][i] +
-                        b6 * K[5][i]);
   T kb[7][6], ynb[6], yb[6];
 #pragma unroll
   for (int s = 0; s < 7; ++s)
 #pragma unroll
     for (int i = 0; i < 6; ++i) kb[s][i] = T(0);
   if (escape) {
-    T r2v[6], r3[6], r4[6], r5[6];
+    const T d1 = T(DP::d1), d3 = T(DP::d3), d4 = T(DP::d4), d5 = T(DP::d5), d6 = T(DP::d6),
+            d7 = T(DP::d7);
+    T yn[6], r2v[6], r3[6], r4[6], r5[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
+      yn[i] = y[i] + h * (b1 * K[0][i] + b3 * K[2][i] + b4 * K[3][i] + b5 * K[4][i] +
+                          b6 * K[5][i]);
       r2v[i] = yn[i] - y[i];
       r3[i] = h * K[0][i] - r2v[i];
       r4[i] = r2v[i] - h * K[6][i] - r3[i];
@@ -324,19 +323,29 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
     kb[4][i] += h * b5 * ynb[i];
     kb[5][i] += h * b6 * ynb[i];
   }
-  // stages, last to first: k_s = f(Y_s), Y_s = y + h sum_j a_sj k_j
+  // stages, last to first: k_s = f(Y_s), Y_s = y + h sum_j a_sj k_j (Y_s formed
+  // when its stage is reached, from the K held in registers)
   const T A[6][5] = {{T(0), T(0), T(0), T(0), T(0)},
-                     {a21, T(0), T(0), T(0), T(0)},
-                     {a31, a32, T(0), T(0), T(0)},
-                     {a41, a42, a43, T(0), T(0)},
-                     {a51, a52, a53, a54, T(0)},
-                     {a61, a62, a63, a64, a65}};
+                     {T(DP::a21), T(0), T(0), T(0), T(0)},
+                     {T(DP::a31), T(DP::a32), T(0), T(0), T(0)},
+                     {T(DP::a41), T(DP::a42), T(DP::a43), T(0), T(0)},
+                     {T(DP::a51), T(DP::a52), T(DP::a53), T(DP::a54), T(0)},
+                     {T(DP::a61), T(DP::a62), T(DP::a63), T(DP::a64), T(DP::a65)}};
+#pragma unroll
   for (int s = 5; s >= 0; --s) {
-    T Yb[6];
-    rhs_vjp(c, dm, Y[s], kb[s], Yb, qbar);
+    T Ys[6], Yb[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < s; ++j) acc += A[s][j] * K[j][i];
+      Ys[i] = (s == 0) ? y[i] : y[i] + h * acc;
+    }
+    rhs_vjp(c, dm, Ys, kb[s], Yb, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       yb[i] += Yb[i];
+#pragma unroll
       for (int j = 0; j < s; ++j) kb[j][i] += h * A[s][j] * Yb[i];
     }
   }
@@ -455,30 +464,39 @@ struct RecHook {
   }
 };
 
-// T: precision of the reverse sweep (the forward replay is FP64 either way).
-template <class T>
-__device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long long* steps) {
+// The trace parameters of the replays (those of the forward run).
+__device__ __forceinline__ TraceParams replay_params(const AdjParams& P) {
+  TraceParams tp;
+  tp.rtol = P.rtol;
+  tp.atol = P.atol;
+  tp.r_out = P.r_out;
+  tp.lambda_max = 0.0;
+  tp.r_capture = P.r_capture;
+  tp.max_steps = P.max_steps;
+  tp.ts = nullptr;
+  tp.park = nullptr;
+  return tp;
+}
+
+// Samples ray i with its parameter tangents (so) and its plain values (sv,
+// exactly as the sampling kernel computes them) and sets up the lane exactly
+// as the forward trace loads it from the state.  false: no conversion point;
+// the ray's outputs are zeroed.
+__device__ bool begin_ray(const AdjParams& P, int64_t i, SampOut<Dual<NSAMP_TANGENTS>>& so,
+                          SampOut<double>& sv, Lane& L, double& cps, double& sps) {
   const int64_t n = P.n;
   double u[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) u[j] = P.u[j * n + i];
-  SampOut<Dual<NSAMP_TANGENTS>> so;
   sample_core(P.sc, u, (double)n, so);
-  // values exactly as the sampling kernel computes them
-  SampOut<double> sv;
   sample_core(P.scv, u, (double)n, sv);
-  double G[NPARAMS];
-#pragma unroll
-  for (int k = 0; k < NPARAMS; ++k) G[k] = 0.0;
   P.flags[i] = 0;
   if (!sv.ok || !so.ok) {
     P.F_ray[i] = 0.0;
     for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = 0.0;
     P.status[i] = RAY_NO_ROOT;
-    return;
+    return false;
   }
-  // the initial lane exactly as the forward trace loads it from the state
-  Lane L;
   const double iR = 1.0 / P.R_km, im = 1.0 / P.ma_eV;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -486,7 +504,6 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
     L.y[3 + j] = (sv.k[j] * P.ma_eV) * im;
   }
   const double om = 1.0 + sv.delta;
-  double sps, cps;
   sincos(sv.psi, &sps, &cps);
   L.R_km = P.R_km;
   L.ma_eV = P.ma_eV;
@@ -509,15 +526,23 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
   L.na = 0;
   L.nr = 0;
   L.last_rej = false;
-  TraceParams tp;
-  tp.rtol = P.rtol;
-  tp.atol = P.atol;
-  tp.r_out = P.r_out;
-  tp.lambda_max = 0.0;
-  tp.r_capture = P.r_capture;
-  tp.max_steps = P.max_steps;
-  tp.ts = nullptr;
-  tp.park = nullptr;
+  return true;
+}
+
+// T: precision of the reverse sweep (the forward replay is FP64 either way).
+// Checkpointed recompute: one replay storing a checkpoint every CK accepted
+// steps, then segment by segment (last first) a replay of the segment that
+// records its steps and the reverse sweep over them.
+template <class T>
+__device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long long* steps) {
+  const int64_t n = P.n;
+  SampOut<Dual<NSAMP_TANGENTS>> so;
+  SampOut<double> sv;
+  Lane L;
+  double sps, cps;
+  if (!begin_ray(P, i, so, sv, L, cps, sps)) return;
+  double G[NPARAMS];
+  TraceParams tp = replay_params(P);
   // forward replay with a checkpoint every CK accepted steps
   const int64_t c0 = P.ck_off[i];
   const int64_t cmax = P.ck_off[i + 1] - c0;
@@ -621,9 +646,9 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
     }
   }
 #pragma unroll
-  for (int j = 0; j < 6; ++j) ybar[j] = (double)yb[j];
+  for (int j = 0; j < 6; ++j) ybar[j] = dval(yb[j]);
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) qbar[k] = (double)qb[k];
+  for (int k = 0; k < NQ; ++k) qbar[k] = dval(qb[k]);
   // assemble dF/dp for this ray
 #pragma unroll
   for (int k = 0; k < NSAMP_TANGENTS; ++k) {
@@ -656,6 +681,304 @@ __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
   if (P.counters) {
     atomicAdd((unsigned long long*)&P.counters[CTR_ACC], (unsigned long long)steps);
     atomicAdd((unsigned long long*)&P.counters[CTR_RAYS], (unsigned long long)rays);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full step tape: every accepted step of every ray is held in device memory at
+// once (SEGREC doubles a step), so that each ray is replayed once.  Two
+// persistent kernels, each lane taking the next ray (longest first) as soon as
+// it is free: the tape kernel replays the rays in FP64, step by step, and
+// records them; the sweep kernel walks each ray's records backwards, one step
+// per iteration, so that the lanes of a warp run the same step adjoint.
+
+constexpr int TAPE_BLOCK = 128;
+constexpr int SWEEP_BLOCK = 128;
+
+struct TapeStart {
+  Lane L;
+  double w;
+  bool ok;
+};
+
+// Samples ray i with its tangents, writes its head record (tangents, dm, the
+// ray's constants) and returns the lane ready for the replay (not inlined: it
+// runs once per ray, and its dual-number sampling is long).
+__device__ __noinline__ TapeStart tape_begin(const AdjParams& P, int64_t i) {
+  TapeStart t;
+  SampOut<Dual<NSAMP_TANGENTS>> so;
+  SampOut<double> sv;
+  double cps, sps;
+  double* hd = P.head + i * HEADREC;
+  t.ok = begin_ray(P, i, so, sv, t.L, cps, sps);
+  t.w = sv.w;
+  if (!t.ok) {
+    hd[HD_NREC] = -1.0;
+    return t;
+  }
+#pragma unroll
+  for (int k = 0; k < NSAMP_TANGENTS; ++k) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      hd[HD_TAN + 7 * k + j] = so.x[j].d[k];
+      hd[HD_TAN + 7 * k + 3 + j] = so.k[j].d[k];
+    }
+    hd[HD_TAN + 7 * k + 6] = so.w.d[k];
+  }
+  hd[HD_DM + 0] = P.cos_tm * cps;
+  hd[HD_DM + 1] = P.cos_tm * sps;
+  hd[HD_DM + 2] = -P.sin_tm;
+  hd[HD_W2] = t.L.c.W2;
+  hd[HD_IW2] = t.L.c.iW2;
+  hd[HD_M + 0] = t.L.c.m0;
+  hd[HD_M + 1] = t.L.c.m1;
+  hd[HD_M + 2] = t.L.c.m2;
+  return t;
+}
+
+// The end of ray i's replay: status, the escape flag and the final state on
+// the tape, the functional and its seed adjoint in the head record.
+__device__ __noinline__ void tape_finish(const AdjParams& P, int64_t i, const Lane& L,
+                                         const RecHook& rh, double w, int st) {
+  const int64_t n = P.n;
+  double* hd = P.head + i * HEADREC;
+  P.status[i] = (uint8_t)st;
+  const bool left_out = rh.nrec > rh.cap;
+  if (left_out || st != RAY_ESCAPED) {
+    if (left_out) {
+      P.flags[i] = 1;   // more steps than the forward pass: no gradient
+      if (P.counters) atomicAdd((unsigned long long*)&P.counters[CTR_PROMOTED], 1ull);
+    }
+    hd[HD_NREC] = -1.0;
+    P.F_ray[i] = 0.0;
+    for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = 0.0;
+    return;
+  }
+  if (rh.nrec >= 1) rh.seg[(int64_t)(rh.nrec - 1) * SEGREC + 8] += (double)FL_ESCAPE;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) rh.seg[(int64_t)rh.nrec * SEGREC + j] = L.y[j];
+  double ybar[6], rsb, dmu_di, Kv;
+  const double Fi = flux_kernel_value(P, L.y, w, ybar, &rsb, &dmu_di, &Kv);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) hd[HD_YBAR + j] = ybar[j];
+  hd[HD_RSBAR] = rsb;
+  hd[HD_K] = Kv;
+  hd[HD_NREC] = (double)rh.nrec;
+  P.F_ray[i] = Fi;
+  P.G_ray[PAR_INCL * n + i] = w * Kv * P.kappa * dmu_di;
+}
+
+__global__ void __launch_bounds__(TAPE_BLOCK) adjoint_tape_kernel(AdjParams P) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const TraceParams tp = replay_params(P);
+  Lane L;
+  RecHook rh;
+  rh.seg = nullptr;
+  rh.nrec = rh.cap = 0;
+  rh.pend_flip = false;
+  double w = 0.0;
+  int64_t item = -1;
+  ClaimChunk ch;
+  long long steps = 0, rays = 0;
+  for (;;) {
+    claim_items(P.queue, P.n, 1, 1, item, ch, [&](int64_t e) -> int64_t {
+      const int64_t i = P.order[e];
+      ++rays;
+      const TapeStart t = tape_begin(P, i);
+      if (!t.ok) return -1;
+      L = t.L;
+      w = t.w;
+      rh.seg = P.tape + P.tape_off[i] * SEGREC;
+      rh.cap = (int)(P.tape_off[i + 1] - P.tape_off[i] - 1);
+      rh.nrec = 0;
+      rh.pend_flip = false;
+      return i;
+    });
+    if (__ballot_sync(FULL, item != -2) == 0) break;
+    if (item >= 0) {
+      const int na0 = L.na;
+      const double sig0 = L.c.sig;
+      const int st = advance(tp, L, rh);
+      if (L.na == na0) {
+        if (L.c.sig != sig0) rh.pend_flip = true;   // switched at the current point
+      } else if (st < 0 && L.c.sig != sig0 && rh.nrec <= rh.cap) {
+        rh.seg[(int64_t)(rh.nrec - 1) * SEGREC + 8] += (double)FL_FLIP_AFTER;
+      }
+      if (st >= 0) {
+        tape_finish(P, item, L, rh, w, st);
+        steps += L.na + L.nr;
+        item = -1;
+      }
+    }
+  }
+  if (P.counters) {
+    atomicAdd((unsigned long long*)&P.counters[CTR_ACC], (unsigned long long)steps);
+    atomicAdd((unsigned long long*)&P.counters[CTR_RAYS], (unsigned long long)rays);
+  }
+}
+
+// dF/dp of ray i from the adjoint at its initial state and the q-adjoints.
+template <class T>
+__device__ __noinline__ void sweep_finish(const AdjParams& P, int64_t i, const T* yb,
+                                          const T* qb) {
+  const int64_t n = P.n;
+  const double* hd = P.head + i * HEADREC;
+  double ybar[6], qbar[NQ], G[NSAMP_TANGENTS];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) ybar[j] = dval(yb[j]);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) qbar[k] = dval(qb[k]);
+  const double Kv = hd[HD_K];
+#pragma unroll
+  for (int k = 0; k < NSAMP_TANGENTS; ++k) {
+    const double* tk = hd + HD_TAN + 7 * k;
+    double g = Kv * tk[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) g += ybar[j] * tk[j] + ybar[3 + j] * tk[3 + j];
+    G[k] = g;
+  }
+  G[PAR_MA] += qbar[Q_CP] * P.dcp_dma;
+  G[PAR_B0] += qbar[Q_CP] * P.dcp_dB0;
+  G[PAR_THM] += qbar[Q_THM];
+  G[PAR_M] += qbar[Q_RS] * P.drsp_dM;
+  G[PAR_R] += qbar[Q_RS] * P.drsp_dR;
+#pragma unroll
+  for (int k = 0; k < NSAMP_TANGENTS; ++k) P.G_ray[k * n + i] = G[k];
+}
+
+template <class T>
+__global__ void __launch_bounds__(SWEEP_BLOCK) adjoint_sweep_kernel(AdjParams P) {
+  constexpr unsigned FULL = 0xffffffffu;
+  int64_t item = -1;
+  ClaimChunk ch;
+  int j = -1;
+  const double* base = nullptr;
+  T yb[6], ye[6], qb[NQ], dm[3];
+  RayConst<T> c;
+  c.rs = T(P.rs_prop);
+  c.cp = T(P.cp);
+  c.pa = T(P.plasma_a);
+  c.disp = P.dispersion;
+  c.plasma = P.plasma;
+  for (;;) {
+    claim_items(P.queue, P.n, 1, 1, item, ch, [&](int64_t e) -> int64_t {
+      const int64_t i = P.order[e];
+      const double* hd = P.head + i * HEADREC;
+      const int nrec = (int)hd[HD_NREC];
+      if (nrec < 0) return -1;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        yb[q] = T(hd[HD_YBAR + q]);
+        ye[q] = yb[q];
+      }
+      qb[Q_RS] = T(hd[HD_RSBAR]);
+      qb[Q_CP] = T(0);
+      qb[Q_THM] = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dm[q] = T(hd[HD_DM + q]);
+      c.W2 = T(hd[HD_W2]);
+      c.iW2 = T(hd[HD_IW2]);
+      c.m0 = T(hd[HD_M + 0]);
+      c.m1 = T(hd[HD_M + 1]);
+      c.m2 = T(hd[HD_M + 2]);
+      base = P.tape + P.tape_off[i] * SEGREC;
+      j = nrec - 1;
+      return i;
+    });
+    if (__ballot_sync(FULL, item != -2) == 0) break;
+    if (item >= 0) {
+      if (j >= 0) {
+        const double* r = base + (int64_t)j * SEGREC;
+        const int fl = (int)r[8];
+        RayConst<T> cj = c;
+        cj.sig = T(r[7]);
+        T y[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) y[q] = T(r[q]);
+        if (fl & FL_FLIP_AFTER) {
+          // the branch switched at the end of this step: undo at y_{n+1}, the
+          // next record's start (or the ray's final state)
+          T yn[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) yn[q] = T(r[SEGREC + q]);
+          saltation(cj, dm, yn, T(r[7]), yb, qb);
+        }
+        step_adjoint(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb,
+                     qb);
+        if (fl & FL_FLIP_BEFORE) saltation(cj, dm, y, T(-r[7]), yb, qb);
+        --j;
+      }
+      if (j < 0) {
+        sweep_finish(P, item, yb, qb);
+        item = -1;
+      }
+    }
+  }
+}
+
+// Longest-first order of the rays by their forward step counts: 32 buckets
+// of floor(log2(nacc + 1)), counted, scanned and scattered (the order within
+// a bucket is that of the atomics; no result depends on it).
+__device__ __forceinline__ int len_bucket(int32_t na) {
+  return __clz((unsigned)(na > 0 ? na : 0) + 1u);
+}
+
+__global__ void order_count_kernel(const int32_t* nacc, int64_t n, unsigned long long* bucket) {
+  __shared__ unsigned int cnt[32];
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[len_bucket(nacc[i])], 1u);
+  __syncthreads();
+  if (threadIdx.x < 32 && cnt[threadIdx.x])
+    atomicAdd(&bucket[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+}
+
+__global__ void order_scan_kernel(unsigned long long* bucket) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long acc = 0;
+  for (int b = 0; b < 32; ++b) {
+    const unsigned long long v = bucket[b];
+    bucket[b] = acc;
+    acc += v;
+  }
+}
+
+__global__ void order_scatter_kernel(const int32_t* nacc, int64_t n, unsigned long long* bucket,
+                                     int64_t* order) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long pos = atomicAdd(&bucket[len_bucket(nacc[i])], 1ull);
+    order[pos] = i;
+  }
+}
+
+// Tape offsets: an exclusive prefix sum of tape_slots(nacc) (one block; fixed
+// order).
+__global__ void tape_offsets_kernel(const int32_t* nacc, int64_t n, int64_t* off) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int64_t chunk = (n + T - 1) / T;
+  const int64_t b = (int64_t)t * chunk, e = (b + chunk < n) ? b + chunk : n;
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += tape_slots(nacc[i]);
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t acc = 0;
+    for (int q = 0; q < T; ++q) {
+      const int64_t v = part[q];
+      part[q] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  int64_t acc = part[t];
+  for (int64_t i = b; i < e; ++i) {
+    off[i] = acc;
+    acc += tape_slots(nacc[i]);
   }
 }
 
@@ -763,13 +1086,15 @@ cudaError_t adjoint_grid(int prec, int* grid, int* block) {
   *block = 64;
   e = (prec == PREC_MIXED)
           ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<float>, *block, 0)
+      : (prec == PREC_DF)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<DF>, *block, 0)
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<double>, *block, 0);
   if (e != cudaSuccess) return e;
   *grid = nsm * (occ > 0 ? occ : 1);
   return cudaSuccess;
 }
 
-cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
+static AdjParams adj_params(const AdjLaunch& a) {
   AdjParams P;
   P.sc = a.sc;
   {
@@ -828,19 +1153,100 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
   P.flags = a.flags;
   P.counters = a.counters;
   P.queue = a.queue;
+  P.tape_off = a.tape_off;
+  P.tape = a.tape;
+  P.head = a.head;
+  P.order = a.order;
+  return P;
+}
+
+// dF/dp and F: deterministic sums of the per-ray terms.
+static cudaError_t launch_sums(const AdjLaunch& a, cudaStream_t stream) {
+  row_sums_kernel<<<NPARAMS, 256, 0, stream>>>(a.G_ray, a.n, a.grad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_sums_kernel<<<1, 256, 0, stream>>>(a.F_ray, a.n, a.F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
+  const AdjParams P = adj_params(a);
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   if (a.prec == PREC_MIXED)
     adjoint_kernel<float><<<a.grid, a.block, 0, stream>>>(P);
+  else if (a.prec == PREC_DF)
+    adjoint_kernel<DF><<<a.grid, a.block, 0, stream>>>(P);
   else
     adjoint_kernel<double><<<a.grid, a.block, 0, stream>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  row_sums_kernel<<<NPARAMS, 256, 0, stream>>>(a.G_ray, a.n, a.grad);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  row_sums_kernel<<<1, 256, 0, stream>>>(a.F_ray, a.n, a.F);
+  return launch_sums(a, stream);
+}
+
+cudaError_t launch_tape_offsets(const int32_t* nacc, int64_t n, int64_t* off,
+                                cudaStream_t stream) {
+  tape_offsets_kernel<<<1, 1024, 0, stream>>>(nacc, n, off);
   return cudaGetLastError();
+}
+
+// One resident grid of a persistent kernel: every SM times its occupancy.
+template <class K>
+static cudaError_t persistent_grid(K kernel, int block, int* grid) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0);
+  if (e != cudaSuccess) return e;
+  *grid = nsm * (occ > 0 ? occ : 1);
+  return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t launch_sweep(const AdjParams& P, cudaStream_t stream) {
+  int grid = 0;
+  cudaError_t e = persistent_grid(adjoint_sweep_kernel<T>, SWEEP_BLOCK, &grid);
+  if (e != cudaSuccess) return e;
+  adjoint_sweep_kernel<T><<<grid, SWEEP_BLOCK, 0, stream>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_tape(const AdjLaunch& a, cudaStream_t stream) {
+  const AdjParams P = adj_params(a);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // longest first
+  int64_t og = (a.n + 255) / 256;
+  if (og > (int64_t)nsm * 4) og = (int64_t)nsm * 4;
+  if ((e = cudaMemsetAsync(a.bucket, 0, 32 * sizeof(unsigned long long), stream)) != cudaSuccess)
+    return e;
+  order_count_kernel<<<(unsigned)og, 256, 0, stream>>>(a.nacc, a.n, a.bucket);
+  order_scan_kernel<<<1, 32, 0, stream>>>(a.bucket);
+  order_scatter_kernel<<<(unsigned)og, 256, 0, stream>>>(a.nacc, a.n, a.bucket, a.order);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the replay onto the tape
+  int grid = 0;
+  if ((e = persistent_grid(adjoint_tape_kernel, TAPE_BLOCK, &grid)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
+    return e;
+  adjoint_tape_kernel<<<grid, TAPE_BLOCK, 0, stream>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the reverse sweep
+  if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
+    return e;
+  if (a.prec == PREC_MIXED)
+    e = launch_sweep<float>(P, stream);
+  else if (a.prec == PREC_DF)
+    e = launch_sweep<DF>(P, stream);
+  else
+    e = launch_sweep<double>(P, stream);
+  if (e != cudaSuccess) return e;
+  return launch_sums(a, stream);
 }
 
 }  // namespace rtk

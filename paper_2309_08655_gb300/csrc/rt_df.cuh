@@ -103,6 +103,11 @@ RT_HD __forceinline__ DF& operator-=(DF& a, DF b) {
 RT_HD __forceinline__ bool operator<(DF a, DF b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
+RT_HD __forceinline__ bool operator>(DF a, DF b) { return b < a; }
+RT_HD __forceinline__ bool operator<=(DF a, DF b) { return !(b < a); }
+RT_HD __forceinline__ bool operator>=(DF a, DF b) { return !(a < b); }
+RT_HD __forceinline__ bool operator==(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
+RT_HD __forceinline__ bool operator!=(DF a, DF b) { return !(a == b); }
 
 // hi is the rounding of hi + lo to FP32
 RT_HD __forceinline__ float df_f(DF a) { return a.hi; }
@@ -131,6 +136,8 @@ RT_HD __forceinline__ DF df_sqrt(DF x) {
   const DF r = x - df_two_prod(y, y);
   return df_fast_sum(y, r.hi * 0.5f / y);
 }
+RT_HD __forceinline__ DF operator/(DF a, DF b) { return df_div(a, b); }
+RT_HD __forceinline__ DF rt_sqrt(DF x) { return df_sqrt(x); }
 
 // x^(-1/5) for x in [1e-6, 1e6] (the step-size controller's power): the FP32
 // estimate y corrected by the series of (1 - r)^(-1/5) in the residual

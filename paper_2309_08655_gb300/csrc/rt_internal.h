@@ -182,7 +182,7 @@ cudaError_t launch_ts_reset(unsigned long long* ts, int n, cudaStream_t stream);
 // Adjoint of the line-flux functional (rt_adjoint.cu).  Parameters, in
 // order: m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad];
 // the first NSAMP_TANGENTS move the sampling.
-enum { PREC_FP64 = 0, PREC_MIXED = 1 };   // the values of RT_PREC_*
+enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_DF = 2 };   // the values of RT_PREC_*
 enum { PAR_MA = 0, PAR_B0, PAR_THM, PAR_M, PAR_R, PAR_INCL, NPARAMS };
 constexpr int NSAMP_TANGENTS = 5;
 constexpr int CK = 32;        // accepted steps per checkpoint
@@ -190,6 +190,21 @@ constexpr int CKREC = 13;     // doubles per checkpoint: y, h, h_resume, sig, fl
 // doubles per accepted step of a segment replay: y[6], h, sig, flags, spare,
 // and the step's seven stage derivatives K[7][6]
 constexpr int SEGREC = 10 + 7 * 6;
+// The full step tape (every accepted step of every ray held in device memory
+// at once, SEGREC doubles each): a ray with nacc forward steps gets
+// tape_slots(nacc) records, the last free one taking its final state.
+__host__ __device__ inline int64_t tape_slots(int32_t nacc) {
+  const int64_t a = nacc > 0 ? nacc : 0;
+  return a + a / 64 + 9;
+}
+// Per-ray head of the tape: the adjoint seed at the escape point (6), its
+// r_s part, K, dm/dtheta_m (3), the number of records (-1: no gradient), the
+// sampling tangents (5 x (x 3, k 3, w)), omega_inf^2, its inverse, m (3).
+constexpr int HEADREC = 52;
+enum {
+  HD_YBAR = 0, HD_RSBAR = 6, HD_K = 7, HD_DM = 8, HD_NREC = 11, HD_TAN = 12, HD_W2 = 47,
+  HD_IW2 = 48, HD_M = 49
+};
 
 struct AdjLaunch {
   const StarDev* star;                          // host descriptor
@@ -203,6 +218,15 @@ struct AdjLaunch {
   const int64_t* ck_off;
   double* ck;
   double* seg;
+  // full-tape mode: tape_off[i] = first record of ray i; head: HEADREC
+  // doubles per ray; order: the rays, longest first (n), built from nacc with
+  // the 32 counters of bucket
+  const int64_t* tape_off;
+  double* tape;
+  double* head;
+  const int32_t* nacc;
+  int64_t* order;
+  unsigned long long* bucket;
   double* F_ray;
   double* G_ray;
   uint8_t* status;
@@ -211,7 +235,7 @@ struct AdjLaunch {
   unsigned long long* queue;
   double* grad;    // NPARAMS
   double* F;       // 1
-  int prec;        // PREC_FP64: FP64 reverse sweep; PREC_MIXED: FP32 reverse sweep
+  int prec;        // reverse sweep in PREC_FP64, PREC_MIXED (FP32) or PREC_DF (double-float)
   int grid, block;
 };
 cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* state,
@@ -219,6 +243,9 @@ cudaError_t launch_flux_value(const StarDev* d_star, int64_t n, const double* st
                               double kappa, double knorm, double* F_ray, double* F_total,
                               cudaStream_t stream);
 cudaError_t launch_ck_offsets(const int32_t* nacc, int64_t n, int64_t* off, cudaStream_t stream);
+cudaError_t launch_tape_offsets(const int32_t* nacc, int64_t n, int64_t* off, cudaStream_t stream);
+// the full-tape gradient: longest-first order, tape kernel, sweep kernel, sums
+cudaError_t launch_adjoint_tape(const AdjLaunch& a, cudaStream_t stream);
 cudaError_t adjoint_grid(int prec, int* grid, int* block);
 cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream);
 

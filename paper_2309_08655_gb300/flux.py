@@ -18,7 +18,7 @@ import torch
 from . import rt
 
 PARAM_NAMES = ("m_a_eV", "B0_G", "theta_m", "M_sun", "R_km", "incl")
-_GRAD_PREC = {"fp64": rt.PREC_FP64, "fp32": rt.PREC_MIXED}
+_GRAD_PREC = {"fp64": rt.PREC_FP64, "df": rt.PREC_DF, "fp32": rt.PREC_MIXED}
 
 
 def _star(params: torch.Tensor, base: dict) -> tuple[rt.Star, float]:

@@ -122,7 +122,8 @@ def lib():
         L.rt_flux_gradient.restype = ctypes.c_int
         L.rt_flux_gradient.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_double,
                                        ctypes.c_double, ctypes.POINTER(rt_trace_opts), _vp, _vp,
-                                       _vp, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+                                       _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                       _vp]
         L.rt_timestamps_reset.restype = ctypes.c_int
         L.rt_timestamps_reset.argtypes = [_vp, ctypes.c_int32, _vp]
         L.rt_batch_graph_create.restype = ctypes.c_int
@@ -374,15 +375,18 @@ def rt_flux_value(star: Star, n, state, weight, status, incl_rad, kappa, F_ray, 
 
 
 def rt_flux_gradient(star: Star, n, uniforms, nacc, incl_rad, kappa, grad, F, status=None,
-                     counters=None, opts: rt_trace_opts | None = None, stream=None) -> int:
-    """Returns the checkpoint bytes used."""
+                     counters=None, opts: rt_trace_opts | None = None, stream=None,
+                     tape_max_bytes: int = -1) -> int:
+    """Returns the bytes of the store used (the full step tape, or the
+    checkpoints when the tape exceeds ``tape_max_bytes``; -1: half of the free
+    device memory, 0: checkpoints always)."""
     if opts is None:
         opts = make_opts()
     nbytes = ctypes.c_int64(0)
     _check(lib().rt_flux_gradient(star.handle, int(n), _ptr(uniforms), _ptr(nacc),
                                   float(incl_rad), float(kappa), ctypes.byref(opts), _ptr(grad),
-                                  _ptr(F), _ptr(status), _ptr(counters), ctypes.byref(nbytes),
-                                  _stream(stream)))
+                                  _ptr(F), _ptr(status), _ptr(counters), int(tape_max_bytes),
+                                  ctypes.byref(nbytes), _stream(stream)))
     return int(nbytes.value)
 
 

@@ -16,7 +16,9 @@ impact parameters up to 50 R, in the requested precision (one warm-up launch
 on an image of at most 32 x 32 pixels first).
 Adjoint: n rays of the misaligned magnetar-like star at m_a = 1e-5 eV, the
 smoothed line flux toward 1.1 rad (kappa 4) and its gradient (one warm-up
-gradient on 256 rays first).  Prints the trace time and step counts.
+gradient on 256 rays first), the backward sweep in the requested precision,
+on the full step tape or (--store checkpoints) the checkpointed recompute.
+Prints the trace time and step counts.
 """
 from __future__ import annotations
 
@@ -34,6 +36,8 @@ from paper_2309_08655_gb300.build import build
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--precision", choices=["fp64", "mixed", "df"], default="fp64")
+    ap.add_argument("--store", choices=["tape", "checkpoints"], default="tape",
+                    help="adjoint mode: the full step tape or the checkpointed recompute")
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--rtol", type=float, default=None)
     ap.add_argument("--config", choices=["config0", "config1"], default="config0")
@@ -123,18 +127,27 @@ def adjoint(a, dev):
     F2 = torch.empty(1, dtype=torch.float64, device=dev)
     uw = torch.from_numpy(I.sample_uniforms(4, 256)).to(dev)
     Fw, nw, sw, iw, ow = flux.flux_forward(p, kw, uw, 4.0)
-    rt.rt_flux_gradient(sw, 256, uw, nw, iw, 4.0, grad, F2, opts=ow)      # warm-up
+    # the backward sweep's arithmetic: --precision fp64, df or mixed (FP32)
+    prec = {"fp64": rt.PREC_FP64, "mixed": rt.PREC_MIXED, "df": rt.PREC_DF}[a.precision]
+    og = rt.make_opts(rtol=ow.rtol, precision=prec)
+    tmb = -1 if a.store == "tape" else 0
+    rt.rt_flux_gradient(sw, 256, uw, nw, iw, 4.0, grad, F2, opts=og,
+                        tape_max_bytes=tmb)      # warm-up
     u = torch.from_numpy(I.sample_uniforms(4, a.n)).to(dev)
     F, nacc, star, incl, opts = flux.flux_forward(p, kw, u, 4.0)
     ctr = torch.zeros(8, dtype=torch.int64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    nb = rt.rt_flux_gradient(star, a.n, u, nacc, incl, 4.0, grad, F2, counters=ctr, opts=opts)
+    nb = rt.rt_flux_gradient(star, a.n, u, nacc, incl, 4.0, grad, F2, counters=ctr, opts=og,
+                             tape_max_bytes=tmb)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "adjoint", "rays": a.n, "gradient_ms": e0.elapsed_time(e1),
-                      "replayed_attempts": int(ctr.cpu()[0]), "checkpoint_bytes": nb,
+    na = nacc.cpu().numpy()
+    print(json.dumps({"mode": "adjoint", "precision": a.precision, "store": a.store,
+                      "rays": a.n, "gradient_ms": e0.elapsed_time(e1),
+                      "replayed_attempts": int(ctr.cpu()[0]), "store_bytes": nb,
+                      "nacc_max": int(na.max()), "nacc_mean": float(na.mean()),
                       "F": float(F.cpu()[0]), "grad": grad.cpu().tolist()}))
 
 

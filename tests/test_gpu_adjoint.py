@@ -198,3 +198,71 @@ def test_adjoint_matches_oracle_at_the_benchmark_kappa(oracle):
     rel = np.abs(g_adj - g_or) / np.maximum(np.abs(g_or), 1e-300)
     print("kappa = (64/pi)^2: adjoint", g_adj, "oracle FD", g_or, "rel", rel)
     assert np.all(rel < 1e-4), (g_adj, g_or, rel)
+
+
+def _gradient(kw, u, prec, tape_max_bytes=-1, incl=1.1, kappa=KAPPA):
+    """dF/dp through the C ABI with the sweep in `prec`; the store's bytes
+    and the counters."""
+    n = u.shape[1]
+    F0, nacc, star, incl_r, _ = flux.flux_forward(_p0(kw, incl=incl), kw, u, kappa)
+    grad = torch.empty(6, dtype=torch.float64, device=G.dev())
+    F2 = torch.empty(1, dtype=torch.float64, device=G.dev())
+    ctr = torch.zeros(8, dtype=torch.int64, device=G.dev())
+    nbytes = rt.rt_flux_gradient(star, n, u, nacc, incl_r, kappa, grad, F2, counters=ctr,
+                                 opts=rt.make_opts(rtol=1e-10, precision=prec),
+                                 tape_max_bytes=tape_max_bytes)
+    torch.cuda.synchronize()
+    return (grad.cpu().numpy(), float(F2.cpu()[0]), float(F0.cpu()[0]), nbytes,
+            ctr.cpu().numpy(), nacc)
+
+
+def test_full_tape_and_checkpoints_give_the_same_gradient():
+    """The full step tape (one replay) and the checkpointed recompute (a
+    replay per segment more) take the same FP64 steps: the same F and
+    gradient to rounding (the kernels contract multiply-adds differently, and
+    a segment restarts from its checkpoint with the right-hand side
+    re-evaluated; the sum over rays cancels, so a component can lose a few
+    digits).  The tape's size is the documented 416 B per slot plus 424 B
+    per ray."""
+    kw = _base()
+    n = 2048
+    u = torch.from_numpy(I.sample_uniforms(9, n)).to(G.dev())
+    gt, Ft, F0, bt, ct, nacc = _gradient(kw, u, rt.PREC_FP64)
+    gc, Fc, _, bc, cc, _ = _gradient(kw, u, rt.PREC_FP64, tape_max_bytes=0)
+    assert abs(Ft - Fc) <= 1e-14 * abs(Fc)
+    assert abs(Ft - F0) <= 1e-13 * abs(F0)
+    rel = np.abs(gt - gc) / np.abs(gc)
+    assert np.all(rel < 1e-7), rel
+    na = nacc.cpu().numpy().astype(np.int64)
+    slots = na + na // 64 + 9
+    assert bt == int(slots.sum()) * 416 + n * 424
+    assert bc == int((na // 32 + 2).sum()) * 104
+    # one replay against two: the first replay's attempts are counted by both
+    assert ct[0] == cc[0] and ct[2] == cc[2] == n and ct[4] == cc[4] == 0
+
+
+def test_full_tape_gradient_is_deterministic():
+    """The longest-first order within a bucket follows the atomics; no ray's
+    result depends on it and the sums run in index order: bit for bit."""
+    kw = _base()
+    u = torch.from_numpy(I.sample_uniforms(10, 3000)).to(G.dev())
+    g1 = _gradient(kw, u, rt.PREC_FP64)[0]
+    g2 = _gradient(kw, u, rt.PREC_FP64)[0]
+    assert np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("store", ["tape", "checkpoints"])
+def test_double_float_sweep_matches_fp64_sweep(store):
+    """The double-float backward sweep (RT_PREC_DF; ~48-bit rounding on the
+    FP32 pipe) over the same FP64 replay: within 1e-8 relative of the FP64
+    sweep per component at the benchmark's kappa (the FP32 sweep's error is
+    ~1e-4 there), and the same F (the replay is the same kernel)."""
+    kappa = (64.0 / math.pi) ** 2
+    kw = _base()
+    u = torch.from_numpy(I.sample_uniforms(11, 4096)).to(G.dev())
+    tmb = -1 if store == "tape" else 0
+    g64, F64, _, _, _, _ = _gradient(kw, u, rt.PREC_FP64, tmb, kappa=kappa)
+    gdf, Fdf, _, _, _, _ = _gradient(kw, u, rt.PREC_DF, tmb, kappa=kappa)
+    assert F64 == Fdf
+    rel = np.abs(gdf - g64) / np.abs(g64)
+    assert np.all(rel < 1e-8), (g64, gdf, rel)
