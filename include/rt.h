@@ -446,7 +446,7 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *   implicit function theorem).  Status, escape and the number of steps are
  *   held fixed (the gradient of the discrete scheme at frozen decisions).
  *   Store: the full step tape (every accepted step with its seven stages,
- *   416 B, plus 424 B per ray) when it fits under tape_max_bytes: one replay
+ *   416 B, plus 488 B per ray) when it fits under tape_max_bytes: one replay
  *   records the rays, longest first, and a second kernel sweeps them
  *   backwards; else a checkpoint every 32 accepted steps (sum over rays of
  *   (nacc/32 + 2) x 104 B) and segment scratch (13 KB per resident thread:

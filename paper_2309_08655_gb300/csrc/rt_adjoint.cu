@@ -694,28 +694,27 @@ __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
 
 constexpr int TAPE_BLOCK = 128;
 constexpr int SWEEP_BLOCK = 128;
+// a warp of the replay claims new rays once this many of its lanes are free
+// (the FP64 forward kernels' default)
+constexpr int TAPE_REFILL = 8;
 
-struct TapeStart {
-  Lane L;
-  double w;
-  bool ok;
-};
-
-// Samples ray i with its tangents, writes its head record (tangents, dm, the
-// ray's constants) and returns the lane ready for the replay (not inlined: it
-// runs once per ray, and its dual-number sampling is long).
-__device__ __noinline__ TapeStart tape_begin(const AdjParams& P, int64_t i) {
-  TapeStart t;
+// Samples ray i with its tangents and writes its head record: tangents, dm,
+// the ray's constants, the initial state and the weight (one thread per ray,
+// ahead of the replay, so that the replay's lanes do not wait on one
+// another's dual-number sampling).
+__global__ void __launch_bounds__(128) adjoint_sample_kernel(AdjParams P) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= P.n) return;
   SampOut<Dual<NSAMP_TANGENTS>> so;
   SampOut<double> sv;
+  Lane L;
   double cps, sps;
   double* hd = P.head + i * HEADREC;
-  t.ok = begin_ray(P, i, so, sv, t.L, cps, sps);
-  t.w = sv.w;
-  if (!t.ok) {
+  if (!begin_ray(P, i, so, sv, L, cps, sps)) {
     hd[HD_NREC] = -1.0;
-    return t;
+    return;
   }
+  hd[HD_NREC] = 0.0;
 #pragma unroll
   for (int k = 0; k < NSAMP_TANGENTS; ++k) {
 #pragma unroll
@@ -728,12 +727,41 @@ __device__ __noinline__ TapeStart tape_begin(const AdjParams& P, int64_t i) {
   hd[HD_DM + 0] = P.cos_tm * cps;
   hd[HD_DM + 1] = P.cos_tm * sps;
   hd[HD_DM + 2] = -P.sin_tm;
-  hd[HD_W2] = t.L.c.W2;
-  hd[HD_IW2] = t.L.c.iW2;
-  hd[HD_M + 0] = t.L.c.m0;
-  hd[HD_M + 1] = t.L.c.m1;
-  hd[HD_M + 2] = t.L.c.m2;
-  return t;
+  hd[HD_W2] = L.c.W2;
+  hd[HD_IW2] = L.c.iW2;
+  hd[HD_M + 0] = L.c.m0;
+  hd[HD_M + 1] = L.c.m1;
+  hd[HD_M + 2] = L.c.m2;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) hd[HD_Y0 + j] = L.y[j];
+  hd[HD_W] = sv.w;
+}
+
+// The lane of ray i from its head record, exactly as begin_ray leaves it.
+__device__ __forceinline__ void tape_load(const AdjParams& P, const double* hd, Lane& L) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) L.y[j] = hd[HD_Y0 + j];
+  L.R_km = P.R_km;
+  L.ma_eV = P.ma_eV;
+  L.c.rs = P.rs_prop;
+  L.c.cp = P.cp;
+  L.c.pa = P.plasma_a;
+  L.c.W2 = hd[HD_W2];
+  L.c.iW2 = hd[HD_IW2];
+  L.c.m0 = hd[HD_M + 0];
+  L.c.m1 = hd[HD_M + 1];
+  L.c.m2 = hd[HD_M + 2];
+  L.c.disp = P.dispersion;
+  L.c.plasma = P.plasma;
+  L.c.sig = gj_side<double>(L.c.m0, L.c.m1, L.c.m2, L.y[0], L.y[1], L.y[2]);
+  L.switching = false;
+  L.h_resume = 0.0;
+  rhs64(L.c, L.y, L.f0);
+  L.h = initial_step(L.c, L.y, L.f0, P.rtol, P.atol, 1e30);
+  L.lam = 0.0;
+  L.na = 0;
+  L.nr = 0;
+  L.last_rej = false;
 }
 
 // The end of ray i's replay: status, the escape flag and the final state on
@@ -781,13 +809,13 @@ __global__ void __launch_bounds__(TAPE_BLOCK) adjoint_tape_kernel(AdjParams P) {
   ClaimChunk ch;
   long long steps = 0, rays = 0;
   for (;;) {
-    claim_items(P.queue, P.n, 1, 1, item, ch, [&](int64_t e) -> int64_t {
+    claim_items(P.queue, P.n, TAPE_REFILL, 1, item, ch, [&](int64_t e) -> int64_t {
       const int64_t i = P.order[e];
       ++rays;
-      const TapeStart t = tape_begin(P, i);
-      if (!t.ok) return -1;
-      L = t.L;
-      w = t.w;
+      const double* hd = P.head + i * HEADREC;
+      if (hd[HD_NREC] < 0.0) return -1;   // no conversion point
+      tape_load(P, hd, L);
+      w = hd[HD_W];
       rh.seg = P.tape + P.tape_off[i] * SEGREC;
       rh.cap = (int)(P.tape_off[i + 1] - P.tape_off[i] - 1);
       rh.nrec = 0;
@@ -1228,6 +1256,9 @@ cudaError_t launch_adjoint_tape(const AdjLaunch& a, cudaStream_t stream) {
   order_count_kernel<<<(unsigned)og, 256, 0, stream>>>(a.nacc, a.n, a.bucket);
   order_scan_kernel<<<1, 32, 0, stream>>>(a.bucket);
   order_scatter_kernel<<<(unsigned)og, 256, 0, stream>>>(a.nacc, a.n, a.bucket, a.order);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // sampling with tangents, one thread per ray
+  adjoint_sample_kernel<<<(unsigned)((a.n + 127) / 128), 128, 0, stream>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // the replay onto the tape
   int grid = 0;

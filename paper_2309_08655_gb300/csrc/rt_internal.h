@@ -199,11 +199,12 @@ __host__ __device__ inline int64_t tape_slots(int32_t nacc) {
 }
 // Per-ray head of the tape: the adjoint seed at the escape point (6), its
 // r_s part, K, dm/dtheta_m (3), the number of records (-1: no gradient), the
-// sampling tangents (5 x (x 3, k 3, w)), omega_inf^2, its inverse, m (3).
-constexpr int HEADREC = 52;
+// sampling tangents (5 x (x 3, k 3, w)), omega_inf^2, its inverse, m (3), the
+// initial state (6) and the weight.
+constexpr int HEADREC = 60;
 enum {
   HD_YBAR = 0, HD_RSBAR = 6, HD_K = 7, HD_DM = 8, HD_NREC = 11, HD_TAN = 12, HD_W2 = 47,
-  HD_IW2 = 48, HD_M = 49
+  HD_IW2 = 48, HD_M = 49, HD_Y0 = 52, HD_W = 58
 };
 
 struct AdjLaunch {

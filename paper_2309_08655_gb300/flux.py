@@ -4,8 +4,9 @@
 with the given uniforms, traces every ray (FP64) and returns the von
 Mises-Fisher-smoothed line flux F toward the observer (rt_flux_value).  Its
 backward pass calls rt_flux_gradient, the reverse-mode adjoint through the
-integrator with step checkpointing (``grad_precision="fp32"``: the backward
-sweep in FP32 over the same FP64 replay).  ``params`` is a float64 tensor
+integrator over a full step tape in device memory (checkpoints every 32 steps
+when the tape does not fit); ``grad_precision`` sets the backward sweep's
+arithmetic over the same FP64 replay: "fp64", "df" (double-float) or "fp32".  ``params`` is a float64 tensor
 (m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad]);
 ``base`` holds the other star parameters (``rt.make_params`` keywords).
 Every step runs in the CUDA library; torch supplies device memory and the

@@ -222,7 +222,7 @@ def test_full_tape_and_checkpoints_give_the_same_gradient():
     gradient to rounding (the kernels contract multiply-adds differently, and
     a segment restarts from its checkpoint with the right-hand side
     re-evaluated; the sum over rays cancels, so a component can lose a few
-    digits).  The tape's size is the documented 416 B per slot plus 424 B
+    digits).  The tape's size is the documented 416 B per slot plus 488 B
     per ray."""
     kw = _base()
     n = 2048
@@ -235,7 +235,7 @@ def test_full_tape_and_checkpoints_give_the_same_gradient():
     assert np.all(rel < 1e-7), rel
     na = nacc.cpu().numpy().astype(np.int64)
     slots = na + na // 64 + 9
-    assert bt == int(slots.sum()) * 416 + n * 424
+    assert bt == int(slots.sum()) * 416 + n * 488
     assert bc == int((na // 32 + 2).sum()) * 104
     # one replay against two: the first replay's attempts are counted by both
     assert ct[0] == cc[0] and ct[2] == cc[2] == n and ct[4] == cc[4] == 0
