@@ -454,9 +454,12 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *   before its sweep (one replay more).
  *   opts.precision sets the arithmetic of the backward sweep (stages, Jacobian
  *   products, adjoint accumulation), the replay being FP64 always:
- *   RT_PREC_FP64 FP64; RT_PREC_DF double-float (FP64-class rounding on the
- *   FP32 pipe); RT_PREC_MIXED FP32 (its error against the FP64 sweep is the
- *   FP32-vs-FP64 gradient error).
+ *   RT_PREC_FP64 FP64; RT_PREC_MIXED the adjoint of the state and its
+ *   Jacobian products in FP64, the tangents of the three constants of the
+ *   ray equations (r_s, the omega_p^2 coefficient, the magnetic axis) and
+ *   their products with the adjoint in FP32 (about 1e-5 from the FP64 sweep,
+ *   at half its cost); RT_PREC_DF double-float (FP64-class rounding on the
+ *   FP32 pipe; slower than FP64 here).
  *     d_grad     out: 6 float64, dF/dp
  *     d_F        out: 1 float64, F recomputed by the adjoint's replay
  *     d_status   out (may be NULL): n final statuses of the replay

@@ -184,6 +184,154 @@ __device__ __noinline__ void rhs_vjp(const RayConst<T>& c, const T* dm, const T*
   }
 }
 
+// Dual number of the mixed sweep: the value and the state-direction tangent in
+// FP64 (the tangent that carries the adjoint along the trajectory, where
+// rounding errors compound), an FP32 copy of the value from its own FP32
+// evaluation, and the NQ parameter tangents in FP32 (their products with the
+// adjoint only add up over the steps).  A product costs 3 FP64 operations
+// instead of the 9 of a four-tangent FP64 dual.
+struct HDual {
+  double v, d;
+  float vf;
+  float q[NQ];
+  HDual() = default;
+  __device__ HDual(int i) : v((double)i), d(0.0), vf((float)i) {  // NOLINT: constants
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) q[k] = 0.0f;
+  }
+  __device__ explicit HDual(double x) : v(x), d(0.0), vf((float)x) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) q[k] = 0.0f;
+  }
+};
+__device__ __forceinline__ HDual operator+(const HDual& a, const HDual& b) {
+  HDual r;
+  r.v = a.v + b.v;
+  r.d = a.d + b.d;
+  r.vf = a.vf + b.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = a.q[k] + b.q[k];
+  return r;
+}
+__device__ __forceinline__ HDual operator-(const HDual& a, const HDual& b) {
+  HDual r;
+  r.v = a.v - b.v;
+  r.d = a.d - b.d;
+  r.vf = a.vf - b.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = a.q[k] - b.q[k];
+  return r;
+}
+__device__ __forceinline__ HDual operator-(const HDual& a) {
+  HDual r;
+  r.v = -a.v;
+  r.d = -a.d;
+  r.vf = -a.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = -a.q[k];
+  return r;
+}
+__device__ __forceinline__ HDual operator*(const HDual& a, const HDual& b) {
+  HDual r;
+  r.v = a.v * b.v;
+  r.d = a.d * b.v + a.v * b.d;
+  r.vf = a.vf * b.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = a.q[k] * b.vf + a.vf * b.q[k];
+  return r;
+}
+__device__ __forceinline__ HDual& operator+=(HDual& a, const HDual& b) {
+  a = a + b;
+  return a;
+}
+__device__ __forceinline__ HDual& operator-=(HDual& a, const HDual& b) {
+  a = a - b;
+  return a;
+}
+__device__ __forceinline__ bool operator<(const HDual& a, const HDual& b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator>(const HDual& a, const HDual& b) { return a.v > b.v; }
+__device__ __forceinline__ HDual rt_rsqrt(const HDual& a) {
+  HDual r;
+  r.v = ::rtk::rt_rsqrt(a.v);
+  r.d = -0.5 * r.v * r.v * r.v * a.d;
+  r.vf = rsqrtf(a.vf);
+  const float cf = -0.5f * r.vf * r.vf * r.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = cf * a.q[k];
+  return r;
+}
+__device__ __forceinline__ HDual rt_sqrt(const HDual& a) {
+  HDual r;
+  r.v = sqrt(a.v);
+  r.d = 0.5 / r.v * a.d;
+  r.vf = sqrtf(a.vf);
+  const float cf = 0.5f / r.vf;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) r.q[k] = cf * a.q[k];
+  return r;
+}
+
+// rhs_vjp for the mixed sweep (HDual): J^T v in FP64, v . df/dq from the FP32
+// parameter tangents (summed in FP32 per stage, accumulated in FP64).
+__device__ __noinline__ void rhs_vjp_h(const RayConst<double>& c, const double* dm,
+                                       const double* y, const double* v, double* out,
+                                       double* qbar) {
+  RayConst<HDual> cd;
+  cd.rs = HDual(c.rs);
+  cd.rs.q[Q_RS] = 1.0f;
+  cd.cp = HDual(c.cp);
+  cd.cp.q[Q_CP] = 1.0f;
+  cd.pa = HDual(c.pa);
+  cd.W2 = HDual(c.W2);
+  cd.iW2 = HDual(c.iW2);
+  cd.m0 = HDual(c.m0);
+  cd.m1 = HDual(c.m1);
+  cd.m2 = HDual(c.m2);
+  cd.m0.q[Q_THM] = (float)dm[0];
+  cd.m1.q[Q_THM] = (float)dm[1];
+  cd.m2.q[Q_THM] = (float)dm[2];
+  cd.sig = HDual(c.sig);
+  cd.disp = c.disp;
+  cd.plasma = c.plasma;
+  HDual yd[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    yd[j] = HDual(y[j]);
+    yd[j].d = v[3 + j];
+    yd[3 + j] = HDual(y[3 + j]);
+    yd[3 + j].d = -v[j];
+  }
+  HDual f[6];
+  ham_rhs<HDual>(cd, yd[0], yd[1], yd[2], yd[3], yd[4], yd[5], f[0], f[1], f[2], f[3], f[4],
+                 f[5]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    out[j] = f[3 + j].d;
+    out[3 + j] = -f[j].d;
+  }
+  float vf[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) vf[j] = (float)v[j];
+#pragma unroll
+  for (int m = 0; m < NQ; ++m) {
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) s += vf[j] * f[j].q[m];
+    qbar[m] += (double)s;
+  }
+}
+
+// The Jacobian product of the sweep: four-tangent duals in T, or (HYB, T =
+// double) the mixed HDual.
+template <bool HYB, class T>
+__device__ __forceinline__ void vjp(const RayConst<T>& c, const T* dm, const T* y, const T* v,
+                                    T* out, T* qbar) {
+  if constexpr (HYB)
+    rhs_vjp_h(c, dm, y, v, out, qbar);
+  else
+    rhs_vjp(c, dm, y, v, out, qbar);
+}
+
 // Adjoint of a branch switch at y from sig_old to -sig_old:
 // ybar <- S^T ybar, and the crossing's dependence on the magnetic axis.
 template <class T>
@@ -214,13 +362,14 @@ __device__ void saltation(RayConst<T> c, const T* dm, const T* y, T sig_old, T* 
 }
 
 // Discrete adjoint of one accepted Dormand-Prince step from y with step h, in
-// the scalar type T (double: the FP64 sweep; float: the single-precision
-// sweep; DF: the double-float sweep), from the step's FP64 record (its seven
-// stage derivatives K, as the replay formed them).
+// the scalar type T (double: the FP64 sweep, or with HYB the mixed sweep whose
+// Jacobian products take FP32 parameter tangents; DF: the double-float
+// sweep), from the step's FP64 record (its seven stage derivatives K, as the
+// replay formed them).
 // ybar: in, the adjoint at the step's end (unused when escape); out, at y.
 // Escape: the step ends at the theta* of the continuous extension where
 // |x| = r_out, and ybar_e is the adjoint there.
-template <class T>
+template <class T, bool HYB = false>
 __device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
                              const double* Krec, bool escape, T r_out, const T* ybar_e, T* ybar,
                              T* qbar) {
@@ -303,7 +452,7 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
       ynb[i] = r2b[i];
       yb[i] -= r2b[i];
     }
-    rhs_vjp(c, dm, yn, kb[6], t, qbar);
+    vjp<HYB>(c, dm, yn, kb[6], t, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) ynb[i] += t[i];
   } else {
@@ -341,7 +490,7 @@ __device__ void step_adjoint(const RayConst<T>& c, const T* dm, const T* y, T h,
       for (int j = 0; j < s; ++j) acc += A[s][j] * K[j][i];
       Ys[i] = (s == 0) ? y[i] : y[i] + h * acc;
     }
-    rhs_vjp(c, dm, Ys, kb[s], Yb, qbar);
+    vjp<HYB>(c, dm, Ys, kb[s], Yb, qbar);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       yb[i] += Yb[i];
@@ -533,7 +682,7 @@ __device__ bool begin_ray(const AdjParams& P, int64_t i, SampOut<Dual<NSAMP_TANG
 // Checkpointed recompute: one replay storing a checkpoint every CK accepted
 // steps, then segment by segment (last first) a replay of the segment that
 // records its steps and the reverse sweep over them.
-template <class T>
+template <class T, bool HYB = false>
 __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long long* steps) {
   const int64_t n = P.n;
   SampOut<Dual<NSAMP_TANGENTS>> so;
@@ -640,8 +789,8 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
         }
         saltation(cj, dm, yn, T(r[7]), yb, qb);
       }
-      step_adjoint(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb,
-                   qb);
+      step_adjoint<T, HYB>(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out),
+                           ye, yb, qb);
       if (fl & FL_FLIP_BEFORE) saltation(cj, dm, y, T(-r[7]), yb, qb);
     }
   }
@@ -667,7 +816,7 @@ __device__ void adjoint_ray(const AdjParams& P, int64_t i, double* seg, long lon
   for (int k = 0; k < NPARAMS; ++k) P.G_ray[k * n + i] = G[k];
 }
 
-template <class T>
+template <class T, bool HYB = false>
 __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double* seg = P.seg + tid * (int64_t)CK * SEGREC;
@@ -675,7 +824,7 @@ __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
   for (;;) {
     const int64_t i = (int64_t)atomicAdd(P.queue, 1ull);
     if (i >= P.n) break;
-    adjoint_ray<T>(P, i, seg, &steps);
+    adjoint_ray<T, HYB>(P, i, seg, &steps);
     ++rays;
   }
   if (P.counters) {
@@ -874,7 +1023,7 @@ __device__ __noinline__ void sweep_finish(const AdjParams& P, int64_t i, const T
   for (int k = 0; k < NSAMP_TANGENTS; ++k) P.G_ray[k * n + i] = G[k];
 }
 
-template <class T>
+template <class T, bool HYB = false>
 __global__ void __launch_bounds__(SWEEP_BLOCK) adjoint_sweep_kernel(AdjParams P) {
   constexpr unsigned FULL = 0xffffffffu;
   int64_t item = -1;
@@ -931,8 +1080,8 @@ __global__ void __launch_bounds__(SWEEP_BLOCK) adjoint_sweep_kernel(AdjParams P)
           for (int q = 0; q < 6; ++q) yn[q] = T(r[SEGREC + q]);
           saltation(cj, dm, yn, T(r[7]), yb, qb);
         }
-        step_adjoint(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out), ye, yb,
-                     qb);
+        step_adjoint<T, HYB>(cj, dm, y, T(r[6]), r + SEG_K, (fl & FL_ESCAPE) != 0, T(P.r_out),
+                             ye, yb, qb);
         if (fl & FL_FLIP_BEFORE) saltation(cj, dm, y, T(-r[7]), yb, qb);
         --j;
       }
@@ -1113,7 +1262,8 @@ cudaError_t adjoint_grid(int prec, int* grid, int* block) {
   if (e != cudaSuccess) return e;
   *block = 64;
   e = (prec == PREC_MIXED)
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<float>, *block, 0)
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<double, true>,
+                                                          *block, 0)
       : (prec == PREC_DF)
           ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<DF>, *block, 0)
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<double>, *block, 0);
@@ -1202,7 +1352,7 @@ cudaError_t launch_adjoint(const AdjLaunch& a, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
   if (a.prec == PREC_MIXED)
-    adjoint_kernel<float><<<a.grid, a.block, 0, stream>>>(P);
+    adjoint_kernel<double, true><<<a.grid, a.block, 0, stream>>>(P);
   else if (a.prec == PREC_DF)
     adjoint_kernel<DF><<<a.grid, a.block, 0, stream>>>(P);
   else
@@ -1232,12 +1382,12 @@ static cudaError_t persistent_grid(K kernel, int block, int* grid) {
   return cudaSuccess;
 }
 
-template <class T>
+template <class T, bool HYB = false>
 static cudaError_t launch_sweep(const AdjParams& P, cudaStream_t stream) {
   int grid = 0;
-  cudaError_t e = persistent_grid(adjoint_sweep_kernel<T>, SWEEP_BLOCK, &grid);
+  cudaError_t e = persistent_grid(adjoint_sweep_kernel<T, HYB>, SWEEP_BLOCK, &grid);
   if (e != cudaSuccess) return e;
-  adjoint_sweep_kernel<T><<<grid, SWEEP_BLOCK, 0, stream>>>(P);
+  adjoint_sweep_kernel<T, HYB><<<grid, SWEEP_BLOCK, 0, stream>>>(P);
   return cudaGetLastError();
 }
 
@@ -1271,7 +1421,7 @@ cudaError_t launch_adjoint_tape(const AdjLaunch& a, cudaStream_t stream) {
   if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
     return e;
   if (a.prec == PREC_MIXED)
-    e = launch_sweep<float>(P, stream);
+    e = launch_sweep<double, true>(P, stream);
   else if (a.prec == PREC_DF)
     e = launch_sweep<DF>(P, stream);
   else

@@ -6,7 +6,8 @@ Mises-Fisher-smoothed line flux F toward the observer (rt_flux_value).  Its
 backward pass calls rt_flux_gradient, the reverse-mode adjoint through the
 integrator over a full step tape in device memory (checkpoints every 32 steps
 when the tape does not fit); ``grad_precision`` sets the backward sweep's
-arithmetic over the same FP64 replay: "fp64", "df" (double-float) or "fp32".  ``params`` is a float64 tensor
+arithmetic over the same FP64 replay: "fp64", "mixed" (FP64 adjoint, FP32
+tangents of the ray equations' constants) or "df" (double-float).  ``params`` is a float64 tensor
 (m_a [eV], B0 [G], theta_m [rad], M [Msun], R [km], inclination [rad]);
 ``base`` holds the other star parameters (``rt.make_params`` keywords).
 Every step runs in the CUDA library; torch supplies device memory and the
@@ -19,7 +20,7 @@ import torch
 from . import rt
 
 PARAM_NAMES = ("m_a_eV", "B0_G", "theta_m", "M_sun", "R_km", "incl")
-_GRAD_PREC = {"fp64": rt.PREC_FP64, "df": rt.PREC_DF, "fp32": rt.PREC_MIXED}
+_GRAD_PREC = {"fp64": rt.PREC_FP64, "df": rt.PREC_DF, "mixed": rt.PREC_MIXED}
 
 
 def _star(params: torch.Tensor, base: dict) -> tuple[rt.Star, float]:

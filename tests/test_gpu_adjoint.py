@@ -144,22 +144,25 @@ def test_gradient_rejects_unsupported_models():
         rt.rt_flux_gradient(star, n, u, nacc, 1.0, KAPPA, g, F)
 
 
-def test_fp32_sweep_close_to_fp64_sweep():
-    """The single-precision backward sweep (RT_PREC_MIXED) over the same FP64
-    replay: the same F, and every gradient component within 1e-3 relative of
-    the FP64 sweep's (FP32 stage rounding and accumulation over ~10^3 steps)."""
+def test_mixed_sweep_close_to_fp64_sweep():
+    """The mixed backward sweep (RT_PREC_MIXED: the adjoint of the state in
+    FP64, the tangents of r_s, the omega_p^2 coefficient and the magnetic axis
+    in FP32) over the same FP64 replay: the same F, and every gradient
+    component within 1e-4 relative of the FP64 sweep's (FP32 rounding of the
+    parameter products, summed over ~10^3 stages a ray; 1.3e-5 worst at the
+    benchmark's 2^18 rays)."""
     kw = _base()
     n = 2048
     u = torch.from_numpy(I.sample_uniforms(4, n)).to(G.dev())
     g = {}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "mixed"):
         p = _p0(kw).requires_grad_(True)
         F = flux.line_flux(p, kw, u, KAPPA, grad_precision=prec)
         F.backward()
         g[prec] = p.grad.numpy().copy()
-    rel = np.abs(g["fp32"] - g["fp64"]) / np.abs(g["fp64"])
-    assert np.all(np.isfinite(g["fp32"]))
-    assert np.all(rel < 1e-3), (g, rel)
+    rel = np.abs(g["mixed"] - g["fp64"]) / np.abs(g["fp64"])
+    assert np.all(np.isfinite(g["mixed"]))
+    assert np.all(rel < 1e-4), (g, rel)
     # the replay (and so F) is FP64 in both
     F0, nacc, star, incl, _ = flux.flux_forward(_p0(kw), kw, u, KAPPA)
     grad = torch.empty(6, dtype=torch.float64, device=G.dev())
