@@ -44,12 +44,35 @@ constexpr double TWO_OVER_SQRTPI = 1.12837916709551257390;
 // (4/sqrt(pi)) x^2 exp(-x^2).  Lower half: erf(x) - c x e^{-x^2} = u; upper
 // half: erfc(x) + c x e^{-x^2} = 1 - u (exact for u >= 1/2), which keeps the
 // tail well conditioned.  Safeguarded Newton iteration.
+// The start of the FP64 iteration: the same safeguarded Newton iteration in
+// FP32 (FP32 exp, erf and erfc issue on the fast pipe) to ~1e-5.  Where FP32
+// cannot resolve the equation (u below ~1e-8: erf(x) and x e^{-x^2} cancel) the
+// FP64 iteration starts from a poor point and takes more steps, nothing else.
+__device__ __forceinline__ float maxwell_seed(bool upper, float v) {
+  const float c = (float)TWO_OVER_SQRTPI;
+  float lo = 0.0f, hi = 30.0f;
+  float x = 1.0876520317f;   // median
+  for (int it = 0; it < 40; ++it) {
+    const float ex = expf(-x * x);
+    const float q = upper ? erfcf(x) + c * x * ex : erff(x) - c * x * ex;
+    const float dq = 2.0f * c * x * x * ex * (upper ? -1.0f : 1.0f);
+    const bool below = upper ? (q > v) : (q < v);
+    if (below) lo = x; else hi = x;
+    float xn = x - (q - v) / dq;
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    if (fabsf(xn - x) <= 1e-5f * x || hi - lo <= 1e-6f * hi) return xn;
+    x = xn;
+  }
+  return x;
+}
+
 __device__ __forceinline__ double maxwell_speed(int fa_model, double u) {
   if (fa_model == FA_DELTA) return 1.0;
   const bool upper = u > 0.5;
   const double v = upper ? 1.0 - u : u;
   double lo = 0.0, hi = 30.0;
-  double x = 1.0876520317;   // median
+  double x = (double)maxwell_seed(upper, (float)v);
+  if (!(x > lo && x < hi)) x = 1.0876520317;   // median
   for (int it = 0; it < 200; ++it) {
     const double ex = exp(-x * x);
     const double q = upper ? erfc(x) + TWO_OVER_SQRTPI * x * ex
@@ -60,7 +83,9 @@ __device__ __forceinline__ double maxwell_speed(int fa_model, double u) {
     if (below) lo = x; else hi = x;
     double xn = x - (q - v) / dq;
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    if (fabs(xn - x) <= 2e-16 * x || hi - lo <= 4e-16 * hi) {
+    // converged: a Newton step of a few ulps (one of exactly 1-2 ulps can
+    // recur for ever where q - v is a rounding-level difference)
+    if (fabs(xn - x) <= 1e-15 * x || hi - lo <= 4e-16 * hi) {
       x = xn;
       break;
     }
@@ -99,6 +124,32 @@ __device__ __forceinline__ void line_plasma(const Line& L, double r, double& P, 
     }
     default: P = 0.0; dP = 0.0; break;
   }
+}
+
+// G and G' in FP32 for the start of the FP64 root iteration; omega_inf^2 - 1
+// (W2m1, a few 1e-6) is passed apart so that K2 keeps its FP32 precision.
+__device__ __forceinline__ float line_G32(const Line& L, float W2m1, float r, float* dG) {
+  const float ir = 1.0f / r;
+  float P = 0.0f, dP = 0.0f;
+  switch (L.plasma) {
+    case PLASMA_GJ: P = (float)L.PR * ir * ir * ir; dP = -3.0f * P * ir; break;
+    case PLASMA_HOMOG: P = (float)L.pa; break;
+    case PLASMA_LINEAR_Z: P = (float)L.pa * r * (float)L.nz; dP = (float)(L.pa * L.nz); break;
+    case PLASMA_RADIAL: P = (float)L.pa * ir * ir * ir; dP = -3.0f * P * ir; break;
+    case PLASMA_TWISTED: P = (float)L.PR * ir * ir * ir * ir; dP = -4.0f * P * ir; break;
+    default: break;
+  }
+  if (L.disp == DISP_ISO) {
+    *dG = dP;
+    return P - 1.0f;
+  }
+  const float rsr = (float)L.rs * ir;
+  const float A = 1.0f - rsr;
+  const float K2 = (W2m1 + rsr) / A;
+  const float s2 = (float)L.s2;
+  const float dK2 = -(1.0f + W2m1) * rsr * ir / (A * A);
+  *dG = dP * (1.0f + K2 * s2) + P * s2 * dK2 - dK2;
+  return P * (1.0f + K2 * s2) - (1.0f + K2);
 }
 
 __device__ __forceinline__ double line_G(const Line& L, double r, double* dG) {
@@ -273,15 +324,30 @@ __device__ void sample_core(const SampConst<T>& s, const double* u, double nsamp
     }
   }
   if (!o.ok) return;
-  // safeguarded Newton on G
+  // safeguarded Newton on G, from a start the same iteration finds in FP32
   double r = 0.5 * (lo + hi);
+  {
+    const float W2m1 = (float)(delta * (2.0 + delta));
+    float flo = (float)lo, fhi = (float)hi, fr = (float)r;
+    for (int it = 0; it < 40; ++it) {
+      float dG;
+      const float g = line_G32(L, W2m1, fr, &dG);
+      if (g > 0.0f) flo = fr; else fhi = fr;
+      float rn = fr - g / dG;
+      if (!(rn > flo && rn < fhi)) rn = 0.5f * (flo + fhi);
+      const bool done = fabsf(rn - fr) <= 1e-5f * fr || fhi - flo <= 1e-6f * fhi;
+      fr = rn;
+      if (done) break;
+    }
+    if ((double)fr > lo && (double)fr < hi) r = (double)fr;
+  }
   for (int it = 0; it < 200; ++it) {
     double dG;
     const double g = line_G(L, r, &dG);
     if (g > 0.0) lo = r; else hi = r;
     double rn = r - g / dG;
     if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
-    const bool done = fabs(rn - r) <= 1e-16 * r || hi - lo <= 4e-16 * hi;
+    const bool done = fabs(rn - r) <= 1e-15 * r || hi - lo <= 4e-16 * hi;
     r = rn;
     if (done) break;
   }
