@@ -90,12 +90,12 @@ def _measure_peaks(rt, stream):
 TRAFFIC = {
     # precision -> (sources, digest, kernel, bytes per traced ray)
     "fp64": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_trace.cu', 'rt_internal.h'),
-             "2b8c4e13855e2cb9", "trace_fp64_kernel", 332385536 / 2096328),
+             "ecbf401b4b0b6157", "trace_fp64_kernel", 334305792 / 2096328),
     "mixed": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_backward.cuh', 'rt_trace_mixed.cu',
                'rt_internal.h'),
-              "26743c2d92e573de", "trace_mixed_kernel", 250965248 / 2096328),
+              "3283184d3aa6675e", "trace_mixed_kernel", 249587456 / 2096328),
     "df": (('rt_device.cuh', 'rt_integrator.cuh', 'rt_df.cuh', 'rt_trace_df.cu', 'rt_internal.h'),
-           "fdd95867d784f634", "trace_df_kernel", 393602816 / 2096328),
+           "f6456f701275e339", "trace_df_kernel", 392003840 / 2096328),
 }
 
 
