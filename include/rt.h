@@ -467,7 +467,8 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *                replay), [2] rays, [4] rays left out (replay longer than
  *                d_nacc allows)
  *     tape_max_bytes  most device bytes the full tape may take (-1: half of
- *                the free device memory; 0: checkpoints always)
+ *                the free device memory; 0: checkpoints always); a tape whose
+ *                allocation fails falls back to the checkpoints
  *     store_bytes out (host, may be NULL): bytes of the tape or checkpoint store
  *   Needs RT_PLASMA_GJ, M_sun > 0 and B0_G > 0.  Synchronous: allocates the
  *   store and 69 B per ray, and frees them before returning; RT_ENOMEM if

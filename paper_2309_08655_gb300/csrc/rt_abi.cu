@@ -726,12 +726,25 @@ rt_status rt_flux_gradient(const rt_star* s, int64_t n, const double* d_uniforms
     }
     limit = (int64_t)(fr / 2);
   }
-  if (tape_bytes <= limit) {
-    if ((e = cudaMalloc(&tape, (size_t)total * rtk::SEGREC * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&head, (size_t)n * rtk::HEADREC * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&order, (size_t)n * sizeof(int64_t))) != cudaSuccess ||
-        (e = cudaMalloc(&bucket, 32 * sizeof(unsigned long long))) != cudaSuccess)
-      return alloc_fail(e, "step tape allocation failed");
+  bool use_tape = tape_bytes <= limit;
+  if (use_tape &&
+      ((e = cudaMalloc(&tape, (size_t)total * rtk::SEGREC * sizeof(double))) != cudaSuccess ||
+       (e = cudaMalloc(&head, (size_t)n * rtk::HEADREC * sizeof(double))) != cudaSuccess ||
+       (e = cudaMalloc(&order, (size_t)n * sizeof(int64_t))) != cudaSuccess ||
+       (e = cudaMalloc(&bucket, 32 * sizeof(unsigned long long))) != cudaSuccess)) {
+    if (e != cudaErrorMemoryAllocation) return alloc_fail(e, "step tape allocation failed");
+    // the tape did not fit after all (fragmentation): the checkpoints instead
+    cudaGetLastError();
+    cudaFree(tape);
+    cudaFree(head);
+    cudaFree(order);
+    cudaFree(bucket);
+    tape = head = nullptr;
+    order = nullptr;
+    bucket = nullptr;
+    use_tape = false;
+  }
+  if (use_tape) {
     if (store_bytes) *store_bytes = tape_bytes;
     a.tape_off = off;
     a.tape = tape;
