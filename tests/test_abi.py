@@ -99,3 +99,31 @@ def test_noalloc_rejects_bad_params_and_host_arrays_without_launch(L):
     assert f(ctypes.byref(good), 0, None, None, None, 4, 4, 4, 0.0, 9.0, hp, None, None, hp,
              None) == rt.RT_EINVAL                  # host output, no rays
     assert b"d_hist" in L.rt_last_error()
+
+
+def _declared_arities():
+    """Parameter counts of the functions include/rt.h declares (comments
+    stripped; `(void)` counts as none)."""
+    txt = open(os.path.join(ROOT, "include", "rt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    out = {}
+    for m in re.finditer(r"\b(rt_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt):
+        args = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_header(L):
+    """Every function the binding types takes as many arguments as rt.h
+    declares: a signature change on one side only fails here, on the CPU."""
+    ar = _declared_arities()
+    assert ar.get("rt_flux_gradient") == 14 and ar.get("rt_trace_forward") == 9
+    typed = 0
+    for name, n in ar.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            continue
+        typed += 1
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+    assert typed >= 20
