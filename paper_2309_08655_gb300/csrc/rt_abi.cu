@@ -1520,7 +1520,7 @@ rt_status rt_batch_autotune(rt_batch* b, const double* d_state, const uint8_t* d
   t.list = nullptr;
   t.list_n = nullptr;
   t.ts = nullptr;
-  // round 1 candidates: block sizes the kernel's launch bounds allow, every
+  // first-stage candidates: block sizes the kernel's launch bounds allow, every
   // resident count
   std::vector<std::pair<int, int>> cand;
   const int blocks[3] = {mixed ? 64 : 32, mixed ? 128 : 64, mixed ? 256 : 128};
