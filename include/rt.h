@@ -458,8 +458,8 @@ rt_status rt_trace_backward(const rt_star* star, int32_t nx, int32_t ny, double 
  *   Jacobian products in FP64, the tangents of the three constants of the
  *   ray equations (r_s, the omega_p^2 coefficient, the magnetic axis) and
  *   their products with the adjoint in FP32 (about 1e-5 from the FP64 sweep,
- *   at half its cost); RT_PREC_DF double-float (FP64-class rounding on the
- *   FP32 pipe; slower than FP64 here).
+ *   in half the FP64 sweep's time); RT_PREC_DF double-float (FP64-class
+ *   rounding on the FP32 pipe; slower than the FP64 sweep on GB300).
  *     d_grad     out: 6 float64, dF/dp
  *     d_F        out: 1 float64, F recomputed by the adjoint's replay
  *     d_status   out (may be NULL): n final statuses of the replay
