@@ -63,6 +63,11 @@ def test_version_and_error_paths_without_gpu(L):
     assert st == rt.RT_EINVAL
     st = L.rt_init_star(None, ctypes.byref(ctypes.c_void_p()))
     assert st == rt.RT_EINVAL and b"NULL" in L.rt_last_error()
+    # the gradient: a NULL star is refused before anything touches a GPU
+    nb = ctypes.c_int64(0)
+    st = L.rt_flux_gradient(None, 16, None, None, 1.0, 4.0, ctypes.byref(rt.make_opts()), None,
+                            None, None, None, -1, ctypes.byref(nb), None)
+    assert st == rt.RT_EINVAL and b"NULL" in L.rt_last_error()
 
 
 def test_objects_are_sm103a():
