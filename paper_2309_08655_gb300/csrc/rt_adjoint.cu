@@ -836,10 +836,12 @@ __global__ void __launch_bounds__(64) adjoint_kernel(AdjParams P) {
 // ---------------------------------------------------------------------------
 // Full step tape: every accepted step of every ray is held in device memory at
 // once (SEGREC doubles a step), so that each ray is replayed once.  Two
-// persistent kernels, each lane taking the next ray (longest first) as soon as
-// it is free: the tape kernel replays the rays in FP64, step by step, and
-// records them; the sweep kernel walks each ray's records backwards, one step
-// per iteration, so that the lanes of a warp run the same step adjoint.
+// persistent kernels claiming the rays longest first from a global queue: the
+// tape kernel replays them in FP64, one attempt per iteration, a warp claiming
+// new rays once TAPE_REFILL of its lanes are free, and records every accepted
+// step; the sweep kernel walks each ray's records backwards, one step per
+// iteration, a lane claiming its next ray as soon as it is free, so that the
+// lanes of a warp run the same step adjoint.
 
 constexpr int TAPE_BLOCK = 128;
 constexpr int SWEEP_BLOCK = 128;
